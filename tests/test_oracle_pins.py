@@ -1,0 +1,292 @@
+"""Pins of the CPU oracle against things other than itself (no GPU needed).
+
+Each test fixes part of the oracle by a closed form, a conservation law, a
+finite difference of the nonlinear forward model, brute force, a second
+independent solver, or an algebraic identity, so that a dropped term, a wrong
+sign or index, or a transposed operand fails at least one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.optimize as so
+import scipy.sparse.linalg as spla
+
+import workloads
+from oracle import born, model, sketch, solve
+
+
+# ---------------------------------------------------------------- operator (Section 2.2)
+
+def test_operator_is_symmetric_m_matrix():
+    p = workloads.small(nx=7, ny=6, nz=5)
+    A = model.operator(p, 0).toarray()
+    assert np.array_equal(A, A.T)
+    off = A - np.diag(np.diag(A))
+    assert (off <= 0).all()
+    # strictly diagonally dominant rows (absorption and boundary terms) -> SPD M-matrix
+    assert (np.diag(A) - np.abs(off).sum(axis=1) > 0).all()
+    assert np.linalg.eigvalsh(A).min() > 0
+
+
+def test_operator_stencil_counts():
+    """Interior cell: 6 neighbours at -D h, diagonal 6 D h + mu_a h^3 (no boundary term)."""
+    p = workloads.small(nx=5, ny=5, nz=5)
+    mua, D = model.wavelength_coefficients(p)
+    A = model.operator(p, 1).tocsr()
+    h = p.grid.h
+    c = p.grid.voxel(2, 2, 2)
+    row = A.getrow(c)
+    assert row.nnz == 7
+    assert math.isclose(A[c, c], 6 * D[1] * h + mua[1] * h ** 3, rel_tol=1e-14)
+    for nb in (c - 1, c + 1, c - 5, c + 5, c - 25, c + 25):
+        assert math.isclose(A[c, nb], -D[1] * h, rel_tol=1e-14)
+
+
+def test_robin_dirichlet_limit_and_corner_cell():
+    """A = 0 gives the Dirichlet face 2 D h; a corner cell has three boundary faces."""
+    assert math.isclose(model.face_coefficient(0.5, 2.0, 0.0), 2 * 0.5 * 2.0)
+    p = workloads.small(nx=4, ny=4, nz=4, n_src=1, n_det=1, robin_A=(0.0, 1.0, 2.0, 3.0, 4.0, 5.0))
+    mua, D = model.wavelength_coefficients(p)
+    A = model.operator(p, 0)
+    h, d = p.grid.h, D[0]
+    beta = [2 * d * h * h / (h + 4 * a * d) for a in (0.0, 1.0, 2.0, 3.0, 4.0, 5.0)]
+    # corner (0,0,0): faces -x, -y, -z; three interior neighbours
+    expect = 3 * d * h + mua[0] * h ** 3 + beta[0] + beta[2] + beta[4]
+    assert math.isclose(A[0, 0], expect, rel_tol=1e-14)
+    last = p.grid.N - 1  # corner (3,3,3): faces +x, +y, +z
+    expect = 3 * d * h + mua[0] * h ** 3 + beta[1] + beta[3] + beta[5]
+    assert math.isclose(A[last, last], expect, rel_tol=1e-14)
+
+
+def test_manufactured_solution_second_order():
+    """phi* = f(x) f(y) f(z), f = cos(k (t - L/2)) with k chosen so that phi* + 2AD dphi*/dn = 0
+    on every face (eqn:robin); q = (3 D k^2 + mu_a) phi*. The FV solution must converge to phi*
+    at second order: this pins the interior stencil, the h^3 absorption and the Robin face term."""
+    D, mua, Arob, L = 0.5, 0.03, 3.0, 24.0
+    k = so.brentq(lambda k: math.cos(k * L / 2) - 2 * Arob * D * k * math.sin(k * L / 2), 1e-6, math.pi / L - 1e-9)
+    errs = []
+    for n in (6, 12, 24):
+        h = L / n
+        c = (np.arange(n) + 0.5) * h
+        f = np.cos(k * (c - L / 2))
+        phi = np.einsum("k,j,i->kji", f, f, f).reshape(-1)
+        q = (3 * D * k * k + mua) * phi
+        A = model.assemble(n, n, n, h, D, mua, [Arob] * 6)
+        ph = spla.spsolve(A.tocsc(), h ** 3 * q)
+        errs.append(np.abs(ph - phi).max() / np.abs(phi).max())
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    assert min(orders) > 1.9, (errs, orders)
+    assert errs[-1] < 5e-4
+
+
+def test_photon_conservation():
+    """Sum over cells of (A phi) = 1: absorbed mu_a h^3 sum(phi) plus what leaves through the
+    boundary faces equals the unit source, because interior fluxes cancel pairwise."""
+    p = workloads.small(nx=9, ny=8, nz=7, robin_A=(3.0, 1.0, 0.0, 3.0, 2.0, 3.0))
+    mua, D = model.wavelength_coefficients(p)
+    phis, _ = solve.fields_splu(p, [2])
+    g = p.grid
+    h = g.h
+    for f in phis[0]:
+        F = f.reshape(g.nz, g.ny, g.nx)
+        absorbed = mua[2] * h ** 3 * f.sum()
+        out = 0.0
+        for face, sl in enumerate(((slice(None), slice(None), 0), (slice(None), slice(None), -1),
+                                   (slice(None), 0, slice(None)), (slice(None), -1, slice(None)),
+                                   (0, slice(None), slice(None)), (-1, slice(None), slice(None)))):
+            A_f = p.robin_A[face]
+            # outward flux through a face from the Robin condition with the half-cell gradient
+            phi_b = F[sl] * 4 * A_f * D[2] / (h + 4 * A_f * D[2])
+            out += (D[2] * (F[sl] - phi_b) / (h / 2) * h * h).sum()
+        assert math.isclose(absorbed + out, 1.0, rel_tol=1e-11)
+
+
+def test_infinite_medium_green_function():
+    """Far from the boundary the field of a unit source is e^{-mu_eff r}/(4 pi D r),
+    mu_eff = sqrt(mu_a / D); the lattice value converges at O(h^2)."""
+    diffs = []
+    for n, h in ((32, 1.5), (64, 0.75)):
+        p = workloads.make_problem(workloads.Grid(n, n, n, h), 1, 1, 1, seed=3)
+        p.src_ijk = np.array([[n // 2, n // 2, n // 2]])
+        mua, D = model.wavelength_coefficients(p)
+        mu = math.sqrt(mua[0] / D[0])
+        phis, _ = solve.fields_separable(p, [0], det=[])
+        F = phis[0, 0].reshape(n, n, n)
+        r = 6.0
+        off = int(round(r / h))
+        G = math.exp(-mu * r) / (4 * math.pi * D[0] * r)
+        diffs.append(abs(F[n // 2, n // 2, n // 2 + off] - G) / G)
+    assert diffs[0] < 0.1 and diffs[1] < 0.02
+    assert diffs[0] / diffs[1] > 3.0
+
+
+# ---------------------------------------------------------------- fields (Section 3 target)
+
+def test_dense_brute_force_matches_splu():
+    p = workloads.small(nx=6, ny=5, nz=4, n_src=2, n_det=2, n_lambda=3)
+    a, b = solve.fields_splu(p)
+    c, d = solve.fields_dense(p)
+    assert np.abs(a - c).max() <= 1e-13 * np.abs(a).max()
+    assert np.abs(b - d).max() <= 1e-13 * np.abs(b).max()
+
+
+@pytest.mark.parametrize("freq", [0.0, 100.0])
+def test_separable_solver_matches_splu(freq):
+    p = workloads.small(nx=13, ny=11, nz=9, freq_mhz=freq)
+    a, b = solve.fields_splu(p)
+    c, d = solve.fields_separable(p)
+    for x, y in ((a, c), (b, d)):
+        rel = np.linalg.norm(x - y, axis=-1) / np.linalg.norm(x, axis=-1)
+        assert rel.max() < 1e-13
+
+
+def test_splu_componentwise_backward_error():
+    """Oettli-Prager: |b - A phi| <= w (|A||phi| + |b|) entry by entry with w at rounding level.
+    For an M-matrix this bounds the entrywise error of phi also in the decayed far field."""
+    p = workloads.make_problem(workloads.Grid(16, 16, 24, 2.0), 2, 2, 2, seed=11, geometry="transmission")
+    phis, _ = solve.fields_splu(p, [1])
+    A = model.operator(p, 1).tocsr()
+    absA = abs(A)
+    for s, f in zip(p.src_voxels(), phis[0]):
+        b = np.zeros(p.grid.N)
+        b[s] = 1.0
+        r = np.abs(b - A @ f)
+        w = r / (absA @ np.abs(f) + b)
+        assert w.max() < 1e-14
+        assert f.min() > 0  # positive inverse of an M-matrix
+
+
+def test_reciprocity():
+    """phi_s(r_d) = phi_d(r_s): A is symmetric (Section 2.1, adjoint field)."""
+    for freq in (0.0, 100.0):
+        p = workloads.small(nx=10, ny=9, nz=8, n_src=3, n_det=4, freq_mhz=freq)
+        phis, phid = solve.fields_splu(p)
+        S, Dv = p.src_voxels(), p.det_voxels()
+        a = phis[:, :, Dv]  # [l, s, d]
+        b = np.transpose(phid[:, :, S], (0, 2, 1))
+        assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max()
+
+
+def test_frequency_domain_limits():
+    """omega -> 0 recovers the CW field; the FD operator is complex symmetric, not Hermitian."""
+    p0 = workloads.small(nx=8, ny=7, nz=6)
+    p1 = workloads.small(nx=8, ny=7, nz=6, freq_mhz=1e-6)
+    a, _ = solve.fields_splu(p0, [0])
+    b, _ = solve.fields_splu(p1, [0])
+    assert np.abs(b.real - a).max() < 1e-9 * np.abs(a).max()
+    p2 = workloads.small(nx=8, ny=7, nz=6, freq_mhz=100.0)
+    A = model.operator(p2, 0).toarray()
+    assert np.array_equal(A, A.T) and not np.allclose(A, A.conj().T)
+
+
+# ---------------------------------------------------------------- Born rows (eqn:lippschwin)
+
+def test_born_entries_are_fd_of_nonlinear_forward_model():
+    """J[(s,d,l),(c,x)] = d phi_s(r_d) / d c_c(x): central differences of the nonlinear discrete
+    forward model (eqn:born without the Born approximation) for every voxel and chromophore of a
+    tiny grid. Pins sign, the h^3 factor, the eps_c(lambda) index and the row/column order."""
+    p = workloads.small(nx=4, ny=4, nz=3, n_src=2, n_det=2, n_lambda=2, h=2.0)
+    # keep sources/detectors inside a 4x4 face: draw positions by hand
+    p.src_ijk = np.array([[1, 1, 2], [2, 2, 2]])
+    p.det_ijk = np.array([[2, 1, 2], [1, 2, 2]])
+    phis, phid = solve.fields_splu(p)
+    J = born.born_matrix(p, phis, phid)
+    N, nc, nl, nd = p.grid.N, p.n_chrom, p.n_lambda, p.n_det
+    delta = 1e-5
+    for lam in range(nl):
+        for x in range(N):
+            e = np.zeros(N)
+            e[x] = delta
+            for c in range(nc):
+                dmua = e * p.eps[lam, c]
+                fp = born.forward_value(p, lam, dmua)
+                fm = born.forward_value(p, lam, -dmua)
+                fd = (fp - fm) / (2 * delta)
+                for s in range(p.n_src):
+                    for d in range(nd):
+                        r = (s * nd + d) * nl + lam
+                        assert abs(J[r, c * N + x] - fd[s, d]) <= 1e-6 * abs(fd[s, d]) + 1e-14
+
+
+def test_born_row_sum_is_uniform_mua_derivative():
+    """sum_x H[(s,d,l),x] = -d phi_s(r_d)/d mu_a(uniform), by central FD on a config-1-like grid."""
+    p = workloads.config(1)
+    lam = 5
+    phis, phid = solve.fields_splu(p, [lam])
+    J = born.born_rows(p, phis, phid, rows=range(p.n_src * p.n_det), lams=[lam])
+    N = p.grid.N
+    H = J[:, :N] / (-(p.grid.h ** 3) * p.eps[lam, 0])
+    delta = 1e-6
+    ones = np.ones(N)
+    fd = (born.forward_value(p, lam, delta * ones) - born.forward_value(p, lam, -delta * ones)) / (2 * delta)
+    lhs = -(p.grid.h ** 3) * H.sum(axis=1)
+    assert np.abs(lhs - fd.reshape(-1)).max() <= 1e-6 * np.abs(fd).max()
+
+
+def test_apply_and_transpose_match_explicit_matrix():
+    p = workloads.small(nx=7, ny=6, nz=5, n_src=3, n_det=2, n_lambda=5)
+    lams = [1, 2, 3]
+    phis, phid = solve.fields_splu(p, lams)
+    J = born.born_matrix(p, phis, phid, lams)
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal(J.shape[1])
+    y = rng.standard_normal(J.shape[0])
+    jx = born.apply(p, phis, phid, x, lams)
+    jty = born.apply_T(p, phis, phid, y, lams)
+    assert np.allclose(jx, J @ x, rtol=1e-13, atol=1e-13 * np.abs(J @ x).max())
+    assert np.allclose(jty, J.T @ y, rtol=1e-13, atol=1e-13 * np.abs(J.T @ y).max())
+    assert math.isclose(jx @ y, x @ jty, rel_tol=1e-12)
+
+
+def test_apply_T_adjoint_solve_form_agrees():
+    """J^T y from stored detector fields equals J^T y from one extra solve per source."""
+    p = workloads.small(nx=9, ny=8, nz=6, n_src=3, n_det=4, n_lambda=3)
+    phis, phid = solve.fields_splu(p)
+    y = np.random.default_rng(1).standard_normal(p.M)
+    g1 = born.apply_T(p, phis, phid, y)
+    g2 = born.apply_T_adjoint_solve(p, phis, y)
+    assert np.abs(g1 - g2).max() <= 1e-12 * np.abs(g1).max()
+
+
+def test_born_symmetry_source_detector_swap():
+    """Swapping the roles of sources and detectors transposes the (s, d) index of H."""
+    p = workloads.small(nx=8, ny=8, nz=6, n_src=3, n_det=3, n_lambda=2)
+    phis, phid = solve.fields_splu(p)
+    J = born.born_matrix(p, phis, phid)
+    q = workloads.small(nx=8, ny=8, nz=6, n_src=3, n_det=3, n_lambda=2)
+    q.src_ijk, q.det_ijk = p.det_ijk.copy(), p.src_ijk.copy()
+    Jq = born.born_matrix(q, phid, phis)
+    nd, nl = 3, 2
+    for s in range(3):
+        for d in range(3):
+            for lam in range(nl):
+                assert np.array_equal(J[(s * nd + d) * nl + lam], Jq[(d * nd + s) * nl + lam])
+
+
+# ---------------------------------------------------------------- sketch (Appendix A.1)
+
+def test_randsvd_recovers_exact_low_rank():
+    rng = np.random.default_rng(2)
+    m, n, r = 120, 300, 12
+    A = rng.standard_normal((m, r)) @ rng.standard_normal((r, n))
+    U, S, V = sketch.randsvd_fixed(A, rng.standard_normal((n, r + 5)), r)
+    assert np.linalg.norm(A - U @ np.diag(S) @ V.T, 2) <= 1e-12 * np.linalg.norm(A, 2)
+    assert np.allclose(U.T @ U, np.eye(r), atol=1e-12) and np.allclose(V.T @ V, np.eye(r), atol=1e-12)
+
+
+def test_randsvd_near_optimal_on_decaying_spectrum():
+    """Error within a small factor of the optimum sigma_{r+1} (Halko et al. bound with p = 20)."""
+    rng = np.random.default_rng(3)
+    m, n, r = 200, 500, 20
+    Qa, _ = np.linalg.qr(rng.standard_normal((m, m)))
+    Qb, _ = np.linalg.qr(rng.standard_normal((n, m)))
+    s = 0.7 ** np.arange(m)
+    A = Qa @ np.diag(s) @ Qb.T
+    U, S, V = sketch.randsvd_fixed(A, rng.standard_normal((n, r + 20)), r)
+    _, _, _, sall = sketch.truncated_svd(A, r)
+    assert math.isclose(sall[r], s[r], rel_tol=1e-10)
+    err = np.linalg.norm(A - U @ np.diag(S) @ V.T, 2)
+    assert s[r] <= err * (1 + 1e-9) and err <= 1.5 * s[r]
+    X = rng.standard_normal((n, 8))
+    assert sketch.probe_error(A, U, S, V, X).max() < 10 * s[r] / s[0]
