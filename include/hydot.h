@@ -1,0 +1,146 @@
+/*
+ * hydot.h -- C ABI of libhydot, the GB300 (sm_103a) hot path of the Born-approximation
+ * method for hyperspectral diffuse optical tomography (Saibaba, Kilmer, Miller & Fantini,
+ * "Fast algorithms for Hyperspectral Diffuse Optical Tomography", arXiv:1410.0986).
+ *
+ * What the library computes
+ *   - Fields (Section 2.2, eqn:discincident and eqn:multipleshifted; Section 3): for every
+ *     wavelength lambda_j and every source s / detector d, the discrete diffusion solve
+ *         A_j phi = e_cell,
+ *     A_j = K + sigma_j M + sigma'_j R restated as a cell-centred finite-volume 7-point
+ *     operator on a box of nx*ny*nz cells of side h: interior faces D_j*h, absorption
+ *     mu_a,j*h^3, Robin faces 2 D_j h^2 / (h + 4 A D_j) (A = 0: Dirichlet), and for a
+ *     modulated source an extra i*omega*h^3/c_medium on the diagonal. mu_a,j = sum_c
+ *     eps_c(lambda_j) c_bg,c and D_j = 1 / (3 (mu_a,j + mu_s'(lambda_j))).
+ *     The adjoint (detector) fields are the same solves with the detector cell as source
+ *     (Section 2.1, reciprocity).
+ *   - Born rows (eqn:lippschwin, eqn:perturbation, eqn:measurement):
+ *         J[(s,d,lambda),(c,x)] = -h^3 eps_c(lambda) phi_s(x;lambda) phi_d(x;lambda).
+ *   - Implicit products y = J x and g += J^T y with the fields resident.
+ *
+ * Conventions (all calls)
+ *   - Voxel index x = (k*ny + j)*nx + i (i fastest), N = nx*ny*nz.
+ *   - A wavelength slice [lam0, lam0+nlam) is addressed by its own arrays: phi_src is
+ *     [nlam][n_src][N] and phi_det is [nlam][n_det][N] for that slice only.
+ *   - Rows of J / entries of y inside a slice: r = (s*n_det + d)*nlam + (lambda - lam0)
+ *     (wavelength fastest, then detector, then source: E_k = I (x) I (x) diag(eps_k)).
+ *   - Columns of J / entries of x and g: c*N + x (chromophore-major).
+ *   - Element type of every bulk array: double for HYDOT_FP64, float for HYDOT_MIXED;
+ *     with omega != 0 the fields are complex (interleaved re, im) of that precision.
+ *   - Bulk arrays (fields, J, x, y, g) are DEVICE pointers owned by the caller; the
+ *     library never frees them. Work is enqueued on the context's stream and is complete
+ *     when that stream is synchronised (hydot_solve_fields synchronises it itself).
+ *   - Every call returns a hydot_status; on error, hydot_last_error(ctx) describes it.
+ *     No call aborts the process or throws across the ABI.
+ */
+#ifndef HYDOT_H
+#define HYDOT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hydot_ctx hydot_ctx; /* opaque: device coefficient tables, workspace, stream */
+
+typedef enum {
+  HYDOT_OK = 0,
+  HYDOT_ERR_ARG = -1,           /* invalid argument; nothing was enqueued */
+  HYDOT_ERR_OOM = -2,           /* device allocation failed */
+  HYDOT_ERR_CUDA = -3,          /* a CUDA call failed (message holds cudaGetErrorString) */
+  HYDOT_ERR_NOT_CONVERGED = -4, /* some field missed its tolerance: best iterate written */
+  HYDOT_ERR_TIMEOUT = -5,       /* a bounded device wait gave up */
+  HYDOT_ERR_STATE = -6          /* call not valid for this context (e.g. complex Born) */
+} hydot_status;
+
+typedef enum {
+  HYDOT_FP64 = 0,  /* FP64 Jacobi-PCG (COCG when omega != 0), no refinement */
+  HYDOT_MIXED = 1  /* FP32 inner PCG/COCG with FP64 residuals and iterative refinement */
+} hydot_precision;
+
+typedef struct {
+  /* grid */
+  int nx, ny, nz;          /* cells per axis, each >= 1 */
+  double h_mm;             /* cell side, mm, > 0 */
+  double robin_A[6];       /* Robin coefficient per face -x,+x,-y,+y,-z,+z (eqn:robin); 0 = Dirichlet */
+  /* medium (host arrays, copied during hydot_setup) */
+  int n_lambda;            /* wavelengths, >= 1 */
+  int n_chrom;             /* chromophore species, 1..16 */
+  const double* eps;       /* [n_lambda][n_chrom] extinction, /mm/mM */
+  const double* c_bg;      /* [n_chrom] background concentration, mM */
+  const double* mus_prime; /* [n_lambda] reduced scattering, /mm */
+  double omega;            /* modulation, rad/ns; 0 => continuous wave, real fields */
+  double c_medium;         /* speed of light in the medium, mm/ns (used when omega != 0) */
+  /* optodes (host arrays, copied): cell indices (i, j, k), all distinct from each other */
+  int n_src, n_det;
+  const int* src_ijk;      /* [n_src][3] */
+  const int* det_ijk;      /* [n_det][3] */
+  /* solver */
+  int precision;           /* hydot_precision */
+  double tol;              /* stop when ||b - A x||_2 <= tol ||b||_2 ...                    */
+  double tol_cw;           /* ... and max_i |b - A x|_i / (|A||x| + |b|)_i <= tol_cw (0: off) */
+  double inner_tol;        /* HYDOT_MIXED: residual reduction per FP32 inner solve (0: 1e-5)  */
+  int max_iter;            /* cap on Krylov iterations per field, all cycles together (0: 20000) */
+  int deflation_k;         /* size of the recycled deflation basis, 0..32 (0: off)            */
+  int max_lambda_per_call; /* largest nlam passed to hydot_solve_fields (0: n_lambda)          */
+} hydot_problem;
+
+typedef struct {
+  int n_fields;            /* fields solved by the call */
+  int n_not_converged;     /* fields that missed tol / tol_cw within max_iter */
+  int iters_max;           /* Krylov iterations of the slowest field (all cycles) */
+  double iters_mean;       /* mean Krylov iterations per field */
+  int cycles_max;          /* refinement cycles of the slowest field */
+  double resid_max;        /* largest final ||b - A x||_2 / ||b||_2 (FP64) */
+  double cw_max;           /* largest final componentwise backward error */
+} hydot_stats;
+
+/* Version of this ABI (major*10000 + minor*100 + patch). */
+int hydot_version(void);
+
+/* Validates *p, copies its host arrays, computes the per-wavelength coefficients
+ * (mu_a, D, the scaled absorption and Robin terms), allocates the workspace for
+ * max_lambda_per_call*(n_src+n_det) simultaneous fields and, when deflation_k > 0, builds the
+ * recycled deflation basis. stream: a cudaStream_t (NULL = the legacy default stream).
+ * On success *out owns everything the library allocated; free it with hydot_destroy.
+ * Errors: HYDOT_ERR_ARG (bad sizes, optodes outside the grid or sharing a cell, bad
+ * tolerances), HYDOT_ERR_OOM, HYDOT_ERR_CUDA. On error *out is NULL. */
+int hydot_setup(const hydot_problem* p, void* stream, hydot_ctx** out);
+
+/* Sets the stream later calls enqueue on. */
+int hydot_set_stream(hydot_ctx* ctx, void* stream);
+
+/* Fields for wavelengths [lam0, lam0+nlam) (eqn:multipleshifted for each source and detector):
+ * writes phi_src [nlam][n_src][N] and phi_det [nlam][n_det][N] (device, caller-owned).
+ * Either pointer may be NULL to skip that set (its solves are not run).
+ * Synchronises the stream (convergence is decided on the device and polled). If st is not
+ * NULL it receives the statistics. Returns HYDOT_ERR_NOT_CONVERGED (best iterates written)
+ * when a field missed tol / tol_cw within max_iter. */
+int hydot_solve_fields(hydot_ctx* ctx, int lam0, int nlam, void* phi_src, void* phi_det,
+                       hydot_stats* st);
+
+/* Born rows [row0, row0+nrows) of the slice [lam0, lam0+nlam) into J (device, row-major,
+ * leading dimension ldJ >= n_chrom*N elements): J[r-row0][c*N + x]. Continuous wave only
+ * (HYDOT_ERR_STATE otherwise). Rows outside the slice are HYDOT_ERR_ARG. Asynchronous. */
+int hydot_born_assemble(hydot_ctx* ctx, const void* phi_src, const void* phi_det, int lam0, int nlam,
+                        long long row0, long long nrows, void* J, long long ldJ);
+
+/* y = J x for the slice: x [n_chrom*N], y [n_src*n_det*nlam] (overwritten). Continuous wave
+ * only. Asynchronous; uses library workspace, so calls on one context must not overlap. */
+int hydot_born_apply(hydot_ctx* ctx, const void* phi_src, const void* phi_det, int lam0, int nlam,
+                     const void* x, void* y);
+
+/* g += J^T y for the slice: y [n_src*n_det*nlam], g [n_chrom*N] (accumulated, so calls over
+ * consecutive slices sum to the full product). Continuous wave only. Asynchronous. */
+int hydot_born_apply_T(hydot_ctx* ctx, const void* phi_src, const void* phi_det, int lam0, int nlam,
+                       const void* y, void* g);
+
+/* Last error message of ctx (or of the last failed hydot_setup when ctx is NULL). */
+const char* hydot_last_error(const hydot_ctx* ctx);
+
+/* Frees everything hydot_setup allocated. NULL is ignored. */
+void hydot_destroy(hydot_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HYDOT_H */

@@ -1,0 +1,85 @@
+"""ctypes view of the C ABI in include/hydot.h (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhydot.so")
+
+HYDOT_OK = 0
+HYDOT_ERR_ARG = -1
+HYDOT_ERR_OOM = -2
+HYDOT_ERR_CUDA = -3
+HYDOT_ERR_NOT_CONVERGED = -4
+HYDOT_ERR_TIMEOUT = -5
+HYDOT_ERR_STATE = -6
+STATUS_NAMES = {0: "HYDOT_OK", -1: "HYDOT_ERR_ARG", -2: "HYDOT_ERR_OOM", -3: "HYDOT_ERR_CUDA",
+                -4: "HYDOT_ERR_NOT_CONVERGED", -5: "HYDOT_ERR_TIMEOUT", -6: "HYDOT_ERR_STATE"}
+
+HYDOT_FP64 = 0
+HYDOT_MIXED = 1
+
+# Every symbol include/hydot.h declares.
+EXPORTS = ("hydot_version", "hydot_setup", "hydot_set_stream", "hydot_solve_fields", "hydot_born_assemble",
+           "hydot_born_apply", "hydot_born_apply_T", "hydot_last_error", "hydot_destroy")
+
+
+class Problem(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+        ("h_mm", C.c_double),
+        ("robin_A", C.c_double * 6),
+        ("n_lambda", C.c_int), ("n_chrom", C.c_int),
+        ("eps", C.POINTER(C.c_double)), ("c_bg", C.POINTER(C.c_double)), ("mus_prime", C.POINTER(C.c_double)),
+        ("omega", C.c_double), ("c_medium", C.c_double),
+        ("n_src", C.c_int), ("n_det", C.c_int),
+        ("src_ijk", C.POINTER(C.c_int)), ("det_ijk", C.POINTER(C.c_int)),
+        ("precision", C.c_int),
+        ("tol", C.c_double), ("tol_cw", C.c_double), ("inner_tol", C.c_double),
+        ("max_iter", C.c_int), ("deflation_k", C.c_int), ("max_lambda_per_call", C.c_int),
+    ]
+
+
+class Stats(C.Structure):
+    _fields_ = [
+        ("n_fields", C.c_int), ("n_not_converged", C.c_int), ("iters_max", C.c_int),
+        ("iters_mean", C.c_double), ("cycles_max", C.c_int), ("resid_max", C.c_double), ("cw_max", C.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    """Load libhydot.so; raises (never falls back) when it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libhydot.so not built ({path}); run __graft_entry__.build() or "
+                           "python -m paper_1410_0986_gb300._build")
+    lib = C.CDLL(path)
+    vp = C.c_void_p
+    lib.hydot_version.restype = C.c_int
+    lib.hydot_setup.argtypes = [C.POINTER(Problem), vp, C.POINTER(vp)]
+    lib.hydot_setup.restype = C.c_int
+    lib.hydot_set_stream.argtypes = [vp, vp]
+    lib.hydot_set_stream.restype = C.c_int
+    lib.hydot_solve_fields.argtypes = [vp, C.c_int, C.c_int, vp, vp, C.POINTER(Stats)]
+    lib.hydot_solve_fields.restype = C.c_int
+    lib.hydot_born_assemble.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_longlong, C.c_longlong, vp, C.c_longlong]
+    lib.hydot_born_assemble.restype = C.c_int
+    lib.hydot_born_apply.argtypes = [vp, vp, vp, C.c_int, C.c_int, vp, vp]
+    lib.hydot_born_apply.restype = C.c_int
+    lib.hydot_born_apply_T.argtypes = [vp, vp, vp, C.c_int, C.c_int, vp, vp]
+    lib.hydot_born_apply_T.restype = C.c_int
+    lib.hydot_last_error.argtypes = [vp]
+    lib.hydot_last_error.restype = C.c_char_p
+    lib.hydot_destroy.argtypes = [vp]
+    lib.hydot_destroy.restype = None
+    _lib = lib
+    return lib

@@ -1,0 +1,182 @@
+"""Python binding of libhydot: same calls as include/hydot.h, argument marshalling only.
+
+PyTorch provides device memory and the stream; every step of the computation runs in
+the library's CUDA kernels. There is no CPU fallback: constructing a Context without
+the built library or without a CUDA device raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _lib
+
+PRECISIONS = {"fp64": _lib.HYDOT_FP64, "mixed": _lib.HYDOT_MIXED}
+
+
+class HydotError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_lib.STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+class Context:
+    """One hydot_ctx: a grid, its spectra and optodes, and the solver workspace.
+
+    Arrays passed to the methods are CUDA tensors laid out as include/hydot.h states;
+    their dtype must be float64 ("fp64") or float32 ("mixed"), complex for omega != 0.
+    """
+
+    def __init__(self, nx: int, ny: int, nz: int, h: float, robin_A: Sequence[float], eps, c_bg, mus_prime,
+                 src_ijk, det_ijk, *, omega: float = 0.0, c_medium: float = 299.792458 / 1.4,
+                 precision: str = "mixed", tol: float = 1e-10, tol_cw: float = 1e-8, inner_tol: float = 0.0,
+                 max_iter: int = 0, deflation_k: int = 0, max_lambda_per_call: int = 0):
+        if not torch.cuda.is_available():
+            raise RuntimeError("libhydot needs a CUDA device; there is no CPU path")
+        self.lib = _lib.load()
+        self._eps = _f64(eps)
+        self._cbg = _f64(c_bg)
+        self._musp = _f64(mus_prime)
+        self._src = np.ascontiguousarray(np.asarray(src_ijk, dtype=np.int32).reshape(-1, 3))
+        self._det = np.ascontiguousarray(np.asarray(det_ijk, dtype=np.int32).reshape(-1, 3))
+        p = _lib.Problem()
+        p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
+        p.h_mm = float(h)
+        for f in range(6):
+            p.robin_A[f] = float(robin_A[f])
+        p.n_lambda, p.n_chrom = self._eps.shape
+        p.eps = self._eps.ctypes.data_as(C.POINTER(C.c_double))
+        p.c_bg = self._cbg.ctypes.data_as(C.POINTER(C.c_double))
+        p.mus_prime = self._musp.ctypes.data_as(C.POINTER(C.c_double))
+        p.omega = float(omega)
+        p.c_medium = float(c_medium)
+        p.n_src, p.n_det = len(self._src), len(self._det)
+        p.src_ijk = self._src.ctypes.data_as(C.POINTER(C.c_int))
+        p.det_ijk = self._det.ctypes.data_as(C.POINTER(C.c_int))
+        p.precision = PRECISIONS[precision]
+        p.tol, p.tol_cw, p.inner_tol = float(tol), float(tol_cw), float(inner_tol)
+        p.max_iter, p.deflation_k, p.max_lambda_per_call = int(max_iter), int(deflation_k), int(max_lambda_per_call)
+        self.problem = p
+        self.nx, self.ny, self.nz, self.N = p.nx, p.ny, p.nz, p.nx * p.ny * p.nz
+        self.n_lambda, self.n_chrom, self.n_src, self.n_det = p.n_lambda, p.n_chrom, p.n_src, p.n_det
+        self.precision = precision
+        self.complex = omega != 0.0
+        real = torch.float64 if precision == "fp64" else torch.float32
+        self.real_dtype = real
+        self.dtype = (torch.complex128 if precision == "fp64" else torch.complex64) if self.complex else real
+        torch.cuda.init()
+        ptr = C.c_void_p()
+        rc = self.lib.hydot_setup(C.byref(p), C.c_void_p(torch.cuda.current_stream().cuda_stream), C.byref(ptr))
+        if rc != 0:
+            raise HydotError(rc, self.lib.hydot_last_error(None).decode())
+        self._ctx = ptr
+
+    @classmethod
+    def from_problem(cls, prob, **kw) -> "Context":
+        """Build from any object with the attributes of a synthetic problem description
+        (grid.nx/ny/nz/h, robin_A, eps, c_bg, mus_prime, src_ijk, det_ijk, omega, c_medium)."""
+        g = prob.grid
+        return cls(g.nx, g.ny, g.nz, g.h, prob.robin_A, prob.eps, prob.c_bg, prob.mus_prime, prob.src_ijk,
+                   prob.det_ijk, omega=prob.omega, c_medium=prob.c_medium, **kw)
+
+    # ------------------------------------------------------------------ helpers
+    def _check(self, rc: int, allow_not_converged: bool = False):
+        if rc == 0 or (allow_not_converged and rc == _lib.HYDOT_ERR_NOT_CONVERGED):
+            return rc
+        raise HydotError(rc, self.lib.hydot_last_error(self._ctx).decode())
+
+    def _stream(self):
+        self.lib.hydot_set_stream(self._ctx, C.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+    def _ptr(self, t: Optional[torch.Tensor], shape, dtype=None) -> Optional[int]:
+        if t is None:
+            return None
+        dtype = dtype or self.dtype
+        if not t.is_cuda or t.dtype != dtype or not t.is_contiguous() or t.numel() != int(np.prod(shape)):
+            raise ValueError(f"expected a contiguous CUDA {dtype} tensor with {int(np.prod(shape))} elements, "
+                             f"got {t.dtype} {tuple(t.shape)} on {t.device}")
+        return t.data_ptr()
+
+    def empty(self, *shape, dtype=None) -> torch.Tensor:
+        return torch.empty(shape, dtype=dtype or self.dtype, device="cuda")
+
+    # ------------------------------------------------------------------ calls
+    def solve_fields(self, lam0: int, nlam: int, phi_src: Optional[torch.Tensor] = None,
+                     phi_det: Optional[torch.Tensor] = None, *, sources: bool = True, detectors: bool = True,
+                     raise_not_converged: bool = True):
+        """hydot_solve_fields. Allocates the outputs when not given. Returns (phi_src, phi_det, stats)."""
+        if phi_src is None and sources and self.n_src:
+            phi_src = self.empty(nlam, self.n_src, self.N)
+        if phi_det is None and detectors and self.n_det:
+            phi_det = self.empty(nlam, self.n_det, self.N)
+        st = _lib.Stats()
+        self._stream()
+        rc = self.lib.hydot_solve_fields(self._ctx, lam0, nlam, self._ptr(phi_src, (nlam, self.n_src, self.N)),
+                                         self._ptr(phi_det, (nlam, self.n_det, self.N)), C.byref(st))
+        self._check(rc, allow_not_converged=not raise_not_converged)
+        return phi_src, phi_det, st.as_dict()
+
+    def born_assemble(self, phi_src, phi_det, lam0: int, nlam: int, row0: int = 0, nrows: Optional[int] = None,
+                      J: Optional[torch.Tensor] = None, ldJ: Optional[int] = None) -> torch.Tensor:
+        M = self.n_src * self.n_det * nlam
+        nrows = M - row0 if nrows is None else nrows
+        cols = self.n_chrom * self.N
+        ldJ = cols if ldJ is None else ldJ
+        if J is None:
+            J = self.empty(nrows, ldJ, dtype=self.real_dtype)
+        self._stream()
+        rc = self.lib.hydot_born_assemble(self._ctx, self._ptr(phi_src, (nlam, self.n_src, self.N), self.real_dtype),
+                                          self._ptr(phi_det, (nlam, self.n_det, self.N), self.real_dtype), lam0, nlam,
+                                          row0, nrows, self._ptr(J, (nrows, ldJ), self.real_dtype), ldJ)
+        self._check(rc)
+        return J
+
+    def born_apply(self, phi_src, phi_det, lam0: int, nlam: int, x: torch.Tensor,
+                   y: Optional[torch.Tensor] = None) -> torch.Tensor:
+        M = self.n_src * self.n_det * nlam
+        if y is None:
+            y = self.empty(M, dtype=self.real_dtype)
+        self._stream()
+        rc = self.lib.hydot_born_apply(self._ctx, self._ptr(phi_src, (nlam, self.n_src, self.N), self.real_dtype),
+                                       self._ptr(phi_det, (nlam, self.n_det, self.N), self.real_dtype), lam0, nlam,
+                                       self._ptr(x, (self.n_chrom * self.N,), self.real_dtype),
+                                       self._ptr(y, (M,), self.real_dtype))
+        self._check(rc)
+        return y
+
+    def born_apply_T(self, phi_src, phi_det, lam0: int, nlam: int, y: torch.Tensor,
+                     g: Optional[torch.Tensor] = None) -> torch.Tensor:
+        M = self.n_src * self.n_det * nlam
+        if g is None:
+            g = torch.zeros(self.n_chrom * self.N, dtype=self.real_dtype, device="cuda")
+        self._stream()
+        rc = self.lib.hydot_born_apply_T(self._ctx, self._ptr(phi_src, (nlam, self.n_src, self.N), self.real_dtype),
+                                         self._ptr(phi_det, (nlam, self.n_det, self.N), self.real_dtype), lam0, nlam,
+                                         self._ptr(y, (M,), self.real_dtype),
+                                         self._ptr(g, (self.n_chrom * self.N,), self.real_dtype))
+        self._check(rc)
+        return g
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self.lib.hydot_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

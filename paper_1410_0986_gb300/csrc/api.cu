@@ -1,0 +1,212 @@
+// C ABI of libhydot: validation, per-wavelength coefficients, context lifetime, dispatch.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <set>
+#include <string>
+
+#include "hydot_internal.cuh"
+
+using hydot::fail;
+
+namespace {
+
+std::string g_setup_error;  // message of the last failed hydot_setup (no context to hold it)
+
+// Per-wavelength coefficients of the scaled operator (Section 2.1-2.2):
+//   mu_a = sum_c eps_c(lambda) c_bg,c            (eqn:perturbation for the background)
+//   D    = 1 / (3 (mu_a + mu_s'))
+//   sigma = mu_a h^2 / D (+ i omega h^2 / (c_m D)),  bhat_f = 2 h / (h + 4 A_f D),  1/(D h).
+void compute_coefficients(hydot_ctx* c) {
+  c->coef.resize(c->n_lambda);
+  for (int j = 0; j < c->n_lambda; ++j) {
+    double mua = 0.0;
+    for (int l = 0; l < c->n_chrom; ++l) mua += c->eps[(size_t)j * c->n_chrom + l] * c->c_bg[l];
+    const double D = 1.0 / (3.0 * (mua + c->mus_prime[j]));
+    hydot::LamCoef& k = c->coef[j];
+    k.mua = mua;
+    k.D = D;
+    k.sigma_re = mua * c->h * c->h / D;
+    k.sigma_im = (c->omega != 0.0) ? c->omega * c->h * c->h / (c->c_medium * D) : 0.0;
+    for (int f = 0; f < 6; ++f) k.bhat[f] = 2.0 * c->h / (c->h + 4.0 * c->robin_A[f] * D);
+    k.inv_Dh = 1.0 / (D * c->h);
+  }
+}
+
+int validate(const hydot_problem* p, std::string& msg) {
+  auto bad = [&](const std::string& m) { msg = m; return HYDOT_ERR_ARG; };
+  if (!p) return bad("problem is NULL");
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1) return bad("grid extents must be >= 1");
+  if (!(p->h_mm > 0.0) || !std::isfinite(p->h_mm)) return bad("h_mm must be finite and > 0");
+  for (int f = 0; f < 6; ++f)
+    if (!(p->robin_A[f] >= 0.0) || !std::isfinite(p->robin_A[f])) return bad("robin_A must be finite and >= 0");
+  if (p->n_lambda < 1) return bad("n_lambda must be >= 1");
+  if (p->n_chrom < 1 || p->n_chrom > 16) return bad("n_chrom must be in 1..16");
+  if (!p->eps || !p->c_bg || !p->mus_prime) return bad("eps, c_bg and mus_prime must be given");
+  for (long long q = 0; q < (long long)p->n_lambda * p->n_chrom; ++q)
+    if (!std::isfinite(p->eps[q]) || p->eps[q] < 0.0) return bad("eps must be finite and >= 0");
+  for (int l = 0; l < p->n_chrom; ++l)
+    if (!std::isfinite(p->c_bg[l]) || p->c_bg[l] < 0.0) return bad("c_bg must be finite and >= 0");
+  for (int j = 0; j < p->n_lambda; ++j)
+    if (!(p->mus_prime[j] > 0.0) || !std::isfinite(p->mus_prime[j])) return bad("mus_prime must be finite and > 0");
+  if (!std::isfinite(p->omega)) return bad("omega must be finite");
+  if (p->omega != 0.0 && !(p->c_medium > 0.0)) return bad("c_medium must be > 0 when omega != 0");
+  if (p->n_src < 0 || p->n_det < 0 || p->n_src + p->n_det < 1) return bad("need at least one source or detector");
+  if ((p->n_src && !p->src_ijk) || (p->n_det && !p->det_ijk)) return bad("optode arrays must be given");
+  std::set<long long> cells;
+  for (int q = 0; q < p->n_src + p->n_det; ++q) {
+    const int* ijk = q < p->n_src ? p->src_ijk + 3 * q : p->det_ijk + 3 * (q - p->n_src);
+    if (ijk[0] < 0 || ijk[0] >= p->nx || ijk[1] < 0 || ijk[1] >= p->ny || ijk[2] < 0 || ijk[2] >= p->nz)
+      return bad("optode outside the grid");
+    long long v = ((long long)ijk[2] * p->ny + ijk[1]) * p->nx + ijk[0];
+    if (!cells.insert(v).second) return bad("two optodes share a cell");
+  }
+  if (p->precision != HYDOT_FP64 && p->precision != HYDOT_MIXED) return bad("unknown precision");
+  if (!(p->tol > 0.0) || !(p->tol < 1.0)) return bad("tol must be in (0, 1)");
+  if (!(p->tol_cw >= 0.0) || !(p->tol_cw < 1.0)) return bad("tol_cw must be in [0, 1)");
+  if (!(p->inner_tol >= 0.0) || !(p->inner_tol < 1.0)) return bad("inner_tol must be in [0, 1)");
+  if (p->max_iter < 0) return bad("max_iter must be >= 0");
+  if (p->deflation_k < 0 || p->deflation_k > 32) return bad("deflation_k must be in 0..32");
+  if (p->max_lambda_per_call < 0 || p->max_lambda_per_call > p->n_lambda)
+    return bad("max_lambda_per_call must be in 0..n_lambda");
+  return HYDOT_OK;
+}
+
+void free_all(hydot_ctx* c) {
+  hydot::solver_free(c);
+  cudaFree(c->d_coef);
+  cudaFree(c->d_eps);
+  cudaFree(c->d_optode);
+  cudaFree(c->d_W);
+  cudaFree(c->d_Ginv);
+  cudaFree(c->d_apply_ws);
+}
+
+}  // namespace
+
+extern "C" {
+
+int hydot_version(void) { return 10000; }
+
+int hydot_setup(const hydot_problem* p, void* stream, hydot_ctx** out) {
+  if (!out) {
+    g_setup_error = "out is NULL";
+    return HYDOT_ERR_ARG;
+  }
+  *out = nullptr;
+  std::string msg;
+  int rc = validate(p, msg);
+  if (rc) {
+    g_setup_error = msg;
+    return rc;
+  }
+  hydot_ctx* c = new (std::nothrow) hydot_ctx();
+  if (!c) {
+    g_setup_error = "host allocation failed";
+    return HYDOT_ERR_OOM;
+  }
+  c->nx = p->nx;
+  c->ny = p->ny;
+  c->nz = p->nz;
+  c->N = (long long)p->nx * p->ny * p->nz;
+  c->h = p->h_mm;
+  std::memcpy(c->robin_A, p->robin_A, sizeof(c->robin_A));
+  c->n_lambda = p->n_lambda;
+  c->n_chrom = p->n_chrom;
+  c->n_src = p->n_src;
+  c->n_det = p->n_det;
+  c->eps.assign(p->eps, p->eps + (size_t)p->n_lambda * p->n_chrom);
+  c->c_bg.assign(p->c_bg, p->c_bg + p->n_chrom);
+  c->mus_prime.assign(p->mus_prime, p->mus_prime + p->n_lambda);
+  c->omega = p->omega;
+  c->c_medium = p->c_medium;
+  c->cplx = p->omega != 0.0;
+  for (int q = 0; q < p->n_src + p->n_det; ++q) {
+    const int* ijk = q < p->n_src ? p->src_ijk + 3 * q : p->det_ijk + 3 * (q - p->n_src);
+    c->optode_voxel.push_back((int)(((long long)ijk[2] * p->ny + ijk[1]) * p->nx + ijk[0]));
+  }
+  c->precision = p->precision;
+  c->tol = p->tol;
+  c->tol_cw = p->tol_cw;
+  c->inner_tol = p->inner_tol;
+  c->max_iter = p->max_iter > 0 ? p->max_iter : 20000;
+  c->deflation_k = p->deflation_k;
+  c->max_fields = (p->max_lambda_per_call > 0 ? p->max_lambda_per_call : p->n_lambda) * (p->n_src + p->n_det);
+  c->stream = (cudaStream_t)stream;
+  compute_coefficients(c);
+
+  auto bail = [&](int code) {
+    g_setup_error = c->err;
+    free_all(c);
+    delete c;
+    return code;
+  };
+#define SETUP_TRY(call)                                                                  \
+  do {                                                                                   \
+    cudaError_t e__ = (call);                                                            \
+    if (e__ != cudaSuccess) {                                                            \
+      c->err = std::string(#call) + ": " + cudaGetErrorString(e__);                      \
+      return bail(e__ == cudaErrorMemoryAllocation ? HYDOT_ERR_OOM : HYDOT_ERR_CUDA);     \
+    }                                                                                    \
+  } while (0)
+  SETUP_TRY(cudaMalloc(&c->d_coef, sizeof(hydot::LamCoef) * c->n_lambda));
+  SETUP_TRY(cudaMemcpy(c->d_coef, c->coef.data(), sizeof(hydot::LamCoef) * c->n_lambda, cudaMemcpyHostToDevice));
+  SETUP_TRY(cudaMalloc(&c->d_eps, sizeof(double) * c->eps.size()));
+  SETUP_TRY(cudaMemcpy(c->d_eps, c->eps.data(), sizeof(double) * c->eps.size(), cudaMemcpyHostToDevice));
+  SETUP_TRY(cudaMalloc(&c->d_optode, sizeof(int) * c->optode_voxel.size()));
+  SETUP_TRY(cudaMemcpy(c->d_optode, c->optode_voxel.data(), sizeof(int) * c->optode_voxel.size(),
+                       cudaMemcpyHostToDevice));
+#undef SETUP_TRY
+  rc = hydot::solver_alloc(c);
+  if (rc) return bail(rc);
+  rc = hydot::build_deflation(c);
+  if (rc) return bail(rc);
+  *out = c;
+  return HYDOT_OK;
+}
+
+int hydot_set_stream(hydot_ctx* ctx, void* stream) {
+  if (!ctx) return HYDOT_ERR_ARG;
+  ctx->stream = (cudaStream_t)stream;
+  return HYDOT_OK;
+}
+
+int hydot_solve_fields(hydot_ctx* ctx, int lam0, int nlam, void* phi_src, void* phi_det, hydot_stats* st) {
+  if (!ctx) return HYDOT_ERR_ARG;
+  if (lam0 < 0 || nlam < 1 || lam0 + nlam > ctx->n_lambda) return fail(ctx, HYDOT_ERR_ARG, "wavelength slice out of range");
+  if (!phi_src && !phi_det) return fail(ctx, HYDOT_ERR_ARG, "phi_src and phi_det are both NULL");
+  if ((phi_src && ctx->n_src == 0) || (phi_det && ctx->n_det == 0))
+    return fail(ctx, HYDOT_ERR_ARG, "output given for an empty optode set");
+  const int nf = (phi_src ? ctx->n_src : 0) + (phi_det ? ctx->n_det : 0);
+  if ((long long)nf * nlam > ctx->max_fields)
+    return fail(ctx, HYDOT_ERR_ARG, "nlam exceeds max_lambda_per_call given to hydot_setup");
+  return hydot::solve_fields_impl(ctx, lam0, nlam, phi_src, phi_det, st);
+}
+
+int hydot_born_assemble(hydot_ctx* ctx, const void* phi_src, const void* phi_det, int lam0, int nlam, long long row0,
+                        long long nrows, void* J, long long ldJ) {
+  if (!ctx) return HYDOT_ERR_ARG;
+  return hydot::born_assemble_impl(ctx, phi_src, phi_det, lam0, nlam, row0, nrows, J, ldJ);
+}
+
+int hydot_born_apply(hydot_ctx* ctx, const void* phi_src, const void* phi_det, int lam0, int nlam, const void* x,
+                     void* y) {
+  if (!ctx) return HYDOT_ERR_ARG;
+  return hydot::born_apply_impl(ctx, phi_src, phi_det, lam0, nlam, x, y);
+}
+
+int hydot_born_apply_T(hydot_ctx* ctx, const void* phi_src, const void* phi_det, int lam0, int nlam, const void* y,
+                       void* g) {
+  if (!ctx) return HYDOT_ERR_ARG;
+  return hydot::born_apply_T_impl(ctx, phi_src, phi_det, lam0, nlam, y, g);
+}
+
+const char* hydot_last_error(const hydot_ctx* ctx) { return ctx ? ctx->err.c_str() : g_setup_error.c_str(); }
+
+void hydot_destroy(hydot_ctx* ctx) {
+  if (!ctx) return;
+  free_all(ctx);
+  delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,406 @@
+// Born rows and implicit Born products (eqn:lippschwin, eqn:perturbation, eqn:measurement).
+//
+//   J[(s,d,a),(c,x)] = -h^3 eps_c(lambda_a) phi_s[a][s][x] phi_d[a][d][x]
+//   y[(s,d,a)]       = -h^3 sum_x phi_s[a][s][x] phi_d[a][d][x] mu_a[x],  mu_a[x] = sum_c eps_c(lambda_a) x[c*N+x]
+//   g[c*N+x]        += -h^3 sum_a eps_c(lambda_a) sum_s phi_s[a][s][x] sum_d Y_a[s][d] phi_d[a][d][x]
+// with slice rows r = (s*n_det + d)*nlam + a.
+#include <algorithm>
+#include <cmath>
+
+#include "hydot_internal.cuh"
+
+namespace hydot {
+
+namespace {
+
+constexpr int MAXC = 16;
+
+// ---------------------------------------------------------------- assembly (write streaming)
+// Blocks walk the slice's rows wavelength-major (all (s,d) of one wavelength, then the next),
+// so the n_src+n_det fields of a wavelength stay in L2 while their rows are written; every
+// element of J is written once with an evict-first store.
+template <typename E, int VEC>
+struct Vec;
+template <> struct Vec<float, 4> { using V = float4; };
+template <> struct Vec<double, 2> { using V = double2; };
+
+template <typename E, int VEC>
+__global__ void __launch_bounds__(256) k_born_rows(const E* __restrict__ ps, const E* __restrict__ pd,
+                                                   const double* __restrict__ eps, int lam0, int nlam, int ns,
+                                                   int nd, int nc, long long N, double h3, long long row0,
+                                                   long long nrows, int sd_lo, int n_sd, E* __restrict__ J,
+                                                   long long ldJ) {
+  using V = typename Vec<E, VEC>::V;
+  const long long nvec = N / VEC;
+  const long long total_rows = (long long)nlam * n_sd;
+  for (long long yy = blockIdx.y; yy < total_rows; yy += gridDim.y) {
+    const int a = (int)(yy / n_sd);
+    const int sd = sd_lo + (int)(yy % n_sd);
+    const long long r = (long long)sd * nlam + a;
+    if (r < row0 || r >= row0 + nrows) continue;
+    const int s = sd / nd, d = sd % nd;
+    const E* fs = ps + ((size_t)a * ns + s) * N;
+    const E* fd = pd + ((size_t)a * nd + d) * N;
+    E* row = J + (size_t)(r - row0) * ldJ;
+    E w[MAXC];
+    for (int c = 0; c < nc; ++c) w[c] = (E)(-h3 * eps[(size_t)(lam0 + a) * nc + c]);
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < nvec; v += (long long)gridDim.x * blockDim.x) {
+      V a4 = reinterpret_cast<const V*>(fs)[v];
+      V b4 = reinterpret_cast<const V*>(fd)[v];
+      V hv;
+      if constexpr (VEC == 4) {
+        hv = make_float4(a4.x * b4.x, a4.y * b4.y, a4.z * b4.z, a4.w * b4.w);
+      } else {
+        hv = make_double2(a4.x * b4.x, a4.y * b4.y);
+      }
+      for (int c = 0; c < nc; ++c) {
+        V o;
+        if constexpr (VEC == 4) {
+          o = make_float4(w[c] * hv.x, w[c] * hv.y, w[c] * hv.z, w[c] * hv.w);
+        } else {
+          o = make_double2(w[c] * hv.x, w[c] * hv.y);
+        }
+        __stcs(reinterpret_cast<V*>(row + (size_t)c * N) + v, o);
+      }
+    }
+    // tail (N not a multiple of VEC) -- also the whole row on the unaligned path
+    for (long long x = nvec * VEC + (long long)blockIdx.x * blockDim.x + threadIdx.x; x < N;
+         x += (long long)gridDim.x * blockDim.x) {
+      E hv = fs[x] * fd[x];
+      for (int c = 0; c < nc; ++c) row[(size_t)c * N + x] = w[c] * hv;
+    }
+  }
+}
+
+template <typename E>
+__global__ void __launch_bounds__(256) k_born_rows_scalar(const E* __restrict__ ps, const E* __restrict__ pd,
+                                                          const double* __restrict__ eps, int lam0, int nlam, int ns,
+                                                          int nd, int nc, long long N, double h3, long long row0,
+                                                          long long nrows, int sd_lo, int n_sd, E* __restrict__ J,
+                                                          long long ldJ) {
+  const long long total_rows = (long long)nlam * n_sd;
+  for (long long yy = blockIdx.y; yy < total_rows; yy += gridDim.y) {
+    const int a = (int)(yy / n_sd);
+    const int sd = sd_lo + (int)(yy % n_sd);
+    const long long r = (long long)sd * nlam + a;
+    if (r < row0 || r >= row0 + nrows) continue;
+    const int s = sd / nd, d = sd % nd;
+    const E* fs = ps + ((size_t)a * ns + s) * N;
+    const E* fd = pd + ((size_t)a * nd + d) * N;
+    E* row = J + (size_t)(r - row0) * ldJ;
+    for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < N; x += (long long)gridDim.x * blockDim.x) {
+      E hv = fs[x] * fd[x];
+      for (int c = 0; c < nc; ++c) row[(size_t)c * N + x] = (E)(-h3 * eps[(size_t)(lam0 + a) * nc + c]) * hv;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- J x
+// Block = (wavelength a, chunk of XC voxels, 32x32 tile of (s, d)). smem holds
+// S[s][x] = phi_s * mu and Dd[d][x] = phi_d for the chunk; 256 threads = 16 voxel groups x
+// 16 (s,d) sub-tiles of 8x8 accumulators. Block partials go to a workspace and a second
+// kernel sums them in a fixed order.
+constexpr int AP_XC = 128;   // voxels per smem stage
+constexpr int AP_XCP = AP_XC + 1;
+constexpr int AP_STAGES = 8; // stages per block
+
+template <typename E>
+constexpr size_t apply_smem_bytes() { return sizeof(E) * (size_t)(2 * 32 * AP_XCP + AP_XC); }
+
+template <typename E>
+__global__ void __launch_bounds__(256) k_apply_partial(const E* __restrict__ ps, const E* __restrict__ pd,
+                                                       const E* __restrict__ xin, const double* __restrict__ eps,
+                                                       int lam0, int ns, int nd, int nc, long long N, int nxb,
+                                                       E* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  E* S = reinterpret_cast<E*>(smraw);  // [32][AP_XCP]  phi_s * mu
+  E* Dd = S + 32 * AP_XCP;             // [32][AP_XCP]  phi_d
+  E* mu = Dd + 32 * AP_XCP;            // [AP_XC]
+  E* red = S;                          // [8][1024], aliases S and Dd after the voxel loop
+  const int xb = blockIdx.x;
+  const int a = blockIdx.y;
+  const int tsd = blockIdx.z;  // (s-tile, d-tile)
+  const int nts = (ns + 31) / 32;
+  const int s0 = (tsd % nts) * 32, d0 = (tsd / nts) * 32;
+  const int t = threadIdx.x;
+  const int grp = t / 16, sub = t % 16;
+  const int si = (sub / 4) * 8, di = (sub % 4) * 8;
+  E w[MAXC];
+  for (int c = 0; c < nc; ++c) w[c] = (E)eps[(size_t)(lam0 + a) * nc + c];
+  E acc[8][8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u)
+#pragma unroll
+    for (int v = 0; v < 8; ++v) acc[u][v] = 0;
+  for (int st = 0; st < AP_STAGES; ++st) {
+    const long long xbase = ((long long)xb * AP_STAGES + st) * AP_XC;
+    if (xbase >= N) break;
+    __syncthreads();
+    for (int q = t; q < AP_XC; q += 256) {
+      long long x = xbase + q;
+      E m = 0;
+      if (x < N)
+        for (int c = 0; c < nc; ++c) m += w[c] * xin[(size_t)c * N + x];
+      mu[q] = m;
+    }
+    __syncthreads();
+    for (int q = t; q < 32 * AP_XC; q += 256) {
+      int row = q / AP_XC, col = q % AP_XC;
+      long long x = xbase + col;
+      int s = s0 + row, d = d0 + row;
+      S[row * AP_XCP + col] = (x < N && s < ns) ? ps[((size_t)a * ns + s) * N + x] * mu[col] : (E)0;
+      Dd[row * AP_XCP + col] = (x < N && d < nd) ? pd[((size_t)a * nd + d) * N + x] : (E)0;
+    }
+    __syncthreads();
+    for (int q = grp; q < AP_XC; q += 16) {
+      E sv[8], dv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) sv[u] = S[(si + u) * AP_XCP + q];
+#pragma unroll
+      for (int v = 0; v < 8; ++v) dv[v] = Dd[(di + v) * AP_XCP + q];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int v = 0; v < 8; ++v) acc[u][v] += sv[u] * dv[v];
+    }
+  }
+  // tree reduction over the 16 voxel groups (fixed order -> deterministic)
+  for (int half = 8; half >= 1; half >>= 1) {
+    __syncthreads();
+    if (grp >= half && grp < 2 * half) {
+      E* dst = red + (size_t)(grp - half) * 1024 + sub * 64;
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int v = 0; v < 8; ++v) dst[u * 8 + v] = acc[u][v];
+    }
+    __syncthreads();
+    if (grp < half) {
+      const E* src = red + (size_t)grp * 1024 + sub * 64;
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int v = 0; v < 8; ++v) acc[u][v] += src[u * 8 + v];
+    }
+  }
+  if (grp == 0) {
+    E* out = part + (((size_t)a * gridDim.z + tsd) * nxb + xb) * 1024;
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+      for (int v = 0; v < 8; ++v) out[(si + u) * 32 + (di + v)] = acc[u][v];
+  }
+}
+
+template <typename E>
+__global__ void k_apply_reduce(const E* __restrict__ part, int nlam, int ns, int nd, int nts, int ntd, int nxb,
+                               double h3, E* __restrict__ y) {
+  long long total = (long long)ns * nd * nlam;
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < total; r += (long long)gridDim.x * blockDim.x) {
+    int a = (int)(r % nlam);
+    int sd = (int)(r / nlam);
+    int s = sd / nd, d = sd % nd;
+    int tsd = (s / 32) + (d / 32) * nts;
+    const E* p = part + (((size_t)a * nts * ntd + tsd) * nxb) * 1024 + (s % 32) * 32 + (d % 32);
+    double sum = 0.0;
+    for (int xb = 0; xb < nxb; ++xb) sum += (double)p[(size_t)xb * 1024];
+    y[r] = (E)(-h3 * sum);
+  }
+}
+
+// ---------------------------------------------------------------- J^T y
+// Thread per voxel; loops over the wavelengths of its group, keeping the detector fields of the
+// voxel in registers: t_a = sum_s phi_s (sum_d Y_a[s][d] phi_d), acc_c += eps_c(lambda_a) t_a.
+constexpr int AT_MAXD = 32;
+
+template <typename E>
+__global__ void __launch_bounds__(256) k_apply_T_partial(const E* __restrict__ ps, const E* __restrict__ pd,
+                                                         const E* __restrict__ y, const double* __restrict__ eps,
+                                                         int lam0, int nlam, int ns, int nd, int nc, long long N,
+                                                         int lam_per_group, E* __restrict__ part) {
+  extern __shared__ unsigned char smraw[];
+  E* Y = reinterpret_cast<E*>(smraw);  // [ns][nd] of one wavelength
+  const int grp = blockIdx.y;
+  const int a0 = grp * lam_per_group, a1 = min(nlam, a0 + lam_per_group);
+  const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool in = x < N;
+  E acc[MAXC];
+  for (int c = 0; c < nc; ++c) acc[c] = 0;
+  for (int a = a0; a < a1; ++a) {
+    __syncthreads();
+    for (int q = threadIdx.x; q < ns * nd; q += blockDim.x) {
+      int s = q / nd, d = q % nd;
+      Y[q] = y[((size_t)s * nd + d) * nlam + a];
+    }
+    __syncthreads();
+    E ta = 0;
+    if (in) {
+      for (int d0 = 0; d0 < nd; d0 += AT_MAXD) {
+        const int dn = min(AT_MAXD, nd - d0);
+        E fd[AT_MAXD];
+#pragma unroll
+        for (int q = 0; q < AT_MAXD; ++q) fd[q] = (q < dn) ? pd[((size_t)a * nd + d0 + q) * N + x] : (E)0;
+        for (int s = 0; s < ns; ++s) {
+          const E* Ys = Y + (size_t)s * nd + d0;
+          E z = 0;
+#pragma unroll
+          for (int q = 0; q < AT_MAXD; ++q) z += (q < dn ? Ys[q] : (E)0) * fd[q];
+          ta += ps[((size_t)a * ns + s) * N + x] * z;
+        }
+      }
+    }
+    for (int c = 0; c < nc; ++c) acc[c] += (E)eps[(size_t)(lam0 + a) * nc + c] * ta;
+  }
+  if (in)
+    for (int c = 0; c < nc; ++c) part[((size_t)grp * nc + c) * N + x] = acc[c];
+}
+
+template <typename E>
+__global__ void k_apply_T_reduce(const E* __restrict__ part, int ngrp, int nc, long long N, double h3,
+                                 E* __restrict__ g) {
+  long long total = (long long)nc * N;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (long long)gridDim.x * blockDim.x) {
+    E sum = 0;
+    for (int gg = 0; gg < ngrp; ++gg) sum += part[(size_t)gg * total + q];
+    g[q] += (E)(-h3) * sum;
+  }
+}
+
+int check_slice(hydot_ctx* ctx, int lam0, int nlam) {
+  if (ctx->cplx) return fail(ctx, HYDOT_ERR_STATE, "Born products are defined for continuous-wave (real) fields only");
+  if (lam0 < 0 || nlam < 1 || lam0 + nlam > ctx->n_lambda) return fail(ctx, HYDOT_ERR_ARG, "wavelength slice out of range");
+  if (ctx->n_chrom > MAXC) return fail(ctx, HYDOT_ERR_ARG, "too many chromophores");
+  return HYDOT_OK;
+}
+
+template <typename E>
+int assemble_t(hydot_ctx* ctx, const E* ps, const E* pd, int lam0, int nlam, long long row0, long long nrows, E* J,
+               long long ldJ) {
+  const long long N = ctx->N;
+  const int ns = ctx->n_src, nd = ctx->n_det, nc = ctx->n_chrom;
+  const double h3 = ctx->h * ctx->h * ctx->h;
+  const int sd_lo = (int)(row0 / nlam);
+  const int sd_hi = (int)((row0 + nrows - 1) / nlam);
+  const int n_sd = sd_hi - sd_lo + 1;
+  const long long total_rows = (long long)nlam * n_sd;
+  constexpr int VEC = sizeof(E) == 4 ? 4 : 2;
+  const bool aligned = (N % VEC == 0) && ((uintptr_t)J % 16 == 0) && ((ldJ * (long long)sizeof(E)) % 16 == 0) &&
+                       ((uintptr_t)ps % 16 == 0) && ((uintptr_t)pd % 16 == 0);
+  const long long per_row = aligned ? N / VEC : N;
+  unsigned gx = (unsigned)std::max<long long>(1, std::min<long long>((per_row + 1023) / 1024, 1024));
+  unsigned gy = (unsigned)std::min<long long>(total_rows, 65535);
+  dim3 grid(gx, gy);
+  if (aligned)
+    k_born_rows<E, VEC><<<grid, 256, 0, ctx->stream>>>(ps, pd, ctx->d_eps, lam0, nlam, ns, nd, nc, N, h3, row0, nrows,
+                                                       sd_lo, n_sd, J, ldJ);
+  else
+    k_born_rows_scalar<E><<<grid, 256, 0, ctx->stream>>>(ps, pd, ctx->d_eps, lam0, nlam, ns, nd, nc, N, h3, row0,
+                                                         nrows, sd_lo, n_sd, J, ldJ);
+  HYDOT_CUDA_TRY(ctx, cudaGetLastError());
+  return HYDOT_OK;
+}
+
+int ensure_ws(hydot_ctx* ctx, size_t bytes) {
+  if (ctx->apply_ws_bytes >= bytes) return HYDOT_OK;
+  if (ctx->d_apply_ws) {
+    // the previous workspace may still be used by queued work on this stream
+    HYDOT_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    cudaFree(ctx->d_apply_ws);
+    ctx->d_apply_ws = nullptr;
+    ctx->apply_ws_bytes = 0;
+  }
+  HYDOT_CUDA_TRY(ctx, cudaMalloc(&ctx->d_apply_ws, bytes));
+  ctx->apply_ws_bytes = bytes;
+  return HYDOT_OK;
+}
+
+template <typename E>
+int apply_t(hydot_ctx* ctx, const E* ps, const E* pd, int lam0, int nlam, const E* x, E* y) {
+  const long long N = ctx->N;
+  const int ns = ctx->n_src, nd = ctx->n_det, nc = ctx->n_chrom;
+  const int nts = (ns + 31) / 32, ntd = (nd + 31) / 32;
+  const long long per_blk = (long long)AP_XC * AP_STAGES;
+  const int nxb = (int)((N + per_blk - 1) / per_blk);
+  size_t bytes = sizeof(E) * (size_t)nlam * nts * ntd * nxb * 1024;
+  int rc = ensure_ws(ctx, bytes);
+  if (rc) return rc;
+  E* part = (E*)ctx->d_apply_ws;
+  dim3 grid(nxb, nlam, nts * ntd);
+  const size_t smem = apply_smem_bytes<E>();
+  HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(k_apply_partial<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_apply_partial<E><<<grid, 256, smem, ctx->stream>>>(ps, pd, x, ctx->d_eps, lam0, ns, nd, nc, N, nxb, part);
+  HYDOT_CUDA_TRY(ctx, cudaGetLastError());
+  long long M = (long long)ns * nd * nlam;
+  k_apply_reduce<E><<<(unsigned)std::min<long long>((M + 255) / 256, 4096), 256, 0, ctx->stream>>>(
+      part, nlam, ns, nd, nts, ntd, nxb, ctx->h * ctx->h * ctx->h, y);
+  HYDOT_CUDA_TRY(ctx, cudaGetLastError());
+  return HYDOT_OK;
+}
+
+template <typename E>
+int apply_T_t(hydot_ctx* ctx, const E* ps, const E* pd, int lam0, int nlam, const E* y, E* g) {
+  const long long N = ctx->N;
+  const int ns = ctx->n_src, nd = ctx->n_det, nc = ctx->n_chrom;
+  // enough blocks to fill the GPU: split the wavelengths into groups with their own partials
+  const long long xblocks = (N + 255) / 256;
+  int ngrp = (int)std::max<long long>(1, std::min<long long>(nlam, (4 * 152 * 8 + xblocks - 1) / xblocks));
+  const int lpg = (nlam + ngrp - 1) / ngrp;
+  ngrp = (nlam + lpg - 1) / lpg;
+  size_t bytes = sizeof(E) * (size_t)ngrp * nc * N;
+  int rc = ensure_ws(ctx, bytes);
+  if (rc) return rc;
+  E* part = (E*)ctx->d_apply_ws;
+  dim3 grid((unsigned)xblocks, ngrp);
+  size_t smem = sizeof(E) * (size_t)ns * nd;
+  if (smem > 48 * 1024) {
+    HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(k_apply_T_partial<E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem));
+  }
+  k_apply_T_partial<E><<<grid, 256, smem, ctx->stream>>>(ps, pd, y, ctx->d_eps, lam0, nlam, ns, nd, nc, N, lpg, part);
+  HYDOT_CUDA_TRY(ctx, cudaGetLastError());
+  long long tot = (long long)nc * N;
+  k_apply_T_reduce<E><<<(unsigned)std::min<long long>((tot + 255) / 256, 8192), 256, 0, ctx->stream>>>(
+      part, ngrp, nc, N, ctx->h * ctx->h * ctx->h, g);
+  HYDOT_CUDA_TRY(ctx, cudaGetLastError());
+  return HYDOT_OK;
+}
+
+}  // namespace
+
+int born_assemble_impl(hydot_ctx* ctx, const void* phi_src, const void* phi_det, int lam0, int nlam, long long row0,
+                       long long nrows, void* J, long long ldJ) {
+  int rc = check_slice(ctx, lam0, nlam);
+  if (rc) return rc;
+  const long long M = (long long)ctx->n_src * ctx->n_det * nlam;
+  if (!phi_src || !phi_det || !J) return fail(ctx, HYDOT_ERR_ARG, "null pointer");
+  if (row0 < 0 || nrows < 0 || row0 + nrows > M) return fail(ctx, HYDOT_ERR_ARG, "row range outside the slice");
+  if (ldJ < (long long)ctx->n_chrom * ctx->N) return fail(ctx, HYDOT_ERR_ARG, "ldJ < n_chrom*N");
+  if (nrows == 0) return HYDOT_OK;
+  if (ctx->precision == HYDOT_MIXED)
+    return assemble_t<float>(ctx, (const float*)phi_src, (const float*)phi_det, lam0, nlam, row0, nrows, (float*)J, ldJ);
+  return assemble_t<double>(ctx, (const double*)phi_src, (const double*)phi_det, lam0, nlam, row0, nrows, (double*)J,
+                            ldJ);
+}
+
+int born_apply_impl(hydot_ctx* ctx, const void* phi_src, const void* phi_det, int lam0, int nlam, const void* x,
+                    void* y) {
+  int rc = check_slice(ctx, lam0, nlam);
+  if (rc) return rc;
+  if (!phi_src || !phi_det || !x || !y) return fail(ctx, HYDOT_ERR_ARG, "null pointer");
+  if (ctx->precision == HYDOT_MIXED)
+    return apply_t<float>(ctx, (const float*)phi_src, (const float*)phi_det, lam0, nlam, (const float*)x, (float*)y);
+  return apply_t<double>(ctx, (const double*)phi_src, (const double*)phi_det, lam0, nlam, (const double*)x, (double*)y);
+}
+
+int born_apply_T_impl(hydot_ctx* ctx, const void* phi_src, const void* phi_det, int lam0, int nlam, const void* y,
+                      void* g) {
+  int rc = check_slice(ctx, lam0, nlam);
+  if (rc) return rc;
+  if (!phi_src || !phi_det || !y || !g) return fail(ctx, HYDOT_ERR_ARG, "null pointer");
+  if (ctx->precision == HYDOT_MIXED)
+    return apply_T_t<float>(ctx, (const float*)phi_src, (const float*)phi_det, lam0, nlam, (const float*)y, (float*)g);
+  return apply_T_t<double>(ctx, (const double*)phi_src, (const double*)phi_det, lam0, nlam, (const double*)y,
+                           (double*)g);
+}
+
+}  // namespace hydot

@@ -1,0 +1,184 @@
+// Internal declarations shared by the translation units of libhydot.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "hydot.h"
+
+namespace hydot {
+
+// ----------------------------------------------------------------------------- scalars
+// Minimal complex type for the frequency-domain (complex-symmetric) solves. All products
+// used by COCG are bilinear (no conjugation); |z| is used only for norms.
+template <typename R>
+struct cpx {
+  R re, im;
+};
+template <typename R>
+__host__ __device__ __forceinline__ cpx<R> operator+(cpx<R> a, cpx<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename R>
+__host__ __device__ __forceinline__ cpx<R> operator-(cpx<R> a, cpx<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename R>
+__host__ __device__ __forceinline__ cpx<R> operator*(cpx<R> a, cpx<R> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename R>
+__host__ __device__ __forceinline__ cpx<R> operator*(R s, cpx<R> a) { return {s * a.re, s * a.im}; }
+template <typename R>
+__host__ __device__ __forceinline__ cpx<R> operator/(cpx<R> a, cpx<R> b) {
+  R den = b.re * b.re + b.im * b.im;
+  return {(a.re * b.re + a.im * b.im) / den, (a.im * b.re - a.re * b.im) / den};
+}
+
+template <typename T> struct Traits;
+template <> struct Traits<float> {
+  using R = float;
+  static constexpr bool cplx = false;
+  __host__ __device__ static float zero() { return 0.f; }
+  __host__ __device__ static float from(double re, double) { return (float)re; }
+  __host__ __device__ static double re(float v) { return v; }
+  __host__ __device__ static double im(float) { return 0.0; }
+  __host__ __device__ static float abs2(float v) { return v * v; }
+};
+template <> struct Traits<double> {
+  using R = double;
+  static constexpr bool cplx = false;
+  __host__ __device__ static double zero() { return 0.0; }
+  __host__ __device__ static double from(double re, double) { return re; }
+  __host__ __device__ static double re(double v) { return v; }
+  __host__ __device__ static double im(double) { return 0.0; }
+  __host__ __device__ static double abs2(double v) { return v * v; }
+};
+template <> struct Traits<cpx<float>> {
+  using R = float;
+  static constexpr bool cplx = true;
+  __host__ __device__ static cpx<float> zero() { return {0.f, 0.f}; }
+  __host__ __device__ static cpx<float> from(double re, double im) { return {(float)re, (float)im}; }
+  __host__ __device__ static double re(cpx<float> v) { return v.re; }
+  __host__ __device__ static double im(cpx<float> v) { return v.im; }
+  __host__ __device__ static float abs2(cpx<float> v) { return v.re * v.re + v.im * v.im; }
+};
+template <> struct Traits<cpx<double>> {
+  using R = double;
+  static constexpr bool cplx = true;
+  __host__ __device__ static cpx<double> zero() { return {0.0, 0.0}; }
+  __host__ __device__ static cpx<double> from(double re, double im) { return {re, im}; }
+  __host__ __device__ static double re(cpx<double> v) { return v.re; }
+  __host__ __device__ static double im(cpx<double> v) { return v.im; }
+  __host__ __device__ static double abs2(cpx<double> v) { return v.re * v.re + v.im * v.im; }
+};
+
+// ----------------------------------------------------------------------------- coefficients
+// Per-wavelength coefficients of the scaled operator  Ahat = A / (D h):
+//   off-diagonal -1 to each existing neighbour,
+//   diagonal 6 + sigma + sum over boundary faces of the cell of (bhat_f - 1),
+//   sigma = mu_a h^2 / D (+ i omega h^2 / (c D)),  bhat_f = 2 h / (h + 4 A_f D).
+// The field of a unit source is phi = x / (D h) where Ahat x = e_cell.
+struct LamCoef {
+  double sigma_re, sigma_im;
+  double bhat[6];
+  double inv_Dh;
+  double mua, D;
+};
+
+// Solver state of one simultaneous field (right-hand side) of a batch.
+enum RhsStatus : int { RHS_INNER = 0, RHS_FINISHED = 1, RHS_DONE = 2 };
+
+struct Tiling {
+  int tx, ty, tz;     // tile extent in cells (tx = 32, ty = 8 threads; tz planes per thread)
+  int ntx, nty, ntz;  // tiles per axis
+  int ntiles;         // tiles per field
+};
+
+}  // namespace hydot
+
+// ----------------------------------------------------------------------------- context
+struct hydot_ctx {
+  // problem
+  int nx, ny, nz;
+  long long N;
+  double h;
+  double robin_A[6];
+  int n_lambda, n_chrom, n_src, n_det;
+  std::vector<double> eps;        // [n_lambda][n_chrom]
+  std::vector<double> c_bg;       // [n_chrom]
+  std::vector<double> mus_prime;  // [n_lambda]
+  double omega, c_medium;
+  std::vector<int> optode_voxel;  // [n_src + n_det] sources then detectors
+  int precision;
+  double tol, tol_cw, inner_tol;
+  int max_iter;
+  int deflation_k;
+  int max_fields;                 // simultaneous fields the workspace holds
+  bool cplx;
+
+  cudaStream_t stream = nullptr;
+  std::string err;
+
+  // per-wavelength tables
+  std::vector<hydot::LamCoef> coef;  // host copy
+  hydot::LamCoef* d_coef = nullptr;
+  double* d_eps = nullptr;           // [n_lambda][n_chrom]
+  int* d_optode = nullptr;           // [n_src + n_det]
+
+  // solver workspace (sized for max_fields simultaneous fields)
+  hydot::Tiling tiling{};
+  void* d_x64 = nullptr;   // [max_fields][N] double (or cpx<double>)
+  void* d_e = nullptr;     // [max_fields][N] inner scalar
+  void* d_r = nullptr;     // [max_fields][N]
+  void* d_p[2] = {nullptr, nullptr};
+  double* d_part = nullptr;  // reduction partials, see solver.cu
+  size_t part_stride = 0;    // doubles per (field) in d_part
+  int* d_status = nullptr;   // [max_fields]
+  int* d_iters = nullptr;    // [max_fields] Krylov iterations, all cycles
+  int* d_cycles = nullptr;   // [max_fields]
+  double* d_scale = nullptr; // [max_fields] ||r|| of the current cycle
+  double* d_final = nullptr; // [max_fields][2] final residual norm, componentwise error
+  int* d_counter = nullptr;  // [counter_len] active-field counters (one per inner iteration)
+  int counter_len = 0;
+  int* h_pinned = nullptr;   // pinned host words for polling
+  // deflation (recycled subspace): W [k][N] FP64 and the k x k Gram blocks
+  double* d_W = nullptr;
+  std::vector<double> gram_L, gram_I, gram_B;  // W^T Lg W, W^T W, W^T B_f W (6 blocks)
+  double* d_Ginv = nullptr;                    // [n_lambda][k][k] inverse of W^T Ahat_j W
+
+  // Born apply workspace
+  void* d_apply_ws = nullptr;
+  size_t apply_ws_bytes = 0;
+};
+
+namespace hydot {
+
+#define HYDOT_CUDA_TRY(ctx, call)                                                     \
+  do {                                                                               \
+    cudaError_t e__ = (call);                                                        \
+    if (e__ != cudaSuccess) {                                                        \
+      (ctx)->err = std::string(#call) + ": " + cudaGetErrorString(e__);              \
+      return e__ == cudaErrorMemoryAllocation ? HYDOT_ERR_OOM : HYDOT_ERR_CUDA;       \
+    }                                                                                \
+  } while (0)
+
+inline int fail(hydot_ctx* ctx, int code, const std::string& msg) {
+  ctx->err = msg;
+  return code;
+}
+
+// solver.cu
+int solve_fields_impl(hydot_ctx* ctx, int lam0, int nlam, void* phi_src, void* phi_det, hydot_stats* st);
+int solver_alloc(hydot_ctx* ctx);
+void solver_free(hydot_ctx* ctx);
+int build_deflation(hydot_ctx* ctx);
+
+// born.cu
+int born_assemble_impl(hydot_ctx* ctx, const void* phi_src, const void* phi_det, int lam0, int nlam,
+                       long long row0, long long nrows, void* J, long long ldJ);
+int born_apply_impl(hydot_ctx* ctx, const void* phi_src, const void* phi_det, int lam0, int nlam,
+                    const void* x, void* y);
+int born_apply_T_impl(hydot_ctx* ctx, const void* phi_src, const void* phi_det, int lam0, int nlam,
+                      const void* y, void* g);
+
+}  // namespace hydot

@@ -1,0 +1,719 @@
+// Batched field solves: matrix-free FV diffusion operator, Jacobi-preconditioned CG (COCG for
+// the complex-symmetric frequency-domain operator) with FP64 residuals and iterative refinement.
+//
+// Each simultaneous field ("rhs") solves  Ahat x = e_cell  with Ahat = A_j / (D_j h) (the
+// operator of eqn:discincident restated as finite volumes, see hydot.h); the field is
+// phi = x / (D_j h). One refinement cycle:
+//   K_res    r64 = b - Ahat x64 in FP64, ||r64||_2 and the componentwise backward error
+//            max_i |r64_i| / (|Ahat||x64| + |b|)_i                         [per-tile partials]
+//   K_decide stop, or start a cycle with scale = ||r64||                   [one thread per rhs]
+//   K_init   r = r64 / scale in the inner precision, rho_0 = r^T D^-1 r
+//   K_A/K_B  inner PCG/COCG on Ahat e = r (two kernels per iteration, see below)
+//   K_fold   x64 += scale * e
+// The inner iteration is split in two passes over memory because alpha needs the global
+// p^T Ahat p before x and r can move:
+//   K_A  p_new = D^-1 r + beta p_old (formed on the fly, also at the stencil neighbours),
+//        gamma = p_new^T Ahat p_new;  writes p_new          (reads r, p_old; writes p_new)
+//   K_B  alpha = rho / gamma; e += alpha p; r -= alpha Ahat p (Ahat p recomputed from p);
+//        rho' = r^T D^-1 r, ||r||^2                         (reads e, r, p; writes e, r)
+// Scalars are never stored: every block of a field sums the per-tile partials of the previous
+// pass in the same fixed order, so all blocks agree bit for bit and the result is reproducible.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "hydot_internal.cuh"
+
+namespace hydot {
+
+namespace {
+
+constexpr int TX = 32;
+constexpr int TY = 8;
+constexpr int NTHREADS = TX * TY;
+constexpr int NWARPS = NTHREADS / 32;
+constexpr int MAX_INNER_PER_CYCLE = 4096;
+constexpr int MAX_CYCLES = 64;
+constexpr int POLL_GROUP = 8;
+
+struct Geo {
+  int nx, ny, nz;
+  long long N;
+  int ntx, nty, ntz, tz, ntiles;
+};
+
+// Per-field partial layout (doubles), with T = ntiles:
+//   [0, 4T)   rho[parity][tile][re,im]
+//   [4T, 6T)  rr[parity][tile]
+//   [6T, 8T)  gamma[tile][re,im]
+//   [8T, 10T) res[tile][rr64, omega]
+__host__ __device__ inline size_t part_stride(int T) { return (size_t)10 * T; }
+
+struct Batch {
+  const LamCoef* coef;
+  const int* optode;  // voxel of optode f (sources then detectors)
+  int lam0, f_begin, nf, nrhs;
+  int* status;
+  int* iters;
+  int* cycles;
+  double* scale;
+  double* fin;
+  double* part;
+  int* counter;
+  double tol_in2;
+  int max_inner, max_iter;
+  double tol, tol_cw;
+};
+
+__device__ __forceinline__ int rhs_lambda(const Batch& b, int rhs) { return b.lam0 + rhs / b.nf; }
+__device__ __forceinline__ long long rhs_source(const Batch& b, int rhs) {
+  return (long long)b.optode[b.f_begin + rhs % b.nf];
+}
+
+// diagonal of Ahat at (i,j,k): 6 + sigma + sum over the cell's boundary faces of (bhat_f - 1)
+struct Diag {
+  double dre, dim;   // 6 + sigma
+  double fa[6];      // bhat_f - 1
+  __device__ void load(const LamCoef& c) {
+    dre = 6.0 + c.sigma_re;
+    dim = c.sigma_im;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) fa[f] = c.bhat[f] - 1.0;
+  }
+  __device__ __forceinline__ double add(const Geo& g, int i, int j, int k) const {
+    double a = 0.0;
+    if (i == 0) a += fa[0];
+    if (i == g.nx - 1) a += fa[1];
+    if (j == 0) a += fa[2];
+    if (j == g.ny - 1) a += fa[3];
+    if (k == 0) a += fa[4];
+    if (k == g.nz - 1) a += fa[5];
+    return a;
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ T make_diag(const Diag& d, double add) {
+  return Traits<T>::from(d.dre + add, d.dim);
+}
+template <typename T>
+__device__ __forceinline__ T inv(T v) {
+  if constexpr (Traits<T>::cplx) {
+    using R = typename Traits<T>::R;
+    R den = v.re * v.re + v.im * v.im;
+    return T{v.re / den, -v.im / den};
+  } else {
+    return (T)1 / v;
+  }
+}
+template <typename T>
+__device__ __forceinline__ T scal(typename Traits<T>::R s, T v) {
+  if constexpr (Traits<T>::cplx) return s * v; else return s * v;
+}
+
+// ---------------------------------------------------------------- block reductions
+template <typename R>
+__device__ __forceinline__ R warp_sum(R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Sum NV per-thread values over the block (deterministic); result valid in thread 0.
+template <int NV, typename R>
+__device__ void block_sum(R (&v)[NV], double (&out)[NV], double* sm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    R s = warp_sum(v[q]);
+    if (lane == 0) sm[q * NWARPS + warp] = (double)s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double s = 0.0;
+      for (int w = 0; w < NWARPS; ++w) s += sm[q * NWARPS + w];
+      out[q] = s;
+    }
+  }
+  __syncthreads();
+}
+
+// Sum NV strided partial arrays over the tiles of one field; every thread gets the result.
+// p points at the first value; element (q, t) is p[q*qstride + t*tstride].
+template <int NV>
+__device__ void tile_sum(const double* p, int qstride, int tstride, int ntiles, double (&out)[NV], double* sm) {
+  double v[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) v[q] = 0.0;
+  for (int t = threadIdx.x; t < ntiles; t += NTHREADS) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] += p[q * qstride + (size_t)t * tstride];
+  }
+  double r[NV];
+  block_sum<NV, double>(v, r, sm);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) sm[64 + q] = r[q];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < NV; ++q) out[q] = sm[64 + q];
+  __syncthreads();
+}
+
+struct TileCoord {
+  int rhs, tile, i, j, k0, k1;
+  bool in;
+};
+__device__ __forceinline__ TileCoord tile_coord(const Geo& g) {
+  TileCoord c;
+  c.rhs = blockIdx.x / g.ntiles;
+  c.tile = blockIdx.x % g.ntiles;
+  int tx = c.tile % g.ntx;
+  int rem = c.tile / g.ntx;
+  int ty = rem % g.nty;
+  int tzi = rem / g.nty;
+  c.i = tx * TX + (threadIdx.x % TX);
+  c.j = ty * TY + (threadIdx.x / TX);
+  c.k0 = tzi * g.tz;
+  c.k1 = min(c.k0 + g.tz, g.nz);
+  c.in = (c.i < g.nx) && (c.j < g.ny);
+  return c;
+}
+
+__device__ __forceinline__ long long vidx(const Geo& g, int i, int j, int k) {
+  return ((long long)k * g.ny + j) * g.nx + i;
+}
+
+// ---------------------------------------------------------------- FP64 residual
+template <typename X>
+__global__ void __launch_bounds__(NTHREADS) k_residual(Geo g, Batch b, const X* __restrict__ x64) {
+  __shared__ double sm[96];
+  TileCoord c = tile_coord(g);
+  if (b.status[c.rhs] != RHS_FINISHED) return;
+  const LamCoef& lc = b.coef[rhs_lambda(b, c.rhs)];
+  Diag dg;
+  dg.load(lc);
+  const long long src = rhs_source(b, c.rhs);
+  const X* x = x64 + (size_t)c.rhs * g.N;
+  double rr = 0.0, om = 0.0;
+  if (c.in) {
+    auto ld = [&](int k) { return x[vidx(g, c.i, c.j, k)]; };
+    X zero = Traits<X>::zero();
+    X xm = c.k0 > 0 ? ld(c.k0 - 1) : zero;
+    X xc = ld(c.k0);
+    for (int k = c.k0; k < c.k1; ++k) {
+      X xp = (k + 1 < g.nz) ? ld(k + 1) : zero;
+      X s = xm + xp;
+      double as = sqrt(Traits<X>::abs2(xm)) + sqrt(Traits<X>::abs2(xp));
+      if (c.i > 0) { X v = x[vidx(g, c.i - 1, c.j, k)]; s = s + v; as += sqrt(Traits<X>::abs2(v)); }
+      if (c.i < g.nx - 1) { X v = x[vidx(g, c.i + 1, c.j, k)]; s = s + v; as += sqrt(Traits<X>::abs2(v)); }
+      if (c.j > 0) { X v = x[vidx(g, c.i, c.j - 1, k)]; s = s + v; as += sqrt(Traits<X>::abs2(v)); }
+      if (c.j < g.ny - 1) { X v = x[vidx(g, c.i, c.j + 1, k)]; s = s + v; as += sqrt(Traits<X>::abs2(v)); }
+      X d = make_diag<X>(dg, dg.add(g, c.i, c.j, k));
+      X ax = d * xc - s;
+      long long id = vidx(g, c.i, c.j, k);
+      double bi = (id == src) ? 1.0 : 0.0;
+      X r = Traits<X>::from(bi, 0.0) - ax;
+      double r2 = Traits<X>::abs2(r);
+      rr += r2;
+      double den = sqrt(Traits<X>::abs2(d)) * sqrt(Traits<X>::abs2(xc)) + as + bi;
+      if (r2 > 0.0) om = fmax(om, den > 0.0 ? sqrt(r2) / den : INFINITY);
+      xm = xc;
+      xc = xp;
+    }
+  }
+  // sum rr, max om
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double s1 = warp_sum(rr), m1 = warp_max(om);
+  if (lane == 0) { sm[warp] = s1; sm[32 + warp] = m1; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0, m = 0.0;
+    for (int w = 0; w < NWARPS; ++w) { s += sm[w]; m = fmax(m, sm[32 + w]); }
+    double* p = b.part + (size_t)c.rhs * part_stride(g.ntiles) + 8 * g.ntiles + 2 * c.tile;
+    p[0] = s;
+    p[1] = m;
+  }
+}
+
+__global__ void k_decide(Geo g, Batch b) {
+  int rhs = blockIdx.x * blockDim.x + threadIdx.x;
+  if (rhs >= b.nrhs) return;
+  if (b.status[rhs] != RHS_FINISHED) return;
+  const double* p = b.part + (size_t)rhs * part_stride(g.ntiles) + 8 * g.ntiles;
+  double rr = 0.0, om = 0.0;
+  for (int t = 0; t < g.ntiles; ++t) { rr += p[2 * t]; om = fmax(om, p[2 * t + 1]); }
+  double res = sqrt(rr);  // ||b|| = 1 for a unit point source
+  b.fin[2 * rhs] = res;
+  b.fin[2 * rhs + 1] = om;
+  bool conv = (res <= b.tol) && (b.tol_cw <= 0.0 || om <= b.tol_cw);
+  if (conv || b.iters[rhs] >= b.max_iter || b.cycles[rhs] >= MAX_CYCLES || rr == 0.0) {
+    b.status[rhs] = RHS_DONE;
+  } else {
+    b.status[rhs] = RHS_INNER;
+    b.scale[rhs] = res;
+    b.cycles[rhs] += 1;
+    atomicAdd(&b.counter[0], 1);
+  }
+}
+
+// ---------------------------------------------------------------- inner init
+template <typename T, typename X>
+__global__ void __launch_bounds__(NTHREADS) k_init(Geo g, Batch b, const X* __restrict__ x64, T* __restrict__ R) {
+  __shared__ double sm[96];
+  TileCoord c = tile_coord(g);
+  if (b.status[c.rhs] != RHS_INNER) return;
+  using Rt = typename Traits<T>::R;
+  const LamCoef& lc = b.coef[rhs_lambda(b, c.rhs)];
+  Diag dg;
+  dg.load(lc);
+  const long long src = rhs_source(b, c.rhs);
+  const double inv_scale = 1.0 / b.scale[c.rhs];
+  const X* x = x64 + (size_t)c.rhs * g.N;
+  T* r = R + (size_t)c.rhs * g.N;
+  Rt acc[3] = {0, 0, 0};  // rho re, rho im, rr
+  if (c.in) {
+    auto ld = [&](int k) { return x[vidx(g, c.i, c.j, k)]; };
+    X zero = Traits<X>::zero();
+    X xm = c.k0 > 0 ? ld(c.k0 - 1) : zero;
+    X xc = ld(c.k0);
+    for (int k = c.k0; k < c.k1; ++k) {
+      X xp = (k + 1 < g.nz) ? ld(k + 1) : zero;
+      X s = xm + xp;
+      if (c.i > 0) s = s + x[vidx(g, c.i - 1, c.j, k)];
+      if (c.i < g.nx - 1) s = s + x[vidx(g, c.i + 1, c.j, k)];
+      if (c.j > 0) s = s + x[vidx(g, c.i, c.j - 1, k)];
+      if (c.j < g.ny - 1) s = s + x[vidx(g, c.i, c.j + 1, k)];
+      double add = dg.add(g, c.i, c.j, k);
+      X d = make_diag<X>(dg, add);
+      long long id = vidx(g, c.i, c.j, k);
+      X r64 = Traits<X>::from(id == src ? 1.0 : 0.0, 0.0) - (d * xc - s);
+      T rv = Traits<T>::from(Traits<X>::re(r64) * inv_scale, Traits<X>::im(r64) * inv_scale);
+      r[id] = rv;
+      T z = rv * inv(make_diag<T>(dg, add));
+      T rz = rv * z;
+      acc[0] += (Rt)Traits<T>::re(rz);
+      acc[1] += (Rt)Traits<T>::im(rz);
+      acc[2] += Traits<T>::abs2(rv);
+      xm = xc;
+      xc = xp;
+    }
+  }
+  double out[3];
+  block_sum<3, Rt>(acc, out, sm);
+  if (threadIdx.x == 0) {
+    double* p = b.part + (size_t)c.rhs * part_stride(g.ntiles);
+    p[2 * c.tile] = out[0];           // rho parity 0
+    p[2 * c.tile + 1] = out[1];
+    p[4 * g.ntiles + c.tile] = out[2];  // rr parity 0
+  }
+}
+
+// ---------------------------------------------------------------- inner K_A
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS) k_dir(Geo g, Batch b, int it, const T* __restrict__ R,
+                                                  const T* __restrict__ Pold, T* __restrict__ Pnew) {
+  __shared__ double sm[96];
+  __shared__ int s_status;
+  TileCoord c = tile_coord(g);
+  // the tile-0 block of this field may flip its status during this launch: read it once
+  if (threadIdx.x == 0) s_status = b.status[c.rhs];
+  __syncthreads();
+  if (s_status != RHS_INNER) return;
+  using Rt = typename Traits<T>::R;
+  const int T_ = g.ntiles;
+  double* pb = b.part + (size_t)c.rhs * part_stride(T_);
+  const int par = it & 1;
+  double cur[3];
+  {
+    double t2[2];
+    tile_sum<2>(pb + 2 * T_ * par, 1, 2, T_, t2, sm);  // rho (re, im) of the current residual
+    cur[0] = t2[0];
+    cur[1] = t2[1];
+    double t1[1];
+    tile_sum<1>(pb + 4 * T_ + T_ * par, 0, 1, T_, t1, sm);
+    cur[2] = t1[0];
+  }
+  // convergence of the inner solve (residual norm relative to the normalised start)
+  if (cur[2] <= b.tol_in2 || it >= b.max_inner || b.iters[c.rhs] >= b.max_iter || cur[2] == 0.0) {
+    if (c.tile == 0 && threadIdx.x == 0) b.status[c.rhs] = RHS_FINISHED;
+    return;
+  }
+  if (c.tile == 0 && threadIdx.x == 0) atomicAdd(&b.counter[1 + it], 1);
+  T beta = Traits<T>::zero();
+  if (it > 0) {
+    double prev[2];
+    tile_sum<2>(pb + 2 * T_ * (par ^ 1), 1, 2, T_, prev, sm);
+    // beta = rho_cur / rho_prev (complex division in double)
+    double den = prev[0] * prev[0] + prev[1] * prev[1];
+    double br = (cur[0] * prev[0] + cur[1] * prev[1]) / den;
+    double bi = (cur[1] * prev[0] - cur[0] * prev[1]) / den;
+    beta = Traits<T>::from(br, bi);
+  }
+  const LamCoef& lc = b.coef[rhs_lambda(b, c.rhs)];
+  Diag dg;
+  dg.load(lc);
+  const T* r = R + (size_t)c.rhs * g.N;
+  const T* po = Pold + (size_t)c.rhs * g.N;
+  T* pn = Pnew + (size_t)c.rhs * g.N;
+  const T dint = make_diag<T>(dg, 0.0);
+  const T idint = inv(dint);
+  const bool first = (it == 0);
+  Rt acc[2] = {0, 0};
+  if (c.in) {
+    auto P = [&](int ii, int jj, int kk) -> T {
+      long long id = vidx(g, ii, jj, kk);
+      double add = dg.add(g, ii, jj, kk);
+      T idd = (add == 0.0) ? idint : inv(make_diag<T>(dg, add));
+      T z = r[id] * idd;
+      return first ? z : z + beta * po[id];
+    };
+    T zero = Traits<T>::zero();
+    T pm = c.k0 > 0 ? P(c.i, c.j, c.k0 - 1) : zero;
+    T pc = P(c.i, c.j, c.k0);
+    for (int k = c.k0; k < c.k1; ++k) {
+      T pp = (k + 1 < g.nz) ? P(c.i, c.j, k + 1) : zero;
+      T s = pm + pp;
+      if (c.i > 0) s = s + P(c.i - 1, c.j, k);
+      if (c.i < g.nx - 1) s = s + P(c.i + 1, c.j, k);
+      if (c.j > 0) s = s + P(c.i, c.j - 1, k);
+      if (c.j < g.ny - 1) s = s + P(c.i, c.j + 1, k);
+      T d = make_diag<T>(dg, dg.add(g, c.i, c.j, k));
+      T q = d * pc - s;
+      T pq = pc * q;
+      acc[0] += (Rt)Traits<T>::re(pq);
+      acc[1] += (Rt)Traits<T>::im(pq);
+      pn[vidx(g, c.i, c.j, k)] = pc;
+      pm = pc;
+      pc = pp;
+    }
+  }
+  double out[2];
+  block_sum<2, Rt>(acc, out, sm);
+  if (threadIdx.x == 0) {
+    pb[6 * T_ + 2 * c.tile] = out[0];
+    pb[6 * T_ + 2 * c.tile + 1] = out[1];
+  }
+}
+
+// ---------------------------------------------------------------- inner K_B
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS) k_update(Geo g, Batch b, int it, T* __restrict__ E, T* __restrict__ R,
+                                                     const T* __restrict__ Pn) {
+  __shared__ double sm[96];
+  TileCoord c = tile_coord(g);
+  if (b.status[c.rhs] != RHS_INNER) return;
+  using Rt = typename Traits<T>::R;
+  const int T_ = g.ntiles;
+  double* pb = b.part + (size_t)c.rhs * part_stride(T_);
+  const int par = it & 1;
+  double rho[2], gam[2];
+  tile_sum<2>(pb + 2 * T_ * par, 1, 2, T_, rho, sm);
+  tile_sum<2>(pb + 6 * T_, 1, 2, T_, gam, sm);
+  double den = gam[0] * gam[0] + gam[1] * gam[1];
+  double ar = (rho[0] * gam[0] + rho[1] * gam[1]) / den;
+  double ai = (rho[1] * gam[0] - rho[0] * gam[1]) / den;
+  const T alpha = Traits<T>::from(ar, ai);
+  const LamCoef& lc = b.coef[rhs_lambda(b, c.rhs)];
+  Diag dg;
+  dg.load(lc);
+  T* e = E + (size_t)c.rhs * g.N;
+  T* r = R + (size_t)c.rhs * g.N;
+  const T* p = Pn + (size_t)c.rhs * g.N;
+  const T idint = inv(make_diag<T>(dg, 0.0));
+  const bool first = (it == 0);
+  Rt acc[3] = {0, 0, 0};
+  if (c.in) {
+    auto ld = [&](int k) { return p[vidx(g, c.i, c.j, k)]; };
+    T zero = Traits<T>::zero();
+    T pm = c.k0 > 0 ? ld(c.k0 - 1) : zero;
+    T pc = ld(c.k0);
+    for (int k = c.k0; k < c.k1; ++k) {
+      T pp = (k + 1 < g.nz) ? ld(k + 1) : zero;
+      T s = pm + pp;
+      if (c.i > 0) s = s + p[vidx(g, c.i - 1, c.j, k)];
+      if (c.i < g.nx - 1) s = s + p[vidx(g, c.i + 1, c.j, k)];
+      if (c.j > 0) s = s + p[vidx(g, c.i, c.j - 1, k)];
+      if (c.j < g.ny - 1) s = s + p[vidx(g, c.i, c.j + 1, k)];
+      double add = dg.add(g, c.i, c.j, k);
+      T d = make_diag<T>(dg, add);
+      T q = d * pc - s;
+      long long id = vidx(g, c.i, c.j, k);
+      T ev = first ? alpha * pc : e[id] + alpha * pc;
+      T rv = r[id] - alpha * q;
+      e[id] = ev;
+      r[id] = rv;
+      T z = rv * ((add == 0.0) ? idint : inv(d));
+      T rz = rv * z;
+      acc[0] += (Rt)Traits<T>::re(rz);
+      acc[1] += (Rt)Traits<T>::im(rz);
+      acc[2] += Traits<T>::abs2(rv);
+      pm = pc;
+      pc = pp;
+    }
+  }
+  double out[3];
+  block_sum<3, Rt>(acc, out, sm);
+  if (threadIdx.x == 0) {
+    pb[2 * T_ * (par ^ 1) + 2 * c.tile] = out[0];
+    pb[2 * T_ * (par ^ 1) + 2 * c.tile + 1] = out[1];
+    pb[4 * T_ + T_ * (par ^ 1) + c.tile] = out[2];
+    if (c.tile == 0) b.iters[c.rhs] += 1;
+  }
+}
+
+// ---------------------------------------------------------------- fold, output
+template <typename T, typename X>
+__global__ void k_fold(Geo g, Batch b, X* __restrict__ x64, const T* __restrict__ E) {
+  for (int rhs = blockIdx.y; rhs < b.nrhs; rhs += gridDim.y) {
+    if (b.status[rhs] != RHS_FINISHED) continue;
+    const double s = b.scale[rhs];
+    X* x = x64 + (size_t)rhs * g.N;
+    const T* e = E + (size_t)rhs * g.N;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < g.N; v += (long long)gridDim.x * blockDim.x) {
+      T ev = e[v];
+      x[v] = x[v] + Traits<X>::from(s * Traits<T>::re(ev), s * Traits<T>::im(ev));
+    }
+  }
+}
+
+template <typename X, typename O>
+__global__ void k_output(Geo g, Batch b, const X* __restrict__ x64, O* __restrict__ phi_src,
+                         O* __restrict__ phi_det, int n_src, int n_det) {
+  for (int rhs = blockIdx.y; rhs < b.nrhs; rhs += gridDim.y) {
+    int a = rhs / b.nf;
+    int f = b.f_begin + rhs % b.nf;
+    const double sc = b.coef[b.lam0 + a].inv_Dh;
+    O* out = (f < n_src) ? phi_src + ((size_t)a * n_src + f) * g.N : phi_det + ((size_t)a * n_det + (f - n_src)) * g.N;
+    const X* x = x64 + (size_t)rhs * g.N;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < g.N; v += (long long)gridDim.x * blockDim.x) {
+      X xv = x[v];
+      out[v] = Traits<O>::from(sc * Traits<X>::re(xv), sc * Traits<X>::im(xv));
+    }
+  }
+}
+
+__global__ void k_reset(Batch b) {
+  int rhs = blockIdx.x * blockDim.x + threadIdx.x;
+  if (rhs >= b.nrhs) return;
+  b.status[rhs] = RHS_FINISHED;
+  b.iters[rhs] = 0;
+  b.cycles[rhs] = 0;
+  b.scale[rhs] = 1.0;
+}
+
+Geo make_geo(const hydot_ctx* ctx) {
+  Geo g;
+  g.nx = ctx->nx;
+  g.ny = ctx->ny;
+  g.nz = ctx->nz;
+  g.N = ctx->N;
+  g.ntx = ctx->tiling.ntx;
+  g.nty = ctx->tiling.nty;
+  g.ntz = ctx->tiling.ntz;
+  g.tz = ctx->tiling.tz;
+  g.ntiles = ctx->tiling.ntiles;
+  return g;
+}
+
+template <typename T, typename X, typename O>
+int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_stats* st) {
+  Geo g = make_geo(ctx);
+  Batch b{};
+  b.coef = ctx->d_coef;
+  b.optode = ctx->d_optode;
+  b.lam0 = lam0;
+  if (phi_src && phi_det) { b.f_begin = 0; b.nf = ctx->n_src + ctx->n_det; }
+  else if (phi_src) { b.f_begin = 0; b.nf = ctx->n_src; }
+  else { b.f_begin = ctx->n_src; b.nf = ctx->n_det; }
+  b.nrhs = b.nf * nlam;
+  b.status = ctx->d_status;
+  b.iters = ctx->d_iters;
+  b.cycles = ctx->d_cycles;
+  b.scale = ctx->d_scale;
+  b.fin = ctx->d_final;
+  b.part = ctx->d_part;
+  b.counter = ctx->d_counter;
+  const bool mixed = ctx->precision == HYDOT_MIXED;
+  const double tin = mixed ? (ctx->inner_tol > 0 ? ctx->inner_tol : 1e-5) : ctx->tol;
+  b.tol_in2 = tin * tin;
+  b.max_inner = MAX_INNER_PER_CYCLE;
+  b.max_iter = ctx->max_iter;
+  b.tol = ctx->tol;
+  b.tol_cw = ctx->tol_cw;
+  cudaStream_t s = ctx->stream;
+
+  X* x64 = (X*)ctx->d_x64;
+  T* E = (T*)ctx->d_e;
+  T* R = (T*)ctx->d_r;
+  T* P[2] = {(T*)ctx->d_p[0], (T*)ctx->d_p[1]};
+  const unsigned nblk = (unsigned)((long long)b.nrhs * g.ntiles);
+  const dim3 blk(NTHREADS);
+
+  HYDOT_CUDA_TRY(ctx, cudaMemsetAsync(x64, 0, sizeof(X) * (size_t)b.nrhs * g.N, s));
+  k_reset<<<(b.nrhs + 255) / 256, 256, 0, s>>>(b);
+  HYDOT_CUDA_TRY(ctx, cudaGetLastError());
+
+  volatile int* hp = ctx->h_pinned;
+  for (int cycle = 0; cycle <= MAX_CYCLES; ++cycle) {
+    k_residual<X><<<nblk, blk, 0, s>>>(g, b, x64);
+    HYDOT_CUDA_TRY(ctx, cudaMemsetAsync(b.counter, 0, sizeof(int) * (size_t)ctx->counter_len, s));
+    k_decide<<<(b.nrhs + 255) / 256, 256, 0, s>>>(g, b);
+    HYDOT_CUDA_TRY(ctx, cudaMemcpyAsync((void*)&hp[0], b.counter, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HYDOT_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    if (hp[0] == 0) break;
+    k_init<T, X><<<nblk, blk, 0, s>>>(g, b, x64, R);
+    HYDOT_CUDA_TRY(ctx, cudaGetLastError());
+    // inner iterations in groups; the group after the one being polled is already queued
+    int it = 0;
+    int pending = -1;  // index of the iteration whose counter is in flight
+    cudaEvent_t ev[2];
+    HYDOT_CUDA_TRY(ctx, cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+    HYDOT_CUDA_TRY(ctx, cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
+    int slot = 0;
+    bool stop = false;
+    while (!stop && it < MAX_INNER_PER_CYCLE) {
+      int g_end = std::min(it + POLL_GROUP, MAX_INNER_PER_CYCLE);
+      for (; it < g_end; ++it) {
+        k_dir<T><<<nblk, blk, 0, s>>>(g, b, it, R, P[it & 1], P[(it + 1) & 1]);
+        k_update<T><<<nblk, blk, 0, s>>>(g, b, it, E, R, P[(it + 1) & 1]);
+      }
+      HYDOT_CUDA_TRY(ctx, cudaGetLastError());
+      HYDOT_CUDA_TRY(ctx, cudaMemcpyAsync((void*)&hp[1 + slot], b.counter + 1 + (it - 1), sizeof(int),
+                                          cudaMemcpyDeviceToHost, s));
+      HYDOT_CUDA_TRY(ctx, cudaEventRecord(ev[slot], s));
+      if (pending >= 0) {
+        int ps = slot ^ 1;
+        HYDOT_CUDA_TRY(ctx, cudaEventSynchronize(ev[ps]));
+        if (hp[1 + ps] == 0) stop = true;
+      }
+      pending = it - 1;
+      slot ^= 1;
+    }
+    HYDOT_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    // any field still marked INNER hit the per-cycle cap: finish it
+    {
+      dim3 fg((unsigned)std::min<long long>((g.N + 255) / 256, 1024), (unsigned)std::min(b.nrhs, 65535));
+      // fields that were still iterating when the cap hit are FINISHED by the next k_dir; run it
+      k_dir<T><<<nblk, blk, 0, s>>>(g, b, MAX_INNER_PER_CYCLE, R, P[0], P[1]);
+      k_fold<T, X><<<fg, 256, 0, s>>>(g, b, x64, E);
+      HYDOT_CUDA_TRY(ctx, cudaGetLastError());
+    }
+  }
+  {
+    dim3 fg((unsigned)std::min<long long>((g.N + 255) / 256, 1024), (unsigned)std::min(b.nrhs, 65535));
+    k_output<X, O><<<fg, 256, 0, s>>>(g, b, x64, phi_src, phi_det, ctx->n_src, ctx->n_det);
+    HYDOT_CUDA_TRY(ctx, cudaGetLastError());
+  }
+  // statistics
+  std::vector<int> iters(b.nrhs), cycles(b.nrhs);
+  std::vector<double> fin(2 * (size_t)b.nrhs);
+  HYDOT_CUDA_TRY(ctx, cudaMemcpyAsync(iters.data(), b.iters, sizeof(int) * b.nrhs, cudaMemcpyDeviceToHost, s));
+  HYDOT_CUDA_TRY(ctx, cudaMemcpyAsync(cycles.data(), b.cycles, sizeof(int) * b.nrhs, cudaMemcpyDeviceToHost, s));
+  HYDOT_CUDA_TRY(ctx, cudaMemcpyAsync(fin.data(), b.fin, sizeof(double) * 2 * b.nrhs, cudaMemcpyDeviceToHost, s));
+  HYDOT_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  int nnc = 0, imax = 0, cmax = 0;
+  double isum = 0, rmax = 0, omax = 0;
+  for (int i = 0; i < b.nrhs; ++i) {
+    bool conv = fin[2 * i] <= ctx->tol && (ctx->tol_cw <= 0 || fin[2 * i + 1] <= ctx->tol_cw);
+    nnc += conv ? 0 : 1;
+    imax = std::max(imax, iters[i]);
+    cmax = std::max(cmax, cycles[i]);
+    isum += iters[i];
+    rmax = std::max(rmax, fin[2 * i]);
+    omax = std::max(omax, fin[2 * i + 1]);
+  }
+  if (st) {
+    st->n_fields = b.nrhs;
+    st->n_not_converged = nnc;
+    st->iters_max = imax;
+    st->iters_mean = b.nrhs ? isum / b.nrhs : 0.0;
+    st->cycles_max = cmax;
+    st->resid_max = rmax;
+    st->cw_max = omax;
+  }
+  if (nnc) {
+    ctx->err = std::to_string(nnc) + " of " + std::to_string(b.nrhs) + " fields missed the tolerance";
+    return HYDOT_ERR_NOT_CONVERGED;
+  }
+  return HYDOT_OK;
+}
+
+}  // namespace
+
+int solver_alloc(hydot_ctx* ctx) {
+  Tiling& t = ctx->tiling;
+  t.tx = TX;
+  t.ty = TY;
+  t.tz = std::min(ctx->nz, 16);
+  t.ntx = (ctx->nx + TX - 1) / TX;
+  t.nty = (ctx->ny + TY - 1) / TY;
+  t.ntz = (ctx->nz + t.tz - 1) / t.tz;
+  t.ntiles = t.ntx * t.nty * t.ntz;
+  const size_t F = (size_t)ctx->max_fields, N = (size_t)ctx->N;
+  const bool mixed = ctx->precision == HYDOT_MIXED;
+  const size_t xw = ctx->cplx ? 16 : 8;
+  const size_t iw = (mixed ? 4 : 8) * (ctx->cplx ? 2 : 1);
+  HYDOT_CUDA_TRY(ctx, cudaMalloc(&ctx->d_x64, xw * F * N));
+  HYDOT_CUDA_TRY(ctx, cudaMalloc(&ctx->d_e, iw * F * N));
+  HYDOT_CUDA_TRY(ctx, cudaMalloc(&ctx->d_r, iw * F * N));
+  HYDOT_CUDA_TRY(ctx, cudaMalloc(&ctx->d_p[0], iw * F * N));
+  HYDOT_CUDA_TRY(ctx, cudaMalloc(&ctx->d_p[1], iw * F * N));
+  ctx->part_stride = part_stride(t.ntiles);
+  HYDOT_CUDA_TRY(ctx, cudaMalloc(&ctx->d_part, sizeof(double) * ctx->part_stride * F));
+  HYDOT_CUDA_TRY(ctx, cudaMemset(ctx->d_part, 0, sizeof(double) * ctx->part_stride * F));
+  HYDOT_CUDA_TRY(ctx, cudaMalloc(&ctx->d_status, sizeof(int) * F));
+  HYDOT_CUDA_TRY(ctx, cudaMalloc(&ctx->d_iters, sizeof(int) * F));
+  HYDOT_CUDA_TRY(ctx, cudaMalloc(&ctx->d_cycles, sizeof(int) * F));
+  HYDOT_CUDA_TRY(ctx, cudaMalloc(&ctx->d_scale, sizeof(double) * F));
+  HYDOT_CUDA_TRY(ctx, cudaMalloc(&ctx->d_final, sizeof(double) * 2 * F));
+  ctx->counter_len = MAX_INNER_PER_CYCLE + 8;
+  HYDOT_CUDA_TRY(ctx, cudaMalloc(&ctx->d_counter, sizeof(int) * ctx->counter_len));
+  HYDOT_CUDA_TRY(ctx, cudaMallocHost(&ctx->h_pinned, sizeof(int) * 8));
+  return HYDOT_OK;
+}
+
+void solver_free(hydot_ctx* ctx) {
+  cudaFree(ctx->d_x64);
+  cudaFree(ctx->d_e);
+  cudaFree(ctx->d_r);
+  cudaFree(ctx->d_p[0]);
+  cudaFree(ctx->d_p[1]);
+  cudaFree(ctx->d_part);
+  cudaFree(ctx->d_status);
+  cudaFree(ctx->d_iters);
+  cudaFree(ctx->d_cycles);
+  cudaFree(ctx->d_scale);
+  cudaFree(ctx->d_final);
+  cudaFree(ctx->d_counter);
+  if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+}
+
+int solve_fields_impl(hydot_ctx* ctx, int lam0, int nlam, void* phi_src, void* phi_det, hydot_stats* st) {
+  const bool mixed = ctx->precision == HYDOT_MIXED;
+  if (!ctx->cplx) {
+    if (mixed) return run_solve<float, double, float>(ctx, lam0, nlam, (float*)phi_src, (float*)phi_det, st);
+    return run_solve<double, double, double>(ctx, lam0, nlam, (double*)phi_src, (double*)phi_det, st);
+  }
+  using cf = cpx<float>;
+  using cd = cpx<double>;
+  if (mixed) return run_solve<cf, cd, cf>(ctx, lam0, nlam, (cf*)phi_src, (cf*)phi_det, st);
+  return run_solve<cd, cd, cd>(ctx, lam0, nlam, (cd*)phi_src, (cd*)phi_det, st);
+}
+
+int build_deflation(hydot_ctx* ctx) {
+  if (ctx->deflation_k == 0) return HYDOT_OK;
+  return fail(ctx, HYDOT_ERR_STATE, "deflation basis not available in this build");
+}
+
+}  // namespace hydot

@@ -1,0 +1,174 @@
+"""Parity of the Born kernels (rows, J x, J^T y, autograd) with the CPU FP64 oracle.
+
+The kernels are fed the oracle's fields (rounded to the kernel's precision), so these
+tests isolate the Born arithmetic from the solver; the solver-to-Born path is covered
+in test_gpu_fields.py.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from oracle import born as oborn
+from oracle import solve as osolve
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def case():
+    # ragged: N = 13*11*9 = 1287 is odd, so the vector path's tail code runs too
+    p = workloads.small(seed=11, nx=13, ny=11, nz=9, n_src=3, n_det=5, n_lambda=4)
+    rs, rd = osolve.fields_splu(p)
+    return p, rs, rd
+
+
+@pytest.fixture(scope="module")
+def case_even():
+    p = workloads.small(seed=12, nx=16, ny=12, nz=10, n_src=34, n_det=33, n_lambda=3, margin=0)
+    rs, rd = osolve.fields_separable(p)
+    return p, rs, rd
+
+
+def _ctx(hd, p, precision):
+    return hd.Context.from_problem(p, precision=precision, tol=1e-10, tol_cw=0.0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("which", ["case", "case_even"])
+def test_born_rows_elementwise(lib, request, precision, which):
+    p, rs, rd = request.getfixturevalue(which)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    with _ctx(lib, p, precision) as ctx:
+        ps = torch.tensor(rs, dtype=dt, device="cuda")
+        pd = torch.tensor(rd, dtype=dt, device="cuda")
+        J = ctx.born_assemble(ps, pd, 0, p.n_lambda).cpu().numpy()
+    Jr = oborn.born_matrix(p, ps.cpu().double().numpy(), pd.cpu().double().numpy())
+    if precision == "fp64":
+        assert np.array_equal(J, Jr)  # same operation order -> same bits
+    else:
+        assert np.all(np.abs(J - Jr) <= 4e-7 * np.abs(Jr) + 1e-45)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_born_row_ranges_and_leading_dimension(lib, case, precision):
+    p, rs, rd = case
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    lams = [1, 2, 3]
+    with _ctx(lib, p, precision) as ctx:
+        ps = torch.tensor(rs[1:], dtype=dt, device="cuda")
+        pd = torch.tensor(rd[1:], dtype=dt, device="cuda")
+        cols = p.n_chrom * p.grid.N
+        M = p.n_src * p.n_det * 3
+        full = ctx.born_assemble(ps, pd, 1, 3).cpu().numpy()
+        for row0, nrows in ((0, 1), (5, 17), (M - 7, 7), (13, M - 13)):
+            Jp = ctx.born_assemble(ps, pd, 1, 3, row0, nrows, ldJ=cols + 5)
+            Jp = Jp.cpu().numpy()
+            assert np.array_equal(Jp[:, :cols], full[row0:row0 + nrows])
+        with pytest.raises(lib.HydotError):
+            ctx.born_assemble(ps, pd, 1, 3, M - 2, 3)
+    Jr = oborn.born_matrix(p, ps.cpu().double().numpy(), pd.cpu().double().numpy(), lams)
+    assert np.allclose(full, Jr, rtol=4e-7 if precision == "mixed" else 0, atol=0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("which", ["case", "case_even"])
+def test_apply_and_apply_T(lib, request, precision, which):
+    p, rs, rd = request.getfixturevalue(which)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    tol = 1e-12 if precision == "fp64" else 2e-5
+    rng = np.random.default_rng(4)
+    x = rng.standard_normal(p.n_chrom * p.grid.N)
+    y = rng.standard_normal(p.M)
+    with _ctx(lib, p, precision) as ctx:
+        ps = torch.tensor(rs, dtype=dt, device="cuda")
+        pd = torch.tensor(rd, dtype=dt, device="cuda")
+        jx = ctx.born_apply(ps, pd, 0, p.n_lambda, torch.tensor(x, dtype=dt, device="cuda")).cpu().numpy()
+        g0 = torch.full((p.n_chrom * p.grid.N,), 0.5, dtype=dt, device="cuda")
+        jty = ctx.born_apply_T(ps, pd, 0, p.n_lambda, torch.tensor(y, dtype=dt, device="cuda"), g0).cpu().numpy()
+    fs, fd = ps.cpu().double().numpy(), pd.cpu().double().numpy()
+    Jr = oborn.born_matrix(p, fs, fd)
+    assert np.abs(jx - Jr @ x).max() <= tol * np.abs(Jr @ x).max()
+    ref = Jr.T @ y + 0.5  # accumulates into g
+    assert np.abs(jty - ref).max() <= tol * np.abs(Jr.T @ y).max()
+    # adjoint identity on the GPU results
+    lhs = float(jx @ y)
+    rhs = float(x @ (jty - 0.5))
+    assert abs(lhs - rhs) <= 10 * tol * abs(lhs) + 1e-30
+
+
+def test_apply_T_matches_adjoint_solve_form(lib, case):
+    """g = J^T y from stored detector fields equals the oracle's one-solve-per-source form."""
+    p, rs, rd = case
+    y = np.random.default_rng(5).standard_normal(p.M)
+    with _ctx(lib, p, "fp64") as ctx:
+        g = ctx.born_apply_T(torch.tensor(rs, device="cuda"), torch.tensor(rd, device="cuda"), 0, p.n_lambda,
+                             torch.tensor(y, device="cuda")).cpu().numpy()
+    g2 = oborn.apply_T_adjoint_solve(p, rs, y)
+    assert np.abs(g - g2).max() <= 1e-11 * np.abs(g2).max()
+
+
+def test_apply_T_accumulates_over_slices(lib, case):
+    p, rs, rd = case
+    y = np.random.default_rng(6).standard_normal(p.M)
+    with _ctx(lib, p, "fp64") as ctx:
+        ps, pd = torch.tensor(rs, device="cuda"), torch.tensor(rd, device="cuda")
+        full = ctx.born_apply_T(ps, pd, 0, 4, torch.tensor(y, device="cuda")).cpu().numpy()
+        # the same product as two slices [0,1) and [1,4): rows of a slice are (s, d, lambda - lam0)
+        Y = y.reshape(p.n_src, p.n_det, 4)
+        g = torch.zeros(p.n_chrom * p.grid.N, dtype=torch.float64, device="cuda")
+        ctx.born_apply_T(ps[:1].contiguous(), pd[:1].contiguous(), 0, 1,
+                         torch.tensor(Y[:, :, :1].reshape(-1).copy(), device="cuda"), g)
+        ctx.born_apply_T(ps[1:].contiguous(), pd[1:].contiguous(), 1, 3,
+                         torch.tensor(Y[:, :, 1:].reshape(-1).copy(), device="cuda"), g)
+    assert np.abs(g.cpu().numpy() - full).max() <= 1e-12 * np.abs(full).max()
+
+
+def test_autograd_gradcheck(lib):
+    from paper_1410_0986_gb300 import born_apply
+
+    p = workloads.small(seed=13, nx=6, ny=5, nz=4, n_src=2, n_det=2, n_lambda=2)
+    rs, rd = osolve.fields_dense(p)
+    with _ctx(lib, p, "fp64") as ctx:
+        ps, pd = torch.tensor(rs, device="cuda"), torch.tensor(rd, device="cuda")
+        x = torch.randn(p.n_chrom * p.grid.N, dtype=torch.float64, device="cuda", requires_grad=True)
+        assert torch.autograd.gradcheck(lambda v: born_apply(v, ctx, ps, pd, 0, 2), (x,), eps=1e-6, atol=1e-9)
+
+
+def test_misfit_gradient_vs_central_differences(lib):
+    """Config-3-style check on a reduced grid: misfit 0.5||J dc - y||^2 with an ellipsoidal
+    anomaly; autograd gradient (mixed-precision fields, FP32 adjoint kernel) against central
+    differences (step 1e-6, FP64 forward) at 64 seeded coordinates, relative 1e-4."""
+    from paper_1410_0986_gb300 import born_apply
+
+    p = workloads.make_problem(workloads.Grid(32, 32, 20, 1.5), 4, 4, 6, seed=17, margin=2)
+    dc = workloads.ellipsoid_anomaly(p.grid, seed=18)
+    dc_true = workloads.ellipsoid_anomaly(p.grid, seed=19)
+    with lib.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=1e-8) as cm, \
+            lib.Context.from_problem(p, precision="fp64", tol=1e-13, tol_cw=1e-11) as cd:
+        ps, pd, _ = cm.solve_fields(0, p.n_lambda)
+        qs, qd, _ = cd.solve_fields(0, p.n_lambda)
+        ytrue = cd.born_apply(qs, qd, 0, p.n_lambda, torch.tensor(dc_true, device="cuda"))
+        noise = torch.tensor(workloads.gaussian(20, p.M), device="cuda")
+        y = ytrue + noise * (ytrue.norm() / p.M ** 0.5) * 10 ** (-30 / 20)
+        x = torch.tensor(dc, dtype=torch.float32, device="cuda", requires_grad=True)
+        r = born_apply(x, cm, ps, pd, 0, p.n_lambda) - y.float()
+        (0.5 * (r * r).sum()).backward()
+        grad = x.grad.double()
+
+        def f(v):
+            rr = cd.born_apply(qs, qd, 0, p.n_lambda, v) - y
+            return 0.5 * float((rr * rr).sum())
+
+        idx = np.random.default_rng(21).choice(p.n_chrom * p.grid.N, size=64, replace=False)
+        base = torch.tensor(dc, device="cuda")
+        h = 1e-6
+        fd = []
+        for i in idx:
+            e = torch.zeros_like(base)
+            e[i] = h
+            fd.append((f(base + e) - f(base - e)) / (2 * h))
+        fd = np.array(fd)
+    g = grad.cpu().numpy()[idx]
+    scale = np.abs(grad.cpu().numpy()).max()
+    assert np.abs(g - fd).max() <= 1e-4 * scale
