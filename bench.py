@@ -1,0 +1,452 @@
+#!/usr/bin/env python
+"""Benchmark of the hyperspectral DOT Born hot path on GB300.
+
+Workload: 64x64x48 grid (h = 2 mm, 196,608 cells), 32 sources on the top face and 32
+detectors on the bottom face, 128 wavelengths on 650-900 nm, 4 chromophores -- 8,192 field
+solves, an explicit FP32 Born matrix of 131,072 x 786,432 assembled in row chunks, and the
+implicit products J x and J^T r. Synthetic, seeded inputs (workloads.config(2)).
+
+One step = one 16-wavelength chunk of that workload, the whole hot path over it:
+  1. 1,024 field solves (FP32 PCG, FP64 residuals and refinement to a componentwise backward
+     error <= 1e-8, so that Born entries meet 1e-5 of their row maximum),
+  2. the chunk's 16,384 Born rows (FP32, 4,096-row launches into a reused 12.9 GB buffer),
+  3. y = J x for the chunk (x = a seeded ellipsoidal anomaly),
+  4. g += J^T r with r = y - y_obs (y_obs = 0: the misfit of the anomaly against data of the
+     unperturbed background); 8 steps make one full gradient.
+Steps walk the 8 chunks in turn (step k, rank r -> chunk (k*world + r) mod 8).
+
+value = field solves per second over whole steps (all four parts timed); the other rates,
+the roofline of the dominant kernel and the CPU oracle baseline are extra keys.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "field solves/s at 1e-6 rel err; Born rows/s; Jᵀr grads/s; % of HBM roofline"
+UNIT = "field solves/s"
+CHUNK = 16
+ROWS_PER_LAUNCH = 4096
+WORKLOAD = ("cw-mixed-64x64x48: 64x64x48 grid (h=2 mm), 32 sources + 32 detectors, 128 wavelengths "
+            "(8,192 field solves), explicit FP32 Born rows 131,072 x 786,432 in row chunks, J x and J^T r")
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        d["source"] = "measured"
+        return d
+    return dict(FALLBACK_PEAKS)
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples during the timed region (read-only queries)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def cpu_sample(lam: int) -> dict:
+    """The oracle, as it stands, on one wavelength of the workload: fields of all 64 optodes
+    (separable exact FP64 solver), the wavelength's 1,024 Born rows (built and discarded in
+    blocks), its J x and its J^T r contribution."""
+    import numpy as np
+
+    import workloads
+    from oracle import born, solve
+
+    p = workloads.config(2)
+    x = workloads.ellipsoid_anomaly(p.grid, seed=workloads.SEED_BASE + 200)
+    t0 = time.perf_counter()
+    a, b = solve.fields_separable(p, [lam])
+    for r0 in range(0, p.n_src * p.n_det, 64):
+        born.born_rows(p, a, b, range(r0, r0 + 64), [lam])
+    y = born.apply(p, a, b, x, [lam])
+    born.apply_T(p, a, b, y, [lam])
+    dt = time.perf_counter() - t0
+    return {"seconds": dt, "solves": p.n_src + p.n_det, "rows": p.n_src * p.n_det}
+
+
+def run_cpu_sample(lam: int = 0) -> dict:
+    """Run cpu_sample in a child process whose BLAS pool size is fixed to the usable cores."""
+    cores = len(os.sched_getaffinity(0))
+    env = dict(os.environ, OMP_NUM_THREADS=str(cores), OPENBLAS_NUM_THREADS=str(cores), MKL_NUM_THREADS=str(cores))
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", str(lam)], env=env,
+                         capture_output=True, text=True, timeout=900)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    d = json.loads(out.stdout.strip().splitlines()[-1])
+    d["cores"] = cores
+    return d
+
+
+def cpu_baseline_entry(d: dict) -> dict:
+    return {"value": d["solves"] / d["seconds"], "unit": UNIT, "cores": d["cores"], "kind": "oracle",
+            "sample": (f"one wavelength of the workload: {d['solves']} fields by the oracle's separable exact "
+                       f"FP64 solver (SuperLU needs ~130 s per factorisation at this size), its {d['rows']} Born "
+                       f"rows, J x and J^T r; numpy with a BLAS pool of {d['cores']} threads; "
+                       f"{d['seconds']:.1f} s")}
+
+
+# ----------------------------------------------------------------------------- distributed
+def init_dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(v: float, world: int) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = init_dist()
+    torch.cuda.set_device(local)
+    import paper_1410_0986_gb300 as hd
+    import workloads
+    from paper_1410_0986_gb300 import shard
+
+    p = workloads.config(2)
+    nchunk = p.n_lambda // CHUNK
+    ns, nd, nc, N = p.n_src, p.n_det, p.n_chrom, p.grid.N
+    Mc = ns * nd * CHUNK
+    t_setup = time.perf_counter()
+    ctx = hd.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=1e-8, max_lambda_per_call=CHUNK,
+                                  deflation_k=args.deflation_k)
+    t_setup = time.perf_counter() - t_setup
+    ps = torch.empty(CHUNK, ns, N, dtype=torch.float32, device="cuda")
+    pd = torch.empty(CHUNK, nd, N, dtype=torch.float32, device="cuda")
+    J = torch.empty(ROWS_PER_LAUNCH, nc * N, dtype=torch.float32, device="cuda")
+    x = torch.tensor(workloads.ellipsoid_anomaly(p.grid, seed=workloads.SEED_BASE + 200), dtype=torch.float32,
+                     device="cuda")
+    y = torch.empty(Mc, dtype=torch.float32, device="cuda")
+    g = torch.zeros(nc * N, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def ev():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        return e
+
+    phase = {"solve": [], "assemble": [], "assemble_launch": [], "apply": [], "apply_T": []}
+    stats = []
+
+    def step(k: int, timed: bool):
+        c = shard.chunk_of_step(k, rank, world, nchunk)
+        lam0 = c * CHUNK
+        e0 = ev()
+        _, _, st = ctx.solve_fields(lam0, CHUNK, ps, pd)
+        e1 = ev()
+        launches = []
+        for row0 in range(0, Mc, ROWS_PER_LAUNCH):
+            a0 = ev()
+            ctx.born_assemble(ps, pd, lam0, CHUNK, row0, min(ROWS_PER_LAUNCH, Mc - row0), J)
+            launches.append((a0, ev()))
+        e2 = ev()
+        ctx.born_apply(ps, pd, lam0, CHUNK, x, y)
+        e3 = ev()
+        # r = y - y_obs with y_obs = 0: the residual is y itself
+        ctx.born_apply_T(ps, pd, lam0, CHUNK, y, g)
+        e4 = ev()
+        if timed:
+            stats.append(st)
+            phase["_ev"] = phase.get("_ev", []) + [(e0, e1, e2, e3, e4, launches)]
+
+    for k in range(args.warmup):
+        step(k, False)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    launches0 = ctx.lib.hydot_kernel_launches(ctx._ctx)
+    clocks = ClockSampler(local)
+    clocks.start()
+    t0 = ev()
+    for k in range(args.warmup, args.warmup + args.steps):
+        step(k, True)
+    t1 = ev()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(world)
+    torch.cuda.synchronize()
+    n_launch = ctx.lib.hydot_kernel_launches(ctx._ctx) - launches0
+    ms = t0.elapsed_time(t1)
+    ms = max_over_ranks(ms, world)
+    for (e0, e1, e2, e3, e4, launches) in phase["_ev"]:
+        phase["solve"].append(e0.elapsed_time(e1))
+        phase["assemble"].append(e1.elapsed_time(e2))
+        phase["assemble_launch"] += [a.elapsed_time(b) for a, b in launches]
+        phase["apply"].append(e2.elapsed_time(e3))
+        phase["apply_T"].append(e3.elapsed_time(e4))
+    K = args.steps
+    solves = K * (ns + nd) * CHUNK * world
+    value = solves / (ms / 1e3)
+    pk = peaks()
+    # dominant kernel: Born-row assembly; algorithmic bytes = the rows written (N * n_chrom * 4 B each)
+    t_launch = statistics.mean(phase["assemble_launch"]) / 1e3
+    bytes_launch = ROWS_PER_LAUNCH * nc * N * 4
+    achieved = bytes_launch / t_launch / 1e9
+    # solver roofline: 6 N w per RHS-iteration (x, r, p read and written once; FP32)
+    iters = sum(s["iters_mean"] * s["n_fields"] for s in stats)
+    t_solve = sum(phase["solve"]) / 1e3
+    solver_gbs = iters * 6 * N * 4 / t_solve / 1e9
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "refinement_dtype": "f64", "data": "synthetic (seeded; workloads.config(2))",
+        "config": {"workload": WORKLOAD, "step": "one 16-wavelength chunk: 1,024 solves + 16,384 Born rows + J x + "
+                   "J^T r", "grid": [64, 64, 48], "n_src": ns, "n_det": nd, "n_lambda": p.n_lambda,
+                   "chunk_lambda": CHUNK, "tol_cw": 1e-8, "tol": 1e-10, "deflation_k": args.deflation_k,
+                   "l2": "inputs larger than L2 (805 MB of fields per chunk, 12.9 GB per Born launch)",
+                   "parallelism": f"lambda-chunks over {world} GPU(s), no data exchange"},
+        "roofline": {"kernel": "k_born_rows (Born-row assembly)", "bound": "hbm", "achieved": achieved,
+                     "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
+                     "peak_source": pk["source"], "traffic": None,
+                     "algorithmic_bytes_per_launch": bytes_launch, "launch_ms": t_launch * 1e3},
+        "rates": {
+            "born_rows_per_s": K * Mc * world / (sum(phase["assemble"]) / 1e3),
+            "grads_per_s": (K / nchunk) / (sum(phase["apply_T"]) / 1e3),
+            "jx_per_s": (K / nchunk) / (sum(phase["apply"]) / 1e3),
+            "solve_phase_solves_per_s": (ns + nd) * CHUNK * K / t_solve,
+            "phase_ms_per_step": {k: sum(v) / K for k, v in phase.items() if k in ("solve", "assemble", "apply",
+                                                                                  "apply_T")},
+        },
+        "solver": {"iters_mean": statistics.mean(s["iters_mean"] for s in stats),
+                   "iters_max": max(s["iters_max"] for s in stats),
+                   "cycles_max": max(s["cycles_max"] for s in stats),
+                   "resid_max": max(s["resid_max"] for s in stats), "cw_max": max(s["cw_max"] for s in stats),
+                   "hbm_gbs_at_6NW_per_iteration": solver_gbs, "hbm_frac": solver_gbs / pk["hbm_gbs"]},
+        "setup_s": t_setup,
+        "clocks": clk,
+        "gpu_launches": int(n_launch),
+    }
+    # end to end through the public API: pinned host inputs in, results back, every step
+    if args.e2e_steps > 0:
+        xh = x.cpu().pin_memory()
+        yh = torch.empty(Mc, dtype=torch.float32).pin_memory()
+        gh = torch.empty(nc * N, dtype=torch.float32).pin_memory()
+        torch.cuda.synchronize()
+        barrier(world)
+        s0 = ev()
+        for k in range(args.e2e_steps):
+            xd = xh.to("cuda", non_blocking=True)
+            c = shard.chunk_of_step(k, rank, world, nchunk)
+            lam0 = c * CHUNK
+            ctx.solve_fields(lam0, CHUNK, ps, pd)
+            for row0 in range(0, Mc, ROWS_PER_LAUNCH):
+                ctx.born_assemble(ps, pd, lam0, CHUNK, row0, min(ROWS_PER_LAUNCH, Mc - row0), J)
+            ctx.born_apply(ps, pd, lam0, CHUNK, xd, y)
+            ctx.born_apply_T(ps, pd, lam0, CHUNK, y, g)
+            yh.copy_(y, non_blocking=True)
+            gh.copy_(g, non_blocking=True)
+        s1 = ev()
+        torch.cuda.synchronize()
+        ems = max_over_ranks(s0.elapsed_time(s1), world)
+        out["e2e"] = {"value": args.e2e_steps * (ns + nd) * CHUNK * world / (ems / 1e3), "unit": UNIT,
+                      "h2d_bytes_per_step": int(xh.numel() * 4), "d2h_bytes_per_step": int((Mc + nc * N) * 4),
+                      "steps": args.e2e_steps}
+    # the plain FP64 GPU solve against the mixed form, both to a field error of 1e-6 (norm-wise)
+    if args.compare_fp64 and rank == 0:
+        out["fp64_vs_mixed_at_1e-6"] = compare_fp64(hd, p)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_entry(run_cpu_sample(0))
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def compare_fp64(hd, p):
+    import torch
+
+    res = {}
+    for prec, kw in (("mixed", dict(tol=1e-7, tol_cw=0.0)), ("fp64", dict(tol=1e-7, tol_cw=0.0))):
+        with hd.Context.from_problem(p, precision=prec, max_lambda_per_call=CHUNK, **kw) as c:
+            c.solve_fields(0, CHUNK)  # warm-up
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            _, _, st = c.solve_fields(CHUNK, CHUNK)
+            b.record()
+            torch.cuda.synchronize()
+            res[prec] = {"solves_per_s": (p.n_src + p.n_det) * CHUNK / (a.elapsed_time(b) / 1e3),
+                         "iters_mean": st["iters_mean"], "resid_max": st["resid_max"]}
+    res["speedup"] = res["mixed"]["solves_per_s"] / res["fp64"]["solves_per_s"]
+    res["criterion"] = "relative residual <= 1e-7 (field error <= 1e-6), 1,024 fields, wavelengths 16-31"
+    return res
+
+
+# ----------------------------------------------------------------------------- profiling cases
+def run_kernel_case(name: str, reps: int = 3):
+    """A small, bounded case of one hot kernel on the workload's grid, for profiler captures:
+    born_rows   512 rows of one 16-wavelength chunk (1.6 GB written per launch)
+    solver      the 64 fields of one wavelength (FP32 PCG + FP64 refinement, ~300 MB of vectors)
+    apply       J x and J^T r over one 16-wavelength chunk of fields
+    """
+    import torch
+
+    import paper_1410_0986_gb300 as hd
+    import workloads
+
+    p = workloads.config(2)
+    ns, nd, nc, N = p.n_src, p.n_det, p.n_chrom, p.grid.N
+    lam_n = 1 if name == "solver" else CHUNK
+    ctx = hd.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=1e-8, max_lambda_per_call=lam_n)
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    ps = torch.rand(lam_n, ns, N, device="cuda", generator=gen)
+    pd = torch.rand(lam_n, nd, N, device="cuda", generator=gen)
+    times = []
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        if name == "born_rows":
+            J = torch.empty(512, nc * N, device="cuda") if not times else J
+            a.record()
+            ctx.born_assemble(ps, pd, 0, CHUNK, 0, 512, J)
+        elif name == "solver":
+            a.record()
+            ctx.solve_fields(0, 1, ps, pd)
+        elif name == "apply":
+            x = torch.rand(nc * N, device="cuda", generator=gen)
+            a.record()
+            y = ctx.born_apply(ps, pd, 0, CHUNK, x)
+            ctx.born_apply_T(ps, pd, 0, CHUNK, y)
+        else:
+            raise SystemExit(f"unknown kernel case {name}")
+        b.record()
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    ctx.close()
+    print(json.dumps({"kernel_case": name, "ms": times}))
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    """The oracle as it stands on the host cores, one bounded wavelength sample per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    for k in range(args.warmup):
+        run_cpu_sample(k % 128)
+    samples = [run_cpu_sample((args.warmup + k) % 128) for k in range(args.steps)]
+    secs = sum(s["seconds"] for s in samples)
+    solves = sum(s["solves"] for s in samples)
+    value = solves / secs
+    d = dict(samples[-1])
+    d["seconds"] = secs / len(samples)
+    cb = cpu_baseline_entry(d)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+           "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * secs / len(samples), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded; workloads.config(2))",
+           "config": {"workload": WORKLOAD, "step": "one wavelength of the workload on the host cores (oracle)"},
+           "cpu_baseline": cb, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                       "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=4)
+    ap.add_argument("--deflation-k", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare-fp64", dest="compare_fp64", action="store_false")
+    ap.add_argument("--cpu-sample", type=int, default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--kernel-case", default=None, help="born_rows | solver | apply: small profiling case")
+    args = ap.parse_args()
+    if args.kernel_case:
+        run_kernel_case(args.kernel_case)
+        return
+    if args.cpu_sample is not None:
+        print(json.dumps(cpu_sample(args.cpu_sample)))
+        return
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

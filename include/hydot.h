@@ -134,6 +134,10 @@ int hydot_born_apply(hydot_ctx* ctx, const void* phi_src, const void* phi_det, i
 int hydot_born_apply_T(hydot_ctx* ctx, const void* phi_src, const void* phi_det, int lam0, int nlam,
                        const void* y, void* g);
 
+/* Number of kernels this context has launched since hydot_setup (instrumentation: lets a
+ * caller count the library's launches inside a timed region). */
+long long hydot_kernel_launches(const hydot_ctx* ctx);
+
 /* Last error message of ctx (or of the last failed hydot_setup when ctx is NULL). */
 const char* hydot_last_error(const hydot_ctx* ctx);
 

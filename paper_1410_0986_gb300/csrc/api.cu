@@ -201,6 +201,8 @@ int hydot_born_apply_T(hydot_ctx* ctx, const void* phi_src, const void* phi_det,
   return hydot::born_apply_T_impl(ctx, phi_src, phi_det, lam0, nlam, y, g);
 }
 
+long long hydot_kernel_launches(const hydot_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
 const char* hydot_last_error(const hydot_ctx* ctx) { return ctx ? ctx->err.c_str() : g_setup_error.c_str(); }
 
 void hydot_destroy(hydot_ctx* ctx) {

@@ -296,6 +296,7 @@ int assemble_t(hydot_ctx* ctx, const E* ps, const E* pd, int lam0, int nlam, lon
   else
     k_born_rows_scalar<E><<<grid, 256, 0, ctx->stream>>>(ps, pd, ctx->d_eps, lam0, nlam, ns, nd, nc, N, h3, row0,
                                                          nrows, sd_lo, n_sd, J, ldJ);
+  ++ctx->launches;
   HYDOT_CUDA_TRY(ctx, cudaGetLastError());
   return HYDOT_OK;
 }
@@ -329,10 +330,12 @@ int apply_t(hydot_ctx* ctx, const E* ps, const E* pd, int lam0, int nlam, const 
   const size_t smem = apply_smem_bytes<E>();
   HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(k_apply_partial<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_apply_partial<E><<<grid, 256, smem, ctx->stream>>>(ps, pd, x, ctx->d_eps, lam0, ns, nd, nc, N, nxb, part);
+  ++ctx->launches;
   HYDOT_CUDA_TRY(ctx, cudaGetLastError());
   long long M = (long long)ns * nd * nlam;
   k_apply_reduce<E><<<(unsigned)std::min<long long>((M + 255) / 256, 4096), 256, 0, ctx->stream>>>(
       part, nlam, ns, nd, nts, ntd, nxb, ctx->h * ctx->h * ctx->h, y);
+  ++ctx->launches;
   HYDOT_CUDA_TRY(ctx, cudaGetLastError());
   return HYDOT_OK;
 }
@@ -357,10 +360,12 @@ int apply_T_t(hydot_ctx* ctx, const E* ps, const E* pd, int lam0, int nlam, cons
                                              (int)smem));
   }
   k_apply_T_partial<E><<<grid, 256, smem, ctx->stream>>>(ps, pd, y, ctx->d_eps, lam0, nlam, ns, nd, nc, N, lpg, part);
+  ++ctx->launches;
   HYDOT_CUDA_TRY(ctx, cudaGetLastError());
   long long tot = (long long)nc * N;
   k_apply_T_reduce<E><<<(unsigned)std::min<long long>((tot + 255) / 256, 8192), 256, 0, ctx->stream>>>(
       part, ngrp, nc, N, ctx->h * ctx->h * ctx->h, g);
+  ++ctx->launches;
   HYDOT_CUDA_TRY(ctx, cudaGetLastError());
   return HYDOT_OK;
 }

@@ -146,6 +146,8 @@ struct hydot_ctx {
   std::vector<double> gram_L, gram_I, gram_B;  // W^T Lg W, W^T W, W^T B_f W (6 blocks)
   double* d_Ginv = nullptr;                    // [n_lambda][k][k] inverse of W^T Ahat_j W
 
+  long long launches = 0;  // kernels enqueued by this context
+
   // Born apply workspace
   void* d_apply_ws = nullptr;
   size_t apply_ws_bytes = 0;

@@ -560,17 +560,21 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
 
   HYDOT_CUDA_TRY(ctx, cudaMemsetAsync(x64, 0, sizeof(X) * (size_t)b.nrhs * g.N, s));
   k_reset<<<(b.nrhs + 255) / 256, 256, 0, s>>>(b);
+  ++ctx->launches;
   HYDOT_CUDA_TRY(ctx, cudaGetLastError());
 
   volatile int* hp = ctx->h_pinned;
   for (int cycle = 0; cycle <= MAX_CYCLES; ++cycle) {
     k_residual<X><<<nblk, blk, 0, s>>>(g, b, x64);
+    ++ctx->launches;
     HYDOT_CUDA_TRY(ctx, cudaMemsetAsync(b.counter, 0, sizeof(int) * (size_t)ctx->counter_len, s));
     k_decide<<<(b.nrhs + 255) / 256, 256, 0, s>>>(g, b);
+    ++ctx->launches;
     HYDOT_CUDA_TRY(ctx, cudaMemcpyAsync((void*)&hp[0], b.counter, sizeof(int), cudaMemcpyDeviceToHost, s));
     HYDOT_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     if (hp[0] == 0) break;
     k_init<T, X><<<nblk, blk, 0, s>>>(g, b, x64, R);
+    ++ctx->launches;
     HYDOT_CUDA_TRY(ctx, cudaGetLastError());
     // inner iterations in groups; the group after the one being polled is already queued
     int it = 0;
@@ -584,7 +588,9 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
       int g_end = std::min(it + POLL_GROUP, MAX_INNER_PER_CYCLE);
       for (; it < g_end; ++it) {
         k_dir<T><<<nblk, blk, 0, s>>>(g, b, it, R, P[it & 1], P[(it + 1) & 1]);
+        ++ctx->launches;
         k_update<T><<<nblk, blk, 0, s>>>(g, b, it, E, R, P[(it + 1) & 1]);
+        ++ctx->launches;
       }
       HYDOT_CUDA_TRY(ctx, cudaGetLastError());
       HYDOT_CUDA_TRY(ctx, cudaMemcpyAsync((void*)&hp[1 + slot], b.counter + 1 + (it - 1), sizeof(int),
@@ -606,13 +612,16 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
       dim3 fg((unsigned)std::min<long long>((g.N + 255) / 256, 1024), (unsigned)std::min(b.nrhs, 65535));
       // fields that were still iterating when the cap hit are FINISHED by the next k_dir; run it
       k_dir<T><<<nblk, blk, 0, s>>>(g, b, MAX_INNER_PER_CYCLE, R, P[0], P[1]);
+      ++ctx->launches;
       k_fold<T, X><<<fg, 256, 0, s>>>(g, b, x64, E);
+      ++ctx->launches;
       HYDOT_CUDA_TRY(ctx, cudaGetLastError());
     }
   }
   {
     dim3 fg((unsigned)std::min<long long>((g.N + 255) / 256, 1024), (unsigned)std::min(b.nrhs, 65535));
     k_output<X, O><<<fg, 256, 0, s>>>(g, b, x64, phi_src, phi_det, ctx->n_src, ctx->n_det);
+    ++ctx->launches;
     HYDOT_CUDA_TRY(ctx, cudaGetLastError());
   }
   // statistics
