@@ -39,6 +39,7 @@ template <> struct Traits<float> {
   using R = float;
   static constexpr bool cplx = false;
   __host__ __device__ static float zero() { return 0.f; }
+  __host__ __device__ static float make(float re, float) { return re; }
   __host__ __device__ static float from(double re, double) { return (float)re; }
   __host__ __device__ static double re(float v) { return v; }
   __host__ __device__ static double im(float) { return 0.0; }
@@ -48,6 +49,7 @@ template <> struct Traits<double> {
   using R = double;
   static constexpr bool cplx = false;
   __host__ __device__ static double zero() { return 0.0; }
+  __host__ __device__ static double make(double re, double) { return re; }
   __host__ __device__ static double from(double re, double) { return re; }
   __host__ __device__ static double re(double v) { return v; }
   __host__ __device__ static double im(double) { return 0.0; }
@@ -57,6 +59,7 @@ template <> struct Traits<cpx<float>> {
   using R = float;
   static constexpr bool cplx = true;
   __host__ __device__ static cpx<float> zero() { return {0.f, 0.f}; }
+  __host__ __device__ static cpx<float> make(float re, float im) { return {re, im}; }
   __host__ __device__ static cpx<float> from(double re, double im) { return {(float)re, (float)im}; }
   __host__ __device__ static double re(cpx<float> v) { return v.re; }
   __host__ __device__ static double im(cpx<float> v) { return v.im; }
@@ -66,6 +69,7 @@ template <> struct Traits<cpx<double>> {
   using R = double;
   static constexpr bool cplx = true;
   __host__ __device__ static cpx<double> zero() { return {0.0, 0.0}; }
+  __host__ __device__ static cpx<double> make(double re, double im) { return {re, im}; }
   __host__ __device__ static cpx<double> from(double re, double im) { return {re, im}; }
   __host__ __device__ static double re(cpx<double> v) { return v.re; }
   __host__ __device__ static double im(cpx<double> v) { return v.im; }

@@ -70,32 +70,43 @@ __device__ __forceinline__ long long rhs_source(const Batch& b, int rhs) {
   return (long long)b.optode[b.f_begin + rhs % b.nf];
 }
 
-// diagonal of Ahat at (i,j,k): 6 + sigma + sum over the cell's boundary faces of (bhat_f - 1)
-struct Diag {
-  double dre, dim;   // 6 + sigma
-  double fa[6];      // bhat_f - 1
+// Diagonal of Ahat in precision R: 6 + sigma on interior cells; a cell on boundary face f adds
+// bhat_f - 1 (one neighbour fewer, one boundary term more). The face set of a cell is a 6-bit
+// mask, so interior cells (mask 0) do no arithmetic for it -- in the FP64 kernels that keeps
+// the slow FP64 pipe for the residual itself.
+template <typename R>
+struct DiagT {
+  R dre, dim;  // 6 + sigma
+  R fa[6];     // bhat_f - 1
   __device__ void load(const LamCoef& c) {
-    dre = 6.0 + c.sigma_re;
-    dim = c.sigma_im;
+    dre = (R)(6.0 + c.sigma_re);
+    dim = (R)c.sigma_im;
 #pragma unroll
-    for (int f = 0; f < 6; ++f) fa[f] = c.bhat[f] - 1.0;
+    for (int f = 0; f < 6; ++f) fa[f] = (R)(c.bhat[f] - 1.0);
   }
-  __device__ __forceinline__ double add(const Geo& g, int i, int j, int k) const {
-    double a = 0.0;
-    if (i == 0) a += fa[0];
-    if (i == g.nx - 1) a += fa[1];
-    if (j == 0) a += fa[2];
-    if (j == g.ny - 1) a += fa[3];
-    if (k == 0) a += fa[4];
-    if (k == g.nz - 1) a += fa[5];
+  __device__ __forceinline__ R add(int m) const {
+    R a = 0;
+#pragma unroll
+    for (int f = 0; f < 6; ++f)
+      if (m & (1 << f)) a += fa[f];
     return a;
   }
 };
 
-template <typename T>
-__device__ __forceinline__ T make_diag(const Diag& d, double add) {
-  return Traits<T>::from(d.dre + add, d.dim);
+__device__ __forceinline__ int face_mask(const Geo& g, int i, int j, int k) {
+  return (i == 0) | ((i == g.nx - 1) << 1) | ((j == 0) << 2) | ((j == g.ny - 1) << 3) | ((k == 0) << 4) |
+         ((k == g.nz - 1) << 5);
 }
+
+template <typename T, typename R>
+__device__ __forceinline__ T diag_at(const DiagT<R>& d, int m) {
+  return Traits<T>::make(m ? d.dre + d.add(m) : d.dre, d.dim);
+}
+
+// Biased binary exponent of |v| (0 for zero and subnormals), read from the bits: integer ops only.
+__device__ __forceinline__ int bexp(double v) { return (__double2hiint(v) >> 20) & 0x7ff; }
+__device__ __forceinline__ int bexp(cpx<double> v) { return max(bexp(v.re), bexp(v.im)); }
+
 template <typename T>
 __device__ __forceinline__ T inv(T v) {
   if constexpr (Traits<T>::cplx) {
@@ -146,21 +157,23 @@ __device__ void block_sum(R (&v)[NV], double (&out)[NV], double* sm) {
 }
 
 // Sum NV strided partial arrays over the tiles of one field; every thread gets the result.
-// p points at the first value; element (q, t) is p[q*qstride + t*tstride].
+// p points at the first value; element (q, t) is p[q*qstride + t*tstride]. One warp does the
+// FP64 work (fixed lane assignment and shuffle tree: every block of a field gets the same bits).
 template <int NV>
 __device__ void tile_sum(const double* p, int qstride, int tstride, int ntiles, double (&out)[NV], double* sm) {
-  double v[NV];
+  if (threadIdx.x < 32) {
+    double v[NV];
 #pragma unroll
-  for (int q = 0; q < NV; ++q) v[q] = 0.0;
-  for (int t = threadIdx.x; t < ntiles; t += NTHREADS) {
+    for (int q = 0; q < NV; ++q) v[q] = 0.0;
+    for (int t = threadIdx.x; t < ntiles; t += 32) {
 #pragma unroll
-    for (int q = 0; q < NV; ++q) v[q] += p[q * qstride + (size_t)t * tstride];
-  }
-  double r[NV];
-  block_sum<NV, double>(v, r, sm);
-  if (threadIdx.x == 0) {
+      for (int q = 0; q < NV; ++q) v[q] += p[q * qstride + (size_t)t * tstride];
+    }
 #pragma unroll
-    for (int q = 0; q < NV; ++q) sm[64 + q] = r[q];
+    for (int q = 0; q < NV; ++q) {
+      double s = warp_sum(v[q]);
+      if (threadIdx.x == 0) sm[64 + q] = s;
+    }
   }
   __syncthreads();
 #pragma unroll
@@ -193,17 +206,27 @@ __device__ __forceinline__ long long vidx(const Geo& g, int i, int j, int k) {
 }
 
 // ---------------------------------------------------------------- FP64 residual
+// r = b - Ahat x64 in FP64 (six adds and one fused multiply-add per cell on the FP64 pipe), its
+// squared norm, and a bound on the componentwise backward error
+//   omega = max_i |r_i| / (|Ahat||x|_i + |b_i|)
+// computed from the binary exponents in the integer pipes: |r_i| < 2^(e_r - 1022) and
+// (|Ahat||x| + |b|)_i >= 2^(max(e_xc + 2, e_nbr, e_b) - 1023) (|diagonal| >= 4), so
+// 2^(e_r + 1 - max(...)) >= omega_i. The bound exceeds the true value by at most a factor ~30,
+// so a stopping test on it is conservative.
 template <typename X>
 __global__ void __launch_bounds__(NTHREADS) k_residual(Geo g, Batch b, const X* __restrict__ x64) {
   __shared__ double sm[96];
+  __shared__ int smi[NWARPS];
   TileCoord c = tile_coord(g);
   if (b.status[c.rhs] != RHS_FINISHED) return;
   const LamCoef& lc = b.coef[rhs_lambda(b, c.rhs)];
-  Diag dg;
+  DiagT<double> dg;
   dg.load(lc);
   const long long src = rhs_source(b, c.rhs);
   const X* x = x64 + (size_t)c.rhs * g.N;
-  double rr = 0.0, om = 0.0;
+  double rr = 0.0;
+  int om_e = -4096;
+  constexpr int cplx_extra = Traits<X>::cplx ? 1 : 0;
   if (c.in) {
     auto ld = [&](int k) { return x[vidx(g, c.i, c.j, k)]; };
     X zero = Traits<X>::zero();
@@ -212,35 +235,38 @@ __global__ void __launch_bounds__(NTHREADS) k_residual(Geo g, Batch b, const X* 
     for (int k = c.k0; k < c.k1; ++k) {
       X xp = (k + 1 < g.nz) ? ld(k + 1) : zero;
       X s = xm + xp;
-      double as = sqrt(Traits<X>::abs2(xm)) + sqrt(Traits<X>::abs2(xp));
-      if (c.i > 0) { X v = x[vidx(g, c.i - 1, c.j, k)]; s = s + v; as += sqrt(Traits<X>::abs2(v)); }
-      if (c.i < g.nx - 1) { X v = x[vidx(g, c.i + 1, c.j, k)]; s = s + v; as += sqrt(Traits<X>::abs2(v)); }
-      if (c.j > 0) { X v = x[vidx(g, c.i, c.j - 1, k)]; s = s + v; as += sqrt(Traits<X>::abs2(v)); }
-      if (c.j < g.ny - 1) { X v = x[vidx(g, c.i, c.j + 1, k)]; s = s + v; as += sqrt(Traits<X>::abs2(v)); }
-      X d = make_diag<X>(dg, dg.add(g, c.i, c.j, k));
+      int ed = max(bexp(xm), bexp(xp));
+      if (c.i > 0) { X v = x[vidx(g, c.i - 1, c.j, k)]; s = s + v; ed = max(ed, bexp(v)); }
+      if (c.i < g.nx - 1) { X v = x[vidx(g, c.i + 1, c.j, k)]; s = s + v; ed = max(ed, bexp(v)); }
+      if (c.j > 0) { X v = x[vidx(g, c.i, c.j - 1, k)]; s = s + v; ed = max(ed, bexp(v)); }
+      if (c.j < g.ny - 1) { X v = x[vidx(g, c.i, c.j + 1, k)]; s = s + v; ed = max(ed, bexp(v)); }
+      X d = diag_at<X>(dg, face_mask(g, c.i, c.j, k));
       X ax = d * xc - s;
       long long id = vidx(g, c.i, c.j, k);
-      double bi = (id == src) ? 1.0 : 0.0;
-      X r = Traits<X>::from(bi, 0.0) - ax;
-      double r2 = Traits<X>::abs2(r);
-      rr += r2;
-      double den = sqrt(Traits<X>::abs2(d)) * sqrt(Traits<X>::abs2(xc)) + as + bi;
-      if (r2 > 0.0) om = fmax(om, den > 0.0 ? sqrt(r2) / den : INFINITY);
+      X r = (id == src) ? Traits<X>::make(1.0, 0.0) - ax : zero - ax;
+      rr += Traits<X>::abs2(r);
+      int ec = bexp(xc);
+      ed = max(ed, ec ? ec + 2 : 0);
+      if (id == src) ed = max(ed, 1023);
+      int er = bexp(r);
+      if (er) om_e = max(om_e, ed ? er + 1 + cplx_extra - ed : 4096);
       xm = xc;
       xc = xp;
     }
   }
-  // sum rr, max om
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double s1 = warp_sum(rr), m1 = warp_max(om);
-  if (lane == 0) { sm[warp] = s1; sm[32 + warp] = m1; }
+  double s1 = warp_sum(rr);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) om_e = max(om_e, __shfl_down_sync(0xffffffffu, om_e, o));
+  if (lane == 0) { sm[warp] = s1; smi[warp] = om_e; }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double s = 0.0, m = 0.0;
-    for (int w = 0; w < NWARPS; ++w) { s += sm[w]; m = fmax(m, sm[32 + w]); }
+    double s = 0.0;
+    int m = -4096;
+    for (int w = 0; w < NWARPS; ++w) { s += sm[w]; m = max(m, smi[w]); }
     double* p = b.part + (size_t)c.rhs * part_stride(g.ntiles) + 8 * g.ntiles + 2 * c.tile;
     p[0] = s;
-    p[1] = m;
+    p[1] = (m <= -4096) ? 0.0 : (m >= 4096 ? INFINITY : ldexp(1.0, m));
   }
 }
 
@@ -273,8 +299,11 @@ __global__ void __launch_bounds__(NTHREADS) k_init(Geo g, Batch b, const X* __re
   if (b.status[c.rhs] != RHS_INNER) return;
   using Rt = typename Traits<T>::R;
   const LamCoef& lc = b.coef[rhs_lambda(b, c.rhs)];
-  Diag dg;
+  DiagT<double> dg;
   dg.load(lc);
+  DiagT<Rt> dgi;
+  dgi.load(lc);
+  const T idint = inv(diag_at<T>(dgi, 0));
   const long long src = rhs_source(b, c.rhs);
   const double inv_scale = 1.0 / b.scale[c.rhs];
   const X* x = x64 + (size_t)c.rhs * g.N;
@@ -292,13 +321,14 @@ __global__ void __launch_bounds__(NTHREADS) k_init(Geo g, Batch b, const X* __re
       if (c.i < g.nx - 1) s = s + x[vidx(g, c.i + 1, c.j, k)];
       if (c.j > 0) s = s + x[vidx(g, c.i, c.j - 1, k)];
       if (c.j < g.ny - 1) s = s + x[vidx(g, c.i, c.j + 1, k)];
-      double add = dg.add(g, c.i, c.j, k);
-      X d = make_diag<X>(dg, add);
+      const int m = face_mask(g, c.i, c.j, k);
+      X d = diag_at<X>(dg, m);
       long long id = vidx(g, c.i, c.j, k);
-      X r64 = Traits<X>::from(id == src ? 1.0 : 0.0, 0.0) - (d * xc - s);
+      X ax = d * xc - s;
+      X r64 = (id == src) ? Traits<X>::make(1.0, 0.0) - ax : zero - ax;
       T rv = Traits<T>::from(Traits<X>::re(r64) * inv_scale, Traits<X>::im(r64) * inv_scale);
       r[id] = rv;
-      T z = rv * inv(make_diag<T>(dg, add));
+      T z = rv * (m ? inv(diag_at<T>(dgi, m)) : idint);
       T rz = rv * z;
       acc[0] += (Rt)Traits<T>::re(rz);
       acc[1] += (Rt)Traits<T>::im(rz);
@@ -352,28 +382,27 @@ __global__ void __launch_bounds__(NTHREADS) k_dir(Geo g, Batch b, int it, const 
   if (it > 0) {
     double prev[2];
     tile_sum<2>(pb + 2 * T_ * (par ^ 1), 1, 2, T_, prev, sm);
-    // beta = rho_cur / rho_prev (complex division in double)
+    // beta = rho_cur / rho_prev (complex division in double, once per block)
     double den = prev[0] * prev[0] + prev[1] * prev[1];
     double br = (cur[0] * prev[0] + cur[1] * prev[1]) / den;
     double bi = (cur[1] * prev[0] - cur[0] * prev[1]) / den;
     beta = Traits<T>::from(br, bi);
   }
   const LamCoef& lc = b.coef[rhs_lambda(b, c.rhs)];
-  Diag dg;
+  DiagT<Rt> dg;
   dg.load(lc);
   const T* r = R + (size_t)c.rhs * g.N;
   const T* po = Pold + (size_t)c.rhs * g.N;
   T* pn = Pnew + (size_t)c.rhs * g.N;
-  const T dint = make_diag<T>(dg, 0.0);
+  const T dint = diag_at<T>(dg, 0);
   const T idint = inv(dint);
   const bool first = (it == 0);
   Rt acc[2] = {0, 0};
   if (c.in) {
     auto P = [&](int ii, int jj, int kk) -> T {
       long long id = vidx(g, ii, jj, kk);
-      double add = dg.add(g, ii, jj, kk);
-      T idd = (add == 0.0) ? idint : inv(make_diag<T>(dg, add));
-      T z = r[id] * idd;
+      const int m = face_mask(g, ii, jj, kk);
+      T z = r[id] * (m ? inv(diag_at<T>(dg, m)) : idint);
       return first ? z : z + beta * po[id];
     };
     T zero = Traits<T>::zero();
@@ -386,8 +415,8 @@ __global__ void __launch_bounds__(NTHREADS) k_dir(Geo g, Batch b, int it, const 
       if (c.i < g.nx - 1) s = s + P(c.i + 1, c.j, k);
       if (c.j > 0) s = s + P(c.i, c.j - 1, k);
       if (c.j < g.ny - 1) s = s + P(c.i, c.j + 1, k);
-      T d = make_diag<T>(dg, dg.add(g, c.i, c.j, k));
-      T q = d * pc - s;
+      const int m = face_mask(g, c.i, c.j, k);
+      T q = (m ? diag_at<T>(dg, m) : dint) * pc - s;
       T pq = pc * q;
       acc[0] += (Rt)Traits<T>::re(pq);
       acc[1] += (Rt)Traits<T>::im(pq);
@@ -423,12 +452,13 @@ __global__ void __launch_bounds__(NTHREADS) k_update(Geo g, Batch b, int it, T* 
   double ai = (rho[1] * gam[0] - rho[0] * gam[1]) / den;
   const T alpha = Traits<T>::from(ar, ai);
   const LamCoef& lc = b.coef[rhs_lambda(b, c.rhs)];
-  Diag dg;
+  DiagT<Rt> dg;
   dg.load(lc);
   T* e = E + (size_t)c.rhs * g.N;
   T* r = R + (size_t)c.rhs * g.N;
   const T* p = Pn + (size_t)c.rhs * g.N;
-  const T idint = inv(make_diag<T>(dg, 0.0));
+  const T dint = diag_at<T>(dg, 0);
+  const T idint = inv(dint);
   const bool first = (it == 0);
   Rt acc[3] = {0, 0, 0};
   if (c.in) {
@@ -443,15 +473,15 @@ __global__ void __launch_bounds__(NTHREADS) k_update(Geo g, Batch b, int it, T* 
       if (c.i < g.nx - 1) s = s + p[vidx(g, c.i + 1, c.j, k)];
       if (c.j > 0) s = s + p[vidx(g, c.i, c.j - 1, k)];
       if (c.j < g.ny - 1) s = s + p[vidx(g, c.i, c.j + 1, k)];
-      double add = dg.add(g, c.i, c.j, k);
-      T d = make_diag<T>(dg, add);
+      const int m = face_mask(g, c.i, c.j, k);
+      T d = m ? diag_at<T>(dg, m) : dint;
       T q = d * pc - s;
       long long id = vidx(g, c.i, c.j, k);
       T ev = first ? alpha * pc : e[id] + alpha * pc;
       T rv = r[id] - alpha * q;
       e[id] = ev;
       r[id] = rv;
-      T z = rv * ((add == 0.0) ? idint : inv(d));
+      T z = rv * (m ? inv(d) : idint);
       T rz = rv * z;
       acc[0] += (Rt)Traits<T>::re(rz);
       acc[1] += (Rt)Traits<T>::im(rz);
