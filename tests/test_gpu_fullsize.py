@@ -1,0 +1,88 @@
+"""Full-size parity at the benchmark's launch configuration (64x64x48 grid, 32 + 32 optodes,
+16-wavelength chunks, FP32 PCG with FP64 refinement to a componentwise backward error <= 1e-8).
+
+Expected values are the oracle's sparse-direct fields at sampled voxels and at every optode
+cell, written by tests/golden/make_golden.py (oracle only). Born entries are checked at those
+voxels against the row maximum of the oracle's H row; J x / J^T y by the adjoint identity.
+"""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "cw_mixed_64x64x48.npz")
+CHUNK = 16
+
+
+@pytest.fixture(scope="module")
+def solved(lib):
+    gold = np.load(GOLD)
+    p = workloads.config(2)
+    ctx = lib.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=1e-8, max_lambda_per_call=CHUNK)
+    out = {}
+    for a, lam in enumerate(gold["lams"]):
+        lam0 = (int(lam) // CHUNK) * CHUNK
+        ps, pd, st = ctx.solve_fields(lam0, CHUNK)
+        out[int(lam)] = (lam0, ps, pd, st, a)
+    yield p, gold, ctx, out
+    ctx.close()
+
+
+def test_fields_at_sampled_voxels(solved):
+    p, gold, ctx, out = solved
+    vox = torch.tensor(gold["vox"], device="cuda")
+    for lam, (lam0, ps, pd, st, a) in out.items():
+        assert st["n_not_converged"] == 0
+        gs = ps[lam - lam0][:, vox].double().cpu().numpy()
+        gd = pd[lam - lam0][:, vox].double().cpu().numpy()
+        for got, ref, nrm in ((gs, gold["phis"][a], gold["norms_s"][a]), (gd, gold["phid"][a], gold["norms_d"][a])):
+            # entrywise error against the field norm (bounds the 1e-6 norm-wise criterion from below)
+            assert (np.abs(got - ref).max(axis=1) / nrm).max() <= 1e-6
+            # far field: entry-by-entry relative accuracy at the optode cells (the Born rows need it)
+            n_opt = p.n_src + p.n_det
+            rel = np.abs(got[:, -n_opt:] - ref[:, -n_opt:]) / np.abs(ref[:, -n_opt:])
+            assert rel.max() <= 1e-5, rel.max()
+
+
+def test_born_rows_at_sampled_voxels(solved, lib):
+    p, gold, ctx, out = solved
+    N, nc, nd = p.grid.N, p.n_chrom, p.n_det
+    h3 = p.grid.h ** 3
+    vox = gold["vox"]
+    cols = torch.tensor(np.concatenate([c * N + vox for c in range(nc)]), device="cuda")
+    for lam, (lam0, ps, pd, st, a) in out.items():
+        s_list = (0, 13, 31)
+        for s in s_list:
+            row0 = s * nd * CHUNK
+            J = ctx.born_assemble(ps, pd, lam0, CHUNK, row0, nd * CHUNK)
+            rows = torch.arange(nd, device="cuda") * CHUNK + (lam - lam0)  # (s, d, lam) for d = 0..nd-1
+            Jr = J[rows]
+            got = Jr[:, cols].double().cpu().numpy().reshape(nd, nc, -1)
+            rowmax_gpu = Jr.abs().max(dim=1).values.double().cpu().numpy()
+            del J, Jr
+            eps = p.eps[lam]
+            ref_h = gold["phis"][a][s][None, :] * gold["phid"][a]  # [nd, vox]
+            ref = -h3 * eps[None, :, None] * ref_h[:, None, :]
+            rowmax = h3 * np.abs(eps).max() * gold["hmax"][a][s]  # [nd]
+            err = np.abs(got - ref).max(axis=(1, 2)) / rowmax
+            assert err.max() <= 1e-5, err.max()
+            assert np.abs(rowmax_gpu - rowmax).max() <= 1e-5 * rowmax.max()
+            assert (np.abs(rowmax_gpu - rowmax) / rowmax).max() <= 1e-5
+
+
+def test_apply_adjoint_identity_full_size(solved):
+    p, gold, ctx, out = solved
+    lam0, ps, pd, st, a = next(iter(out.values()))
+    g = torch.Generator(device="cuda").manual_seed(3)
+    x = torch.randn(p.n_chrom * p.grid.N, device="cuda", generator=g)
+    y = torch.randn(p.n_src * p.n_det * CHUNK, device="cuda", generator=g)
+    jx = ctx.born_apply(ps, pd, lam0, CHUNK, x)
+    jty = ctx.born_apply_T(ps, pd, lam0, CHUNK, y)
+    lhs = float((jx.double() * y.double()).sum())
+    rhs = float((x.double() * jty.double()).sum())
+    assert abs(lhs - rhs) <= 1e-5 * max(abs(lhs), 1e-300) + 1e-5 * float(jx.double().abs().sum() * y.abs().max())
