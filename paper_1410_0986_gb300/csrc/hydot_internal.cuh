@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of libhydot.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -44,6 +45,8 @@ template <> struct Traits<float> {
   __host__ __device__ static double re(float v) { return v; }
   __host__ __device__ static double im(float) { return 0.0; }
   __host__ __device__ static float abs2(float v) { return v * v; }
+  __host__ __device__ static float rre(float v) { return v; }
+  __host__ __device__ static float rim(float) { return 0.f; }
 };
 template <> struct Traits<double> {
   using R = double;
@@ -54,6 +57,8 @@ template <> struct Traits<double> {
   __host__ __device__ static double re(double v) { return v; }
   __host__ __device__ static double im(double) { return 0.0; }
   __host__ __device__ static double abs2(double v) { return v * v; }
+  __host__ __device__ static double rre(double v) { return v; }
+  __host__ __device__ static double rim(double) { return 0.0; }
 };
 template <> struct Traits<cpx<float>> {
   using R = float;
@@ -64,6 +69,8 @@ template <> struct Traits<cpx<float>> {
   __host__ __device__ static double re(cpx<float> v) { return v.re; }
   __host__ __device__ static double im(cpx<float> v) { return v.im; }
   __host__ __device__ static float abs2(cpx<float> v) { return v.re * v.re + v.im * v.im; }
+  __host__ __device__ static float rre(cpx<float> v) { return v.re; }
+  __host__ __device__ static float rim(cpx<float> v) { return v.im; }
 };
 template <> struct Traits<cpx<double>> {
   using R = double;
@@ -74,6 +81,8 @@ template <> struct Traits<cpx<double>> {
   __host__ __device__ static double re(cpx<double> v) { return v.re; }
   __host__ __device__ static double im(cpx<double> v) { return v.im; }
   __host__ __device__ static double abs2(cpx<double> v) { return v.re * v.re + v.im * v.im; }
+  __host__ __device__ static double rre(cpx<double> v) { return v.re; }
+  __host__ __device__ static double rim(cpx<double> v) { return v.im; }
 };
 
 // ----------------------------------------------------------------------------- coefficients
@@ -145,6 +154,9 @@ struct hydot_ctx {
   int* d_counter = nullptr;  // [counter_len] active-field counters (one per inner iteration)
   int counter_len = 0;
   int* h_pinned = nullptr;   // pinned host words for polling
+  int* d_err = nullptr;      // set by a kernel whose bounded wait gave up
+  bool use_tma = false;      // FP32 real inner kernels with TMA tile loads (nx % 4 == 0)
+  CUtensorMap tm_r{}, tm_p[2]{};  // 4-D maps {nx, ny, nz, max_fields} of d_r, d_p[0], d_p[1]
   // deflation (recycled subspace): W [k][N] FP64 and the k x k Gram blocks
   double* d_W = nullptr;
   std::vector<double> gram_L, gram_I, gram_B;  // W^T Lg W, W^T W, W^T B_f W (6 blocks)

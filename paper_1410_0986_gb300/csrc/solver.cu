@@ -19,10 +19,14 @@
 // Scalars are never stored: every block of a field sums the per-tile partials of the previous
 // pass in the same fixed order, so all blocks agree bit for bit and the result is reproducible.
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
+#include <cudaTypedefs.h>
 
 #include "hydot_internal.cuh"
+#include "tma.cuh"
 
 namespace hydot {
 
@@ -60,6 +64,7 @@ struct Batch {
   double* fin;
   double* part;
   int* counter;
+  int* err;
   double tol_in2;
   int max_inner, max_iter;
   double tol, tol_cw;
@@ -330,8 +335,8 @@ __global__ void __launch_bounds__(NTHREADS) k_init(Geo g, Batch b, const X* __re
       r[id] = rv;
       T z = rv * (m ? inv(diag_at<T>(dgi, m)) : idint);
       T rz = rv * z;
-      acc[0] += (Rt)Traits<T>::re(rz);
-      acc[1] += (Rt)Traits<T>::im(rz);
+      acc[0] += Traits<T>::rre(rz);
+      acc[1] += Traits<T>::rim(rz);
       acc[2] += Traits<T>::abs2(rv);
       xm = xc;
       xc = xp;
@@ -418,8 +423,8 @@ __global__ void __launch_bounds__(NTHREADS) k_dir(Geo g, Batch b, int it, const 
       const int m = face_mask(g, c.i, c.j, k);
       T q = (m ? diag_at<T>(dg, m) : dint) * pc - s;
       T pq = pc * q;
-      acc[0] += (Rt)Traits<T>::re(pq);
-      acc[1] += (Rt)Traits<T>::im(pq);
+      acc[0] += Traits<T>::rre(pq);
+      acc[1] += Traits<T>::rim(pq);
       pn[vidx(g, c.i, c.j, k)] = pc;
       pm = pc;
       pc = pp;
@@ -483,8 +488,8 @@ __global__ void __launch_bounds__(NTHREADS) k_update(Geo g, Batch b, int it, T* 
       r[id] = rv;
       T z = rv * (m ? inv(d) : idint);
       T rz = rv * z;
-      acc[0] += (Rt)Traits<T>::re(rz);
-      acc[1] += (Rt)Traits<T>::im(rz);
+      acc[0] += Traits<T>::rre(rz);
+      acc[1] += Traits<T>::rim(rz);
       acc[2] += Traits<T>::abs2(rv);
       pm = pc;
       pc = pp;
@@ -496,6 +501,210 @@ __global__ void __launch_bounds__(NTHREADS) k_update(Geo g, Batch b, int it, T* 
     pb[2 * T_ * (par ^ 1) + 2 * c.tile] = out[0];
     pb[2 * T_ * (par ^ 1) + 2 * c.tile + 1] = out[1];
     pb[4 * T_ + T_ * (par ^ 1) + c.tile] = out[2];
+    if (c.tile == 0) b.iters[c.rhs] += 1;
+  }
+}
+
+// ---------------------------------------------------------------- inner K_A / K_B with TMA tiles
+// FP32 real fields whose row pitch is a multiple of 16 bytes. A block owns a 32 x 8 x TZT tile;
+// one thread issues a 4-D TMA load of the tile plus a one-cell halo (rounded out to x0-4 so the
+// x coordinate stays 16-byte aligned) into shared memory; cells outside the grid arrive as zeros,
+// so the stencil adds its six neighbours without branches (the Robin/Dirichlet faces live in the
+// diagonal). The wait on the mbarrier is bounded: on timeout the block flags b.err, waits
+// (bounded) for its copy to land and returns.
+constexpr int TZT = 8;
+constexpr int BXT = 40, BYT = 10, BZT = TZT + 2;
+constexpr int BOXN = BXT * BYT * BZT;
+constexpr uint32_t BOX_BYTES = BOXN * 4;
+constexpr size_t tma_smem(int nbox) { return (size_t)nbox * BOX_BYTES + 128; }
+
+__device__ __forceinline__ float* align128(unsigned char* p) {
+  return reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(p) + 127) & ~uintptr_t(127));
+}
+
+// Wait for the tile; false (after flagging) when the bounded wait gave up.
+__device__ __forceinline__ bool tile_ready(uint64_t* mbar, int* err) {
+  if (mbar_wait_bounded(mbar, 0)) return true;
+  atomicExch(err, 1);
+  mbar_wait_bounded(mbar, 0);  // let the copy in flight land before shared memory is released
+  return false;
+}
+
+__global__ void __launch_bounds__(NTHREADS) k_dir_tma(Geo g, Batch b, int it, const __grid_constant__ CUtensorMap mapR,
+                                                      const __grid_constant__ CUtensorMap mapPold,
+                                                      float* __restrict__ Pnew) {
+  extern __shared__ unsigned char dsm[];
+  float* bR = align128(dsm);
+  float* bP = bR + BOXN;
+  __shared__ uint64_t mbar;
+  __shared__ double sm[96];
+  __shared__ int s_status;
+  __shared__ int s_ok;
+  TileCoord c = tile_coord(g);
+  if (threadIdx.x == 0) s_status = b.status[c.rhs];
+  __syncthreads();
+  if (s_status != RHS_INNER) return;
+  const int T_ = g.ntiles;
+  double* pb = b.part + (size_t)c.rhs * part_stride(T_);
+  const int par = it & 1;
+  double cur[3];
+  {
+    double t2[2];
+    tile_sum<2>(pb + 2 * T_ * par, 1, 2, T_, t2, sm);
+    cur[0] = t2[0];
+    cur[1] = t2[1];
+    double t1[1];
+    tile_sum<1>(pb + 4 * T_ + T_ * par, 0, 1, T_, t1, sm);
+    cur[2] = t1[0];
+  }
+  if (cur[2] <= b.tol_in2 || it >= b.max_inner || b.iters[c.rhs] >= b.max_iter || cur[2] == 0.0) {
+    if (c.tile == 0 && threadIdx.x == 0) b.status[c.rhs] = RHS_FINISHED;
+    return;
+  }
+  const bool first = (it == 0);
+  const int x0 = (c.tile % g.ntx) * TX, y0 = ((c.tile / g.ntx) % g.nty) * TY, z0 = c.k0;
+  if (threadIdx.x == 0) {
+    mbar_init(&mbar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (c.tile == 0) atomicAdd(&b.counter[1 + it], 1);
+    mbar_expect_tx(&mbar, first ? BOX_BYTES : 2 * BOX_BYTES);
+    tma_load_4d(bR, &mapR, &mbar, x0 - 4, y0 - 1, z0 - 1, c.rhs);
+    if (!first) tma_load_4d(bP, &mapPold, &mbar, x0 - 4, y0 - 1, z0 - 1, c.rhs);
+  }
+  float beta = 0.f;
+  if (!first) {
+    double prev[1];
+    tile_sum<1>(pb + 2 * T_ * (par ^ 1), 0, 2, T_, prev, sm);
+    beta = (float)(cur[0] / prev[0]);
+  }
+  const LamCoef& lc = b.coef[rhs_lambda(b, c.rhs)];
+  DiagT<float> dg;
+  dg.load(lc);
+  const float dint = dg.dre;
+  const float idint = 1.f / dint;
+  if (threadIdx.x == 0) s_ok = tile_ready(&mbar, b.err);
+  __syncthreads();
+  if (!s_ok) return;
+  // p_new = D^-1 r + beta p_old over the whole box, in place (zeros stay zeros outside the grid)
+  for (int q = threadIdx.x; q < BOXN; q += NTHREADS) {
+    const int il = q % BXT, jl = (q / BXT) % BYT, kl = q / (BXT * BYT);
+    const int gi = x0 - 4 + il, gj = y0 - 1 + jl, gk = z0 - 1 + kl;
+    const int m = face_mask(g, gi, gj, gk);
+    const float z = bR[q] * (m ? 1.f / (dint + dg.add(m)) : idint);
+    bR[q] = first ? z : fmaf(beta, bP[q], z);
+  }
+  __syncthreads();
+  float acc = 0.f;
+  if (c.in) {
+    const int lx = threadIdx.x % TX + 4, ly = threadIdx.x / TX + 1;
+    float* out = Pnew + (size_t)c.rhs * g.N;
+    for (int kk = 0; kk < TZT; ++kk) {
+      const int k = z0 + kk;
+      if (k >= g.nz) break;
+      const int ci = ((kk + 1) * BYT + ly) * BXT + lx;
+      const float pc = bR[ci];
+      const float s = (bR[ci - 1] + bR[ci + 1]) + (bR[ci - BXT] + bR[ci + BXT]) +
+                      (bR[ci - BXT * BYT] + bR[ci + BXT * BYT]);
+      const int m = face_mask(g, c.i, c.j, k);
+      const float q = (m ? dint + dg.add(m) : dint) * pc - s;
+      acc = fmaf(pc, q, acc);
+      out[vidx(g, c.i, c.j, k)] = pc;
+    }
+  }
+  float a1[1] = {acc};
+  double o1[1];
+  block_sum<1, float>(a1, o1, sm);
+  if (threadIdx.x == 0) {
+    pb[6 * T_ + 2 * c.tile] = o1[0];
+    pb[6 * T_ + 2 * c.tile + 1] = 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(NTHREADS) k_update_tma(Geo g, Batch b, int it, float* __restrict__ E,
+                                                         float* __restrict__ R,
+                                                         const __grid_constant__ CUtensorMap mapP) {
+  extern __shared__ unsigned char dsm[];
+  float* bP = align128(dsm);
+  __shared__ uint64_t mbar;
+  __shared__ double sm[96];
+  __shared__ int s_ok;
+  TileCoord c = tile_coord(g);
+  if (b.status[c.rhs] != RHS_INNER) return;
+  const int T_ = g.ntiles;
+  double* pb = b.part + (size_t)c.rhs * part_stride(T_);
+  const int par = it & 1;
+  const int x0 = (c.tile % g.ntx) * TX, y0 = ((c.tile / g.ntx) % g.nty) * TY, z0 = c.k0;
+  if (threadIdx.x == 0) {
+    mbar_init(&mbar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(&mbar, BOX_BYTES);
+    tma_load_4d(bP, &mapP, &mbar, x0 - 4, y0 - 1, z0 - 1, c.rhs);
+  }
+  // while the tile is in flight: alpha, and this thread's e and r columns
+  double rho[1], gam[1];
+  tile_sum<1>(pb + 2 * T_ * par, 0, 2, T_, rho, sm);
+  tile_sum<1>(pb + 6 * T_, 0, 2, T_, gam, sm);
+  const float alpha = (float)(rho[0] / gam[0]);
+  const bool first = (it == 0);
+  float* e = E + (size_t)c.rhs * g.N;
+  float* r = R + (size_t)c.rhs * g.N;
+  const int nk = min(TZT, g.nz - z0);
+  float ev[TZT], rv[TZT];
+  if (c.in) {
+#pragma unroll
+    for (int kk = 0; kk < TZT; ++kk) {
+      if (kk < nk) {
+        const long long id = vidx(g, c.i, c.j, z0 + kk);
+        rv[kk] = r[id];
+        ev[kk] = first ? 0.f : e[id];
+      }
+    }
+  }
+  const LamCoef& lc = b.coef[rhs_lambda(b, c.rhs)];
+  DiagT<float> dg;
+  dg.load(lc);
+  const float dint = dg.dre;
+  const float idint = 1.f / dint;
+  if (threadIdx.x == 0) s_ok = tile_ready(&mbar, b.err);
+  __syncthreads();
+  if (!s_ok) return;
+  float acc[2] = {0.f, 0.f};
+  if (c.in) {
+    const int lx = threadIdx.x % TX + 4, ly = threadIdx.x / TX + 1;
+#pragma unroll
+    for (int kk = 0; kk < TZT; ++kk) {
+      if (kk < nk) {
+        const int k = z0 + kk;
+        const int ci = ((kk + 1) * BYT + ly) * BXT + lx;
+        const float pc = bP[ci];
+        const float s = (bP[ci - 1] + bP[ci + 1]) + (bP[ci - BXT] + bP[ci + BXT]) +
+                        (bP[ci - BXT * BYT] + bP[ci + BXT * BYT]);
+        const int m = face_mask(g, c.i, c.j, k);
+        const float d = m ? dint + dg.add(m) : dint;
+        const float q = d * pc - s;
+        const float en = fmaf(alpha, pc, ev[kk]);
+        const float rn = fmaf(-alpha, q, rv[kk]);
+        const long long id = vidx(g, c.i, c.j, k);
+        e[id] = en;
+        r[id] = rn;
+        const float z = rn * (m ? 1.f / d : idint);
+        acc[0] = fmaf(rn, z, acc[0]);
+        acc[1] = fmaf(rn, rn, acc[1]);
+      }
+    }
+  }
+  double out[2];
+  block_sum<2, float>(acc, out, sm);
+  if (threadIdx.x == 0) {
+    pb[2 * T_ * (par ^ 1) + 2 * c.tile] = out[0];
+    pb[2 * T_ * (par ^ 1) + 2 * c.tile + 1] = 0.0;
+    pb[4 * T_ + T_ * (par ^ 1) + c.tile] = out[1];
     if (c.tile == 0) b.iters[c.rhs] += 1;
   }
 }
@@ -572,6 +781,7 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
   b.fin = ctx->d_final;
   b.part = ctx->d_part;
   b.counter = ctx->d_counter;
+  b.err = ctx->d_err;
   const bool mixed = ctx->precision == HYDOT_MIXED;
   const double tin = mixed ? (ctx->inner_tol > 0 ? ctx->inner_tol : 1e-5) : ctx->tol;
   b.tol_in2 = tin * tin;
@@ -589,6 +799,7 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
   const dim3 blk(NTHREADS);
 
   HYDOT_CUDA_TRY(ctx, cudaMemsetAsync(x64, 0, sizeof(X) * (size_t)b.nrhs * g.N, s));
+  HYDOT_CUDA_TRY(ctx, cudaMemsetAsync(b.err, 0, sizeof(int), s));
   k_reset<<<(b.nrhs + 255) / 256, 256, 0, s>>>(b);
   ++ctx->launches;
   HYDOT_CUDA_TRY(ctx, cudaGetLastError());
@@ -617,6 +828,15 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
     while (!stop && it < MAX_INNER_PER_CYCLE) {
       int g_end = std::min(it + POLL_GROUP, MAX_INNER_PER_CYCLE);
       for (; it < g_end; ++it) {
+        if constexpr (std::is_same<T, float>::value) {
+          if (ctx->use_tma) {
+            k_dir_tma<<<nblk, blk, tma_smem(2), s>>>(g, b, it, ctx->tm_r, ctx->tm_p[it & 1], P[(it + 1) & 1]);
+            ++ctx->launches;
+            k_update_tma<<<nblk, blk, tma_smem(1), s>>>(g, b, it, E, R, ctx->tm_p[(it + 1) & 1]);
+            ++ctx->launches;
+            continue;
+          }
+        }
         k_dir<T><<<nblk, blk, 0, s>>>(g, b, it, R, P[it & 1], P[(it + 1) & 1]);
         ++ctx->launches;
         k_update<T><<<nblk, blk, 0, s>>>(g, b, it, E, R, P[(it + 1) & 1]);
@@ -660,7 +880,10 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
   HYDOT_CUDA_TRY(ctx, cudaMemcpyAsync(iters.data(), b.iters, sizeof(int) * b.nrhs, cudaMemcpyDeviceToHost, s));
   HYDOT_CUDA_TRY(ctx, cudaMemcpyAsync(cycles.data(), b.cycles, sizeof(int) * b.nrhs, cudaMemcpyDeviceToHost, s));
   HYDOT_CUDA_TRY(ctx, cudaMemcpyAsync(fin.data(), b.fin, sizeof(double) * 2 * b.nrhs, cudaMemcpyDeviceToHost, s));
+  int timed_out = 0;
+  HYDOT_CUDA_TRY(ctx, cudaMemcpyAsync(&timed_out, b.err, sizeof(int), cudaMemcpyDeviceToHost, s));
   HYDOT_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  if (timed_out) return fail(ctx, HYDOT_ERR_TIMEOUT, "a bounded wait for a TMA tile gave up; fields are not valid");
   int nnc = 0, imax = 0, cmax = 0;
   double isum = 0, rmax = 0, omax = 0;
   for (int i = 0; i < b.nrhs; ++i) {
@@ -690,11 +913,45 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
 
 }  // namespace
 
+namespace {
+
+bool getenv_flag(const char* name) {
+  const char* v = std::getenv(name);
+  return v && *v && std::strcmp(v, "0") != 0;
+}
+
+// 4-D tensor map {nx, ny, nz, max_fields} of an FP32 field buffer, box = one TMA tile with halo.
+int encode_field_map(hydot_ctx* ctx, void* base, CUtensorMap* map) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+      return fail(ctx, HYDOT_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t nx = ctx->nx, ny = ctx->ny, nz = ctx->nz, F = ctx->max_fields;
+  cuuint64_t dims[4] = {nx, ny, nz, F};
+  cuuint64_t strides[3] = {nx * 4, nx * ny * 4, nx * ny * nz * 4};
+  cuuint32_t box[4] = {(cuuint32_t)BXT, (cuuint32_t)BYT, (cuuint32_t)BZT, 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(ctx, HYDOT_ERR_CUDA, "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
+  return HYDOT_OK;
+}
+
+}  // namespace
+
 int solver_alloc(hydot_ctx* ctx) {
   Tiling& t = ctx->tiling;
   t.tx = TX;
   t.ty = TY;
-  t.tz = std::min(ctx->nz, 16);
+  // FP32 real fields with a 16-byte row pitch take the TMA inner kernels (8-plane tiles)
+  ctx->use_tma = ctx->precision == HYDOT_MIXED && !ctx->cplx && (ctx->nx % 4 == 0) && !getenv_flag("HYDOT_NO_TMA");
+  t.tz = ctx->use_tma ? std::min(ctx->nz, TZT) : std::min(ctx->nz, 16);
   t.ntx = (ctx->nx + TX - 1) / TX;
   t.nty = (ctx->ny + TY - 1) / TY;
   t.ntz = (ctx->nz + t.tz - 1) / t.tz;
@@ -719,6 +976,14 @@ int solver_alloc(hydot_ctx* ctx) {
   ctx->counter_len = MAX_INNER_PER_CYCLE + 8;
   HYDOT_CUDA_TRY(ctx, cudaMalloc(&ctx->d_counter, sizeof(int) * ctx->counter_len));
   HYDOT_CUDA_TRY(ctx, cudaMallocHost(&ctx->h_pinned, sizeof(int) * 8));
+  HYDOT_CUDA_TRY(ctx, cudaMalloc(&ctx->d_err, sizeof(int)));
+  HYDOT_CUDA_TRY(ctx, cudaMemset(ctx->d_err, 0, sizeof(int)));
+  if (ctx->use_tma) {
+    int rc = encode_field_map(ctx, ctx->d_r, &ctx->tm_r);
+    if (!rc) rc = encode_field_map(ctx, ctx->d_p[0], &ctx->tm_p[0]);
+    if (!rc) rc = encode_field_map(ctx, ctx->d_p[1], &ctx->tm_p[1]);
+    if (rc) return rc;
+  }
   return HYDOT_OK;
 }
 
@@ -735,6 +1000,7 @@ void solver_free(hydot_ctx* ctx) {
   cudaFree(ctx->d_scale);
   cudaFree(ctx->d_final);
   cudaFree(ctx->d_counter);
+  cudaFree(ctx->d_err);
   if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
 }
 

@@ -46,6 +46,11 @@ CASES = {
                                                                     geometry="transmission", margin=1), None),
     "mixed-faces-17x12x10": (lambda: workloads.small(seed=6, nx=17, ny=12, nz=10, n_src=2, n_det=2, n_lambda=2,
                                                      robin_A=(0.0, 3.0, 1.0, 3.0, 0.5, 3.0)), None),
+    # nx % 4 == 0: the FP32 path takes the TMA tile kernels; ragged tiles in x, y and z
+    "tma-ragged-36x19x21": (lambda: workloads.make_problem(workloads.Grid(36, 19, 21, 2.0), 3, 3, 3, seed=10,
+                                                           geometry="transmission", margin=1), None),
+    "tma-faces-40x16x9": (lambda: workloads.small(seed=14, nx=40, ny=16, nz=9, n_src=2, n_det=3, n_lambda=2,
+                                                  robin_A=(0.0, 3.0, 1.0, 3.0, 0.5, 2.0)), None),
 }
 
 
@@ -75,6 +80,20 @@ def test_fields_mixed_and_born_rows(hd, oracle_fields, name):
     assert rel_err(ps, rs) <= 1e-6 and rel_err(pd, rd) <= 1e-6
     assert born_rowmax_err(p, ps, pd, rs, rd) <= 1e-5
     assert st["cycles_max"] >= 2 and st["cw_max"] <= 1e-8
+
+
+def test_tma_and_generic_kernels_agree(hd, oracle_fields, monkeypatch):
+    """The TMA tile kernels and the generic kernels solve the same systems to the same tolerance."""
+    p, (rs, rd) = oracle_fields["tma-ragged-36x19x21"]
+    out = []
+    for flag in ("0", "1"):
+        monkeypatch.setenv("HYDOT_NO_TMA", flag)
+        with hd.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=1e-8) as ctx:
+            ps, pd, st = ctx.solve_fields(0, p.n_lambda)
+        out.append((ps, pd))
+        assert rel_err(ps, rs) <= 1e-6 and born_rowmax_err(p, ps, pd, rs, rd) <= 1e-5
+    a, b = out
+    assert (a[0] - b[0]).abs().max() <= 1e-6 * a[0].abs().max()
 
 
 def test_config1_fp64_fields_and_born_matrix(hd):
