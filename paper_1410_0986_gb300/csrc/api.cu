@@ -75,6 +75,7 @@ int validate(const hydot_problem* p, std::string& msg) {
 void free_all(hydot_ctx* c) {
   hydot::solver_free(c);
   cudaFree(c->d_coef);
+  cudaFree(c->d_coef_f);
   cudaFree(c->d_eps);
   cudaFree(c->d_optode);
   cudaFree(c->d_W);
@@ -151,6 +152,17 @@ int hydot_setup(const hydot_problem* p, void* stream, hydot_ctx** out) {
   } while (0)
   SETUP_TRY(cudaMalloc(&c->d_coef, sizeof(hydot::LamCoef) * c->n_lambda));
   SETUP_TRY(cudaMemcpy(c->d_coef, c->coef.data(), sizeof(hydot::LamCoef) * c->n_lambda, cudaMemcpyHostToDevice));
+  {
+    std::vector<hydot::LamCoefF> cf(c->n_lambda);
+    for (int j = 0; j < c->n_lambda; ++j) {
+      cf[j].dint = (float)(6.0 + c->coef[j].sigma_re);
+      cf[j].dim = (float)c->coef[j].sigma_im;
+      cf[j].idint = (float)(1.0 / (6.0 + c->coef[j].sigma_re));
+      for (int f = 0; f < 6; ++f) cf[j].fa[f] = (float)(c->coef[j].bhat[f] - 1.0);
+    }
+    SETUP_TRY(cudaMalloc(&c->d_coef_f, sizeof(hydot::LamCoefF) * c->n_lambda));
+    SETUP_TRY(cudaMemcpy(c->d_coef_f, cf.data(), sizeof(hydot::LamCoefF) * c->n_lambda, cudaMemcpyHostToDevice));
+  }
   SETUP_TRY(cudaMalloc(&c->d_eps, sizeof(double) * c->eps.size()));
   SETUP_TRY(cudaMemcpy(c->d_eps, c->eps.data(), sizeof(double) * c->eps.size(), cudaMemcpyHostToDevice));
   SETUP_TRY(cudaMalloc(&c->d_optode, sizeof(int) * c->optode_voxel.size()));

@@ -98,6 +98,14 @@ struct LamCoef {
   double mua, D;
 };
 
+// The same coefficients in FP32 for the inner kernels (no FP64 conversion on the device).
+struct LamCoefF {
+  float dint;   // 6 + sigma_re: diagonal of an interior cell
+  float dim;    // sigma_im
+  float idint;  // 1 / dint
+  float fa[6];  // bhat_f - 1
+};
+
 // Solver state of one simultaneous field (right-hand side) of a batch.
 enum RhsStatus : int { RHS_INNER = 0, RHS_FINISHED = 1, RHS_DONE = 2 };
 
@@ -135,6 +143,7 @@ struct hydot_ctx {
   // per-wavelength tables
   std::vector<hydot::LamCoef> coef;  // host copy
   hydot::LamCoef* d_coef = nullptr;
+  hydot::LamCoefF* d_coef_f = nullptr;
   double* d_eps = nullptr;           // [n_lambda][n_chrom]
   int* d_optode = nullptr;           // [n_src + n_det]
 

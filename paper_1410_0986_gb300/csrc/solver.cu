@@ -134,11 +134,6 @@ __device__ __forceinline__ R warp_sum(R v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
 }
-__device__ __forceinline__ double warp_max(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
-  return v;
-}
 
 // Sum NV per-thread values over the block (deterministic); result valid in thread 0.
 template <int NV, typename R>
@@ -522,190 +517,260 @@ __device__ __forceinline__ float* align128(unsigned char* p) {
   return reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(p) + 127) & ~uintptr_t(127));
 }
 
-// Wait for the tile; false (after flagging) when the bounded wait gave up.
-__device__ __forceinline__ bool tile_ready(uint64_t* mbar, int* err) {
-  if (mbar_wait_bounded(mbar, 0)) return true;
-  atomicExch(err, 1);
-  mbar_wait_bounded(mbar, 0);  // let the copy in flight land before shared memory is released
-  return false;
+// A block owns one (field, x-tile, y-tile) column and marches its z-tiles with two TMA stages:
+// the load of tile z+1 is in flight while tile z is computed. Per-field scalars (convergence,
+// alpha, beta) are formed once per block by one lane and broadcast through shared memory, so
+// the FP64 pipe only sums the per-tile partials. The block writes its column's partial sums to
+// the slot of its first z-tile and zeros to the others (the per-tile layout of the partials is
+// shared with the generic kernels).
+struct ColCoord {
+  int rhs, x0, y0, i, j, slot0;
+  bool in;
+};
+__device__ __forceinline__ ColCoord col_coord(const Geo& g) {
+  ColCoord c;
+  const int ncol = g.ntx * g.nty;
+  c.rhs = blockIdx.x / ncol;
+  const int col = blockIdx.x % ncol;
+  c.x0 = (col % g.ntx) * TX;
+  c.y0 = (col / g.ntx) * TY;
+  c.i = c.x0 + threadIdx.x % TX;
+  c.j = c.y0 + threadIdx.x / TX;
+  c.in = (c.i < g.nx) && (c.j < g.ny);
+  c.slot0 = col;  // tile index of (col, z-tile 0)
+  return c;
 }
 
-__global__ void __launch_bounds__(NTHREADS) k_dir_tma(Geo g, Batch b, int it, const __grid_constant__ CUtensorMap mapR,
+__device__ __forceinline__ float diag_f(const LamCoefF& cf, int m) {
+  float a = cf.dint;
+#pragma unroll
+  for (int f = 0; f < 6; ++f)
+    if (m & (1 << f)) a += cf.fa[f];
+  return a;
+}
+
+// Wait for stage s (use number u of that stage). Thread 0 waits, the block learns the outcome.
+__device__ __forceinline__ bool stage_ready(uint64_t* mbar, int s, int u, int* err, int* s_ok) {
+  if (threadIdx.x == 0) {
+    bool ok = mbar_wait_bounded(&mbar[s], (uint32_t)(u & 1));
+    if (!ok) atomicExch(err, 1);
+    *s_ok = ok;
+  }
+  __syncthreads();
+  return *s_ok != 0;
+}
+
+__global__ void __launch_bounds__(NTHREADS) k_dir_tma(Geo g, Batch b, int it, const LamCoefF* __restrict__ coef_f,
+                                                      const __grid_constant__ CUtensorMap mapR,
                                                       const __grid_constant__ CUtensorMap mapPold,
                                                       float* __restrict__ Pnew) {
   extern __shared__ unsigned char dsm[];
-  float* bR = align128(dsm);
-  float* bP = bR + BOXN;
-  __shared__ uint64_t mbar;
+  float* buf = align128(dsm);  // [2 stages][r box, p_old box]
+  __shared__ uint64_t mbar[2];
   __shared__ double sm[96];
-  __shared__ int s_status;
-  __shared__ int s_ok;
-  TileCoord c = tile_coord(g);
-  if (threadIdx.x == 0) s_status = b.status[c.rhs];
-  __syncthreads();
-  if (s_status != RHS_INNER) return;
+  __shared__ float s_beta;
+  __shared__ int s_go, s_ok;
+  const ColCoord c = col_coord(g);
   const int T_ = g.ntiles;
   double* pb = b.part + (size_t)c.rhs * part_stride(T_);
   const int par = it & 1;
-  double cur[3];
-  {
-    double t2[2];
-    tile_sum<2>(pb + 2 * T_ * par, 1, 2, T_, t2, sm);
-    cur[0] = t2[0];
-    cur[1] = t2[1];
-    double t1[1];
-    tile_sum<1>(pb + 4 * T_ + T_ * par, 0, 1, T_, t1, sm);
-    cur[2] = t1[0];
-  }
-  if (cur[2] <= b.tol_in2 || it >= b.max_inner || b.iters[c.rhs] >= b.max_iter || cur[2] == 0.0) {
-    if (c.tile == 0 && threadIdx.x == 0) b.status[c.rhs] = RHS_FINISHED;
-    return;
-  }
   const bool first = (it == 0);
-  const int x0 = (c.tile % g.ntx) * TX, y0 = ((c.tile / g.ntx) % g.nty) * TY, z0 = c.k0;
+  if (threadIdx.x < 32) {
+    const int st = b.status[c.rhs];
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0;
+    if (st == RHS_INNER)
+      for (int t = threadIdx.x; t < T_; t += 32) {
+        v0 += pb[2 * T_ * par + 2 * t];
+        v1 += pb[4 * T_ + T_ * par + t];
+        if (!first) v2 += pb[2 * T_ * (par ^ 1) + 2 * t];
+      }
+    v0 = warp_sum(v0);
+    v1 = warp_sum(v1);
+    v2 = warp_sum(v2);
+    if (threadIdx.x == 0) {
+      int go = 0;
+      float beta = 0.f;
+      if (st == RHS_INNER) {
+        const bool done = v1 <= b.tol_in2 || it >= b.max_inner || b.iters[c.rhs] >= b.max_iter || v1 == 0.0;
+        if (done) {
+          if (c.slot0 == 0) b.status[c.rhs] = RHS_FINISHED;
+        } else {
+          go = 1;
+          beta = first ? 0.f : (float)(v0 / v2);
+          if (c.slot0 == 0) atomicAdd(&b.counter[1 + it], 1);
+        }
+      }
+      s_go = go;
+      s_beta = beta;
+    }
+  }
+  __syncthreads();
+  if (!s_go) return;
+  const float beta = s_beta;
+  const LamCoefF cf = coef_f[rhs_lambda(b, c.rhs)];
+  const int nbox = first ? 1 : 2;
   if (threadIdx.x == 0) {
-    mbar_init(&mbar, 1);
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
     mbar_fence_init();
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    if (c.tile == 0) atomicAdd(&b.counter[1 + it], 1);
-    mbar_expect_tx(&mbar, first ? BOX_BYTES : 2 * BOX_BYTES);
-    tma_load_4d(bR, &mapR, &mbar, x0 - 4, y0 - 1, z0 - 1, c.rhs);
-    if (!first) tma_load_4d(bP, &mapPold, &mbar, x0 - 4, y0 - 1, z0 - 1, c.rhs);
-  }
-  float beta = 0.f;
-  if (!first) {
-    double prev[1];
-    tile_sum<1>(pb + 2 * T_ * (par ^ 1), 0, 2, T_, prev, sm);
-    beta = (float)(cur[0] / prev[0]);
-  }
-  const LamCoef& lc = b.coef[rhs_lambda(b, c.rhs)];
-  DiagT<float> dg;
-  dg.load(lc);
-  const float dint = dg.dre;
-  const float idint = 1.f / dint;
-  if (threadIdx.x == 0) s_ok = tile_ready(&mbar, b.err);
-  __syncthreads();
-  if (!s_ok) return;
-  // p_new = D^-1 r + beta p_old over the whole box, in place (zeros stay zeros outside the grid)
-  for (int q = threadIdx.x; q < BOXN; q += NTHREADS) {
-    const int il = q % BXT, jl = (q / BXT) % BYT, kl = q / (BXT * BYT);
-    const int gi = x0 - 4 + il, gj = y0 - 1 + jl, gk = z0 - 1 + kl;
-    const int m = face_mask(g, gi, gj, gk);
-    const float z = bR[q] * (m ? 1.f / (dint + dg.add(m)) : idint);
-    bR[q] = first ? z : fmaf(beta, bP[q], z);
-  }
-  __syncthreads();
+  auto issue = [&](int tz) {
+    float* dst = buf + (tz & 1) * 2 * BOXN;
+    mbar_expect_tx(&mbar[tz & 1], nbox * BOX_BYTES);
+    tma_load_4d(dst, &mapR, &mbar[tz & 1], c.x0 - 4, c.y0 - 1, tz * TZT - 1, c.rhs);
+    if (!first) tma_load_4d(dst + BOXN, &mapPold, &mbar[tz & 1], c.x0 - 4, c.y0 - 1, tz * TZT - 1, c.rhs);
+  };
+  if (threadIdx.x == 0) issue(0);
   float acc = 0.f;
-  if (c.in) {
-    const int lx = threadIdx.x % TX + 4, ly = threadIdx.x / TX + 1;
-    float* out = Pnew + (size_t)c.rhs * g.N;
-    for (int kk = 0; kk < TZT; ++kk) {
-      const int k = z0 + kk;
-      if (k >= g.nz) break;
-      const int ci = ((kk + 1) * BYT + ly) * BXT + lx;
-      const float pc = bR[ci];
-      const float s = (bR[ci - 1] + bR[ci + 1]) + (bR[ci - BXT] + bR[ci + BXT]) +
-                      (bR[ci - BXT * BYT] + bR[ci + BXT * BYT]);
-      const int m = face_mask(g, c.i, c.j, k);
-      const float q = (m ? dint + dg.add(m) : dint) * pc - s;
-      acc = fmaf(pc, q, acc);
-      out[vidx(g, c.i, c.j, k)] = pc;
+  float* out = Pnew + (size_t)c.rhs * g.N;
+  const int lx = threadIdx.x % TX + 4, ly = threadIdx.x / TX + 1;
+  for (int tz = 0; tz < g.ntz; ++tz) {
+    if (threadIdx.x == 0 && tz + 1 < g.ntz) issue(tz + 1);
+    if (!stage_ready(mbar, tz & 1, tz >> 1, b.err, &s_ok)) {
+      if (threadIdx.x == 0 && tz + 1 < g.ntz) mbar_wait_bounded(&mbar[(tz + 1) & 1], (uint32_t)(((tz + 1) >> 1) & 1));
+      return;
     }
+    float* bR = buf + (tz & 1) * 2 * BOXN;
+    const float* bP = bR + BOXN;
+    const int z0 = tz * TZT;
+    // p_new = D^-1 r + beta p_old on the box columns x0-1 .. x0+32, in place
+    for (int q = threadIdx.x; q < 34 * BYT * BZT; q += NTHREADS) {
+      const int il = 3 + q % 34, jl = (q / 34) % BYT, kl = q / (34 * BYT);
+      const int bi = (kl * BYT + jl) * BXT + il;
+      const int m = face_mask(g, c.x0 - 4 + il, c.y0 - 1 + jl, z0 - 1 + kl);
+      const float zv = bR[bi] * (m ? 1.f / diag_f(cf, m) : cf.idint);
+      bR[bi] = first ? zv : fmaf(beta, bP[bi], zv);
+    }
+    __syncthreads();
+    if (c.in) {
+      for (int kk = 0; kk < TZT; ++kk) {
+        const int k = z0 + kk;
+        if (k >= g.nz) break;
+        const int ci = ((kk + 1) * BYT + ly) * BXT + lx;
+        const float pc = bR[ci];
+        const float sn = (bR[ci - 1] + bR[ci + 1]) + (bR[ci - BXT] + bR[ci + BXT]) +
+                         (bR[ci - BXT * BYT] + bR[ci + BXT * BYT]);
+        const int m = face_mask(g, c.i, c.j, k);
+        const float q = (m ? diag_f(cf, m) : cf.dint) * pc - sn;
+        acc = fmaf(pc, q, acc);
+        out[vidx(g, c.i, c.j, k)] = pc;
+      }
+    }
+    __syncthreads();  // stage tz & 1 is free for tile tz + 2
   }
   float a1[1] = {acc};
   double o1[1];
   block_sum<1, float>(a1, o1, sm);
-  if (threadIdx.x == 0) {
-    pb[6 * T_ + 2 * c.tile] = o1[0];
-    pb[6 * T_ + 2 * c.tile + 1] = 0.0;
+  if (threadIdx.x < g.ntz) {
+    const int slot = c.slot0 + threadIdx.x * g.ntx * g.nty;
+    pb[6 * T_ + 2 * slot] = threadIdx.x == 0 ? o1[0] : 0.0;
+    pb[6 * T_ + 2 * slot + 1] = 0.0;
   }
 }
 
-__global__ void __launch_bounds__(NTHREADS) k_update_tma(Geo g, Batch b, int it, float* __restrict__ E,
-                                                         float* __restrict__ R,
-                                                         const __grid_constant__ CUtensorMap mapP) {
+__global__ void __launch_bounds__(NTHREADS, 5) k_update_tma(Geo g, Batch b, int it, const LamCoefF* __restrict__ coef_f,
+                                                            float* __restrict__ E, float* __restrict__ R,
+                                                            const __grid_constant__ CUtensorMap mapP) {
   extern __shared__ unsigned char dsm[];
-  float* bP = align128(dsm);
-  __shared__ uint64_t mbar;
+  float* buf = align128(dsm);  // [2 stages][p box]
+  __shared__ uint64_t mbar[2];
   __shared__ double sm[96];
-  __shared__ int s_ok;
-  TileCoord c = tile_coord(g);
-  if (b.status[c.rhs] != RHS_INNER) return;
+  __shared__ float s_alpha;
+  __shared__ int s_go, s_ok;
+  const ColCoord c = col_coord(g);
   const int T_ = g.ntiles;
   double* pb = b.part + (size_t)c.rhs * part_stride(T_);
   const int par = it & 1;
-  const int x0 = (c.tile % g.ntx) * TX, y0 = ((c.tile / g.ntx) % g.nty) * TY, z0 = c.k0;
+  const bool first = (it == 0);
+  if (threadIdx.x < 32) {
+    const int st = b.status[c.rhs];
+    double v0 = 0.0, v1 = 0.0;
+    if (st == RHS_INNER)
+      for (int t = threadIdx.x; t < T_; t += 32) {
+        v0 += pb[2 * T_ * par + 2 * t];
+        v1 += pb[6 * T_ + 2 * t];
+      }
+    v0 = warp_sum(v0);
+    v1 = warp_sum(v1);
+    if (threadIdx.x == 0) {
+      s_go = st == RHS_INNER;
+      s_alpha = s_go ? (float)(v0 / v1) : 0.f;
+    }
+  }
+  __syncthreads();
+  if (!s_go) return;
+  const float alpha = s_alpha;
+  const LamCoefF cf = coef_f[rhs_lambda(b, c.rhs)];
   if (threadIdx.x == 0) {
-    mbar_init(&mbar, 1);
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
     mbar_fence_init();
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    mbar_expect_tx(&mbar, BOX_BYTES);
-    tma_load_4d(bP, &mapP, &mbar, x0 - 4, y0 - 1, z0 - 1, c.rhs);
-  }
-  // while the tile is in flight: alpha, and this thread's e and r columns
-  double rho[1], gam[1];
-  tile_sum<1>(pb + 2 * T_ * par, 0, 2, T_, rho, sm);
-  tile_sum<1>(pb + 6 * T_, 0, 2, T_, gam, sm);
-  const float alpha = (float)(rho[0] / gam[0]);
-  const bool first = (it == 0);
+  auto issue = [&](int tz) {
+    mbar_expect_tx(&mbar[tz & 1], BOX_BYTES);
+    tma_load_4d(buf + (tz & 1) * BOXN, &mapP, &mbar[tz & 1], c.x0 - 4, c.y0 - 1, tz * TZT - 1, c.rhs);
+  };
+  if (threadIdx.x == 0) issue(0);
   float* e = E + (size_t)c.rhs * g.N;
   float* r = R + (size_t)c.rhs * g.N;
-  const int nk = min(TZT, g.nz - z0);
-  float ev[TZT], rv[TZT];
-  if (c.in) {
-#pragma unroll
-    for (int kk = 0; kk < TZT; ++kk) {
-      if (kk < nk) {
-        const long long id = vidx(g, c.i, c.j, z0 + kk);
-        rv[kk] = r[id];
-        ev[kk] = first ? 0.f : e[id];
-      }
-    }
-  }
-  const LamCoef& lc = b.coef[rhs_lambda(b, c.rhs)];
-  DiagT<float> dg;
-  dg.load(lc);
-  const float dint = dg.dre;
-  const float idint = 1.f / dint;
-  if (threadIdx.x == 0) s_ok = tile_ready(&mbar, b.err);
-  __syncthreads();
-  if (!s_ok) return;
+  const int lx = threadIdx.x % TX + 4, ly = threadIdx.x / TX + 1;
   float acc[2] = {0.f, 0.f};
-  if (c.in) {
-    const int lx = threadIdx.x % TX + 4, ly = threadIdx.x / TX + 1;
+  for (int tz = 0; tz < g.ntz; ++tz) {
+    if (threadIdx.x == 0 && tz + 1 < g.ntz) issue(tz + 1);
+    const int z0 = tz * TZT;
+    const int nk = min(TZT, g.nz - z0);
+    float ev[TZT], rv[TZT];
+    if (c.in) {
 #pragma unroll
-    for (int kk = 0; kk < TZT; ++kk) {
-      if (kk < nk) {
-        const int k = z0 + kk;
-        const int ci = ((kk + 1) * BYT + ly) * BXT + lx;
-        const float pc = bP[ci];
-        const float s = (bP[ci - 1] + bP[ci + 1]) + (bP[ci - BXT] + bP[ci + BXT]) +
-                        (bP[ci - BXT * BYT] + bP[ci + BXT * BYT]);
-        const int m = face_mask(g, c.i, c.j, k);
-        const float d = m ? dint + dg.add(m) : dint;
-        const float q = d * pc - s;
-        const float en = fmaf(alpha, pc, ev[kk]);
-        const float rn = fmaf(-alpha, q, rv[kk]);
-        const long long id = vidx(g, c.i, c.j, k);
-        e[id] = en;
-        r[id] = rn;
-        const float z = rn * (m ? 1.f / d : idint);
-        acc[0] = fmaf(rn, z, acc[0]);
-        acc[1] = fmaf(rn, rn, acc[1]);
+      for (int kk = 0; kk < TZT; ++kk) {
+        if (kk < nk) {
+          const long long id = vidx(g, c.i, c.j, z0 + kk);
+          rv[kk] = r[id];
+          ev[kk] = first ? 0.f : e[id];
+        }
       }
     }
+    if (!stage_ready(mbar, tz & 1, tz >> 1, b.err, &s_ok)) {
+      if (threadIdx.x == 0 && tz + 1 < g.ntz) mbar_wait_bounded(&mbar[(tz + 1) & 1], (uint32_t)(((tz + 1) >> 1) & 1));
+      return;
+    }
+    const float* bP = buf + (tz & 1) * BOXN;
+    if (c.in) {
+#pragma unroll
+      for (int kk = 0; kk < TZT; ++kk) {
+        if (kk < nk) {
+          const int k = z0 + kk;
+          const int ci = ((kk + 1) * BYT + ly) * BXT + lx;
+          const float pc = bP[ci];
+          const float sn = (bP[ci - 1] + bP[ci + 1]) + (bP[ci - BXT] + bP[ci + BXT]) +
+                           (bP[ci - BXT * BYT] + bP[ci + BXT * BYT]);
+          const int m = face_mask(g, c.i, c.j, k);
+          const float d = m ? diag_f(cf, m) : cf.dint;
+          const float q = d * pc - sn;
+          const float en = fmaf(alpha, pc, ev[kk]);
+          const float rn = fmaf(-alpha, q, rv[kk]);
+          const long long id = vidx(g, c.i, c.j, k);
+          e[id] = en;
+          r[id] = rn;
+          const float zv = rn * (m ? 1.f / d : cf.idint);
+          acc[0] = fmaf(rn, zv, acc[0]);
+          acc[1] = fmaf(rn, rn, acc[1]);
+        }
+      }
+    }
+    __syncthreads();  // stage tz & 1 is free for tile tz + 2
   }
   double out[2];
   block_sum<2, float>(acc, out, sm);
-  if (threadIdx.x == 0) {
-    pb[2 * T_ * (par ^ 1) + 2 * c.tile] = out[0];
-    pb[2 * T_ * (par ^ 1) + 2 * c.tile + 1] = 0.0;
-    pb[4 * T_ + T_ * (par ^ 1) + c.tile] = out[1];
-    if (c.tile == 0) b.iters[c.rhs] += 1;
+  if (threadIdx.x < g.ntz) {
+    const int slot = c.slot0 + threadIdx.x * g.ntx * g.nty;
+    const bool z = threadIdx.x == 0;
+    pb[2 * T_ * (par ^ 1) + 2 * slot] = z ? out[0] : 0.0;
+    pb[2 * T_ * (par ^ 1) + 2 * slot + 1] = 0.0;
+    pb[4 * T_ + T_ * (par ^ 1) + slot] = z ? out[1] : 0.0;
+    if (z && c.slot0 == 0) b.iters[c.rhs] += 1;
   }
 }
 
@@ -830,9 +895,11 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
       for (; it < g_end; ++it) {
         if constexpr (std::is_same<T, float>::value) {
           if (ctx->use_tma) {
-            k_dir_tma<<<nblk, blk, tma_smem(2), s>>>(g, b, it, ctx->tm_r, ctx->tm_p[it & 1], P[(it + 1) & 1]);
+            const unsigned ncb = (unsigned)((long long)b.nrhs * g.ntx * g.nty);
+            k_dir_tma<<<ncb, blk, tma_smem(4), s>>>(g, b, it, ctx->d_coef_f, ctx->tm_r, ctx->tm_p[it & 1],
+                                                    P[(it + 1) & 1]);
             ++ctx->launches;
-            k_update_tma<<<nblk, blk, tma_smem(1), s>>>(g, b, it, E, R, ctx->tm_p[(it + 1) & 1]);
+            k_update_tma<<<ncb, blk, tma_smem(2), s>>>(g, b, it, ctx->d_coef_f, E, R, ctx->tm_p[(it + 1) & 1]);
             ++ctx->launches;
             continue;
           }
@@ -979,6 +1046,8 @@ int solver_alloc(hydot_ctx* ctx) {
   HYDOT_CUDA_TRY(ctx, cudaMalloc(&ctx->d_err, sizeof(int)));
   HYDOT_CUDA_TRY(ctx, cudaMemset(ctx->d_err, 0, sizeof(int)));
   if (ctx->use_tma) {
+    HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(k_dir_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem(4)));
+    HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(k_update_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem(2)));
     int rc = encode_field_map(ctx, ctx->d_r, &ctx->tm_r);
     if (!rc) rc = encode_field_map(ctx, ctx->d_p[0], &ctx->tm_p[0]);
     if (!rc) rc = encode_field_map(ctx, ctx->d_p[1], &ctx->tm_p[1]);
