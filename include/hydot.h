@@ -82,6 +82,17 @@ typedef struct {
   int max_iter;            /* cap on Krylov iterations per field, all cycles together (0: 20000) */
   int deflation_k;         /* size of the recycled deflation basis, 0..32 (0: off)            */
   int max_lambda_per_call; /* largest nlam passed to hydot_solve_fields (0: n_lambda)          */
+  double cw_floor;         /* >= 0. With c = cw_floor > 0 the componentwise test of a field f at
+                            * wavelength j uses |b - A x|_i / (|A||x| + |b| + theta_f)_i with
+                            * theta_f = c * sigma_j * min |x_f| over its partner optode cells
+                            * (detectors for a source field, sources for a detector field;
+                            * sigma_j = mu_a h^2 / D in the operator scaled by 1/(D h)). Since
+                            * (A/(D h)) 1 >= sigma_j entrywise and A^-1 >= 0, the residual entries
+                            * this admits change the field by at most tol_cw * c times its smallest
+                            * partner value anywhere, so c = tau / tol_cw keeps every Born entry
+                            * J[(s,d,.),.] within about tau of its row maximum while cells far from
+                            * every optode stop driving refinement. 0: plain componentwise test.
+                            * Continuous wave only (ignored when omega != 0). */
 } hydot_problem;
 
 typedef struct {

@@ -38,6 +38,7 @@ class Problem(C.Structure):
         ("precision", C.c_int),
         ("tol", C.c_double), ("tol_cw", C.c_double), ("inner_tol", C.c_double),
         ("max_iter", C.c_int), ("deflation_k", C.c_int), ("max_lambda_per_call", C.c_int),
+        ("cw_floor", C.c_double),
     ]
 
 

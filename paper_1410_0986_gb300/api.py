@@ -37,7 +37,7 @@ class Context:
     def __init__(self, nx: int, ny: int, nz: int, h: float, robin_A: Sequence[float], eps, c_bg, mus_prime,
                  src_ijk, det_ijk, *, omega: float = 0.0, c_medium: float = 299.792458 / 1.4,
                  precision: str = "mixed", tol: float = 1e-10, tol_cw: float = 1e-8, inner_tol: float = 0.0,
-                 max_iter: int = 0, deflation_k: int = 0, max_lambda_per_call: int = 0):
+                 max_iter: int = 0, deflation_k: int = 0, max_lambda_per_call: int = 0, cw_floor: float = 0.0):
         if not torch.cuda.is_available():
             raise RuntimeError("libhydot needs a CUDA device; there is no CPU path")
         self.lib = _lib.load()
@@ -63,6 +63,7 @@ class Context:
         p.precision = PRECISIONS[precision]
         p.tol, p.tol_cw, p.inner_tol = float(tol), float(tol_cw), float(inner_tol)
         p.max_iter, p.deflation_k, p.max_lambda_per_call = int(max_iter), int(deflation_k), int(max_lambda_per_call)
+        p.cw_floor = float(cw_floor)
         self.problem = p
         self.nx, self.ny, self.nz, self.N = p.nx, p.ny, p.nz, p.nx * p.ny * p.nz
         self.n_lambda, self.n_chrom, self.n_src, self.n_det = p.n_lambda, p.n_chrom, p.n_src, p.n_det

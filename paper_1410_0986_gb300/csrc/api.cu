@@ -69,6 +69,7 @@ int validate(const hydot_problem* p, std::string& msg) {
   if (p->deflation_k < 0 || p->deflation_k > 32) return bad("deflation_k must be in 0..32");
   if (p->max_lambda_per_call < 0 || p->max_lambda_per_call > p->n_lambda)
     return bad("max_lambda_per_call must be in 0..n_lambda");
+  if (!(p->cw_floor >= 0.0) || !std::isfinite(p->cw_floor)) return bad("cw_floor must be finite and >= 0");
   return HYDOT_OK;
 }
 
@@ -132,6 +133,7 @@ int hydot_setup(const hydot_problem* p, void* stream, hydot_ctx** out) {
   c->inner_tol = p->inner_tol;
   c->max_iter = p->max_iter > 0 ? p->max_iter : 20000;
   c->deflation_k = p->deflation_k;
+  c->cw_floor = p->omega == 0.0 ? p->cw_floor : 0.0;
   c->max_fields = (p->max_lambda_per_call > 0 ? p->max_lambda_per_call : p->n_lambda) * (p->n_src + p->n_det);
   c->stream = (cudaStream_t)stream;
   compute_coefficients(c);

@@ -131,7 +131,7 @@ struct hydot_ctx {
   double omega, c_medium;
   std::vector<int> optode_voxel;  // [n_src + n_det] sources then detectors
   int precision;
-  double tol, tol_cw, inner_tol;
+  double tol, tol_cw, inner_tol, cw_floor;
   int max_iter;
   int deflation_k;
   int max_fields;                 // simultaneous fields the workspace holds
@@ -158,7 +158,10 @@ struct hydot_ctx {
   int* d_status = nullptr;   // [max_fields]
   int* d_iters = nullptr;    // [max_fields] Krylov iterations, all cycles
   int* d_cycles = nullptr;   // [max_fields]
-  double* d_scale = nullptr; // [max_fields] ||r|| of the current cycle
+  double* d_scale = nullptr; // [max_fields] 1 / (scale of the FP32 residual) of the current cycle
+  double* d_next = nullptr;  // [max_fields] ||r64|| of the latest residual (next cycle's scale)
+  double* d_rr0 = nullptr;   // [max_fields] ||r32||^2 at the start of the inner solve
+  double* d_theta = nullptr; // [max_fields] floor of the componentwise test
   double* d_final = nullptr; // [max_fields][2] final residual norm, componentwise error
   int* d_counter = nullptr;  // [counter_len] active-field counters (one per inner iteration)
   int counter_len = 0;

@@ -4,10 +4,11 @@
 // Each simultaneous field ("rhs") solves  Ahat x = e_cell  with Ahat = A_j / (D_j h) (the
 // operator of eqn:discincident restated as finite volumes, see hydot.h); the field is
 // phi = x / (D_j h). One refinement cycle:
-//   K_res    r64 = b - Ahat x64 in FP64, ||r64||_2 and the componentwise backward error
-//            max_i |r64_i| / (|Ahat||x64| + |b|)_i                         [per-tile partials]
-//   K_decide stop, or start a cycle with scale = ||r64||                   [one thread per rhs]
-//   K_init   r = r64 / scale in the inner precision, rho_0 = r^T D^-1 r
+//   K_theta  floor of the componentwise test from the partner optode cells (optional)
+//   K_res    r64 = b - Ahat x64 in FP64, ||r64||_2, the componentwise backward error
+//            max_i |r64_i| / (|Ahat||x64| + |b| + theta)_i, and the inner right-hand side
+//            r = r64 / scale in the inner precision with rho_0 = r^T D^-1 r  [per-tile partials]
+//   K_decide stop, or start a cycle                                        [one thread per rhs]
 //   K_A/K_B  inner PCG/COCG on Ahat e = r (two kernels per iteration, see below)
 //   K_fold   x64 += scale * e
 // The inner iteration is split in two passes over memory because alpha needs the global
@@ -61,13 +62,17 @@ struct Batch {
   int* iters;
   int* cycles;
   double* scale;
+  double* next;
+  double* rr0;
+  double* theta;
   double* fin;
   double* part;
   int* counter;
   int* err;
   double tol_in2;
   int max_inner, max_iter;
-  double tol, tol_cw;
+  double tol, tol_cw, cw_floor;
+  int n_src, n_det;
 };
 
 __device__ __forceinline__ int rhs_lambda(const Batch& b, int rhs) { return b.lam0 + rhs / b.nf; }
@@ -206,25 +211,37 @@ __device__ __forceinline__ long long vidx(const Geo& g, int i, int j, int k) {
 }
 
 // ---------------------------------------------------------------- FP64 residual
-// r = b - Ahat x64 in FP64 (six adds and one fused multiply-add per cell on the FP64 pipe), its
-// squared norm, and a bound on the componentwise backward error
-//   omega = max_i |r_i| / (|Ahat||x|_i + |b_i|)
-// computed from the binary exponents in the integer pipes: |r_i| < 2^(e_r - 1022) and
-// (|Ahat||x| + |b|)_i >= 2^(max(e_xc + 2, e_nbr, e_b) - 1023) (|diagonal| >= 4), so
-// 2^(e_r + 1 - max(...)) >= omega_i. The bound exceeds the true value by at most a factor ~30,
-// so a stopping test on it is conservative.
-template <typename X>
-__global__ void __launch_bounds__(NTHREADS) k_residual(Geo g, Batch b, const X* __restrict__ x64) {
+// One pass per refinement cycle over the fields that finished an inner solve:
+//   r64 = b - Ahat x64 in FP64 (six adds and one fused multiply-add per cell on the FP64 pipe),
+//   ||r64||^2, and a bound on the componentwise backward error
+//     omega = max_i |r64_i| / (|Ahat||x|_i + |b_i| + theta)
+//   from binary exponents in the integer pipes: |r_i| < 2^(e_r - 1022) and the denominator is
+//   >= 2^(max(e_xc + 2, e_nbr, e_b, e_theta) - 1023) (|diagonal| >= 4), so 2^(e_r + 1 - max)
+//   >= omega_i; the bound exceeds the true value by at most a factor ~30 (conservative).
+// It also writes the next inner solve's right-hand side r = r64 / s in the inner precision,
+// with s = ||r64|| of the previous cycle (known before this pass; the inner solve's tolerance is
+// relative to its own start, so r need not have unit norm), and the partials of
+// rho_0 = r^T D^-1 r and ||r||^2 that the first inner iteration needs.
+template <typename T, typename X>
+__global__ void __launch_bounds__(NTHREADS) k_residual(Geo g, Batch b, const X* __restrict__ x64, T* __restrict__ R) {
   __shared__ double sm[96];
   __shared__ int smi[NWARPS];
   TileCoord c = tile_coord(g);
   if (b.status[c.rhs] != RHS_FINISHED) return;
+  using Rt = typename Traits<T>::R;
   const LamCoef& lc = b.coef[rhs_lambda(b, c.rhs)];
   DiagT<double> dg;
   dg.load(lc);
+  DiagT<Rt> dgi;
+  dgi.load(lc);
+  const T idint = inv(diag_at<T>(dgi, 0));
   const long long src = rhs_source(b, c.rhs);
+  const double pre = 1.0 / b.next[c.rhs];
+  const int etheta = bexp(b.theta[c.rhs]);
   const X* x = x64 + (size_t)c.rhs * g.N;
+  T* r = R + (size_t)c.rhs * g.N;
   double rr = 0.0;
+  Rt acc[3] = {0, 0, 0};  // rho_0 re, im, ||r||^2
   int om_e = -4096;
   constexpr int cplx_extra = Traits<X>::cplx ? 1 : 0;
   if (c.in) {
@@ -234,22 +251,29 @@ __global__ void __launch_bounds__(NTHREADS) k_residual(Geo g, Batch b, const X* 
     X xc = ld(c.k0);
     for (int k = c.k0; k < c.k1; ++k) {
       X xp = (k + 1 < g.nz) ? ld(k + 1) : zero;
-      X s = xm + xp;
-      int ed = max(bexp(xm), bexp(xp));
-      if (c.i > 0) { X v = x[vidx(g, c.i - 1, c.j, k)]; s = s + v; ed = max(ed, bexp(v)); }
-      if (c.i < g.nx - 1) { X v = x[vidx(g, c.i + 1, c.j, k)]; s = s + v; ed = max(ed, bexp(v)); }
-      if (c.j > 0) { X v = x[vidx(g, c.i, c.j - 1, k)]; s = s + v; ed = max(ed, bexp(v)); }
-      if (c.j < g.ny - 1) { X v = x[vidx(g, c.i, c.j + 1, k)]; s = s + v; ed = max(ed, bexp(v)); }
-      X d = diag_at<X>(dg, face_mask(g, c.i, c.j, k));
-      X ax = d * xc - s;
+      X sn = xm + xp;
+      int ed = max(max(bexp(xm), bexp(xp)), etheta);
+      if (c.i > 0) { X v = x[vidx(g, c.i - 1, c.j, k)]; sn = sn + v; ed = max(ed, bexp(v)); }
+      if (c.i < g.nx - 1) { X v = x[vidx(g, c.i + 1, c.j, k)]; sn = sn + v; ed = max(ed, bexp(v)); }
+      if (c.j > 0) { X v = x[vidx(g, c.i, c.j - 1, k)]; sn = sn + v; ed = max(ed, bexp(v)); }
+      if (c.j < g.ny - 1) { X v = x[vidx(g, c.i, c.j + 1, k)]; sn = sn + v; ed = max(ed, bexp(v)); }
+      const int m = face_mask(g, c.i, c.j, k);
+      X d = diag_at<X>(dg, m);
+      X ax = d * xc - sn;
       long long id = vidx(g, c.i, c.j, k);
-      X r = (id == src) ? Traits<X>::make(1.0, 0.0) - ax : zero - ax;
-      rr += Traits<X>::abs2(r);
+      X r64 = (id == src) ? Traits<X>::make(1.0, 0.0) - ax : zero - ax;
+      rr += Traits<X>::abs2(r64);
       int ec = bexp(xc);
       ed = max(ed, ec ? ec + 2 : 0);
       if (id == src) ed = max(ed, 1023);
-      int er = bexp(r);
+      int er = bexp(r64);
       if (er) om_e = max(om_e, ed ? er + 1 + cplx_extra - ed : 4096);
+      T rv = Traits<T>::from(Traits<X>::re(r64) * pre, Traits<X>::im(r64) * pre);
+      r[id] = rv;
+      T rz = rv * (rv * (m ? inv(diag_at<T>(dgi, m)) : idint));
+      acc[0] += Traits<T>::rre(rz);
+      acc[1] += Traits<T>::rim(rz);
+      acc[2] += Traits<T>::abs2(rv);
       xm = xc;
       xc = xp;
     }
@@ -258,25 +282,55 @@ __global__ void __launch_bounds__(NTHREADS) k_residual(Geo g, Batch b, const X* 
   double s1 = warp_sum(rr);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) om_e = max(om_e, __shfl_down_sync(0xffffffffu, om_e, o));
-  if (lane == 0) { sm[warp] = s1; smi[warp] = om_e; }
-  __syncthreads();
+  if (lane == 0) { sm[32 + warp] = s1; smi[warp] = om_e; }
+  double out[3];
+  block_sum<3, Rt>(acc, out, sm);  // (its barriers also publish sm[32..] and smi)
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    int m = -4096;
-    for (int w = 0; w < NWARPS; ++w) { s += sm[w]; m = max(m, smi[w]); }
-    double* p = b.part + (size_t)c.rhs * part_stride(g.ntiles) + 8 * g.ntiles + 2 * c.tile;
-    p[0] = s;
-    p[1] = (m <= -4096) ? 0.0 : (m >= 4096 ? INFINITY : ldexp(1.0, m));
+    double sr = 0.0;
+    int mx = -4096;
+    for (int w = 0; w < NWARPS; ++w) { sr += sm[32 + w]; mx = max(mx, smi[w]); }
+    const int T_ = g.ntiles;
+    double* pb = b.part + (size_t)c.rhs * part_stride(T_);
+    pb[8 * T_ + 2 * c.tile] = sr;
+    pb[8 * T_ + 2 * c.tile + 1] = (mx <= -4096) ? 0.0 : (mx >= 4096 ? INFINITY : ldexp(1.0, mx));
+    pb[2 * c.tile] = out[0];          // rho parity 0
+    pb[2 * c.tile + 1] = out[1];
+    pb[4 * T_ + c.tile] = out[2];     // ||r||^2 parity 0
   }
+}
+
+// Floor of the componentwise test: theta = cw_floor * sigma * min |x| over the field's partner
+// optode cells (detectors for a source field, sources for a detector field).
+template <typename X>
+__global__ void k_theta(Geo g, Batch b, const X* __restrict__ x64, const int* __restrict__ optode) {
+  int rhs = blockIdx.x * blockDim.x + threadIdx.x;
+  if (rhs >= b.nrhs) return;
+  if (b.status[rhs] != RHS_FINISHED) return;
+  const int f = b.f_begin + rhs % b.nf;
+  const bool is_src = f < b.n_src;
+  const int p0 = is_src ? b.n_src : 0, np = is_src ? b.n_det : b.n_src;
+  double th = 0.0;
+  if (b.cw_floor > 0.0 && np > 0) {
+    const X* x = x64 + (size_t)rhs * g.N;
+    double mn = INFINITY;
+    for (int q = 0; q < np; ++q) mn = fmin(mn, sqrt(Traits<X>::abs2(x[optode[p0 + q]])));
+    th = b.cw_floor * b.coef[rhs_lambda(b, rhs)].sigma_re * mn;
+  }
+  b.theta[rhs] = th;
 }
 
 __global__ void k_decide(Geo g, Batch b) {
   int rhs = blockIdx.x * blockDim.x + threadIdx.x;
   if (rhs >= b.nrhs) return;
   if (b.status[rhs] != RHS_FINISHED) return;
-  const double* p = b.part + (size_t)rhs * part_stride(g.ntiles) + 8 * g.ntiles;
-  double rr = 0.0, om = 0.0;
-  for (int t = 0; t < g.ntiles; ++t) { rr += p[2 * t]; om = fmax(om, p[2 * t + 1]); }
+  const int T_ = g.ntiles;
+  const double* pb = b.part + (size_t)rhs * part_stride(T_);
+  double rr = 0.0, om = 0.0, rr0 = 0.0;
+  for (int t = 0; t < T_; ++t) {
+    rr += pb[8 * T_ + 2 * t];
+    om = fmax(om, pb[8 * T_ + 2 * t + 1]);
+    rr0 += pb[4 * T_ + t];
+  }
   double res = sqrt(rr);  // ||b|| = 1 for a unit point source
   b.fin[2 * rhs] = res;
   b.fin[2 * rhs + 1] = om;
@@ -285,65 +339,11 @@ __global__ void k_decide(Geo g, Batch b) {
     b.status[rhs] = RHS_DONE;
   } else {
     b.status[rhs] = RHS_INNER;
-    b.scale[rhs] = res;
+    b.scale[rhs] = b.next[rhs];  // the inner right-hand side is r64 / scale: x += scale * e
+    b.next[rhs] = res;
+    b.rr0[rhs] = rr0;
     b.cycles[rhs] += 1;
     atomicAdd(&b.counter[0], 1);
-  }
-}
-
-// ---------------------------------------------------------------- inner init
-template <typename T, typename X>
-__global__ void __launch_bounds__(NTHREADS) k_init(Geo g, Batch b, const X* __restrict__ x64, T* __restrict__ R) {
-  __shared__ double sm[96];
-  TileCoord c = tile_coord(g);
-  if (b.status[c.rhs] != RHS_INNER) return;
-  using Rt = typename Traits<T>::R;
-  const LamCoef& lc = b.coef[rhs_lambda(b, c.rhs)];
-  DiagT<double> dg;
-  dg.load(lc);
-  DiagT<Rt> dgi;
-  dgi.load(lc);
-  const T idint = inv(diag_at<T>(dgi, 0));
-  const long long src = rhs_source(b, c.rhs);
-  const double inv_scale = 1.0 / b.scale[c.rhs];
-  const X* x = x64 + (size_t)c.rhs * g.N;
-  T* r = R + (size_t)c.rhs * g.N;
-  Rt acc[3] = {0, 0, 0};  // rho re, rho im, rr
-  if (c.in) {
-    auto ld = [&](int k) { return x[vidx(g, c.i, c.j, k)]; };
-    X zero = Traits<X>::zero();
-    X xm = c.k0 > 0 ? ld(c.k0 - 1) : zero;
-    X xc = ld(c.k0);
-    for (int k = c.k0; k < c.k1; ++k) {
-      X xp = (k + 1 < g.nz) ? ld(k + 1) : zero;
-      X s = xm + xp;
-      if (c.i > 0) s = s + x[vidx(g, c.i - 1, c.j, k)];
-      if (c.i < g.nx - 1) s = s + x[vidx(g, c.i + 1, c.j, k)];
-      if (c.j > 0) s = s + x[vidx(g, c.i, c.j - 1, k)];
-      if (c.j < g.ny - 1) s = s + x[vidx(g, c.i, c.j + 1, k)];
-      const int m = face_mask(g, c.i, c.j, k);
-      X d = diag_at<X>(dg, m);
-      long long id = vidx(g, c.i, c.j, k);
-      X ax = d * xc - s;
-      X r64 = (id == src) ? Traits<X>::make(1.0, 0.0) - ax : zero - ax;
-      T rv = Traits<T>::from(Traits<X>::re(r64) * inv_scale, Traits<X>::im(r64) * inv_scale);
-      r[id] = rv;
-      T z = rv * (m ? inv(diag_at<T>(dgi, m)) : idint);
-      T rz = rv * z;
-      acc[0] += Traits<T>::rre(rz);
-      acc[1] += Traits<T>::rim(rz);
-      acc[2] += Traits<T>::abs2(rv);
-      xm = xc;
-      xc = xp;
-    }
-  }
-  double out[3];
-  block_sum<3, Rt>(acc, out, sm);
-  if (threadIdx.x == 0) {
-    double* p = b.part + (size_t)c.rhs * part_stride(g.ntiles);
-    p[2 * c.tile] = out[0];           // rho parity 0
-    p[2 * c.tile + 1] = out[1];
-    p[4 * g.ntiles + c.tile] = out[2];  // rr parity 0
   }
 }
 
@@ -373,7 +373,7 @@ __global__ void __launch_bounds__(NTHREADS) k_dir(Geo g, Batch b, int it, const 
     cur[2] = t1[0];
   }
   // convergence of the inner solve (residual norm relative to the normalised start)
-  if (cur[2] <= b.tol_in2 || it >= b.max_inner || b.iters[c.rhs] >= b.max_iter || cur[2] == 0.0) {
+  if (cur[2] <= b.tol_in2 * b.rr0[c.rhs] || it >= b.max_inner || b.iters[c.rhs] >= b.max_iter || cur[2] == 0.0) {
     if (c.tile == 0 && threadIdx.x == 0) b.status[c.rhs] = RHS_FINISHED;
     return;
   }
@@ -591,7 +591,8 @@ __global__ void __launch_bounds__(NTHREADS) k_dir_tma(Geo g, Batch b, int it, co
       int go = 0;
       float beta = 0.f;
       if (st == RHS_INNER) {
-        const bool done = v1 <= b.tol_in2 || it >= b.max_inner || b.iters[c.rhs] >= b.max_iter || v1 == 0.0;
+        const bool done = v1 <= b.tol_in2 * b.rr0[c.rhs] || it >= b.max_inner || b.iters[c.rhs] >= b.max_iter ||
+                          v1 == 0.0;
         if (done) {
           if (c.slot0 == 0) b.status[c.rhs] = RHS_FINISHED;
         } else {
@@ -634,27 +635,46 @@ __global__ void __launch_bounds__(NTHREADS) k_dir_tma(Geo g, Batch b, int it, co
     float* bR = buf + (tz & 1) * 2 * BOXN;
     const float* bP = bR + BOXN;
     const int z0 = tz * TZT;
-    // p_new = D^-1 r + beta p_old on the box columns x0-1 .. x0+32, in place
-    for (int q = threadIdx.x; q < 34 * BYT * BZT; q += NTHREADS) {
-      const int il = 3 + q % 34, jl = (q / 34) % BYT, kl = q / (34 * BYT);
-      const int bi = (kl * BYT + jl) * BXT + il;
-      const int m = face_mask(g, c.x0 - 4 + il, c.y0 - 1 + jl, z0 - 1 + kl);
-      const float zv = bR[bi] * (m ? 1.f / diag_f(cf, m) : cf.idint);
-      bR[bi] = first ? zv : fmaf(beta, bP[bi], zv);
+    // p_new = D^-1 r + beta p_old on the box columns x0-1 .. x0+32, in place. Pass A: each warp
+    // takes whole (y, z) rows of the 32 own columns (consecutive words: no bank conflicts);
+    // pass B: the two x-halo columns.
+    {
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+      const int gi = c.x0 + lane;
+      const int xbits = (gi == 0) | ((gi == g.nx - 1) << 1);
+      for (int row = warp; row < BYT * BZT; row += NWARPS) {
+        const int jl = row % BYT, kl = row / BYT;
+        const int gj = c.y0 - 1 + jl, gk = z0 - 1 + kl;
+        const int m = xbits | ((gj == 0) << 2) | ((gj == g.ny - 1) << 3) | ((gk == 0) << 4) | ((gk == g.nz - 1) << 5);
+        const int bi = row * BXT + 4 + lane;
+        const float zv = bR[bi] * (m ? 1.f / diag_f(cf, m) : cf.idint);
+        bR[bi] = first ? zv : fmaf(beta, bP[bi], zv);
+      }
+      for (int q = threadIdx.x; q < 2 * BYT * BZT; q += NTHREADS) {
+        const int row = q >> 1, il = (q & 1) ? 36 : 3;
+        const int jl = row % BYT, kl = row / BYT;
+        const int bi = row * BXT + il;
+        const int m = face_mask(g, c.x0 - 4 + il, c.y0 - 1 + jl, z0 - 1 + kl);
+        const float zv = bR[bi] * (m ? 1.f / diag_f(cf, m) : cf.idint);
+        bR[bi] = first ? zv : fmaf(beta, bP[bi], zv);
+      }
     }
     __syncthreads();
     if (c.in) {
+      const int cb = ly * BXT + lx;  // (y, x) offset of this thread's column in a plane
+      float pm = bR[cb], pc = bR[BXT * BYT + cb];
       for (int kk = 0; kk < TZT; ++kk) {
         const int k = z0 + kk;
         if (k >= g.nz) break;
-        const int ci = ((kk + 1) * BYT + ly) * BXT + lx;
-        const float pc = bR[ci];
-        const float sn = (bR[ci - 1] + bR[ci + 1]) + (bR[ci - BXT] + bR[ci + BXT]) +
-                         (bR[ci - BXT * BYT] + bR[ci + BXT * BYT]);
+        const int ci = (kk + 1) * BXT * BYT + cb;
+        const float pp = bR[ci + BXT * BYT];
+        const float sn = (bR[ci - 1] + bR[ci + 1]) + (bR[ci - BXT] + bR[ci + BXT]) + (pm + pp);
         const int m = face_mask(g, c.i, c.j, k);
         const float q = (m ? diag_f(cf, m) : cf.dint) * pc - sn;
         acc = fmaf(pc, q, acc);
         out[vidx(g, c.i, c.j, k)] = pc;
+        pm = pc;
+        pc = pp;
       }
     }
     __syncthreads();  // stage tz & 1 is free for tile tz + 2
@@ -738,14 +758,15 @@ __global__ void __launch_bounds__(NTHREADS, 5) k_update_tma(Geo g, Batch b, int 
     }
     const float* bP = buf + (tz & 1) * BOXN;
     if (c.in) {
+      const int cb = ly * BXT + lx;
+      float pm = bP[cb], pc = bP[BXT * BYT + cb];
 #pragma unroll
       for (int kk = 0; kk < TZT; ++kk) {
         if (kk < nk) {
           const int k = z0 + kk;
-          const int ci = ((kk + 1) * BYT + ly) * BXT + lx;
-          const float pc = bP[ci];
-          const float sn = (bP[ci - 1] + bP[ci + 1]) + (bP[ci - BXT] + bP[ci + BXT]) +
-                           (bP[ci - BXT * BYT] + bP[ci + BXT * BYT]);
+          const int ci = (kk + 1) * BXT * BYT + cb;
+          const float pp = bP[ci + BXT * BYT];
+          const float sn = (bP[ci - 1] + bP[ci + 1]) + (bP[ci - BXT] + bP[ci + BXT]) + (pm + pp);
           const int m = face_mask(g, c.i, c.j, k);
           const float d = m ? diag_f(cf, m) : cf.dint;
           const float q = d * pc - sn;
@@ -757,6 +778,8 @@ __global__ void __launch_bounds__(NTHREADS, 5) k_update_tma(Geo g, Batch b, int 
           const float zv = rn * (m ? 1.f / d : cf.idint);
           acc[0] = fmaf(rn, zv, acc[0]);
           acc[1] = fmaf(rn, rn, acc[1]);
+          pm = pc;
+          pc = pp;
         }
       }
     }
@@ -812,6 +835,8 @@ __global__ void k_reset(Batch b) {
   b.iters[rhs] = 0;
   b.cycles[rhs] = 0;
   b.scale[rhs] = 1.0;
+  b.next[rhs] = 1.0;
+  b.theta[rhs] = 0.0;
 }
 
 Geo make_geo(const hydot_ctx* ctx) {
@@ -843,6 +868,12 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
   b.iters = ctx->d_iters;
   b.cycles = ctx->d_cycles;
   b.scale = ctx->d_scale;
+  b.next = ctx->d_next;
+  b.rr0 = ctx->d_rr0;
+  b.theta = ctx->d_theta;
+  b.cw_floor = ctx->cw_floor;
+  b.n_src = ctx->n_src;
+  b.n_det = ctx->n_det;
   b.fin = ctx->d_final;
   b.part = ctx->d_part;
   b.counter = ctx->d_counter;
@@ -871,17 +902,19 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
 
   volatile int* hp = ctx->h_pinned;
   for (int cycle = 0; cycle <= MAX_CYCLES; ++cycle) {
-    k_residual<X><<<nblk, blk, 0, s>>>(g, b, x64);
+    if (b.cw_floor > 0.0) {
+      k_theta<X><<<(b.nrhs + 255) / 256, 256, 0, s>>>(g, b, x64, ctx->d_optode);
+      ++ctx->launches;
+    }
+    k_residual<T, X><<<nblk, blk, 0, s>>>(g, b, x64, R);
     ++ctx->launches;
     HYDOT_CUDA_TRY(ctx, cudaMemsetAsync(b.counter, 0, sizeof(int) * (size_t)ctx->counter_len, s));
     k_decide<<<(b.nrhs + 255) / 256, 256, 0, s>>>(g, b);
     ++ctx->launches;
+    HYDOT_CUDA_TRY(ctx, cudaGetLastError());
     HYDOT_CUDA_TRY(ctx, cudaMemcpyAsync((void*)&hp[0], b.counter, sizeof(int), cudaMemcpyDeviceToHost, s));
     HYDOT_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     if (hp[0] == 0) break;
-    k_init<T, X><<<nblk, blk, 0, s>>>(g, b, x64, R);
-    ++ctx->launches;
-    HYDOT_CUDA_TRY(ctx, cudaGetLastError());
     // inner iterations in groups; the group after the one being polled is already queued
     int it = 0;
     int pending = -1;  // index of the iteration whose counter is in flight
@@ -1039,6 +1072,9 @@ int solver_alloc(hydot_ctx* ctx) {
   HYDOT_CUDA_TRY(ctx, cudaMalloc(&ctx->d_iters, sizeof(int) * F));
   HYDOT_CUDA_TRY(ctx, cudaMalloc(&ctx->d_cycles, sizeof(int) * F));
   HYDOT_CUDA_TRY(ctx, cudaMalloc(&ctx->d_scale, sizeof(double) * F));
+  HYDOT_CUDA_TRY(ctx, cudaMalloc(&ctx->d_next, sizeof(double) * F));
+  HYDOT_CUDA_TRY(ctx, cudaMalloc(&ctx->d_rr0, sizeof(double) * F));
+  HYDOT_CUDA_TRY(ctx, cudaMalloc(&ctx->d_theta, sizeof(double) * F));
   HYDOT_CUDA_TRY(ctx, cudaMalloc(&ctx->d_final, sizeof(double) * 2 * F));
   ctx->counter_len = MAX_INNER_PER_CYCLE + 8;
   HYDOT_CUDA_TRY(ctx, cudaMalloc(&ctx->d_counter, sizeof(int) * ctx->counter_len));
@@ -1067,6 +1103,9 @@ void solver_free(hydot_ctx* ctx) {
   cudaFree(ctx->d_iters);
   cudaFree(ctx->d_cycles);
   cudaFree(ctx->d_scale);
+  cudaFree(ctx->d_next);
+  cudaFree(ctx->d_rr0);
+  cudaFree(ctx->d_theta);
   cudaFree(ctx->d_final);
   cudaFree(ctx->d_counter);
   cudaFree(ctx->d_err);

@@ -56,6 +56,7 @@ int main(void) {
   O(hydot_problem, omega); O(hydot_problem, c_medium); O(hydot_problem, n_src); O(hydot_problem, src_ijk);
   O(hydot_problem, precision); O(hydot_problem, tol); O(hydot_problem, tol_cw); O(hydot_problem, inner_tol);
   O(hydot_problem, max_iter); O(hydot_problem, deflation_k); O(hydot_problem, max_lambda_per_call);
+  O(hydot_problem, cw_floor);
   return 0;
 }''')
     exe = tmp_path / "layout"
@@ -106,6 +107,7 @@ def _problem(**over):
     ({"precision": 7}, "precision"),
     ({"deflation_k": 33}, "deflation_k"),
     ({"max_lambda_per_call": 4}, "max_lambda_per_call"),
+    ({"cw_floor": -1.0}, "cw_floor"),
 ])
 def test_setup_rejects_bad_arguments_without_a_device(lib, over, needle):
     p, keep = _problem(**over)

@@ -82,6 +82,21 @@ def test_fields_mixed_and_born_rows(hd, oracle_fields, name):
     assert st["cycles_max"] >= 2 and st["cw_max"] <= 1e-8
 
 
+@pytest.mark.parametrize("name", ["transmission-ragged-37x19x21", "tma-ragged-36x19x21", "reflection-13x11x9"])
+def test_born_aware_floor(hd, oracle_fields, name):
+    """cw_floor = 1e-6 / tol_cw: cells far from every optode stop driving refinement, yet every Born
+    entry stays within 1e-5 of its row maximum and the fields within 1e-6 (norm-wise)."""
+    p, (rs, rd) = oracle_fields[name]
+    cyc = []
+    for floor in (0.0, 100.0):
+        with hd.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=1e-8, cw_floor=floor) as ctx:
+            ps, pd, st = ctx.solve_fields(0, p.n_lambda)
+        assert rel_err(ps, rs) <= 1e-6 and rel_err(pd, rd) <= 1e-6
+        assert born_rowmax_err(p, ps, pd, rs, rd) <= 1e-5
+        cyc.append(st["cycles_max"])
+    assert cyc[1] <= cyc[0]
+
+
 def test_tma_and_generic_kernels_agree(hd, oracle_fields, monkeypatch):
     """The TMA tile kernels and the generic kernels solve the same systems to the same tolerance."""
     p, (rs, rd) = oracle_fields["tma-ragged-36x19x21"]
