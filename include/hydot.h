@@ -145,6 +145,27 @@ int hydot_born_apply(hydot_ctx* ctx, const void* phi_src, const void* phi_det, i
 int hydot_born_apply_T(hydot_ctx* ctx, const void* phi_src, const void* phi_det, int lam0, int nlam,
                        const void* y, void* g);
 
+/* y = J x for one wavelength slice in FP32 without allocating device memory and without a
+ * context. The paper has no counterpart: this exists for callers that cannot allocate device
+ * memory themselves (code running where cudaMalloc is not allowed, or whose allocator is owned
+ * by someone else). The computation is hydot_born_apply's; its per-block partial sums and the
+ * slice's extinction coefficients are kept in a 16 MiB file-scope device array that every GPU
+ * holds from the library's load until the process exits.
+ *   N, n_src, n_det, n_chrom, nlam: sizes (>= 1, n_chrom <= 16); h_mm: cell side.
+ *   eps: HOST [nlam][n_chrom] extinction coefficients of the slice's wavelengths.
+ *   phi_src [nlam][n_src][N], phi_det [nlam][n_det][N], x [n_chrom*N], y [n_src*n_det*nlam]:
+ *   DEVICE float arrays owned by the caller, layouts as for hydot_born_apply.
+ *   stream: a cudaStream_t (NULL = legacy default stream); the call is asynchronous on it.
+ * Limits: nlam*n_chrom <= 8192 and nlam*ceil(n_src/32)*ceil(n_det/32)*ceil(N/1024) <= 4096
+ * (16 MiB of partial sums); larger sizes return HYDOT_ERR_ARG with a message from
+ * hydot_last_error(NULL). The first call on a device, with that device current, looks up the
+ * array's device address (cudaGetSymbolAddress) once; make that first call before any stream
+ * capture. All calls share the array, which keeps the last call's contents (nothing in it needs
+ * to start at zero): calls that overlap on the GPU, on any streams of one device, race. */
+int hydot_born_apply_noalloc(long long N, int n_src, int n_det, int n_chrom, int nlam, double h_mm,
+                             const double* eps, const float* phi_src, const float* phi_det, const float* x,
+                             float* y, void* stream);
+
 /* Number of kernels this context has launched since hydot_setup (instrumentation: lets a
  * caller count the library's launches inside a timed region). */
 long long hydot_kernel_launches(const hydot_ctx* ctx);

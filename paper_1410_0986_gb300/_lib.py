@@ -22,7 +22,8 @@ HYDOT_MIXED = 1
 
 # Every symbol include/hydot.h declares.
 EXPORTS = ("hydot_version", "hydot_setup", "hydot_set_stream", "hydot_solve_fields", "hydot_born_assemble",
-           "hydot_born_apply", "hydot_born_apply_T", "hydot_kernel_launches", "hydot_last_error", "hydot_destroy")
+           "hydot_born_apply", "hydot_born_apply_T", "hydot_born_apply_noalloc", "hydot_kernel_launches",
+           "hydot_last_error", "hydot_destroy")
 
 
 class Problem(C.Structure):
@@ -78,6 +79,9 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.hydot_born_apply.restype = C.c_int
     lib.hydot_born_apply_T.argtypes = [vp, vp, vp, C.c_int, C.c_int, vp, vp]
     lib.hydot_born_apply_T.restype = C.c_int
+    lib.hydot_born_apply_noalloc.argtypes = [C.c_longlong, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
+                                             C.POINTER(C.c_double), vp, vp, vp, vp, vp]
+    lib.hydot_born_apply_noalloc.restype = C.c_int
     lib.hydot_kernel_launches.argtypes = [vp]
     lib.hydot_kernel_launches.restype = C.c_longlong
     lib.hydot_last_error.argtypes = [vp]

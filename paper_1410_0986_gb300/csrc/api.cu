@@ -86,6 +86,11 @@ void free_all(hydot_ctx* c) {
 
 }  // namespace
 
+namespace hydot {
+// Message of a failed call that has no context (reported by hydot_last_error(NULL)).
+void set_context_free_error(const std::string& msg) { g_setup_error = msg; }
+}  // namespace hydot
+
 extern "C" {
 
 int hydot_version(void) { return 10000; }

@@ -203,6 +203,9 @@ int solver_alloc(hydot_ctx* ctx);
 void solver_free(hydot_ctx* ctx);
 int build_deflation(hydot_ctx* ctx);
 
+// api.cu
+void set_context_free_error(const std::string& msg);
+
 // born.cu
 int born_assemble_impl(hydot_ctx* ctx, const void* phi_src, const void* phi_det, int lam0, int nlam,
                        long long row0, long long nrows, void* J, long long ldJ);
