@@ -44,6 +44,18 @@ TOL_CW = 1e-8
 CW_FLOOR = 100.0
 WORKLOAD = ("cw-mixed-64x64x48: 64x64x48 grid (h=2 mm), 32 sources + 32 detectors, 128 wavelengths "
             "(8,192 field solves), explicit FP32 Born rows 131,072 x 786,432 in row chunks, J x and J^T r")
+KERNEL_NAMES = {"dir": "k_dir_tma (inner PCG pass 1)", "update": "k_update_tma (inner PCG pass 2)",
+                "residual": "k_residual (FP64 residual)", "born_rows": "k_born_rows (Born-row assembly)",
+                "apply": "k_apply_partial+reduce (J x)", "apply_T": "k_apply_T_partial+reduce (J^T y)"}
+# DRAM bytes (read + write, ncu) per algorithmic byte, from the captures summarised under profiles/
+# (smaller cases of the same kernels, scaled by the units processed: active fields or rows)
+DRAM_PER_ALGORITHMIC_BYTE = {"dir": (100.96e6 + 24.81e6) / (64 * 3 * 196608 * 4),
+                             "update": (151.25e6 + 43.85e6) / (64 * 5 * 196608 * 4),
+                             "born_rows": (893.83e6 + 12.96e9) / (4096 * 4 * 196608 * 4)}
+TRAFFIC_NOTE = {"dir": "ncu on 64 fields of one wavelength (profiles/solver_tma_64fields.md), scaled by active fields; "
+                       "writes partly still in L2 at kernel end",
+                "update": "ncu on 64 fields of one wavelength (profiles/solver_tma_64fields.md), scaled by active fields",
+                "born_rows": "ncu on a full 4,096-row launch of the benchmark (profiles/k_born_rows_4096rows.md)"}
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
 
 
@@ -238,7 +250,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier(world)
     torch.cuda.synchronize()
-    launches0 = ctx.lib.hydot_kernel_launches(ctx._ctx)
+    launches0 = ctx.kernel_launches()
+    ctx.set_kernel_timing(True)
     clocks = ClockSampler(local)
     clocks.start()
     t0 = ev()
@@ -249,7 +262,9 @@ def run_ours(args):
     clk = clocks.stop()
     barrier(world)
     torch.cuda.synchronize()
-    n_launch = ctx.lib.hydot_kernel_launches(ctx._ctx) - launches0
+    n_launch = ctx.kernel_launches() - launches0
+    kstats = ctx.kernel_stats()
+    ctx.set_kernel_timing(False)
     ms = t0.elapsed_time(t1)
     ms = max_over_ranks(ms, world)
     for (e0, e1, e2, e3, e4, launches) in phase["_ev"]:
@@ -262,10 +277,14 @@ def run_ours(args):
     solves = K * (ns + nd) * CHUNK * world
     value = solves / (ms / 1e3)
     pk = peaks()
-    # dominant kernel: Born-row assembly; algorithmic bytes = the rows written (N * n_chrom * 4 B each)
-    t_launch = statistics.mean(phase["assemble_launch"]) / 1e3
-    bytes_launch = ROWS_PER_LAUNCH * nc * N * 4
+    # dominant kernel = the one with the most device time in the timed region (CUDA events on the
+    # library's stream); achieved = its algorithmic bytes per launch / its mean launch time
+    dom = max(kstats, key=lambda k: kstats[k]["ms"])
+    kd = kstats[dom]
+    t_launch = kd["ms"] / kd["launches"] / 1e3
+    bytes_launch = kd["bytes"] / kd["launches"]
     achieved = bytes_launch / t_launch / 1e9
+    dram_ratio = DRAM_PER_ALGORITHMIC_BYTE.get(dom)
     # solver roofline: 6 N w per RHS-iteration (x, r, p read and written once; FP32)
     iters = sum(s["iters_mean"] * s["n_fields"] for s in stats)
     t_solve = sum(phase["solve"]) / 1e3
@@ -279,10 +298,19 @@ def run_ours(args):
                    "chunk_lambda": CHUNK, "tol_cw": TOL_CW, "cw_floor": CW_FLOOR, "tol": 1e-10, "deflation_k": args.deflation_k,
                    "l2": "inputs larger than L2 (805 MB of fields per chunk, 12.9 GB per Born launch)",
                    "parallelism": f"lambda-chunks over {world} GPU(s), no data exchange"},
-        "roofline": {"kernel": "k_born_rows (Born-row assembly)", "bound": "hbm", "achieved": achieved,
+        "roofline": {"kernel": KERNEL_NAMES[dom], "bound": "hbm", "achieved": achieved,
                      "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
-                     "peak_source": pk["source"], "traffic": None,
-                     "algorithmic_bytes_per_launch": bytes_launch, "launch_ms": t_launch * 1e3},
+                     "peak_source": pk["source"],
+                     "traffic": None if dram_ratio is None else dram_ratio * bytes_launch,
+                     "traffic_note": TRAFFIC_NOTE.get(dom),
+                     "algorithmic_bytes_per_launch": bytes_launch, "launch_ms": t_launch * 1e3,
+                     "launches": kd["launches"]},
+        "kernels": {KERNEL_NAMES[k]: {"ms": v["ms"], "launches": v["launches"],
+                                      "share": v["ms"] / max(1e-9, sum(w["ms"] for w in kstats.values())),
+                                      "gbs": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 else None,
+                                      "hbm_frac": ((v["bytes"] / (v["ms"] / 1e3) / 1e9) / pk["hbm_gbs"])
+                                      if v["ms"] > 0 else None}
+                    for k, v in kstats.items()},
         "rates": {
             "born_rows_per_s": K * Mc * world / (sum(phase["assemble"]) / 1e3),
             "grads_per_s": (K / nchunk) / (sum(phase["apply_T"]) / 1e3),

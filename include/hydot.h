@@ -166,6 +166,29 @@ int hydot_born_apply_noalloc(long long N, int n_src, int n_det, int n_chrom, int
                              const double* eps, const float* phi_src, const float* phi_det, const float* x,
                              float* y, void* stream);
 
+/* Kernels whose time the instrumentation below accumulates. */
+typedef enum {
+  HYDOT_KERNEL_DIR = 0,        /* inner PCG pass 1: p = D^-1 r + beta p, gamma = p^T A p */
+  HYDOT_KERNEL_UPDATE = 1,     /* inner PCG pass 2: x += alpha p, r -= alpha A p, rho */
+  HYDOT_KERNEL_RESIDUAL = 2,   /* FP64 residual and refinement test, once per cycle */
+  HYDOT_KERNEL_BORN_ROWS = 3,  /* Born-row assembly */
+  HYDOT_KERNEL_APPLY = 4,      /* J x (partial sums) */
+  HYDOT_KERNEL_APPLY_T = 5,    /* J^T y (partial sums) */
+  HYDOT_KERNEL_COUNT = 6
+} hydot_kernel;
+
+/* Instrumentation: on != 0 makes later calls record CUDA events around each launch of the
+ * kernels above (on the context's stream) and count the algorithmic bytes each launch moves
+ * (the bytes the operation must read and write once: 12 B per cell and active field for
+ * HYDOT_KERNEL_DIR, 20 B for HYDOT_KERNEL_UPDATE in FP32, 12 B for HYDOT_KERNEL_RESIDUAL, the rows
+ * written for HYDOT_KERNEL_BORN_ROWS, the fields read for the products). Resets the totals. */
+int hydot_set_kernel_timing(hydot_ctx* ctx, int on);
+
+/* Totals since the last hydot_set_kernel_timing: summed device time in ms, launches, and
+ * algorithmic bytes of `kernel` (a hydot_kernel). Synchronises the context's stream. Any output
+ * pointer may be NULL. */
+int hydot_kernel_stats(hydot_ctx* ctx, int kernel, double* ms, long long* launches, double* bytes);
+
 /* Number of kernels this context has launched since hydot_setup (instrumentation: lets a
  * caller count the library's launches inside a timed region). */
 long long hydot_kernel_launches(const hydot_ctx* ctx);

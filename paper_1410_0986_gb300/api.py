@@ -165,6 +165,23 @@ class Context:
         self._check(rc)
         return g
 
+    # ------------------------------------------------------------------ instrumentation
+    def set_kernel_timing(self, on: bool = True):
+        """Record CUDA events around the hot kernels from now on (resets the totals)."""
+        self._check(self.lib.hydot_set_kernel_timing(self._ctx, 1 if on else 0))
+
+    def kernel_stats(self) -> dict:
+        """{kernel: {"ms", "launches", "bytes"}} since set_kernel_timing (synchronises)."""
+        out = {}
+        for name, kid in _lib.KERNELS.items():
+            ms, n, by = C.c_double(), C.c_longlong(), C.c_double()
+            self._check(self.lib.hydot_kernel_stats(self._ctx, kid, C.byref(ms), C.byref(n), C.byref(by)))
+            out[name] = {"ms": ms.value, "launches": n.value, "bytes": by.value}
+        return out
+
+    def kernel_launches(self) -> int:
+        return int(self.lib.hydot_kernel_launches(self._ctx))
+
     def close(self):
         if getattr(self, "_ctx", None):
             self.lib.hydot_destroy(self._ctx)

@@ -74,6 +74,9 @@ int validate(const hydot_problem* p, std::string& msg) {
 }
 
 void free_all(hydot_ctx* c) {
+  cudaStreamSynchronize(c->stream);
+  for (cudaEvent_t e : c->timer.pool) cudaEventDestroy(e);
+  c->timer.pool.clear();
   hydot::solver_free(c);
   cudaFree(c->d_coef);
   cudaFree(c->d_coef_f);
@@ -89,6 +92,42 @@ void free_all(hydot_ctx* c) {
 namespace hydot {
 // Message of a failed call that has no context (reported by hydot_last_error(NULL)).
 void set_context_free_error(const std::string& msg) { g_setup_error = msg; }
+
+cudaEvent_t timer_begin(hydot_ctx* ctx) {
+  KernelTimer& t = ctx->timer;
+  if (!t.on) return nullptr;
+  if (t.used + 2 > t.pool.size()) {
+    for (int q = 0; q < 64; ++q) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+      t.pool.push_back(e);
+    }
+  }
+  cudaEvent_t a = t.pool[t.used++];
+  cudaEventRecord(a, ctx->stream);
+  return a;
+}
+
+void timer_end(hydot_ctx* ctx, cudaEvent_t a, int kind, double bytes) {
+  KernelTimer& t = ctx->timer;
+  if (!t.on || !a) return;
+  cudaEvent_t b = t.pool[t.used++];
+  cudaEventRecord(b, ctx->stream);
+  t.pending.push_back({a, b, kind});
+  t.n[kind] += 1;
+  t.bytes[kind] += bytes;
+}
+
+void timer_flush(hydot_ctx* ctx) {
+  KernelTimer& t = ctx->timer;
+  for (const auto& p : t.pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess)
+      t.ms[p.kind] += ms;
+  }
+  t.pending.clear();
+  t.used = 0;
+}
 }  // namespace hydot
 
 extern "C" {
@@ -221,6 +260,32 @@ int hydot_born_apply_T(hydot_ctx* ctx, const void* phi_src, const void* phi_det,
 }
 
 long long hydot_kernel_launches(const hydot_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int hydot_set_kernel_timing(hydot_ctx* ctx, int on) {
+  if (!ctx) return HYDOT_ERR_ARG;
+  cudaStreamSynchronize(ctx->stream);
+  hydot::timer_flush(ctx);
+  hydot::KernelTimer& t = ctx->timer;
+  t.on = on != 0;
+  for (int k = 0; k < HYDOT_KERNEL_COUNT; ++k) {
+    t.ms[k] = 0.0;
+    t.n[k] = 0;
+    t.bytes[k] = 0.0;
+  }
+  return HYDOT_OK;
+}
+
+int hydot_kernel_stats(hydot_ctx* ctx, int kernel, double* ms, long long* launches, double* bytes) {
+  if (!ctx) return HYDOT_ERR_ARG;
+  if (kernel < 0 || kernel >= HYDOT_KERNEL_COUNT) return fail(ctx, HYDOT_ERR_ARG, "unknown kernel id");
+  HYDOT_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  hydot::timer_flush(ctx);
+  const hydot::KernelTimer& t = ctx->timer;
+  if (ms) *ms = t.ms[kernel];
+  if (launches) *launches = t.n[kernel];
+  if (bytes) *bytes = t.bytes[kernel];
+  return HYDOT_OK;
+}
 
 const char* hydot_last_error(const hydot_ctx* ctx) { return ctx ? ctx->err.c_str() : g_setup_error.c_str(); }
 

@@ -290,6 +290,7 @@ int assemble_t(hydot_ctx* ctx, const E* ps, const E* pd, int lam0, int nlam, lon
   unsigned gx = (unsigned)std::max<long long>(1, std::min<long long>((per_row + 1023) / 1024, 1024));
   unsigned gy = (unsigned)std::min<long long>(total_rows, 65535);
   dim3 grid(gx, gy);
+  cudaEvent_t t0 = timer_begin(ctx);
   if (aligned)
     k_born_rows<E, VEC><<<grid, 256, 0, ctx->stream>>>(ps, pd, ctx->d_eps, lam0, nlam, ns, nd, nc, N, h3, row0, nrows,
                                                        sd_lo, n_sd, J, ldJ);
@@ -297,6 +298,7 @@ int assemble_t(hydot_ctx* ctx, const E* ps, const E* pd, int lam0, int nlam, lon
     k_born_rows_scalar<E><<<grid, 256, 0, ctx->stream>>>(ps, pd, ctx->d_eps, lam0, nlam, ns, nd, nc, N, h3, row0,
                                                          nrows, sd_lo, n_sd, J, ldJ);
   ++ctx->launches;
+  timer_end(ctx, t0, HYDOT_KERNEL_BORN_ROWS, (double)nrows * nc * (double)N * sizeof(E));
   HYDOT_CUDA_TRY(ctx, cudaGetLastError());
   return HYDOT_OK;
 }
@@ -329,6 +331,7 @@ int apply_t(hydot_ctx* ctx, const E* ps, const E* pd, int lam0, int nlam, const 
   dim3 grid(nxb, nlam, nts * ntd);
   const size_t smem = apply_smem_bytes<E>();
   HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(k_apply_partial<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  cudaEvent_t t0 = timer_begin(ctx);
   k_apply_partial<E><<<grid, 256, smem, ctx->stream>>>(ps, pd, x, ctx->d_eps, lam0, ns, nd, nc, N, nxb, part);
   ++ctx->launches;
   HYDOT_CUDA_TRY(ctx, cudaGetLastError());
@@ -336,6 +339,7 @@ int apply_t(hydot_ctx* ctx, const E* ps, const E* pd, int lam0, int nlam, const 
   k_apply_reduce<E><<<(unsigned)std::min<long long>((M + 255) / 256, 4096), 256, 0, ctx->stream>>>(
       part, nlam, ns, nd, nts, ntd, nxb, ctx->h * ctx->h * ctx->h, y);
   ++ctx->launches;
+  timer_end(ctx, t0, HYDOT_KERNEL_APPLY, ((double)nlam * (ns + nd) + nc) * (double)N * sizeof(E));
   HYDOT_CUDA_TRY(ctx, cudaGetLastError());
   return HYDOT_OK;
 }
@@ -359,6 +363,7 @@ int apply_T_t(hydot_ctx* ctx, const E* ps, const E* pd, int lam0, int nlam, cons
     HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(k_apply_T_partial<E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem));
   }
+  cudaEvent_t t0 = timer_begin(ctx);
   k_apply_T_partial<E><<<grid, 256, smem, ctx->stream>>>(ps, pd, y, ctx->d_eps, lam0, nlam, ns, nd, nc, N, lpg, part);
   ++ctx->launches;
   HYDOT_CUDA_TRY(ctx, cudaGetLastError());
@@ -366,6 +371,7 @@ int apply_T_t(hydot_ctx* ctx, const E* ps, const E* pd, int lam0, int nlam, cons
   k_apply_T_reduce<E><<<(unsigned)std::min<long long>((tot + 255) / 256, 8192), 256, 0, ctx->stream>>>(
       part, ngrp, nc, N, ctx->h * ctx->h * ctx->h, g);
   ++ctx->launches;
+  timer_end(ctx, t0, HYDOT_KERNEL_APPLY_T, ((double)nlam * (ns + nd) + 2.0 * nc) * (double)N * sizeof(E));
   HYDOT_CUDA_TRY(ctx, cudaGetLastError());
   return HYDOT_OK;
 }

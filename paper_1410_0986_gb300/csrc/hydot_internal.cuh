@@ -115,6 +115,21 @@ struct Tiling {
   int ntiles;         // tiles per field
 };
 
+// Event-based per-kernel timing (instrumentation, off by default).
+struct KernelTimer {
+  struct Pend {
+    cudaEvent_t a, b;
+    int kind;
+  };
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  std::vector<Pend> pending;
+  double ms[HYDOT_KERNEL_COUNT] = {0};
+  long long n[HYDOT_KERNEL_COUNT] = {0};
+  double bytes[HYDOT_KERNEL_COUNT] = {0};
+};
+
 }  // namespace hydot
 
 // ----------------------------------------------------------------------------- context
@@ -175,6 +190,7 @@ struct hydot_ctx {
   double* d_Ginv = nullptr;                    // [n_lambda][k][k] inverse of W^T Ahat_j W
 
   long long launches = 0;  // kernels enqueued by this context
+  hydot::KernelTimer timer;
 
   // Born apply workspace
   void* d_apply_ws = nullptr;
@@ -205,6 +221,12 @@ int build_deflation(hydot_ctx* ctx);
 
 // api.cu
 void set_context_free_error(const std::string& msg);
+
+// Instrumentation helpers (api.cu): a timed launch is bracketed by timer_begin/timer_end;
+// timer_flush reads the completed events (call after the stream was synchronised).
+cudaEvent_t timer_begin(hydot_ctx* ctx);
+void timer_end(hydot_ctx* ctx, cudaEvent_t a, int kind, double bytes);
+void timer_flush(hydot_ctx* ctx);
 
 // born.cu
 int born_assemble_impl(hydot_ctx* ctx, const void* phi_src, const void* phi_det, int lam0, int nlam,

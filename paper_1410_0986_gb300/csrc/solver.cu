@@ -901,13 +901,17 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
   HYDOT_CUDA_TRY(ctx, cudaGetLastError());
 
   volatile int* hp = ctx->h_pinned;
+  int prev_active = b.nrhs;
   for (int cycle = 0; cycle <= MAX_CYCLES; ++cycle) {
     if (b.cw_floor > 0.0) {
       k_theta<X><<<(b.nrhs + 255) / 256, 256, 0, s>>>(g, b, x64, ctx->d_optode);
       ++ctx->launches;
     }
+    cudaEvent_t t_res = timer_begin(ctx);
     k_residual<T, X><<<nblk, blk, 0, s>>>(g, b, x64, R);
     ++ctx->launches;
+    timer_end(ctx, t_res, HYDOT_KERNEL_RESIDUAL,
+              (double)(cycle == 0 ? b.nrhs : prev_active) * (double)g.N * (double)(sizeof(X) + sizeof(T)));
     HYDOT_CUDA_TRY(ctx, cudaMemsetAsync(b.counter, 0, sizeof(int) * (size_t)ctx->counter_len, s));
     k_decide<<<(b.nrhs + 255) / 256, 256, 0, s>>>(g, b);
     ++ctx->launches;
@@ -915,6 +919,7 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
     HYDOT_CUDA_TRY(ctx, cudaMemcpyAsync((void*)&hp[0], b.counter, sizeof(int), cudaMemcpyDeviceToHost, s));
     HYDOT_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     if (hp[0] == 0) break;
+    prev_active = hp[0];
     // inner iterations in groups; the group after the one being polled is already queued
     int it = 0;
     int pending = -1;  // index of the iteration whose counter is in flight
@@ -929,18 +934,26 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
         if constexpr (std::is_same<T, float>::value) {
           if (ctx->use_tma) {
             const unsigned ncb = (unsigned)((long long)b.nrhs * g.ntx * g.nty);
+            cudaEvent_t t0 = timer_begin(ctx);
             k_dir_tma<<<ncb, blk, tma_smem(4), s>>>(g, b, it, ctx->d_coef_f, ctx->tm_r, ctx->tm_p[it & 1],
                                                     P[(it + 1) & 1]);
             ++ctx->launches;
+            timer_end(ctx, t0, HYDOT_KERNEL_DIR, 0.0);
+            t0 = timer_begin(ctx);
             k_update_tma<<<ncb, blk, tma_smem(2), s>>>(g, b, it, ctx->d_coef_f, E, R, ctx->tm_p[(it + 1) & 1]);
             ++ctx->launches;
+            timer_end(ctx, t0, HYDOT_KERNEL_UPDATE, 0.0);
             continue;
           }
         }
+        cudaEvent_t t0 = timer_begin(ctx);
         k_dir<T><<<nblk, blk, 0, s>>>(g, b, it, R, P[it & 1], P[(it + 1) & 1]);
         ++ctx->launches;
+        timer_end(ctx, t0, HYDOT_KERNEL_DIR, 0.0);
+        t0 = timer_begin(ctx);
         k_update<T><<<nblk, blk, 0, s>>>(g, b, it, E, R, P[(it + 1) & 1]);
         ++ctx->launches;
+        timer_end(ctx, t0, HYDOT_KERNEL_UPDATE, 0.0);
       }
       HYDOT_CUDA_TRY(ctx, cudaGetLastError());
       HYDOT_CUDA_TRY(ctx, cudaMemcpyAsync((void*)&hp[1 + slot], b.counter + 1 + (it - 1), sizeof(int),
@@ -957,6 +970,18 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
     HYDOT_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     cudaEventDestroy(ev[0]);
     cudaEventDestroy(ev[1]);
+    if (ctx->timer.on) {
+      // algorithmic bytes of the inner passes: fields active at each iteration (the counters
+      // k_dir increments) x 12 B (pass 1) or 20 B (pass 2) per cell in the inner precision
+      std::vector<int> cnt(it);
+      if (it > 0)
+        HYDOT_CUDA_TRY(ctx, cudaMemcpy(cnt.data(), b.counter + 1, sizeof(int) * it, cudaMemcpyDeviceToHost));
+      double active = 0.0;
+      for (int q = 0; q < it; ++q) active += cnt[q];
+      ctx->timer.bytes[HYDOT_KERNEL_DIR] += active * 3.0 * (double)g.N * sizeof(T);
+      ctx->timer.bytes[HYDOT_KERNEL_UPDATE] += active * 5.0 * (double)g.N * sizeof(T);
+      timer_flush(ctx);
+    }
     // any field still marked INNER hit the per-cycle cap: finish it
     {
       dim3 fg((unsigned)std::min<long long>((g.N + 255) / 256, 1024), (unsigned)std::min(b.nrhs, 65535));
