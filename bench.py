@@ -356,11 +356,37 @@ def run_ours(args):
     # the plain FP64 GPU solve against the mixed form, both to a field error of 1e-6 (norm-wise)
     if args.compare_fp64 and rank == 0:
         out["fp64_vs_mixed_at_1e-6"] = compare_fp64(hd, p)
+        out["deflation"] = compare_deflation(hd, p)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_entry(run_cpu_sample(0))
     ctx.close()
     if rank == 0:
         print(json.dumps(out))
+
+
+def compare_deflation(hd, p, k=16):
+    """Krylov iterations and time of one 16-wavelength chunk without and with the recycled
+    deflation subspace (the analogue of the paper's timing table over k)."""
+    import torch
+
+    res = {}
+    for kk in (0, k):
+        t0 = time.perf_counter()
+        with hd.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=TOL_CW, cw_floor=CW_FLOOR,
+                                     max_lambda_per_call=CHUNK, deflation_k=kk) as c:
+            setup = time.perf_counter() - t0
+            c.solve_fields(0, CHUNK)
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            _, _, st = c.solve_fields(CHUNK, CHUNK)
+            b.record()
+            torch.cuda.synchronize()
+            res[f"k={kk}"] = {"solves_per_s": (p.n_src + p.n_det) * CHUNK / (a.elapsed_time(b) / 1e3),
+                              "iters_mean": st["iters_mean"], "iters_max": st["iters_max"],
+                              "cycles_max": st["cycles_max"], "setup_s": setup}
+    return res
 
 
 def compare_fp64(hd, p):

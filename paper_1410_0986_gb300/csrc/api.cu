@@ -84,6 +84,7 @@ void free_all(hydot_ctx* c) {
   cudaFree(c->d_optode);
   cudaFree(c->d_W);
   cudaFree(c->d_Ginv);
+  cudaFree(c->d_defl_coef);
   cudaFree(c->d_apply_ws);
 }
 
@@ -178,6 +179,11 @@ int hydot_setup(const hydot_problem* p, void* stream, hydot_ctx** out) {
   c->max_iter = p->max_iter > 0 ? p->max_iter : 20000;
   c->deflation_k = p->deflation_k;
   c->cw_floor = p->omega == 0.0 ? p->cw_floor : 0.0;
+  if (p->deflation_k > 0 && p->omega != 0.0) {
+    g_setup_error = "deflation is available for continuous-wave (real) fields only";
+    delete c;
+    return HYDOT_ERR_ARG;
+  }
   c->max_fields = (p->max_lambda_per_call > 0 ? p->max_lambda_per_call : p->n_lambda) * (p->n_src + p->n_det);
   c->stream = (cudaStream_t)stream;
   compute_coefficients(c);

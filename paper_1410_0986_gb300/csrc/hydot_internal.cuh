@@ -188,6 +188,8 @@ struct hydot_ctx {
   double* d_W = nullptr;
   std::vector<double> gram_L, gram_I, gram_B;  // W^T Lg W, W^T W, W^T B_f W (6 blocks)
   double* d_Ginv = nullptr;                    // [n_lambda][k][k] inverse of W^T Ahat_j W
+  double* d_defl_coef = nullptr;               // [max_fields][k] G_j^-1 W^T b per field
+  std::vector<double> deflation_ritz;          // Ritz values of the base operator (ascending)
 
   long long launches = 0;  // kernels enqueued by this context
   hydot::KernelTimer timer;
@@ -217,7 +219,10 @@ inline int fail(hydot_ctx* ctx, int code, const std::string& msg) {
 int solve_fields_impl(hydot_ctx* ctx, int lam0, int nlam, void* phi_src, void* phi_det, hydot_stats* st);
 int solver_alloc(hydot_ctx* ctx);
 void solver_free(hydot_ctx* ctx);
+
+// deflation.cu
 int build_deflation(hydot_ctx* ctx);
+int deflate_initial_guess(hydot_ctx* ctx, int lam0, int f_begin, int nf, int nrhs, double* x64);
 
 // api.cu
 void set_context_free_error(const std::string& msg);

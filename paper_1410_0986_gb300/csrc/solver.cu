@@ -894,7 +894,17 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
   const unsigned nblk = (unsigned)((long long)b.nrhs * g.ntiles);
   const dim3 blk(NTHREADS);
 
-  HYDOT_CUDA_TRY(ctx, cudaMemsetAsync(x64, 0, sizeof(X) * (size_t)b.nrhs * g.N, s));
+  if constexpr (std::is_same<X, double>::value) {
+    if (ctx->deflation_k > 0) {
+      // Galerkin initial guess from the recycled subspace (shared by all wavelengths)
+      int rc = deflate_initial_guess(ctx, lam0, b.f_begin, b.nf, b.nrhs, x64);
+      if (rc) return rc;
+    } else {
+      HYDOT_CUDA_TRY(ctx, cudaMemsetAsync(x64, 0, sizeof(X) * (size_t)b.nrhs * g.N, s));
+    }
+  } else {
+    HYDOT_CUDA_TRY(ctx, cudaMemsetAsync(x64, 0, sizeof(X) * (size_t)b.nrhs * g.N, s));
+  }
   HYDOT_CUDA_TRY(ctx, cudaMemsetAsync(b.err, 0, sizeof(int), s));
   k_reset<<<(b.nrhs + 255) / 256, 256, 0, s>>>(b);
   ++ctx->launches;
@@ -1149,9 +1159,5 @@ int solve_fields_impl(hydot_ctx* ctx, int lam0, int nlam, void* phi_src, void* p
   return run_solve<cd, cd, cd>(ctx, lam0, nlam, (cd*)phi_src, (cd*)phi_det, st);
 }
 
-int build_deflation(hydot_ctx* ctx) {
-  if (ctx->deflation_k == 0) return HYDOT_OK;
-  return fail(ctx, HYDOT_ERR_STATE, "deflation basis not available in this build");
-}
 
 }  // namespace hydot

@@ -97,6 +97,21 @@ def test_born_aware_floor(hd, oracle_fields, name):
     assert cyc[1] <= cyc[0]
 
 
+@pytest.mark.parametrize("name,precision", [("tma-ragged-36x19x21", "mixed"), ("transmission-ragged-37x19x21", "mixed"),
+                                            ("reflection-13x11x9", "fp64")])
+def test_recycled_deflation(hd, oracle_fields, name, precision):
+    """Fields from the deflated start (W from Lanczos on the mean-shift operator, per-wavelength
+    Galerkin matrices from shift-independent k x k blocks) meet the same tolerances."""
+    p, (rs, rd) = oracle_fields[name]
+    kw = dict(tol=1e-13, tol_cw=0.0) if precision == "fp64" else dict(tol=1e-10, tol_cw=1e-8, cw_floor=100.0)
+    with hd.Context.from_problem(p, precision=precision, deflation_k=8, **kw) as ctx:
+        ps, pd, st = ctx.solve_fields(0, p.n_lambda)
+    tol = 1e-10 if precision == "fp64" else 1e-6
+    assert rel_err(ps, rs) <= tol and rel_err(pd, rd) <= tol
+    assert born_rowmax_err(p, ps, pd, rs, rd) <= 1e-5
+    assert st["n_not_converged"] == 0
+
+
 def test_tma_and_generic_kernels_agree(hd, oracle_fields, monkeypatch):
     """The TMA tile kernels and the generic kernels solve the same systems to the same tolerance."""
     p, (rs, rd) = oracle_fields["tma-ragged-36x19x21"]
