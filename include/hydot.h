@@ -174,7 +174,9 @@ typedef enum {
   HYDOT_KERNEL_BORN_ROWS = 3,  /* Born-row assembly */
   HYDOT_KERNEL_APPLY = 4,      /* J x (partial sums) */
   HYDOT_KERNEL_APPLY_T = 5,    /* J^T y (partial sums) */
-  HYDOT_KERNEL_COUNT = 6
+  HYDOT_KERNEL_SKETCH_RANGE = 6,   /* tensor-core Y = J Omega (work counted in flops) */
+  HYDOT_KERNEL_SKETCH_PROJECT = 7, /* tensor-core B^T += J^T Q (work counted in flops) */
+  HYDOT_KERNEL_COUNT = 8
 } hydot_kernel;
 
 /* Instrumentation: on != 0 makes later calls record CUDA events around each launch of the
@@ -192,6 +194,24 @@ int hydot_kernel_stats(hydot_ctx* ctx, int kernel, double* ms, long long* launch
 /* Number of kernels this context has launched since hydot_setup (instrumentation: lets a
  * caller count the library's launches inside a timed region). */
 long long hydot_kernel_launches(const hydot_ctx* ctx);
+
+/* Randomised sketch of J, pass 1 (Appendix A.1, alg:randsvd: Y = A Omega with Gaussian Omega):
+ *   Y[r][k] = sum_(c,x) J[r,(c,x)] Omega[(c,x),k]  for the rows r of the slice [lam0, lam0+nlam).
+ * omega_t: DEVICE BF16 (raw 16-bit) [n_chrom][ncols][N], Omega transposed per chromophore.
+ * Y: DEVICE float [n_src*n_det*nlam][ldY], ldY >= 224; columns >= ncols are written as 0.
+ * Computed on the tensor cores (BF16 operands, FP32 accumulation). Needs HYDOT_MIXED, omega == 0,
+ * N divisible by 8 and ncols <= 224. Synchronises the stream; HYDOT_ERR_TIMEOUT if a bounded
+ * device wait gave up. */
+int hydot_sketch_range(hydot_ctx* ctx, const void* phi_src, const void* phi_det, int lam0, int nlam,
+                       const void* omega_t, int ncols, float* Y, long long ldY);
+
+/* Randomised sketch of J, pass 2 (B = Q^T A): Bt[(c,x)][k] += sum_r J[r,(c,x)] Q[r][k] over the rows
+ * r of the slice, so calls over consecutive slices merge the row blocks into B^T (Section 4.2).
+ * Q: DEVICE float [n_src*n_det*nlam][ldQ] (the slice's rows of the orthonormal range basis),
+ * Bt: DEVICE float [n_chrom*N][ldB], ldB >= 224, accumulated. Tensor cores, same requirements as
+ * hydot_sketch_range. Synchronises the stream. */
+int hydot_sketch_project(hydot_ctx* ctx, const void* phi_src, const void* phi_det, int lam0, int nlam,
+                         const float* Q, int ncols, long long ldQ, float* Bt, long long ldB);
 
 /* Last error message of ctx (or of the last failed hydot_setup when ctx is NULL). */
 const char* hydot_last_error(const hydot_ctx* ctx);

@@ -165,6 +165,38 @@ class Context:
         self._check(rc)
         return g
 
+    # ------------------------------------------------------------------ randomised sketch
+    def sketch_range(self, phi_src, phi_det, lam0: int, nlam: int, omega_t: torch.Tensor, ncols: int,
+                     Y: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """hydot_sketch_range: Y = J Omega (Y has 224 columns; omega_t is bfloat16 [n_chrom][ncols][N])."""
+        M = self.n_src * self.n_det * nlam
+        if Y is None:
+            Y = torch.empty(M, 224, dtype=torch.float32, device="cuda")
+        if omega_t.dtype != torch.bfloat16 or not omega_t.is_contiguous() or omega_t.numel() != self.n_chrom * ncols * self.N:
+            raise ValueError("omega_t must be a contiguous bfloat16 tensor [n_chrom][ncols][N]")
+        self._stream()
+        rc = self.lib.hydot_sketch_range(self._ctx, self._ptr(phi_src, (nlam, self.n_src, self.N), torch.float32),
+                                         self._ptr(phi_det, (nlam, self.n_det, self.N), torch.float32), lam0, nlam,
+                                         omega_t.data_ptr(), ncols, self._ptr(Y, (M, Y.shape[1]), torch.float32),
+                                         Y.shape[1])
+        self._check(rc)
+        return Y
+
+    def sketch_project(self, phi_src, phi_det, lam0: int, nlam: int, Q: torch.Tensor, ncols: int,
+                       Bt: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """hydot_sketch_project: Bt += J^T Q over the slice (Bt [n_chrom*N][224], accumulated)."""
+        M = self.n_src * self.n_det * nlam
+        if Bt is None:
+            Bt = torch.zeros(self.n_chrom * self.N, 224, dtype=torch.float32, device="cuda")
+        self._stream()
+        rc = self.lib.hydot_sketch_project(self._ctx, self._ptr(phi_src, (nlam, self.n_src, self.N), torch.float32),
+                                           self._ptr(phi_det, (nlam, self.n_det, self.N), torch.float32), lam0, nlam,
+                                           self._ptr(Q, (M, Q.shape[1]), torch.float32), ncols, Q.shape[1],
+                                           self._ptr(Bt, (self.n_chrom * self.N, Bt.shape[1]), torch.float32),
+                                           Bt.shape[1])
+        self._check(rc)
+        return Bt
+
     # ------------------------------------------------------------------ instrumentation
     def set_kernel_timing(self, on: bool = True):
         """Record CUDA events around the hot kernels from now on (resets the totals)."""

@@ -86,6 +86,7 @@ void free_all(hydot_ctx* c) {
   cudaFree(c->d_Ginv);
   cudaFree(c->d_defl_coef);
   cudaFree(c->d_apply_ws);
+  cudaFree(c->d_sketch_ws);
 }
 
 }  // namespace
@@ -263,6 +264,29 @@ int hydot_born_apply_T(hydot_ctx* ctx, const void* phi_src, const void* phi_det,
                        void* g) {
   if (!ctx) return HYDOT_ERR_ARG;
   return hydot::born_apply_T_impl(ctx, phi_src, phi_det, lam0, nlam, y, g);
+}
+
+static int sketch_finish(hydot_ctx* ctx, int rc) {
+  if (rc) return rc;
+  int timed_out = 0;
+  HYDOT_CUDA_TRY(ctx, cudaMemcpyAsync(&timed_out, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  HYDOT_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  if (timed_out) return fail(ctx, HYDOT_ERR_TIMEOUT, "a bounded wait in the sketch kernel gave up; output is not valid");
+  return HYDOT_OK;
+}
+
+int hydot_sketch_range(hydot_ctx* ctx, const void* phi_src, const void* phi_det, int lam0, int nlam,
+                       const void* omega_t, int ncols, float* Y, long long ldY) {
+  if (!ctx) return HYDOT_ERR_ARG;
+  return sketch_finish(ctx, hydot::sketch_range_impl(ctx, (const float*)phi_src, (const float*)phi_det, lam0, nlam,
+                                                     omega_t, ncols, Y, ldY));
+}
+
+int hydot_sketch_project(hydot_ctx* ctx, const void* phi_src, const void* phi_det, int lam0, int nlam,
+                         const float* Q, int ncols, long long ldQ, float* Bt, long long ldB) {
+  if (!ctx) return HYDOT_ERR_ARG;
+  return sketch_finish(ctx, hydot::sketch_project_impl(ctx, (const float*)phi_src, (const float*)phi_det, lam0, nlam,
+                                                       Q, ncols, ldQ, Bt, ldB));
 }
 
 long long hydot_kernel_launches(const hydot_ctx* ctx) { return ctx ? ctx->launches : 0; }

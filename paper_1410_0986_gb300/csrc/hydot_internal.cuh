@@ -194,6 +194,10 @@ struct hydot_ctx {
   long long launches = 0;  // kernels enqueued by this context
   hydot::KernelTimer timer;
 
+  // sketch operand workspace (BF16 B operands)
+  void* d_sketch_ws = nullptr;
+  size_t sketch_ws_bytes = 0;
+
   // Born apply workspace
   void* d_apply_ws = nullptr;
   size_t apply_ws_bytes = 0;
@@ -219,6 +223,12 @@ inline int fail(hydot_ctx* ctx, int code, const std::string& msg) {
 int solve_fields_impl(hydot_ctx* ctx, int lam0, int nlam, void* phi_src, void* phi_det, hydot_stats* st);
 int solver_alloc(hydot_ctx* ctx);
 void solver_free(hydot_ctx* ctx);
+
+// sketch.cu
+int sketch_range_impl(hydot_ctx* ctx, const float* ps, const float* pd, int lam0, int nlam, const void* omega_t,
+                      int ncols, float* Y, long long ldY);
+int sketch_project_impl(hydot_ctx* ctx, const float* ps, const float* pd, int lam0, int nlam, const float* Q,
+                        int ncols, long long ldQ, float* Bt, long long ldB);
 
 // deflation.cu
 int build_deflation(hydot_ctx* ctx);

@@ -1,0 +1,430 @@
+// Randomised low-rank sketch of the Born matrix on the tcgen05 tensor cores (Appendix A.1,
+// alg:randsvd, at a fixed rank; Section 4.2 agglomeration as a sum over row blocks).
+//
+//   pass 1 (range):       Y = J Omega,  Y[(s,d,l), k] = -h^3 sum_x phi_s(x) phi_d(x) M_l[x, k],
+//                         M_l = sum_c eps_c(lambda_l) Omega_c                 (rows of one slice)
+//   pass 2 (projection):  B^T[(c,x), k] += -h^3 sum_(s,d,l) eps_c(lambda_l) phi_s(x) phi_d(x) Q[(s,d,l), k]
+//                         (summing over wavelength slices merges the row blocks)
+//
+// Both passes are one BF16 x BF16 -> FP32 tcgen05 GEMM with a 128 x 224 accumulator in tensor
+// memory: the A tile (the Hadamard product of a source and a detector field) is formed by the
+// CTA's threads straight into shared memory in the 128-byte swizzled K-major layout, the B tile
+// (M_l or eps-scaled Q, prepared once per call in BF16) arrives by TMA with the same swizzle, and
+// one thread issues the MMAs. Two pipeline stages; every mbarrier wait is bounded.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <cudaTypedefs.h>
+#include <vector>
+
+#include <cuda_bf16.h>
+
+#include "hydot_internal.cuh"
+#include "tcgen05.cuh"
+
+namespace hydot {
+
+namespace {
+
+constexpr int SK_M = 128;                      // accumulator rows (TMEM lanes)
+constexpr int SK_N = 224;                      // sketch columns (rank + oversampling, padded to 16)
+constexpr int SK_K = 64;                       // K per stage: one 128-byte swizzle row of BF16
+constexpr int SK_A_BYTES = SK_M * SK_K * 2;    // 16 KiB
+constexpr int SK_B_BYTES = SK_N * SK_K * 2;    // 28 KiB
+constexpr int SK_STAGE = SK_A_BYTES + SK_B_BYTES;
+constexpr int SK_STAGES = 2;
+constexpr size_t SK_SMEM = (size_t)SK_STAGES * SK_STAGE + 1024;
+constexpr uint32_t SK_TMEM_COLS = 256;
+
+struct SketchArgs {
+  const float* ps;   // [nlam][ns][N]
+  const float* pd;   // [nlam][nd][N]
+  int ns, nd, nlam;
+  long long N;
+  long long P;       // pairs of the slice: nlam * ns * nd (internal order (l, s, d), d fastest)
+  int tiles_per_lam; // pass 1: ceil(ns * nd / 128)
+  int chrom;         // pass 2: chromophore of this launch
+  float scale;       // -h^3
+  float* out;
+  long long ldo;
+  int* err;
+};
+
+__device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
+  return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// Bounded wait by one thread; on timeout the error flag is raised and the wait is retried once
+// (bounded) so that no copy or MMA is left writing into shared memory that is about to be reused.
+__device__ __forceinline__ void wait_or_flag(uint64_t* m, uint32_t parity, int* err) {
+  if (!mbar_wait_bounded(m, parity)) {
+    atomicExch(err, 1);
+    mbar_wait_bounded(m, parity);
+  }
+}
+
+// MODE 0: range pass (rows = (s,d) pairs of one wavelength, K = voxels).
+// MODE 1: projection pass (rows = voxels, K = pairs of the slice).
+template <int MODE>
+__global__ void __launch_bounds__(128) k_sketch_gemm(SketchArgs a, const __grid_constant__ CUtensorMap mapB) {
+  extern __shared__ uint8_t sk_dsm[];
+  uint8_t* base = align1024(sk_dsm);
+  __shared__ uint64_t full[SK_STAGES], empty[SK_STAGES], done;
+  __shared__ uint32_t s_tmem;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  int lam = 0, tile = 0;
+  long long x0 = 0;
+  if (MODE == 0) {
+    lam = blockIdx.x / a.tiles_per_lam;
+    tile = blockIdx.x % a.tiles_per_lam;
+  } else {
+    x0 = (long long)blockIdx.x * SK_M;
+  }
+  const long long K = (MODE == 0) ? a.N : a.P;
+  const int nk = (int)((K + SK_K - 1) / SK_K);
+  if (warp == 0) tmem_alloc(&s_tmem, SK_TMEM_COLS);
+  if (tid == 0) {
+    for (int q = 0; q < SK_STAGES; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], 1);
+    }
+    mbar_init(&done, 1);
+    mbar_fence_init();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  constexpr uint32_t IDESC = idesc_bf16_f32(SK_M, SK_N);
+  const int npairs = a.ns * a.nd;
+
+  for (int t = 0; t < nk; ++t) {
+    const int st = t & 1;
+    uint8_t* As = base + st * SK_STAGE;
+    uint8_t* Bs = As + SK_A_BYTES;
+    if (t >= SK_STAGES) {
+      if (tid == 0) wait_or_flag(&empty[st], (uint32_t)(((t - SK_STAGES) >> 1) & 1), a.err);
+      __syncthreads();
+    }
+    if (tid == 0) {
+      mbar_expect_tx(&full[st], SK_B_BYTES);
+      if (MODE == 0) tma_load_3d(Bs, &mapB, &full[st], t * SK_K, 0, lam);
+      else tma_load_3d(Bs, &mapB, &full[st], t * SK_K, 0, a.chrom);
+    }
+    // ---- A tile: 128 rows x 64 K of Hadamard products, BF16, swizzled K-major
+    if (MODE == 0) {
+      const long long xk = (long long)t * SK_K;
+#pragma unroll 2
+      for (int j = 0; j < 8; ++j) {
+        const int cidx = tid + 128 * j;
+        const int row = cidx >> 3, ch = cidx & 7;
+        const int q = tile * SK_M + row;
+        uint4 pk = make_uint4(0u, 0u, 0u, 0u);
+        const long long xv = xk + ch * 8;
+        if (q < npairs && xv < a.N) {
+          const int s = q / a.nd, d = q - s * a.nd;
+          const float4* fs = reinterpret_cast<const float4*>(a.ps + ((size_t)lam * a.ns + s) * a.N + xv);
+          const float4* fd = reinterpret_cast<const float4*>(a.pd + ((size_t)lam * a.nd + d) * a.N + xv);
+          const float4 s0 = __ldg(fs), s1 = __ldg(fs + 1), d0 = __ldg(fd), d1 = __ldg(fd + 1);
+          pk.x = pack_bf16x2(s0.x * d0.x, s0.y * d0.y);
+          pk.y = pack_bf16x2(s0.z * d0.z, s0.w * d0.w);
+          pk.z = pack_bf16x2(s1.x * d1.x, s1.y * d1.y);
+          pk.w = pack_bf16x2(s1.z * d1.z, s1.w * d1.w);
+        }
+        *reinterpret_cast<uint4*>(As + sw128_offset(row, ch * 8)) = pk;
+      }
+    } else {
+      const long long x = x0 + tid;
+      const long long p0 = (long long)t * SK_K;
+      // decode p0 once, then step (l, s, d) with d fastest
+      int d = (int)(p0 % a.nd);
+      const long long ls0 = p0 / a.nd;
+      int s = (int)(ls0 % a.ns), l = (int)(ls0 / a.ns);
+      const bool xin = x < a.N;
+      float fsv = (xin && p0 < a.P) ? __ldg(a.ps + ((size_t)l * a.ns + s) * a.N + x) : 0.f;
+      for (int ch = 0; ch < 8; ++ch) {
+        float v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const long long p = p0 + ch * 8 + i;
+          v[i] = (xin && p < a.P) ? fsv * __ldg(a.pd + ((size_t)l * a.nd + d) * a.N + x) : 0.f;
+          if (++d == a.nd) {
+            d = 0;
+            if (++s == a.ns) {
+              s = 0;
+              ++l;
+            }
+            if (xin && p + 1 < a.P) fsv = __ldg(a.ps + ((size_t)l * a.ns + s) * a.N + x);
+          }
+        }
+        uint4 pk;
+        pk.x = pack_bf16x2(v[0], v[1]);
+        pk.y = pack_bf16x2(v[2], v[3]);
+        pk.z = pack_bf16x2(v[4], v[5]);
+        pk.w = pack_bf16x2(v[6], v[7]);
+        *reinterpret_cast<uint4*>(As + sw128_offset(tid, ch * 8)) = pk;
+      }
+    }
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      wait_or_flag(&full[st], (uint32_t)((t >> 1) & 1), a.err);
+      tc_fence_after();
+      const uint32_t a_addr = smem_addr(As), b_addr = smem_addr(Bs);
+#pragma unroll
+      for (int kk = 0; kk < SK_K / 16; ++kk) {
+        tc_mma_bf16(tmem, smem_desc_sw128(a_addr + kk * 32), smem_desc_sw128(b_addr + kk * 32), IDESC,
+                    (t > 0 || kk > 0) ? 1u : 0u);
+      }
+      tc_commit(&empty[st]);
+    }
+  }
+  if (tid == 0) {
+    tc_commit(&done);
+    wait_or_flag(&done, 0, a.err);
+  }
+  __syncthreads();
+  tc_fence_after();
+  // ---- epilogue: warp w owns TMEM lanes 32w..32w+31, i.e. accumulator rows 32w + lane
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  const int row = tid;
+  float* dst = nullptr;
+  bool ok = false;
+  if (MODE == 0) {
+    const int q = tile * SK_M + row;
+    if (q < npairs) {
+      const int s = q / a.nd, d = q - s * a.nd;
+      const long long r = ((long long)s * a.nd + d) * a.nlam + lam;
+      dst = a.out + r * a.ldo;
+      ok = true;
+    }
+  } else {
+    const long long x = x0 + row;
+    if (x < a.N) {
+      dst = a.out + ((long long)a.chrom * a.N + x) * a.ldo;
+      ok = true;
+    }
+  }
+  for (int c0 = 0; c0 < SK_N; c0 += 16) {
+    float v[16];
+    tmem_ld16(tmem + lane_base + (uint32_t)c0, v);
+    if (ok) {
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        if (MODE == 0) dst[c0 + q] = a.scale * v[q];
+        else dst[c0 + q] += a.scale * v[q];
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, SK_TMEM_COLS);
+}
+
+// Mt[l][k][x] = sum_c eps_c(lambda_(lam0+l)) * Omega_t[c][k][x] in BF16 (k >= ncols: 0); 8 voxels per thread.
+__global__ void k_form_mt(const __nv_bfloat16* __restrict__ om, const double* __restrict__ eps, int lam0, int nlam,
+                          int nc, int ncols, long long N, __nv_bfloat16* __restrict__ Mt) {
+  const long long nv = N / 8;
+  const long long total = (long long)nlam * SK_N * nv;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (long long)gridDim.x * blockDim.x) {
+    const long long xv = q % nv;
+    const int k = (int)((q / nv) % SK_N);
+    const int l = (int)(q / (nv * SK_N));
+    float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (k < ncols) {
+      for (int c = 0; c < nc; ++c) {
+        const float e = (float)eps[(size_t)(lam0 + l) * nc + c];
+        const uint4 raw = *reinterpret_cast<const uint4*>(om + ((size_t)c * ncols + k) * N + xv * 8);
+        const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&raw);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float2 f = __bfloat1622float2(h[i]);
+          acc[2 * i] = fmaf(e, f.x, acc[2 * i]);
+          acc[2 * i + 1] = fmaf(e, f.y, acc[2 * i + 1]);
+        }
+      }
+    }
+    uint4 out;
+    out.x = pack_bf16x2(acc[0], acc[1]);
+    out.y = pack_bf16x2(acc[2], acc[3]);
+    out.z = pack_bf16x2(acc[4], acc[5]);
+    out.w = pack_bf16x2(acc[6], acc[7]);
+    *reinterpret_cast<uint4*>(Mt + ((size_t)l * SK_N + k) * N + xv * 8) = out;
+  }
+}
+
+// Qc[c][k][p] = eps_c(lambda of pair p) * Q[row(p)][k] in BF16, pairs p = (l, s, d) of the slice
+// (d fastest), row(p) = (s*nd + d)*nlam + l; p >= P or k >= ncols: 0.
+__global__ void k_form_qc(const float* __restrict__ Q, long long ldq, const double* __restrict__ eps, int lam0,
+                          int nlam, int ns, int nd, int nc, int ncols, long long P, long long Pp,
+                          __nv_bfloat16* __restrict__ Qc) {
+  const long long total = (long long)nc * SK_N * Pp;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (long long)gridDim.x * blockDim.x) {
+    const long long p = q % Pp;
+    const int k = (int)((q / Pp) % SK_N);
+    const int c = (int)(q / (Pp * SK_N));
+    float v = 0.f;
+    if (p < P && k < ncols) {
+      const int d = (int)(p % nd);
+      const long long ls = p / nd;
+      const int s = (int)(ls % ns), l = (int)(ls / ns);
+      const long long r = ((long long)s * nd + d) * nlam + l;
+      v = (float)eps[(size_t)(lam0 + l) * nc + c] * Q[r * ldq + k];
+    }
+    Qc[q] = __float2bfloat16_rn(v);
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder(hydot_ctx* ctx) {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  if (!fn) fail(ctx, HYDOT_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  return fn;
+}
+
+// 3-D BF16 map {inner, 224, outer} with a {64, 224, 1} box in the 128-byte swizzle.
+int encode_b_map(hydot_ctx* ctx, void* base, long long inner, long long outer, CUtensorMap* map) {
+  auto enc = tensor_map_encoder(ctx);
+  if (!enc) return HYDOT_ERR_CUDA;
+  cuuint64_t dims[3] = {(cuuint64_t)inner, (cuuint64_t)SK_N, (cuuint64_t)outer};
+  cuuint64_t strides[2] = {(cuuint64_t)inner * 2, (cuuint64_t)inner * 2 * SK_N};
+  cuuint32_t box[3] = {(cuuint32_t)SK_K, (cuuint32_t)SK_N, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(ctx, HYDOT_ERR_CUDA, "cuTensorMapEncodeTiled failed for a sketch operand");
+  return HYDOT_OK;
+}
+
+int sketch_ws(hydot_ctx* ctx, size_t bytes) {
+  if (ctx->sketch_ws_bytes >= bytes) return HYDOT_OK;
+  if (ctx->d_sketch_ws) {
+    HYDOT_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    cudaFree(ctx->d_sketch_ws);
+    ctx->d_sketch_ws = nullptr;
+    ctx->sketch_ws_bytes = 0;
+  }
+  HYDOT_CUDA_TRY(ctx, cudaMalloc(&ctx->d_sketch_ws, bytes));
+  ctx->sketch_ws_bytes = bytes;
+  return HYDOT_OK;
+}
+
+int sketch_check(hydot_ctx* ctx, int lam0, int nlam, int ncols) {
+  if (ctx->cplx) return fail(ctx, HYDOT_ERR_STATE, "the sketch is defined for continuous-wave (real) fields only");
+  if (ctx->precision != HYDOT_MIXED) return fail(ctx, HYDOT_ERR_STATE, "the sketch takes FP32 fields (HYDOT_MIXED)");
+  if (lam0 < 0 || nlam < 1 || lam0 + nlam > ctx->n_lambda) return fail(ctx, HYDOT_ERR_ARG, "wavelength slice out of range");
+  if (ncols < 1 || ncols > SK_N) return fail(ctx, HYDOT_ERR_ARG, "ncols must be in 1..224");
+  if (ctx->N % 8 != 0) return fail(ctx, HYDOT_ERR_ARG, "the sketch needs N divisible by 8");
+  return HYDOT_OK;
+}
+
+int set_sketch_smem(hydot_ctx* ctx) {
+  static bool done = false;
+  if (!done) {
+    HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(k_sketch_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SK_SMEM));
+    HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(k_sketch_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SK_SMEM));
+    done = true;
+  }
+  return HYDOT_OK;
+}
+
+}  // namespace
+
+int sketch_range_impl(hydot_ctx* ctx, const float* ps, const float* pd, int lam0, int nlam, const void* omega_t,
+                      int ncols, float* Y, long long ldY) {
+  int rc = sketch_check(ctx, lam0, nlam, ncols);
+  if (rc) return rc;
+  if (!ps || !pd || !omega_t || !Y) return fail(ctx, HYDOT_ERR_ARG, "null pointer");
+  if (ldY < SK_N) return fail(ctx, HYDOT_ERR_ARG, "ldY must be >= 224");
+  const long long N = ctx->N;
+  const size_t mt_bytes = (size_t)nlam * SK_N * N * 2;
+  if ((rc = sketch_ws(ctx, mt_bytes))) return rc;
+  if ((rc = set_sketch_smem(ctx))) return rc;
+  __nv_bfloat16* Mt = (__nv_bfloat16*)ctx->d_sketch_ws;
+  const long long tot = (long long)nlam * SK_N * (N / 8);
+  k_form_mt<<<(unsigned)std::min<long long>((tot + 255) / 256, 152 * 32), 256, 0, ctx->stream>>>(
+      (const __nv_bfloat16*)omega_t, ctx->d_eps, lam0, nlam, ctx->n_chrom, ncols, N, Mt);
+  ++ctx->launches;
+  HYDOT_CUDA_TRY(ctx, cudaGetLastError());
+  CUtensorMap map;
+  if ((rc = encode_b_map(ctx, Mt, N, nlam, &map))) return rc;
+  SketchArgs a{};
+  a.ps = ps;
+  a.pd = pd;
+  a.ns = ctx->n_src;
+  a.nd = ctx->n_det;
+  a.nlam = nlam;
+  a.N = N;
+  a.P = (long long)nlam * a.ns * a.nd;
+  a.tiles_per_lam = (a.ns * a.nd + SK_M - 1) / SK_M;
+  a.scale = (float)(-ctx->h * ctx->h * ctx->h);
+  a.out = Y;
+  a.ldo = ldY;
+  a.err = ctx->d_err;
+  HYDOT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
+  cudaEvent_t t0 = timer_begin(ctx);
+  k_sketch_gemm<0><<<(unsigned)(nlam * a.tiles_per_lam), 128, SK_SMEM, ctx->stream>>>(a, map);
+  ++ctx->launches;
+  timer_end(ctx, t0, HYDOT_KERNEL_SKETCH_RANGE, 2.0 * (double)a.P * (double)N * ncols);
+  HYDOT_CUDA_TRY(ctx, cudaGetLastError());
+  return HYDOT_OK;
+}
+
+int sketch_project_impl(hydot_ctx* ctx, const float* ps, const float* pd, int lam0, int nlam, const float* Q,
+                        int ncols, long long ldQ, float* Bt, long long ldB) {
+  int rc = sketch_check(ctx, lam0, nlam, ncols);
+  if (rc) return rc;
+  if (!ps || !pd || !Q || !Bt) return fail(ctx, HYDOT_ERR_ARG, "null pointer");
+  if (ldB < SK_N || ldQ < ncols) return fail(ctx, HYDOT_ERR_ARG, "ldB must be >= 224 and ldQ >= ncols");
+  const long long N = ctx->N;
+  const int nc = ctx->n_chrom;
+  const long long P = (long long)nlam * ctx->n_src * ctx->n_det;
+  const long long Pp = (P + 7) / 8 * 8;
+  if ((rc = sketch_ws(ctx, (size_t)nc * SK_N * Pp * 2))) return rc;
+  if ((rc = set_sketch_smem(ctx))) return rc;
+  __nv_bfloat16* Qc = (__nv_bfloat16*)ctx->d_sketch_ws;
+  const long long tot = (long long)nc * SK_N * Pp;
+  k_form_qc<<<(unsigned)std::min<long long>((tot + 255) / 256, 152 * 32), 256, 0, ctx->stream>>>(
+      Q, ldQ, ctx->d_eps, lam0, nlam, ctx->n_src, ctx->n_det, nc, ncols, P, Pp, Qc);
+  ++ctx->launches;
+  HYDOT_CUDA_TRY(ctx, cudaGetLastError());
+  CUtensorMap map;
+  if ((rc = encode_b_map(ctx, Qc, Pp, nc, &map))) return rc;
+  SketchArgs a{};
+  a.ps = ps;
+  a.pd = pd;
+  a.ns = ctx->n_src;
+  a.nd = ctx->n_det;
+  a.nlam = nlam;
+  a.N = N;
+  a.P = P;
+  a.scale = (float)(-ctx->h * ctx->h * ctx->h);
+  a.out = Bt;
+  a.ldo = ldB;
+  a.err = ctx->d_err;
+  HYDOT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
+  const unsigned grid = (unsigned)((N + SK_M - 1) / SK_M);
+  cudaEvent_t t0 = timer_begin(ctx);
+  for (int c = 0; c < nc; ++c) {
+    a.chrom = c;
+    k_sketch_gemm<1><<<grid, 128, SK_SMEM, ctx->stream>>>(a, map);
+    ++ctx->launches;
+  }
+  timer_end(ctx, t0, HYDOT_KERNEL_SKETCH_PROJECT, 2.0 * (double)nc * (double)N * (double)P * ncols);
+  HYDOT_CUDA_TRY(ctx, cudaGetLastError());
+  return HYDOT_OK;
+}
+
+}  // namespace hydot

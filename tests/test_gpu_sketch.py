@@ -1,0 +1,101 @@
+"""Parity of the tensor-core sketch passes (Appendix A.1) with the CPU oracle.
+
+Pass 1 computes Y = J Omega and pass 2 B^T = J^T Q on the tcgen05 tensor cores with BF16
+operands and FP32 accumulation. Two references: (i) the same products with the operands rounded
+to BF16 the way the kernels round them, evaluated in FP64 -- this checks the tensor-core data path
+(layout, swizzle, descriptors, accumulation) to FP32 accumulation accuracy; (ii) the oracle's FP64
+J times the FP64 Omega / Q -- the end-to-end error, bounded by BF16's 2^-9 relative rounding.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from oracle import born as oborn
+from oracle import solve as osolve
+
+pytestmark = pytest.mark.gpu
+
+
+def bf16_round(a):
+    """Round float32 values to bfloat16 (round to nearest even), returned as float64."""
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    u = a.view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+@pytest.fixture(scope="module")
+def case():
+    # 40 sources x 36 detectors: 1,440 pairs per wavelength -> 12 row tiles, the last one partial
+    p = workloads.small(seed=21, nx=16, ny=12, nz=10, n_src=40, n_det=36, n_lambda=3, margin=0)
+    rs, rd = osolve.fields_separable(p)
+    return p, rs.astype(np.float32), rd.astype(np.float32)
+
+
+def test_sketch_range_pass(lib, case):
+    p, rs, rd = case
+    N, nc, ncols = p.grid.N, p.n_chrom, 200
+    om = workloads.gaussian(31, (nc, ncols, N)).astype(np.float32)
+    om_b = bf16_round(om)
+    with lib.Context.from_problem(p, precision="mixed", tol=1e-8, tol_cw=0.0) as ctx:
+        Y = ctx.sketch_range(torch.tensor(rs, device="cuda"), torch.tensor(rd, device="cuda"), 0, p.n_lambda,
+                             torch.tensor(om, device="cuda").to(torch.bfloat16), ncols).cpu().double().numpy()
+    assert np.all(Y[:, ncols:] == 0.0)
+    Y = Y[:, :ncols]
+    h3 = p.grid.h ** 3
+    # (i) emulate the kernels' operand rounding: A = bf16(fp32(phi_s * phi_d)), M = bf16(sum_c eps_c Omega_c)
+    nd, nl = p.n_det, p.n_lambda
+    ref_i = np.empty_like(Y)
+    for lam in range(nl):
+        M = bf16_round(np.einsum("c,ckx->kx", p.eps[lam].astype(np.float32), om_b.astype(np.float32)).astype(np.float32))
+        for s in range(p.n_src):
+            A = bf16_round(rs[lam, s][None, :] * rd[lam])  # [nd, N]
+            rows = [(s * nd + d) * nl + lam for d in range(nd)]
+            ref_i[rows] = -h3 * A @ M.T
+    err_i = np.abs(Y - ref_i).max(axis=1) / np.abs(ref_i).max(axis=1)
+    assert err_i.max() <= 2e-3, err_i.max()
+    # (ii) end to end against the FP64 oracle
+    J = oborn.born_matrix(p, rs.astype(np.float64), rd.astype(np.float64))
+    Omega = np.concatenate([om[c].T for c in range(nc)], axis=0).astype(np.float64)  # [(c,x), k]
+    ref = J @ Omega
+    rel = np.linalg.norm(Y - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert rel.max() <= 2e-2, rel.max()
+
+
+def test_sketch_project_pass_accumulates_over_slices(lib, case):
+    p, rs, rd = case
+    N, nc, ncols = p.grid.N, p.n_chrom, 200
+    M = p.M
+    Q = workloads.gaussian(32, (M, ncols)).astype(np.float32)
+    Qp = np.zeros((M, 224), dtype=np.float32)
+    Qp[:, :ncols] = Q
+    nd, nl = p.n_det, p.n_lambda
+    with lib.Context.from_problem(p, precision="mixed", tol=1e-8, tol_cw=0.0) as ctx:
+        ps, pd = torch.tensor(rs, device="cuda"), torch.tensor(rd, device="cuda")
+        Bt = torch.zeros(nc * N, 224, device="cuda")
+        # two slices [0,1) and [1,3): rows of a slice are (s, d, lambda - lam0)
+        for lam0, nlam in ((0, 1), (1, 2)):
+            rows = [(s * nd + d) * nl + lam for s in range(p.n_src) for d in range(nd) for lam in range(lam0, lam0 + nlam)]
+            Qs = torch.tensor(Qp[rows], device="cuda")
+            ctx.sketch_project(ps[lam0:lam0 + nlam].contiguous(), pd[lam0:lam0 + nlam].contiguous(), lam0, nlam, Qs,
+                               ncols, Bt)
+        Bt = Bt.cpu().double().numpy()
+    assert np.all(Bt[:, ncols:] == 0.0)
+    Bt = Bt[:, :ncols]
+    J = oborn.born_matrix(p, rs.astype(np.float64), rd.astype(np.float64))
+    ref = J.T @ Q.astype(np.float64)
+    rel = np.linalg.norm(Bt - ref, axis=0) / np.linalg.norm(ref, axis=0)
+    assert rel.max() <= 2e-2, rel.max()
+    # exact operand emulation: A = bf16(phi_s phi_d), B = bf16(eps_c * Q)
+    h3 = p.grid.h ** 3
+    ref_i = np.zeros_like(ref)
+    for lam in range(nl):
+        for s in range(p.n_src):
+            A = bf16_round(rs[lam, s][None, :] * rd[lam])  # [nd, N]
+            rows = [(s * nd + d) * nl + lam for d in range(nd)]
+            for c in range(nc):
+                Bq = bf16_round((np.float32(p.eps[lam, c]) * Q[rows]).astype(np.float32))
+                ref_i[c * N:(c + 1) * N] += -h3 * A.T @ Bq
+    err_i = np.abs(Bt - ref_i).max(axis=0) / np.abs(ref_i).max(axis=0)
+    assert err_i.max() <= 2e-3, err_i.max()
