@@ -213,6 +213,20 @@ int hydot_sketch_range(hydot_ctx* ctx, const void* phi_src, const void* phi_det,
 int hydot_sketch_project(hydot_ctx* ctx, const void* phi_src, const void* phi_det, int lam0, int nlam,
                          const float* Q, int ncols, long long ldQ, float* Bt, long long ldB);
 
+/* Orthonormal basis of range(Y) in place (the basis step of alg:randsvd): two rounds of
+ * Y <- Y V diag(lambda^-1/2) from the FP64 Gram Y^T Y = V diag(lambda) V^T. Directions whose
+ * singular value is below 1e-6 of the largest become zero columns; *rank_out (may be NULL) gets the
+ * number kept. Y: DEVICE float [rows][ldY], first ncols (<= 224) columns. Synchronous. */
+int hydot_sketch_orthonormalize(hydot_ctx* ctx, float* Y, long long rows, int ncols, long long ldY, int* rank_out);
+
+/* Rank-`rank` factors J ~ U diag(S) V^T from Q (the orthonormal range basis, rows x ncols) and
+ * Bt = (Q^T J)^T (nb = n_chrom*N rows): the FP64 Gram of Bt gives U_B and S (descending), then
+ * V = Bt U_B diag(1/S) and U = Q U_B (Section 4.4's final recompression). U: DEVICE float
+ * [rows][ldU], V: DEVICE float [nb][ldV], S: HOST double [rank]. Synchronous. */
+int hydot_sketch_factor(hydot_ctx* ctx, const float* Q, long long rows, long long ldQ, const float* Bt, long long nb,
+                        long long ldB, int ncols, int rank, float* U, long long ldU, double* S, float* V,
+                        long long ldV);
+
 /* Last error message of ctx (or of the last failed hydot_setup when ctx is NULL). */
 const char* hydot_last_error(const hydot_ctx* ctx);
 

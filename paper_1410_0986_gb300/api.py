@@ -197,6 +197,25 @@ class Context:
         self._check(rc)
         return Bt
 
+    def sketch_orthonormalize(self, Y: torch.Tensor, ncols: int) -> int:
+        """hydot_sketch_orthonormalize in place; returns the number of directions kept."""
+        k = C.c_int()
+        self._stream()
+        self._check(self.lib.hydot_sketch_orthonormalize(self._ctx, self._ptr(Y, tuple(Y.shape), torch.float32),
+                                                         Y.shape[0], ncols, Y.shape[1], C.byref(k)))
+        return k.value
+
+    def sketch_factor(self, Q: torch.Tensor, Bt: torch.Tensor, ncols: int, rank: int):
+        """hydot_sketch_factor: (U [rows][rank], S [rank] numpy, V [n_chrom*N][rank])."""
+        U = torch.empty(Q.shape[0], rank, dtype=torch.float32, device="cuda")
+        V = torch.empty(Bt.shape[0], rank, dtype=torch.float32, device="cuda")
+        S = (C.c_double * rank)()
+        self._stream()
+        self._check(self.lib.hydot_sketch_factor(self._ctx, self._ptr(Q, tuple(Q.shape), torch.float32), Q.shape[0],
+                                                 Q.shape[1], self._ptr(Bt, tuple(Bt.shape), torch.float32), Bt.shape[0],
+                                                 Bt.shape[1], ncols, rank, U.data_ptr(), rank, S, V.data_ptr(), rank))
+        return U, np.array(S[:]), V
+
     # ------------------------------------------------------------------ instrumentation
     def set_kernel_timing(self, on: bool = True):
         """Record CUDA events around the hot kernels from now on (resets the totals)."""

@@ -289,6 +289,18 @@ int hydot_sketch_project(hydot_ctx* ctx, const void* phi_src, const void* phi_de
                                                        Q, ncols, ldQ, Bt, ldB));
 }
 
+int hydot_sketch_orthonormalize(hydot_ctx* ctx, float* Y, long long rows, int ncols, long long ldY, int* rank_out) {
+  if (!ctx) return HYDOT_ERR_ARG;
+  return hydot::sketch_orthonormalize_impl(ctx, Y, rows, ncols, ldY, rank_out);
+}
+
+int hydot_sketch_factor(hydot_ctx* ctx, const float* Q, long long rows, long long ldQ, const float* Bt, long long nb,
+                        long long ldB, int ncols, int rank, float* U, long long ldU, double* S, float* V,
+                        long long ldV) {
+  if (!ctx) return HYDOT_ERR_ARG;
+  return hydot::sketch_factor_impl(ctx, Q, rows, ldQ, Bt, nb, ldB, ncols, rank, U, ldU, S, V, ldV);
+}
+
 long long hydot_kernel_launches(const hydot_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
 int hydot_set_kernel_timing(hydot_ctx* ctx, int on) {

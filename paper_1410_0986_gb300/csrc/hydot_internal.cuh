@@ -229,6 +229,9 @@ int sketch_range_impl(hydot_ctx* ctx, const float* ps, const float* pd, int lam0
                       int ncols, float* Y, long long ldY);
 int sketch_project_impl(hydot_ctx* ctx, const float* ps, const float* pd, int lam0, int nlam, const float* Q,
                         int ncols, long long ldQ, float* Bt, long long ldB);
+int sketch_orthonormalize_impl(hydot_ctx* ctx, float* Y, long long rows, int ncols, long long ldY, int* rank_out);
+int sketch_factor_impl(hydot_ctx* ctx, const float* Q, long long rows, long long ldQ, const float* Bt, long long nb,
+                       long long ldB, int ncols, int rank, float* U, long long ldU, double* S, float* V, long long ldV);
 
 // deflation.cu
 int build_deflation(hydot_ctx* ctx);

@@ -19,6 +19,7 @@
 
 #include <cuda_bf16.h>
 
+#include "dense.h"
 #include "hydot_internal.cuh"
 #include "tcgen05.cuh"
 
@@ -425,6 +426,246 @@ int sketch_project_impl(hydot_ctx* ctx, const float* ps, const float* pd, int la
   timer_end(ctx, t0, HYDOT_KERNEL_SKETCH_PROJECT, 2.0 * (double)nc * (double)N * (double)P * ncols);
   HYDOT_CUDA_TRY(ctx, cudaGetLastError());
   return HYDOT_OK;
+}
+
+}  // namespace hydot
+
+// ---------------------------------------------------------------- tall-skinny helpers
+// Orthonormalisation of the range sketch and the final factors use the n x n (n <= 224) Gram
+// matrices of tall-skinny operands, accumulated in FP64 (the Gram squares the condition number),
+// and products with small n x m matrices.
+namespace hydot {
+namespace {
+
+constexpr int GT = 32;  // Gram tile (columns)
+
+// partial[chunk][pair][GT][GT] = X[rows of chunk][tile i]^T X[rows of chunk][tile j], pair = (i <= j)
+__global__ void __launch_bounds__(256) k_gram64(const float* __restrict__ X, long long rows, long long ldx, int n,
+                                                int ntile, long long rows_per_chunk, double* __restrict__ part) {
+  __shared__ double Xi[64][GT + 1], Xj[64][GT + 1];
+  const int chunk = blockIdx.x, pair = blockIdx.y;
+  int ti = 0, rem = pair;
+  while (rem >= ntile - ti) {
+    rem -= ntile - ti;
+    ++ti;
+  }
+  const int tj = ti + rem;
+  const int t = threadIdx.x;
+  const int ii = t >> 3, jj = (t & 7) * 4;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  const long long r0 = (long long)chunk * rows_per_chunk;
+  const long long r1 = min(rows, r0 + rows_per_chunk);
+  for (long long rb = r0; rb < r1; rb += 64) {
+    for (int q = t; q < 64 * GT; q += 256) {
+      const int rr = q / GT, cc = q % GT;
+      const long long r = rb + rr;
+      const int ci = ti * GT + cc, cj = tj * GT + cc;
+      Xi[rr][cc] = (r < r1 && ci < n) ? (double)X[r * ldx + ci] : 0.0;
+      Xj[rr][cc] = (r < r1 && cj < n) ? (double)X[r * ldx + cj] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int rr = 0; rr < 64; ++rr) {
+      const double a = Xi[rr][ii];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] += a * Xj[rr][jj + q];
+    }
+    __syncthreads();
+  }
+  double* out = part + (((size_t)chunk * gridDim.y + pair) * GT + ii) * GT + jj;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) out[q] = acc[q];
+}
+
+__global__ void k_gram_reduce(const double* __restrict__ part, int nchunk, int npair, int ntile, int n,
+                              double* __restrict__ G) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= npair * GT * GT) return;
+  const int pair = idx / (GT * GT), ij = idx % (GT * GT), ii = ij / GT, jj = ij % GT;
+  int ti = 0, rem = pair;
+  while (rem >= ntile - ti) {
+    rem -= ntile - ti;
+    ++ti;
+  }
+  const int tj = ti + rem;
+  double s = 0.0;
+  for (int c = 0; c < nchunk; ++c) s += part[((size_t)c * npair + pair) * GT * GT + ij];
+  const int a = ti * GT + ii, b = tj * GT + jj;
+  if (a < n && b < n) {
+    G[(size_t)a * n + b] = s;
+    G[(size_t)b * n + a] = s;
+  }
+}
+
+// Z[r][j] = sum_k X[r][k] W[k][j] for j < m (Z columns m..ldz-1 untouched), FP32.
+__global__ void __launch_bounds__(256) k_right_mul(const float* __restrict__ X, long long rows, long long ldx, int n,
+                                                   const float* __restrict__ W, int m, float* __restrict__ Z,
+                                                   long long ldz) {
+  __shared__ float Xs[64][33];
+  __shared__ float Ws[32][64];
+  const int t = threadIdx.x, tr = t >> 4, tc = t & 15;
+  const long long r0 = (long long)blockIdx.x * 64;
+  const int c0 = blockIdx.y * 64;
+  float acc[4][4] = {};
+  for (int k0 = 0; k0 < n; k0 += 32) {
+    for (int q = t; q < 64 * 32; q += 256) {
+      const int rr = q / 32, kk = q % 32;
+      const long long r = r0 + rr;
+      Xs[rr][kk] = (r < rows && k0 + kk < n) ? X[r * ldx + k0 + kk] : 0.f;
+    }
+    for (int q = t; q < 32 * 64; q += 256) {
+      const int kk = q / 64, cc = q % 64;
+      Ws[kk][cc] = (k0 + kk < n && c0 + cc < m) ? W[(size_t)(k0 + kk) * m + c0 + cc] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < 32; ++kk) {
+      float a[4], w[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[u] = Xs[tr * 4 + u][kk];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) w[v] = Ws[kk][tc * 4 + v];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(a[u], w[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const long long r = r0 + tr * 4 + u;
+    if (r >= rows) continue;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int c = c0 + tc * 4 + v;
+      if (c < m) Z[r * ldz + c] = acc[u][v];
+    }
+  }
+}
+
+// G = X[:, :n]^T X[:, :n] (n x n, FP64) to the host.
+int gram(hydot_ctx* ctx, const float* X, long long rows, long long ldx, int n, std::vector<double>& G) {
+  const int ntile = (n + GT - 1) / GT;
+  const int npair = ntile * (ntile + 1) / 2;
+  const long long want = std::max<long long>(1, 4 * 152 / npair);
+  const long long nchunk = std::max<long long>(1, std::min<long long>(want, (rows + 63) / 64));
+  const long long rpc = ((rows + nchunk - 1) / nchunk + 63) / 64 * 64;
+  const long long nch = (rows + rpc - 1) / rpc;
+  double *part = nullptr, *dG = nullptr;
+  HYDOT_CUDA_TRY(ctx, cudaMalloc(&part, sizeof(double) * (size_t)nch * npair * GT * GT));
+  cudaError_t e = cudaMalloc(&dG, sizeof(double) * (size_t)n * n);
+  if (e != cudaSuccess) {
+    cudaFree(part);
+    return fail(ctx, HYDOT_ERR_OOM, "cudaMalloc of the Gram matrix failed");
+  }
+  k_gram64<<<dim3((unsigned)nch, npair), 256, 0, ctx->stream>>>(X, rows, ldx, n, ntile, rpc, part);
+  k_gram_reduce<<<(npair * GT * GT + 255) / 256, 256, 0, ctx->stream>>>(part, (int)nch, npair, ntile, n, dG);
+  ctx->launches += 2;
+  G.assign((size_t)n * n, 0.0);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(G.data(), dG, sizeof(double) * n * n, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  cudaFree(part);
+  cudaFree(dG);
+  if (e != cudaSuccess) return fail(ctx, HYDOT_ERR_CUDA, std::string("Gram: ") + cudaGetErrorString(e));
+  return HYDOT_OK;
+}
+
+// Z = X W with W (n x m) given on the host.
+int right_mul(hydot_ctx* ctx, const float* X, long long rows, long long ldx, int n, const std::vector<float>& W, int m,
+              float* Z, long long ldz) {
+  float* dW = nullptr;
+  HYDOT_CUDA_TRY(ctx, cudaMalloc(&dW, sizeof(float) * (size_t)n * m));
+  cudaError_t e = cudaMemcpyAsync(dW, W.data(), sizeof(float) * (size_t)n * m, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) {
+    k_right_mul<<<dim3((unsigned)((rows + 63) / 64), (m + 63) / 64), 256, 0, ctx->stream>>>(X, rows, ldx, n, dW, m, Z, ldz);
+    ++ctx->launches;
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  cudaFree(dW);
+  if (e != cudaSuccess) return fail(ctx, HYDOT_ERR_CUDA, std::string("right_mul: ") + cudaGetErrorString(e));
+  return HYDOT_OK;
+}
+
+// eigen-pairs of a symmetric n x n matrix, descending
+void eig_desc(const std::vector<double>& G, int n, std::vector<double>& lam, std::vector<double>& V) {
+  std::vector<double> l, Z;
+  jacobi_eig(G, n, l, Z);
+  std::vector<int> ord(n);
+  for (int i = 0; i < n; ++i) ord[i] = i;
+  std::sort(ord.begin(), ord.end(), [&](int a, int b) { return l[a] > l[b]; });
+  lam.resize(n);
+  V.assign((size_t)n * n, 0.0);
+  for (int j = 0; j < n; ++j) {
+    lam[j] = l[ord[j]];
+    for (int i = 0; i < n; ++i) V[(size_t)i * n + j] = Z[(size_t)i * n + ord[j]];
+  }
+}
+
+}  // namespace
+
+// Orthonormal basis of range(Y) in place: two rounds of Y <- Y V_k diag(lambda_k^-1/2) from the FP64
+// Gram Y^T Y = V diag(lambda) V^T, keeping the directions whose singular value exceeds 1e-6 of the
+// largest (the rest are set to zero columns). *rank_out receives the number kept.
+int sketch_orthonormalize_impl(hydot_ctx* ctx, float* Y, long long rows, int ncols, long long ldY, int* rank_out) {
+  if (!Y || rows < 1 || ncols < 1 || ncols > SK_N || ldY < ncols) return fail(ctx, HYDOT_ERR_ARG, "bad Y shape");
+  float* Z = nullptr;
+  HYDOT_CUDA_TRY(ctx, cudaMalloc(&Z, sizeof(float) * (size_t)rows * ncols));
+  int kept = ncols;
+  for (int round = 0; round < 2; ++round) {
+    std::vector<double> G, lam, V;
+    int rc = gram(ctx, Y, rows, ldY, ncols, G);
+    if (rc) { cudaFree(Z); return rc; }
+    eig_desc(G, ncols, lam, V);
+    const double smax = std::sqrt(std::max(lam[0], 0.0));
+    kept = 0;
+    std::vector<float> W((size_t)ncols * ncols, 0.f);
+    for (int j = 0; j < ncols; ++j) {
+      const double sj = std::sqrt(std::max(lam[j], 0.0));
+      if (!(sj > 1e-6 * smax) || smax == 0.0) break;
+      ++kept;
+      for (int i = 0; i < ncols; ++i) W[(size_t)i * ncols + j] = (float)(V[(size_t)i * ncols + j] / sj);
+    }
+    rc = right_mul(ctx, Y, rows, ldY, ncols, W, ncols, Z, ncols);
+    if (!rc) {
+      cudaError_t e = cudaMemcpy2DAsync(Y, sizeof(float) * ldY, Z, sizeof(float) * ncols, sizeof(float) * ncols, rows,
+                                        cudaMemcpyDeviceToDevice, ctx->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+      if (e != cudaSuccess) rc = fail(ctx, HYDOT_ERR_CUDA, std::string("copy: ") + cudaGetErrorString(e));
+    }
+    if (rc) { cudaFree(Z); return rc; }
+  }
+  cudaFree(Z);
+  if (rank_out) *rank_out = kept;
+  return HYDOT_OK;
+}
+
+// Rank-r factors from the projected sketch: with B = Q^T J (given as Bt = B^T, nb x ncols) the Gram
+// B B^T = U_B diag(S^2) U_B^T gives S, V = B^T U_B diag(1/S) and U = Q U_B, so J ~ U diag(S) V^T
+// (the final recompression of Section 4.4, truncated to `rank`).
+int sketch_factor_impl(hydot_ctx* ctx, const float* Q, long long rows, long long ldQ, const float* Bt, long long nb,
+                       long long ldB, int ncols, int rank, float* U, long long ldU, double* S, float* V, long long ldV) {
+  if (!Q || !Bt || !U || !S || !V) return fail(ctx, HYDOT_ERR_ARG, "null pointer");
+  if (ncols < 1 || ncols > SK_N || rank < 1 || rank > ncols || ldQ < ncols || ldB < ncols || ldU < rank || ldV < rank)
+    return fail(ctx, HYDOT_ERR_ARG, "bad sketch factor shapes");
+  std::vector<double> G, lam, UB;
+  int rc = gram(ctx, Bt, nb, ldB, ncols, G);
+  if (rc) return rc;
+  eig_desc(G, ncols, lam, UB);
+  std::vector<float> WV((size_t)ncols * rank, 0.f), WU((size_t)ncols * rank, 0.f);
+  for (int j = 0; j < rank; ++j) {
+    const double sj = std::sqrt(std::max(lam[j], 0.0));
+    S[j] = sj;
+    for (int i = 0; i < ncols; ++i) {
+      WU[(size_t)i * rank + j] = (float)UB[(size_t)i * ncols + j];
+      WV[(size_t)i * rank + j] = sj > 0.0 ? (float)(UB[(size_t)i * ncols + j] / sj) : 0.f;
+    }
+  }
+  rc = right_mul(ctx, Bt, nb, ldB, ncols, WV, rank, V, ldV);
+  if (!rc) rc = right_mul(ctx, Q, rows, ldQ, ncols, WU, rank, U, ldU);
+  return rc;
 }
 
 }  // namespace hydot

@@ -99,3 +99,30 @@ def test_sketch_project_pass_accumulates_over_slices(lib, case):
                 ref_i[c * N:(c + 1) * N] += -h3 * A.T @ Bq
     err_i = np.abs(Bt - ref_i).max(axis=0) / np.abs(ref_i).max(axis=0)
     assert err_i.max() <= 2e-3, err_i.max()
+
+
+def test_rank_r_factorisation_near_optimal(lib, case):
+    """Full pipeline (range, orthonormalisation, projection over two row blocks, recompression):
+    the error of U S V^T is within a small factor of the exact optimum sigma_(r+1) plus the BF16
+    floor, the factors are orthonormal, and the leading singular values match J's."""
+    from paper_1410_0986_gb300.sketch import born_sketch, chunk_rows
+
+    p, rs, rd = case
+    N, nc = p.grid.N, p.n_chrom
+    rank, over = 200, 20
+    om = workloads.gaussian(33, (nc, rank + over, N)).astype(np.float32)
+    chunks = [(0, 1), (1, 2)]
+    with lib.Context.from_problem(p, precision="mixed", tol=1e-8, tol_cw=0.0) as ctx:
+        ps, pd = torch.tensor(rs, device="cuda"), torch.tensor(rd, device="cuda")
+        U, S, V, kept = born_sketch(ctx, chunks, torch.tensor(om, device="cuda").to(torch.bfloat16), rank, over,
+                                    lambda l0, nl: (ps[l0:l0 + nl].contiguous(), pd[l0:l0 + nl].contiguous()))
+        rows = chunk_rows(ctx, chunks)
+        U, V = U.cpu().double().numpy(), V.cpu().double().numpy()
+    J = oborn.born_matrix(p, rs.astype(np.float64), rd.astype(np.float64))[rows]
+    sig = np.linalg.svd(J, compute_uv=False)
+    assert kept == rank + over
+    assert np.abs(U.T @ U - np.eye(rank)).max() < 1e-3
+    assert np.abs(V.T @ V - np.eye(rank)).max() < 1e-2
+    assert np.abs(S[:20] / sig[:20] - 1).max() < 1e-2
+    err = np.linalg.norm(J - (U * S) @ V.T, 2)
+    assert err <= 10 * sig[rank] + 1e-2 * sig[0], (err / sig[0], sig[rank] / sig[0])
