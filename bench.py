@@ -46,7 +46,9 @@ WORKLOAD = ("cw-mixed-64x64x48: 64x64x48 grid (h=2 mm), 32 sources + 32 detector
             "(8,192 field solves), explicit FP32 Born rows 131,072 x 786,432 in row chunks, J x and J^T r")
 KERNEL_NAMES = {"dir": "k_dir_tma (inner PCG pass 1)", "update": "k_update_tma (inner PCG pass 2)",
                 "residual": "k_residual (FP64 residual)", "born_rows": "k_born_rows (Born-row assembly)",
-                "apply": "k_apply_partial+reduce (J x)", "apply_T": "k_apply_T_partial+reduce (J^T y)"}
+                "apply": "k_apply_partial+reduce (J x)", "apply_T": "k_apply_T_partial+reduce (J^T y)",
+                "sketch_range": "k_sketch_gemm<0> (tensor-core Y = J Omega)",
+                "sketch_project": "k_sketch_gemm<1> (tensor-core B^T += J^T Q)"}
 # DRAM bytes (read + write, ncu) per algorithmic byte, from the captures summarised under profiles/
 # (smaller cases of the same kernels, scaled by the units processed: active fields or rows)
 DRAM_PER_ALGORITHMIC_BYTE = {"dir": (100.96e6 + 24.81e6) / (64 * 3 * 196608 * 4),
@@ -310,7 +312,7 @@ def run_ours(args):
                                       "gbs": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 else None,
                                       "hbm_frac": ((v["bytes"] / (v["ms"] / 1e3) / 1e9) / pk["hbm_gbs"])
                                       if v["ms"] > 0 else None}
-                    for k, v in kstats.items()},
+                    for k, v in kstats.items() if v["launches"] > 0},
         "rates": {
             "born_rows_per_s": K * Mc * world / (sum(phase["assemble"]) / 1e3),
             "grads_per_s": (K / nchunk) / (sum(phase["apply_T"]) / 1e3),
@@ -354,14 +356,73 @@ def run_ours(args):
                       "h2d_bytes_per_step": int(xh.numel() * 4), "d2h_bytes_per_step": int((Mc + nc * N) * 4),
                       "steps": args.e2e_steps}
     # the plain FP64 GPU solve against the mixed form, both to a field error of 1e-6 (norm-wise)
+    ctx.close()
+    del ps, pd, J
+    torch.cuda.empty_cache()
     if args.compare_fp64 and rank == 0:
         out["fp64_vs_mixed_at_1e-6"] = compare_fp64(hd, p)
         out["deflation"] = compare_deflation(hd, p)
+    if rank == 0 and not args.no_sketch:
+        out["sketch"] = sketch_phase(hd, pk)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_entry(run_cpu_sample(0))
-    ctx.close()
     if rank == 0:
         print(json.dumps(out))
+
+
+def sketch_phase(hd, pk, n_lam=4, rank=200, over=20, n_probe=32):
+    """Rank-200 randomised sketch of J on a wavelength chunk of the 128x128x96 / 64+64-optode /
+    512-wavelength workload (Appendix A.1): fields solved on the GPU, both tensor-core passes,
+    orthonormalisation and recompression, and the error of U S V^T against the exact implicit J x
+    on seeded Gaussian probes."""
+    import numpy as np
+    import torch
+
+    import workloads
+    from paper_1410_0986_gb300.sketch import born_sketch
+
+    p = workloads.config(5)
+    N, nc = p.grid.N, p.n_chrom
+    out = {"workload": f"128x128x96 (h=1 mm), 64+64 optodes, wavelengths 0-{n_lam - 1} of 512: "
+                       f"J chunk {64 * 64 * n_lam} x {nc * N}, rank {rank} + {over}"}
+    with hd.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=TOL_CW, cw_floor=CW_FLOOR,
+                                 max_lambda_per_call=n_lam) as ctx:
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        ps, pd, st = ctx.solve_fields(0, n_lam)
+        b.record()
+        torch.cuda.synchronize()
+        out["fields"] = {"solves": st["n_fields"], "solves_per_s": st["n_fields"] / (a.elapsed_time(b) / 1e3),
+                         "iters_mean": st["iters_mean"], "cycles_max": st["cycles_max"]}
+        gen = torch.Generator(device="cuda").manual_seed(workloads.SEED_BASE + 5)
+        om = torch.randn(nc, rank + over, N, device="cuda", generator=gen).to(torch.bfloat16)
+        ctx.set_kernel_timing(True)
+        t0 = time.perf_counter()
+        U, S, V, kept = born_sketch(ctx, [(0, n_lam)], om, rank, over, lambda l0, nl: (ps, pd))
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        ks = ctx.kernel_stats()
+        ctx.set_kernel_timing(False)
+        del om
+        X = torch.randn(nc * N, n_probe, device="cuda", generator=gen)
+        errs = []
+        for q in range(n_probe):
+            jx = ctx.born_apply(ps, pd, 0, n_lam, X[:, q].contiguous()).double()
+            lr = (U.double() @ (torch.tensor(S, device="cuda") * (V.double().T @ X[:, q].double())))
+            errs.append(float((jx - lr).norm() / jx.norm()))
+    for name, key in (("range", "sketch_range"), ("project", "sketch_project")):
+        k = ks[key]
+        tf = k["bytes"] / (k["ms"] / 1e3) / 1e12 if k["ms"] > 0 else None
+        out[name] = {"ms": k["ms"], "launches": k["launches"], "algorithmic_tflop": k["bytes"] / 1e12,
+                     "tflops": tf, "peak_tflops": pk["bf16_tflops"], "frac": tf / pk["bf16_tflops"] if tf else None}
+    # the projection pass issues one MMA pass per chromophore: executed = n_chrom x algorithmic flops
+    out["project"]["executed_over_algorithmic"] = nc
+    out["wall_s"] = wall
+    out["kept_directions"] = kept
+    out["singular_values"] = {"s1": float(S[0]), "s200": float(S[rank - 1])}
+    out["probe_error"] = {"max": max(errs), "median": float(np.median(errs)), "n": n_probe}
+    return out
 
 
 def compare_deflation(hd, p, k=16):
@@ -415,6 +476,7 @@ def run_kernel_case(name: str, reps: int = 3):
     """A small, bounded case of one hot kernel on the workload's grid, for profiler captures:
     born_rows   512 rows of one 16-wavelength chunk (1.6 GB written per launch)
     solver      the 64 fields of one wavelength (FP32 PCG + FP64 refinement, ~300 MB of vectors)
+    sketch      the tensor-core range pass Y = J Omega over one 16-wavelength chunk (rank 200 + 20)
     apply       J x and J^T r over one 16-wavelength chunk of fields
     """
     import torch
@@ -441,6 +503,10 @@ def run_kernel_case(name: str, reps: int = 3):
         elif name == "solver":
             a.record()
             ctx.solve_fields(0, 1, ps, pd)
+        elif name == "sketch":
+            om = torch.randn(nc, 220, N, device="cuda", generator=gen).to(torch.bfloat16) if not times else om
+            a.record()
+            ctx.sketch_range(ps, pd, 0, CHUNK, om, 220)
         elif name == "apply":
             x = torch.rand(nc * N, device="cuda", generator=gen)
             a.record()
@@ -489,6 +555,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=4)
     ap.add_argument("--deflation-k", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sketch", action="store_true")
     ap.add_argument("--no-compare-fp64", dest="compare_fp64", action="store_false")
     ap.add_argument("--cpu-sample", type=int, default=None, help=argparse.SUPPRESS)
     ap.add_argument("--kernel-case", default=None, help="born_rows | solver | apply: small profiling case")
