@@ -20,10 +20,10 @@
 // Scalars are never stored: every block of a field sums the per-tile partials of the previous
 // pass in the same fixed order, so all blocks agree bit for bit and the result is reproducible.
 #include <algorithm>
-#include <type_traits>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <type_traits>
 #include <cudaTypedefs.h>
 
 #include "hydot_internal.cuh"
@@ -560,23 +560,61 @@ __device__ __forceinline__ bool stage_ready(uint64_t* mbar, int s, int u, int* e
   return *s_ok != 0;
 }
 
-__global__ void __launch_bounds__(NTHREADS) k_dir_tma(Geo g, Batch b, int it, const LamCoefF* __restrict__ coef_f,
-                                                      const __grid_constant__ CUtensorMap mapR,
-                                                      const __grid_constant__ CUtensorMap mapPold,
-                                                      float* __restrict__ Pnew) {
+// Pass 1 with a rolling window of planes. A block owns a (field, x-tile, y-tile, z-segment)
+// column; r and p_old arrive by TMA in slabs of RP planes (box 40 x 10 x RP: the tile plus its
+// one-cell x-y halo, x rounded out to x0-4 for the 16-byte rule; no z-halo), RS slab buffers.
+// Per slab: (B) p_new = D^-1 r + beta p_old is formed once per cell of the tile and its x-y
+// halo, in place over r; a barrier; (D) the stencil runs on the planes whose upper neighbour is
+// now formed (the slab's planes shifted down by one, the first of them in the previous slab's
+// buffer). The z-neighbours of a cell are the same thread's values of the adjacent planes, kept
+// in registers. A slab buffer is refilled at the barrier after its last read, so RS - 2 slabs
+// are in flight while a slab is processed. The diagonal and its inverse depend on the cell only
+// through its face mask: each thread precomputes them for its column and its halo cell (four z
+// cases: interior, bottom, top, both).
+constexpr int RP = 4;                 // planes per slab
+constexpr int RS = 4;                 // slab buffers
+constexpr int PLN = BXT * BYT;        // floats in one box plane
+constexpr uint32_t SLAB_BYTES = RP * PLN * 4;
+constexpr size_t roll_smem() { return (size_t)RS * 2 * SLAB_BYTES + 128; }
+
+__device__ __forceinline__ void col_diag(const LamCoefF& cf, int mxy, float (&d)[4], float (&di)[4]) {
+#pragma unroll
+  for (int zb = 0; zb < 4; ++zb) {
+    const int m = mxy | ((zb & 1) << 4) | ((zb >> 1) << 5);
+    d[zb] = m ? diag_f(cf, m) : cf.dint;
+    di[zb] = m ? 1.f / d[zb] : cf.idint;
+  }
+}
+// v[zb] with selects (a dynamic index would put the array in local memory)
+__device__ __forceinline__ float pick4(const float (&v)[4], int zb) {
+  return zb == 0 ? v[0] : (zb == 1 ? v[1] : (zb == 2 ? v[2] : v[3]));
+}
+
+__global__ void __launch_bounds__(NTHREADS, 4) k_dir_roll(Geo g, Batch b, int it, int seg,
+                                                          const LamCoefF* __restrict__ coef_f,
+                                                          const __grid_constant__ CUtensorMap mapR,
+                                                          const __grid_constant__ CUtensorMap mapPold,
+                                                          float* __restrict__ Pnew) {
   extern __shared__ unsigned char dsm[];
-  float* buf = align128(dsm);  // [2 stages][r box, p_old box]
-  __shared__ uint64_t mbar[2];
+  float* slab = align128(dsm);  // [RS][r -> p_new, p_old][RP planes]
+  __shared__ uint64_t mbar[RS];
   __shared__ double sm[96];
   __shared__ float s_beta;
-  __shared__ int s_go, s_ok;
-  const ColCoord c = col_coord(g);
+  __shared__ int s_go;
+  const int ncol = g.ntx * g.nty;
+  const int nseg = (g.nz + seg - 1) / seg;
+  const int rhs = blockIdx.x / (ncol * nseg);
+  const int rem = blockIdx.x - rhs * ncol * nseg;
+  const int zs = rem / ncol, col = rem - zs * ncol;
+  const int x0 = (col % g.ntx) * TX, y0 = (col / g.ntx) * TY;
+  const int z0 = zs * seg, z1 = min(z0 + seg, g.nz);
+  const bool lead = (col == 0 && zs == 0);
   const int T_ = g.ntiles;
-  double* pb = b.part + (size_t)c.rhs * part_stride(T_);
+  double* pb = b.part + (size_t)rhs * part_stride(T_);
   const int par = it & 1;
   const bool first = (it == 0);
   if (threadIdx.x < 32) {
-    const int st = b.status[c.rhs];
+    const int st = b.status[rhs];
     double v0 = 0.0, v1 = 0.0, v2 = 0.0;
     if (st == RHS_INNER)
       for (int t = threadIdx.x; t < T_; t += 32) {
@@ -591,14 +629,14 @@ __global__ void __launch_bounds__(NTHREADS) k_dir_tma(Geo g, Batch b, int it, co
       int go = 0;
       float beta = 0.f;
       if (st == RHS_INNER) {
-        const bool done = v1 <= b.tol_in2 * b.rr0[c.rhs] || it >= b.max_inner || b.iters[c.rhs] >= b.max_iter ||
+        const bool done = v1 <= b.tol_in2 * b.rr0[rhs] || it >= b.max_inner || b.iters[rhs] >= b.max_iter ||
                           v1 == 0.0;
         if (done) {
-          if (c.slot0 == 0) b.status[c.rhs] = RHS_FINISHED;
+          if (lead) b.status[rhs] = RHS_FINISHED;
         } else {
           go = 1;
           beta = first ? 0.f : (float)(v0 / v2);
-          if (c.slot0 == 0) atomicAdd(&b.counter[1 + it], 1);
+          if (lead) atomicAdd(&b.counter[1 + it], 1);
         }
       }
       s_go = go;
@@ -608,82 +646,126 @@ __global__ void __launch_bounds__(NTHREADS) k_dir_tma(Geo g, Batch b, int it, co
   __syncthreads();
   if (!s_go) return;
   const float beta = s_beta;
-  const LamCoefF cf = coef_f[rhs_lambda(b, c.rhs)];
-  const int nbox = first ? 1 : 2;
+  const LamCoefF cf = coef_f[rhs_lambda(b, rhs)];
+  const int np = z1 - z0 + 2;  // planes z0-1 .. z1 (t = plane - (z0 - 1))
+  const int nslab = (np + RP - 1) / RP;
+  const uint32_t tx_bytes = (first ? 1u : 2u) * SLAB_BYTES;
   if (threadIdx.x == 0) {
-    mbar_init(&mbar[0], 1);
-    mbar_init(&mbar[1], 1);
+    for (int q = 0; q < RS; ++q) mbar_init(&mbar[q], 1);
     mbar_fence_init();
   }
   __syncthreads();
-  auto issue = [&](int tz) {
-    float* dst = buf + (tz & 1) * 2 * BOXN;
-    mbar_expect_tx(&mbar[tz & 1], nbox * BOX_BYTES);
-    tma_load_4d(dst, &mapR, &mbar[tz & 1], c.x0 - 4, c.y0 - 1, tz * TZT - 1, c.rhs);
-    if (!first) tma_load_4d(dst + BOXN, &mapPold, &mbar[tz & 1], c.x0 - 4, c.y0 - 1, tz * TZT - 1, c.rhs);
+  auto issue = [&](int q) {
+    float* dst = slab + (q % RS) * 2 * RP * PLN;
+    mbar_expect_tx(&mbar[q % RS], tx_bytes);
+    tma_load_4d(dst, &mapR, &mbar[q % RS], x0 - 4, y0 - 1, z0 - 1 + q * RP, rhs);
+    if (!first) tma_load_4d(dst + RP * PLN, &mapPold, &mbar[q % RS], x0 - 4, y0 - 1, z0 - 1 + q * RP, rhs);
   };
-  if (threadIdx.x == 0) issue(0);
-  float acc = 0.f;
-  float* out = Pnew + (size_t)c.rhs * g.N;
-  const int lx = threadIdx.x % TX + 4, ly = threadIdx.x / TX + 1;
-  for (int tz = 0; tz < g.ntz; ++tz) {
-    if (threadIdx.x == 0 && tz + 1 < g.ntz) issue(tz + 1);
-    if (!stage_ready(mbar, tz & 1, tz >> 1, b.err, &s_ok)) {
-      if (threadIdx.x == 0 && tz + 1 < g.ntz) mbar_wait_bounded(&mbar[(tz + 1) & 1], (uint32_t)(((tz + 1) >> 1) & 1));
+  if (threadIdx.x == 0)
+    for (int q = 0; q < min(RS, nslab); ++q) issue(q);
+
+  // own column and halo cell of this thread
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int i = x0 + tx, j = y0 + ty;
+  const bool in = (i < g.nx) && (j < g.ny);
+  const int ob = (ty + 1) * BXT + tx + 4;
+  float dd[4], di[4];
+  col_diag(cf, (i == 0) | ((i == g.nx - 1) << 1) | ((j == 0) << 2) | ((j == g.ny - 1) << 3), dd, di);
+  // halo: threads 0..63 take the rows y0-1 and y0+8, threads 64..79 the columns x0-1 and x0+32
+  const int h = threadIdx.x;
+  const bool has_halo = h < 2 * TX + 2 * TY;
+  int hb = 0;
+  float hdi[4] = {0.f, 0.f, 0.f, 0.f};
+  if (has_halo) {
+    int hx, hy;
+    if (h < 2 * TX) {
+      hx = h % TX;
+      hy = (h < TX) ? -1 : TY;
+    } else {
+      hx = (h - 2 * TX < TY) ? -1 : TX;
+      hy = (h - 2 * TX) % TY;
+    }
+    hb = (hy + 1) * BXT + hx + 4;
+    const int gi = x0 + hx, gj = y0 + hy;
+    float hd[4];
+    col_diag(cf, (gi == 0) | ((gi == g.nx - 1) << 1) | ((gj == 0) << 2) | ((gj == g.ny - 1) << 3), hd, hdi);
+  }
+  const int plane_n = g.nx * g.ny;
+  float* out = Pnew + (size_t)rhs * g.N + (size_t)j * g.nx + i;
+  float acc = 0.f, pm2 = 0.f, pm1 = 0.f;  // own p_new of the previous slab's last two planes
+  const float* prev = slab;               // previous slab's p_new planes
+  for (int q = 0; q < nslab; ++q) {
+    float* cur = slab + (q % RS) * 2 * RP * PLN;
+    const bool ok = mbar_wait_bounded(&mbar[q % RS], (uint32_t)((q / RS) & 1));
+    const int t0 = q * RP;
+    const int a0 = z0 - 1 + t0;  // first plane formed from this slab
+    float pv[RP];
+    // (B) p_new in place; slabs without a grid z-face take the interior diagonal
+    auto form = [&](auto edge) {
+#pragma unroll
+      for (int u = 0; u < RP; ++u) {
+        int zb = 0;
+        if constexpr (decltype(edge)::value) zb = (a0 + u == 0) | ((a0 + u == g.nz - 1) << 1);
+        float* pl = cur + u * PLN;
+        float v = pl[ob] * (decltype(edge)::value ? pick4(di, zb) : di[0]);
+        if (!first) v = fmaf(beta, pl[RP * PLN + ob], v);
+        pl[ob] = v;
+        pv[u] = v;
+        if (has_halo) {
+          float hv = pl[hb] * (decltype(edge)::value ? pick4(hdi, zb) : hdi[0]);
+          if (!first) hv = fmaf(beta, pl[RP * PLN + hb], hv);
+          pl[hb] = hv;
+        }
+      }
+    };
+    if (a0 <= 0 || a0 + RP - 1 >= g.nz - 1) form(std::true_type{});
+    else form(std::false_type{});
+    // the in-place writes are ordered before the copy that later refills this buffer
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (!__syncthreads_and(ok)) {
+      // a slab never arrived: flag it, wait (bounded) for the copies issued so far, return
+      if (threadIdx.x == 0) {
+        atomicExch(b.err, 1);
+        const int last = min(max(RS - 1, q + RS - 3), nslab - 1);
+        for (int u = q; u <= last; ++u) mbar_wait_bounded(&mbar[u % RS], (uint32_t)((u / RS) & 1));
+      }
       return;
     }
-    float* bR = buf + (tz & 1) * 2 * BOXN;
-    const float* bP = bR + BOXN;
-    const int z0 = tz * TZT;
-    // p_new = D^-1 r + beta p_old on the box columns x0-1 .. x0+32, in place. Pass A: each warp
-    // takes whole (y, z) rows of the 32 own columns (consecutive words: no bank conflicts);
-    // pass B: the two x-halo columns.
-    {
-      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-      const int gi = c.x0 + lane;
-      const int xbits = (gi == 0) | ((gi == g.nx - 1) << 1);
-      for (int row = warp; row < BYT * BZT; row += NWARPS) {
-        const int jl = row % BYT, kl = row / BYT;
-        const int gj = c.y0 - 1 + jl, gk = z0 - 1 + kl;
-        const int m = xbits | ((gj == 0) << 2) | ((gj == g.ny - 1) << 3) | ((gk == 0) << 4) | ((gk == g.nz - 1) << 5);
-        const int bi = row * BXT + 4 + lane;
-        const float zv = bR[bi] * (m ? 1.f / diag_f(cf, m) : cf.idint);
-        bR[bi] = first ? zv : fmaf(beta, bP[bi], zv);
+    // every thread is past the stencils that read slab q - 2: refill its buffer
+    if (threadIdx.x == 0 && q >= 2 && q - 2 + RS < nslab) issue(q - 2 + RS);
+    // (D) stencils of the planes t0 - 1 .. t0 + RP - 2 (plane t0 - 1 lies in the previous slab)
+    auto stencil = [&](auto edge) {
+      float* o = out + (ptrdiff_t)(a0 - 1) * plane_n;
+#pragma unroll
+      for (int u = 0; u < RP; ++u) {
+        const int c = a0 - 1 + u;
+        float d = dd[0];
+        if constexpr (decltype(edge)::value) {
+          if (c < z0 || c >= z1) continue;
+          d = pick4(dd, (c == 0) | ((c == g.nz - 1) << 1));
+        }
+        const float* pl = (u == 0) ? prev + (RP - 1) * PLN : cur + (u - 1) * PLN;
+        const float below = (u == 0) ? pm2 : (u == 1 ? pm1 : pv[u - 2]);
+        const float centre = (u == 0) ? pm1 : pv[u - 1];
+        const float sn = (pl[ob - 1] + pl[ob + 1]) + (pl[ob - BXT] + pl[ob + BXT]) + (below + pv[u]);
+        acc = fmaf(centre, d * centre - sn, acc);
+        o[u * plane_n] = centre;
       }
-      for (int q = threadIdx.x; q < 2 * BYT * BZT; q += NTHREADS) {
-        const int row = q >> 1, il = (q & 1) ? 36 : 3;
-        const int jl = row % BYT, kl = row / BYT;
-        const int bi = row * BXT + il;
-        const int m = face_mask(g, c.x0 - 4 + il, c.y0 - 1 + jl, z0 - 1 + kl);
-        const float zv = bR[bi] * (m ? 1.f / diag_f(cf, m) : cf.idint);
-        bR[bi] = first ? zv : fmaf(beta, bP[bi], zv);
-      }
+    };
+    if (in) {
+      if (a0 - 1 < max(z0, 1) || a0 + RP - 2 > min(z1 - 1, g.nz - 2)) stencil(std::true_type{});
+      else stencil(std::false_type{});
     }
-    __syncthreads();
-    if (c.in) {
-      const int cb = ly * BXT + lx;  // (y, x) offset of this thread's column in a plane
-      float pm = bR[cb], pc = bR[BXT * BYT + cb];
-      for (int kk = 0; kk < TZT; ++kk) {
-        const int k = z0 + kk;
-        if (k >= g.nz) break;
-        const int ci = (kk + 1) * BXT * BYT + cb;
-        const float pp = bR[ci + BXT * BYT];
-        const float sn = (bR[ci - 1] + bR[ci + 1]) + (bR[ci - BXT] + bR[ci + BXT]) + (pm + pp);
-        const int m = face_mask(g, c.i, c.j, k);
-        const float q = (m ? diag_f(cf, m) : cf.dint) * pc - sn;
-        acc = fmaf(pc, q, acc);
-        out[vidx(g, c.i, c.j, k)] = pc;
-        pm = pc;
-        pc = pp;
-      }
-    }
-    __syncthreads();  // stage tz & 1 is free for tile tz + 2
+    pm2 = pv[RP - 2];
+    pm1 = pv[RP - 1];
+    prev = cur;
   }
   float a1[1] = {acc};
   double o1[1];
   block_sum<1, float>(a1, o1, sm);
-  if (threadIdx.x < g.ntz) {
-    const int slot = c.slot0 + threadIdx.x * g.ntx * g.nty;
+  const int nsl = (z1 - z0 + g.tz - 1) / g.tz;
+  if (threadIdx.x < nsl) {
+    const int slot = col + (z0 / g.tz + threadIdx.x) * ncol;
     pb[6 * T_ + 2 * slot] = threadIdx.x == 0 ? o1[0] : 0.0;
     pb[6 * T_ + 2 * slot + 1] = 0.0;
   }
@@ -945,8 +1027,10 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
           if (ctx->use_tma) {
             const unsigned ncb = (unsigned)((long long)b.nrhs * g.ntx * g.nty);
             cudaEvent_t t0 = timer_begin(ctx);
-            k_dir_tma<<<ncb, blk, tma_smem(4), s>>>(g, b, it, ctx->d_coef_f, ctx->tm_r, ctx->tm_p[it & 1],
-                                                    P[(it + 1) & 1]);
+            const int seg = ctx->dir_seg;
+            const unsigned nrb = (unsigned)((long long)ncb * ((g.nz + seg - 1) / seg));
+            k_dir_roll<<<nrb, blk, roll_smem(), s>>>(g, b, it, seg, ctx->d_coef_f, ctx->tm_r4, ctx->tm_p4[it & 1],
+                                                     P[(it + 1) & 1]);
             ++ctx->launches;
             timer_end(ctx, t0, HYDOT_KERNEL_DIR, 0.0);
             t0 = timer_begin(ctx);
@@ -1055,8 +1139,9 @@ bool getenv_flag(const char* name) {
   return v && *v && std::strcmp(v, "0") != 0;
 }
 
-// 4-D tensor map {nx, ny, nz, max_fields} of an FP32 field buffer, box = one TMA tile with halo.
-int encode_field_map(hydot_ctx* ctx, void* base, CUtensorMap* map) {
+// 4-D tensor map {nx, ny, nz, max_fields} of an FP32 field buffer; box 40 x 10 x bz (a 32 x 8 tile
+// with its x-y halo, bz planes).
+int encode_field_map(hydot_ctx* ctx, void* base, CUtensorMap* map, int bz) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     void* fn = nullptr;
@@ -1069,7 +1154,7 @@ int encode_field_map(hydot_ctx* ctx, void* base, CUtensorMap* map) {
   const cuuint64_t nx = ctx->nx, ny = ctx->ny, nz = ctx->nz, F = ctx->max_fields;
   cuuint64_t dims[4] = {nx, ny, nz, F};
   cuuint64_t strides[3] = {nx * 4, nx * ny * 4, nx * ny * nz * 4};
-  cuuint32_t box[4] = {(cuuint32_t)BXT, (cuuint32_t)BYT, (cuuint32_t)BZT, 1};
+  cuuint32_t box[4] = {(cuuint32_t)BXT, (cuuint32_t)BYT, (cuuint32_t)bz, 1};
   cuuint32_t estr[4] = {1, 1, 1, 1};
   CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, estr,
                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -1117,12 +1202,21 @@ int solver_alloc(hydot_ctx* ctx) {
   HYDOT_CUDA_TRY(ctx, cudaMalloc(&ctx->d_err, sizeof(int)));
   HYDOT_CUDA_TRY(ctx, cudaMemset(ctx->d_err, 0, sizeof(int)));
   if (ctx->use_tma) {
-    HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(k_dir_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem(4)));
+    HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(k_dir_roll, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)roll_smem()));
     HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(k_update_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem(2)));
-    int rc = encode_field_map(ctx, ctx->d_r, &ctx->tm_r);
-    if (!rc) rc = encode_field_map(ctx, ctx->d_p[0], &ctx->tm_p[0]);
-    if (!rc) rc = encode_field_map(ctx, ctx->d_p[1], &ctx->tm_p[1]);
+    int rc = encode_field_map(ctx, ctx->d_r, &ctx->tm_r, BZT);
+    if (!rc) rc = encode_field_map(ctx, ctx->d_p[0], &ctx->tm_p[0], BZT);
+    if (!rc) rc = encode_field_map(ctx, ctx->d_p[1], &ctx->tm_p[1], BZT);
+    if (!rc) rc = encode_field_map(ctx, ctx->d_r, &ctx->tm_r4, RP);
+    if (!rc) rc = encode_field_map(ctx, ctx->d_p[0], &ctx->tm_p4[0], RP);
+    if (!rc) rc = encode_field_map(ctx, ctx->d_p[1], &ctx->tm_p4[1], RP);
     if (rc) return rc;
+    // whole columns unless the blocks of one wavelength's fields would leave most SMs idle
+    ctx->dir_seg = t.ntz * t.tz;
+    if (const char* v = std::getenv("HYDOT_DIR_SEG")) {
+      const int want = std::atoi(v);
+      if (want > 0) ctx->dir_seg = std::max(t.tz, (want + t.tz - 1) / t.tz * t.tz);
+    }
   }
   return HYDOT_OK;
 }
