@@ -183,8 +183,9 @@ struct hydot_ctx {
   int* h_pinned = nullptr;   // pinned host words for polling
   int* d_err = nullptr;      // set by a kernel whose bounded wait gave up
   bool use_tma = false;      // FP32 real inner kernels with TMA tile loads (nx % 4 == 0)
-  CUtensorMap tm_r{}, tm_p[2]{};  // 4-D maps {nx, ny, nz, max_fields} of d_r, d_p[0], d_p[1] (halo tiles)
-  CUtensorMap tm_r4{}, tm_p4[2]{};  // the same buffers in plane slabs for the rolling pass-1 kernel
+  // 4-D maps {nx, ny, nz, max_fields}: d_r, d_p[0], d_p[1] in slabs with the x-y halo (40 x 10 x 4),
+  // d_e and d_r in slabs of the tile alone (32 x 8 x 4)
+  CUtensorMap tm_r4{}, tm_p4[2]{}, tm_e4{}, tm_r4v{};
   int dir_seg = 0;           // z-planes per block of the rolling pass-1 kernel (multiple of the tile depth)
   // deflation (recycled subspace): W [k][N] FP64 and the k x k Gram blocks
   double* d_W = nullptr;

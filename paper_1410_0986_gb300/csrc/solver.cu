@@ -500,45 +500,20 @@ __global__ void __launch_bounds__(NTHREADS) k_update(Geo g, Batch b, int it, T* 
   }
 }
 
-// ---------------------------------------------------------------- inner K_A / K_B with TMA tiles
-// FP32 real fields whose row pitch is a multiple of 16 bytes. A block owns a 32 x 8 x TZT tile;
-// one thread issues a 4-D TMA load of the tile plus a one-cell halo (rounded out to x0-4 so the
-// x coordinate stays 16-byte aligned) into shared memory; cells outside the grid arrive as zeros,
-// so the stencil adds its six neighbours without branches (the Robin/Dirichlet faces live in the
-// diagonal). The wait on the mbarrier is bounded: on timeout the block flags b.err, waits
-// (bounded) for its copy to land and returns.
-constexpr int TZT = 8;
-constexpr int BXT = 40, BYT = 10, BZT = TZT + 2;
-constexpr int BOXN = BXT * BYT * BZT;
-constexpr uint32_t BOX_BYTES = BOXN * 4;
-constexpr size_t tma_smem(int nbox) { return (size_t)nbox * BOX_BYTES + 128; }
+// ---------------------------------------------------------------- inner passes with TMA slabs
+// FP32 real fields whose row pitch is a multiple of 16 bytes (nx % 4 == 0). Tiles are 32 x 8 cells
+// in x-y; TMA copies bring planes of a tile plus its one-cell x-y halo (x rounded out to x0 - 4 so
+// the x coordinate stays 16-byte aligned); cells outside the grid arrive as zeros, so the stencil
+// adds its six neighbours without branches (the Robin/Dirichlet faces live in the diagonal).
+// Every wait on an mbarrier is bounded: on timeout the block flags b.err, waits (bounded) for the
+// copies it issued and returns. The partial sums of a block go to the slot of its first 8-plane
+// tile and zeros to the others (the per-tile layout of the partials is shared with the generic
+// kernels). Per-field scalars (convergence, alpha, beta) are formed once per block by one lane.
+constexpr int TZT = 8;               // planes per partial-sum tile on this path
+constexpr int BXT = 40, BYT = 10;    // x-y extent of a halo box
 
 __device__ __forceinline__ float* align128(unsigned char* p) {
   return reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(p) + 127) & ~uintptr_t(127));
-}
-
-// A block owns one (field, x-tile, y-tile) column and marches its z-tiles with two TMA stages:
-// the load of tile z+1 is in flight while tile z is computed. Per-field scalars (convergence,
-// alpha, beta) are formed once per block by one lane and broadcast through shared memory, so
-// the FP64 pipe only sums the per-tile partials. The block writes its column's partial sums to
-// the slot of its first z-tile and zeros to the others (the per-tile layout of the partials is
-// shared with the generic kernels).
-struct ColCoord {
-  int rhs, x0, y0, i, j, slot0;
-  bool in;
-};
-__device__ __forceinline__ ColCoord col_coord(const Geo& g) {
-  ColCoord c;
-  const int ncol = g.ntx * g.nty;
-  c.rhs = blockIdx.x / ncol;
-  const int col = blockIdx.x % ncol;
-  c.x0 = (col % g.ntx) * TX;
-  c.y0 = (col / g.ntx) * TY;
-  c.i = c.x0 + threadIdx.x % TX;
-  c.j = c.y0 + threadIdx.x / TX;
-  c.in = (c.i < g.nx) && (c.j < g.ny);
-  c.slot0 = col;  // tile index of (col, z-tile 0)
-  return c;
 }
 
 __device__ __forceinline__ float diag_f(const LamCoefF& cf, int m) {
@@ -547,17 +522,6 @@ __device__ __forceinline__ float diag_f(const LamCoefF& cf, int m) {
   for (int f = 0; f < 6; ++f)
     if (m & (1 << f)) a += cf.fa[f];
   return a;
-}
-
-// Wait for stage s (use number u of that stage). Thread 0 waits, the block learns the outcome.
-__device__ __forceinline__ bool stage_ready(uint64_t* mbar, int s, int u, int* err, int* s_ok) {
-  if (threadIdx.x == 0) {
-    bool ok = mbar_wait_bounded(&mbar[s], (uint32_t)(u & 1));
-    if (!ok) atomicExch(err, 1);
-    *s_ok = ok;
-  }
-  __syncthreads();
-  return *s_ok != 0;
 }
 
 // Pass 1 with a rolling window of planes. A block owns a (field, x-tile, y-tile, z-segment)
@@ -771,22 +735,40 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_dir_roll(Geo g, Batch b, int it
   }
 }
 
-__global__ void __launch_bounds__(NTHREADS, 5) k_update_tma(Geo g, Batch b, int it, const LamCoefF* __restrict__ coef_f,
-                                                            float* __restrict__ E, float* __restrict__ R,
-                                                            const __grid_constant__ CUtensorMap mapP) {
+// Pass 2 with the same rolling window: a slab holds RP planes of p (tile + x-y halo) and of e
+// and r (tile only), all by TMA; the stencil of plane k runs once plane k+1 of p is resident.
+// Threads write nothing to shared memory, so one barrier per slab only guards the refill.
+constexpr uint32_t UP_P = RP * PLN * 4;          // p planes of a slab (bytes)
+constexpr uint32_t UP_V = RP * TX * TY * 4;      // e or r planes of a slab (bytes)
+constexpr uint32_t UP_SLAB = UP_P + 2 * UP_V;
+constexpr size_t upd_smem() { return (size_t)RS * UP_SLAB + 128; }
+
+__global__ void __launch_bounds__(NTHREADS, 3) k_update_roll(Geo g, Batch b, int it, int seg,
+                                                             const LamCoefF* __restrict__ coef_f,
+                                                             float* __restrict__ E, float* __restrict__ R,
+                                                             const __grid_constant__ CUtensorMap mapP,
+                                                             const __grid_constant__ CUtensorMap mapE,
+                                                             const __grid_constant__ CUtensorMap mapR) {
   extern __shared__ unsigned char dsm[];
-  float* buf = align128(dsm);  // [2 stages][p box]
-  __shared__ uint64_t mbar[2];
+  unsigned char* slab = reinterpret_cast<unsigned char*>(align128(dsm));  // [RS][p | e | r]
+  __shared__ uint64_t mbar[RS];
   __shared__ double sm[96];
   __shared__ float s_alpha;
-  __shared__ int s_go, s_ok;
-  const ColCoord c = col_coord(g);
+  __shared__ int s_go;
+  const int ncol = g.ntx * g.nty;
+  const int nseg = (g.nz + seg - 1) / seg;
+  const int rhs = blockIdx.x / (ncol * nseg);
+  const int rem = blockIdx.x - rhs * ncol * nseg;
+  const int zs = rem / ncol, col = rem - zs * ncol;
+  const int x0 = (col % g.ntx) * TX, y0 = (col / g.ntx) * TY;
+  const int z0 = zs * seg, z1 = min(z0 + seg, g.nz);
+  const bool lead = (col == 0 && zs == 0);
   const int T_ = g.ntiles;
-  double* pb = b.part + (size_t)c.rhs * part_stride(T_);
+  double* pb = b.part + (size_t)rhs * part_stride(T_);
   const int par = it & 1;
   const bool first = (it == 0);
   if (threadIdx.x < 32) {
-    const int st = b.status[c.rhs];
+    const int st = b.status[rhs];
     double v0 = 0.0, v1 = 0.0;
     if (st == RHS_INNER)
       for (int t = threadIdx.x; t < T_; t += 32) {
@@ -803,79 +785,104 @@ __global__ void __launch_bounds__(NTHREADS, 5) k_update_tma(Geo g, Batch b, int 
   __syncthreads();
   if (!s_go) return;
   const float alpha = s_alpha;
-  const LamCoefF cf = coef_f[rhs_lambda(b, c.rhs)];
+  const LamCoefF cf = coef_f[rhs_lambda(b, rhs)];
+  const int np = z1 - z0 + 2;
+  const int nslab = (np + RP - 1) / RP;
+  const uint32_t tx_bytes = UP_P + (first ? 1u : 2u) * UP_V;
   if (threadIdx.x == 0) {
-    mbar_init(&mbar[0], 1);
-    mbar_init(&mbar[1], 1);
+    for (int q = 0; q < RS; ++q) mbar_init(&mbar[q], 1);
     mbar_fence_init();
   }
   __syncthreads();
-  auto issue = [&](int tz) {
-    mbar_expect_tx(&mbar[tz & 1], BOX_BYTES);
-    tma_load_4d(buf + (tz & 1) * BOXN, &mapP, &mbar[tz & 1], c.x0 - 4, c.y0 - 1, tz * TZT - 1, c.rhs);
+  auto issue = [&](int q) {
+    unsigned char* dst = slab + (size_t)(q % RS) * UP_SLAB;
+    const int zq = z0 - 1 + q * RP;
+    mbar_expect_tx(&mbar[q % RS], tx_bytes);
+    tma_load_4d(dst, &mapP, &mbar[q % RS], x0 - 4, y0 - 1, zq, rhs);
+    if (!first) tma_load_4d(dst + UP_P, &mapE, &mbar[q % RS], x0, y0, zq, rhs);
+    tma_load_4d(dst + UP_P + UP_V, &mapR, &mbar[q % RS], x0, y0, zq, rhs);
   };
-  if (threadIdx.x == 0) issue(0);
-  float* e = E + (size_t)c.rhs * g.N;
-  float* r = R + (size_t)c.rhs * g.N;
-  const int lx = threadIdx.x % TX + 4, ly = threadIdx.x / TX + 1;
-  float acc[2] = {0.f, 0.f};
-  for (int tz = 0; tz < g.ntz; ++tz) {
-    if (threadIdx.x == 0 && tz + 1 < g.ntz) issue(tz + 1);
-    const int z0 = tz * TZT;
-    const int nk = min(TZT, g.nz - z0);
-    float ev[TZT], rv[TZT];
-    if (c.in) {
-#pragma unroll
-      for (int kk = 0; kk < TZT; ++kk) {
-        if (kk < nk) {
-          const long long id = vidx(g, c.i, c.j, z0 + kk);
-          rv[kk] = r[id];
-          ev[kk] = first ? 0.f : e[id];
-        }
+  if (threadIdx.x == 0)
+    for (int q = 0; q < min(RS, nslab); ++q) issue(q);
+
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int i = x0 + tx, j = y0 + ty;
+  const bool in = (i < g.nx) && (j < g.ny);
+  const int ob = (ty + 1) * BXT + tx + 4;
+  const int ov = threadIdx.x;  // (ty, tx) in an e / r plane
+  float dd[4], di[4];
+  col_diag(cf, (i == 0) | ((i == g.nx - 1) << 1) | ((j == 0) << 2) | ((j == g.ny - 1) << 3), dd, di);
+  const int plane_n = g.nx * g.ny;
+  const size_t base = (size_t)rhs * g.N + (size_t)j * g.nx + i;
+  float acc0 = 0.f, acc1 = 0.f, pm2 = 0.f, pm1 = 0.f;
+  const unsigned char* prev = slab;
+  for (int q = 0; q < nslab; ++q) {
+    const unsigned char* cur = slab + (size_t)(q % RS) * UP_SLAB;
+    const bool ok = mbar_wait_bounded(&mbar[q % RS], (uint32_t)((q / RS) & 1));
+    if (!__syncthreads_and(ok)) {
+      if (threadIdx.x == 0) {
+        atomicExch(b.err, 1);
+        const int last = min(max(RS - 1, q + RS - 3), nslab - 1);
+        for (int u = q; u <= last; ++u) mbar_wait_bounded(&mbar[u % RS], (uint32_t)((u / RS) & 1));
       }
-    }
-    if (!stage_ready(mbar, tz & 1, tz >> 1, b.err, &s_ok)) {
-      if (threadIdx.x == 0 && tz + 1 < g.ntz) mbar_wait_bounded(&mbar[(tz + 1) & 1], (uint32_t)(((tz + 1) >> 1) & 1));
       return;
     }
-    const float* bP = buf + (tz & 1) * BOXN;
-    if (c.in) {
-      const int cb = ly * BXT + lx;
-      float pm = bP[cb], pc = bP[BXT * BYT + cb];
+    // every thread is past the stencils that read slab q - 2: refill its buffer
+    if (threadIdx.x == 0 && q >= 2 && q - 2 + RS < nslab) issue(q - 2 + RS);
+    const int a0 = z0 - 1 + q * RP;
+    const float* cp = reinterpret_cast<const float*>(cur);
+    float pv[RP];
 #pragma unroll
-      for (int kk = 0; kk < TZT; ++kk) {
-        if (kk < nk) {
-          const int k = z0 + kk;
-          const int ci = (kk + 1) * BXT * BYT + cb;
-          const float pp = bP[ci + BXT * BYT];
-          const float sn = (bP[ci - 1] + bP[ci + 1]) + (bP[ci - BXT] + bP[ci + BXT]) + (pm + pp);
-          const int m = face_mask(g, c.i, c.j, k);
-          const float d = m ? diag_f(cf, m) : cf.dint;
-          const float q = d * pc - sn;
-          const float en = fmaf(alpha, pc, ev[kk]);
-          const float rn = fmaf(-alpha, q, rv[kk]);
-          const long long id = vidx(g, c.i, c.j, k);
-          e[id] = en;
-          r[id] = rn;
-          const float zv = rn * (m ? 1.f / d : cf.idint);
-          acc[0] = fmaf(rn, zv, acc[0]);
-          acc[1] = fmaf(rn, rn, acc[1]);
-          pm = pc;
-          pc = pp;
+    for (int u = 0; u < RP; ++u) pv[u] = cp[u * PLN + ob];
+    auto stencil = [&](auto edge) {
+      const size_t o0 = base + (ptrdiff_t)(a0 - 1) * plane_n;
+#pragma unroll
+      for (int u = 0; u < RP; ++u) {
+        const int c = a0 - 1 + u;
+        float d = dd[0], dinv = di[0];
+        if constexpr (decltype(edge)::value) {
+          if (c < z0 || c >= z1) continue;
+          const int zc = (c == 0) | ((c == g.nz - 1) << 1);
+          d = pick4(dd, zc);
+          dinv = pick4(di, zc);
         }
+        const unsigned char* sl = (u == 0) ? prev : cur;
+        const int pu = (u == 0) ? RP - 1 : u - 1;
+        const float* pl = reinterpret_cast<const float*>(sl) + pu * PLN;
+        const float* ev = reinterpret_cast<const float*>(sl + UP_P) + pu * TX * TY;
+        const float* rv = reinterpret_cast<const float*>(sl + UP_P + UP_V) + pu * TX * TY;
+        const float below = (u == 0) ? pm2 : (u == 1 ? pm1 : pv[u - 2]);
+        const float centre = (u == 0) ? pm1 : pv[u - 1];
+        const float sn = (pl[ob - 1] + pl[ob + 1]) + (pl[ob - BXT] + pl[ob + BXT]) + (below + pv[u]);
+        const float qv = d * centre - sn;
+        const float en = first ? alpha * centre : fmaf(alpha, centre, ev[ov]);
+        const float rn = fmaf(-alpha, qv, rv[ov]);
+        const size_t id = o0 + (size_t)u * plane_n;
+        E[id] = en;
+        R[id] = rn;
+        acc0 = fmaf(rn, rn * dinv, acc0);
+        acc1 = fmaf(rn, rn, acc1);
       }
+    };
+    if (in) {
+      if (a0 - 1 < max(z0, 1) || a0 + RP - 2 > min(z1 - 1, g.nz - 2)) stencil(std::true_type{});
+      else stencil(std::false_type{});
     }
-    __syncthreads();  // stage tz & 1 is free for tile tz + 2
+    pm2 = pv[RP - 2];
+    pm1 = pv[RP - 1];
+    prev = cur;
   }
-  double out[2];
-  block_sum<2, float>(acc, out, sm);
-  if (threadIdx.x < g.ntz) {
-    const int slot = c.slot0 + threadIdx.x * g.ntx * g.nty;
+  float accs[2] = {acc0, acc1};
+  double outs[2];
+  block_sum<2, float>(accs, outs, sm);
+  const int nsl = (z1 - z0 + g.tz - 1) / g.tz;
+  if (threadIdx.x < nsl) {
+    const int slot = col + (z0 / g.tz + threadIdx.x) * ncol;
     const bool z = threadIdx.x == 0;
-    pb[2 * T_ * (par ^ 1) + 2 * slot] = z ? out[0] : 0.0;
+    pb[2 * T_ * (par ^ 1) + 2 * slot] = z ? outs[0] : 0.0;
     pb[2 * T_ * (par ^ 1) + 2 * slot + 1] = 0.0;
-    pb[4 * T_ + T_ * (par ^ 1) + slot] = z ? out[1] : 0.0;
-    if (z && c.slot0 == 0) b.iters[c.rhs] += 1;
+    pb[4 * T_ + T_ * (par ^ 1) + slot] = z ? outs[1] : 0.0;
+    if (z && lead) b.iters[rhs] += 1;
   }
 }
 
@@ -1034,7 +1041,8 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
             ++ctx->launches;
             timer_end(ctx, t0, HYDOT_KERNEL_DIR, 0.0);
             t0 = timer_begin(ctx);
-            k_update_tma<<<ncb, blk, tma_smem(2), s>>>(g, b, it, ctx->d_coef_f, E, R, ctx->tm_p[(it + 1) & 1]);
+            k_update_roll<<<nrb, blk, upd_smem(), s>>>(g, b, it, seg, ctx->d_coef_f, E, R, ctx->tm_p4[(it + 1) & 1],
+                                                       ctx->tm_e4, ctx->tm_r4v);
             ++ctx->launches;
             timer_end(ctx, t0, HYDOT_KERNEL_UPDATE, 0.0);
             continue;
@@ -1139,9 +1147,8 @@ bool getenv_flag(const char* name) {
   return v && *v && std::strcmp(v, "0") != 0;
 }
 
-// 4-D tensor map {nx, ny, nz, max_fields} of an FP32 field buffer; box 40 x 10 x bz (a 32 x 8 tile
-// with its x-y halo, bz planes).
-int encode_field_map(hydot_ctx* ctx, void* base, CUtensorMap* map, int bz) {
+// 4-D tensor map {nx, ny, nz, max_fields} of an FP32 field buffer with a bx x by x bz box.
+int encode_field_map(hydot_ctx* ctx, void* base, CUtensorMap* map, int bx, int by, int bz) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     void* fn = nullptr;
@@ -1154,7 +1161,7 @@ int encode_field_map(hydot_ctx* ctx, void* base, CUtensorMap* map, int bz) {
   const cuuint64_t nx = ctx->nx, ny = ctx->ny, nz = ctx->nz, F = ctx->max_fields;
   cuuint64_t dims[4] = {nx, ny, nz, F};
   cuuint64_t strides[3] = {nx * 4, nx * ny * 4, nx * ny * nz * 4};
-  cuuint32_t box[4] = {(cuuint32_t)BXT, (cuuint32_t)BYT, (cuuint32_t)bz, 1};
+  cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz, 1};
   cuuint32_t estr[4] = {1, 1, 1, 1};
   CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, estr,
                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -1203,13 +1210,13 @@ int solver_alloc(hydot_ctx* ctx) {
   HYDOT_CUDA_TRY(ctx, cudaMemset(ctx->d_err, 0, sizeof(int)));
   if (ctx->use_tma) {
     HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(k_dir_roll, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)roll_smem()));
-    HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(k_update_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem(2)));
-    int rc = encode_field_map(ctx, ctx->d_r, &ctx->tm_r, BZT);
-    if (!rc) rc = encode_field_map(ctx, ctx->d_p[0], &ctx->tm_p[0], BZT);
-    if (!rc) rc = encode_field_map(ctx, ctx->d_p[1], &ctx->tm_p[1], BZT);
-    if (!rc) rc = encode_field_map(ctx, ctx->d_r, &ctx->tm_r4, RP);
-    if (!rc) rc = encode_field_map(ctx, ctx->d_p[0], &ctx->tm_p4[0], RP);
-    if (!rc) rc = encode_field_map(ctx, ctx->d_p[1], &ctx->tm_p4[1], RP);
+    HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(k_update_roll, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd_smem()));
+    // halo slabs of r and p (pass 1 reads r and p_old, pass 2 reads p_new), plain slabs of e and r
+    int rc = encode_field_map(ctx, ctx->d_r, &ctx->tm_r4, BXT, BYT, RP);
+    if (!rc) rc = encode_field_map(ctx, ctx->d_p[0], &ctx->tm_p4[0], BXT, BYT, RP);
+    if (!rc) rc = encode_field_map(ctx, ctx->d_p[1], &ctx->tm_p4[1], BXT, BYT, RP);
+    if (!rc) rc = encode_field_map(ctx, ctx->d_e, &ctx->tm_e4, TX, TY, RP);
+    if (!rc) rc = encode_field_map(ctx, ctx->d_r, &ctx->tm_r4v, TX, TY, RP);
     if (rc) return rc;
     // whole columns unless the blocks of one wavelength's fields would leave most SMs idle
     ctx->dir_seg = t.ntz * t.tz;
