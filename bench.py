@@ -325,7 +325,8 @@ def run_ours(args):
                    "iters_max": max(s["iters_max"] for s in stats),
                    "cycles_max": max(s["cycles_max"] for s in stats),
                    "resid_max": max(s["resid_max"] for s in stats), "cw_max": max(s["cw_max"] for s in stats),
-                   "hbm_gbs_at_6NW_per_iteration": solver_gbs, "hbm_frac": solver_gbs / pk["hbm_gbs"]},
+                   "hbm_gbs_at_6NW_per_iteration": solver_gbs, "hbm_frac": solver_gbs / pk["hbm_gbs"],
+                   "autotune": ctx.tuning()},
         "setup_s": t_setup,
         "clocks": clk,
         "gpu_launches": int(n_launch),

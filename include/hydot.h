@@ -195,6 +195,19 @@ int hydot_kernel_stats(hydot_ctx* ctx, int kernel, double* ms, long long* launch
  * caller count the library's launches inside a timed region). */
 long long hydot_kernel_launches(const hydot_ctx* ctx);
 
+/* Autotuning of the inner passes (HYDOT_MIXED, real fields, nx % 4 == 0). The two passes stream
+ * TMA slabs of `planes` z-planes through `buffers` shared-memory buffers; the variants below give
+ * bitwise identical results and differ in data in flight and blocks per SM. While *variant is
+ * -1 the solver times groups of inner iterations with each variant in turn (within the first
+ * solves of the context) and then keeps the fastest per cell-iteration; the environment variable
+ * HYDOT_ROLL_VARIANT=<index> fixes the choice at setup. */
+#define HYDOT_ROLL_VARIANTS 4
+
+/* The chosen variant (-1 while tuning, or when the context does not use these passes) and, for
+ * each variant i < HYDOT_ROLL_VARIANTS, its planes, buffers and measured ns per cell-iteration
+ * (0 if not timed yet). Any output pointer may be NULL; arrays hold HYDOT_ROLL_VARIANTS entries. */
+int hydot_get_tuning(const hydot_ctx* ctx, int* variant, int* planes, int* buffers, double* ns_per_cell);
+
 /* Randomised sketch of J, pass 1 (Appendix A.1, alg:randsvd: Y = A Omega with Gaussian Omega):
  *   Y[r][k] = sum_(c,x) J[r,(c,x)] Omega[(c,x),k]  for the rows r of the slice [lam0, lam0+nlam).
  * omega_t: DEVICE BF16 (raw 16-bit) [n_chrom][ncols][N], Omega transposed per chromophore.

@@ -233,6 +233,16 @@ class Context:
     def kernel_launches(self) -> int:
         return int(self.lib.hydot_kernel_launches(self._ctx))
 
+    def tuning(self) -> dict:
+        """Autotuner state of the inner passes: chosen variant (-1 while tuning) and, per variant,
+        slab planes, slab buffers and measured ns per cell-iteration (0 if not timed)."""
+        n = _lib.ROLL_VARIANTS
+        v = C.c_int(0)
+        planes, bufs, ns = (C.c_int * n)(), (C.c_int * n)(), (C.c_double * n)()
+        self._check(self.lib.hydot_get_tuning(self._ctx, C.byref(v), planes, bufs, ns))
+        return {"variant": v.value, "variants": [{"planes": planes[i], "buffers": bufs[i], "ns_per_cell": ns[i]}
+                                                 for i in range(n)]}
+
     def close(self):
         if getattr(self, "_ctx", None):
             self.lib.hydot_destroy(self._ctx)

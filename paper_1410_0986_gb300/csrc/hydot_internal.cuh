@@ -183,9 +183,17 @@ struct hydot_ctx {
   int* h_pinned = nullptr;   // pinned host words for polling
   int* d_err = nullptr;      // set by a kernel whose bounded wait gave up
   bool use_tma = false;      // FP32 real inner kernels with TMA tile loads (nx % 4 == 0)
-  // 4-D maps {nx, ny, nz, max_fields}: d_r, d_p[0], d_p[1] in slabs with the x-y halo (40 x 10 x 4),
-  // d_e and d_r in slabs of the tile alone (32 x 8 x 4)
-  CUtensorMap tm_r4{}, tm_p4[2]{}, tm_e4{}, tm_r4v{};
+  // 4-D maps {nx, ny, nz, max_fields} per slab depth 2, 4, 8: d_r, d_p[0], d_p[1] in slabs with the
+  // x-y halo (40 x 10 x depth), d_e and d_r in slabs of the tile alone (32 x 8 x depth)
+  CUtensorMap tm_rh[3]{}, tm_ph[3][2]{}, tm_e[3]{}, tm_rv[3]{};
+  // autotuner of the rolling inner passes: variant -1 while groups of iterations are being timed
+  struct {
+    int variant = -1;
+    int samples[HYDOT_ROLL_VARIANTS] = {};
+    double ms[HYDOT_ROLL_VARIANTS] = {};
+    double cells[HYDOT_ROLL_VARIANTS] = {};
+  } tune;
+  cudaEvent_t tune_ev[2] = {nullptr, nullptr};
   int dir_seg = 0;           // z-planes per block of the rolling pass-1 kernel (multiple of the tile depth)
   // deflation (recycled subspace): W [k][N] FP64 and the k x k Gram blocks
   double* d_W = nullptr;
@@ -224,6 +232,7 @@ inline int fail(hydot_ctx* ctx, int code, const std::string& msg) {
 
 // solver.cu
 int solve_fields_impl(hydot_ctx* ctx, int lam0, int nlam, void* phi_src, void* phi_det, hydot_stats* st);
+int get_tuning_impl(const hydot_ctx* ctx, int* variant, int* planes, int* buffers, double* ns_per_cell);
 int solver_alloc(hydot_ctx* ctx);
 void solver_free(hydot_ctx* ctx);
 

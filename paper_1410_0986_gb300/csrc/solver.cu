@@ -535,11 +535,12 @@ __device__ __forceinline__ float diag_f(const LamCoefF& cf, int m) {
 // are in flight while a slab is processed. The diagonal and its inverse depend on the cell only
 // through its face mask: each thread precomputes them for its column and its halo cell (four z
 // cases: interior, bottom, top, both).
-constexpr int RP = 4;                 // planes per slab
-constexpr int RS = 4;                 // slab buffers
+// RP (planes per slab) and RS (slab buffers) are template parameters; the variants compute the
+// same values in the same order (bitwise identical results) and differ only in how much data is
+// in flight per block and how many blocks fit on an SM, which the autotuner times.
 constexpr int PLN = BXT * BYT;        // floats in one box plane
-constexpr uint32_t SLAB_BYTES = RP * PLN * 4;
-constexpr size_t roll_smem() { return (size_t)RS * 2 * SLAB_BYTES + 128; }
+template <int RP, int RS>
+constexpr size_t roll_smem() { return (size_t)RS * 2 * RP * PLN * 4 + 128; }
 
 __device__ __forceinline__ void col_diag(const LamCoefF& cf, int mxy, float (&d)[4], float (&di)[4]) {
 #pragma unroll
@@ -554,7 +555,8 @@ __device__ __forceinline__ float pick4(const float (&v)[4], int zb) {
   return zb == 0 ? v[0] : (zb == 1 ? v[1] : (zb == 2 ? v[2] : v[3]));
 }
 
-__global__ void __launch_bounds__(NTHREADS, 4) k_dir_roll(Geo g, Batch b, int it, int seg,
+template <int RP, int RS, int MINB>
+__global__ void __launch_bounds__(NTHREADS, MINB) k_dir_roll(Geo g, Batch b, int it, int seg,
                                                           const LamCoefF* __restrict__ coef_f,
                                                           const __grid_constant__ CUtensorMap mapR,
                                                           const __grid_constant__ CUtensorMap mapPold,
@@ -564,7 +566,8 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_dir_roll(Geo g, Batch b, int it
   __shared__ uint64_t mbar[RS];
   __shared__ double sm[96];
   __shared__ float s_beta;
-  __shared__ int s_go;
+  __shared__ int s_go, s_st;
+  constexpr uint32_t SLAB_BYTES = RP * PLN * 4;
   const int ncol = g.ntx * g.nty;
   const int nseg = (g.nz + seg - 1) / seg;
   const int rhs = blockIdx.x / (ncol * nseg);
@@ -577,56 +580,64 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_dir_roll(Geo g, Batch b, int it
   double* pb = b.part + (size_t)rhs * part_stride(T_);
   const int par = it & 1;
   const bool first = (it == 0);
-  if (threadIdx.x < 32) {
-    const int st = b.status[rhs];
-    double v0 = 0.0, v1 = 0.0, v2 = 0.0;
-    if (st == RHS_INNER)
-      for (int t = threadIdx.x; t < T_; t += 32) {
-        v0 += pb[2 * T_ * par + 2 * t];
-        v1 += pb[4 * T_ + T_ * par + t];
-        if (!first) v2 += pb[2 * T_ * (par ^ 1) + 2 * t];
-      }
-    v0 = warp_sum(v0);
-    v1 = warp_sum(v1);
-    v2 = warp_sum(v2);
-    if (threadIdx.x == 0) {
-      int go = 0;
-      float beta = 0.f;
-      if (st == RHS_INNER) {
-        const bool done = v1 <= b.tol_in2 * b.rr0[rhs] || it >= b.max_inner || b.iters[rhs] >= b.max_iter ||
-                          v1 == 0.0;
-        if (done) {
-          if (lead) b.status[rhs] = RHS_FINISHED;
-        } else {
-          go = 1;
-          beta = first ? 0.f : (float)(v0 / v2);
-          if (lead) atomicAdd(&b.counter[1 + it], 1);
-        }
-      }
-      s_go = go;
-      s_beta = beta;
-    }
-  }
-  __syncthreads();
-  if (!s_go) return;
-  const float beta = s_beta;
-  const LamCoefF cf = coef_f[rhs_lambda(b, rhs)];
   const int np = z1 - z0 + 2;  // planes z0-1 .. z1 (t = plane - (z0 - 1))
   const int nslab = (np + RP - 1) / RP;
+  const int nfirst = min(RS, nslab);
   const uint32_t tx_bytes = (first ? 1u : 2u) * SLAB_BYTES;
-  if (threadIdx.x == 0) {
-    for (int q = 0; q < RS; ++q) mbar_init(&mbar[q], 1);
-    mbar_fence_init();
-  }
-  __syncthreads();
   auto issue = [&](int q) {
     float* dst = slab + (q % RS) * 2 * RP * PLN;
     mbar_expect_tx(&mbar[q % RS], tx_bytes);
     tma_load_4d(dst, &mapR, &mbar[q % RS], x0 - 4, y0 - 1, z0 - 1 + q * RP, rhs);
     if (!first) tma_load_4d(dst + RP * PLN, &mapPold, &mbar[q % RS], x0 - 4, y0 - 1, z0 - 1 + q * RP, rhs);
   };
-  if (threadIdx.x == 0)
-    for (int q = 0; q < min(RS, nslab); ++q) issue(q);
+  // A field still iterating gets its first slabs requested at once; the convergence test and
+  // beta (FP64 sums of the per-tile partials) are formed while they are in flight. A field that
+  // stops here still waits (bounded) for those copies before the block exits.
+  if (threadIdx.x == 0) {
+    const int st = b.status[rhs];
+    s_st = st;
+    if (st == RHS_INNER) {
+      for (int q = 0; q < RS; ++q) mbar_init(&mbar[q], 1);
+      mbar_fence_init();
+      for (int q = 0; q < nfirst; ++q) issue(q);
+    }
+  }
+  __syncthreads();
+  if (s_st != RHS_INNER) return;
+  if (threadIdx.x < 32) {
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0;
+    for (int t = threadIdx.x; t < T_; t += 32) {
+      v0 += pb[2 * T_ * par + 2 * t];
+      v1 += pb[4 * T_ + T_ * par + t];
+      if (!first) v2 += pb[2 * T_ * (par ^ 1) + 2 * t];
+    }
+    v0 = warp_sum(v0);
+    v1 = warp_sum(v1);
+    v2 = warp_sum(v2);
+    if (threadIdx.x == 0) {
+      int go = 0;
+      float beta = 0.f;
+      const bool done = v1 <= b.tol_in2 * b.rr0[rhs] || it >= b.max_inner || b.iters[rhs] >= b.max_iter ||
+                        v1 == 0.0;
+      if (done) {
+        if (lead) b.status[rhs] = RHS_FINISHED;
+      } else {
+        go = 1;
+        beta = first ? 0.f : (float)(v0 / v2);
+        if (lead) atomicAdd(&b.counter[1 + it], 1);
+      }
+      s_go = go;
+      s_beta = beta;
+    }
+  }
+  const LamCoefF cf = coef_f[rhs_lambda(b, rhs)];
+  __syncthreads();
+  if (!s_go) {
+    if (threadIdx.x == 0)
+      for (int q = 0; q < nfirst; ++q) mbar_wait_bounded(&mbar[q % RS], 0u);
+    return;
+  }
+  const float beta = s_beta;
 
   // own column and halo cell of this thread
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
@@ -738,12 +749,13 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_dir_roll(Geo g, Batch b, int it
 // Pass 2 with the same rolling window: a slab holds RP planes of p (tile + x-y halo) and of e
 // and r (tile only), all by TMA; the stencil of plane k runs once plane k+1 of p is resident.
 // Threads write nothing to shared memory, so one barrier per slab only guards the refill.
-constexpr uint32_t UP_P = RP * PLN * 4;          // p planes of a slab (bytes)
-constexpr uint32_t UP_V = RP * TX * TY * 4;      // e or r planes of a slab (bytes)
-constexpr uint32_t UP_SLAB = UP_P + 2 * UP_V;
-constexpr size_t upd_smem() { return (size_t)RS * UP_SLAB + 128; }
+template <int RP>
+__host__ __device__ constexpr uint32_t upd_slab() { return RP * PLN * 4 + 2 * RP * TX * TY * 4; }  // p | e | r
+template <int RP, int RS>
+constexpr size_t upd_smem() { return (size_t)RS * upd_slab<RP>() + 128; }
 
-__global__ void __launch_bounds__(NTHREADS, 3) k_update_roll(Geo g, Batch b, int it, int seg,
+template <int RP, int RS, int MINB>
+__global__ void __launch_bounds__(NTHREADS, MINB) k_update_roll(Geo g, Batch b, int it, int seg,
                                                              const LamCoefF* __restrict__ coef_f,
                                                              float* __restrict__ E, float* __restrict__ R,
                                                              const __grid_constant__ CUtensorMap mapP,
@@ -754,7 +766,10 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_update_roll(Geo g, Batch b, int
   __shared__ uint64_t mbar[RS];
   __shared__ double sm[96];
   __shared__ float s_alpha;
-  __shared__ int s_go;
+  __shared__ int s_st;
+  constexpr uint32_t UP_P = RP * PLN * 4;      // p planes of a slab (bytes)
+  constexpr uint32_t UP_V = RP * TX * TY * 4;  // e or r planes of a slab (bytes)
+  constexpr uint32_t UP_SLAB = upd_slab<RP>();
   const int ncol = g.ntx * g.nty;
   const int nseg = (g.nz + seg - 1) / seg;
   const int rhs = blockIdx.x / (ncol * nseg);
@@ -767,33 +782,9 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_update_roll(Geo g, Batch b, int
   double* pb = b.part + (size_t)rhs * part_stride(T_);
   const int par = it & 1;
   const bool first = (it == 0);
-  if (threadIdx.x < 32) {
-    const int st = b.status[rhs];
-    double v0 = 0.0, v1 = 0.0;
-    if (st == RHS_INNER)
-      for (int t = threadIdx.x; t < T_; t += 32) {
-        v0 += pb[2 * T_ * par + 2 * t];
-        v1 += pb[6 * T_ + 2 * t];
-      }
-    v0 = warp_sum(v0);
-    v1 = warp_sum(v1);
-    if (threadIdx.x == 0) {
-      s_go = st == RHS_INNER;
-      s_alpha = s_go ? (float)(v0 / v1) : 0.f;
-    }
-  }
-  __syncthreads();
-  if (!s_go) return;
-  const float alpha = s_alpha;
-  const LamCoefF cf = coef_f[rhs_lambda(b, rhs)];
   const int np = z1 - z0 + 2;
   const int nslab = (np + RP - 1) / RP;
   const uint32_t tx_bytes = UP_P + (first ? 1u : 2u) * UP_V;
-  if (threadIdx.x == 0) {
-    for (int q = 0; q < RS; ++q) mbar_init(&mbar[q], 1);
-    mbar_fence_init();
-  }
-  __syncthreads();
   auto issue = [&](int q) {
     unsigned char* dst = slab + (size_t)(q % RS) * UP_SLAB;
     const int zq = z0 - 1 + q * RP;
@@ -802,8 +793,32 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_update_roll(Geo g, Batch b, int
     if (!first) tma_load_4d(dst + UP_P, &mapE, &mbar[q % RS], x0, y0, zq, rhs);
     tma_load_4d(dst + UP_P + UP_V, &mapR, &mbar[q % RS], x0, y0, zq, rhs);
   };
-  if (threadIdx.x == 0)
-    for (int q = 0; q < min(RS, nslab); ++q) issue(q);
+  // a field still iterating (pass 1 ran for it) gets its first slabs requested at once; alpha is
+  // formed from the partials while they are in flight
+  if (threadIdx.x == 0) {
+    const int st = b.status[rhs];
+    s_st = st;
+    if (st == RHS_INNER) {
+      for (int q = 0; q < RS; ++q) mbar_init(&mbar[q], 1);
+      mbar_fence_init();
+      for (int q = 0; q < min(RS, nslab); ++q) issue(q);
+    }
+  }
+  __syncthreads();
+  if (s_st != RHS_INNER) return;
+  if (threadIdx.x < 32) {
+    double v0 = 0.0, v1 = 0.0;
+    for (int t = threadIdx.x; t < T_; t += 32) {
+      v0 += pb[2 * T_ * par + 2 * t];
+      v1 += pb[6 * T_ + 2 * t];
+    }
+    v0 = warp_sum(v0);
+    v1 = warp_sum(v1);
+    if (threadIdx.x == 0) s_alpha = (float)(v0 / v1);
+  }
+  const LamCoefF cf = coef_f[rhs_lambda(b, rhs)];
+  __syncthreads();
+  const float alpha = s_alpha;
 
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const int i = x0 + tx, j = y0 + ty;
@@ -942,6 +957,87 @@ Geo make_geo(const hydot_ctx* ctx) {
   return g;
 }
 
+// ---------------------------------------------------------------- rolling-pass variants
+// {planes per slab, slab buffers}; the autotuner picks one per context (they give identical bits).
+struct RollVariant {
+  int rp, rs;
+};
+constexpr RollVariant ROLL_VARIANTS[HYDOT_ROLL_VARIANTS] = {{4, 4}, {2, 6}, {8, 3}, {4, 5}};
+
+__host__ __device__ constexpr int rp_index(int rp) { return rp == 2 ? 0 : (rp == 4 ? 1 : 2); }
+
+template <int RP, int RS, int MB1, int MB2>
+int roll_attrs(hydot_ctx* ctx) {
+  HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(k_dir_roll<RP, RS, MB1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)roll_smem<RP, RS>()));
+  HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(k_update_roll<RP, RS, MB2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)upd_smem<RP, RS>()));
+  return HYDOT_OK;
+}
+
+// One inner iteration (pass 1, pass 2) with variant <RP, RS>.
+template <int RP, int RS, int MB1, int MB2>
+void roll_iteration(hydot_ctx* ctx, const Geo& g, const Batch& b, int it, unsigned nrb, float* E, float* R,
+                    float* const* P) {
+  const int k = rp_index(RP);
+  const int seg = ctx->dir_seg;
+  cudaStream_t s = ctx->stream;
+  cudaEvent_t t0 = timer_begin(ctx);
+  k_dir_roll<RP, RS, MB1><<<nrb, NTHREADS, roll_smem<RP, RS>(), s>>>(g, b, it, seg, ctx->d_coef_f, ctx->tm_rh[k],
+                                                                   ctx->tm_ph[k][it & 1], P[(it + 1) & 1]);
+  ++ctx->launches;
+  timer_end(ctx, t0, HYDOT_KERNEL_DIR, 0.0);
+  t0 = timer_begin(ctx);
+  k_update_roll<RP, RS, MB2><<<nrb, NTHREADS, upd_smem<RP, RS>(), s>>>(g, b, it, seg, ctx->d_coef_f, E, R,
+                                                                     ctx->tm_ph[k][(it + 1) & 1], ctx->tm_e[k],
+                                                                     ctx->tm_rv[k]);
+  ++ctx->launches;
+  timer_end(ctx, t0, HYDOT_KERNEL_UPDATE, 0.0);
+}
+
+void roll_dispatch(hydot_ctx* ctx, int v, const Geo& g, const Batch& b, int it, unsigned nrb, float* E, float* R,
+                   float* const* P) {
+  switch (v) {
+    case 1: roll_iteration<2, 6, 4, 4>(ctx, g, b, it, nrb, E, R, P); break;
+    case 2: roll_iteration<8, 3, 2, 2>(ctx, g, b, it, nrb, E, R, P); break;
+    case 3: roll_iteration<4, 5, 3, 3>(ctx, g, b, it, nrb, E, R, P); break;
+    default: roll_iteration<4, 4, 4, 3>(ctx, g, b, it, nrb, E, R, P); break;
+  }
+}
+
+int roll_setup(hydot_ctx* ctx) {
+  int rc = roll_attrs<4, 4, 4, 3>(ctx);
+  if (!rc) rc = roll_attrs<2, 6, 4, 4>(ctx);
+  if (!rc) rc = roll_attrs<8, 3, 2, 2>(ctx);
+  if (!rc) rc = roll_attrs<4, 5, 3, 3>(ctx);
+  return rc;
+}
+
+// Variant for the next group of inner iterations: the chosen one, else (tuning) the variant with
+// the fewest timed groups so far.
+int roll_pick(hydot_ctx* ctx) {
+  if (ctx->tune.variant >= 0) return ctx->tune.variant;
+  int best = 0;
+  for (int v = 1; v < HYDOT_ROLL_VARIANTS; ++v)
+    if (ctx->tune.samples[v] < ctx->tune.samples[best]) best = v;
+  return best;
+}
+
+// Record a timed group; once every variant has TUNE_SAMPLES groups, keep the fastest per cell-iteration.
+constexpr int TUNE_SAMPLES = 2;
+void roll_record(hydot_ctx* ctx, int v, double ms, double cell_iters) {
+  if (ctx->tune.variant >= 0 || cell_iters <= 0.0) return;
+  ctx->tune.ms[v] += ms;
+  ctx->tune.cells[v] += cell_iters;
+  ctx->tune.samples[v] += 1;
+  for (int q = 0; q < HYDOT_ROLL_VARIANTS; ++q)
+    if (ctx->tune.samples[q] < TUNE_SAMPLES) return;
+  int best = 0;
+  for (int q = 1; q < HYDOT_ROLL_VARIANTS; ++q)
+    if (ctx->tune.ms[q] / ctx->tune.cells[q] < ctx->tune.ms[best] / ctx->tune.cells[best]) best = q;
+  ctx->tune.variant = best;
+}
+
 template <typename T, typename X, typename O>
 int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_stats* st) {
   Geo g = make_geo(ctx);
@@ -1029,22 +1125,17 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
     bool stop = false;
     while (!stop && it < MAX_INNER_PER_CYCLE) {
       int g_end = std::min(it + POLL_GROUP, MAX_INNER_PER_CYCLE);
+      // autotuning: a group that does not start the cycle runs one candidate variant and is timed
+      const int variant = ctx->use_tma ? roll_pick(ctx) : 0;
+      const bool tuning = ctx->use_tma && ctx->tune.variant < 0 && it > 0;
+      const int g_begin = it;
+      if (tuning) HYDOT_CUDA_TRY(ctx, cudaEventRecord(ctx->tune_ev[0], s));
       for (; it < g_end; ++it) {
         if constexpr (std::is_same<T, float>::value) {
           if (ctx->use_tma) {
-            const unsigned ncb = (unsigned)((long long)b.nrhs * g.ntx * g.nty);
-            cudaEvent_t t0 = timer_begin(ctx);
             const int seg = ctx->dir_seg;
-            const unsigned nrb = (unsigned)((long long)ncb * ((g.nz + seg - 1) / seg));
-            k_dir_roll<<<nrb, blk, roll_smem(), s>>>(g, b, it, seg, ctx->d_coef_f, ctx->tm_r4, ctx->tm_p4[it & 1],
-                                                     P[(it + 1) & 1]);
-            ++ctx->launches;
-            timer_end(ctx, t0, HYDOT_KERNEL_DIR, 0.0);
-            t0 = timer_begin(ctx);
-            k_update_roll<<<nrb, blk, upd_smem(), s>>>(g, b, it, seg, ctx->d_coef_f, E, R, ctx->tm_p4[(it + 1) & 1],
-                                                       ctx->tm_e4, ctx->tm_r4v);
-            ++ctx->launches;
-            timer_end(ctx, t0, HYDOT_KERNEL_UPDATE, 0.0);
+            const unsigned nrb = (unsigned)((long long)b.nrhs * g.ntx * g.nty * ((g.nz + seg - 1) / seg));
+            roll_dispatch(ctx, variant, g, b, it, nrb, (float*)E, (float*)R, (float* const*)P);
             continue;
           }
         }
@@ -1058,6 +1149,20 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
         timer_end(ctx, t0, HYDOT_KERNEL_UPDATE, 0.0);
       }
       HYDOT_CUDA_TRY(ctx, cudaGetLastError());
+      if (tuning) {
+        // time of the group per active cell-iteration (fields that ran x cells)
+        HYDOT_CUDA_TRY(ctx, cudaEventRecord(ctx->tune_ev[1], s));
+        int cnt[POLL_GROUP];
+        HYDOT_CUDA_TRY(ctx, cudaMemcpyAsync(cnt, b.counter + 1 + g_begin, sizeof(int) * (it - g_begin),
+                                            cudaMemcpyDeviceToHost, s));
+        HYDOT_CUDA_TRY(ctx, cudaEventSynchronize(ctx->tune_ev[1]));
+        float ms = 0.f;
+        HYDOT_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, ctx->tune_ev[0], ctx->tune_ev[1]));
+        double work = 0.0;
+        for (int q = 0; q < it - g_begin; ++q) work += (double)cnt[q] * (double)g.N;
+        // a group in which fields converged mixes full and empty launches: only whole groups count
+        if (cnt[0] == cnt[it - g_begin - 1]) roll_record(ctx, variant, ms, work);
+      }
       HYDOT_CUDA_TRY(ctx, cudaMemcpyAsync((void*)&hp[1 + slot], b.counter + 1 + (it - 1), sizeof(int),
                                           cudaMemcpyDeviceToHost, s));
       HYDOT_CUDA_TRY(ctx, cudaEventRecord(ev[slot], s));
@@ -1209,15 +1314,24 @@ int solver_alloc(hydot_ctx* ctx) {
   HYDOT_CUDA_TRY(ctx, cudaMalloc(&ctx->d_err, sizeof(int)));
   HYDOT_CUDA_TRY(ctx, cudaMemset(ctx->d_err, 0, sizeof(int)));
   if (ctx->use_tma) {
-    HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(k_dir_roll, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)roll_smem()));
-    HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(k_update_roll, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd_smem()));
-    // halo slabs of r and p (pass 1 reads r and p_old, pass 2 reads p_new), plain slabs of e and r
-    int rc = encode_field_map(ctx, ctx->d_r, &ctx->tm_r4, BXT, BYT, RP);
-    if (!rc) rc = encode_field_map(ctx, ctx->d_p[0], &ctx->tm_p4[0], BXT, BYT, RP);
-    if (!rc) rc = encode_field_map(ctx, ctx->d_p[1], &ctx->tm_p4[1], BXT, BYT, RP);
-    if (!rc) rc = encode_field_map(ctx, ctx->d_e, &ctx->tm_e4, TX, TY, RP);
-    if (!rc) rc = encode_field_map(ctx, ctx->d_r, &ctx->tm_r4v, TX, TY, RP);
+    int rc = roll_setup(ctx);
+    // per slab depth (2, 4, 8 planes): halo slabs of r and p (pass 1 reads r and p_old, pass 2 reads
+    // p_new), plain slabs of e and r
+    for (int k = 0; k < 3 && !rc; ++k) {
+      const int bz = 2 << k;
+      rc = encode_field_map(ctx, ctx->d_r, &ctx->tm_rh[k], BXT, BYT, bz);
+      if (!rc) rc = encode_field_map(ctx, ctx->d_p[0], &ctx->tm_ph[k][0], BXT, BYT, bz);
+      if (!rc) rc = encode_field_map(ctx, ctx->d_p[1], &ctx->tm_ph[k][1], BXT, BYT, bz);
+      if (!rc) rc = encode_field_map(ctx, ctx->d_e, &ctx->tm_e[k], TX, TY, bz);
+      if (!rc) rc = encode_field_map(ctx, ctx->d_r, &ctx->tm_rv[k], TX, TY, bz);
+    }
     if (rc) return rc;
+    HYDOT_CUDA_TRY(ctx, cudaEventCreate(&ctx->tune_ev[0]));
+    HYDOT_CUDA_TRY(ctx, cudaEventCreate(&ctx->tune_ev[1]));
+    if (const char* v = std::getenv("HYDOT_ROLL_VARIANT")) {
+      const int want = std::atoi(v);
+      if (want >= 0 && want < HYDOT_ROLL_VARIANTS) ctx->tune.variant = want;
+    }
     // whole columns unless the blocks of one wavelength's fields would leave most SMs idle
     ctx->dir_seg = t.ntz * t.tz;
     if (const char* v = std::getenv("HYDOT_DIR_SEG")) {
@@ -1246,6 +1360,19 @@ void solver_free(hydot_ctx* ctx) {
   cudaFree(ctx->d_counter);
   cudaFree(ctx->d_err);
   if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+  if (ctx->tune_ev[0]) cudaEventDestroy(ctx->tune_ev[0]);
+  if (ctx->tune_ev[1]) cudaEventDestroy(ctx->tune_ev[1]);
+}
+
+int get_tuning_impl(const hydot_ctx* ctx, int* variant, int* planes, int* buffers, double* ns_per_cell) {
+  if (variant) *variant = ctx->use_tma ? ctx->tune.variant : -1;
+  for (int v = 0; v < HYDOT_ROLL_VARIANTS; ++v) {
+    if (planes) planes[v] = ROLL_VARIANTS[v].rp;
+    if (buffers) buffers[v] = ROLL_VARIANTS[v].rs;
+    if (ns_per_cell)
+      ns_per_cell[v] = ctx->tune.cells[v] > 0.0 ? 1e6 * ctx->tune.ms[v] / ctx->tune.cells[v] : 0.0;
+  }
+  return HYDOT_OK;
 }
 
 int solve_fields_impl(hydot_ctx* ctx, int lam0, int nlam, void* phi_src, void* phi_det, hydot_stats* st) {

@@ -200,3 +200,28 @@ def test_bitwise_repeatable(hd):
         a, b, _ = ctx.solve_fields(0, 2)
         c, d, _ = ctx.solve_fields(0, 2)
     assert torch.equal(a, c) and torch.equal(b, d)
+
+
+def test_roll_variants_bitwise_identical_and_autotuner_settles(hd, oracle_fields, monkeypatch):
+    """The slab shapes the autotuner chooses from give the same bits; an untuned context times the
+    variants on groups of inner iterations and then keeps one."""
+    p = workloads.make_problem(workloads.Grid(64, 40, 36, 2.0), 4, 4, 4, seed=21, geometry="transmission")
+    out = []
+    for v in range(4):
+        monkeypatch.setenv("HYDOT_ROLL_VARIANT", str(v))
+        with hd.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=1e-8, cw_floor=100.0) as ctx:
+            ps, pd, st = ctx.solve_fields(0, p.n_lambda)
+            assert ctx.tuning()["variant"] == v
+        out.append((ps, pd))
+    for ps, pd in out[1:]:
+        assert torch.equal(ps, out[0][0]) and torch.equal(pd, out[0][1])
+    monkeypatch.delenv("HYDOT_ROLL_VARIANT")
+    with hd.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=1e-8, cw_floor=100.0) as ctx:
+        assert ctx.tuning()["variant"] == -1
+        for _ in range(3):
+            ps, pd, st = ctx.solve_fields(0, p.n_lambda)
+            assert torch.equal(ps, out[0][0]) and torch.equal(pd, out[0][1])
+        tu = ctx.tuning()
+    assert tu["variant"] in range(4)
+    assert all(v["ns_per_cell"] > 0 for v in tu["variants"])
+    assert [(v["planes"], v["buffers"]) for v in tu["variants"]] == [(4, 4), (2, 6), (8, 3), (4, 5)]
