@@ -363,6 +363,7 @@ def run_ours(args):
     if args.compare_fp64 and rank == 0:
         out["fp64_vs_mixed_at_1e-6"] = compare_fp64(hd, p)
         out["deflation"] = compare_deflation(hd, p)
+        out["cuda_graphs"] = compare_graphs(hd, p)
     if rank == 0 and not args.no_sketch:
         out["sketch"] = sketch_phase(hd, pk)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -448,6 +449,44 @@ def compare_deflation(hd, p, k=16):
             res[f"k={kk}"] = {"solves_per_s": (p.n_src + p.n_det) * CHUNK / (a.elapsed_time(b) / 1e3),
                               "iters_mean": st["iters_mean"], "iters_max": st["iters_max"],
                               "cycles_max": st["cycles_max"], "setup_s": setup}
+    return res
+
+
+def compare_graphs(hd, p):
+    """Field solves/s with groups of inner iterations replayed from a CUDA graph against direct
+    launches, on the benchmark chunk and on a small problem (config-1 grid, 16 wavelengths, FP32
+    inner) where launch cost matters; kernel timing is off, the autotuned variant is kept."""
+    import os
+    import torch
+    import workloads
+
+    small = workloads.config(1)
+    cases = {"cw-mixed-64x64x48 chunk (1,024 fields)": (p, CHUNK),
+             "24x24x16 grid, 16 wavelengths (256 fields)": (small, small.n_lambda)}
+    res = {}
+    for name, (prob, nl) in cases.items():
+        row = {}
+        for label, flag in (("graph", "0"), ("direct", "1")):
+            os.environ["HYDOT_NO_GRAPHS"] = flag
+            try:
+                with hd.Context.from_problem(prob, precision="mixed", tol=1e-10, tol_cw=TOL_CW, cw_floor=CW_FLOOR,
+                                             max_lambda_per_call=nl) as c:
+                    for _ in range(3):
+                        c.solve_fields(0, nl)  # autotuning settles, graph captured
+                    torch.cuda.synchronize()
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    reps = 2
+                    a.record()
+                    for _ in range(reps):
+                        c.solve_fields(0, nl)
+                    b.record()
+                    torch.cuda.synchronize()
+                    row[label] = (prob.n_src + prob.n_det) * nl * reps / (a.elapsed_time(b) / 1e3)
+            finally:
+                os.environ.pop("HYDOT_NO_GRAPHS", None)
+        row["speedup"] = row["graph"] / row["direct"]
+        res[name] = row
     return res
 
 

@@ -194,6 +194,11 @@ struct hydot_ctx {
     double cells[HYDOT_ROLL_VARIANTS] = {};
   } tune;
   cudaEvent_t tune_ev[2] = {nullptr, nullptr};
+  int* d_it = nullptr;               // device-resident base of the inner iteration index
+  bool use_graphs = true;            // replay groups of inner iterations from a CUDA graph
+  void* inner_exec = nullptr;        // cudaGraphExec_t of one group
+  cudaStream_t cap_stream = nullptr;  // private non-blocking stream the group is captured on
+  std::vector<unsigned char> inner_key;  // what the graph was captured for
   int dir_seg = 0;           // z-planes per block of the rolling pass-1 kernel (multiple of the tile depth)
   // deflation (recycled subspace): W [k][N] FP64 and the k x k Gram blocks
   double* d_W = nullptr;

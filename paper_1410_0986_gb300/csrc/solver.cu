@@ -556,7 +556,8 @@ __device__ __forceinline__ float pick4(const float (&v)[4], int zb) {
 }
 
 template <int RP, int RS, int MINB>
-__global__ void __launch_bounds__(NTHREADS, MINB) k_dir_roll(Geo g, Batch b, int it, int seg,
+__global__ void __launch_bounds__(NTHREADS, MINB) k_dir_roll(Geo g, Batch b, const int* __restrict__ it_dev, int k,
+                                                             int seg,
                                                           const LamCoefF* __restrict__ coef_f,
                                                           const __grid_constant__ CUtensorMap mapR,
                                                           const __grid_constant__ CUtensorMap mapPold,
@@ -568,6 +569,7 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_dir_roll(Geo g, Batch b, int
   __shared__ float s_beta;
   __shared__ int s_go, s_st;
   constexpr uint32_t SLAB_BYTES = RP * PLN * 4;
+  const int it = *it_dev + k;  // iteration index: group base on the device + offset in the group
   const int ncol = g.ntx * g.nty;
   const int nseg = (g.nz + seg - 1) / seg;
   const int rhs = blockIdx.x / (ncol * nseg);
@@ -755,7 +757,8 @@ template <int RP, int RS>
 constexpr size_t upd_smem() { return (size_t)RS * upd_slab<RP>() + 128; }
 
 template <int RP, int RS, int MINB>
-__global__ void __launch_bounds__(NTHREADS, MINB) k_update_roll(Geo g, Batch b, int it, int seg,
+__global__ void __launch_bounds__(NTHREADS, MINB) k_update_roll(Geo g, Batch b, const int* __restrict__ it_dev,
+                                                                int k, int seg,
                                                              const LamCoefF* __restrict__ coef_f,
                                                              float* __restrict__ E, float* __restrict__ R,
                                                              const __grid_constant__ CUtensorMap mapP,
@@ -770,6 +773,7 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_update_roll(Geo g, Batch b, 
   constexpr uint32_t UP_P = RP * PLN * 4;      // p planes of a slab (bytes)
   constexpr uint32_t UP_V = RP * TX * TY * 4;  // e or r planes of a slab (bytes)
   constexpr uint32_t UP_SLAB = upd_slab<RP>();
+  const int it = *it_dev + k;  // iteration index: group base on the device + offset in the group
   const int ncol = g.ntx * g.nty;
   const int nseg = (g.nz + seg - 1) / seg;
   const int rhs = blockIdx.x / (ncol * nseg);
@@ -983,12 +987,14 @@ void roll_iteration(hydot_ctx* ctx, const Geo& g, const Batch& b, int it, unsign
   const int seg = ctx->dir_seg;
   cudaStream_t s = ctx->stream;
   cudaEvent_t t0 = timer_begin(ctx);
-  k_dir_roll<RP, RS, MB1><<<nrb, NTHREADS, roll_smem<RP, RS>(), s>>>(g, b, it, seg, ctx->d_coef_f, ctx->tm_rh[k],
-                                                                   ctx->tm_ph[k][it & 1], P[(it + 1) & 1]);
+  const int o = it % POLL_GROUP;  // groups start at multiples of POLL_GROUP (even): parity of it = parity of o
+  k_dir_roll<RP, RS, MB1><<<nrb, NTHREADS, roll_smem<RP, RS>(), s>>>(g, b, ctx->d_it, o, seg, ctx->d_coef_f,
+                                                                   ctx->tm_rh[k], ctx->tm_ph[k][it & 1],
+                                                                   P[(it + 1) & 1]);
   ++ctx->launches;
   timer_end(ctx, t0, HYDOT_KERNEL_DIR, 0.0);
   t0 = timer_begin(ctx);
-  k_update_roll<RP, RS, MB2><<<nrb, NTHREADS, upd_smem<RP, RS>(), s>>>(g, b, it, seg, ctx->d_coef_f, E, R,
+  k_update_roll<RP, RS, MB2><<<nrb, NTHREADS, upd_smem<RP, RS>(), s>>>(g, b, ctx->d_it, o, seg, ctx->d_coef_f, E, R,
                                                                      ctx->tm_ph[k][(it + 1) & 1], ctx->tm_e[k],
                                                                      ctx->tm_rv[k]);
   ++ctx->launches;
@@ -1036,6 +1042,78 @@ void roll_record(hydot_ctx* ctx, int v, double ms, double cell_iters) {
   for (int q = 1; q < HYDOT_ROLL_VARIANTS; ++q)
     if (ctx->tune.ms[q] / ctx->tune.cells[q] < ctx->tune.ms[best] / ctx->tune.cells[best]) best = q;
   ctx->tune.variant = best;
+}
+
+// Advances the device-resident iteration base by one group (the last node of a group).
+__global__ void k_bump(int* v, int d) { *v += d; }
+
+// One group of POLL_GROUP inner iterations of the rolling passes plus the base advance, captured
+// once into a CUDA graph and replayed while the batch, the variant and the grid stay the same
+// (the iteration index comes from the device, so every group of a cycle replays the same graph).
+struct GraphKey {
+  Batch b;
+  Geo g;
+  int variant, seg;
+  unsigned nrb;
+  const void *E, *R, *P0, *P1;
+};
+
+int inner_graph_launch(hydot_ctx* ctx, const Geo& g, const Batch& b, int variant, unsigned nrb, float* E, float* R,
+                       float* const* P) {
+  GraphKey key;
+  std::memset(&key, 0, sizeof(key));
+  key.b = b;
+  key.g = g;
+  key.variant = variant;
+  key.seg = ctx->dir_seg;
+  key.nrb = nrb;
+  key.E = E;
+  key.R = R;
+  key.P0 = P[0];
+  key.P1 = P[1];
+  cudaStream_t s = ctx->stream;
+  const bool same = ctx->inner_exec && ctx->inner_key.size() == sizeof(key) &&
+                    std::memcmp(ctx->inner_key.data(), &key, sizeof(key)) == 0;
+  if (!same) {
+    // captured on the context's private stream (the caller's may be the legacy default stream,
+    // which cannot be captured); the graph is then launched on the caller's stream
+    const long long launches = ctx->launches;
+    cudaGraph_t graph = nullptr;
+    cudaStream_t cs = ctx->cap_stream;
+    HYDOT_CUDA_TRY(ctx, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    ctx->stream = cs;
+    for (int o = 0; o < POLL_GROUP; ++o) roll_dispatch(ctx, variant, g, b, o, nrb, E, R, P);
+    k_bump<<<1, 1, 0, cs>>>(ctx->d_it, POLL_GROUP);
+    ctx->stream = s;
+    cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    ctx->launches = launches;
+    if (e != cudaSuccess) return fail(ctx, HYDOT_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    cudaGraphExec_t exec = (cudaGraphExec_t)ctx->inner_exec;
+    bool updated = false;
+    if (exec) {
+      cudaGraphExecUpdateResultInfo info;
+      updated = cudaGraphExecUpdate(exec, graph, &info) == cudaSuccess;
+      if (!updated) {
+        (void)cudaGetLastError();
+        cudaGraphExecDestroy(exec);
+        ctx->inner_exec = nullptr;
+      }
+    }
+    if (!updated) {
+      e = cudaGraphInstantiate(&exec, graph, 0);
+      if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return fail(ctx, HYDOT_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+      }
+      ctx->inner_exec = exec;
+    }
+    cudaGraphDestroy(graph);
+    ctx->inner_key.assign(reinterpret_cast<const unsigned char*>(&key),
+                          reinterpret_cast<const unsigned char*>(&key) + sizeof(key));
+  }
+  HYDOT_CUDA_TRY(ctx, cudaGraphLaunch((cudaGraphExec_t)ctx->inner_exec, s));
+  ctx->launches += 2 * POLL_GROUP + 1;
+  return HYDOT_OK;
 }
 
 template <typename T, typename X, typename O>
@@ -1123,22 +1201,30 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
     HYDOT_CUDA_TRY(ctx, cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
     int slot = 0;
     bool stop = false;
+    // rolling passes (FP32 real fields, TMA): the iteration index lives on the device
+    const bool roll = std::is_same<T, float>::value && ctx->use_tma;
+    const unsigned nrb =
+        roll ? (unsigned)((long long)b.nrhs * g.ntx * g.nty * ((g.nz + ctx->dir_seg - 1) / ctx->dir_seg)) : 0u;
+    if (roll) HYDOT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_it, 0, sizeof(int), s));
     while (!stop && it < MAX_INNER_PER_CYCLE) {
       int g_end = std::min(it + POLL_GROUP, MAX_INNER_PER_CYCLE);
       // autotuning: a group that does not start the cycle runs one candidate variant and is timed
-      const int variant = ctx->use_tma ? roll_pick(ctx) : 0;
-      const bool tuning = ctx->use_tma && ctx->tune.variant < 0 && it > 0;
+      const int variant = roll ? roll_pick(ctx) : 0;
+      const bool tuning = roll && ctx->tune.variant < 0 && it > 0;
       const int g_begin = it;
       if (tuning) HYDOT_CUDA_TRY(ctx, cudaEventRecord(ctx->tune_ev[0], s));
-      for (; it < g_end; ++it) {
-        if constexpr (std::is_same<T, float>::value) {
-          if (ctx->use_tma) {
-            const int seg = ctx->dir_seg;
-            const unsigned nrb = (unsigned)((long long)b.nrhs * g.ntx * g.nty * ((g.nz + seg - 1) / seg));
-            roll_dispatch(ctx, variant, g, b, it, nrb, (float*)E, (float*)R, (float* const*)P);
-            continue;
-          }
+      if (roll) {
+        if (ctx->use_graphs && !tuning && ctx->tune.variant >= 0 && !ctx->timer.on) {
+          int rc = inner_graph_launch(ctx, g, b, variant, nrb, (float*)E, (float*)R, (float* const*)P);
+          if (rc) return rc;
+          it = g_end;
+        } else {
+          for (; it < g_end; ++it) roll_dispatch(ctx, variant, g, b, it, nrb, (float*)E, (float*)R, (float* const*)P);
+          k_bump<<<1, 1, 0, s>>>(ctx->d_it, POLL_GROUP);
+          ++ctx->launches;
         }
+      }
+      for (; it < g_end; ++it) {
         cudaEvent_t t0 = timer_begin(ctx);
         k_dir<T><<<nblk, blk, 0, s>>>(g, b, it, R, P[it & 1], P[(it + 1) & 1]);
         ++ctx->launches;
@@ -1313,6 +1399,10 @@ int solver_alloc(hydot_ctx* ctx) {
   HYDOT_CUDA_TRY(ctx, cudaMallocHost(&ctx->h_pinned, sizeof(int) * 8));
   HYDOT_CUDA_TRY(ctx, cudaMalloc(&ctx->d_err, sizeof(int)));
   HYDOT_CUDA_TRY(ctx, cudaMemset(ctx->d_err, 0, sizeof(int)));
+  HYDOT_CUDA_TRY(ctx, cudaMalloc(&ctx->d_it, sizeof(int)));
+  HYDOT_CUDA_TRY(ctx, cudaMemset(ctx->d_it, 0, sizeof(int)));
+  ctx->use_graphs = !getenv_flag("HYDOT_NO_GRAPHS");
+  HYDOT_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
   if (ctx->use_tma) {
     int rc = roll_setup(ctx);
     // per slab depth (2, 4, 8 planes): halo slabs of r and p (pass 1 reads r and p_old, pass 2 reads
@@ -1360,6 +1450,9 @@ void solver_free(hydot_ctx* ctx) {
   cudaFree(ctx->d_counter);
   cudaFree(ctx->d_err);
   if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+  cudaFree(ctx->d_it);
+  if (ctx->inner_exec) cudaGraphExecDestroy((cudaGraphExec_t)ctx->inner_exec);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   if (ctx->tune_ev[0]) cudaEventDestroy(ctx->tune_ev[0]);
   if (ctx->tune_ev[1]) cudaEventDestroy(ctx->tune_ev[1]);
 }

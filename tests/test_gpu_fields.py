@@ -225,3 +225,20 @@ def test_roll_variants_bitwise_identical_and_autotuner_settles(hd, oracle_fields
     assert tu["variant"] in range(4)
     assert all(v["ns_per_cell"] > 0 for v in tu["variants"])
     assert [(v["planes"], v["buffers"]) for v in tu["variants"]] == [(4, 4), (2, 6), (8, 3), (4, 5)]
+
+
+def test_graph_replay_matches_direct_launches(hd, monkeypatch):
+    """Groups of inner iterations replayed from a CUDA graph give the bits of direct launches."""
+    p = workloads.make_problem(workloads.Grid(24, 24, 16, 2.0), 8, 8, 4, seed=23, geometry="reflection")
+    monkeypatch.setenv("HYDOT_ROLL_VARIANT", "0")
+    res = {}
+    for flag in ("0", "1"):
+        monkeypatch.setenv("HYDOT_NO_GRAPHS", flag)
+        with hd.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=1e-8, cw_floor=100.0) as ctx:
+            a = ctx.solve_fields(0, p.n_lambda)
+            b_ = ctx.solve_fields(0, p.n_lambda)  # second call replays the cached graph
+            c = ctx.solve_fields(1, 2)            # another batch: the graph is updated
+        res[flag] = (a, b_, c)
+    for q in range(3):
+        assert torch.equal(res["0"][q][0], res["1"][q][0]) and torch.equal(res["0"][q][1], res["1"][q][1])
+    assert torch.equal(res["0"][0][0], res["0"][1][0])
