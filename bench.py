@@ -47,8 +47,8 @@ WORKLOAD = ("cw-mixed-64x64x48: 64x64x48 grid (h=2 mm), 32 sources + 32 detector
 KERNEL_NAMES = {"dir": "k_dir_tma (inner PCG pass 1)", "update": "k_update_tma (inner PCG pass 2)",
                 "residual": "k_residual (FP64 residual)", "born_rows": "k_born_rows (Born-row assembly)",
                 "apply": "k_apply_partial+reduce (J x)", "apply_T": "k_apply_T_partial+reduce (J^T y)",
-                "sketch_range": "k_sketch_gemm<0> (tensor-core Y = J Omega)",
-                "sketch_project": "k_sketch_gemm<1> (tensor-core B^T += J^T Q)"}
+                "sketch_range": "k_range_ws (tensor-core Y = J Omega)",
+                "sketch_project": "k_project_ws (tensor-core B^T += J^T Q)"}
 # DRAM bytes (read + write, ncu) per algorithmic byte, from the captures summarised under profiles/
 # (smaller cases of the same kernels, scaled by the units processed: active fields or rows)
 DRAM_PER_ALGORITHMIC_BYTE = {"dir": (100.96e6 + 24.81e6) / (64 * 3 * 196608 * 4),
@@ -418,8 +418,6 @@ def sketch_phase(hd, pk, n_lam=4, rank=200, over=20, n_probe=32):
         tf = k["bytes"] / (k["ms"] / 1e3) / 1e12 if k["ms"] > 0 else None
         out[name] = {"ms": k["ms"], "launches": k["launches"], "algorithmic_tflop": k["bytes"] / 1e12,
                      "tflops": tf, "peak_tflops": pk["bf16_tflops"], "frac": tf / pk["bf16_tflops"] if tf else None}
-    # the projection pass issues one MMA pass per chromophore: executed = n_chrom x algorithmic flops
-    out["project"]["executed_over_algorithmic"] = nc
     out["wall_s"] = wall
     out["kept_directions"] = kept
     out["singular_values"] = {"s1": float(S[0]), "s200": float(S[rank - 1])}
@@ -516,7 +514,8 @@ def run_kernel_case(name: str, reps: int = 3):
     """A small, bounded case of one hot kernel on the workload's grid, for profiler captures:
     born_rows   512 rows of one 16-wavelength chunk (1.6 GB written per launch)
     solver      the 64 fields of one wavelength (FP32 PCG + FP64 refinement, ~300 MB of vectors)
-    sketch      the tensor-core range pass Y = J Omega over one 16-wavelength chunk (rank 200 + 20)
+    sketch      the tensor-core passes Y = J Omega and B^T += J^T Q over one 16-wavelength chunk
+                (rank 200 + 20)
     apply       J x and J^T r over one 16-wavelength chunk of fields
     """
     import torch
@@ -544,9 +543,13 @@ def run_kernel_case(name: str, reps: int = 3):
             a.record()
             ctx.solve_fields(0, 1, ps, pd)
         elif name == "sketch":
-            om = torch.randn(nc, 220, N, device="cuda", generator=gen).to(torch.bfloat16) if not times else om
+            if not times:
+                om = torch.randn(nc, 220, N, device="cuda", generator=gen).to(torch.bfloat16)
+                Q = torch.randn(ns * nd * CHUNK, 224, device="cuda", generator=gen)
+                Bt = torch.zeros(nc * N, 224, device="cuda")
             a.record()
             ctx.sketch_range(ps, pd, 0, CHUNK, om, 220)
+            ctx.sketch_project(ps, pd, 0, CHUNK, Q, 220, Bt)
         elif name == "apply":
             x = torch.rand(nc * N, device="cuda", generator=gen)
             a.record()

@@ -227,6 +227,407 @@ __global__ void __launch_bounds__(128) k_sketch_gemm(SketchArgs a, const __grid_
   if (warp == 0) tmem_dealloc(tmem, SK_TMEM_COLS);
 }
 
+// ---------------------------------------------------------------- warp-specialised range pass
+// Y = J Omega for a (wavelength, source block, detector block) item and a range of K-steps:
+//   warp 0        TMA producer: per K-step the B tile (M_l, 224 x 64 BF16, 128-byte swizzle) and
+//                 the FP32 field slabs of the item's sources (2 S_a rows) and detectors (D_t rows);
+//   warp 1        one thread issues the MMAs: two 128 x 224 accumulators in tensor memory (the
+//                 item's first and second S_a sources x D_t detectors) share each B tile;
+//   warps 2..9    form the A tiles (Hadamard products, BF16, swizzled K-major) from the field
+//                 slabs in shared memory, then read the accumulators back (epilogue).
+// RG_STAGES operand stages and 2 A stages; the K range of an item is split over CTAs (partials
+// summed by a second kernel in a fixed order) so that the grid covers the SMs.
+constexpr int RG_THREADS = 320;
+constexpr int RG_STAGES = 3;
+constexpr int RG_FROWS = 72;                                   // field rows per stage (2 S_a + D_t <= 72)
+constexpr uint32_t RG_B_BYTES = SK_N * SK_K * 2;               // 28,672
+constexpr uint32_t RG_F_BYTES = RG_FROWS * SK_K * 4;           // 18,432
+constexpr uint32_t RG_STAGE = RG_B_BYTES + RG_F_BYTES;         // 47,104 = 46 x 1024
+constexpr uint32_t RG_A_STAGE = 2 * SK_A_BYTES;                // two 128 x 64 A tiles
+constexpr size_t RG_SMEM = (size_t)RG_STAGES * RG_STAGE + 2 * RG_A_STAGE + 1024;
+constexpr uint32_t RG_TMEM_COLS = 512;                         // accumulators at columns 0 and 256
+
+struct RangeArgs {
+  int ns, nd, nlam;
+  long long N;
+  int S_a, D_t, nsb, ndb;    // sources per accumulator, detectors per block, source / detector blocks
+  int nk, k_per_split, nsplit;
+  long long P;               // rows of Y in the slice
+  float* out;                // Y (nsplit == 1, scaled) or partials [nsplit][P][SK_N]
+  long long ldo;
+  float scale;
+  int* err;
+};
+
+__global__ void __launch_bounds__(RG_THREADS, 1)
+    k_range_ws(RangeArgs a, const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapPs,
+               const __grid_constant__ CUtensorMap mapPd) {
+  extern __shared__ uint8_t sk_dsm[];
+  uint8_t* base = align1024(sk_dsm);
+  uint8_t* abuf = base + (size_t)RG_STAGES * RG_STAGE;
+  __shared__ uint64_t full[RG_STAGES], empty[RG_STAGES], afull[2], aempty[2], accf;
+  __shared__ uint32_t s_tmem;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int item = blockIdx.x / a.nsplit, ks = blockIdx.x - item * a.nsplit;
+  const int l = item / (a.nsb * a.ndb);
+  const int rem = item - l * a.nsb * a.ndb;
+  const int sb = rem / a.ndb, db = rem - sb * a.ndb;
+  const int s0 = sb * 2 * a.S_a, d0 = db * a.D_t;
+  const int kt0 = ks * a.k_per_split, kt1 = min(a.nk, kt0 + a.k_per_split);
+  const int nku = max(kt1 - kt0, 0);
+  if (tid == 0) {
+    for (int q = 0; q < RG_STAGES; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], 9);  // 8 former warps + the MMA commit
+    }
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(&afull[q], 8);
+      mbar_init(&aempty[q], 1);
+    }
+    mbar_init(&accf, 1);
+    mbar_fence_init();
+  }
+  if (warp == 1) tmem_alloc(&s_tmem, RG_TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  const uint32_t fbytes = (uint32_t)(2 * a.S_a + a.D_t) * SK_K * 4;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int u = 0; u < nku; ++u) {
+        const int st = u % RG_STAGES;
+        if (u >= RG_STAGES) wait_or_flag(&empty[st], (uint32_t)((u / RG_STAGES - 1) & 1), a.err);
+        uint8_t* sb_ = base + (size_t)st * RG_STAGE;
+        const int x = (kt0 + u) * SK_K;
+        mbar_expect_tx(&full[st], RG_B_BYTES + fbytes);
+        tma_load_3d(sb_, &mapB, &full[st], x, 0, l);
+        tma_load_3d(sb_ + RG_B_BYTES, &mapPs, &full[st], x, s0, l);
+        tma_load_3d(sb_ + RG_B_BYTES + 2 * a.S_a * SK_K * 4, &mapPd, &full[st], x, d0, l);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t IDESC = idesc_bf16_f32(SK_M, SK_N);
+      for (int u = 0; u < nku; ++u) {
+        const int st = u % RG_STAGES, as = u & 1;
+        wait_or_flag(&full[st], (uint32_t)((u / RG_STAGES) & 1), a.err);
+        wait_or_flag(&afull[as], (uint32_t)((u >> 1) & 1), a.err);
+        tc_fence_after();
+        const uint32_t b_addr = smem_addr(base + (size_t)st * RG_STAGE);
+        const uint32_t a_addr = smem_addr(abuf + (size_t)as * RG_A_STAGE);
+#pragma unroll
+        for (int acc = 0; acc < 2; ++acc)
+#pragma unroll
+          for (int kk = 0; kk < SK_K / 16; ++kk)
+            tc_mma_bf16(tmem + (uint32_t)(acc * 256), smem_desc_sw128(a_addr + acc * SK_A_BYTES + kk * 32),
+                        smem_desc_sw128(b_addr + kk * 32), IDESC, (u > 0 || kk > 0) ? 1u : 0u);
+        tc_commit(&empty[st]);
+        tc_commit(&aempty[as]);
+      }
+      tc_commit(&accf);
+    }
+  } else {
+    // ---- A formers. Thread f keeps detector chunks (d, 8 voxels) pc = f, f + 256, ... in registers
+    // and multiplies each by the matching chunk of every source of the item (those reads are warp
+    // broadcasts), so each field value is read from shared memory about once per K-step.
+    const int f = tid - 64;
+    const int rows = a.S_a * a.D_t;
+    const int C = a.D_t * 8;
+    // rows that no pair maps to stay zero: write them once in both A stages
+    for (int e = f; e < 2 * 2 * (SK_M - rows) * 8; e += 256) {
+      const int ch = e & 7, rr = rows + ((e >> 3) % (SK_M - rows)), sa = (e >> 3) / (SK_M - rows);
+      *reinterpret_cast<uint4*>(abuf + (size_t)(sa >> 1) * RG_A_STAGE + (sa & 1) * SK_A_BYTES +
+                                sw128_offset(rr, ch * 8)) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    for (int u = 0; u < nku; ++u) {
+      const int st = u % RG_STAGES, as = u & 1;
+      if (!mbar_wait_bounded(&full[st], (uint32_t)((u / RG_STAGES) & 1))) atomicExch(a.err, 1);
+      if (u >= 2 && !mbar_wait_bounded(&aempty[as], (uint32_t)((u / 2 - 1) & 1))) atomicExch(a.err, 1);
+      const float* fps = reinterpret_cast<const float*>(base + (size_t)st * RG_STAGE + RG_B_BYTES);
+      const float* fpd = fps + 2 * a.S_a * SK_K;
+      uint8_t* At = abuf + (size_t)as * RG_A_STAGE;
+      for (int pc = f; pc < C; pc += 256) {
+        const int dl = pc >> 3, ch = pc & 7;
+        const float4 d0v = *reinterpret_cast<const float4*>(fpd + dl * SK_K + ch * 8);
+        const float4 d1v = *reinterpret_cast<const float4*>(fpd + dl * SK_K + ch * 8 + 4);
+        for (int sl = 0; sl < 2 * a.S_a; ++sl) {
+          const int acc = sl >= a.S_a ? 1 : 0;
+          const int rr = (sl - acc * a.S_a) * a.D_t + dl;
+          const float4 s0v = *reinterpret_cast<const float4*>(fps + sl * SK_K + ch * 8);
+          const float4 s1v = *reinterpret_cast<const float4*>(fps + sl * SK_K + ch * 8 + 4);
+          uint4 pk;
+          pk.x = pack_bf16x2(s0v.x * d0v.x, s0v.y * d0v.y);
+          pk.y = pack_bf16x2(s0v.z * d0v.z, s0v.w * d0v.w);
+          pk.z = pack_bf16x2(s1v.x * d1v.x, s1v.y * d1v.y);
+          pk.w = pack_bf16x2(s1v.z * d1v.z, s1v.w * d1v.w);
+          *reinterpret_cast<uint4*>(At + acc * SK_A_BYTES + sw128_offset(rr, ch * 8)) = pk;
+        }
+      }
+      fence_async_smem();
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&afull[as]);
+        mbar_arrive(&empty[st]);
+      }
+    }
+    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 of accumulator (w - 2) / 4
+    if (!mbar_wait_bounded(&accf, 0u)) atomicExch(a.err, 1);
+    tc_fence_after();
+    const int q4 = warp & 3, acc = (warp - 2) >> 2;
+    const int rr = q4 * 32 + lane;
+    bool ok = nku > 0 && rr < rows;
+    long long r_out = 0;
+    if (ok) {
+      const int s = s0 + acc * a.S_a + rr / a.D_t, d = d0 + rr % a.D_t;
+      ok = s < a.ns && d < a.nd;
+      r_out = ((long long)s * a.nd + d) * a.nlam + l;
+    }
+    float* dst = nullptr;
+    float sc = 1.f;
+    if (a.nsplit == 1) {
+      dst = a.out + r_out * a.ldo;
+      sc = a.scale;
+    } else {
+      dst = a.out + ((long long)ks * a.P + r_out) * SK_N;
+    }
+    const uint32_t tbase = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(acc * 256);
+    for (int c0 = 0; c0 < SK_N; c0 += 16) {
+      float v[16];
+      tmem_ld16(tbase + (uint32_t)c0, v);
+      if (ok) {
+#pragma unroll
+        for (int q = 0; q < 16; q += 4)
+          *reinterpret_cast<float4*>(dst + c0 + q) = make_float4(sc * v[q], sc * v[q + 1], sc * v[q + 2], sc * v[q + 3]);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) tmem_dealloc(tmem, RG_TMEM_COLS);
+}
+
+// Y[r][k] = scale * sum_s part[s][r][k] (fixed order over the K splits)
+__global__ void k_range_reduce(const float* __restrict__ part, int nsplit, long long P, float scale,
+                               float* __restrict__ Y, long long ldY) {
+  const long long total = P * (SK_N / 4);
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (long long)gridDim.x * blockDim.x) {
+    const long long r = q / (SK_N / 4);
+    const int k4 = (int)(q - r * (SK_N / 4)) * 4;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int sp = 0; sp < nsplit; ++sp) {
+      const float4 v = *reinterpret_cast<const float4*>(part + ((long long)sp * P + r) * SK_N + k4);
+      acc.x += v.x;
+      acc.y += v.y;
+      acc.z += v.z;
+      acc.w += v.w;
+    }
+    *reinterpret_cast<float4*>(Y + r * ldY + k4) = make_float4(scale * acc.x, scale * acc.y, scale * acc.z, scale * acc.w);
+  }
+}
+
+// ---------------------------------------------------------------- warp-specialised projection pass
+// B^T[(c,x), k] += -h^3 sum_(l,s,d) eps_c(l) phi_s(x) phi_d(x) Q[(s,d,l), k] for a tile of 128 voxels
+// and two chromophores (two 128 x 224 accumulators sharing each A tile). K runs over the pairs of
+// each wavelength (padded to a multiple of 64 per wavelength). The tile's fields of the current
+// wavelength (n_src + n_det rows of 128 voxels, FP32) stay in shared memory while its K-steps run.
+//   warp 0        TMA: the two B tiles (eps_c-scaled Q, 224 x 64 BF16 each) per K-step;
+//   warp 1        one thread issues the MMAs;
+//   warp 2        TMA: the field block of each wavelength, once its predecessor is consumed;
+//   warps 3..10   form the A tiles and read the accumulators back.
+constexpr int PJ_THREADS = 352;
+constexpr int PJ_M = 128;                                     // voxels per tile
+constexpr uint32_t PJ_B_STAGE = 2 * SK_N * SK_K * 2;          // two B tiles: 57,344 B
+constexpr uint32_t PJ_F_BYTES = 128 * PJ_M * 4;               // n_src + n_det <= 128 rows: 65,536 B
+constexpr size_t PJ_SMEM = 2 * (size_t)PJ_B_STAGE + 2 * (size_t)SK_A_BYTES + PJ_F_BYTES + 1024;
+
+struct ProjArgs {
+  int ns, nd, nlam, nc, Kl;  // Kl: K-steps per wavelength
+  long long N;
+  float* Bt;
+  long long ldB;
+  float scale;
+  int* err;
+};
+
+__global__ void __launch_bounds__(PJ_THREADS, 1)
+    k_project_ws(ProjArgs a, const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapPs,
+                 const __grid_constant__ CUtensorMap mapPd) {
+  extern __shared__ uint8_t sk_dsm[];
+  uint8_t* base = align1024(sk_dsm);
+  uint8_t* abuf = base + 2 * (size_t)PJ_B_STAGE;
+  float* fld = reinterpret_cast<float*>(abuf + 2 * (size_t)SK_A_BYTES);  // [ns + nd][128]
+  __shared__ uint64_t bfull[2], bempty[2], afull[2], aempty[2], ffull, fempty, accf;
+  __shared__ uint32_t s_tmem;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tile = blockIdx.x / ((a.nc + 1) / 2), cp = blockIdx.x - tile * ((a.nc + 1) / 2);
+  const long long x0 = (long long)tile * PJ_M;
+  const int c0 = 2 * cp;
+  const int nku = a.nlam * a.Kl;
+  if (tid == 0) {
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(&bfull[q], 1);
+      mbar_init(&bempty[q], 1);
+      mbar_init(&afull[q], 8);
+      mbar_init(&aempty[q], 1);
+    }
+    mbar_init(&ffull, 1);
+    mbar_init(&fempty, 8);
+    mbar_init(&accf, 1);
+    mbar_fence_init();
+  }
+  if (warp == 1) tmem_alloc(&s_tmem, RG_TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int u = 0; u < nku; ++u) {
+        const int bs = u & 1;
+        if (u >= 2) wait_or_flag(&bempty[bs], (uint32_t)((u / 2 - 1) & 1), a.err);
+        uint8_t* dst = base + (size_t)bs * PJ_B_STAGE;
+        mbar_expect_tx(&bfull[bs], PJ_B_STAGE);
+        tma_load_3d(dst, &mapB, &bfull[bs], u * SK_K, 0, c0);
+        tma_load_3d(dst + SK_N * SK_K * 2, &mapB, &bfull[bs], u * SK_K, 0, c0 + 1);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t IDESC = idesc_bf16_f32(SK_M, SK_N);
+      for (int u = 0; u < nku; ++u) {
+        const int bs = u & 1;
+        wait_or_flag(&bfull[bs], (uint32_t)((u >> 1) & 1), a.err);
+        wait_or_flag(&afull[bs], (uint32_t)((u >> 1) & 1), a.err);
+        tc_fence_after();
+        const uint32_t b_addr = smem_addr(base + (size_t)bs * PJ_B_STAGE);
+        const uint32_t a_addr = smem_addr(abuf + (size_t)bs * SK_A_BYTES);
+#pragma unroll
+        for (int acc = 0; acc < 2; ++acc)
+#pragma unroll
+          for (int kk = 0; kk < SK_K / 16; ++kk)
+            tc_mma_bf16(tmem + (uint32_t)(acc * 256), smem_desc_sw128(a_addr + kk * 32),
+                        smem_desc_sw128(b_addr + acc * SK_N * SK_K * 2 + kk * 32), IDESC, (u > 0 || kk > 0) ? 1u : 0u);
+        tc_commit(&bempty[bs]);
+        tc_commit(&aempty[bs]);
+      }
+      tc_commit(&accf);
+    }
+  } else if (warp == 2) {
+    if (lane == 0) {
+      const uint32_t fb = (uint32_t)(a.ns + a.nd) * PJ_M * 4;
+      for (int l = 0; l < a.nlam; ++l) {
+        if (l >= 1) wait_or_flag(&fempty, (uint32_t)((l - 1) & 1), a.err);
+        mbar_expect_tx(&ffull, fb);
+        tma_load_3d(fld, &mapPs, &ffull, (int)x0, 0, l);
+        tma_load_3d(fld + a.ns * PJ_M, &mapPd, &ffull, (int)x0, 0, l);
+      }
+    }
+  } else {
+    // ---- A formers: thread f takes voxel row (id & 127) and pair chunk (id >> 7) for id = j*256 + f
+    const int f = tid - 96;
+    const int npairs = a.ns * a.nd;
+    const bool nd8 = (a.nd & 7) == 0;
+    const float* psm = fld;
+    const float* pdm = fld + a.ns * PJ_M;
+    for (int u = 0; u < nku; ++u) {
+      const int l = u / a.Kl, kq = u - l * a.Kl, as = u & 1;
+      if (kq == 0 && !mbar_wait_bounded(&ffull, (uint32_t)(l & 1))) atomicExch(a.err, 1);
+      if (u >= 2 && !mbar_wait_bounded(&aempty[as], (uint32_t)((u / 2 - 1) & 1))) atomicExch(a.err, 1);
+      uint8_t* At = abuf + (size_t)as * SK_A_BYTES;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int id = j * 256 + f;
+        const int row = id & (PJ_M - 1), ch = id >> 7;
+        const int q0 = kq * SK_K + ch * 8;
+        int s = q0 / a.nd, d = q0 - s * a.nd;
+        float v[8];
+        if (nd8 && q0 + 8 <= npairs) {
+          // the 8 pairs share their source (n_det % 8 == 0): one source value, 8 detector values
+          const float sv = psm[s * PJ_M + row];
+          const float* pr = pdm + d * PJ_M + row;
+#pragma unroll
+          for (int i = 0; i < 8; ++i) v[i] = sv * pr[i * PJ_M];
+        } else {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            // clamped indices keep every read inside the field block; the padding pairs give 0
+            const float pv = psm[min(s, a.ns - 1) * PJ_M + row] * pdm[d * PJ_M + row];
+            v[i] = (q0 + i < npairs) ? pv : 0.f;
+            if (++d == a.nd) {
+              d = 0;
+              ++s;
+            }
+          }
+        }
+        uint4 pk;
+        pk.x = pack_bf16x2(v[0], v[1]);
+        pk.y = pack_bf16x2(v[2], v[3]);
+        pk.z = pack_bf16x2(v[4], v[5]);
+        pk.w = pack_bf16x2(v[6], v[7]);
+        *reinterpret_cast<uint4*>(At + sw128_offset(row, ch * 8)) = pk;
+      }
+      fence_async_smem();
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&afull[as]);
+        if (kq == a.Kl - 1) mbar_arrive(&fempty);
+      }
+    }
+    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 of accumulator (w - 3) / 4
+    if (!mbar_wait_bounded(&accf, 0u)) atomicExch(a.err, 1);
+    tc_fence_after();
+    const int q4 = warp & 3, acc = (warp - 3) >> 2;
+    const long long x = x0 + q4 * 32 + lane;
+    const int c = c0 + acc;
+    const bool ok = nku > 0 && x < a.N && c < a.nc;
+    float* dst = a.Bt + ((long long)c * a.N + x) * a.ldB;
+    const uint32_t tbase = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(acc * 256);
+    for (int k0 = 0; k0 < SK_N; k0 += 16) {
+      float v[16];
+      tmem_ld16(tbase + (uint32_t)k0, v);
+      if (ok) {
+#pragma unroll
+        for (int q = 0; q < 16; q += 4) {
+          float4 o = *reinterpret_cast<float4*>(dst + k0 + q);
+          o.x = fmaf(a.scale, v[q], o.x);
+          o.y = fmaf(a.scale, v[q + 1], o.y);
+          o.z = fmaf(a.scale, v[q + 2], o.z);
+          o.w = fmaf(a.scale, v[q + 3], o.w);
+          *reinterpret_cast<float4*>(dst + k0 + q) = o;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) tmem_dealloc(tmem, RG_TMEM_COLS);
+}
+
+// Qc[c][k][l * Pl + q] = eps_c(lambda_l) * Q[row][k] for the pairs q = s * nd + d < ns * nd of
+// wavelength l (row = (s*nd + d)*nlam + l), zero on the padding q >= ns * nd and for k >= ncols.
+__global__ void k_form_qc_padded(const float* __restrict__ Q, long long ldq, const double* __restrict__ eps, int lam0,
+                                 int nlam, int ns, int nd, int nc, int ncols, long long Pl,
+                                 __nv_bfloat16* __restrict__ Qc) {
+  const long long Pt = (long long)nlam * Pl;
+  const long long total = (long long)nc * SK_N * Pt;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const long long pp = i % Pt;
+    const int k = (int)((i / Pt) % SK_N);
+    const int c = (int)(i / (Pt * SK_N));
+    const int l = (int)(pp / Pl);
+    const long long q = pp - (long long)l * Pl;
+    float v = 0.f;
+    if (q < (long long)ns * nd && k < ncols) {
+      const long long r = q * nlam + l;
+      v = (float)eps[(size_t)(lam0 + l) * nc + c] * Q[r * ldq + k];
+    }
+    Qc[i] = __float2bfloat16_rn(v);
+  }
+}
+
 // Mt[l][k][x] = sum_c eps_c(lambda_(lam0+l)) * Omega_t[c][k][x] in BF16 (k >= ncols: 0); 8 voxels per thread.
 __global__ void k_form_mt(const __nv_bfloat16* __restrict__ om, const double* __restrict__ eps, int lam0, int nlam,
                           int nc, int ncols, long long N, __nv_bfloat16* __restrict__ Mt) {
@@ -309,6 +710,22 @@ int encode_b_map(hydot_ctx* ctx, void* base, long long inner, long long outer, C
   return HYDOT_OK;
 }
 
+// 3-D FP32 map {d0, d1, d2} (d0 innermost, contiguous) with a {b0, b1, 1} box, no swizzle.
+int encode_f32_map(hydot_ctx* ctx, const void* base, long long d0, long long d1, long long d2, int b0, int b1,
+                   CUtensorMap* map) {
+  auto enc = tensor_map_encoder(ctx);
+  if (!enc) return HYDOT_ERR_CUDA;
+  cuuint64_t dims[3] = {(cuuint64_t)d0, (cuuint64_t)d1, (cuuint64_t)d2};
+  cuuint64_t strides[2] = {(cuuint64_t)d0 * 4, (cuuint64_t)d0 * 4 * d1};
+  cuuint32_t box[3] = {(cuuint32_t)b0, (cuuint32_t)b1, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(ctx, HYDOT_ERR_CUDA, "cuTensorMapEncodeTiled failed for a field slab map");
+  return HYDOT_OK;
+}
+
 int sketch_ws(hydot_ctx* ctx, size_t bytes) {
   if (ctx->sketch_ws_bytes >= bytes) return HYDOT_OK;
   if (ctx->d_sketch_ws) {
@@ -336,6 +753,8 @@ int set_sketch_smem(hydot_ctx* ctx) {
   if (!done) {
     HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(k_sketch_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SK_SMEM));
     HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(k_sketch_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SK_SMEM));
+    HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(k_range_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RG_SMEM));
+    HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(k_project_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PJ_SMEM));
     done = true;
   }
   return HYDOT_OK;
@@ -348,37 +767,66 @@ int sketch_range_impl(hydot_ctx* ctx, const float* ps, const float* pd, int lam0
   int rc = sketch_check(ctx, lam0, nlam, ncols);
   if (rc) return rc;
   if (!ps || !pd || !omega_t || !Y) return fail(ctx, HYDOT_ERR_ARG, "null pointer");
-  if (ldY < SK_N) return fail(ctx, HYDOT_ERR_ARG, "ldY must be >= 224");
+  if (ldY < SK_N || ldY % 4 != 0 || (reinterpret_cast<uintptr_t>(Y) & 15) != 0)
+    return fail(ctx, HYDOT_ERR_ARG, "Y must be 16-byte aligned with ldY >= 224 and ldY % 4 == 0");
   const long long N = ctx->N;
-  const size_t mt_bytes = (size_t)nlam * SK_N * N * 2;
-  if ((rc = sketch_ws(ctx, mt_bytes))) return rc;
+  const int ns = ctx->n_src, nd = ctx->n_det;
+  const long long P = (long long)nlam * ns * nd;
+  // items: (wavelength, block of 2 S_a sources, block of D_t detectors); each accumulator holds
+  // S_a x D_t pairs (<= 128 rows)
+  const int D_t = std::min(nd, 64);
+  const int S_a = std::min(32, SK_M / D_t);
+  const int nsb = (ns + 2 * S_a - 1) / (2 * S_a), ndb = (nd + D_t - 1) / D_t;
+  const long long items = (long long)nlam * nsb * ndb;
+  const int nk = (int)((N + SK_K - 1) / SK_K);
+  // split K so that the grid fills about eight waves of one CTA per SM, each split >= 32 K-steps
+  int nsplit = (int)std::max<long long>(1, std::min<long long>((8 * 152 + items - 1) / items, std::max(1, nk / 32)));
+  const int kps = (nk + nsplit - 1) / nsplit;
+  nsplit = (nk + kps - 1) / kps;
+  const size_t mt_bytes = ((size_t)nlam * SK_N * N * 2 + 255) / 256 * 256;
+  const size_t part_bytes = nsplit > 1 ? (size_t)nsplit * P * SK_N * 4 : 0;
+  if ((rc = sketch_ws(ctx, mt_bytes + part_bytes))) return rc;
   if ((rc = set_sketch_smem(ctx))) return rc;
   __nv_bfloat16* Mt = (__nv_bfloat16*)ctx->d_sketch_ws;
+  float* part = (float*)((uint8_t*)ctx->d_sketch_ws + mt_bytes);
   const long long tot = (long long)nlam * SK_N * (N / 8);
   k_form_mt<<<(unsigned)std::min<long long>((tot + 255) / 256, 152 * 32), 256, 0, ctx->stream>>>(
       (const __nv_bfloat16*)omega_t, ctx->d_eps, lam0, nlam, ctx->n_chrom, ncols, N, Mt);
   ++ctx->launches;
   HYDOT_CUDA_TRY(ctx, cudaGetLastError());
-  CUtensorMap map;
-  if ((rc = encode_b_map(ctx, Mt, N, nlam, &map))) return rc;
-  SketchArgs a{};
-  a.ps = ps;
-  a.pd = pd;
-  a.ns = ctx->n_src;
-  a.nd = ctx->n_det;
+  CUtensorMap mapB, mapPs, mapPd;
+  if ((rc = encode_b_map(ctx, Mt, N, nlam, &mapB))) return rc;
+  if ((rc = encode_f32_map(ctx, ps, N, ns, nlam, SK_K, 2 * S_a, &mapPs))) return rc;
+  if ((rc = encode_f32_map(ctx, pd, N, nd, nlam, SK_K, D_t, &mapPd))) return rc;
+  RangeArgs a{};
+  a.ns = ns;
+  a.nd = nd;
   a.nlam = nlam;
   a.N = N;
-  a.P = (long long)nlam * a.ns * a.nd;
-  a.tiles_per_lam = (a.ns * a.nd + SK_M - 1) / SK_M;
-  a.scale = (float)(-ctx->h * ctx->h * ctx->h);
-  a.out = Y;
+  a.S_a = S_a;
+  a.D_t = D_t;
+  a.nsb = nsb;
+  a.ndb = ndb;
+  a.nk = nk;
+  a.k_per_split = kps;
+  a.nsplit = nsplit;
+  a.P = P;
+  a.out = nsplit > 1 ? part : Y;
   a.ldo = ldY;
+  a.scale = (float)(-ctx->h * ctx->h * ctx->h);
   a.err = ctx->d_err;
   HYDOT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
+  if (nd * ns * nlam == 0) return HYDOT_OK;
   cudaEvent_t t0 = timer_begin(ctx);
-  k_sketch_gemm<0><<<(unsigned)(nlam * a.tiles_per_lam), 128, SK_SMEM, ctx->stream>>>(a, map);
+  k_range_ws<<<(unsigned)(items * nsplit), RG_THREADS, RG_SMEM, ctx->stream>>>(a, mapB, mapPs, mapPd);
   ++ctx->launches;
-  timer_end(ctx, t0, HYDOT_KERNEL_SKETCH_RANGE, 2.0 * (double)a.P * (double)N * ncols);
+  if (nsplit > 1) {
+    const long long tq = P * (SK_N / 4);
+    k_range_reduce<<<(unsigned)std::min<long long>((tq + 255) / 256, 152 * 16), 256, 0, ctx->stream>>>(
+        part, nsplit, P, a.scale, Y, ldY);
+    ++ctx->launches;
+  }
+  timer_end(ctx, t0, HYDOT_KERNEL_SKETCH_RANGE, 2.0 * (double)P * (double)N * ncols);
   HYDOT_CUDA_TRY(ctx, cudaGetLastError());
   return HYDOT_OK;
 }
@@ -390,15 +838,53 @@ int sketch_project_impl(hydot_ctx* ctx, const float* ps, const float* pd, int la
   if (!ps || !pd || !Q || !Bt) return fail(ctx, HYDOT_ERR_ARG, "null pointer");
   if (ldB < SK_N || ldQ < ncols) return fail(ctx, HYDOT_ERR_ARG, "ldB must be >= 224 and ldQ >= ncols");
   const long long N = ctx->N;
-  const int nc = ctx->n_chrom;
-  const long long P = (long long)nlam * ctx->n_src * ctx->n_det;
+  const int nc = ctx->n_chrom, ns = ctx->n_src, nd = ctx->n_det;
+  const long long P = (long long)nlam * ns * nd;
+  if ((rc = set_sketch_smem(ctx))) return rc;
+  HYDOT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
+  if (P == 0) return HYDOT_OK;
+  const float scale = (float)(-ctx->h * ctx->h * ctx->h);
+  if (ns + nd <= 128 && ldB % 4 == 0 && (reinterpret_cast<uintptr_t>(Bt) & 15) == 0) {
+    // warp-specialised kernel: per-wavelength pair blocks padded to whole K-steps
+    const int Kl = (int)(((long long)ns * nd + SK_K - 1) / SK_K);
+    const long long Pl = (long long)Kl * SK_K;
+    if ((rc = sketch_ws(ctx, (size_t)nc * SK_N * nlam * Pl * 2))) return rc;
+    __nv_bfloat16* Qc = (__nv_bfloat16*)ctx->d_sketch_ws;
+    const long long tot = (long long)nc * SK_N * nlam * Pl;
+    k_form_qc_padded<<<(unsigned)std::min<long long>((tot + 255) / 256, 152 * 32), 256, 0, ctx->stream>>>(
+        Q, ldQ, ctx->d_eps, lam0, nlam, ns, nd, nc, ncols, Pl, Qc);
+    ++ctx->launches;
+    HYDOT_CUDA_TRY(ctx, cudaGetLastError());
+    CUtensorMap mapB, mapPs, mapPd;
+    if ((rc = encode_b_map(ctx, Qc, nlam * Pl, nc, &mapB))) return rc;
+    if ((rc = encode_f32_map(ctx, ps, N, ns, nlam, PJ_M, ns, &mapPs))) return rc;
+    if ((rc = encode_f32_map(ctx, pd, N, nd, nlam, PJ_M, nd, &mapPd))) return rc;
+    ProjArgs a{};
+    a.ns = ns;
+    a.nd = nd;
+    a.nlam = nlam;
+    a.nc = nc;
+    a.Kl = Kl;
+    a.N = N;
+    a.Bt = Bt;
+    a.ldB = ldB;
+    a.scale = scale;
+    a.err = ctx->d_err;
+    const long long grid = ((N + PJ_M - 1) / PJ_M) * ((nc + 1) / 2);
+    cudaEvent_t t0 = timer_begin(ctx);
+    k_project_ws<<<(unsigned)grid, PJ_THREADS, PJ_SMEM, ctx->stream>>>(a, mapB, mapPs, mapPd);
+    ++ctx->launches;
+    timer_end(ctx, t0, HYDOT_KERNEL_SKETCH_PROJECT, 2.0 * (double)nc * (double)N * (double)P * ncols);
+    HYDOT_CUDA_TRY(ctx, cudaGetLastError());
+    return HYDOT_OK;
+  }
+  // general shapes: one launch per chromophore, A tiles formed from global loads
   const long long Pp = (P + 7) / 8 * 8;
   if ((rc = sketch_ws(ctx, (size_t)nc * SK_N * Pp * 2))) return rc;
-  if ((rc = set_sketch_smem(ctx))) return rc;
   __nv_bfloat16* Qc = (__nv_bfloat16*)ctx->d_sketch_ws;
   const long long tot = (long long)nc * SK_N * Pp;
   k_form_qc<<<(unsigned)std::min<long long>((tot + 255) / 256, 152 * 32), 256, 0, ctx->stream>>>(
-      Q, ldQ, ctx->d_eps, lam0, nlam, ctx->n_src, ctx->n_det, nc, ncols, P, Pp, Qc);
+      Q, ldQ, ctx->d_eps, lam0, nlam, ns, nd, nc, ncols, P, Pp, Qc);
   ++ctx->launches;
   HYDOT_CUDA_TRY(ctx, cudaGetLastError());
   CUtensorMap map;
@@ -406,16 +892,15 @@ int sketch_project_impl(hydot_ctx* ctx, const float* ps, const float* pd, int la
   SketchArgs a{};
   a.ps = ps;
   a.pd = pd;
-  a.ns = ctx->n_src;
-  a.nd = ctx->n_det;
+  a.ns = ns;
+  a.nd = nd;
   a.nlam = nlam;
   a.N = N;
   a.P = P;
-  a.scale = (float)(-ctx->h * ctx->h * ctx->h);
+  a.scale = scale;
   a.out = Bt;
   a.ldo = ldB;
   a.err = ctx->d_err;
-  HYDOT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
   const unsigned grid = (unsigned)((N + SK_M - 1) / SK_M);
   cudaEvent_t t0 = timer_begin(ctx);
   for (int c = 0; c < nc; ++c) {

@@ -126,3 +126,71 @@ def test_rank_r_factorisation_near_optimal(lib, case):
     assert np.abs(S[:20] / sig[:20] - 1).max() < 1e-2
     err = np.linalg.norm(J - (U * S) @ V.T, 2)
     assert err <= 10 * sig[rank] + 1e-2 * sig[0], (err / sig[0], sig[rank] / sig[0])
+
+
+def _range_ref_bf16(p, rs, rd, om_b, rows_sel):
+    """-h^3 bf16(phi_s phi_d) @ bf16(sum_c eps_c Omega_c)^T for the selected rows (s, d, lambda)."""
+    nd, nl, h3 = p.n_det, p.n_lambda, p.grid.h ** 3
+    out = {}
+    Ms = {}
+    for r in rows_sel:
+        lam = r % nl
+        s, d = divmod(r // nl, nd)
+        if lam not in Ms:
+            Ms[lam] = bf16_round(np.einsum("c,ckx->kx", p.eps[lam].astype(np.float32),
+                                           om_b.astype(np.float32)).astype(np.float32))
+        a = bf16_round(rs[lam, s] * rd[lam, d])
+        out[r] = -h3 * Ms[lam] @ a
+    return out
+
+
+@pytest.mark.parametrize("shape", [
+    # (grid, n_src, n_det, n_lambda): K split over CTAs (long K, few items)
+    ((48, 40, 32), 8, 8, 2),
+    # detectors per block below 64 and not a power of two; partial source blocks
+    ((24, 20, 16), 30, 24, 2),
+    # more than 64 detectors: two detector blocks, the second partial
+    ((16, 16, 12), 6, 100, 1),
+])
+def test_sketch_range_shapes(lib, shape):
+    (nx, ny, nz), ns, nd, nl = shape
+    p = workloads.make_problem(workloads.Grid(nx, ny, nz, 2.0), ns, nd, nl, seed=41, geometry="transmission", margin=0)
+    rs, rd = osolve.fields_separable(p)
+    rs, rd = rs.astype(np.float32), rd.astype(np.float32)
+    N, nc, ncols = p.grid.N, p.n_chrom, 220
+    om = workloads.gaussian(43, (nc, ncols, N)).astype(np.float32)
+    om_b = bf16_round(om)
+    with lib.Context.from_problem(p, precision="mixed", tol=1e-8, tol_cw=0.0) as ctx:
+        Y = ctx.sketch_range(torch.tensor(rs, device="cuda"), torch.tensor(rd, device="cuda"), 0, nl,
+                             torch.tensor(om, device="cuda").to(torch.bfloat16), ncols).cpu().double().numpy()
+    assert np.all(Y[:, ncols:] == 0.0)
+    rng = np.random.default_rng(5)
+    rows = sorted(set(rng.choice(p.M, size=min(p.M, 48), replace=False).tolist()) | {0, p.M - 1})
+    ref = _range_ref_bf16(p, rs, rd, om_b, rows)
+    for r in rows:
+        err = np.abs(Y[r, :ncols] - ref[r]).max() / np.abs(ref[r]).max()
+        assert err <= 2e-3, (r, err)
+
+
+def test_sketch_project_general_shape_fallback(lib):
+    """n_src + n_det > 128: the projection takes the general kernel; same emulated reference."""
+    p = workloads.make_problem(workloads.Grid(12, 12, 4, 2.0), 72, 64, 1, seed=44, geometry="transmission", margin=0)
+    rs, rd = osolve.fields_separable(p)
+    rs, rd = rs.astype(np.float32), rd.astype(np.float32)
+    N, nc, ncols, nd = p.grid.N, p.n_chrom, 200, p.n_det
+    Q = workloads.gaussian(45, (p.M, ncols)).astype(np.float32)
+    with lib.Context.from_problem(p, precision="mixed", tol=1e-8, tol_cw=0.0) as ctx:
+        Bt = torch.zeros(nc * N, 224, device="cuda")
+        Qp = torch.zeros(p.M, 224, device="cuda")
+        Qp[:, :ncols] = torch.tensor(Q, device="cuda")
+        ctx.sketch_project(torch.tensor(rs, device="cuda"), torch.tensor(rd, device="cuda"), 0, 1, Qp, ncols, Bt)
+        Bt = Bt.cpu().double().numpy()[:, :ncols]
+    h3 = p.grid.h ** 3
+    ref = np.zeros_like(Bt)
+    for s in range(p.n_src):
+        A = bf16_round(rs[0, s][None, :] * rd[0])
+        rows = [s * nd + d for d in range(nd)]
+        for c in range(nc):
+            ref[c * N:(c + 1) * N] += -h3 * A.T @ bf16_round((np.float32(p.eps[0, c]) * Q[rows]).astype(np.float32))
+    err = np.abs(Bt - ref).max(axis=0) / np.abs(ref).max(axis=0)
+    assert err.max() <= 2e-3, err.max()
