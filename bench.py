@@ -44,19 +44,20 @@ TOL_CW = 1e-8
 CW_FLOOR = 100.0
 WORKLOAD = ("cw-mixed-64x64x48: 64x64x48 grid (h=2 mm), 32 sources + 32 detectors, 128 wavelengths "
             "(8,192 field solves), explicit FP32 Born rows 131,072 x 786,432 in row chunks, J x and J^T r")
-KERNEL_NAMES = {"dir": "k_dir_tma (inner PCG pass 1)", "update": "k_update_tma (inner PCG pass 2)",
+KERNEL_NAMES = {"dir": "k_dir_roll (inner PCG pass 1)", "update": "k_update_roll (inner PCG pass 2)",
                 "residual": "k_residual (FP64 residual)", "born_rows": "k_born_rows (Born-row assembly)",
                 "apply": "k_apply_partial+reduce (J x)", "apply_T": "k_apply_T_partial+reduce (J^T y)",
                 "sketch_range": "k_range_ws (tensor-core Y = J Omega)",
                 "sketch_project": "k_project_ws (tensor-core B^T += J^T Q)"}
 # DRAM bytes (read + write, ncu) per algorithmic byte, from the captures summarised under profiles/
 # (smaller cases of the same kernels, scaled by the units processed: active fields or rows)
-DRAM_PER_ALGORITHMIC_BYTE = {"dir": (100.96e6 + 24.81e6) / (64 * 3 * 196608 * 4),
-                             "update": (151.25e6 + 43.85e6) / (64 * 5 * 196608 * 4),
+DRAM_PER_ALGORITHMIC_BYTE = {"dir": (100.97e6 + 22.14e6) / (64 * 3 * 196608 * 4),
+                             "update": (151.25e6 + 46.51e6) / (64 * 5 * 196608 * 4),
                              "born_rows": (893.83e6 + 12.96e9) / (4096 * 4 * 196608 * 4)}
-TRAFFIC_NOTE = {"dir": "ncu on 64 fields of one wavelength (profiles/solver_tma_64fields.md), scaled by active fields; "
-                       "writes partly still in L2 at kernel end",
-                "update": "ncu on 64 fields of one wavelength (profiles/solver_tma_64fields.md), scaled by active fields",
+TRAFFIC_NOTE = {"dir": "ncu on 64 fields of one wavelength (profiles/solver_roll_64fields.md), scaled by active "
+                       "fields; writes partly still in L2 at kernel end",
+                "update": "ncu on 64 fields of one wavelength (profiles/solver_roll_64fields.md), scaled by active "
+                          "fields; writes partly still in L2 at kernel end",
                 "born_rows": "ncu on a full 4,096-row launch of the benchmark (profiles/k_born_rows_4096rows.md)"}
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
 
