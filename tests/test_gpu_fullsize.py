@@ -88,3 +88,60 @@ def test_apply_adjoint_identity_full_size(solved):
     lhs = float((jx.double() * y.double()).sum())
     rhs = float((x.double() * jty.double()).sum())
     assert abs(lhs - rhs) <= 1e-5 * max(abs(lhs), 1e-300) + 1e-5 * float(jx.double().abs().sum() * y.abs().max())
+
+
+def test_config3_misfit_gradient_on_a_wavelength_slice(lib):
+    """Config 3 at full grid size (96x96x64, h = 1.5 mm, 24 + 24 optodes) on wavelengths 0-3:
+    misfit 0.5 ||J dc - y||^2 with the seeded ellipsoidal anomaly, y = J dc_true + noise at 30 dB;
+    the autograd gradient (mixed-precision fields, FP32 adjoint kernel) against the oracle's
+    J^T (J dc - y) from its own FP64 fields, at 64 seeded coordinates, relative 1e-4 of the largest
+    component. The misfit is quadratic in dc, so this component equals the central difference of
+    the FP64 misfit up to rounding."""
+    from oracle import born as oborn
+    from oracle import solve as osolve
+    from paper_1410_0986_gb300 import born_apply
+
+    p = workloads.config(3)
+    lams = [0, 1, 2, 3]
+    nl = len(lams)
+    dc = workloads.ellipsoid_anomaly(p.grid, seed=301)
+    dc_true = workloads.ellipsoid_anomaly(p.grid, seed=302)
+    rs, rd = osolve.fields_separable(p, lams)
+    y_true = oborn.apply(p, rs, rd, dc_true, lams)
+    M = y_true.size
+    y = y_true + workloads.gaussian(303, M) * (np.linalg.norm(y_true) / M ** 0.5) * 10 ** (-30 / 20)
+    g_ref = oborn.apply_T(p, rs, rd, oborn.apply(p, rs, rd, dc, lams) - y, lams)
+    del rs, rd
+    with lib.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=1e-8, cw_floor=CW_FLOOR,
+                                  max_lambda_per_call=nl) as ctx:
+        ps, pd, st = ctx.solve_fields(0, nl)
+        x = torch.tensor(dc, dtype=torch.float32, device="cuda", requires_grad=True)
+        r = born_apply(x, ctx, ps, pd, 0, nl) - torch.tensor(y, dtype=torch.float32, device="cuda")
+        (0.5 * (r * r).sum()).backward()
+        g = x.grad.double().cpu().numpy()
+    idx = np.random.default_rng(304).choice(g.size, size=64, replace=False)
+    scale = np.abs(g_ref).max()
+    assert np.abs(g[idx] - g_ref[idx]).max() <= 1e-4 * scale
+    assert np.abs(g - g_ref).max() <= 1e-3 * scale  # every component, looser (FP32 sums over 4 x 576 rows)
+
+
+@pytest.mark.parametrize("which", [0, 1])
+def test_config4_frequency_domain_phantoms(lib, which):
+    """Config 4 frequency-domain phantoms (100 MHz, complex-symmetric COCG in complex64 with
+    complex128 refinement), the two smallest grids of the uneven batch on wavelengths 0-1: fields at
+    every optode cell and 2,000 sampled voxels against the oracle's complex128 fields."""
+    from oracle import solve as osolve
+
+    p = workloads.config4_batch()[which]
+    lams = [0, 1]
+    rs, rd = osolve.fields_separable(p, lams)
+    with lib.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=1e-8, max_lambda_per_call=2) as ctx:
+        ps, pd, st = ctx.solve_fields(0, 2)
+    assert ps.dtype == torch.complex64 and st["n_not_converged"] == 0
+    vox = np.unique(np.concatenate([np.random.default_rng(401 + which).choice(p.grid.N, 2000, replace=False),
+                                    p.src_voxels(), p.det_voxels()]))
+    for got, ref in ((ps, rs), (pd, rd)):
+        g = got.cpu().numpy()[:, :, vox].astype(np.complex128)
+        rr = ref[:, :, vox]
+        rel = np.linalg.norm(g - rr, axis=-1) / np.linalg.norm(rr, axis=-1)
+        assert rel.max() <= 1e-6, rel.max()
