@@ -157,6 +157,28 @@ def test_splu_componentwise_backward_error():
         assert f.min() > 0  # positive inverse of an M-matrix
 
 
+def test_separable_solver_entrywise_in_the_far_field():
+    """The fast-diagonalisation solve with its residual correction is accurate entry by entry:
+    positive everywhere (inverse of an M-matrix applied to a unit source), componentwise backward
+    error at rounding level against the assembled operator, and equal to SuperLU entry by entry
+    where the transmission field has decayed by 16 orders of magnitude. Without the correction the
+    same solve is accurate in norm but off by ~1e-3 relative in the far field."""
+    p = workloads.make_problem(workloads.Grid(32, 32, 40, 3.0), 2, 2, 1, seed=12, geometry="transmission")
+    A = model.operator(p, 0).tocsr()
+    absA = abs(A)
+    b = np.zeros((2, p.grid.N))
+    b[np.arange(2), p.src_voxels()] = 1.0
+    plain = solve.solve_separable(p, 0, b, refine=0)
+    fixed = solve.solve_separable(p, 0, b)
+    ref, _ = solve.fields_splu(p)
+    assert fixed.min() < 1e-15 * fixed.max()  # the far field really has decayed
+    assert np.abs(plain / ref[0] - 1.0).max() > 1e-5  # uncorrected: accurate in norm only
+    assert fixed.min() > 0
+    w = np.abs(b - (A @ fixed.T).T) / ((absA @ np.abs(fixed).T).T + b)
+    assert w.max() < 1e-12
+    assert np.abs(fixed / ref[0] - 1.0).max() < 1e-12
+
+
 def test_reciprocity():
     """phi_s(r_d) = phi_d(r_s): A is symmetric (Section 2.1, adjoint field)."""
     for freq in (0.0, 100.0):
