@@ -408,6 +408,12 @@ def sketch_phase(hd, pk, n_lam=4, rank=200, over=20, n_probe=32):
         ks = ctx.kernel_stats()
         ctx.set_kernel_timing(False)
         del om
+        # ||J||_F^2 of the chunk from the fields: h^6 sum_l (sum_c eps_c^2) sum_x (sum_s phi_s^2)(sum_d phi_d^2);
+        # J - U S V^T is J minus its projection, so sqrt(1 - sum S^2 / ||J||_F^2) is the Frobenius
+        # error of the rank-200 factors, which is also the RMS error over Gaussian probes
+        e2 = torch.tensor((p.eps[:n_lam] ** 2).sum(1), device="cuda", dtype=torch.float64)
+        jf2 = float((p.grid.h ** 6) * (e2 * ((ps.double() ** 2).sum(1) * (pd.double() ** 2).sum(1)).sum(1)).sum())
+        frob_err = float(max(0.0, 1.0 - float((torch.tensor(S[:rank]) ** 2).sum()) / jf2) ** 0.5)
         X = torch.randn(nc * N, n_probe, device="cuda", generator=gen)
         errs = []
         for q in range(n_probe):
@@ -422,7 +428,9 @@ def sketch_phase(hd, pk, n_lam=4, rank=200, over=20, n_probe=32):
     out["wall_s"] = wall
     out["kept_directions"] = kept
     out["singular_values"] = {"s1": float(S[0]), "s200": float(S[rank - 1])}
-    out["probe_error"] = {"max": max(errs), "median": float(np.median(errs)), "n": n_probe}
+    out["probe_error"] = {"max": max(errs), "median": float(np.median(errs)), "rms": float(np.sqrt(np.mean(np.square(errs)))),
+                          "n": n_probe}
+    out["frobenius_error_of_factors"] = frob_err
     return out
 
 

@@ -208,6 +208,13 @@ long long hydot_kernel_launches(const hydot_ctx* ctx);
  * (0 if not timed yet). Any output pointer may be NULL; arrays hold HYDOT_ROLL_VARIANTS entries. */
 int hydot_get_tuning(const hydot_ctx* ctx, int* variant, int* planes, int* buffers, double* ns_per_cell);
 
+/* Failure-path self-test (no counterpart in the paper): one thread waits on a shared-memory
+ * mbarrier that nothing arrives at, through the same bounded poll loop the pipelined kernels use
+ * for their TMA and tensor-core waits, but with `polls` polls (1..2^22) instead of their limit;
+ * it raises the device error flag and returns. The call returns HYDOT_ERR_TIMEOUT with a message,
+ * and the context stays usable (the flag is cleared). Synchronises the stream. */
+int hydot_wait_selftest(hydot_ctx* ctx, int polls);
+
 /* Randomised sketch of J, pass 1 (Appendix A.1, alg:randsvd: Y = A Omega with Gaussian Omega):
  *   Y[r][k] = sum_(c,x) J[r,(c,x)] Omega[(c,x),k]  for the rows r of the slice [lam0, lam0+nlam).
  * omega_t: DEVICE BF16 (raw 16-bit) [n_chrom][ncols][N], Omega transposed per chromophore.

@@ -233,6 +233,11 @@ class Context:
     def kernel_launches(self) -> int:
         return int(self.lib.hydot_kernel_launches(self._ctx))
 
+    def wait_selftest(self, polls: int = 1000) -> None:
+        """hydot_wait_selftest: a bounded device wait that runs out; raises HydotError
+        (HYDOT_ERR_TIMEOUT) as every pipelined kernel's timeout would."""
+        self._check(self.lib.hydot_wait_selftest(self._ctx, int(polls)))
+
     def tuning(self) -> dict:
         """Autotuner state of the inner passes: chosen variant (-1 while tuning) and, per variant,
         slab planes, slab buffers and measured ns per cell-iteration (0 if not timed)."""

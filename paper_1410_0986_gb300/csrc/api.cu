@@ -303,6 +303,11 @@ int hydot_sketch_factor(hydot_ctx* ctx, const float* Q, long long rows, long lon
 
 long long hydot_kernel_launches(const hydot_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
+int hydot_wait_selftest(hydot_ctx* ctx, int polls) {
+  if (!ctx) return HYDOT_ERR_ARG;
+  return hydot::wait_selftest_impl(ctx, polls);
+}
+
 int hydot_get_tuning(const hydot_ctx* ctx, int* variant, int* planes, int* buffers, double* ns_per_cell) {
   if (!ctx) return HYDOT_ERR_ARG;
   return hydot::get_tuning_impl(ctx, variant, planes, buffers, ns_per_cell);

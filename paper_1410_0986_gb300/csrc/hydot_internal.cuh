@@ -238,6 +238,7 @@ inline int fail(hydot_ctx* ctx, int code, const std::string& msg) {
 // solver.cu
 int solve_fields_impl(hydot_ctx* ctx, int lam0, int nlam, void* phi_src, void* phi_det, hydot_stats* st);
 int get_tuning_impl(const hydot_ctx* ctx, int* variant, int* planes, int* buffers, double* ns_per_cell);
+int wait_selftest_impl(hydot_ctx* ctx, int polls);
 int solver_alloc(hydot_ctx* ctx);
 void solver_free(hydot_ctx* ctx);
 

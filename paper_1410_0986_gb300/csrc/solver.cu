@@ -1457,6 +1457,33 @@ void solver_free(hydot_ctx* ctx) {
   if (ctx->tune_ev[1]) cudaEventDestroy(ctx->tune_ev[1]);
 }
 
+namespace {
+// One thread waits on a shared-memory mbarrier that nothing arrives at, through the same bounded
+// poll loop as the pipelined kernels, then raises the error flag and returns.
+__global__ void k_wait_selftest(int* err, uint32_t polls) {
+  __shared__ uint64_t m;
+  if (threadIdx.x == 0) {
+    mbar_init(&m, 1);
+    mbar_fence_init();
+    if (!mbar_wait_polls(&m, 0u, polls)) atomicExch(err, 1);
+  }
+}
+}  // namespace
+
+int wait_selftest_impl(hydot_ctx* ctx, int polls) {
+  if (polls < 1 || (uint32_t)polls > WAIT_POLLS) return fail(ctx, HYDOT_ERR_ARG, "polls must be in 1..2^22");
+  HYDOT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
+  k_wait_selftest<<<1, 32, 0, ctx->stream>>>(ctx->d_err, (uint32_t)polls);
+  ++ctx->launches;
+  HYDOT_CUDA_TRY(ctx, cudaGetLastError());
+  int flag = 0;
+  HYDOT_CUDA_TRY(ctx, cudaMemcpyAsync(&flag, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  HYDOT_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  HYDOT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
+  if (flag) return fail(ctx, HYDOT_ERR_TIMEOUT, "bounded wait gave up (self-test)");
+  return HYDOT_OK;
+}
+
 int get_tuning_impl(const hydot_ctx* ctx, int* variant, int* planes, int* buffers, double* ns_per_cell) {
   if (variant) *variant = ctx->use_tma ? ctx->tune.variant : -1;
   for (int v = 0; v < HYDOT_ROLL_VARIANTS; ++v) {

@@ -42,11 +42,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* m, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait for phase `parity`; false when the limit was reached.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* m, uint32_t parity) {
-  for (uint32_t i = 0; i < WAIT_POLLS; ++i)
+// Wait for phase `parity` with at most `limit` polls; false when the limit was reached.
+__device__ __forceinline__ bool mbar_wait_polls(uint64_t* m, uint32_t parity, uint32_t limit) {
+  for (uint32_t i = 0; i < limit; ++i)
     if (mbar_try_wait(m, parity)) return true;
   return false;
+}
+
+// Bounded wait used by the pipelined kernels.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* m, uint32_t parity) {
+  return mbar_wait_polls(m, parity, WAIT_POLLS);
 }
 
 // 4-D tiled tensor load global -> shared; coordinates innermost first. The x coordinate times the

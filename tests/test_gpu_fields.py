@@ -242,3 +242,17 @@ def test_graph_replay_matches_direct_launches(hd, monkeypatch):
     for q in range(3):
         assert torch.equal(res["0"][q][0], res["1"][q][0]) and torch.equal(res["0"][q][1], res["1"][q][1])
     assert torch.equal(res["0"][0][0], res["0"][1][0])
+
+
+def test_bounded_wait_timeout_keeps_context_usable(hd):
+    """A device wait that runs out (an mbarrier nothing arrives at, through the kernels' bounded
+    poll loop) comes back as HYDOT_ERR_TIMEOUT; the context then solves as before."""
+    p = workloads.small(seed=5, nx=16, ny=11, nz=9, n_src=2, n_det=2, n_lambda=2)
+    with hd.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=1e-8) as ctx:
+        a, b, _ = ctx.solve_fields(0, 2)
+        with pytest.raises(hd.HydotError) as ei:
+            ctx.wait_selftest(2000)
+        assert ei.value.code == -5
+        c, d, st = ctx.solve_fields(0, 2)
+        assert st["n_not_converged"] == 0
+    assert torch.equal(a, c) and torch.equal(b, d)
