@@ -96,27 +96,51 @@ __global__ void __launch_bounds__(256) k_born_rows_scalar(const E* __restrict__ 
 }
 
 // ---------------------------------------------------------------- J x
-// Block = (wavelength a, chunk of XC voxels, 32x32 tile of (s, d)). smem holds
-// S[s][x] = phi_s * mu and Dd[d][x] = phi_d for the chunk; 256 threads = 16 voxel groups x
-// 16 (s,d) sub-tiles of 8x8 accumulators. Block partials go to a workspace and a second
-// kernel sums them in a fixed order.
-constexpr int AP_XC = 128;   // voxels per smem stage
-constexpr int AP_XCP = AP_XC + 1;
+// Block = (wavelength a, chunk of AP_STAGES x AP_XC voxels, 32x32 tile of (s, d)). Each stage of
+// AP_XC voxels (phi_s and phi_d rows of the tile, and the chromophore maps x_c) is copied into
+// shared memory with cp.async while the previous stage is contracted (two buffers). 256 threads =
+// 16 voxel groups x 16 (s, d) sub-tiles; a thread accumulates s-rows si0 + 4u and d-rows
+// di0 + 4v (u, v < 8), which with a row stride of AP_XC + 16 bytes keeps the tile reads of a warp
+// on distinct banks. mu_a(x) = sum_c eps_c(lambda_a) x_c is formed by each thread for its voxels.
+// Block partials go to a workspace and a second kernel sums them in a fixed order.
+constexpr int AP_XC = 128;   // voxels per stage
 constexpr int AP_STAGES = 8; // stages per block
 
 template <typename E>
-constexpr size_t apply_smem_bytes() { return sizeof(E) * (size_t)(2 * 32 * AP_XCP + AP_XC); }
+__host__ __device__ constexpr int ap_ld() { return AP_XC + 16 / (int)sizeof(E); }  // padded row stride (elements)
+// elements of one stage buffer: S [32][LD], D [32][LD], X [nc][AP_XC]
+template <typename E>
+__host__ __device__ constexpr size_t apply_buf_elems(int nc) { return (size_t)64 * ap_ld<E>() + (size_t)nc * AP_XC; }
+template <typename E>
+size_t apply_smem_bytes(int nc) {
+  return std::max(sizeof(E) * 2 * apply_buf_elems<E>(nc), sizeof(E) * 8 * 1024);  // the reduction reuses it
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(src_bytes)
+               : "memory");
+}
+template <int B>
+__device__ __forceinline__ void cp_async_small(void* dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src), "n"(B), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N_>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N_) : "memory"); }
 
 template <typename E>
 __global__ void __launch_bounds__(256) k_apply_partial(const E* __restrict__ ps, const E* __restrict__ pd,
                                                        const E* __restrict__ xin, const double* __restrict__ eps,
-                                                       int lam0, int ns, int nd, int nc, long long N, int nxb,
+                                                       int lam0, int ns, int nd, int nc, long long N, int nxb, int vec,
                                                        E* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  E* S = reinterpret_cast<E*>(smraw);  // [32][AP_XCP]  phi_s * mu
-  E* Dd = S + 32 * AP_XCP;             // [32][AP_XCP]  phi_d
-  E* mu = Dd + 32 * AP_XCP;            // [AP_XC]
-  E* red = S;                          // [8][1024], aliases S and Dd after the voxel loop
+  constexpr int LD = ap_ld<E>();
+  constexpr int VE = 16 / (int)sizeof(E);  // elements per 16-byte copy
+  E* buf0 = reinterpret_cast<E*>(smraw);   // per buffer: S [32][LD], D [32][LD], X [nc][AP_XC]
+  E* red = buf0;                           // [8][1024], reused after the voxel loop
   const int xb = blockIdx.x;
   const int a = blockIdx.y;
   const int tsd = blockIdx.z;  // (s-tile, d-tile)
@@ -124,63 +148,125 @@ __global__ void __launch_bounds__(256) k_apply_partial(const E* __restrict__ ps,
   const int s0 = (tsd % nts) * 32, d0 = (tsd / nts) * 32;
   const int t = threadIdx.x;
   const int grp = t / 16, sub = t % 16;
-  const int si = (sub / 4) * 8, di = (sub % 4) * 8;
-  E w[MAXC];
-  for (int c = 0; c < nc; ++c) w[c] = (E)eps[(size_t)(lam0 + a) * nc + c];
+  const int si0 = sub / 4, di0 = sub % 4;
+  __shared__ E w[MAXC];  // eps_c(lambda_a)
+  __shared__ E mu[AP_XC];  // mu_a of the stage's voxels
+  if (t < nc) w[t] = (E)eps[(size_t)(lam0 + a) * nc + t];
+  const E* srow = ps + ((size_t)a * ns + s0) * N;
+  const E* drow = pd + ((size_t)a * nd + d0) * N;
+  auto load = [&](int st, E* b) {
+    const long long xbase = ((long long)xb * AP_STAGES + st) * AP_XC;
+    E* S = b;
+    E* D = b + 32 * LD;
+    E* X = b + 64 * LD;
+    if (vec) {
+      constexpr int CH = AP_XC / VE;  // 16-byte chunks per row
+      for (int q = t; q < (64 + nc) * CH; q += 256) {
+        const int row = q / CH, col = (q % CH) * VE;
+        const long long x = xbase + col;
+        const E* src;
+        E* dst;
+        bool ok;
+        if (row < 32) {
+          ok = s0 + row < ns;
+          src = srow + (size_t)row * N + x;
+          dst = S + row * LD + col;
+        } else if (row < 64) {
+          ok = d0 + row - 32 < nd;
+          src = drow + (size_t)(row - 32) * N + x;
+          dst = D + (row - 32) * LD + col;
+        } else {
+          ok = true;
+          src = xin + (size_t)(row - 64) * N + x;
+          dst = X + (row - 64) * AP_XC + col;
+        }
+        ok = ok && x < N;  // N is a multiple of VE here: a chunk is inside or outside as a whole
+        cp_async16(dst, ok ? src : xin, ok ? 16u : 0u);
+      }
+    } else {
+      for (int q = t; q < (64 + nc) * AP_XC; q += 256) {
+        const int row = q / AP_XC, col = q % AP_XC;
+        const long long x = xbase + col;
+        const E* src;
+        E* dst;
+        bool ok;
+        if (row < 32) {
+          ok = s0 + row < ns;
+          src = srow + (size_t)row * N + x;
+          dst = S + row * LD + col;
+        } else if (row < 64) {
+          ok = d0 + row - 32 < nd;
+          src = drow + (size_t)(row - 32) * N + x;
+          dst = D + (row - 32) * LD + col;
+        } else {
+          ok = true;
+          src = xin + (size_t)(row - 64) * N + x;
+          dst = X + (row - 64) * AP_XC + col;
+        }
+        ok = ok && x < N;
+        cp_async_small<(int)sizeof(E)>(dst, ok ? src : xin, ok ? (uint32_t)sizeof(E) : 0u);
+      }
+    }
+    cp_async_commit();
+  };
   E acc[8][8];
 #pragma unroll
   for (int u = 0; u < 8; ++u)
 #pragma unroll
     for (int v = 0; v < 8; ++v) acc[u][v] = 0;
-  for (int st = 0; st < AP_STAGES; ++st) {
-    const long long xbase = ((long long)xb * AP_STAGES + st) * AP_XC;
-    if (xbase >= N) break;
-    __syncthreads();
-    for (int q = t; q < AP_XC; q += 256) {
-      long long x = xbase + q;
-      E m = 0;
-      if (x < N)
-        for (int c = 0; c < nc; ++c) m += w[c] * xin[(size_t)c * N + x];
-      mu[q] = m;
+  const long long nstage = min((long long)AP_STAGES, (N - (long long)xb * AP_STAGES * AP_XC + AP_XC - 1) / AP_XC);
+  load(0, buf0);
+  for (int st = 0; st < nstage; ++st) {
+    E* b = buf0 + (st & 1) * apply_buf_elems<E>(nc);
+    if (st + 1 < nstage) {
+      load(st + 1, buf0 + ((st + 1) & 1) * apply_buf_elems<E>(nc));
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
     }
     __syncthreads();
-    for (int q = t; q < 32 * AP_XC; q += 256) {
-      int row = q / AP_XC, col = q % AP_XC;
-      long long x = xbase + col;
-      int s = s0 + row, d = d0 + row;
-      S[row * AP_XCP + col] = (x < N && s < ns) ? ps[((size_t)a * ns + s) * N + x] * mu[col] : (E)0;
-      Dd[row * AP_XCP + col] = (x < N && d < nd) ? pd[((size_t)a * nd + d) * N + x] : (E)0;
+    const E* S = b;
+    const E* D = b + 32 * LD;
+    const E* X = b + 64 * LD;
+    if (t < AP_XC) {
+      E m = 0;
+      for (int c = 0; c < nc; ++c) m += w[c] * X[c * AP_XC + t];
+      mu[t] = m;
     }
     __syncthreads();
     for (int q = grp; q < AP_XC; q += 16) {
+      const E m = mu[q];
       E sv[8], dv[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) sv[u] = S[(si + u) * AP_XCP + q];
+      for (int u = 0; u < 8; ++u) sv[u] = S[(si0 + 4 * u) * LD + q] * m;
 #pragma unroll
-      for (int v = 0; v < 8; ++v) dv[v] = Dd[(di + v) * AP_XCP + q];
+      for (int v = 0; v < 8; ++v) dv[v] = D[(di0 + 4 * v) * LD + q];
 #pragma unroll
       for (int u = 0; u < 8; ++u)
 #pragma unroll
         for (int v = 0; v < 8; ++v) acc[u][v] += sv[u] * dv[v];
     }
+    __syncthreads();  // buffer (st & 1) is refilled by the load of stage st + 2
   }
   // tree reduction over the 16 voxel groups (fixed order -> deterministic)
   for (int half = 8; half >= 1; half >>= 1) {
     __syncthreads();
+    // element (u, v) of sub-tile `sub` at (u*8 + v)*16 + sub: the 16 sub-tiles of a voxel group
+    // hit 16 consecutive words
     if (grp >= half && grp < 2 * half) {
-      E* dst = red + (size_t)(grp - half) * 1024 + sub * 64;
+      E* dst = red + (size_t)(grp - half) * 1024 + sub;
 #pragma unroll
       for (int u = 0; u < 8; ++u)
 #pragma unroll
-        for (int v = 0; v < 8; ++v) dst[u * 8 + v] = acc[u][v];
+        for (int v = 0; v < 8; ++v) dst[(u * 8 + v) * 16] = acc[u][v];
     }
     __syncthreads();
     if (grp < half) {
-      const E* src = red + (size_t)grp * 1024 + sub * 64;
+      const E* src = red + (size_t)grp * 1024 + sub;
 #pragma unroll
       for (int u = 0; u < 8; ++u)
 #pragma unroll
-        for (int v = 0; v < 8; ++v) acc[u][v] += src[u * 8 + v];
+        for (int v = 0; v < 8; ++v) acc[u][v] += src[(u * 8 + v) * 16];
     }
   }
   if (grp == 0) {
@@ -188,8 +274,14 @@ __global__ void __launch_bounds__(256) k_apply_partial(const E* __restrict__ ps,
 #pragma unroll
     for (int u = 0; u < 8; ++u)
 #pragma unroll
-      for (int v = 0; v < 8; ++v) out[(si + u) * 32 + (di + v)] = acc[u][v];
+      for (int v = 0; v < 8; ++v) out[(si0 + 4 * u) * 32 + (di0 + 4 * v)] = acc[u][v];
   }
+}
+
+// 16-byte copies need 16-byte aligned rows: N * element size a multiple of 16 and aligned bases.
+inline int apply_vec_ok(const void* a, const void* b, const void* c, long long N, size_t es) {
+  const auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+  return ((N * (long long)es) % 16 == 0 && al(a) && al(b) && al(c)) ? 1 : 0;
 }
 
 template <typename E>
@@ -209,50 +301,88 @@ __global__ void k_apply_reduce(const E* __restrict__ part, int nlam, int ns, int
 }
 
 // ---------------------------------------------------------------- J^T y
-// Thread per voxel; loops over the wavelengths of its group, keeping the detector fields of the
-// voxel in registers: t_a = sum_s phi_s (sum_d Y_a[s][d] phi_d), acc_c += eps_c(lambda_a) t_a.
-constexpr int AT_MAXD = 32;
+// Thread per voxel; loops over the wavelengths of its group. Per wavelength and block of (up to)
+// 32 detectors x 32 sources, the thread first loads the 64 field values of its voxel (independent
+// coalesced loads, all in flight together), then t_a += sum_s phi_s (sum_d Y_a[s][d] phi_d) with
+// Y_a in shared memory (rows padded to a multiple of 4, read as 16-byte broadcasts), and
+// acc_c += eps_c(lambda_a) t_a.
+constexpr int AT_B = 32;
 
 template <typename E>
-__global__ void __launch_bounds__(256) k_apply_T_partial(const E* __restrict__ ps, const E* __restrict__ pd,
+__host__ __device__ constexpr int at_ld(int nd) { return (nd + 3) / 4 * 4; }  // padded row of Y
+
+// FULL: n_src and n_det are multiples of 32 (no guards inside the blocks)
+template <typename E, bool FULL>
+__global__ void __launch_bounds__(256, 2) k_apply_T_partial(const E* __restrict__ ps, const E* __restrict__ pd,
                                                          const E* __restrict__ y, const double* __restrict__ eps,
                                                          int lam0, int nlam, int ns, int nd, int nc, long long N,
                                                          int lam_per_group, E* __restrict__ part) {
-  extern __shared__ unsigned char smraw[];
-  E* Y = reinterpret_cast<E*>(smraw);  // [ns][nd] of one wavelength
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int LDY = at_ld<E>(nd);
+  E* Y = reinterpret_cast<E*>(smraw);          // [ns][LDY] of one wavelength, zero-padded
+  E* Tl = Y + (size_t)ns * LDY;                // [wavelengths of the group][256]: t_a per voxel
   const int grp = blockIdx.y;
   const int a0 = grp * lam_per_group, a1 = min(nlam, a0 + lam_per_group);
   const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const bool in = x < N;
-  E acc[MAXC];
-  for (int c = 0; c < nc; ++c) acc[c] = 0;
   for (int a = a0; a < a1; ++a) {
     __syncthreads();
-    for (int q = threadIdx.x; q < ns * nd; q += blockDim.x) {
-      int s = q / nd, d = q % nd;
-      Y[q] = y[((size_t)s * nd + d) * nlam + a];
+    for (int q = threadIdx.x; q < ns * LDY; q += blockDim.x) {
+      const int s = q / LDY, d = q % LDY;
+      Y[q] = d < nd ? y[((size_t)s * nd + d) * nlam + a] : (E)0;
     }
     __syncthreads();
     E ta = 0;
     if (in) {
-      for (int d0 = 0; d0 < nd; d0 += AT_MAXD) {
-        const int dn = min(AT_MAXD, nd - d0);
-        E fd[AT_MAXD];
+      for (int d0 = 0; d0 < nd; d0 += AT_B) {
+        const int dn = FULL ? AT_B : min(AT_B, nd - d0);
+        E fd[AT_B];
 #pragma unroll
-        for (int q = 0; q < AT_MAXD; ++q) fd[q] = (q < dn) ? pd[((size_t)a * nd + d0 + q) * N + x] : (E)0;
-        for (int s = 0; s < ns; ++s) {
-          const E* Ys = Y + (size_t)s * nd + d0;
-          E z = 0;
+        for (int q = 0; q < AT_B; ++q) fd[q] = (q < dn) ? pd[((size_t)a * nd + d0 + q) * N + x] : (E)0;
+        const int dq = FULL ? AT_B / 4 : (dn + 3) / 4;  // 4-wide groups of Y within this detector block
+        for (int s0 = 0; s0 < ns; s0 += AT_B) {
+          const int sn = FULL ? AT_B : min(AT_B, ns - s0);
+          E fs[AT_B];
 #pragma unroll
-          for (int q = 0; q < AT_MAXD; ++q) z += (q < dn ? Ys[q] : (E)0) * fd[q];
-          ta += ps[((size_t)a * ns + s) * N + x] * z;
+          for (int q = 0; q < AT_B; ++q) fs[q] = (q < sn) ? ps[((size_t)a * ns + s0 + q) * N + x] : (E)0;
+#pragma unroll
+          for (int s = 0; s < AT_B; ++s) {
+            if (s >= sn) break;
+            const E* Ys = Y + (size_t)(s0 + s) * LDY + d0;
+            E z = 0;
+            if constexpr (sizeof(E) == 4) {
+              // four independent partial sums (no serial chain of 32 dependent FMAs)
+              float z0 = 0.f, z1 = 0.f, z2 = 0.f, z3 = 0.f;
+#pragma unroll
+              for (int g = 0; g < AT_B / 4; ++g) {
+                if (g < dq) {
+                  const float4 yv = *reinterpret_cast<const float4*>(Ys + 4 * g);
+                  z0 = fmaf(yv.x, fd[4 * g], z0);
+                  z1 = fmaf(yv.y, fd[4 * g + 1], z1);
+                  z2 = fmaf(yv.z, fd[4 * g + 2], z2);
+                  z3 = fmaf(yv.w, fd[4 * g + 3], z3);
+                }
+              }
+              z = (z0 + z1) + (z2 + z3);
+            } else {
+#pragma unroll
+              for (int q = 0; q < AT_B; ++q)
+                if (q < dn) z += Ys[q] * fd[q];
+            }
+            ta += fs[s] * z;
+          }
         }
       }
     }
-    for (int c = 0; c < nc; ++c) acc[c] += (E)eps[(size_t)(lam0 + a) * nc + c] * ta;
+    Tl[(a - a0) * 256 + threadIdx.x] = ta;
   }
+  // acc_c = sum_a eps_c(lambda_a) t_a (the t_a wait in shared memory, not in registers)
   if (in)
-    for (int c = 0; c < nc; ++c) part[((size_t)grp * nc + c) * N + x] = acc[c];
+    for (int c = 0; c < nc; ++c) {
+      E acc = 0;
+      for (int a = a0; a < a1; ++a) acc += (E)eps[(size_t)(lam0 + a) * nc + c] * Tl[(a - a0) * 256 + threadIdx.x];
+      part[((size_t)grp * nc + c) * N + x] = acc;
+    }
 }
 
 template <typename E>
@@ -329,10 +459,11 @@ int apply_t(hydot_ctx* ctx, const E* ps, const E* pd, int lam0, int nlam, const 
   if (rc) return rc;
   E* part = (E*)ctx->d_apply_ws;
   dim3 grid(nxb, nlam, nts * ntd);
-  const size_t smem = apply_smem_bytes<E>();
+  const size_t smem = apply_smem_bytes<E>(nc);
   HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(k_apply_partial<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int vec = apply_vec_ok(ps, pd, x, N, sizeof(E));
   cudaEvent_t t0 = timer_begin(ctx);
-  k_apply_partial<E><<<grid, 256, smem, ctx->stream>>>(ps, pd, x, ctx->d_eps, lam0, ns, nd, nc, N, nxb, part);
+  k_apply_partial<E><<<grid, 256, smem, ctx->stream>>>(ps, pd, x, ctx->d_eps, lam0, ns, nd, nc, N, nxb, vec, part);
   ++ctx->launches;
   HYDOT_CUDA_TRY(ctx, cudaGetLastError());
   long long M = (long long)ns * nd * nlam;
@@ -358,13 +489,16 @@ int apply_T_t(hydot_ctx* ctx, const E* ps, const E* pd, int lam0, int nlam, cons
   if (rc) return rc;
   E* part = (E*)ctx->d_apply_ws;
   dim3 grid((unsigned)xblocks, ngrp);
-  size_t smem = sizeof(E) * (size_t)ns * nd;
+  // one wavelength's Y block and the per-wavelength t_a of the block's voxels
+  const size_t smem = sizeof(E) * ((size_t)ns * at_ld<E>(nd) + (size_t)lpg * 256);
+  if (smem > 200 * 1024) return fail(ctx, HYDOT_ERR_ARG, "n_src x n_det too large for the J^T y kernel");
+  const bool full = ns % AT_B == 0 && nd % AT_B == 0;
+  auto kern = full ? k_apply_T_partial<E, true> : k_apply_T_partial<E, false>;
   if (smem > 48 * 1024) {
-    HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(k_apply_T_partial<E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem));
+    HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   }
   cudaEvent_t t0 = timer_begin(ctx);
-  k_apply_T_partial<E><<<grid, 256, smem, ctx->stream>>>(ps, pd, y, ctx->d_eps, lam0, nlam, ns, nd, nc, N, lpg, part);
+  kern<<<grid, 256, smem, ctx->stream>>>(ps, pd, y, ctx->d_eps, lam0, nlam, ns, nd, nc, N, lpg, part);
   ++ctx->launches;
   HYDOT_CUDA_TRY(ctx, cudaGetLastError());
   long long tot = (long long)nc * N;
@@ -482,13 +616,13 @@ extern "C" int hydot_born_apply_noalloc(long long N, int n_src, int n_det, int n
     set_context_free_error(std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e));
     return HYDOT_ERR_CUDA;
   }
-  const size_t smem = apply_smem_bytes<float>();
+  const size_t smem = apply_smem_bytes<float>(n_chrom);
   e = cudaFuncSetAttribute(k_apply_partial<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess) {
     dim3 grid((unsigned)nxb, nlam, nts * ntd);
     // every partial slot is written before it is read, so nothing in the array needs clearing
     k_apply_partial<float><<<grid, 256, smem, s>>>(phi_src, phi_det, x, d_eps, 0, n_src, n_det, n_chrom, N,
-                                                   (int)nxb, part);
+                                                   (int)nxb, apply_vec_ok(phi_src, phi_det, x, N, 4), part);
     const long long M = (long long)n_src * n_det * nlam;
     k_apply_reduce<float><<<(unsigned)std::min<long long>((M + 255) / 256, 4096), 256, 0, s>>>(
         part, nlam, n_src, n_det, nts, ntd, (int)nxb, h_mm * h_mm * h_mm, y);
