@@ -172,3 +172,24 @@ def test_misfit_gradient_vs_central_differences(lib):
     g = grad.cpu().numpy()[idx]
     scale = np.abs(grad.cpu().numpy()).max()
     assert np.abs(g - fd).max() <= 1e-4 * scale
+
+
+@pytest.mark.parametrize("ns,nd", [(32, 32), (64, 32), (40, 100), (3, 5)])
+def test_apply_and_apply_T_optode_blocks(lib, ns, nd):
+    """J x and J^T y in FP32 against the FP64 oracle for optode counts that fill whole 32-wide
+    blocks (the guard-free path) and ones that leave partial blocks (40 x 100: several detector
+    blocks, the last one partial)."""
+    p = workloads.make_problem(workloads.Grid(16, 16, 12, 2.0), ns, nd, 3, seed=51, geometry="transmission", margin=0)
+    rs, rd = osolve.fields_separable(p)
+    y = workloads.gaussian(52, p.M)
+    xv = workloads.gaussian(53, p.n_chrom * p.grid.N)
+    g_ref = oborn.apply_T(p, rs, rd, y)
+    y_ref = oborn.apply(p, rs, rd, xv)
+    with lib.Context.from_problem(p, precision="mixed", tol=1e-8, tol_cw=0.0) as ctx:
+        ps = torch.tensor(rs, dtype=torch.float32, device="cuda")
+        pd = torch.tensor(rd, dtype=torch.float32, device="cuda")
+        g = torch.zeros(p.n_chrom * p.grid.N, device="cuda")
+        ctx.born_apply_T(ps, pd, 0, p.n_lambda, torch.tensor(y, dtype=torch.float32, device="cuda"), g)
+        yy = ctx.born_apply(ps, pd, 0, p.n_lambda, torch.tensor(xv, dtype=torch.float32, device="cuda"))
+    assert np.abs(g.double().cpu().numpy() - g_ref).max() <= 2e-5 * np.abs(g_ref).max()
+    assert np.abs(yy.double().cpu().numpy() - y_ref).max() <= 2e-5 * np.abs(y_ref).max()
