@@ -216,28 +216,58 @@ int hydot_get_tuning(const hydot_ctx* ctx, int* variant, int* planes, int* buffe
 int hydot_wait_selftest(hydot_ctx* ctx, int polls);
 
 /* Randomised sketch of J, pass 1 (Appendix A.1, alg:randsvd: Y = A Omega with Gaussian Omega):
- *   Y[r][k] = sum_(c,x) J[r,(c,x)] Omega[(c,x),k]  for the rows r of the slice [lam0, lam0+nlam).
+ *   Y[r][k] = sum_(c,x) J[r,(c,x)] Omega[(c,x),k]
+ * for the rows r of the sources src0 .. src0+nsrc-1 (the row block H_i of Section 4.1 for a block of
+ * sources) and the wavelengths of the slice [lam0, lam0+nlam); row r = ((s - src0)*n_det + d)*nlam
+ * + (lambda - lam0). phi_src/phi_det: the slice's fields of all sources/detectors.
  * omega_t: DEVICE BF16 (raw 16-bit) [n_chrom][ncols][N], Omega transposed per chromophore.
- * Y: DEVICE float [n_src*n_det*nlam][ldY], ldY >= 224; columns >= ncols are written as 0.
- * Computed on the tensor cores (BF16 operands, FP32 accumulation). Needs HYDOT_MIXED, omega == 0,
- * N divisible by 8 and ncols <= 224. Synchronises the stream; HYDOT_ERR_TIMEOUT if a bounded
- * device wait gave up. */
-int hydot_sketch_range(hydot_ctx* ctx, const void* phi_src, const void* phi_det, int lam0, int nlam,
-                       const void* omega_t, int ncols, float* Y, long long ldY);
+ * Y: DEVICE float [nsrc*n_det*nlam][ldY], 16-byte aligned, ldY >= 224 and ldY % 4 == 0; columns
+ * >= ncols are written as 0. Computed on the tensor cores (BF16 operands, FP32 accumulation).
+ * Needs HYDOT_MIXED, omega == 0, N divisible by 8 and ncols <= 224. Synchronises the stream;
+ * HYDOT_ERR_TIMEOUT if a bounded device wait gave up. */
+int hydot_sketch_range(hydot_ctx* ctx, const void* phi_src, const void* phi_det, int lam0, int nlam, int src0,
+                       int nsrc, const void* omega_t, int ncols, float* Y, long long ldY);
 
 /* Randomised sketch of J, pass 2 (B = Q^T A): Bt[(c,x)][k] += sum_r J[r,(c,x)] Q[r][k] over the rows
- * r of the slice, so calls over consecutive slices merge the row blocks into B^T (Section 4.2).
- * Q: DEVICE float [n_src*n_det*nlam][ldQ] (the slice's rows of the orthonormal range basis),
- * Bt: DEVICE float [n_chrom*N][ldB], ldB >= 224, accumulated. Tensor cores, same requirements as
- * hydot_sketch_range. Synchronises the stream. */
-int hydot_sketch_project(hydot_ctx* ctx, const void* phi_src, const void* phi_det, int lam0, int nlam,
-                         const float* Q, int ncols, long long ldQ, float* Bt, long long ldB);
+ * r of the sources src0 .. src0+nsrc-1 and the slice, so calls over consecutive slices merge the
+ * row blocks into B^T (Section 4.2). Q: DEVICE float [nsrc*n_det*nlam][ldQ] (those rows of the
+ * orthonormal range basis, ordered as in hydot_sketch_range), Bt: DEVICE float [n_chrom*N][ldB],
+ * ldB >= 224, accumulated. Tensor cores, same requirements as hydot_sketch_range. Synchronises the
+ * stream. */
+int hydot_sketch_project(hydot_ctx* ctx, const void* phi_src, const void* phi_det, int lam0, int nlam, int src0,
+                         int nsrc, const float* Q, int ncols, long long ldQ, float* Bt, long long ldB);
 
 /* Orthonormal basis of range(Y) in place (the basis step of alg:randsvd): two rounds of
  * Y <- Y V diag(lambda^-1/2) from the FP64 Gram Y^T Y = V diag(lambda) V^T. Directions whose
  * singular value is below 1e-6 of the largest become zero columns; *rank_out (may be NULL) gets the
- * number kept. Y: DEVICE float [rows][ldY], first ncols (<= 224) columns. Synchronous. */
-int hydot_sketch_orthonormalize(hydot_ctx* ctx, float* Y, long long rows, int ncols, long long ldY, int* rank_out);
+ * number kept, *smax_out (may be NULL) the largest singular value of the input Y. The columns come
+ * out in descending order of singular value. Y: DEVICE float [rows][ldY], first ncols (<= 224)
+ * columns. Synchronous. */
+int hydot_sketch_orthonormalize(hydot_ctx* ctx, float* Y, long long rows, int ncols, long long ldY, int* rank_out,
+                                double* smax_out);
+
+/* Adaptive rank (the error estimator of alg:randsvd): Q DEVICE float [rows][ldQ], nq <= 224
+ * orthonormal columns in descending singular-value order (hydot_sketch_orthonormalize), Y2 DEVICE
+ * float [rows][ldY2] = A Omega_2 for k (1..32) further Gaussian columns. *rank receives the smallest
+ * r (at least 1) with || Y2 - Q_r Q_r^T Y2 ||_2 <= tol * s1, where Q_r are the first r columns and s1
+ * is the caller's scale (the largest singular value of A Omega_1); nq when none qualifies.
+ * *estimate (may be NULL) receives || Y2 - Q_r Q_r^T Y2 ||_2 / s1 for that r. Sums in FP64.
+ * Synchronous. */
+int hydot_sketch_rank(hydot_ctx* ctx, const float* Q, long long ldQ, long long rows, int nq, const float* Y2,
+                      long long ldY2, int k, double s1, double tol, int* rank, double* estimate);
+
+/* Agglomeration of the low-rank factors of two stacked row blocks (Section 4.3, Algorithm
+ * alg:recursive): [H1; H2] ~ [U1 diag(S1) V1^T; U2 diag(S2) V2^T] is recompressed to U diag(S) V^T
+ * with U = [U1 E1; U2 E2] (rows m1 + m2), keeping the singular values of [diag(S1) V1^T; diag(S2)
+ * V2^T] above tol times the largest (at most max_rank of them). Inputs: U1 [m1][ldU1], V1 [n][ldV1]
+ * (r1 columns), likewise block 2, all DEVICE float; S1, S2 HOST double. Outputs: U DEVICE float
+ * [m1+m2][ldU], V DEVICE float [n][ldV] (not aliasing the inputs), S HOST double [r1+r2] (first
+ * *rank_out entries set), *rank_out the merged rank. The Gram of the stacked factors is formed in
+ * FP64 from tall-skinny products and diagonalised on the host. Synchronous. */
+int hydot_sketch_merge(hydot_ctx* ctx, const float* U1, long long ldU1, long long m1, const double* S1, const float* V1,
+                       long long ldV1, int r1, const float* U2, long long ldU2, long long m2, const double* S2,
+                       const float* V2, long long ldV2, int r2, long long n, double tol, int max_rank, float* U,
+                       long long ldU, double* S, float* V, long long ldV, int* rank_out);
 
 /* Rank-`rank` factors J ~ U diag(S) V^T from Q (the orthonormal range basis, rows x ncols) and
  * Bt = (Q^T J)^T (nb = n_chrom*N rows): the FP64 Gram of Bt gives U_B and S (descending), then

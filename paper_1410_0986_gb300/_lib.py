@@ -23,7 +23,8 @@ HYDOT_MIXED = 1
 # Every symbol include/hydot.h declares.
 EXPORTS = ("hydot_version", "hydot_setup", "hydot_set_stream", "hydot_solve_fields", "hydot_born_assemble",
            "hydot_born_apply", "hydot_born_apply_T", "hydot_born_apply_noalloc", "hydot_sketch_range",
-           "hydot_sketch_project", "hydot_sketch_orthonormalize", "hydot_sketch_factor", "hydot_set_kernel_timing",
+           "hydot_sketch_project", "hydot_sketch_orthonormalize", "hydot_sketch_rank", "hydot_sketch_merge",
+           "hydot_sketch_factor", "hydot_set_kernel_timing",
            "hydot_kernel_stats", "hydot_kernel_launches", "hydot_get_tuning", "hydot_wait_selftest",
            "hydot_last_error", "hydot_destroy")
 ROLL_VARIANTS = 4  # HYDOT_ROLL_VARIANTS
@@ -87,12 +88,22 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.hydot_born_apply_noalloc.argtypes = [C.c_longlong, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
                                              C.POINTER(C.c_double), vp, vp, vp, vp, vp]
     lib.hydot_born_apply_noalloc.restype = C.c_int
-    lib.hydot_sketch_range.argtypes = [vp, vp, vp, C.c_int, C.c_int, vp, C.c_int, vp, C.c_longlong]
+    lib.hydot_sketch_range.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, C.c_int, vp, C.c_longlong]
     lib.hydot_sketch_range.restype = C.c_int
-    lib.hydot_sketch_project.argtypes = [vp, vp, vp, C.c_int, C.c_int, vp, C.c_int, C.c_longlong, vp, C.c_longlong]
+    lib.hydot_sketch_project.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, C.c_int, C.c_longlong, vp,
+                                         C.c_longlong]
     lib.hydot_sketch_project.restype = C.c_int
-    lib.hydot_sketch_orthonormalize.argtypes = [vp, vp, C.c_longlong, C.c_int, C.c_longlong, C.POINTER(C.c_int)]
+    lib.hydot_sketch_orthonormalize.argtypes = [vp, vp, C.c_longlong, C.c_int, C.c_longlong, C.POINTER(C.c_int),
+                                                C.POINTER(C.c_double)]
     lib.hydot_sketch_orthonormalize.restype = C.c_int
+    lib.hydot_sketch_rank.argtypes = [vp, vp, C.c_longlong, C.c_longlong, C.c_int, vp, C.c_longlong, C.c_int,
+                                      C.c_double, C.c_double, C.POINTER(C.c_int), C.POINTER(C.c_double)]
+    lib.hydot_sketch_rank.restype = C.c_int
+    lib.hydot_sketch_merge.argtypes = [vp, vp, C.c_longlong, C.c_longlong, C.POINTER(C.c_double), vp, C.c_longlong,
+                                       C.c_int, vp, C.c_longlong, C.c_longlong, C.POINTER(C.c_double), vp,
+                                       C.c_longlong, C.c_int, C.c_longlong, C.c_double, C.c_int, vp, C.c_longlong,
+                                       C.POINTER(C.c_double), vp, C.c_longlong, C.POINTER(C.c_int)]
+    lib.hydot_sketch_merge.restype = C.c_int
     lib.hydot_sketch_factor.argtypes = [vp, vp, C.c_longlong, C.c_longlong, vp, C.c_longlong, C.c_longlong, C.c_int,
                                         C.c_int, vp, C.c_longlong, C.POINTER(C.c_double), vp, C.c_longlong]
     lib.hydot_sketch_factor.restype = C.c_int

@@ -167,9 +167,11 @@ class Context:
 
     # ------------------------------------------------------------------ randomised sketch
     def sketch_range(self, phi_src, phi_det, lam0: int, nlam: int, omega_t: torch.Tensor, ncols: int,
-                     Y: Optional[torch.Tensor] = None) -> torch.Tensor:
-        """hydot_sketch_range: Y = J Omega (Y has 224 columns; omega_t is bfloat16 [n_chrom][ncols][N])."""
-        M = self.n_src * self.n_det * nlam
+                     Y: Optional[torch.Tensor] = None, src0: int = 0, nsrc: Optional[int] = None) -> torch.Tensor:
+        """hydot_sketch_range: Y = J Omega over the rows of sources src0 .. src0+nsrc-1 (Y has 224
+        columns; omega_t is bfloat16 [n_chrom][ncols][N])."""
+        nsrc = self.n_src - src0 if nsrc is None else nsrc
+        M = nsrc * self.n_det * nlam
         if Y is None:
             Y = torch.empty(M, 224, dtype=torch.float32, device="cuda")
         if omega_t.dtype != torch.bfloat16 or not omega_t.is_contiguous() or omega_t.numel() != self.n_chrom * ncols * self.N:
@@ -177,33 +179,75 @@ class Context:
         self._stream()
         rc = self.lib.hydot_sketch_range(self._ctx, self._ptr(phi_src, (nlam, self.n_src, self.N), torch.float32),
                                          self._ptr(phi_det, (nlam, self.n_det, self.N), torch.float32), lam0, nlam,
-                                         omega_t.data_ptr(), ncols, self._ptr(Y, (M, Y.shape[1]), torch.float32),
-                                         Y.shape[1])
+                                         src0, nsrc, omega_t.data_ptr(), ncols,
+                                         self._ptr(Y, (M, Y.shape[1]), torch.float32), Y.shape[1])
         self._check(rc)
         return Y
 
     def sketch_project(self, phi_src, phi_det, lam0: int, nlam: int, Q: torch.Tensor, ncols: int,
-                       Bt: Optional[torch.Tensor] = None) -> torch.Tensor:
-        """hydot_sketch_project: Bt += J^T Q over the slice (Bt [n_chrom*N][224], accumulated)."""
-        M = self.n_src * self.n_det * nlam
+                       Bt: Optional[torch.Tensor] = None, src0: int = 0, nsrc: Optional[int] = None) -> torch.Tensor:
+        """hydot_sketch_project: Bt += J^T Q over the slice and the rows of sources src0 .. src0+nsrc-1
+        (Bt [n_chrom*N][224], accumulated)."""
+        nsrc = self.n_src - src0 if nsrc is None else nsrc
+        M = nsrc * self.n_det * nlam
         if Bt is None:
             Bt = torch.zeros(self.n_chrom * self.N, 224, dtype=torch.float32, device="cuda")
         self._stream()
         rc = self.lib.hydot_sketch_project(self._ctx, self._ptr(phi_src, (nlam, self.n_src, self.N), torch.float32),
                                            self._ptr(phi_det, (nlam, self.n_det, self.N), torch.float32), lam0, nlam,
-                                           self._ptr(Q, (M, Q.shape[1]), torch.float32), ncols, Q.shape[1],
+                                           src0, nsrc, self._ptr(Q, (M, Q.shape[1]), torch.float32), ncols, Q.shape[1],
                                            self._ptr(Bt, (self.n_chrom * self.N, Bt.shape[1]), torch.float32),
                                            Bt.shape[1])
         self._check(rc)
         return Bt
 
-    def sketch_orthonormalize(self, Y: torch.Tensor, ncols: int) -> int:
-        """hydot_sketch_orthonormalize in place; returns the number of directions kept."""
+    def sketch_orthonormalize(self, Y: torch.Tensor, ncols: int, return_smax: bool = False):
+        """hydot_sketch_orthonormalize in place; returns the number of directions kept (and the largest
+        singular value of the input when return_smax)."""
         k = C.c_int()
+        smax = C.c_double()
         self._stream()
         self._check(self.lib.hydot_sketch_orthonormalize(self._ctx, self._ptr(Y, tuple(Y.shape), torch.float32),
-                                                         Y.shape[0], ncols, Y.shape[1], C.byref(k)))
-        return k.value
+                                                         Y.shape[0], ncols, Y.shape[1], C.byref(k), C.byref(smax)))
+        return (k.value, smax.value) if return_smax else k.value
+
+    def sketch_rank(self, Y: torch.Tensor, nq: int, col2: int, k: int, s1: float, tol: float):
+        """hydot_sketch_rank with Q = Y[:, :nq] and the test sketch Y2 = Y[:, col2:col2+k] (both in one
+        row-major buffer): (smallest adequate rank, its error estimate relative to s1)."""
+        if col2 + k > Y.shape[1] or nq > col2:
+            raise ValueError("Q and Y2 must be disjoint column ranges of Y")
+        r = C.c_int()
+        est = C.c_double()
+        base = self._ptr(Y, tuple(Y.shape), torch.float32)
+        self._stream()
+        self._check(self.lib.hydot_sketch_rank(self._ctx, base, Y.shape[1], Y.shape[0], nq, base + 4 * col2,
+                                               Y.shape[1], k, float(s1), float(tol), C.byref(r), C.byref(est)))
+        return r.value, est.value
+
+    def sketch_merge(self, f1, f2, tol: float, max_rank: int):
+        """hydot_sketch_merge of two factorisations (U [m][r], S numpy [r], V [n][r]) of stacked row
+        blocks; returns (U [m1+m2][rank], S [rank], V [n][rank])."""
+        (U1, S1, V1), (U2, S2, V2) = f1, f2
+        r1, r2 = U1.shape[1], U2.shape[1]
+        n = V1.shape[0]
+        cap = min(max_rank, r1 + r2)
+        U = torch.empty(U1.shape[0] + U2.shape[0], cap, dtype=torch.float32, device="cuda")
+        V = torch.empty(n, cap, dtype=torch.float32, device="cuda")
+        S = np.zeros(r1 + r2)
+        s1 = np.ascontiguousarray(S1, dtype=np.float64)
+        s2 = np.ascontiguousarray(S2, dtype=np.float64)
+        rank = C.c_int()
+        dp = C.POINTER(C.c_double)
+        self._stream()
+        self._check(self.lib.hydot_sketch_merge(
+            self._ctx, self._ptr(U1, tuple(U1.shape), torch.float32), r1, U1.shape[0], s1.ctypes.data_as(dp),
+            self._ptr(V1, tuple(V1.shape), torch.float32), r1, r1,
+            self._ptr(U2, tuple(U2.shape), torch.float32), r2, U2.shape[0], s2.ctypes.data_as(dp),
+            self._ptr(V2, tuple(V2.shape), torch.float32), r2, r2, n, float(tol), cap,
+            self._ptr(U, tuple(U.shape), torch.float32), cap, S.ctypes.data_as(dp),
+            self._ptr(V, tuple(V.shape), torch.float32), cap, C.byref(rank)))
+        r = rank.value
+        return U[:, :r].contiguous(), S[:r].copy(), V[:, :r].contiguous()
 
     def sketch_factor(self, Q: torch.Tensor, Bt: torch.Tensor, ncols: int, rank: int):
         """hydot_sketch_factor: (U [rows][rank], S [rank] numpy, V [n_chrom*N][rank])."""

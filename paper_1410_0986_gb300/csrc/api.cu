@@ -275,23 +275,39 @@ static int sketch_finish(hydot_ctx* ctx, int rc) {
   return HYDOT_OK;
 }
 
-int hydot_sketch_range(hydot_ctx* ctx, const void* phi_src, const void* phi_det, int lam0, int nlam,
-                       const void* omega_t, int ncols, float* Y, long long ldY) {
+int hydot_sketch_range(hydot_ctx* ctx, const void* phi_src, const void* phi_det, int lam0, int nlam, int src0,
+                       int nsrc, const void* omega_t, int ncols, float* Y, long long ldY) {
   if (!ctx) return HYDOT_ERR_ARG;
   return sketch_finish(ctx, hydot::sketch_range_impl(ctx, (const float*)phi_src, (const float*)phi_det, lam0, nlam,
-                                                     omega_t, ncols, Y, ldY));
+                                                     src0, nsrc, omega_t, ncols, Y, ldY));
 }
 
-int hydot_sketch_project(hydot_ctx* ctx, const void* phi_src, const void* phi_det, int lam0, int nlam,
-                         const float* Q, int ncols, long long ldQ, float* Bt, long long ldB) {
+int hydot_sketch_project(hydot_ctx* ctx, const void* phi_src, const void* phi_det, int lam0, int nlam, int src0,
+                         int nsrc, const float* Q, int ncols, long long ldQ, float* Bt, long long ldB) {
   if (!ctx) return HYDOT_ERR_ARG;
   return sketch_finish(ctx, hydot::sketch_project_impl(ctx, (const float*)phi_src, (const float*)phi_det, lam0, nlam,
-                                                       Q, ncols, ldQ, Bt, ldB));
+                                                       src0, nsrc, Q, ncols, ldQ, Bt, ldB));
 }
 
-int hydot_sketch_orthonormalize(hydot_ctx* ctx, float* Y, long long rows, int ncols, long long ldY, int* rank_out) {
+int hydot_sketch_orthonormalize(hydot_ctx* ctx, float* Y, long long rows, int ncols, long long ldY, int* rank_out,
+                                double* smax_out) {
   if (!ctx) return HYDOT_ERR_ARG;
-  return hydot::sketch_orthonormalize_impl(ctx, Y, rows, ncols, ldY, rank_out);
+  return hydot::sketch_orthonormalize_impl(ctx, Y, rows, ncols, ldY, rank_out, smax_out);
+}
+
+int hydot_sketch_rank(hydot_ctx* ctx, const float* Q, long long ldQ, long long rows, int nq, const float* Y2,
+                      long long ldY2, int k, double s1, double tol, int* rank, double* estimate) {
+  if (!ctx) return HYDOT_ERR_ARG;
+  return hydot::sketch_rank_impl(ctx, Q, ldQ, rows, nq, Y2, ldY2, k, s1, tol, rank, estimate);
+}
+
+int hydot_sketch_merge(hydot_ctx* ctx, const float* U1, long long ldU1, long long m1, const double* S1, const float* V1,
+                       long long ldV1, int r1, const float* U2, long long ldU2, long long m2, const double* S2,
+                       const float* V2, long long ldV2, int r2, long long n, double tol, int max_rank, float* U,
+                       long long ldU, double* S, float* V, long long ldV, int* rank_out) {
+  if (!ctx) return HYDOT_ERR_ARG;
+  return hydot::sketch_merge_impl(ctx, U1, ldU1, m1, S1, V1, ldV1, r1, U2, ldU2, m2, S2, V2, ldV2, r2, n, tol,
+                                  max_rank, U, ldU, S, V, ldV, rank_out);
 }
 
 int hydot_sketch_factor(hydot_ctx* ctx, const float* Q, long long rows, long long ldQ, const float* Bt, long long nb,

@@ -243,11 +243,18 @@ int solver_alloc(hydot_ctx* ctx);
 void solver_free(hydot_ctx* ctx);
 
 // sketch.cu
-int sketch_range_impl(hydot_ctx* ctx, const float* ps, const float* pd, int lam0, int nlam, const void* omega_t,
-                      int ncols, float* Y, long long ldY);
-int sketch_project_impl(hydot_ctx* ctx, const float* ps, const float* pd, int lam0, int nlam, const float* Q,
-                        int ncols, long long ldQ, float* Bt, long long ldB);
-int sketch_orthonormalize_impl(hydot_ctx* ctx, float* Y, long long rows, int ncols, long long ldY, int* rank_out);
+int sketch_range_impl(hydot_ctx* ctx, const float* ps, const float* pd, int lam0, int nlam, int src0, int nsr,
+                      const void* omega_t, int ncols, float* Y, long long ldY);
+int sketch_project_impl(hydot_ctx* ctx, const float* ps, const float* pd, int lam0, int nlam, int src0, int nsr,
+                        const float* Q, int ncols, long long ldQ, float* Bt, long long ldB);
+int sketch_orthonormalize_impl(hydot_ctx* ctx, float* Y, long long rows, int ncols, long long ldY, int* rank_out,
+                               double* smax_out);
+int sketch_rank_impl(hydot_ctx* ctx, const float* Q, long long ldQ, long long rows, int nq, const float* Y2,
+                     long long ldY2, int k, double s1, double tol, int* rank, double* estimate);
+int sketch_merge_impl(hydot_ctx* ctx, const float* U1, long long ldU1, long long m1, const double* S1, const float* V1,
+                      long long ldV1, int r1, const float* U2, long long ldU2, long long m2, const double* S2,
+                      const float* V2, long long ldV2, int r2, long long n, double tol, int max_rank, float* U,
+                      long long ldU, double* S, float* V, long long ldV, int* rank_out);
 int sketch_factor_impl(hydot_ctx* ctx, const float* Q, long long rows, long long ldQ, const float* Bt, long long nb,
                        long long ldB, int ncols, int rank, float* U, long long ldU, double* S, float* V, long long ldV);
 

@@ -38,13 +38,13 @@ constexpr size_t SK_SMEM = (size_t)SK_STAGES * SK_STAGE + 1024;
 constexpr uint32_t SK_TMEM_COLS = 256;
 
 struct SketchArgs {
-  const float* ps;   // [nlam][ns][N]
+  const float* ps;   // [nlam][nsf][N]
   const float* pd;   // [nlam][nd][N]
-  int ns, nd, nlam;
+  int ns, nd, nlam;  // ns: sources of the range src0 .. src0 + ns - 1
+  int nsf, src0;     // sources in the field array; first source of the range
   long long N;
   long long P;       // pairs of the slice: nlam * ns * nd (internal order (l, s, d), d fastest)
-  int tiles_per_lam; // pass 1: ceil(ns * nd / 128)
-  int chrom;         // pass 2: chromophore of this launch
+  int chrom;         // chromophore of this launch
   float scale;       // -h^3
   float* out;
   long long ldo;
@@ -69,24 +69,16 @@ __device__ __forceinline__ void wait_or_flag(uint64_t* m, uint32_t parity, int* 
   }
 }
 
-// MODE 0: range pass (rows = (s,d) pairs of one wavelength, K = voxels).
-// MODE 1: projection pass (rows = voxels, K = pairs of the slice).
-template <int MODE>
-__global__ void __launch_bounds__(128) k_sketch_gemm(SketchArgs a, const __grid_constant__ CUtensorMap mapB) {
+// Projection pass for general optode counts (rows = voxels, K = pairs of the slice), one
+// chromophore per launch; the A tile is formed from global loads.
+__global__ void __launch_bounds__(128) k_project_generic(SketchArgs a, const __grid_constant__ CUtensorMap mapB) {
   extern __shared__ uint8_t sk_dsm[];
   uint8_t* base = align1024(sk_dsm);
   __shared__ uint64_t full[SK_STAGES], empty[SK_STAGES], done;
   __shared__ uint32_t s_tmem;
   const int tid = threadIdx.x, warp = tid >> 5;
-  int lam = 0, tile = 0;
-  long long x0 = 0;
-  if (MODE == 0) {
-    lam = blockIdx.x / a.tiles_per_lam;
-    tile = blockIdx.x % a.tiles_per_lam;
-  } else {
-    x0 = (long long)blockIdx.x * SK_M;
-  }
-  const long long K = (MODE == 0) ? a.N : a.P;
+  const long long x0 = (long long)blockIdx.x * SK_M;
+  const long long K = a.P;
   const int nk = (int)((K + SK_K - 1) / SK_K);
   if (warp == 0) tmem_alloc(&s_tmem, SK_TMEM_COLS);
   if (tid == 0) {
@@ -102,7 +94,6 @@ __global__ void __launch_bounds__(128) k_sketch_gemm(SketchArgs a, const __grid_
   tc_fence_after();
   const uint32_t tmem = s_tmem;
   constexpr uint32_t IDESC = idesc_bf16_f32(SK_M, SK_N);
-  const int npairs = a.ns * a.nd;
 
   for (int t = 0; t < nk; ++t) {
     const int st = t & 1;
@@ -114,32 +105,10 @@ __global__ void __launch_bounds__(128) k_sketch_gemm(SketchArgs a, const __grid_
     }
     if (tid == 0) {
       mbar_expect_tx(&full[st], SK_B_BYTES);
-      if (MODE == 0) tma_load_3d(Bs, &mapB, &full[st], t * SK_K, 0, lam);
-      else tma_load_3d(Bs, &mapB, &full[st], t * SK_K, 0, a.chrom);
+      tma_load_3d(Bs, &mapB, &full[st], t * SK_K, 0, a.chrom);
     }
     // ---- A tile: 128 rows x 64 K of Hadamard products, BF16, swizzled K-major
-    if (MODE == 0) {
-      const long long xk = (long long)t * SK_K;
-#pragma unroll 2
-      for (int j = 0; j < 8; ++j) {
-        const int cidx = tid + 128 * j;
-        const int row = cidx >> 3, ch = cidx & 7;
-        const int q = tile * SK_M + row;
-        uint4 pk = make_uint4(0u, 0u, 0u, 0u);
-        const long long xv = xk + ch * 8;
-        if (q < npairs && xv < a.N) {
-          const int s = q / a.nd, d = q - s * a.nd;
-          const float4* fs = reinterpret_cast<const float4*>(a.ps + ((size_t)lam * a.ns + s) * a.N + xv);
-          const float4* fd = reinterpret_cast<const float4*>(a.pd + ((size_t)lam * a.nd + d) * a.N + xv);
-          const float4 s0 = __ldg(fs), s1 = __ldg(fs + 1), d0 = __ldg(fd), d1 = __ldg(fd + 1);
-          pk.x = pack_bf16x2(s0.x * d0.x, s0.y * d0.y);
-          pk.y = pack_bf16x2(s0.z * d0.z, s0.w * d0.w);
-          pk.z = pack_bf16x2(s1.x * d1.x, s1.y * d1.y);
-          pk.w = pack_bf16x2(s1.z * d1.z, s1.w * d1.w);
-        }
-        *reinterpret_cast<uint4*>(As + sw128_offset(row, ch * 8)) = pk;
-      }
-    } else {
+    {
       const long long x = x0 + tid;
       const long long p0 = (long long)t * SK_K;
       // decode p0 once, then step (l, s, d) with d fastest
@@ -147,7 +116,7 @@ __global__ void __launch_bounds__(128) k_sketch_gemm(SketchArgs a, const __grid_
       const long long ls0 = p0 / a.nd;
       int s = (int)(ls0 % a.ns), l = (int)(ls0 / a.ns);
       const bool xin = x < a.N;
-      float fsv = (xin && p0 < a.P) ? __ldg(a.ps + ((size_t)l * a.ns + s) * a.N + x) : 0.f;
+      float fsv = (xin && p0 < a.P) ? __ldg(a.ps + ((size_t)l * a.nsf + a.src0 + s) * a.N + x) : 0.f;
       for (int ch = 0; ch < 8; ++ch) {
         float v[8];
 #pragma unroll
@@ -160,7 +129,7 @@ __global__ void __launch_bounds__(128) k_sketch_gemm(SketchArgs a, const __grid_
               s = 0;
               ++l;
             }
-            if (xin && p + 1 < a.P) fsv = __ldg(a.ps + ((size_t)l * a.ns + s) * a.N + x);
+            if (xin && p + 1 < a.P) fsv = __ldg(a.ps + ((size_t)l * a.nsf + a.src0 + s) * a.N + x);
           }
         }
         uint4 pk;
@@ -194,31 +163,16 @@ __global__ void __launch_bounds__(128) k_sketch_gemm(SketchArgs a, const __grid_
   // ---- epilogue: warp w owns TMEM lanes 32w..32w+31, i.e. accumulator rows 32w + lane
   const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
   const int row = tid;
-  float* dst = nullptr;
-  bool ok = false;
-  if (MODE == 0) {
-    const int q = tile * SK_M + row;
-    if (q < npairs) {
-      const int s = q / a.nd, d = q - s * a.nd;
-      const long long r = ((long long)s * a.nd + d) * a.nlam + lam;
-      dst = a.out + r * a.ldo;
-      ok = true;
-    }
-  } else {
-    const long long x = x0 + row;
-    if (x < a.N) {
-      dst = a.out + ((long long)a.chrom * a.N + x) * a.ldo;
-      ok = true;
-    }
-  }
+  const long long x = x0 + row;
+  const bool ok = x < a.N;
+  float* dst = a.out + ((long long)a.chrom * a.N + (ok ? x : 0)) * a.ldo;
   for (int c0 = 0; c0 < SK_N; c0 += 16) {
     float v[16];
     tmem_ld16(tmem + lane_base + (uint32_t)c0, v);
     if (ok) {
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
-        if (MODE == 0) dst[c0 + q] = a.scale * v[q];
-        else dst[c0 + q] += a.scale * v[q];
+        dst[c0 + q] += a.scale * v[q];
       }
     }
   }
@@ -248,7 +202,8 @@ constexpr size_t RG_SMEM = (size_t)RG_STAGES * RG_STAGE + 2 * RG_A_STAGE + 1024;
 constexpr uint32_t RG_TMEM_COLS = 512;                         // accumulators at columns 0 and 256
 
 struct RangeArgs {
-  int ns, nd, nlam;
+  int ns, nd, nlam;          // ns: sources of the range src0 .. src0 + ns - 1
+  int src0;
   long long N;
   int S_a, D_t, nsb, ndb;    // sources per accumulator, detectors per block, source / detector blocks
   int nk, k_per_split, nsplit;
@@ -272,7 +227,7 @@ __global__ void __launch_bounds__(RG_THREADS, 1)
   const int l = item / (a.nsb * a.ndb);
   const int rem = item - l * a.nsb * a.ndb;
   const int sb = rem / a.ndb, db = rem - sb * a.ndb;
-  const int s0 = sb * 2 * a.S_a, d0 = db * a.D_t;
+  const int s0 = a.src0 + sb * 2 * a.S_a, d0 = db * a.D_t;
   const int kt0 = ks * a.k_per_split, kt1 = min(a.nk, kt0 + a.k_per_split);
   const int nku = max(kt1 - kt0, 0);
   if (tid == 0) {
@@ -381,8 +336,8 @@ __global__ void __launch_bounds__(RG_THREADS, 1)
     long long r_out = 0;
     if (ok) {
       const int s = s0 + acc * a.S_a + rr / a.D_t, d = d0 + rr % a.D_t;
-      ok = s < a.ns && d < a.nd;
-      r_out = ((long long)s * a.nd + d) * a.nlam + l;
+      ok = s < a.src0 + a.ns && d < a.nd;
+      r_out = ((long long)(s - a.src0) * a.nd + d) * a.nlam + l;
     }
     float* dst = nullptr;
     float sc = 1.f;
@@ -443,7 +398,8 @@ constexpr uint32_t PJ_F_BYTES = 128 * PJ_M * 4;               // n_src + n_det <
 constexpr size_t PJ_SMEM = 2 * (size_t)PJ_B_STAGE + 2 * (size_t)SK_A_BYTES + PJ_F_BYTES + 1024;
 
 struct ProjArgs {
-  int ns, nd, nlam, nc, Kl;  // Kl: K-steps per wavelength
+  int ns, nd, nlam, nc, Kl;  // ns: sources of the range src0 .. src0 + ns - 1; Kl: K-steps per wavelength
+  int src0;
   long long N;
   float* Bt;
   long long ldB;
@@ -521,7 +477,7 @@ __global__ void __launch_bounds__(PJ_THREADS, 1)
       for (int l = 0; l < a.nlam; ++l) {
         if (l >= 1) wait_or_flag(&fempty, (uint32_t)((l - 1) & 1), a.err);
         mbar_expect_tx(&ffull, fb);
-        tma_load_3d(fld, &mapPs, &ffull, (int)x0, 0, l);
+        tma_load_3d(fld, &mapPs, &ffull, (int)x0, a.src0, l);
         tma_load_3d(fld + a.ns * PJ_M, &mapPd, &ffull, (int)x0, 0, l);
       }
     }
@@ -751,8 +707,7 @@ int sketch_check(hydot_ctx* ctx, int lam0, int nlam, int ncols) {
 int set_sketch_smem(hydot_ctx* ctx) {
   static bool done = false;
   if (!done) {
-    HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(k_sketch_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SK_SMEM));
-    HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(k_sketch_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SK_SMEM));
+    HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(k_project_generic, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SK_SMEM));
     HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(k_range_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RG_SMEM));
     HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(k_project_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PJ_SMEM));
     done = true;
@@ -762,15 +717,16 @@ int set_sketch_smem(hydot_ctx* ctx) {
 
 }  // namespace
 
-int sketch_range_impl(hydot_ctx* ctx, const float* ps, const float* pd, int lam0, int nlam, const void* omega_t,
-                      int ncols, float* Y, long long ldY) {
+int sketch_range_impl(hydot_ctx* ctx, const float* ps, const float* pd, int lam0, int nlam, int src0, int nsr,
+                      const void* omega_t, int ncols, float* Y, long long ldY) {
   int rc = sketch_check(ctx, lam0, nlam, ncols);
   if (rc) return rc;
+  if (src0 < 0 || nsr < 1 || src0 + nsr > ctx->n_src) return fail(ctx, HYDOT_ERR_ARG, "source range out of range");
   if (!ps || !pd || !omega_t || !Y) return fail(ctx, HYDOT_ERR_ARG, "null pointer");
   if (ldY < SK_N || ldY % 4 != 0 || (reinterpret_cast<uintptr_t>(Y) & 15) != 0)
     return fail(ctx, HYDOT_ERR_ARG, "Y must be 16-byte aligned with ldY >= 224 and ldY % 4 == 0");
   const long long N = ctx->N;
-  const int ns = ctx->n_src, nd = ctx->n_det;
+  const int ns = nsr, nd = ctx->n_det;
   const long long P = (long long)nlam * ns * nd;
   // items: (wavelength, block of 2 S_a sources, block of D_t detectors); each accumulator holds
   // S_a x D_t pairs (<= 128 rows)
@@ -796,10 +752,11 @@ int sketch_range_impl(hydot_ctx* ctx, const float* ps, const float* pd, int lam0
   HYDOT_CUDA_TRY(ctx, cudaGetLastError());
   CUtensorMap mapB, mapPs, mapPd;
   if ((rc = encode_b_map(ctx, Mt, N, nlam, &mapB))) return rc;
-  if ((rc = encode_f32_map(ctx, ps, N, ns, nlam, SK_K, 2 * S_a, &mapPs))) return rc;
+  if ((rc = encode_f32_map(ctx, ps, N, ctx->n_src, nlam, SK_K, 2 * S_a, &mapPs))) return rc;
   if ((rc = encode_f32_map(ctx, pd, N, nd, nlam, SK_K, D_t, &mapPd))) return rc;
   RangeArgs a{};
   a.ns = ns;
+  a.src0 = src0;
   a.nd = nd;
   a.nlam = nlam;
   a.N = N;
@@ -831,14 +788,15 @@ int sketch_range_impl(hydot_ctx* ctx, const float* ps, const float* pd, int lam0
   return HYDOT_OK;
 }
 
-int sketch_project_impl(hydot_ctx* ctx, const float* ps, const float* pd, int lam0, int nlam, const float* Q,
-                        int ncols, long long ldQ, float* Bt, long long ldB) {
+int sketch_project_impl(hydot_ctx* ctx, const float* ps, const float* pd, int lam0, int nlam, int src0, int nsr,
+                        const float* Q, int ncols, long long ldQ, float* Bt, long long ldB) {
   int rc = sketch_check(ctx, lam0, nlam, ncols);
   if (rc) return rc;
+  if (src0 < 0 || nsr < 1 || src0 + nsr > ctx->n_src) return fail(ctx, HYDOT_ERR_ARG, "source range out of range");
   if (!ps || !pd || !Q || !Bt) return fail(ctx, HYDOT_ERR_ARG, "null pointer");
   if (ldB < SK_N || ldQ < ncols) return fail(ctx, HYDOT_ERR_ARG, "ldB must be >= 224 and ldQ >= ncols");
   const long long N = ctx->N;
-  const int nc = ctx->n_chrom, ns = ctx->n_src, nd = ctx->n_det;
+  const int nc = ctx->n_chrom, ns = nsr, nd = ctx->n_det;
   const long long P = (long long)nlam * ns * nd;
   if ((rc = set_sketch_smem(ctx))) return rc;
   HYDOT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
@@ -857,10 +815,11 @@ int sketch_project_impl(hydot_ctx* ctx, const float* ps, const float* pd, int la
     HYDOT_CUDA_TRY(ctx, cudaGetLastError());
     CUtensorMap mapB, mapPs, mapPd;
     if ((rc = encode_b_map(ctx, Qc, nlam * Pl, nc, &mapB))) return rc;
-    if ((rc = encode_f32_map(ctx, ps, N, ns, nlam, PJ_M, ns, &mapPs))) return rc;
+    if ((rc = encode_f32_map(ctx, ps, N, ctx->n_src, nlam, PJ_M, ns, &mapPs))) return rc;
     if ((rc = encode_f32_map(ctx, pd, N, nd, nlam, PJ_M, nd, &mapPd))) return rc;
     ProjArgs a{};
     a.ns = ns;
+    a.src0 = src0;
     a.nd = nd;
     a.nlam = nlam;
     a.nc = nc;
@@ -893,6 +852,8 @@ int sketch_project_impl(hydot_ctx* ctx, const float* ps, const float* pd, int la
   a.ps = ps;
   a.pd = pd;
   a.ns = ns;
+  a.nsf = ctx->n_src;
+  a.src0 = src0;
   a.nd = nd;
   a.nlam = nlam;
   a.N = N;
@@ -905,7 +866,7 @@ int sketch_project_impl(hydot_ctx* ctx, const float* ps, const float* pd, int la
   cudaEvent_t t0 = timer_begin(ctx);
   for (int c = 0; c < nc; ++c) {
     a.chrom = c;
-    k_sketch_gemm<1><<<grid, 128, SK_SMEM, ctx->stream>>>(a, map);
+    k_project_generic<<<grid, 128, SK_SMEM, ctx->stream>>>(a, map);
     ++ctx->launches;
   }
   timer_end(ctx, t0, HYDOT_KERNEL_SKETCH_PROJECT, 2.0 * (double)nc * (double)N * (double)P * ncols);
@@ -982,10 +943,55 @@ __global__ void k_gram_reduce(const double* __restrict__ part, int nchunk, int n
   }
 }
 
-// Z[r][j] = sum_k X[r][k] W[k][j] for j < m (Z columns m..ldz-1 untouched), FP32.
+// partial[chunk][ti][tj][GT][GT] = X[rows of chunk][tile ti]^T Y[rows of chunk][tile tj] in FP64
+__global__ void __launch_bounds__(256) k_cross64(const float* __restrict__ X, long long ldx, int nx,
+                                                 const float* __restrict__ Y, long long ldy, int ny, long long rows,
+                                                 long long rows_per_chunk, double* __restrict__ part) {
+  __shared__ double Xi[64][GT + 1], Yj[64][GT + 1];
+  const int chunk = blockIdx.x, ti = blockIdx.y, tj = blockIdx.z;
+  const int t = threadIdx.x;
+  const int ii = t >> 3, jj = (t & 7) * 4;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  const long long r0 = (long long)chunk * rows_per_chunk;
+  const long long r1 = min(rows, r0 + rows_per_chunk);
+  for (long long rb = r0; rb < r1; rb += 64) {
+    for (int q = t; q < 64 * GT; q += 256) {
+      const int rr = q / GT, cc = q % GT;
+      const long long r = rb + rr;
+      const int ci = ti * GT + cc, cj = tj * GT + cc;
+      Xi[rr][cc] = (r < r1 && ci < nx) ? (double)X[r * ldx + ci] : 0.0;
+      Yj[rr][cc] = (r < r1 && cj < ny) ? (double)Y[r * ldy + cj] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int rr = 0; rr < 64; ++rr) {
+      const double a = Xi[rr][ii];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] += a * Yj[rr][jj + q];
+    }
+    __syncthreads();
+  }
+  double* out = part + ((((size_t)chunk * gridDim.y + ti) * gridDim.z + tj) * GT + ii) * GT + jj;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) out[q] = acc[q];
+}
+
+__global__ void k_cross_reduce(const double* __restrict__ part, int nchunk, int ntx, int nty, int nx, int ny,
+                               double* __restrict__ G) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= ntx * nty * GT * GT) return;
+  const int tile = idx / (GT * GT), ij = idx % (GT * GT), ii = ij / GT, jj = ij % GT;
+  const int ti = tile / nty, tj = tile % nty;
+  double s = 0.0;
+  for (int c = 0; c < nchunk; ++c) s += part[((size_t)c * ntx * nty + tile) * GT * GT + ij];
+  const int a = ti * GT + ii, b = tj * GT + jj;
+  if (a < nx && b < ny) G[(size_t)a * ny + b] = s;
+}
+
+// Z[r][j] (+)= sum_k X[r][k] W[k][j] for j < m (Z columns m..ldz-1 untouched), FP32.
 __global__ void __launch_bounds__(256) k_right_mul(const float* __restrict__ X, long long rows, long long ldx, int n,
                                                    const float* __restrict__ W, int m, float* __restrict__ Z,
-                                                   long long ldz) {
+                                                   long long ldz, int accumulate) {
   __shared__ float Xs[64][33];
   __shared__ float Ws[32][64];
   const int t = threadIdx.x, tr = t >> 4, tc = t & 15;
@@ -1024,7 +1030,7 @@ __global__ void __launch_bounds__(256) k_right_mul(const float* __restrict__ X, 
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       const int c = c0 + tc * 4 + v;
-      if (c < m) Z[r * ldz + c] = acc[u][v];
+      if (c < m) Z[r * ldz + c] = accumulate ? Z[r * ldz + c] + acc[u][v] : acc[u][v];
     }
   }
 }
@@ -1057,14 +1063,43 @@ int gram(hydot_ctx* ctx, const float* X, long long rows, long long ldx, int n, s
   return HYDOT_OK;
 }
 
-// Z = X W with W (n x m) given on the host.
+// C = X[:, :nx]^T Y[:, :ny] (nx x ny, FP64, row-major) to the host.
+int cross(hydot_ctx* ctx, const float* X, long long ldx, int nx, const float* Y, long long ldy, int ny, long long rows,
+          std::vector<double>& Cm) {
+  const int ntx = (nx + GT - 1) / GT, nty = (ny + GT - 1) / GT;
+  const long long want = std::max<long long>(1, 4 * 152 / (ntx * nty));
+  const long long nchunk = std::max<long long>(1, std::min<long long>(want, (rows + 63) / 64));
+  const long long rpc = ((rows + nchunk - 1) / nchunk + 63) / 64 * 64;
+  const long long nch = (rows + rpc - 1) / rpc;
+  double *part = nullptr, *dC = nullptr;
+  HYDOT_CUDA_TRY(ctx, cudaMalloc(&part, sizeof(double) * (size_t)nch * ntx * nty * GT * GT));
+  cudaError_t e = cudaMalloc(&dC, sizeof(double) * (size_t)nx * ny);
+  if (e != cudaSuccess) {
+    cudaFree(part);
+    return fail(ctx, HYDOT_ERR_OOM, "cudaMalloc of a cross product failed");
+  }
+  k_cross64<<<dim3((unsigned)nch, ntx, nty), 256, 0, ctx->stream>>>(X, ldx, nx, Y, ldy, ny, rows, rpc, part);
+  k_cross_reduce<<<(ntx * nty * GT * GT + 255) / 256, 256, 0, ctx->stream>>>(part, (int)nch, ntx, nty, nx, ny, dC);
+  ctx->launches += 2;
+  Cm.assign((size_t)nx * ny, 0.0);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(Cm.data(), dC, sizeof(double) * nx * ny, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  cudaFree(part);
+  cudaFree(dC);
+  if (e != cudaSuccess) return fail(ctx, HYDOT_ERR_CUDA, std::string("cross: ") + cudaGetErrorString(e));
+  return HYDOT_OK;
+}
+
+// Z = X W (or Z += X W) with W (n x m) given on the host.
 int right_mul(hydot_ctx* ctx, const float* X, long long rows, long long ldx, int n, const std::vector<float>& W, int m,
-              float* Z, long long ldz) {
+              float* Z, long long ldz, bool accumulate = false) {
   float* dW = nullptr;
   HYDOT_CUDA_TRY(ctx, cudaMalloc(&dW, sizeof(float) * (size_t)n * m));
   cudaError_t e = cudaMemcpyAsync(dW, W.data(), sizeof(float) * (size_t)n * m, cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess) {
-    k_right_mul<<<dim3((unsigned)((rows + 63) / 64), (m + 63) / 64), 256, 0, ctx->stream>>>(X, rows, ldx, n, dW, m, Z, ldz);
+    k_right_mul<<<dim3((unsigned)((rows + 63) / 64), (m + 63) / 64), 256, 0, ctx->stream>>>(X, rows, ldx, n, dW, m, Z, ldz,
+                                                                                          accumulate ? 1 : 0);
     ++ctx->launches;
     e = cudaGetLastError();
   }
@@ -1094,7 +1129,8 @@ void eig_desc(const std::vector<double>& G, int n, std::vector<double>& lam, std
 // Orthonormal basis of range(Y) in place: two rounds of Y <- Y V_k diag(lambda_k^-1/2) from the FP64
 // Gram Y^T Y = V diag(lambda) V^T, keeping the directions whose singular value exceeds 1e-6 of the
 // largest (the rest are set to zero columns). *rank_out receives the number kept.
-int sketch_orthonormalize_impl(hydot_ctx* ctx, float* Y, long long rows, int ncols, long long ldY, int* rank_out) {
+int sketch_orthonormalize_impl(hydot_ctx* ctx, float* Y, long long rows, int ncols, long long ldY, int* rank_out,
+                               double* smax_out) {
   if (!Y || rows < 1 || ncols < 1 || ncols > SK_N || ldY < ncols) return fail(ctx, HYDOT_ERR_ARG, "bad Y shape");
   float* Z = nullptr;
   HYDOT_CUDA_TRY(ctx, cudaMalloc(&Z, sizeof(float) * (size_t)rows * ncols));
@@ -1105,6 +1141,7 @@ int sketch_orthonormalize_impl(hydot_ctx* ctx, float* Y, long long rows, int nco
     if (rc) { cudaFree(Z); return rc; }
     eig_desc(G, ncols, lam, V);
     const double smax = std::sqrt(std::max(lam[0], 0.0));
+    if (round == 0 && smax_out) *smax_out = smax;
     kept = 0;
     std::vector<float> W((size_t)ncols * ncols, 0.f);
     for (int j = 0; j < ncols; ++j) {
@@ -1151,6 +1188,97 @@ int sketch_factor_impl(hydot_ctx* ctx, const float* Q, long long rows, long long
   rc = right_mul(ctx, Bt, nb, ldB, ncols, WV, rank, V, ldV);
   if (!rc) rc = right_mul(ctx, Q, rows, ldQ, ncols, WU, rank, U, ldU);
   return rc;
+}
+
+// Adaptive rank (Appendix A.1, alg:randsvd error estimator): with Q the orthonormal basis of range(A
+// Omega_1) (columns in descending singular-value order) and Y2 = A Omega_2 for k further Gaussian
+// columns, the smallest r with e_r = || Y2 - Q_r Q_r^T Y2 ||_2 <= tol * s1. Because Q is orthonormal,
+// (Y2 - Q_r Q_r^T Y2)^T (Y2 - Q_r Q_r^T Y2) = Y2^T Y2 - sum_(i<r) c_i c_i^T with c_i = Q[:, i]^T Y2, so all
+// e_r follow from the k x k Gram of Y2 and the nq x k product Q^T Y2 (both FP64).
+int sketch_rank_impl(hydot_ctx* ctx, const float* Q, long long ldQ, long long rows, int nq, const float* Y2,
+                     long long ldY2, int k, double s1, double tol, int* rank, double* estimate) {
+  if (!Q || !Y2 || !rank || rows < 1 || nq < 1 || nq > SK_N || k < 1 || k > 32 || ldQ < nq || ldY2 < k)
+    return fail(ctx, HYDOT_ERR_ARG, "bad arguments to the rank estimator");
+  std::vector<double> C, G2;
+  int rc = cross(ctx, Q, ldQ, nq, Y2, ldY2, k, rows, C);
+  if (!rc) rc = cross(ctx, Y2, ldY2, k, Y2, ldY2, k, rows, G2);
+  if (rc) return rc;
+  std::vector<double> R = G2, lam, V;
+  int r = 0;
+  double e = 0.0;
+  for (;; ++r) {
+    jacobi_eig(R, k, lam, V);
+    double lmax = 0.0;
+    for (double v : lam) lmax = std::max(lmax, v);
+    e = std::sqrt(std::max(lmax, 0.0));
+    if (e <= tol * s1 || r == nq) break;
+    for (int a = 0; a < k; ++a)
+      for (int b = 0; b < k; ++b) R[(size_t)a * k + b] -= C[(size_t)r * k + a] * C[(size_t)r * k + b];
+  }
+  *rank = std::max(r, 1);
+  if (estimate) *estimate = s1 > 0.0 ? e / s1 : 0.0;
+  return HYDOT_OK;
+}
+
+// Agglomeration of two low-rank factorisations of stacked row blocks (Section 4.3):
+//   [H1; H2] ~ [U1 S1 V1^T; U2 S2 V2^T] = blockdiag(U1, U2) W,  W = [S1 V1^T; S2 V2^T].
+// W W^T = [[S1 V1^T V1 S1, S1 V1^T V2 S2], [S2 V2^T V1 S1, S2 V2^T V2 S2]] ((r1+r2)^2, FP64 from the
+// tall-skinny products) = E diag(lambda) E^T; keeping the r directions with sqrt(lambda_i) >
+// tol * sqrt(lambda_1) (at most max_rank) gives W ~ E_r diag(S) V^T with S = sqrt(lambda_r) and
+// V = W^T E_r diag(1/S), hence U = blockdiag(U1, U2) E_r: the merged factors are again a truncated SVD.
+int sketch_merge_impl(hydot_ctx* ctx, const float* U1, long long ldU1, long long m1, const double* S1, const float* V1,
+                      long long ldV1, int r1, const float* U2, long long ldU2, long long m2, const double* S2,
+                      const float* V2, long long ldV2, int r2, long long n, double tol, int max_rank, float* U,
+                      long long ldU, double* S, float* V, long long ldV, int* rank_out) {
+  if (!U1 || !S1 || !V1 || !U2 || !S2 || !V2 || !U || !S || !V || !rank_out)
+    return fail(ctx, HYDOT_ERR_ARG, "null pointer");
+  const int rt = r1 + r2;
+  if (r1 < 1 || r2 < 1 || rt > 2 * SK_N || max_rank < 1 || m1 < 1 || m2 < 1 || n < 1 || ldU1 < r1 || ldU2 < r2 ||
+      ldV1 < r1 || ldV2 < r2)
+    return fail(ctx, HYDOT_ERR_ARG, "bad factor shapes for the merge");
+  std::vector<double> C12, G11, G22;
+  int rc = cross(ctx, V1, ldV1, r1, V2, ldV2, r2, n, C12);
+  if (!rc) rc = cross(ctx, V1, ldV1, r1, V1, ldV1, r1, n, G11);
+  if (!rc) rc = cross(ctx, V2, ldV2, r2, V2, ldV2, r2, n, G22);
+  if (rc) return rc;
+  std::vector<double> G((size_t)rt * rt, 0.0);
+  for (int i = 0; i < r1; ++i)
+    for (int j = 0; j < r1; ++j) G[(size_t)i * rt + j] = S1[i] * G11[(size_t)i * r1 + j] * S1[j];
+  for (int i = 0; i < r2; ++i)
+    for (int j = 0; j < r2; ++j) G[(size_t)(r1 + i) * rt + r1 + j] = S2[i] * G22[(size_t)i * r2 + j] * S2[j];
+  for (int i = 0; i < r1; ++i)
+    for (int j = 0; j < r2; ++j) {
+      const double v = S1[i] * C12[(size_t)i * r2 + j] * S2[j];
+      G[(size_t)i * rt + r1 + j] = v;
+      G[(size_t)(r1 + j) * rt + i] = v;
+    }
+  std::vector<double> lam, E;
+  eig_desc(G, rt, lam, E);
+  const double s_1 = std::sqrt(std::max(lam[0], 0.0));
+  int r = 0;
+  while (r < rt && r < max_rank && std::sqrt(std::max(lam[r], 0.0)) > tol * s_1 && lam[r] > 0.0) ++r;
+  r = std::max(r, 1);
+  if (ldU < r || ldV < r) return fail(ctx, HYDOT_ERR_ARG, "ldU / ldV smaller than the merged rank");
+  std::vector<float> E1((size_t)r1 * r), E2((size_t)r2 * r), W1((size_t)r1 * r), W2((size_t)r2 * r);
+  for (int j = 0; j < r; ++j) {
+    const double sj = std::sqrt(std::max(lam[j], 0.0));
+    S[j] = sj;
+    for (int i = 0; i < r1; ++i) {
+      E1[(size_t)i * r + j] = (float)E[(size_t)i * rt + j];
+      W1[(size_t)i * r + j] = sj > 0.0 ? (float)(S1[i] * E[(size_t)i * rt + j] / sj) : 0.f;
+    }
+    for (int i = 0; i < r2; ++i) {
+      E2[(size_t)i * r + j] = (float)E[(size_t)(r1 + i) * rt + j];
+      W2[(size_t)i * r + j] = sj > 0.0 ? (float)(S2[i] * E[(size_t)(r1 + i) * rt + j] / sj) : 0.f;
+    }
+  }
+  rc = right_mul(ctx, U1, m1, ldU1, r1, E1, r, U, ldU);
+  if (!rc) rc = right_mul(ctx, U2, m2, ldU2, r2, E2, r, U + m1 * ldU, ldU);
+  if (!rc) rc = right_mul(ctx, V1, n, ldV1, r1, W1, r, V, ldV);
+  if (!rc) rc = right_mul(ctx, V2, n, ldV2, r2, W2, r, V, ldV, true);
+  if (rc) return rc;
+  *rank_out = r;
+  return HYDOT_OK;
 }
 
 }  // namespace hydot

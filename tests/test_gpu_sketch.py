@@ -194,3 +194,42 @@ def test_sketch_project_general_shape_fallback(lib):
             ref[c * N:(c + 1) * N] += -h3 * A.T @ bf16_round((np.float32(p.eps[0, c]) * Q[rows]).astype(np.float32))
     err = np.abs(Bt - ref).max(axis=0) / np.abs(ref).max(axis=0)
     assert err.max() <= 2e-3, err.max()
+
+
+def test_recursive_compression_against_exact_recursion(lib):
+    """Algorithm alg:recursive on the GPU (randomised leaves with the adaptive-rank estimator,
+    tensor-core passes, agglomeration by hydot_sketch_merge) against the oracle's recursion with
+    exact SVDs on the same source tree: the error of U S V^T stays inside the Section 4.5 bound
+    (plus the BF16 floor of the passes), and the ranks kept at the leaves and at the root are close
+    to the exact ones."""
+    from oracle import sketch as osk
+    from paper_1410_0986_gb300 import tree
+
+    p0 = workloads.make_problem(workloads.Grid(16, 16, 12, 2.0), 8, 6, 2, seed=71, geometry="transmission", margin=0)
+    p, order, root = tree.order_problem(p0)
+    rs, rd = osolve.fields_separable(p)
+    J = oborn.born_matrix(p, rs, rd)  # rows (s, d, lambda) with sources in tree order
+    nd, nl, N, nc = p.n_det, p.n_lambda, p.grid.N, p.n_chrom
+    eps = 1e-2
+    blocks = {s: J[[(s * nd + d) * nl + a for d in range(nd) for a in range(nl)]] for s in range(p.n_src)}
+    ref_tree = osk.geometric_bisection(np.asarray(p.src_ijk, float)[:, :2] + 0.5, (0.0, 0.0),
+                                       (float(p.grid.nx), float(p.grid.ny)))
+    assert [i for l in osk.tree_leaves(ref_tree) for i in l] == list(range(p.n_src))  # already in tree order
+    Ur, Sr, Vr, ranks_ref = osk.recursive_lowrank(blocks, ref_tree, eps)
+    om = workloads.gaussian(72, (nc, 220, N)).astype(np.float32)
+    ranks = []
+    with lib.Context.from_problem(p, precision="mixed", tol=1e-8, tol_cw=0.0) as ctx:
+        ps = torch.tensor(rs, dtype=torch.float32, device="cuda")
+        pd = torch.tensor(rd, dtype=torch.float32, device="cuda")
+        U, S, V = tree.compress(ctx, root, ps, pd, 0, nl, torch.tensor(om, device="cuda").to(torch.bfloat16), eps,
+                                log=lambda kind, node, r: ranks.append((kind, node.lo, node.hi, r)))
+        U, V = U.double().cpu().numpy(), V.double().cpu().numpy()
+    Jhat = U @ (S[:, None] * V.T)
+    L = root.depth()
+    fro = np.linalg.norm(J)
+    err = np.linalg.norm(J - Jhat)
+    assert err <= osk.recursive_error_bound(eps, L, fro) + 1e-2 * fro, (err / fro)
+    assert np.linalg.norm(J - Jhat, 2) <= 3 * eps * np.linalg.norm(J, 2) + 1e-2 * np.linalg.norm(J, 2)
+    r_root = S.size
+    assert abs(r_root - Sr.size) <= max(3, Sr.size // 4), (r_root, Sr.size)
+    assert np.abs(S[:5] / Sr[:5] - 1).max() < 2e-2

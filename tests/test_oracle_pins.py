@@ -312,3 +312,79 @@ def test_randsvd_near_optimal_on_decaying_spectrum():
     assert s[r] <= err * (1 + 1e-9) and err <= 1.5 * s[r]
     X = rng.standard_normal((n, 8))
     assert sketch.probe_error(A, U, S, V, X).max() < 10 * s[r] / s[0]
+
+
+def _random_points(n, seed):
+    rng = np.random.default_rng(seed)
+    return rng.uniform(0.0, 10.0, size=(n, 2))
+
+
+def test_geometric_bisection_follows_the_split_rule():
+    """Every leaf has at most two points, the leaves partition the points, and at every inner node
+    the two sides are separated by the centre of the node box's widest side."""
+    from oracle import sketch as osk
+
+    pts = _random_points(37, 1)
+    tree = osk.geometric_bisection(pts, (0.0, 0.0), (10.0, 10.0))
+    leaves = osk.tree_leaves(tree)
+    assert all(1 <= len(l) <= 2 for l in leaves)
+    assert sorted(i for l in leaves for i in l) == list(range(37))
+
+    def check(t, lo, hi):
+        if osk.tree_is_leaf(t):
+            return
+        low = [i for l in osk.tree_leaves(t[0]) for i in l]
+        high = [i for l in osk.tree_leaves(t[1]) for i in l]
+        members = low + high
+        lo, hi = list(lo), list(hi)
+        while True:  # cuts that leave every point on one side only shrink the box
+            ax = int(np.argmax(np.subtract(hi, lo)))
+            cut = (lo[ax] + hi[ax]) / 2.0
+            below = pts[members, ax] <= cut
+            if below.all():
+                hi[ax] = cut
+            elif not below.any():
+                lo[ax] = cut
+            else:
+                break
+        assert pts[low, ax].max() <= cut < pts[high, ax].min()
+        hi1, lo2 = list(hi), list(lo)
+        hi1[ax] = cut
+        lo2[ax] = cut
+        check(t[0], lo, hi1)
+        check(t[1], lo2, hi)
+
+    check(tree, (0.0, 0.0), (10.0, 10.0))
+    assert osk.tree_depth(tree) >= 4
+
+
+def test_recursive_lowrank_exact_and_within_the_section_bound():
+    """With eps at rounding level the recursion reproduces H; at a moderate eps its Frobenius error
+    is inside 2^(L/2) (L+1) eps ||H||_F, the merges never exceed the sum of their children's ranks,
+    and merging two exact SVDs without truncation gives the stacked matrix's singular values."""
+    from oracle import sketch as osk
+
+    p = workloads.make_problem(workloads.Grid(10, 9, 8, 2.0), 6, 4, 2, seed=13, geometry="transmission", margin=0)
+    rs, rd = solve.fields_splu(p)
+    J = born.born_matrix(p, rs, rd)
+    nd, nl = p.n_det, p.n_lambda
+    blocks = {s: J[[(s * nd + d) * nl + a for d in range(nd) for a in range(nl)]] for s in range(p.n_src)}
+    xy = np.asarray(p.src_ijk, float)[:, :2] + 0.5
+    tree = osk.geometric_bisection(xy, (0.0, 0.0), (float(p.grid.nx), float(p.grid.ny)))
+    order = [i for l in osk.tree_leaves(tree) for i in l]
+    H = np.vstack([blocks[i] for i in order])
+    U, S, V, _ = osk.recursive_lowrank(blocks, tree, 1e-15)
+    assert np.abs(U @ (S[:, None] * V.T) - H).max() <= 1e-10 * np.abs(H).max()
+    L = osk.tree_depth(tree)
+    for eps in (1e-2, 1e-3, 1e-5):
+        U, S, V, ranks = osk.recursive_lowrank(blocks, tree, eps)
+        err = np.linalg.norm(H - U @ (S[:, None] * V.T))
+        assert err <= osk.recursive_error_bound(eps, L, np.linalg.norm(H))
+        if eps >= 1e-3:
+            assert S.size < min(H.shape)  # the truncation compresses
+    A = blocks[order[0]]
+    B = blocks[order[1]]
+    f = [np.linalg.svd(X, full_matrices=False) for X in (A, B)]
+    W = np.vstack([s[:, None] * vt for (_, s, vt) in f])
+    assert np.allclose(np.linalg.svd(W, compute_uv=False), np.linalg.svd(np.vstack([A, B]), compute_uv=False),
+                       rtol=1e-10, atol=1e-14 * np.abs(A).max())
