@@ -431,6 +431,49 @@ def sketch_phase(hd, pk, n_lam=4, rank=200, over=20, n_probe=32):
     out["probe_error"] = {"max": max(errs), "median": float(np.median(errs)), "rms": float(np.sqrt(np.mean(np.square(errs)))),
                           "n": n_probe}
     out["frobenius_error_of_factors"] = frob_err
+    out["recursive"] = tree_phase(hd, p, n_lam)
+    return out
+
+
+def tree_phase(hd, p, n_lam, tol=1e-2, leaf_rank=100, merge_rank=160, n_probe=16):
+    """Recursive compression (Section 4, alg:recursive) of the same chunk: sources ordered by the
+    geometric bisection tree, randomised leaves with the adaptive-rank estimator, agglomeration up
+    the tree; wall time, ranks, and the probe and Frobenius errors of the result."""
+    import numpy as np
+    import torch
+
+    import workloads
+    from paper_1410_0986_gb300 import tree
+
+    q, order, root = tree.order_problem(p)
+    N, nc = q.grid.N, q.n_chrom
+    out = {"tol": tol, "leaves": len(root.leaves()), "depth": root.depth(), "leaf_rank_cap": leaf_rank,
+           "merge_rank_cap": merge_rank}
+    with hd.Context.from_problem(q, precision="mixed", tol=1e-10, tol_cw=TOL_CW, cw_floor=CW_FLOOR,
+                                 max_lambda_per_call=n_lam) as ctx:
+        ps, pd, st = ctx.solve_fields(0, n_lam)
+        gen = torch.Generator(device="cuda").manual_seed(workloads.SEED_BASE + 55)
+        om = torch.randn(nc, leaf_rank + 30, N, device="cuda", generator=gen).to(torch.bfloat16)
+        ranks = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        U, S, V = tree.compress(ctx, root, ps, pd, 0, n_lam, om, tol, leaf_rank=leaf_rank, merge_rank=merge_rank,
+                                log=lambda kind, node, r: ranks.append((kind, r)))
+        torch.cuda.synchronize()
+        out["wall_s"] = time.perf_counter() - t0
+        del om
+        leaf = [r for k, r in ranks if k == "leaf"]
+        out["ranks"] = {"leaf_mean": float(np.mean(leaf)), "leaf_max": int(max(leaf)), "root": int(S.size)}
+        e2 = torch.tensor((q.eps[:n_lam] ** 2).sum(1), device="cuda", dtype=torch.float64)
+        jf2 = float((q.grid.h ** 6) * (e2 * ((ps.double() ** 2).sum(1) * (pd.double() ** 2).sum(1)).sum(1)).sum())
+        out["frobenius_error_of_factors"] = float(max(0.0, 1.0 - float((torch.tensor(S) ** 2).sum()) / jf2) ** 0.5)
+        X = torch.randn(nc * N, n_probe, device="cuda", generator=gen)
+        errs = []
+        for k in range(n_probe):
+            jx = ctx.born_apply(ps, pd, 0, n_lam, X[:, k].contiguous()).double()
+            lr = U.double() @ (torch.tensor(S, device="cuda") * (V.double().T @ X[:, k].double()))
+            errs.append(float((jx - lr).norm() / jx.norm()))
+        out["probe_error"] = {"median": float(np.median(errs)), "max": max(errs), "n": n_probe}
     return out
 
 

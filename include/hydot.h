@@ -238,7 +238,8 @@ int hydot_sketch_project(hydot_ctx* ctx, const void* phi_src, const void* phi_de
                          int nsrc, const float* Q, int ncols, long long ldQ, float* Bt, long long ldB);
 
 /* Orthonormal basis of range(Y) in place (the basis step of alg:randsvd): two rounds of
- * Y <- Y V diag(lambda^-1/2) from the FP64 Gram Y^T Y = V diag(lambda) V^T. Directions whose
+ * Y <- Y V diag(lambda^-1/2) from the Gram Y^T Y = V diag(lambda) V^T (FP32 products, FP64 sums across
+ * 64-row blocks, eigen-decomposition in FP64 on the host). Directions whose
  * singular value is below 1e-6 of the largest become zero columns; *rank_out (may be NULL) gets the
  * number kept, *smax_out (may be NULL) the largest singular value of the input Y. The columns come
  * out in descending order of singular value. Y: DEVICE float [rows][ldY], first ncols (<= 224)
@@ -251,7 +252,8 @@ int hydot_sketch_orthonormalize(hydot_ctx* ctx, float* Y, long long rows, int nc
  * float [rows][ldY2] = A Omega_2 for k (1..32) further Gaussian columns. *rank receives the smallest
  * r (at least 1) with || Y2 - Q_r Q_r^T Y2 ||_2 <= tol * s1, where Q_r are the first r columns and s1
  * is the caller's scale (the largest singular value of A Omega_1); nq when none qualifies.
- * *estimate (may be NULL) receives || Y2 - Q_r Q_r^T Y2 ||_2 / s1 for that r. Sums in FP64.
+ * *estimate (may be NULL) receives || Y2 - Q_r Q_r^T Y2 ||_2 / s1 for that r. Products in FP32, sums across
+ * 64-row blocks in FP64.
  * Synchronous. */
 int hydot_sketch_rank(hydot_ctx* ctx, const float* Q, long long ldQ, long long rows, int nq, const float* Y2,
                       long long ldY2, int k, double s1, double tol, int* rank, double* estimate);
@@ -262,15 +264,16 @@ int hydot_sketch_rank(hydot_ctx* ctx, const float* Q, long long ldQ, long long r
  * V2^T] above tol times the largest (at most max_rank of them). Inputs: U1 [m1][ldU1], V1 [n][ldV1]
  * (r1 columns), likewise block 2, all DEVICE float; S1, S2 HOST double. Outputs: U DEVICE float
  * [m1+m2][ldU], V DEVICE float [n][ldV] (not aliasing the inputs), S HOST double [r1+r2] (first
- * *rank_out entries set), *rank_out the merged rank. The Gram of the stacked factors is formed in
- * FP64 from tall-skinny products and diagonalised on the host. Synchronous. */
+ * *rank_out entries set), *rank_out the merged rank. The Gram of the stacked factors is formed from
+ * tall-skinny products (FP32 products, FP64 block sums) and diagonalised in FP64 on the host. Synchronous. */
 int hydot_sketch_merge(hydot_ctx* ctx, const float* U1, long long ldU1, long long m1, const double* S1, const float* V1,
                        long long ldV1, int r1, const float* U2, long long ldU2, long long m2, const double* S2,
                        const float* V2, long long ldV2, int r2, long long n, double tol, int max_rank, float* U,
                        long long ldU, double* S, float* V, long long ldV, int* rank_out);
 
 /* Rank-`rank` factors J ~ U diag(S) V^T from Q (the orthonormal range basis, rows x ncols) and
- * Bt = (Q^T J)^T (nb = n_chrom*N rows): the FP64 Gram of Bt gives U_B and S (descending), then
+ * Bt = (Q^T J)^T (nb = n_chrom*N rows): the Gram of Bt (FP32 products, FP64 block sums) gives U_B and S
+ * (descending), then
  * V = Bt U_B diag(1/S) and U = Q U_B (Section 4.4's final recompression). U: DEVICE float
  * [rows][ldU], V: DEVICE float [nb][ldV], S: HOST double [rank]. Synchronous. */
 int hydot_sketch_factor(hydot_ctx* ctx, const float* Q, long long rows, long long ldQ, const float* Bt, long long nb,

@@ -243,7 +243,7 @@ int build_deflation(hydot_ctx* ctx) {
     T[(size_t)i * mm + i] = alpha[i];
     if (i + 1 < mm) T[(size_t)i * mm + i + 1] = T[(size_t)(i + 1) * mm + i] = beta[i];
   }
-  jacobi_eig(T, mm, lam, Z);
+  sym_eig(T, mm, lam, Z);
   std::vector<int> order(mm);
   for (int i = 0; i < mm; ++i) order[i] = i;
   std::sort(order.begin(), order.end(), [&](int a, int b) { return lam[a] < lam[b]; });

@@ -877,9 +877,11 @@ int sketch_project_impl(hydot_ctx* ctx, const float* ps, const float* pd, int la
 }  // namespace hydot
 
 // ---------------------------------------------------------------- tall-skinny helpers
-// Orthonormalisation of the range sketch and the final factors use the n x n (n <= 224) Gram
-// matrices of tall-skinny operands, accumulated in FP64 (the Gram squares the condition number),
-// and products with small n x m matrices.
+// Orthonormalisation of the range sketch, the final factors and the merges use the n x n (n <= 224)
+// Gram matrices and cross products of tall-skinny operands: FP32 products summed in FP32 within
+// 64-row blocks and in FP64 across blocks (the Gram squares the condition number; the second round
+// of the orthonormalisation restores what the block sums lose), and products with small n x m
+// matrices.
 namespace hydot {
 namespace {
 
@@ -888,7 +890,7 @@ constexpr int GT = 32;  // Gram tile (columns)
 // partial[chunk][pair][GT][GT] = X[rows of chunk][tile i]^T X[rows of chunk][tile j], pair = (i <= j)
 __global__ void __launch_bounds__(256) k_gram64(const float* __restrict__ X, long long rows, long long ldx, int n,
                                                 int ntile, long long rows_per_chunk, double* __restrict__ part) {
-  __shared__ double Xi[64][GT + 1], Xj[64][GT + 1];
+  __shared__ float Xi[64][GT + 1], Xj[64][GT + 1];
   const int chunk = blockIdx.x, pair = blockIdx.y;
   int ti = 0, rem = pair;
   while (rem >= ntile - ti) {
@@ -906,16 +908,21 @@ __global__ void __launch_bounds__(256) k_gram64(const float* __restrict__ X, lon
       const int rr = q / GT, cc = q % GT;
       const long long r = rb + rr;
       const int ci = ti * GT + cc, cj = tj * GT + cc;
-      Xi[rr][cc] = (r < r1 && ci < n) ? (double)X[r * ldx + ci] : 0.0;
-      Xj[rr][cc] = (r < r1 && cj < n) ? (double)X[r * ldx + cj] : 0.0;
+      Xi[rr][cc] = (r < r1 && ci < n) ? X[r * ldx + ci] : 0.f;
+      Xj[rr][cc] = (r < r1 && cj < n) ? X[r * ldx + cj] : 0.f;
     }
     __syncthreads();
+    // FP32 products and sums within the 64-row block, FP64 across blocks (GB300's FP64 rate is
+    // ~1/64 of FP32; the block sums carry ~1e-6 relative error)
+    float blk[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 4
     for (int rr = 0; rr < 64; ++rr) {
-      const double a = Xi[rr][ii];
+      const float a = Xi[rr][ii];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] += a * Xj[rr][jj + q];
+      for (int q = 0; q < 4; ++q) blk[q] = fmaf(a, Xj[rr][jj + q], blk[q]);
     }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] += (double)blk[q];
     __syncthreads();
   }
   double* out = part + (((size_t)chunk * gridDim.y + pair) * GT + ii) * GT + jj;
@@ -943,11 +950,11 @@ __global__ void k_gram_reduce(const double* __restrict__ part, int nchunk, int n
   }
 }
 
-// partial[chunk][ti][tj][GT][GT] = X[rows of chunk][tile ti]^T Y[rows of chunk][tile tj] in FP64
+// partial[chunk][ti][tj][GT][GT] = X[rows of chunk][tile ti]^T Y[rows of chunk][tile tj] (FP64 across blocks)
 __global__ void __launch_bounds__(256) k_cross64(const float* __restrict__ X, long long ldx, int nx,
                                                  const float* __restrict__ Y, long long ldy, int ny, long long rows,
                                                  long long rows_per_chunk, double* __restrict__ part) {
-  __shared__ double Xi[64][GT + 1], Yj[64][GT + 1];
+  __shared__ float Xi[64][GT + 1], Yj[64][GT + 1];
   const int chunk = blockIdx.x, ti = blockIdx.y, tj = blockIdx.z;
   const int t = threadIdx.x;
   const int ii = t >> 3, jj = (t & 7) * 4;
@@ -959,16 +966,19 @@ __global__ void __launch_bounds__(256) k_cross64(const float* __restrict__ X, lo
       const int rr = q / GT, cc = q % GT;
       const long long r = rb + rr;
       const int ci = ti * GT + cc, cj = tj * GT + cc;
-      Xi[rr][cc] = (r < r1 && ci < nx) ? (double)X[r * ldx + ci] : 0.0;
-      Yj[rr][cc] = (r < r1 && cj < ny) ? (double)Y[r * ldy + cj] : 0.0;
+      Xi[rr][cc] = (r < r1 && ci < nx) ? X[r * ldx + ci] : 0.f;
+      Yj[rr][cc] = (r < r1 && cj < ny) ? Y[r * ldy + cj] : 0.f;
     }
     __syncthreads();
+    float blk[4] = {0.f, 0.f, 0.f, 0.f};  // FP32 within the block, FP64 across blocks
 #pragma unroll 4
     for (int rr = 0; rr < 64; ++rr) {
-      const double a = Xi[rr][ii];
+      const float a = Xi[rr][ii];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] += a * Yj[rr][jj + q];
+      for (int q = 0; q < 4; ++q) blk[q] = fmaf(a, Yj[rr][jj + q], blk[q]);
     }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] += (double)blk[q];
     __syncthreads();
   }
   double* out = part + ((((size_t)chunk * gridDim.y + ti) * gridDim.z + tj) * GT + ii) * GT + jj;
@@ -1112,7 +1122,7 @@ int right_mul(hydot_ctx* ctx, const float* X, long long rows, long long ldx, int
 // eigen-pairs of a symmetric n x n matrix, descending
 void eig_desc(const std::vector<double>& G, int n, std::vector<double>& lam, std::vector<double>& V) {
   std::vector<double> l, Z;
-  jacobi_eig(G, n, l, Z);
+  sym_eig(G, n, l, Z);
   std::vector<int> ord(n);
   for (int i = 0; i < n; ++i) ord[i] = i;
   std::sort(ord.begin(), ord.end(), [&](int a, int b) { return l[a] > l[b]; });
@@ -1207,7 +1217,7 @@ int sketch_rank_impl(hydot_ctx* ctx, const float* Q, long long ldQ, long long ro
   int r = 0;
   double e = 0.0;
   for (;; ++r) {
-    jacobi_eig(R, k, lam, V);
+    sym_eig(R, k, lam, V);
     double lmax = 0.0;
     for (double v : lam) lmax = std::max(lmax, v);
     e = std::sqrt(std::max(lmax, 0.0));
