@@ -208,6 +208,14 @@ long long hydot_kernel_launches(const hydot_ctx* ctx);
  * (0 if not timed yet). Any output pointer may be NULL; arrays hold HYDOT_ROLL_VARIANTS entries. */
 int hydot_get_tuning(const hydot_ctx* ctx, int* variant, int* planes, int* buffers, double* ns_per_cell);
 
+/* Absorption perturbation for the nonlinear forward model (eqn:lippschwin without the Born
+ * approximation): later hydot_solve_fields calls solve (A_lambda + h^3 diag(dmu_a)) phi = e with
+ * dmu_a(x; lambda) = sum_c eps_c(lambda) dc[c][x], the diffusion coefficient staying the
+ * background's. dc: HOST double [n_chrom][N] concentration changes (mM), copied; NULL removes the
+ * perturbation. Perturbed solves run the generic (non-TMA) inner kernels; results stay FP32 fields
+ * with FP64 refinement (or FP64 throughout), to the context's tolerances. Synchronous. */
+int hydot_set_absorption(hydot_ctx* ctx, const double* dc);
+
 /* Failure-path self-test (no counterpart in the paper): one thread waits on a shared-memory
  * mbarrier that nothing arrives at, through the same bounded poll loop the pipelined kernels use
  * for their TMA and tensor-core waits, but with `polls` polls (1..2^22) instead of their limit;

@@ -25,7 +25,8 @@ EXPORTS = ("hydot_version", "hydot_setup", "hydot_set_stream", "hydot_solve_fiel
            "hydot_born_apply", "hydot_born_apply_T", "hydot_born_apply_noalloc", "hydot_sketch_range",
            "hydot_sketch_project", "hydot_sketch_orthonormalize", "hydot_sketch_rank", "hydot_sketch_merge",
            "hydot_sketch_factor", "hydot_set_kernel_timing",
-           "hydot_kernel_stats", "hydot_kernel_launches", "hydot_get_tuning", "hydot_wait_selftest",
+           "hydot_kernel_stats", "hydot_kernel_launches", "hydot_get_tuning", "hydot_set_absorption",
+           "hydot_wait_selftest",
            "hydot_last_error", "hydot_destroy")
 ROLL_VARIANTS = 4  # HYDOT_ROLL_VARIANTS
 KERNELS = {"dir": 0, "update": 1, "residual": 2, "born_rows": 3, "apply": 4, "apply_T": 5, "sketch_range": 6,
@@ -117,6 +118,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.hydot_get_tuning.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                      C.POINTER(C.c_double)]
     lib.hydot_get_tuning.restype = C.c_int
+    lib.hydot_set_absorption.argtypes = [vp, C.POINTER(C.c_double)]
+    lib.hydot_set_absorption.restype = C.c_int
     lib.hydot_wait_selftest.argtypes = [vp, C.c_int]
     lib.hydot_wait_selftest.restype = C.c_int
     lib.hydot_last_error.argtypes = [vp]

@@ -277,6 +277,18 @@ class Context:
     def kernel_launches(self) -> int:
         return int(self.lib.hydot_kernel_launches(self._ctx))
 
+    def set_absorption(self, dc: Optional[np.ndarray]) -> None:
+        """hydot_set_absorption: dc [n_chrom * N] concentration changes (mM, chromophore-major), or
+        None to return to the background medium."""
+        if dc is None:
+            self._check(self.lib.hydot_set_absorption(self._ctx, None))
+            return
+        a = np.ascontiguousarray(dc, dtype=np.float64).reshape(-1)
+        if a.size != self.n_chrom * self.N:
+            raise ValueError("dc must have n_chrom * N entries")
+        self._stream()
+        self._check(self.lib.hydot_set_absorption(self._ctx, a.ctypes.data_as(C.POINTER(C.c_double))))
+
     def wait_selftest(self, polls: int = 1000) -> None:
         """hydot_wait_selftest: a bounded device wait that runs out; raises HydotError
         (HYDOT_ERR_TIMEOUT) as every pipelined kernel's timeout would."""

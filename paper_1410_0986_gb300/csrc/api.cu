@@ -319,6 +319,11 @@ int hydot_sketch_factor(hydot_ctx* ctx, const float* Q, long long rows, long lon
 
 long long hydot_kernel_launches(const hydot_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
+int hydot_set_absorption(hydot_ctx* ctx, const double* dc) {
+  if (!ctx) return HYDOT_ERR_ARG;
+  return hydot::set_absorption_impl(ctx, dc);
+}
+
 int hydot_wait_selftest(hydot_ctx* ctx, int polls) {
   if (!ctx) return HYDOT_ERR_ARG;
   return hydot::wait_selftest_impl(ctx, polls);

@@ -195,6 +195,10 @@ struct hydot_ctx {
   } tune;
   cudaEvent_t tune_ev[2] = {nullptr, nullptr};
   int* d_it = nullptr;               // device-resident base of the inner iteration index
+  // absorption perturbation dc [n_chrom][N] (mM, FP64) and the per-slice diagonal increments
+  double* d_dc = nullptr;
+  double* d_dsig_d = nullptr;        // [max_lambda_per_call][N]
+  float* d_dsig_f = nullptr;
   bool use_graphs = true;            // replay groups of inner iterations from a CUDA graph
   void* inner_exec = nullptr;        // cudaGraphExec_t of one group
   cudaStream_t cap_stream = nullptr;  // private non-blocking stream the group is captured on
@@ -239,6 +243,7 @@ inline int fail(hydot_ctx* ctx, int code, const std::string& msg) {
 int solve_fields_impl(hydot_ctx* ctx, int lam0, int nlam, void* phi_src, void* phi_det, hydot_stats* st);
 int get_tuning_impl(const hydot_ctx* ctx, int* variant, int* planes, int* buffers, double* ns_per_cell);
 int wait_selftest_impl(hydot_ctx* ctx, int polls);
+int set_absorption_impl(hydot_ctx* ctx, const double* dc);
 int solver_alloc(hydot_ctx* ctx);
 void solver_free(hydot_ctx* ctx);
 

@@ -73,7 +73,21 @@ struct Batch {
   int max_inner, max_iter;
   double tol, tol_cw, cw_floor;
   int n_src, n_det;
+  // per-voxel increment of the scaled diagonal, h^2 dmu_a(x; lambda) / D(lambda), for the
+  // wavelengths of the slice ([nlam][N]); null without an absorption perturbation
+  const float* dsig_f;
+  const double* dsig_d;
 };
+
+// Increment of the diagonal of field rhs at voxel id in precision T (real part only).
+template <typename T>
+__device__ __forceinline__ T dsig_at(const Batch& b, int rhs, long long id, long long N) {
+  if constexpr (sizeof(typename Traits<T>::R) == 8) {
+    return Traits<T>::make(b.dsig_d[(size_t)(rhs / b.nf) * N + id], 0.0);
+  } else {
+    return Traits<T>::make(b.dsig_f[(size_t)(rhs / b.nf) * N + id], 0.0);
+  }
+}
 
 __device__ __forceinline__ int rhs_lambda(const Batch& b, int rhs) { return b.lam0 + rhs / b.nf; }
 __device__ __forceinline__ long long rhs_source(const Batch& b, int rhs) {
@@ -258,9 +272,10 @@ __global__ void __launch_bounds__(NTHREADS) k_residual(Geo g, Batch b, const X* 
       if (c.j > 0) { X v = x[vidx(g, c.i, c.j - 1, k)]; sn = sn + v; ed = max(ed, bexp(v)); }
       if (c.j < g.ny - 1) { X v = x[vidx(g, c.i, c.j + 1, k)]; sn = sn + v; ed = max(ed, bexp(v)); }
       const int m = face_mask(g, c.i, c.j, k);
-      X d = diag_at<X>(dg, m);
-      X ax = d * xc - sn;
       long long id = vidx(g, c.i, c.j, k);
+      X d = diag_at<X>(dg, m);
+      if (b.dsig_d) d = d + dsig_at<X>(b, c.rhs, id, g.N);
+      X ax = d * xc - sn;
       X r64 = (id == src) ? Traits<X>::make(1.0, 0.0) - ax : zero - ax;
       rr += Traits<X>::abs2(r64);
       int ec = bexp(xc);
@@ -270,7 +285,8 @@ __global__ void __launch_bounds__(NTHREADS) k_residual(Geo g, Batch b, const X* 
       if (er) om_e = max(om_e, ed ? er + 1 + cplx_extra - ed : 4096);
       T rv = Traits<T>::from(Traits<X>::re(r64) * pre, Traits<X>::im(r64) * pre);
       r[id] = rv;
-      T rz = rv * (rv * (m ? inv(diag_at<T>(dgi, m)) : idint));
+      T rz = rv * (rv * ((m || b.dsig_f) ? inv(diag_at<T>(dgi, m) + (b.dsig_f ? dsig_at<T>(b, c.rhs, id, g.N) : Traits<T>::zero()))
+                                           : idint));
       acc[0] += Traits<T>::rre(rz);
       acc[1] += Traits<T>::rim(rz);
       acc[2] += Traits<T>::abs2(rv);
@@ -398,11 +414,13 @@ __global__ void __launch_bounds__(NTHREADS) k_dir(Geo g, Batch b, int it, const 
   const T idint = inv(dint);
   const bool first = (it == 0);
   Rt acc[2] = {0, 0};
+  const bool het = b.dsig_f != nullptr;  // per-voxel absorption perturbation on the diagonal
   if (c.in) {
     auto P = [&](int ii, int jj, int kk) -> T {
       long long id = vidx(g, ii, jj, kk);
       const int m = face_mask(g, ii, jj, kk);
-      T z = r[id] * (m ? inv(diag_at<T>(dg, m)) : idint);
+      T z = het ? r[id] * inv((m ? diag_at<T>(dg, m) : dint) + dsig_at<T>(b, c.rhs, id, g.N))
+                : r[id] * (m ? inv(diag_at<T>(dg, m)) : idint);
       return first ? z : z + beta * po[id];
     };
     T zero = Traits<T>::zero();
@@ -416,7 +434,9 @@ __global__ void __launch_bounds__(NTHREADS) k_dir(Geo g, Batch b, int it, const 
       if (c.j > 0) s = s + P(c.i, c.j - 1, k);
       if (c.j < g.ny - 1) s = s + P(c.i, c.j + 1, k);
       const int m = face_mask(g, c.i, c.j, k);
-      T q = (m ? diag_at<T>(dg, m) : dint) * pc - s;
+      T dk = m ? diag_at<T>(dg, m) : dint;
+      if (het) dk = dk + dsig_at<T>(b, c.rhs, vidx(g, c.i, c.j, k), g.N);
+      T q = dk * pc - s;
       T pq = pc * q;
       acc[0] += Traits<T>::rre(pq);
       acc[1] += Traits<T>::rim(pq);
@@ -474,14 +494,16 @@ __global__ void __launch_bounds__(NTHREADS) k_update(Geo g, Batch b, int it, T* 
       if (c.j > 0) s = s + p[vidx(g, c.i, c.j - 1, k)];
       if (c.j < g.ny - 1) s = s + p[vidx(g, c.i, c.j + 1, k)];
       const int m = face_mask(g, c.i, c.j, k);
-      T d = m ? diag_at<T>(dg, m) : dint;
-      T q = d * pc - s;
       long long id = vidx(g, c.i, c.j, k);
+      T d = m ? diag_at<T>(dg, m) : dint;
+      const bool het = b.dsig_f != nullptr;
+      if (het) d = d + dsig_at<T>(b, c.rhs, id, g.N);
+      T q = d * pc - s;
       T ev = first ? alpha * pc : e[id] + alpha * pc;
       T rv = r[id] - alpha * q;
       e[id] = ev;
       r[id] = rv;
-      T z = rv * (m ? inv(d) : idint);
+      T z = rv * ((m || het) ? inv(d) : idint);
       T rz = rv * z;
       acc[0] += Traits<T>::rre(rz);
       acc[1] += Traits<T>::rim(rz);
@@ -961,6 +983,25 @@ Geo make_geo(const hydot_ctx* ctx) {
   return g;
 }
 
+// ---------------------------------------------------------------- absorption perturbation
+// dsig[l][x] = h^2 sum_c eps_c(lambda_(lam0+l)) dc_c(x) / D(lambda): the perturbation
+// h^3 dmu_a(x) of the absorption term (the diffusion coefficient stays the background's, as in
+// the Born model of eqn:lippschwin) in the scaled operator A / (D h).
+__global__ void k_dsig(const double* __restrict__ dc, const double* __restrict__ eps, const LamCoef* __restrict__ coef,
+                       int lam0, int nlam, int nc, long long N, double h2, double* __restrict__ out_d,
+                       float* __restrict__ out_f) {
+  const long long total = (long long)nlam * N;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (long long)gridDim.x * blockDim.x) {
+    const int l = (int)(q / N);
+    const long long x = q - (long long)l * N;
+    double dm = 0.0;
+    for (int c = 0; c < nc; ++c) dm += eps[(size_t)(lam0 + l) * nc + c] * dc[(size_t)c * N + x];
+    const double v = h2 * dm / coef[lam0 + l].D;
+    out_d[q] = v;
+    out_f[q] = (float)v;
+  }
+}
+
 // ---------------------------------------------------------------- rolling-pass variants
 // {planes per slab, slab buffers}; the autotuner picks one per context (they give identical bits).
 struct RollVariant {
@@ -1141,6 +1182,18 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
   b.part = ctx->d_part;
   b.counter = ctx->d_counter;
   b.err = ctx->d_err;
+  b.dsig_d = nullptr;
+  b.dsig_f = nullptr;
+  if (ctx->d_dc) {
+    const long long tot = (long long)nlam * ctx->N;
+    k_dsig<<<(unsigned)std::min<long long>((tot + 255) / 256, 152 * 64), 256, 0, ctx->stream>>>(
+        ctx->d_dc, ctx->d_eps, ctx->d_coef, lam0, nlam, ctx->n_chrom, ctx->N, ctx->h * ctx->h, ctx->d_dsig_d,
+        ctx->d_dsig_f);
+    ++ctx->launches;
+    HYDOT_CUDA_TRY(ctx, cudaGetLastError());
+    b.dsig_d = ctx->d_dsig_d;
+    b.dsig_f = ctx->d_dsig_f;
+  }
   const bool mixed = ctx->precision == HYDOT_MIXED;
   const double tin = mixed ? (ctx->inner_tol > 0 ? ctx->inner_tol : 1e-5) : ctx->tol;
   b.tol_in2 = tin * tin;
@@ -1202,7 +1255,7 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
     int slot = 0;
     bool stop = false;
     // rolling passes (FP32 real fields, TMA): the iteration index lives on the device
-    const bool roll = std::is_same<T, float>::value && ctx->use_tma;
+    const bool roll = std::is_same<T, float>::value && ctx->use_tma && !ctx->d_dc;
     const unsigned nrb =
         roll ? (unsigned)((long long)b.nrhs * g.ntx * g.nty * ((g.nz + ctx->dir_seg - 1) / ctx->dir_seg)) : 0u;
     if (roll) HYDOT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_it, 0, sizeof(int), s));
@@ -1451,6 +1504,9 @@ void solver_free(hydot_ctx* ctx) {
   cudaFree(ctx->d_err);
   if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
   cudaFree(ctx->d_it);
+  cudaFree(ctx->d_dc);
+  cudaFree(ctx->d_dsig_d);
+  cudaFree(ctx->d_dsig_f);
   if (ctx->inner_exec) cudaGraphExecDestroy((cudaGraphExec_t)ctx->inner_exec);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   if (ctx->tune_ev[0]) cudaEventDestroy(ctx->tune_ev[0]);
@@ -1481,6 +1537,29 @@ int wait_selftest_impl(hydot_ctx* ctx, int polls) {
   HYDOT_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
   HYDOT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
   if (flag) return fail(ctx, HYDOT_ERR_TIMEOUT, "bounded wait gave up (self-test)");
+  return HYDOT_OK;
+}
+
+int set_absorption_impl(hydot_ctx* ctx, const double* dc) {
+  if (!dc) {
+    cudaFree(ctx->d_dc);
+    cudaFree(ctx->d_dsig_d);
+    cudaFree(ctx->d_dsig_f);
+    ctx->d_dc = nullptr;
+    ctx->d_dsig_d = nullptr;
+    ctx->d_dsig_f = nullptr;
+    return HYDOT_OK;
+  }
+  const size_t n = (size_t)ctx->n_chrom * ctx->N;
+  // one increment per wavelength of the largest slice (max_fields / (n_src + n_det) wavelengths)
+  const size_t m = (size_t)std::max(1, ctx->max_fields / std::max(1, ctx->n_src + ctx->n_det)) * ctx->N;
+  if (!ctx->d_dc) {
+    HYDOT_CUDA_TRY(ctx, cudaMalloc(&ctx->d_dc, sizeof(double) * n));
+    HYDOT_CUDA_TRY(ctx, cudaMalloc(&ctx->d_dsig_d, sizeof(double) * m));
+    HYDOT_CUDA_TRY(ctx, cudaMalloc(&ctx->d_dsig_f, sizeof(float) * m));
+  }
+  HYDOT_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->d_dc, dc, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
+  HYDOT_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
   return HYDOT_OK;
 }
 

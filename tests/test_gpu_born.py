@@ -193,3 +193,68 @@ def test_apply_and_apply_T_optode_blocks(lib, ns, nd):
         yy = ctx.born_apply(ps, pd, 0, p.n_lambda, torch.tensor(xv, dtype=torch.float32, device="cuda"))
     assert np.abs(g.double().cpu().numpy() - g_ref).max() <= 2e-5 * np.abs(g_ref).max()
     assert np.abs(yy.double().cpu().numpy() - y_ref).max() <= 2e-5 * np.abs(y_ref).max()
+
+
+def _perturbed_fields_oracle(p, dc):
+    """Oracle fields of the perturbed medium: sparse LU of A_lambda + h^3 diag(dmu_a)."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    from oracle import model
+
+    N = p.grid.N
+    nc = p.n_chrom
+    out_s = np.empty((p.n_lambda, p.n_src, N))
+    out_d = np.empty((p.n_lambda, p.n_det, N))
+    for lam in range(p.n_lambda):
+        dmua = sum(p.eps[lam, c] * dc[c * N:(c + 1) * N] for c in range(nc))
+        lu = spla.splu((model.operator(p, lam) + sp.diags(p.grid.h ** 3 * dmua)).tocsc())
+        for out, cells in ((out_s, p.src_voxels()), (out_d, p.det_voxels())):
+            for a, v in enumerate(cells):
+                e = np.zeros(N)
+                e[v] = 1.0
+                out[lam, a] = lu.solve(e)
+    return out_s, out_d
+
+
+@pytest.mark.parametrize("grid,precision", [((17, 12, 10), "mixed"), ((20, 16, 12), "mixed"), ((17, 12, 10), "fp64")])
+def test_absorption_perturbation_fields(lib, grid, precision):
+    """hydot_set_absorption: fields of the perturbed medium (the nonlinear forward model) against
+    the oracle's sparse LU; 20 x 16 x 12 would take the TMA inner kernels without the perturbation."""
+    p = workloads.make_problem(workloads.Grid(*grid, 2.0), 2, 3, 2, seed=81, geometry="transmission", margin=1)
+    dc = workloads.ellipsoid_anomaly(p.grid, seed=82, contrast=0.5)
+    rs, rd = _perturbed_fields_oracle(p, dc)
+    kw = dict(tol=1e-13, tol_cw=0.0) if precision == "fp64" else dict(tol=1e-10, tol_cw=1e-8)
+    with lib.Context.from_problem(p, precision=precision, **kw) as ctx:
+        ctx.set_absorption(dc)
+        ps, pd, st = ctx.solve_fields(0, p.n_lambda)
+        ctx.set_absorption(None)
+        qs, _, _ = ctx.solve_fields(0, p.n_lambda)
+    tol = 1e-10 if precision == "fp64" else 1e-6
+    for got, ref in ((ps, rs), (pd, rd)):
+        g = got.double().cpu().numpy()
+        assert (np.linalg.norm(g - ref, axis=-1) / np.linalg.norm(ref, axis=-1)).max() <= tol
+    # the perturbation absorbs: removing it raises every field
+    assert (qs.double() - ps.double()).min() >= -1e-6 * float(qs.abs().max())
+
+
+def test_born_error_is_first_order_in_the_contrast(lib):
+    """The Born model y(0) + t J dc against the nonlinear forward model y(t) (the perturbed fields
+    at the detector cells): the relative error vanishes with t and grows linearly (halving t halves
+    it), as the remainder of the first-order expansion must."""
+    p = workloads.make_problem(workloads.Grid(24, 24, 16, 2.0), 3, 3, 2, seed=83, geometry="transmission")
+    dc = workloads.ellipsoid_anomaly(p.grid, seed=84, contrast=0.005)
+    det = torch.tensor(p.det_voxels(), device="cuda")
+    with lib.Context.from_problem(p, precision="fp64", tol=1e-13, tol_cw=0.0) as ctx:
+        ps, pd, _ = ctx.solve_fields(0, p.n_lambda)
+        y0 = ps[:, :, det].permute(1, 2, 0).reshape(-1)  # rows (s, d, lambda)
+        jdc = ctx.born_apply(ps, pd, 0, p.n_lambda, torch.tensor(dc, device="cuda"))
+        errs = []
+        for t in (2.0, 1.0, 0.5, 0.25):
+            ctx.set_absorption(t * dc)
+            qs, _, _ = ctx.solve_fields(0, p.n_lambda, detectors=False)
+            yt = qs[:, :, det].permute(1, 2, 0).reshape(-1)
+            errs.append(float((yt - y0 - t * jdc).norm() / (yt - y0).norm()))
+        ctx.set_absorption(None)
+    ratios = [errs[i] / errs[i + 1] for i in range(3)]
+    assert errs[-1] < 0.05, errs
+    assert all(1.7 < r < 2.3 for r in ratios), (errs, ratios)
