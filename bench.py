@@ -365,6 +365,7 @@ def run_ours(args):
         out["fp64_vs_mixed_at_1e-6"] = compare_fp64(hd, p)
         out["deflation"] = compare_deflation(hd, p)
         out["cuda_graphs"] = compare_graphs(hd, p)
+        out["born_validity"] = born_validity(hd, p)
     if rank == 0 and not args.no_sketch:
         out["sketch"] = sketch_phase(hd, pk)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -537,6 +538,40 @@ def compare_graphs(hd, p):
                 os.environ.pop("HYDOT_NO_GRAPHS", None)
         row["speedup"] = row["graph"] / row["direct"]
         res[name] = row
+    return res
+
+
+def born_validity(hd, p, contrasts=(0.001, 0.005, 0.01, 0.02, 0.05, 0.1), lam=0):
+    """Experiment-3-style check of the Born model on the benchmark grid: the relative error of
+    y(0) + J dc against the nonlinear forward model y(dc) (fields of the perturbed medium at the
+    detector cells) for the seeded three-ellipsoid anomaly at several contrasts, one wavelength."""
+    import torch
+
+    import workloads
+
+    base = workloads.ellipsoid_anomaly(p.grid, seed=workloads.SEED_BASE + 90, contrast=1.0)
+    det = torch.tensor(p.det_voxels(), device="cuda")
+    res = {"wavelength": lam, "anomaly": "3 ellipsoids, semi-axes 3-8 cells, all chromophores"}
+    with hd.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=1e-10, max_lambda_per_call=1) as ctx:
+        ps, pd, _ = ctx.solve_fields(lam, 1)
+        y0 = ps[0][:, det].reshape(-1).double()
+        curve = {}
+        for cst in contrasts:
+            dc = cst * base
+            jdc = ctx.born_apply(ps, pd, lam, 1, torch.tensor(dc, dtype=torch.float32, device="cuda")).double()
+            ctx.set_absorption(dc)
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            qs, _, _ = ctx.solve_fields(lam, 1, detectors=False)
+            b.record()
+            torch.cuda.synchronize()
+            yt = qs[0][:, det].reshape(-1).double()
+            curve[f"{cst:g} mM"] = {"born_rel_error": float((yt - y0 - jdc).norm() / (yt - y0).norm()),
+                                    "perturbed_solves_per_s": p.n_src / (a.elapsed_time(b) / 1e3)}
+            ctx.set_absorption(None)
+        res["curve"] = curve
     return res
 
 
