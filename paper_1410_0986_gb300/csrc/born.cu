@@ -6,6 +6,7 @@
 // with slice rows r = (s*n_det + d)*nlam + a.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 
 #include "hydot_internal.cuh"
 
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(256) k_apply_partial(const E* __restrict__ ps,
   const int grp = t / 16, sub = t % 16;
   const int si0 = sub / 4, di0 = sub % 4;
   __shared__ E w[MAXC];  // eps_c(lambda_a)
-  __shared__ E mu[AP_XC];  // mu_a of the stage's voxels
+  __shared__ __align__(16) E mu[AP_XC];  // mu_a of the stage's voxels
   if (t < nc) w[t] = (E)eps[(size_t)(lam0 + a) * nc + t];
   const E* srow = ps + ((size_t)a * ns + s0) * N;
   const E* drow = pd + ((size_t)a * nd + d0) * N;
@@ -234,17 +235,48 @@ __global__ void __launch_bounds__(256) k_apply_partial(const E* __restrict__ ps,
       mu[t] = m;
     }
     __syncthreads();
-    for (int q = grp; q < AP_XC; q += 16) {
-      const E m = mu[q];
-      E sv[8], dv[8];
+    if constexpr (sizeof(E) == 4) {
+      // scale the source rows by mu once, then contract 4-voxel quads with 16-byte reads:
+      // per quad 8 + 8 vector reads feed 256 FMAs
+      for (int q = t; q < 32 * AP_XC / 4; q += 256) {
+        float4* sp = reinterpret_cast<float4*>(const_cast<E*>(S) + (q / (AP_XC / 4)) * LD) + q % (AP_XC / 4);
+        const float4 m4 = reinterpret_cast<const float4*>(mu)[q % (AP_XC / 4)];
+        float4 v4 = *sp;
+        v4.x *= m4.x; v4.y *= m4.y; v4.z *= m4.z; v4.w *= m4.w;
+        *sp = v4;
+      }
+      __syncthreads();
+      // quads of warp w = grp / 2: (w / 2) * 8 + (w % 2) * 2 + {0, 1, 4, 5}, the odd group 4 quads
+      // (16 banks) after the even one; with the 4-bank row skew the 8 distinct 16-byte words a
+      // warp reads cover the 32 banks once
+      const int qbase = (grp >> 2) * 8 + ((grp >> 1) & 1) * 2 + (grp & 1) * 4;
+#pragma unroll 1
+      for (int qd = 0; qd < 2; ++qd) {
+        const int x0 = (qbase + qd) * 4;
+        float4 dv[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) sv[u] = S[(si0 + 4 * u) * LD + q] * m;
+        for (int v = 0; v < 8; ++v) dv[v] = *reinterpret_cast<const float4*>(D + (di0 + 4 * v) * LD + x0);
 #pragma unroll
-      for (int v = 0; v < 8; ++v) dv[v] = D[(di0 + 4 * v) * LD + q];
+        for (int u = 0; u < 8; ++u) {
+          const float4 sv = *reinterpret_cast<const float4*>(S + (si0 + 4 * u) * LD + x0);
 #pragma unroll
-      for (int u = 0; u < 8; ++u)
+          for (int v = 0; v < 8; ++v)
+            acc[u][v] += sv.x * dv[v].x + sv.y * dv[v].y + sv.z * dv[v].z + sv.w * dv[v].w;
+        }
+      }
+    } else {
+      for (int q = grp; q < AP_XC; q += 16) {
+        const E m = mu[q];
+        E sv[8], dv[8];
 #pragma unroll
-        for (int v = 0; v < 8; ++v) acc[u][v] += sv[u] * dv[v];
+        for (int u = 0; u < 8; ++u) sv[u] = S[(si0 + 4 * u) * LD + q] * m;
+#pragma unroll
+        for (int v = 0; v < 8; ++v) dv[v] = D[(di0 + 4 * v) * LD + q];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+          for (int v = 0; v < 8; ++v) acc[u][v] += sv[u] * dv[v];
+      }
     }
     __syncthreads();  // buffer (st & 1) is refilled by the load of stage st + 2
   }
@@ -284,20 +316,40 @@ inline int apply_vec_ok(const void* a, const void* b, const void* c, long long N
   return ((N * (long long)es) % 16 == 0 && al(a) && al(b) && al(c)) ? 1 : 0;
 }
 
+// Block = 32 consecutive entries of one (wavelength, optode tile) partial block; its 8 warps take
+// every 8th voxel block (reads of 128 contiguous bytes per warp) and the 8 FP64 sums are added in
+// warp order, so the result does not depend on scheduling.
 template <typename E>
-__global__ void k_apply_reduce(const E* __restrict__ part, int nlam, int ns, int nd, int nts, int ntd, int nxb,
-                               double h3, E* __restrict__ y) {
-  long long total = (long long)ns * nd * nlam;
-  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < total; r += (long long)gridDim.x * blockDim.x) {
-    int a = (int)(r % nlam);
-    int sd = (int)(r / nlam);
-    int s = sd / nd, d = sd % nd;
-    int tsd = (s / 32) + (d / 32) * nts;
-    const E* p = part + (((size_t)a * nts * ntd + tsd) * nxb) * 1024 + (s % 32) * 32 + (d % 32);
-    double sum = 0.0;
-    for (int xb = 0; xb < nxb; ++xb) sum += (double)p[(size_t)xb * 1024];
-    y[r] = (E)(-h3 * sum);
+__global__ void __launch_bounds__(256) k_apply_reduce(const E* __restrict__ part, int nlam, int ns, int nd, int nts,
+                                                      int ntd, int nxb, double h3, E* __restrict__ y) {
+  __shared__ double red[8][32];
+  const int ntile = nts * ntd;
+  const int e0 = (int)(blockIdx.x % 32) * 32;
+  const long long at = blockIdx.x / 32;  // a * ntile + tile
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const E* p = part + (size_t)at * nxb * 1024 + e0 + lane;
+  double sum = 0.0;
+#pragma unroll 4
+  for (int xb = w; xb < nxb; xb += 8) sum += (double)p[(size_t)xb * 1024];
+  red[w][lane] = sum;
+  __syncthreads();
+  if (w == 0) {
+    double tot = 0.0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) tot += red[i][lane];
+    const int e = e0 + lane;
+    const int a = (int)(at / ntile), tile = (int)(at % ntile);
+    const int s = (tile % nts) * 32 + e / 32, d = (tile / nts) * 32 + e % 32;
+    if (s < ns && d < nd) y[((size_t)s * nd + d) * nlam + a] = (E)(-h3 * tot);
   }
+}
+
+template <typename E>
+cudaError_t launch_apply_reduce(const E* part, int nlam, int ns, int nd, int nts, int ntd, int nxb, double h3, E* y,
+                                cudaStream_t st) {
+  const unsigned blocks = (unsigned)((size_t)nlam * nts * ntd * 32);
+  k_apply_reduce<E><<<blocks, 256, 0, st>>>(part, nlam, ns, nd, nts, ntd, nxb, h3, y);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- J^T y
@@ -385,6 +437,155 @@ __global__ void __launch_bounds__(256, 2) k_apply_T_partial(const E* __restrict_
     }
 }
 
+// Register-tiled variant (FP32, up to 4 chromophores, N a multiple of 4). Block = 256-voxel chunk x
+// group of wavelengths; 256 threads = 64 voxel quads x 4 source groups (thread t: quad t / 4, group
+// t % 4). The sources are taken in tiles of 4 * SPT; a thread owns SPT sources of the tile and the
+// 4 voxels of its quad and accumulates W[s][x] = sum_d Y_a[s][d] phi_d(x) over detector chunks of
+// TT_DC, staged (phi_d rows of the chunk and Y_a of the tile) in shared memory by cp.async, two
+// stages in flight. Per detector a warp reads one 16-byte word of phi_d per quad (8 quads: 128
+// contiguous bytes) and two of Y (4 groups: distinct banks) for 4 * SPT FMAs. After the last chunk
+// of a tile t_a(x) += sum_s phi_s(x) W[s][x] with phi_s read from global memory straight into
+// registers (issued before the detector loop), and after the last tile of a wavelength
+// acc_c(x) += eps_c(lambda_a) t_a(x). The 4 groups' partial sums are added by shuffles at the end.
+constexpr int TT_XC = 256;  // voxels per block
+constexpr int TT_DC = 32;   // detectors per stage
+constexpr int TT_NC = 4;    // chromophores held in registers
+constexpr size_t TT_STAGE_FLOATS = (size_t)TT_DC * TT_XC + (size_t)TT_DC * 32;  // phi_d chunk + Y tile
+constexpr size_t TT_SMEM = 2 * TT_STAGE_FLOATS * sizeof(float);
+
+template <int SPT>
+__global__ void __launch_bounds__(256, 2) k_apply_T_tile(const float* __restrict__ ps, const float* __restrict__ pd,
+                                                      const float* __restrict__ y, const double* __restrict__ eps,
+                                                      int lam0, int nlam, int ns, int nd, int nc, long long N,
+                                                      int lam_per_group, float* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float* buf0 = reinterpret_cast<float*>(smraw);
+  const int t = threadIdx.x;
+  const int q = t >> 2, g = t & 3;
+  const int grp = blockIdx.y;
+  const int a0 = grp * lam_per_group, a1 = min(nlam, a0 + lam_per_group);
+  const long long xb = (long long)blockIdx.x * TT_XC;
+  const long long x0 = xb + 4 * q;
+  const bool in = x0 < N;  // N % 4 == 0: a quad is inside or outside as a whole
+  constexpr int ST = 4 * SPT;  // sources per tile
+  const int nst = (ns + ST - 1) / ST, ndc = (nd + TT_DC - 1) / TT_DC;
+  const int per_a = nst * ndc;
+  const int nstage = (a1 - a0) * per_a;
+  auto load = [&](int k, float* b) {
+    const int a = a0 + k / per_a, st = (k % per_a) / ndc, dc = k % ndc;
+    const int d0 = dc * TT_DC, dn = min(TT_DC, nd - d0);
+    float* Dt = b;                                // [TT_DC][TT_XC]
+    float* Yt = b + (size_t)TT_DC * TT_XC;        // [TT_DC][4][8]: Y_a[s0 + g*SPT + j][d0 + d] at d*32 + g*8 + j
+    const float* drow = pd + ((size_t)a * nd + d0) * N + xb;
+    for (int c = t; c < dn * (TT_XC / 4); c += 256) {
+      const int d = c / (TT_XC / 4), col = (c % (TT_XC / 4)) * 4;
+      const bool ok = xb + col < N;
+      cp_async16(Dt + d * TT_XC + col, ok ? (const void*)(drow + (size_t)d * N + col) : (const void*)pd, ok ? 16u : 0u);
+    }
+    const int s0 = st * ST;
+    for (int c = t; c < TT_DC * 32; c += 256) {
+      const int d = c / 32, gg = (c % 32) / 8, j = c % 8;
+      const int s = s0 + gg * SPT + j;
+      const bool ok = j < SPT && s < ns && d < dn;
+      cp_async_small<4>(Yt + c, ok ? (const void*)(y + ((size_t)s * nd + d0 + d) * nlam + a) : (const void*)y,
+                        ok ? 4u : 0u);
+    }
+    cp_async_commit();
+  };
+  float acc[TT_NC][4], tacc[4], W[SPT][4];
+  float4 fs[SPT];
+#pragma unroll
+  for (int c = 0; c < TT_NC; ++c)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc[c][i] = 0.f;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) tacc[i] = 0.f;
+#pragma unroll
+  for (int j = 0; j < SPT; ++j) {
+    fs[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) W[j][i] = 0.f;
+  }
+  if (nstage > 0) load(0, buf0);
+  for (int k = 0; k < nstage; ++k) {
+    const int a = a0 + k / per_a, st = (k % per_a) / ndc, dc = k % ndc;
+    if (dc == 0 && in) {  // phi_s of this tile: consumed after the tile's last detector chunk
+      const int sb = st * ST + g * SPT;
+#pragma unroll
+      for (int j = 0; j < SPT; ++j)
+        fs[j] = sb + j < ns ? *reinterpret_cast<const float4*>(ps + ((size_t)a * ns + sb + j) * N + x0)
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    float* b = buf0 + (k & 1) * TT_STAGE_FLOATS;
+    if (k + 1 < nstage) {
+      load(k + 1, buf0 + ((k + 1) & 1) * TT_STAGE_FLOATS);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const float* Dt = b + 4 * q;
+    const float* Yt = b + (size_t)TT_DC * TT_XC + g * 8;
+    const int dn = min(TT_DC, nd - dc * TT_DC);
+#pragma unroll 4
+    for (int d = 0; d < dn; ++d) {
+      const float4 f = *reinterpret_cast<const float4*>(Dt + d * TT_XC);
+      const float4 ya = *reinterpret_cast<const float4*>(Yt + d * 32);
+      float yv[8] = {ya.x, ya.y, ya.z, ya.w, 0.f, 0.f, 0.f, 0.f};
+      if constexpr (SPT > 4) {
+        const float4 yb = *reinterpret_cast<const float4*>(Yt + d * 32 + 4);
+        yv[4] = yb.x; yv[5] = yb.y; yv[6] = yb.z; yv[7] = yb.w;
+      }
+#pragma unroll
+      for (int j = 0; j < SPT; ++j) {
+        W[j][0] = fmaf(yv[j], f.x, W[j][0]);
+        W[j][1] = fmaf(yv[j], f.y, W[j][1]);
+        W[j][2] = fmaf(yv[j], f.z, W[j][2]);
+        W[j][3] = fmaf(yv[j], f.w, W[j][3]);
+      }
+    }
+    __syncthreads();  // buffer (k & 1) is refilled by the load of stage k + 2
+    if (dc == ndc - 1) {
+#pragma unroll
+      for (int j = 0; j < SPT; ++j) {
+        tacc[0] = fmaf(fs[j].x, W[j][0], tacc[0]);
+        tacc[1] = fmaf(fs[j].y, W[j][1], tacc[1]);
+        tacc[2] = fmaf(fs[j].z, W[j][2], tacc[2]);
+        tacc[3] = fmaf(fs[j].w, W[j][3], tacc[3]);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) W[j][i] = 0.f;
+      }
+      if (st == nst - 1) {
+#pragma unroll
+        for (int c = 0; c < TT_NC; ++c) {
+          const float e = c < nc ? (float)eps[(size_t)(lam0 + a) * nc + c] : 0.f;
+#pragma unroll
+          for (int i = 0; i < 4; ++i) acc[c][i] = fmaf(e, tacc[i], acc[c][i]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) tacc[i] = 0.f;
+      }
+    }
+  }
+  // sum the 4 source groups of a quad (lanes 4q' .. 4q' + 3 of a warp), fixed order
+#pragma unroll
+  for (int c = 0; c < TT_NC; ++c)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      acc[c][i] += __shfl_xor_sync(0xffffffffu, acc[c][i], 1);
+      acc[c][i] += __shfl_xor_sync(0xffffffffu, acc[c][i], 2);
+    }
+  if (in && g < nc) {
+    float4 o;
+    // lane g writes chromophore g (g < nc <= 4)
+    o.x = g == 0 ? acc[0][0] : g == 1 ? acc[1][0] : g == 2 ? acc[2][0] : acc[3][0];
+    o.y = g == 0 ? acc[0][1] : g == 1 ? acc[1][1] : g == 2 ? acc[2][1] : acc[3][1];
+    o.z = g == 0 ? acc[0][2] : g == 1 ? acc[1][2] : g == 2 ? acc[2][2] : acc[3][2];
+    o.w = g == 0 ? acc[0][3] : g == 1 ? acc[1][3] : g == 2 ? acc[2][3] : acc[3][3];
+    *reinterpret_cast<float4*>(part + ((size_t)grp * nc + g) * N + x0) = o;
+  }
+}
+
 template <typename E>
 __global__ void k_apply_T_reduce(const E* __restrict__ part, int ngrp, int nc, long long N, double h3,
                                  E* __restrict__ g) {
@@ -466,11 +667,51 @@ int apply_t(hydot_ctx* ctx, const E* ps, const E* pd, int lam0, int nlam, const 
   k_apply_partial<E><<<grid, 256, smem, ctx->stream>>>(ps, pd, x, ctx->d_eps, lam0, ns, nd, nc, N, nxb, vec, part);
   ++ctx->launches;
   HYDOT_CUDA_TRY(ctx, cudaGetLastError());
-  long long M = (long long)ns * nd * nlam;
-  k_apply_reduce<E><<<(unsigned)std::min<long long>((M + 255) / 256, 4096), 256, 0, ctx->stream>>>(
-      part, nlam, ns, nd, nts, ntd, nxb, ctx->h * ctx->h * ctx->h, y);
+  HYDOT_CUDA_TRY(ctx, launch_apply_reduce<E>(part, nlam, ns, nd, nts, ntd, nxb, ctx->h * ctx->h * ctx->h, y,
+                                              ctx->stream));
   ++ctx->launches;
   timer_end(ctx, t0, HYDOT_KERNEL_APPLY, ((double)nlam * (ns + nd) + nc) * (double)N * sizeof(E));
+  HYDOT_CUDA_TRY(ctx, cudaGetLastError());
+  return HYDOT_OK;
+}
+
+// sources per thread of the register-tiled J^T y kernel: per detector a source tile costs 4 * SPT
+// FMAs plus about 6 issue slots of loads and addressing, so pick the SPT with the fewest
+// tiles x (4 * SPT + 6)
+int tile_spt(int ns) {
+  int best = 8, cost = 1 << 30;
+  for (int spt : {8, 6, 4, 2}) {
+    const int c = (ns + 4 * spt - 1) / (4 * spt) * (4 * spt + 6);
+    if (c < cost) best = spt, cost = c;
+  }
+  return best;
+}
+
+int apply_T_tile(hydot_ctx* ctx, const float* ps, const float* pd, int lam0, int nlam, const float* y, float* g) {
+  const long long N = ctx->N;
+  const int ns = ctx->n_src, nd = ctx->n_det, nc = ctx->n_chrom;
+  const long long xblocks = (N + TT_XC - 1) / TT_XC;
+  // about four waves of two blocks per SM; each wavelength group writes its own partial sums
+  int ngrp = (int)std::max<long long>(1, std::min<long long>(nlam, (4 * 2 * 152 + xblocks - 1) / xblocks));
+  const int lpg = (nlam + ngrp - 1) / ngrp;
+  ngrp = (nlam + lpg - 1) / lpg;
+  int rc = ensure_ws(ctx, sizeof(float) * (size_t)ngrp * nc * N);
+  if (rc) return rc;
+  float* part = (float*)ctx->d_apply_ws;
+  const int spt = tile_spt(ns);
+  auto kern = spt == 8 ? k_apply_T_tile<8> : spt == 6 ? k_apply_T_tile<6> : spt == 4 ? k_apply_T_tile<4>
+                                                                                      : k_apply_T_tile<2>;
+  HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TT_SMEM));
+  dim3 grid((unsigned)xblocks, ngrp);
+  cudaEvent_t t0 = timer_begin(ctx);
+  kern<<<grid, 256, TT_SMEM, ctx->stream>>>(ps, pd, y, ctx->d_eps, lam0, nlam, ns, nd, nc, N, lpg, part);
+  ++ctx->launches;
+  HYDOT_CUDA_TRY(ctx, cudaGetLastError());
+  long long tot = (long long)nc * N;
+  k_apply_T_reduce<float><<<(unsigned)std::min<long long>((tot + 255) / 256, 8192), 256, 0, ctx->stream>>>(
+      part, ngrp, nc, N, ctx->h * ctx->h * ctx->h, g);
+  ++ctx->launches;
+  timer_end(ctx, t0, HYDOT_KERNEL_APPLY_T, ((double)nlam * (ns + nd) + 2.0 * nc) * (double)N * sizeof(float));
   HYDOT_CUDA_TRY(ctx, cudaGetLastError());
   return HYDOT_OK;
 }
@@ -479,6 +720,10 @@ template <typename E>
 int apply_T_t(hydot_ctx* ctx, const E* ps, const E* pd, int lam0, int nlam, const E* y, E* g) {
   const long long N = ctx->N;
   const int ns = ctx->n_src, nd = ctx->n_det, nc = ctx->n_chrom;
+  if constexpr (sizeof(E) == 4) {
+    if (nc <= TT_NC && N % 4 == 0 && (uintptr_t)ps % 16 == 0 && (uintptr_t)pd % 16 == 0 && !getenv("HYDOT_NO_TILE_T"))
+      return apply_T_tile(ctx, ps, pd, lam0, nlam, y, g);
+  }
   // enough blocks to fill the GPU: split the wavelengths into groups with their own partials
   const long long xblocks = (N + 255) / 256;
   int ngrp = (int)std::max<long long>(1, std::min<long long>(nlam, (4 * 152 * 8 + xblocks - 1) / xblocks));
@@ -623,10 +868,7 @@ extern "C" int hydot_born_apply_noalloc(long long N, int n_src, int n_det, int n
     // every partial slot is written before it is read, so nothing in the array needs clearing
     k_apply_partial<float><<<grid, 256, smem, s>>>(phi_src, phi_det, x, d_eps, 0, n_src, n_det, n_chrom, N,
                                                    (int)nxb, apply_vec_ok(phi_src, phi_det, x, N, 4), part);
-    const long long M = (long long)n_src * n_det * nlam;
-    k_apply_reduce<float><<<(unsigned)std::min<long long>((M + 255) / 256, 4096), 256, 0, s>>>(
-        part, nlam, n_src, n_det, nts, ntd, (int)nxb, h_mm * h_mm * h_mm, y);
-    e = cudaGetLastError();
+    e = launch_apply_reduce<float>(part, nlam, n_src, n_det, nts, ntd, (int)nxb, h_mm * h_mm * h_mm, y, s);
   }
   if (e != cudaSuccess) {
     set_context_free_error(std::string("launch: ") + cudaGetErrorString(e));

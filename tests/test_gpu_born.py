@@ -174,12 +174,14 @@ def test_misfit_gradient_vs_central_differences(lib):
     assert np.abs(g - fd).max() <= 1e-4 * scale
 
 
-@pytest.mark.parametrize("ns,nd", [(32, 32), (64, 32), (40, 100), (3, 5)])
-def test_apply_and_apply_T_optode_blocks(lib, ns, nd):
+@pytest.mark.parametrize("ns,nd,grid", [(32, 32, (16, 16, 12)), (64, 32, (16, 16, 12)), (40, 100, (16, 16, 12)),
+                                        (3, 5, (16, 16, 12)), (24, 24, (20, 14, 9)), (16, 7, (20, 14, 9))])
+def test_apply_and_apply_T_optode_blocks(lib, ns, nd, grid):
     """J x and J^T y in FP32 against the FP64 oracle for optode counts that fill whole 32-wide
     blocks (the guard-free path) and ones that leave partial blocks (40 x 100: several detector
-    blocks, the last one partial)."""
-    p = workloads.make_problem(workloads.Grid(16, 16, 12, 2.0), ns, nd, 3, seed=51, geometry="transmission", margin=0)
+    blocks, the last one partial); the 20 x 14 x 9 grid (N = 2520) ends in a partial 256-voxel
+    chunk of the register-tiled J^T y kernel, with 24 sources (tiles of 24) and 16 (tiles of 16)."""
+    p = workloads.make_problem(workloads.Grid(*grid, 2.0), ns, nd, 3, seed=51, geometry="transmission", margin=0)
     rs, rd = osolve.fields_separable(p)
     y = workloads.gaussian(52, p.M)
     xv = workloads.gaussian(53, p.n_chrom * p.grid.N)
@@ -193,6 +195,28 @@ def test_apply_and_apply_T_optode_blocks(lib, ns, nd):
         yy = ctx.born_apply(ps, pd, 0, p.n_lambda, torch.tensor(xv, dtype=torch.float32, device="cuda"))
     assert np.abs(g.double().cpu().numpy() - g_ref).max() <= 2e-5 * np.abs(g_ref).max()
     assert np.abs(yy.double().cpu().numpy() - y_ref).max() <= 2e-5 * np.abs(y_ref).max()
+
+
+def test_apply_T_tiled_and_per_voxel_kernels_agree(lib, monkeypatch):
+    """The register-tiled J^T y kernel and the per-voxel one (taken when HYDOT_NO_TILE_T is set, and
+    for FP64, more than 4 chromophores or N not a multiple of 4) give the same gradient to FP32
+    rounding, on a case with two source tiles, two detector chunks and a partial voxel chunk."""
+    p = workloads.make_problem(workloads.Grid(20, 14, 9, 2.0), 40, 36, 5, seed=54, geometry="transmission", margin=0)
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    N = p.grid.N
+    ps = torch.rand(p.n_lambda, p.n_src, N, device="cuda", generator=gen)
+    pd = torch.rand(p.n_lambda, p.n_det, N, device="cuda", generator=gen)
+    y = torch.randn(p.M, device="cuda", generator=gen)
+    out = []
+    with lib.Context.from_problem(p, precision="mixed", tol=1e-8, tol_cw=0.0) as ctx:
+        for flag in (None, "1"):
+            if flag:
+                monkeypatch.setenv("HYDOT_NO_TILE_T", flag)
+            g = torch.zeros(p.n_chrom * N, device="cuda")
+            ctx.born_apply_T(ps, pd, 0, p.n_lambda, y, g)
+            out.append(g.double().cpu())
+    scale = out[1].abs().max()
+    assert (out[0] - out[1]).abs().max() <= 1e-5 * scale
 
 
 def _perturbed_fields_oracle(p, dc):
