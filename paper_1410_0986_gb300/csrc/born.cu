@@ -97,11 +97,12 @@ __global__ void __launch_bounds__(256) k_born_rows_scalar(const E* __restrict__ 
 }
 
 // ---------------------------------------------------------------- J x
-// Block = (wavelength a, chunk of AP_STAGES x AP_XC voxels, 32x32 tile of (s, d)). Each stage of
+// Block = (wavelength a, chunk of AP_STAGES x AP_XC voxels, TILE x TILE tile of (s, d), TILE = 4U
+// with U in {8, 6, 4, 2} chosen per problem so that the tiles pad n_src and n_det little). Each stage of
 // AP_XC voxels (phi_s and phi_d rows of the tile, and the chromophore maps x_c) is copied into
 // shared memory with cp.async while the previous stage is contracted (two buffers). 256 threads =
 // 16 voxel groups x 16 (s, d) sub-tiles; a thread accumulates s-rows si0 + 4u and d-rows
-// di0 + 4v (u, v < 8), which with a row stride of AP_XC + 16 bytes keeps the tile reads of a warp
+// di0 + 4v (u, v < U), which with a row stride of AP_XC + 16 bytes keeps the tile reads of a warp
 // on distinct banks. mu_a(x) = sum_c eps_c(lambda_a) x_c is formed by each thread for its voxels.
 // Block partials go to a workspace and a second kernel sums them in a fixed order.
 constexpr int AP_XC = 128;   // voxels per stage
@@ -109,12 +110,14 @@ constexpr int AP_STAGES = 8; // stages per block
 
 template <typename E>
 __host__ __device__ constexpr int ap_ld() { return AP_XC + 16 / (int)sizeof(E); }  // padded row stride (elements)
-// elements of one stage buffer: S [32][LD], D [32][LD], X [nc][AP_XC]
-template <typename E>
-__host__ __device__ constexpr size_t apply_buf_elems(int nc) { return (size_t)64 * ap_ld<E>() + (size_t)nc * AP_XC; }
-template <typename E>
+// elements of one stage buffer: S [TILE][LD], D [TILE][LD], X [nc][AP_XC]
+template <typename E, int U>
+__host__ __device__ constexpr size_t apply_buf_elems(int nc) {
+  return (size_t)8 * U * ap_ld<E>() + (size_t)nc * AP_XC;
+}
+template <typename E, int U>
 size_t apply_smem_bytes(int nc) {
-  return std::max(sizeof(E) * 2 * apply_buf_elems<E>(nc), sizeof(E) * 8 * 1024);  // the reduction reuses it
+  return std::max(sizeof(E) * 2 * apply_buf_elems<E, U>(nc), sizeof(E) * 8 * 1024);  // the reduction reuses it
 }
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src, uint32_t src_bytes) {
@@ -132,7 +135,7 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N_>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N_) : "memory"); }
 
-template <typename E>
+template <typename E, int U>
 __global__ void __launch_bounds__(256) k_apply_partial(const E* __restrict__ ps, const E* __restrict__ pd,
                                                        const E* __restrict__ xin, const double* __restrict__ eps,
                                                        int lam0, int ns, int nd, int nc, long long N, int nxb, int vec,
@@ -140,13 +143,14 @@ __global__ void __launch_bounds__(256) k_apply_partial(const E* __restrict__ ps,
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int LD = ap_ld<E>();
   constexpr int VE = 16 / (int)sizeof(E);  // elements per 16-byte copy
-  E* buf0 = reinterpret_cast<E*>(smraw);   // per buffer: S [32][LD], D [32][LD], X [nc][AP_XC]
+  constexpr int TILE = 4 * U;
+  E* buf0 = reinterpret_cast<E*>(smraw);   // per buffer: S [TILE][LD], D [TILE][LD], X [nc][AP_XC]
   E* red = buf0;                           // [8][1024], reused after the voxel loop
   const int xb = blockIdx.x;
   const int a = blockIdx.y;
   const int tsd = blockIdx.z;  // (s-tile, d-tile)
-  const int nts = (ns + 31) / 32;
-  const int s0 = (tsd % nts) * 32, d0 = (tsd / nts) * 32;
+  const int nts = (ns + TILE - 1) / TILE;
+  const int s0 = (tsd % nts) * TILE, d0 = (tsd / nts) * TILE;
   const int t = threadIdx.x;
   const int grp = t / 16, sub = t % 16;
   const int si0 = sub / 4, di0 = sub % 4;
@@ -158,51 +162,50 @@ __global__ void __launch_bounds__(256) k_apply_partial(const E* __restrict__ ps,
   auto load = [&](int st, E* b) {
     const long long xbase = ((long long)xb * AP_STAGES + st) * AP_XC;
     E* S = b;
-    E* D = b + 32 * LD;
-    E* X = b + 64 * LD;
+    E* D = b + TILE * LD;
+    E* X = b + 2 * TILE * LD;
     if (vec) {
+      // thread t copies 16-byte chunk t % CH of rows t / CH + RPI * i of S, D and X
       constexpr int CH = AP_XC / VE;  // 16-byte chunks per row
-      for (int q = t; q < (64 + nc) * CH; q += 256) {
-        const int row = q / CH, col = (q % CH) * VE;
-        const long long x = xbase + col;
-        const E* src;
-        E* dst;
-        bool ok;
-        if (row < 32) {
-          ok = s0 + row < ns;
-          src = srow + (size_t)row * N + x;
-          dst = S + row * LD + col;
-        } else if (row < 64) {
-          ok = d0 + row - 32 < nd;
-          src = drow + (size_t)(row - 32) * N + x;
-          dst = D + (row - 32) * LD + col;
-        } else {
-          ok = true;
-          src = xin + (size_t)(row - 64) * N + x;
-          dst = X + (row - 64) * AP_XC + col;
-        }
-        ok = ok && x < N;  // N is a multiple of VE here: a chunk is inside or outside as a whole
-        cp_async16(dst, ok ? src : xin, ok ? 16u : 0u);
+      constexpr int RPI = 256 / CH;   // rows per pass of the block
+      const int r0 = t / CH, col = (t % CH) * VE;
+      const long long x = xbase + col;
+      const bool xok = x < N;  // N is a multiple of VE here: a chunk is inside or outside as a whole
+      const E* sp = srow + (size_t)r0 * N + x;
+      const E* dp = drow + (size_t)r0 * N + x;
+#pragma unroll
+      for (int i = 0; i < TILE / RPI; ++i) {
+        const bool ok = xok && s0 + r0 + RPI * i < ns;
+        cp_async16(S + (r0 + RPI * i) * LD + col, ok ? (const void*)(sp + (size_t)RPI * i * N) : (const void*)xin,
+                   ok ? 16u : 0u);
       }
+#pragma unroll
+      for (int i = 0; i < TILE / RPI; ++i) {
+        const bool ok = xok && d0 + r0 + RPI * i < nd;
+        cp_async16(D + (r0 + RPI * i) * LD + col, ok ? (const void*)(dp + (size_t)RPI * i * N) : (const void*)xin,
+                   ok ? 16u : 0u);
+      }
+      for (int r = r0; r < nc; r += RPI)
+        cp_async16(X + r * AP_XC + col, xok ? (const void*)(xin + (size_t)r * N + x) : (const void*)xin, xok ? 16u : 0u);
     } else {
-      for (int q = t; q < (64 + nc) * AP_XC; q += 256) {
+      for (int q = t; q < (2 * TILE + nc) * AP_XC; q += 256) {
         const int row = q / AP_XC, col = q % AP_XC;
         const long long x = xbase + col;
         const E* src;
         E* dst;
         bool ok;
-        if (row < 32) {
+        if (row < TILE) {
           ok = s0 + row < ns;
           src = srow + (size_t)row * N + x;
           dst = S + row * LD + col;
-        } else if (row < 64) {
-          ok = d0 + row - 32 < nd;
-          src = drow + (size_t)(row - 32) * N + x;
-          dst = D + (row - 32) * LD + col;
+        } else if (row < 2 * TILE) {
+          ok = d0 + row - TILE < nd;
+          src = drow + (size_t)(row - TILE) * N + x;
+          dst = D + (row - TILE) * LD + col;
         } else {
           ok = true;
-          src = xin + (size_t)(row - 64) * N + x;
-          dst = X + (row - 64) * AP_XC + col;
+          src = xin + (size_t)(row - 2 * TILE) * N + x;
+          dst = X + (row - 2 * TILE) * AP_XC + col;
         }
         ok = ok && x < N;
         cp_async_small<(int)sizeof(E)>(dst, ok ? src : xin, ok ? (uint32_t)sizeof(E) : 0u);
@@ -210,40 +213,44 @@ __global__ void __launch_bounds__(256) k_apply_partial(const E* __restrict__ ps,
     }
     cp_async_commit();
   };
-  E acc[8][8];
+  E acc[U][U];
 #pragma unroll
-  for (int u = 0; u < 8; ++u)
+  for (int u = 0; u < U; ++u)
 #pragma unroll
-    for (int v = 0; v < 8; ++v) acc[u][v] = 0;
+    for (int v = 0; v < U; ++v) acc[u][v] = 0;
   const long long nstage = min((long long)AP_STAGES, (N - (long long)xb * AP_STAGES * AP_XC + AP_XC - 1) / AP_XC);
   load(0, buf0);
   for (int st = 0; st < nstage; ++st) {
-    E* b = buf0 + (st & 1) * apply_buf_elems<E>(nc);
+    E* b = buf0 + (st & 1) * apply_buf_elems<E, U>(nc);
     if (st + 1 < nstage) {
-      load(st + 1, buf0 + ((st + 1) & 1) * apply_buf_elems<E>(nc));
+      load(st + 1, buf0 + ((st + 1) & 1) * apply_buf_elems<E, U>(nc));
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
     }
     __syncthreads();
     const E* S = b;
-    const E* D = b + 32 * LD;
-    const E* X = b + 64 * LD;
-    if (t < AP_XC) {
-      E m = 0;
-      for (int c = 0; c < nc; ++c) m += w[c] * X[c * AP_XC + t];
-      mu[t] = m;
-    }
-    __syncthreads();
+    const E* D = b + TILE * LD;
+    const E* X = b + 2 * TILE * LD;
     if constexpr (sizeof(E) == 4) {
       // scale the source rows by mu once, then contract 4-voxel quads with 16-byte reads:
-      // per quad 8 + 8 vector reads feed 256 FMAs
-      for (int q = t; q < 32 * AP_XC / 4; q += 256) {
-        float4* sp = reinterpret_cast<float4*>(const_cast<E*>(S) + (q / (AP_XC / 4)) * LD) + q % (AP_XC / 4);
-        const float4 m4 = reinterpret_cast<const float4*>(mu)[q % (AP_XC / 4)];
-        float4 v4 = *sp;
-        v4.x *= m4.x; v4.y *= m4.y; v4.z *= m4.z; v4.w *= m4.w;
-        *sp = v4;
+      // per quad 8 + 8 vector reads feed 256 FMAs. Thread t scales voxel quad t % 32 of rows
+      // t / 32 + 8i and forms mu for those 4 voxels itself.
+      {
+        const int cq = 4 * (t & 31), r0 = t >> 5;
+        float4 m4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int c = 0; c < nc; ++c) {
+          const float4 x4 = *reinterpret_cast<const float4*>(X + c * AP_XC + cq);
+          m4.x = fmaf(w[c], x4.x, m4.x); m4.y = fmaf(w[c], x4.y, m4.y);
+          m4.z = fmaf(w[c], x4.z, m4.z); m4.w = fmaf(w[c], x4.w, m4.w);
+        }
+#pragma unroll
+        for (int i = 0; i < TILE / 8; ++i) {
+          float4* sp = reinterpret_cast<float4*>(const_cast<E*>(S) + (r0 + 8 * i) * LD + cq);
+          float4 v4 = *sp;
+          v4.x *= m4.x; v4.y *= m4.y; v4.z *= m4.z; v4.w *= m4.w;
+          *sp = v4;
+        }
       }
       __syncthreads();
       // quads of warp w = grp / 2: (w / 2) * 8 + (w % 2) * 2 + {0, 1, 4, 5}, the odd group 4 quads
@@ -253,29 +260,39 @@ __global__ void __launch_bounds__(256) k_apply_partial(const E* __restrict__ ps,
 #pragma unroll 1
       for (int qd = 0; qd < 2; ++qd) {
         const int x0 = (qbase + qd) * 4;
-        float4 dv[8];
+        float4 dv[U];
 #pragma unroll
-        for (int v = 0; v < 8; ++v) dv[v] = *reinterpret_cast<const float4*>(D + (di0 + 4 * v) * LD + x0);
+        for (int v = 0; v < U; ++v) dv[v] = *reinterpret_cast<const float4*>(D + (di0 + 4 * v) * LD + x0);
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < U; ++u) {
           const float4 sv = *reinterpret_cast<const float4*>(S + (si0 + 4 * u) * LD + x0);
 #pragma unroll
-          for (int v = 0; v < 8; ++v)
-            acc[u][v] += sv.x * dv[v].x + sv.y * dv[v].y + sv.z * dv[v].z + sv.w * dv[v].w;
+          for (int v = 0; v < U; ++v) {
+            acc[u][v] = fmaf(sv.x, dv[v].x, acc[u][v]);
+            acc[u][v] = fmaf(sv.y, dv[v].y, acc[u][v]);
+            acc[u][v] = fmaf(sv.z, dv[v].z, acc[u][v]);
+            acc[u][v] = fmaf(sv.w, dv[v].w, acc[u][v]);
+          }
         }
       }
     } else {
+      if (t < AP_XC) {
+        E m = 0;
+        for (int c = 0; c < nc; ++c) m += w[c] * X[c * AP_XC + t];
+        mu[t] = m;
+      }
+      __syncthreads();
       for (int q = grp; q < AP_XC; q += 16) {
         const E m = mu[q];
-        E sv[8], dv[8];
+        E sv[U], dv[U];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) sv[u] = S[(si0 + 4 * u) * LD + q] * m;
+        for (int u = 0; u < U; ++u) sv[u] = S[(si0 + 4 * u) * LD + q] * m;
 #pragma unroll
-        for (int v = 0; v < 8; ++v) dv[v] = D[(di0 + 4 * v) * LD + q];
+        for (int v = 0; v < U; ++v) dv[v] = D[(di0 + 4 * v) * LD + q];
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
+        for (int u = 0; u < U; ++u)
 #pragma unroll
-          for (int v = 0; v < 8; ++v) acc[u][v] += sv[u] * dv[v];
+          for (int v = 0; v < U; ++v) acc[u][v] += sv[u] * dv[v];
       }
     }
     __syncthreads();  // buffer (st & 1) is refilled by the load of stage st + 2
@@ -283,30 +300,30 @@ __global__ void __launch_bounds__(256) k_apply_partial(const E* __restrict__ ps,
   // tree reduction over the 16 voxel groups (fixed order -> deterministic)
   for (int half = 8; half >= 1; half >>= 1) {
     __syncthreads();
-    // element (u, v) of sub-tile `sub` at (u*8 + v)*16 + sub: the 16 sub-tiles of a voxel group
+    // element (u, v) of sub-tile `sub` at (u*U + v)*16 + sub: the 16 sub-tiles of a voxel group
     // hit 16 consecutive words
     if (grp >= half && grp < 2 * half) {
       E* dst = red + (size_t)(grp - half) * 1024 + sub;
 #pragma unroll
-      for (int u = 0; u < 8; ++u)
+      for (int u = 0; u < U; ++u)
 #pragma unroll
-        for (int v = 0; v < 8; ++v) dst[(u * 8 + v) * 16] = acc[u][v];
+        for (int v = 0; v < U; ++v) dst[(u * U + v) * 16] = acc[u][v];
     }
     __syncthreads();
     if (grp < half) {
       const E* src = red + (size_t)grp * 1024 + sub;
 #pragma unroll
-      for (int u = 0; u < 8; ++u)
+      for (int u = 0; u < U; ++u)
 #pragma unroll
-        for (int v = 0; v < 8; ++v) acc[u][v] += src[(u * 8 + v) * 16];
+        for (int v = 0; v < U; ++v) acc[u][v] += src[(u * U + v) * 16];
     }
   }
   if (grp == 0) {
     E* out = part + (((size_t)a * gridDim.z + tsd) * nxb + xb) * 1024;
 #pragma unroll
-    for (int u = 0; u < 8; ++u)
+    for (int u = 0; u < U; ++u)
 #pragma unroll
-      for (int v = 0; v < 8; ++v) out[(si0 + 4 * u) * 32 + (di0 + 4 * v)] = acc[u][v];
+      for (int v = 0; v < U; ++v) out[(si0 + 4 * u) * 32 + (di0 + 4 * v)] = acc[u][v];
   }
 }
 
@@ -316,18 +333,19 @@ inline int apply_vec_ok(const void* a, const void* b, const void* c, long long N
   return ((N * (long long)es) % 16 == 0 && al(a) && al(b) && al(c)) ? 1 : 0;
 }
 
-// Block = 32 consecutive entries of one (wavelength, optode tile) partial block; its 8 warps take
-// every 8th voxel block (reads of 128 contiguous bytes per warp) and the 8 FP64 sums are added in
-// warp order, so the result does not depend on scheduling.
+// Block = one source row (32 slots) of one (wavelength, optode tile) partial block; its 8 warps
+// take every 8th voxel block (reads of 128 contiguous bytes per warp) and the 8 FP64 sums are added
+// in warp order, so the result does not depend on scheduling. A partial block holds the tile's
+// entry (s, d) at slot s * 32 + d; slots with d >= tile are never written, and their sums are dropped.
 template <typename E>
 __global__ void __launch_bounds__(256) k_apply_reduce(const E* __restrict__ part, int nlam, int ns, int nd, int nts,
-                                                      int ntd, int nxb, double h3, E* __restrict__ y) {
+                                                      int ntd, int tile_w, int nxb, double h3, E* __restrict__ y) {
   __shared__ double red[8][32];
   const int ntile = nts * ntd;
-  const int e0 = (int)(blockIdx.x % 32) * 32;
-  const long long at = blockIdx.x / 32;  // a * ntile + tile
+  const int sl = (int)(blockIdx.x % tile_w);
+  const long long at = blockIdx.x / tile_w;  // a * ntile + tile
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const E* p = part + (size_t)at * nxb * 1024 + e0 + lane;
+  const E* p = part + (size_t)at * nxb * 1024 + sl * 32 + lane;
   double sum = 0.0;
 #pragma unroll 4
   for (int xb = w; xb < nxb; xb += 8) sum += (double)p[(size_t)xb * 1024];
@@ -337,19 +355,52 @@ __global__ void __launch_bounds__(256) k_apply_reduce(const E* __restrict__ part
     double tot = 0.0;
 #pragma unroll
     for (int i = 0; i < 8; ++i) tot += red[i][lane];
-    const int e = e0 + lane;
     const int a = (int)(at / ntile), tile = (int)(at % ntile);
-    const int s = (tile % nts) * 32 + e / 32, d = (tile / nts) * 32 + e % 32;
-    if (s < ns && d < nd) y[((size_t)s * nd + d) * nlam + a] = (E)(-h3 * tot);
+    const int s = (tile % nts) * tile_w + sl, d = (tile / nts) * tile_w + lane;
+    if (lane < tile_w && s < ns && d < nd) y[((size_t)s * nd + d) * nlam + a] = (E)(-h3 * tot);
   }
 }
 
 template <typename E>
-cudaError_t launch_apply_reduce(const E* part, int nlam, int ns, int nd, int nts, int ntd, int nxb, double h3, E* y,
-                                cudaStream_t st) {
-  const unsigned blocks = (unsigned)((size_t)nlam * nts * ntd * 32);
-  k_apply_reduce<E><<<blocks, 256, 0, st>>>(part, nlam, ns, nd, nts, ntd, nxb, h3, y);
+cudaError_t launch_apply_reduce(const E* part, int nlam, int ns, int nd, int nts, int ntd, int tile_w, int nxb,
+                                double h3, E* y, cudaStream_t st) {
+  const unsigned blocks = (unsigned)((size_t)nlam * nts * ntd * tile_w);
+  k_apply_reduce<E><<<blocks, 256, 0, st>>>(part, nlam, ns, nd, nts, ntd, tile_w, nxb, h3, y);
   return cudaGetLastError();
+}
+
+// J x tile width 4U: per voxel quad a tile costs 4 U^2 FMAs, 2U shared reads and about 8 issue
+// slots of staging, so pick the U with the fewest tiles x (4 U^2 + 2U + 8)
+int apply_u(int ns, int nd) {
+  int best = 8;
+  long long cost = -1;
+  for (int u : {8, 6, 4, 2}) {
+    const long long c = (long long)((ns + 4 * u - 1) / (4 * u)) * ((nd + 4 * u - 1) / (4 * u)) * (4 * u * u + 2 * u + 8);
+    if (cost < 0 || c < cost) best = u, cost = c;
+  }
+  return best;
+}
+
+template <typename E, int U>
+cudaError_t launch_apply_partial(dim3 grid, cudaStream_t st, const E* ps, const E* pd, const E* x, const double* eps,
+                                 int lam0, int ns, int nd, int nc, long long N, int nxb, int vec, E* part) {
+  const size_t smem = apply_smem_bytes<E, U>(nc);
+  cudaError_t e = cudaFuncSetAttribute(k_apply_partial<E, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_apply_partial<E, U><<<grid, 256, smem, st>>>(ps, pd, x, eps, lam0, ns, nd, nc, N, nxb, vec, part);
+  return cudaGetLastError();
+}
+
+template <typename E>
+cudaError_t launch_apply_partial_u(int u, dim3 grid, cudaStream_t st, const E* ps, const E* pd, const E* x,
+                                   const double* eps, int lam0, int ns, int nd, int nc, long long N, int nxb, int vec,
+                                   E* part) {
+  switch (u) {
+    case 6: return launch_apply_partial<E, 6>(grid, st, ps, pd, x, eps, lam0, ns, nd, nc, N, nxb, vec, part);
+    case 4: return launch_apply_partial<E, 4>(grid, st, ps, pd, x, eps, lam0, ns, nd, nc, N, nxb, vec, part);
+    case 2: return launch_apply_partial<E, 2>(grid, st, ps, pd, x, eps, lam0, ns, nd, nc, N, nxb, vec, part);
+    default: return launch_apply_partial<E, 8>(grid, st, ps, pd, x, eps, lam0, ns, nd, nc, N, nxb, vec, part);
+  }
 }
 
 // ---------------------------------------------------------------- J^T y
@@ -460,6 +511,7 @@ __global__ void __launch_bounds__(256, 2) k_apply_T_tile(const float* __restrict
                                                       int lam_per_group, float* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char smraw[];
   float* buf0 = reinterpret_cast<float*>(smraw);
+  float* epsf = buf0 + 2 * TT_STAGE_FLOATS;  // [lam_per_group][TT_NC] eps_c(lambda) of the group, FP32
   const int t = threadIdx.x;
   const int q = t >> 2, g = t & 3;
   const int grp = blockIdx.y;
@@ -469,28 +521,43 @@ __global__ void __launch_bounds__(256, 2) k_apply_T_tile(const float* __restrict
   const bool in = x0 < N;  // N % 4 == 0: a quad is inside or outside as a whole
   constexpr int ST = 4 * SPT;  // sources per tile
   const int nst = (ns + ST - 1) / ST, ndc = (nd + TT_DC - 1) / TT_DC;
-  const int per_a = nst * ndc;
-  const int nstage = (a1 - a0) * per_a;
-  auto load = [&](int k, float* b) {
-    const int a = a0 + k / per_a, st = (k % per_a) / ndc, dc = k % ndc;
-    const int d0 = dc * TT_DC, dn = min(TT_DC, nd - d0);
-    float* Dt = b;                                // [TT_DC][TT_XC]
-    float* Yt = b + (size_t)TT_DC * TT_XC;        // [TT_DC][4][8]: Y_a[s0 + g*SPT + j][d0 + d] at d*32 + g*8 + j
-    const float* drow = pd + ((size_t)a * nd + d0) * N + xb;
-    for (int c = t; c < dn * (TT_XC / 4); c += 256) {
-      const int d = c / (TT_XC / 4), col = (c % (TT_XC / 4)) * 4;
-      const bool ok = xb + col < N;
-      cp_async16(Dt + d * TT_XC + col, ok ? (const void*)(drow + (size_t)d * N + col) : (const void*)pd, ok ? 16u : 0u);
+  const int nstage = (a1 - a0) * nst * ndc;
+  for (int e = t; e < (a1 - a0) * TT_NC; e += 256) {
+    const int c = e % TT_NC;
+    epsf[e] = c < nc ? (float)eps[(size_t)(lam0 + a0 + e / TT_NC) * nc + c] : 0.f;
+  }
+  // staging roles, fixed for the whole block: detector rows (t >> 6) + 4i at voxel column 4 (t & 63)
+  // (i < 8); Y entries of detectors (t >> 5) + 8i (i < 4), source slot j = t & 7 of group (t & 31) >> 3
+  const int dr = t >> 6, dcol = (t & 63) * 4;
+  const bool dok = xb + dcol < N;
+  const int yr = t >> 5, yg = (t & 31) >> 3, yj = t & 7;
+  const size_t N4 = (size_t)4 * N;
+  // stage k = ((a - a0) * nst + st) * ndc + dc, kept as counters rather than divisions
+  int la = a0, lst = 0, ldc = 0;  // stage to load next
+  auto load = [&](float* b) {
+    const int d0 = ldc * TT_DC, dn = min(TT_DC, nd - d0);
+    float* Dt = b + dr * TT_XC + dcol;
+    const float* src = pd + ((size_t)la * nd + d0 + dr) * N + xb + dcol;
+#pragma unroll
+    for (int i = 0; i < TT_DC / 4; ++i) {
+      if (dr + 4 * i < dn)
+        cp_async16(Dt + i * 4 * TT_XC, dok ? (const void*)(src + i * N4) : (const void*)pd, dok ? 16u : 0u);
     }
-    const int s0 = st * ST;
-    for (int c = t; c < TT_DC * 32; c += 256) {
-      const int d = c / 32, gg = (c % 32) / 8, j = c % 8;
-      const int s = s0 + gg * SPT + j;
-      const bool ok = j < SPT && s < ns && d < dn;
-      cp_async_small<4>(Yt + c, ok ? (const void*)(y + ((size_t)s * nd + d0 + d) * nlam + a) : (const void*)y,
+    const int s = lst * ST + yg * SPT + yj;
+    const bool sok = yj < SPT && s < ns;
+    float* Yt = b + (size_t)TT_DC * TT_XC + yr * 32 + yg * 8 + yj;  // Y_a[s][d0 + d] at d*32 + group*8 + j
+    const float* ysrc = y + ((size_t)(sok ? s : 0) * nd + d0 + yr) * nlam + la;
+#pragma unroll
+    for (int i = 0; i < TT_DC / 8; ++i) {
+      const bool ok = sok && yr + 8 * i < dn;
+      cp_async_small<4>(Yt + i * 8 * 32, ok ? (const void*)(ysrc + (size_t)i * 8 * nlam) : (const void*)y,
                         ok ? 4u : 0u);
     }
     cp_async_commit();
+    if (++ldc == ndc) {
+      ldc = 0;
+      if (++lst == nst) lst = 0, ++la;
+    }
   };
   float acc[TT_NC][4], tacc[4], W[SPT][4];
   float4 fs[SPT];
@@ -506,19 +573,19 @@ __global__ void __launch_bounds__(256, 2) k_apply_T_tile(const float* __restrict
 #pragma unroll
     for (int i = 0; i < 4; ++i) W[j][i] = 0.f;
   }
-  if (nstage > 0) load(0, buf0);
+  if (nstage > 0) load(buf0);
+  int a = a0, st = 0, dc = 0;  // stage being contracted
   for (int k = 0; k < nstage; ++k) {
-    const int a = a0 + k / per_a, st = (k % per_a) / ndc, dc = k % ndc;
     if (dc == 0 && in) {  // phi_s of this tile: consumed after the tile's last detector chunk
       const int sb = st * ST + g * SPT;
+      const float* sp = ps + ((size_t)a * ns + sb) * N + x0;
 #pragma unroll
       for (int j = 0; j < SPT; ++j)
-        fs[j] = sb + j < ns ? *reinterpret_cast<const float4*>(ps + ((size_t)a * ns + sb + j) * N + x0)
-                            : make_float4(0.f, 0.f, 0.f, 0.f);
+        fs[j] = sb + j < ns ? *reinterpret_cast<const float4*>(sp + (size_t)j * N) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     float* b = buf0 + (k & 1) * TT_STAGE_FLOATS;
     if (k + 1 < nstage) {
-      load(k + 1, buf0 + ((k + 1) & 1) * TT_STAGE_FLOATS);
+      load(buf0 + ((k + 1) & 1) * TT_STAGE_FLOATS);
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
@@ -556,15 +623,19 @@ __global__ void __launch_bounds__(256, 2) k_apply_T_tile(const float* __restrict
         for (int i = 0; i < 4; ++i) W[j][i] = 0.f;
       }
       if (st == nst - 1) {
+        const float4 e4 = *reinterpret_cast<const float4*>(epsf + (a - a0) * TT_NC);
+        const float ev[TT_NC] = {e4.x, e4.y, e4.z, e4.w};
 #pragma unroll
-        for (int c = 0; c < TT_NC; ++c) {
-          const float e = c < nc ? (float)eps[(size_t)(lam0 + a) * nc + c] : 0.f;
+        for (int c = 0; c < TT_NC; ++c)
 #pragma unroll
-          for (int i = 0; i < 4; ++i) acc[c][i] = fmaf(e, tacc[i], acc[c][i]);
-        }
+          for (int i = 0; i < 4; ++i) acc[c][i] = fmaf(ev[c], tacc[i], acc[c][i]);
 #pragma unroll
         for (int i = 0; i < 4; ++i) tacc[i] = 0.f;
       }
+    }
+    if (++dc == ndc) {
+      dc = 0;
+      if (++st == nst) st = 0, ++a;
     }
   }
   // sum the 4 source groups of a quad (lanes 4q' .. 4q' + 3 of a warp), fixed order
@@ -585,6 +656,7 @@ __global__ void __launch_bounds__(256, 2) k_apply_T_tile(const float* __restrict
     *reinterpret_cast<float4*>(part + ((size_t)grp * nc + g) * N + x0) = o;
   }
 }
+
 
 template <typename E>
 __global__ void k_apply_T_reduce(const E* __restrict__ part, int ngrp, int nc, long long N, double h3,
@@ -652,7 +724,8 @@ template <typename E>
 int apply_t(hydot_ctx* ctx, const E* ps, const E* pd, int lam0, int nlam, const E* x, E* y) {
   const long long N = ctx->N;
   const int ns = ctx->n_src, nd = ctx->n_det, nc = ctx->n_chrom;
-  const int nts = (ns + 31) / 32, ntd = (nd + 31) / 32;
+  const int u = apply_u(ns, nd), tw = 4 * u;
+  const int nts = (ns + tw - 1) / tw, ntd = (nd + tw - 1) / tw;
   const long long per_blk = (long long)AP_XC * AP_STAGES;
   const int nxb = (int)((N + per_blk - 1) / per_blk);
   size_t bytes = sizeof(E) * (size_t)nlam * nts * ntd * nxb * 1024;
@@ -660,14 +733,12 @@ int apply_t(hydot_ctx* ctx, const E* ps, const E* pd, int lam0, int nlam, const 
   if (rc) return rc;
   E* part = (E*)ctx->d_apply_ws;
   dim3 grid(nxb, nlam, nts * ntd);
-  const size_t smem = apply_smem_bytes<E>(nc);
-  HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(k_apply_partial<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int vec = apply_vec_ok(ps, pd, x, N, sizeof(E));
   cudaEvent_t t0 = timer_begin(ctx);
-  k_apply_partial<E><<<grid, 256, smem, ctx->stream>>>(ps, pd, x, ctx->d_eps, lam0, ns, nd, nc, N, nxb, vec, part);
+  HYDOT_CUDA_TRY(ctx, launch_apply_partial_u<E>(u, grid, ctx->stream, ps, pd, x, ctx->d_eps, lam0, ns, nd, nc, N,
+                                                nxb, vec, part));
   ++ctx->launches;
-  HYDOT_CUDA_TRY(ctx, cudaGetLastError());
-  HYDOT_CUDA_TRY(ctx, launch_apply_reduce<E>(part, nlam, ns, nd, nts, ntd, nxb, ctx->h * ctx->h * ctx->h, y,
+  HYDOT_CUDA_TRY(ctx, launch_apply_reduce<E>(part, nlam, ns, nd, nts, ntd, tw, nxb, ctx->h * ctx->h * ctx->h, y,
                                               ctx->stream));
   ++ctx->launches;
   timer_end(ctx, t0, HYDOT_KERNEL_APPLY, ((double)nlam * (ns + nd) + nc) * (double)N * sizeof(E));
@@ -701,10 +772,12 @@ int apply_T_tile(hydot_ctx* ctx, const float* ps, const float* pd, int lam0, int
   const int spt = tile_spt(ns);
   auto kern = spt == 8 ? k_apply_T_tile<8> : spt == 6 ? k_apply_T_tile<6> : spt == 4 ? k_apply_T_tile<4>
                                                                                       : k_apply_T_tile<2>;
-  HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TT_SMEM));
+  const size_t smem = TT_SMEM + sizeof(float) * (size_t)lpg * TT_NC;
+  if (smem > 200 * 1024) return fail(ctx, HYDOT_ERR_ARG, "too many wavelengths per J^T y call");
+  HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid((unsigned)xblocks, ngrp);
   cudaEvent_t t0 = timer_begin(ctx);
-  kern<<<grid, 256, TT_SMEM, ctx->stream>>>(ps, pd, y, ctx->d_eps, lam0, nlam, ns, nd, nc, N, lpg, part);
+  kern<<<grid, 256, smem, ctx->stream>>>(ps, pd, y, ctx->d_eps, lam0, nlam, ns, nd, nc, N, lpg, part);
   ++ctx->launches;
   HYDOT_CUDA_TRY(ctx, cudaGetLastError());
   long long tot = (long long)nc * N;
@@ -861,14 +934,14 @@ extern "C" int hydot_born_apply_noalloc(long long N, int n_src, int n_det, int n
     set_context_free_error(std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e));
     return HYDOT_ERR_CUDA;
   }
-  const size_t smem = apply_smem_bytes<float>(n_chrom);
-  e = cudaFuncSetAttribute(k_apply_partial<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess) {
+  {
     dim3 grid((unsigned)nxb, nlam, nts * ntd);
-    // every partial slot is written before it is read, so nothing in the array needs clearing
-    k_apply_partial<float><<<grid, 256, smem, s>>>(phi_src, phi_det, x, d_eps, 0, n_src, n_det, n_chrom, N,
-                                                   (int)nxb, apply_vec_ok(phi_src, phi_det, x, N, 4), part);
-    e = launch_apply_reduce<float>(part, nlam, n_src, n_det, nts, ntd, (int)nxb, h_mm * h_mm * h_mm, y, s);
+    // 32-wide optode tiles; every partial slot that is summed is written first, so nothing in the
+    // array needs clearing
+    e = launch_apply_partial<float, 8>(grid, s, phi_src, phi_det, x, d_eps, 0, n_src, n_det, n_chrom, N, (int)nxb,
+                                       apply_vec_ok(phi_src, phi_det, x, N, 4), part);
+    if (e == cudaSuccess)
+      e = launch_apply_reduce<float>(part, nlam, n_src, n_det, nts, ntd, 32, (int)nxb, h_mm * h_mm * h_mm, y, s);
   }
   if (e != cudaSuccess) {
     set_context_free_error(std::string("launch: ") + cudaGetErrorString(e));
