@@ -97,16 +97,18 @@ __global__ void __launch_bounds__(256) k_born_rows_scalar(const E* __restrict__ 
 }
 
 // ---------------------------------------------------------------- J x
-// Block = (wavelength a, chunk of AP_STAGES x AP_XC voxels, TILE x TILE tile of (s, d), TILE = 4U
+// Block = (wavelength a, chunk of spb x AP_XC voxels, TILE x TILE tile of (s, d), TILE = 4U
 // with U in {8, 6, 4, 2} chosen per problem so that the tiles pad n_src and n_det little). Each stage of
 // AP_XC voxels (phi_s and phi_d rows of the tile, and the chromophore maps x_c) is copied into
-// shared memory with cp.async while the previous stage is contracted (two buffers). 256 threads =
+// shared memory with cp.async two stages ahead of the one being contracted (three buffers). 256 threads =
 // 16 voxel groups x 16 (s, d) sub-tiles; a thread accumulates s-rows si0 + 4u and d-rows
 // di0 + 4v (u, v < U), which with a row stride of AP_XC + 16 bytes keeps the tile reads of a warp
 // on distinct banks. mu_a(x) = sum_c eps_c(lambda_a) x_c is formed by each thread for its voxels.
 // Block partials go to a workspace and a second kernel sums them in a fixed order.
 constexpr int AP_XC = 128;   // voxels per stage
-constexpr int AP_STAGES = 8; // stages per block
+constexpr int AP_STAGES = 8; // stages per block of the allocation-free entry point (the library picks
+                              // 4 .. 32 per problem, see apply_spb)
+constexpr int AP_NBUF = 3;    // stage buffers: two stages in flight while one is contracted
 
 template <typename E>
 __host__ __device__ constexpr int ap_ld() { return AP_XC + 16 / (int)sizeof(E); }  // padded row stride (elements)
@@ -117,7 +119,7 @@ __host__ __device__ constexpr size_t apply_buf_elems(int nc) {
 }
 template <typename E, int U>
 size_t apply_smem_bytes(int nc) {
-  return std::max(sizeof(E) * 2 * apply_buf_elems<E, U>(nc), sizeof(E) * 8 * 1024);  // the reduction reuses it
+  return std::max(sizeof(E) * AP_NBUF * apply_buf_elems<E, U>(nc), sizeof(E) * 8 * 1024);  // the reduction reuses it
 }
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src, uint32_t src_bytes) {
@@ -138,8 +140,8 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 template <typename E, int U>
 __global__ void __launch_bounds__(256) k_apply_partial(const E* __restrict__ ps, const E* __restrict__ pd,
                                                        const E* __restrict__ xin, const double* __restrict__ eps,
-                                                       int lam0, int ns, int nd, int nc, long long N, int nxb, int vec,
-                                                       E* __restrict__ part) {
+                                                       int lam0, int ns, int nd, int nc, long long N, int nxb, int spb,
+                                                       int vec, E* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int LD = ap_ld<E>();
   constexpr int VE = 16 / (int)sizeof(E);  // elements per 16-byte copy
@@ -160,7 +162,7 @@ __global__ void __launch_bounds__(256) k_apply_partial(const E* __restrict__ ps,
   const E* srow = ps + ((size_t)a * ns + s0) * N;
   const E* drow = pd + ((size_t)a * nd + d0) * N;
   auto load = [&](int st, E* b) {
-    const long long xbase = ((long long)xb * AP_STAGES + st) * AP_XC;
+    const long long xbase = ((long long)xb * spb + st) * AP_XC;
     E* S = b;
     E* D = b + TILE * LD;
     E* X = b + 2 * TILE * LD;
@@ -218,12 +220,17 @@ __global__ void __launch_bounds__(256) k_apply_partial(const E* __restrict__ ps,
   for (int u = 0; u < U; ++u)
 #pragma unroll
     for (int v = 0; v < U; ++v) acc[u][v] = 0;
-  const long long nstage = min((long long)AP_STAGES, (N - (long long)xb * AP_STAGES * AP_XC + AP_XC - 1) / AP_XC);
+  const long long nstage = min((long long)spb, (N - (long long)xb * spb * AP_XC + AP_XC - 1) / AP_XC);
+  const size_t be = apply_buf_elems<E, U>(nc);  // elements per stage buffer
+  static_assert(AP_NBUF == 2 || AP_NBUF == 3, "two or three stage buffers");
   load(0, buf0);
+  if (AP_NBUF == 3 && nstage > 1) load(1, buf0 + be);
   for (int st = 0; st < nstage; ++st) {
-    E* b = buf0 + (st & 1) * apply_buf_elems<E, U>(nc);
-    if (st + 1 < nstage) {
-      load(st + 1, buf0 + ((st + 1) & 1) * apply_buf_elems<E, U>(nc));
+    E* b = buf0 + (st % AP_NBUF) * be;
+    if (st + AP_NBUF - 1 < nstage) {
+      load(st + AP_NBUF - 1, buf0 + ((st + AP_NBUF - 1) % AP_NBUF) * be);
+      cp_async_wait<AP_NBUF - 1>();
+    } else if (AP_NBUF == 3 && st + 1 < nstage) {
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
@@ -295,7 +302,7 @@ __global__ void __launch_bounds__(256) k_apply_partial(const E* __restrict__ ps,
           for (int v = 0; v < U; ++v) acc[u][v] += sv[u] * dv[v];
       }
     }
-    __syncthreads();  // buffer (st & 1) is refilled by the load of stage st + 2
+    __syncthreads();  // this buffer is refilled by the load issued in the next iteration
   }
   // tree reduction over the 16 voxel groups (fixed order -> deterministic)
   for (int half = 8; half >= 1; half >>= 1) {
@@ -383,24 +390,34 @@ int apply_u(int ns, int nd) {
 
 template <typename E, int U>
 cudaError_t launch_apply_partial(dim3 grid, cudaStream_t st, const E* ps, const E* pd, const E* x, const double* eps,
-                                 int lam0, int ns, int nd, int nc, long long N, int nxb, int vec, E* part) {
+                                 int lam0, int ns, int nd, int nc, long long N, int nxb, int spb, int vec, E* part) {
   const size_t smem = apply_smem_bytes<E, U>(nc);
   cudaError_t e = cudaFuncSetAttribute(k_apply_partial<E, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_apply_partial<E, U><<<grid, 256, smem, st>>>(ps, pd, x, eps, lam0, ns, nd, nc, N, nxb, vec, part);
+  k_apply_partial<E, U><<<grid, 256, smem, st>>>(ps, pd, x, eps, lam0, ns, nd, nc, N, nxb, spb, vec, part);
   return cudaGetLastError();
 }
 
 template <typename E>
 cudaError_t launch_apply_partial_u(int u, dim3 grid, cudaStream_t st, const E* ps, const E* pd, const E* x,
-                                   const double* eps, int lam0, int ns, int nd, int nc, long long N, int nxb, int vec,
-                                   E* part) {
+                                   const double* eps, int lam0, int ns, int nd, int nc, long long N, int nxb, int spb,
+                                   int vec, E* part) {
   switch (u) {
-    case 6: return launch_apply_partial<E, 6>(grid, st, ps, pd, x, eps, lam0, ns, nd, nc, N, nxb, vec, part);
-    case 4: return launch_apply_partial<E, 4>(grid, st, ps, pd, x, eps, lam0, ns, nd, nc, N, nxb, vec, part);
-    case 2: return launch_apply_partial<E, 2>(grid, st, ps, pd, x, eps, lam0, ns, nd, nc, N, nxb, vec, part);
-    default: return launch_apply_partial<E, 8>(grid, st, ps, pd, x, eps, lam0, ns, nd, nc, N, nxb, vec, part);
+    case 6: return launch_apply_partial<E, 6>(grid, st, ps, pd, x, eps, lam0, ns, nd, nc, N, nxb, spb, vec, part);
+    case 4: return launch_apply_partial<E, 4>(grid, st, ps, pd, x, eps, lam0, ns, nd, nc, N, nxb, spb, vec, part);
+    case 2: return launch_apply_partial<E, 2>(grid, st, ps, pd, x, eps, lam0, ns, nd, nc, N, nxb, spb, vec, part);
+    default: return launch_apply_partial<E, 8>(grid, st, ps, pd, x, eps, lam0, ns, nd, nc, N, nxb, spb, vec, part);
   }
+}
+
+// stages (of AP_XC voxels) per J x block: the largest of 32, 16, 8 that leaves at least four waves
+// of two blocks per SM (fewer, longer blocks mean fewer partial sums and block epilogues), else 4
+int apply_spb(long long N, int nlam, int ntiles) {
+  for (int spb : {32, 16, 8}) {
+    const long long nxb = (N + (long long)spb * AP_XC - 1) / ((long long)spb * AP_XC);
+    if (nxb * nlam * ntiles >= 4LL * 2 * 152) return spb;
+  }
+  return 4;
 }
 
 // ---------------------------------------------------------------- J^T y
@@ -502,16 +519,17 @@ constexpr int TT_XC = 256;  // voxels per block
 constexpr int TT_DC = 32;   // detectors per stage
 constexpr int TT_NC = 4;    // chromophores held in registers
 constexpr size_t TT_STAGE_FLOATS = (size_t)TT_DC * TT_XC + (size_t)TT_DC * 32;  // phi_d chunk + Y tile
-constexpr size_t TT_SMEM = 2 * TT_STAGE_FLOATS * sizeof(float);
+constexpr int TT_NBUF = 2;  // stage buffers: one stage in flight while one is contracted
+constexpr size_t TT_SMEM = TT_NBUF * TT_STAGE_FLOATS * sizeof(float);
 
 template <int SPT>
 __global__ void __launch_bounds__(256, 2) k_apply_T_tile(const float* __restrict__ ps, const float* __restrict__ pd,
-                                                      const float* __restrict__ y, const double* __restrict__ eps,
+                                                      const float* __restrict__ yT, const double* __restrict__ eps,
                                                       int lam0, int nlam, int ns, int nd, int nc, long long N,
                                                       int lam_per_group, float* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char smraw[];
   float* buf0 = reinterpret_cast<float*>(smraw);
-  float* epsf = buf0 + 2 * TT_STAGE_FLOATS;  // [lam_per_group][TT_NC] eps_c(lambda) of the group, FP32
+  float* epsf = buf0 + TT_NBUF * TT_STAGE_FLOATS;  // [lam_per_group][TT_NC] eps_c(lambda) of the group, FP32
   const int t = threadIdx.x;
   const int q = t >> 2, g = t & 3;
   const int grp = blockIdx.y;
@@ -546,11 +564,12 @@ __global__ void __launch_bounds__(256, 2) k_apply_T_tile(const float* __restrict
     const int s = lst * ST + yg * SPT + yj;
     const bool sok = yj < SPT && s < ns;
     float* Yt = b + (size_t)TT_DC * TT_XC + yr * 32 + yg * 8 + yj;  // Y_a[s][d0 + d] at d*32 + group*8 + j
-    const float* ysrc = y + ((size_t)(sok ? s : 0) * nd + d0 + yr) * nlam + la;
+    // yT [nlam][nd][ns]: the sources of one detector are contiguous, a warp reads one 128-byte row
+    const float* ysrc = yT + ((size_t)la * nd + d0 + yr) * ns + (sok ? s : 0);
 #pragma unroll
     for (int i = 0; i < TT_DC / 8; ++i) {
       const bool ok = sok && yr + 8 * i < dn;
-      cp_async_small<4>(Yt + i * 8 * 32, ok ? (const void*)(ysrc + (size_t)i * 8 * nlam) : (const void*)y,
+      cp_async_small<4>(Yt + i * 8 * 32, ok ? (const void*)(ysrc + (size_t)i * 8 * ns) : (const void*)yT,
                         ok ? 4u : 0u);
     }
     cp_async_commit();
@@ -573,7 +592,9 @@ __global__ void __launch_bounds__(256, 2) k_apply_T_tile(const float* __restrict
 #pragma unroll
     for (int i = 0; i < 4; ++i) W[j][i] = 0.f;
   }
+  static_assert(TT_NBUF == 2 || TT_NBUF == 3, "two or three stage buffers");
   if (nstage > 0) load(buf0);
+  if (TT_NBUF == 3 && nstage > 1) load(buf0 + TT_STAGE_FLOATS);
   int a = a0, st = 0, dc = 0;  // stage being contracted
   for (int k = 0; k < nstage; ++k) {
     if (dc == 0 && in) {  // phi_s of this tile: consumed after the tile's last detector chunk
@@ -583,9 +604,11 @@ __global__ void __launch_bounds__(256, 2) k_apply_T_tile(const float* __restrict
       for (int j = 0; j < SPT; ++j)
         fs[j] = sb + j < ns ? *reinterpret_cast<const float4*>(sp + (size_t)j * N) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    float* b = buf0 + (k & 1) * TT_STAGE_FLOATS;
-    if (k + 1 < nstage) {
-      load(buf0 + ((k + 1) & 1) * TT_STAGE_FLOATS);
+    float* b = buf0 + (k % TT_NBUF) * TT_STAGE_FLOATS;
+    if (k + TT_NBUF - 1 < nstage) {
+      load(buf0 + ((k + TT_NBUF - 1) % TT_NBUF) * TT_STAGE_FLOATS);
+      cp_async_wait<TT_NBUF - 1>();
+    } else if (TT_NBUF == 3 && k + 1 < nstage) {
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
@@ -611,7 +634,7 @@ __global__ void __launch_bounds__(256, 2) k_apply_T_tile(const float* __restrict
         W[j][3] = fmaf(yv[j], f.w, W[j][3]);
       }
     }
-    __syncthreads();  // buffer (k & 1) is refilled by the load of stage k + 2
+    __syncthreads();  // this buffer is refilled by the load issued in the next iteration
     if (dc == ndc - 1) {
 #pragma unroll
       for (int j = 0; j < SPT; ++j) {
@@ -726,7 +749,8 @@ int apply_t(hydot_ctx* ctx, const E* ps, const E* pd, int lam0, int nlam, const 
   const int ns = ctx->n_src, nd = ctx->n_det, nc = ctx->n_chrom;
   const int u = apply_u(ns, nd), tw = 4 * u;
   const int nts = (ns + tw - 1) / tw, ntd = (nd + tw - 1) / tw;
-  const long long per_blk = (long long)AP_XC * AP_STAGES;
+  const int spb = apply_spb(N, nlam, nts * ntd);
+  const long long per_blk = (long long)AP_XC * spb;
   const int nxb = (int)((N + per_blk - 1) / per_blk);
   size_t bytes = sizeof(E) * (size_t)nlam * nts * ntd * nxb * 1024;
   int rc = ensure_ws(ctx, bytes);
@@ -736,7 +760,7 @@ int apply_t(hydot_ctx* ctx, const E* ps, const E* pd, int lam0, int nlam, const 
   const int vec = apply_vec_ok(ps, pd, x, N, sizeof(E));
   cudaEvent_t t0 = timer_begin(ctx);
   HYDOT_CUDA_TRY(ctx, launch_apply_partial_u<E>(u, grid, ctx->stream, ps, pd, x, ctx->d_eps, lam0, ns, nd, nc, N,
-                                                nxb, vec, part));
+                                                nxb, spb, vec, part));
   ++ctx->launches;
   HYDOT_CUDA_TRY(ctx, launch_apply_reduce<E>(part, nlam, ns, nd, nts, ntd, tw, nxb, ctx->h * ctx->h * ctx->h, y,
                                               ctx->stream));
@@ -744,6 +768,18 @@ int apply_t(hydot_ctx* ctx, const E* ps, const E* pd, int lam0, int nlam, const 
   timer_end(ctx, t0, HYDOT_KERNEL_APPLY, ((double)nlam * (ns + nd) + nc) * (double)N * sizeof(E));
   HYDOT_CUDA_TRY(ctx, cudaGetLastError());
   return HYDOT_OK;
+}
+
+// yT[(a * nd + d) * ns + s] = y[(s * nd + d) * nlam + a]: the slice's residual with the sources of
+// each (wavelength, detector) contiguous, for the register-tiled J^T y kernel's staging
+__global__ void k_transpose_y(const float* __restrict__ y, int nlam, int ns, int nd, float* __restrict__ yT) {
+  const long long M = (long long)nlam * ns * nd;
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < M; r += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(r % ns);
+    const long long ad = r / ns;
+    const int d = (int)(ad % nd), a = (int)(ad / nd);
+    yT[r] = y[((size_t)s * nd + d) * nlam + a];
+  }
 }
 
 // sources per thread of the register-tiled J^T y kernel: per detector a source tile costs 4 * SPT
@@ -766,9 +802,12 @@ int apply_T_tile(hydot_ctx* ctx, const float* ps, const float* pd, int lam0, int
   int ngrp = (int)std::max<long long>(1, std::min<long long>(nlam, (4 * 2 * 152 + xblocks - 1) / xblocks));
   const int lpg = (nlam + ngrp - 1) / ngrp;
   ngrp = (nlam + lpg - 1) / lpg;
-  int rc = ensure_ws(ctx, sizeof(float) * (size_t)ngrp * nc * N);
+  const size_t part_elems = (size_t)ngrp * nc * N;
+  const long long M = (long long)nlam * ns * nd;
+  int rc = ensure_ws(ctx, sizeof(float) * (part_elems + (size_t)M));
   if (rc) return rc;
   float* part = (float*)ctx->d_apply_ws;
+  float* yT = part + part_elems;
   const int spt = tile_spt(ns);
   auto kern = spt == 8 ? k_apply_T_tile<8> : spt == 6 ? k_apply_T_tile<6> : spt == 4 ? k_apply_T_tile<4>
                                                                                       : k_apply_T_tile<2>;
@@ -777,7 +816,9 @@ int apply_T_tile(hydot_ctx* ctx, const float* ps, const float* pd, int lam0, int
   HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid((unsigned)xblocks, ngrp);
   cudaEvent_t t0 = timer_begin(ctx);
-  kern<<<grid, 256, smem, ctx->stream>>>(ps, pd, y, ctx->d_eps, lam0, nlam, ns, nd, nc, N, lpg, part);
+  k_transpose_y<<<(unsigned)std::min<long long>((M + 255) / 256, 4096), 256, 0, ctx->stream>>>(y, nlam, ns, nd, yT);
+  ++ctx->launches;
+  kern<<<grid, 256, smem, ctx->stream>>>(ps, pd, yT, ctx->d_eps, lam0, nlam, ns, nd, nc, N, lpg, part);
   ++ctx->launches;
   HYDOT_CUDA_TRY(ctx, cudaGetLastError());
   long long tot = (long long)nc * N;
@@ -939,7 +980,7 @@ extern "C" int hydot_born_apply_noalloc(long long N, int n_src, int n_det, int n
     // 32-wide optode tiles; every partial slot that is summed is written first, so nothing in the
     // array needs clearing
     e = launch_apply_partial<float, 8>(grid, s, phi_src, phi_det, x, d_eps, 0, n_src, n_det, n_chrom, N, (int)nxb,
-                                       apply_vec_ok(phi_src, phi_det, x, N, 4), part);
+                                       AP_STAGES, apply_vec_ok(phi_src, phi_det, x, N, 4), part);
     if (e == cudaSuccess)
       e = launch_apply_reduce<float>(part, nlam, n_src, n_det, nts, ntd, 32, (int)nxb, h_mm * h_mm * h_mm, y, s);
   }
