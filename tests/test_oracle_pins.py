@@ -5,6 +5,7 @@ finite difference of the nonlinear forward model, brute force, a second
 independent solver, or an algebraic identity, so that a dropped term, a wrong
 sign or index, or a transposed operand fails at least one of them.
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -388,3 +389,82 @@ def test_recursive_lowrank_exact_and_within_the_section_bound():
     W = np.vstack([s[:, None] * vt for (_, s, vt) in f])
     assert np.allclose(np.linalg.svd(W, compute_uv=False), np.linalg.svd(np.vstack([A, B]), compute_uv=False),
                        rtol=1e-10, atol=1e-14 * np.abs(A).max())
+
+
+# --------------------------------------------------------------------------- shift-invariant guess
+def _cg_iterates(A, b, m):
+    """m steps of plain (unpreconditioned) conjugate gradients from zero."""
+    x = np.zeros_like(b)
+    r = b.copy()
+    p = r.copy()
+    rr = r @ r
+    for _ in range(m):
+        q = A @ p
+        a = rr / (p @ q)
+        x += a * p
+        r -= a * q
+        rr2 = r @ r
+        p = r + (rr2 / rr) * p
+        rr = rr2
+    return x
+
+
+def test_shift_guess_is_cg_iterate_when_shifts_are_pure():
+    """With Dirichlet faces the boundary term of Ahat_j does not depend on the wavelength, so Ahat_j =
+    Ahat_0 + (sigma_j - mean sigma) I and K_m(Ahat_0, e) = K_m(Ahat_j, e): the Galerkin guess is then
+    the m-th conjugate-gradient iterate of Ahat_j x = e (the CG iterate is the Galerkin solution over
+    the Krylov space), computed here by a separate recurrence."""
+    from oracle import shift
+
+    p = workloads.small(seed=71, nx=9, ny=8, nz=7, n_src=2, n_det=2, n_lambda=5)
+    p = dataclasses.replace(p, robin_A=np.zeros(6))
+    mua, D = model.wavelength_coefficients(p)
+    cell = int(p.src_voxels()[0])
+    e = np.zeros(p.grid.N)
+    e[cell] = 1.0
+    for m in (6, 15):
+        for j in (0, 4):
+            g = shift.shift_guess(p, j, cell, m)
+            x = _cg_iterates(shift.scaled_operator(p, j), e, m) / (D[j] * p.grid.h)
+            assert np.abs(g - x).max() <= 1e-9 * np.abs(x).max()
+
+
+def test_shift_guess_exact_when_the_krylov_space_is_invariant():
+    """On a tiny grid m = N steps exhaust the Krylov space, or Lanczos stops early where the space is
+    invariant (here for the optode on the grid's mirror plane j = 1 of ny = 3). With pure shifts
+    (Dirichlet faces) a space invariant under Ahat_0 is invariant under every Ahat_j and holds
+    Ahat_j^-1 e: the guess is then the solution itself."""
+    from oracle import shift
+
+    p = workloads.small(seed=72, nx=4, ny=3, nz=3, n_src=1, n_det=1, n_lambda=3)
+    p = dataclasses.replace(p, robin_A=np.zeros(6))
+    assert int(p.det_ijk[0][1]) == 1  # on the mirror plane: an invariant space smaller than N
+    for j in range(p.n_lambda):
+        for cell in (int(p.src_voxels()[0]), int(p.det_voxels()[0])):
+            e = np.zeros(p.grid.N)
+            e[cell] = 1.0
+            exact = solve.solve_splu(p, j, e[None])[0]
+            g = shift.shift_guess(p, j, cell, p.grid.N)
+            assert np.abs(g - exact).max() <= 1e-10 * np.abs(exact).max()
+
+
+def test_shift_guess_energy_error_decreases_with_m():
+    """The Galerkin guess minimises the Ahat_j-norm of the error over the Krylov space, and the spaces
+    are nested, so that error cannot grow with m (Robin faces: the shifts are not pure here)."""
+    from oracle import shift
+
+    p = workloads.small(seed=73, nx=10, ny=9, nz=8, n_src=1, n_det=1, n_lambda=4)
+    _, D = model.wavelength_coefficients(p)
+    cell = int(p.src_voxels()[0])
+    e = np.zeros(p.grid.N)
+    e[cell] = 1.0
+    for j in (0, 3):
+        A = shift.scaled_operator(p, j)
+        xs = solve.solve_splu(p, j, e[None])[0] * (D[j] * p.grid.h)
+        errs = []
+        for m in (2, 5, 10, 20, 40):
+            g = shift.shift_guess(p, j, cell, m) * (D[j] * p.grid.h)
+            d = xs - g
+            errs.append(float(d @ (A @ d)))
+        assert all(b <= a * (1 + 1e-9) for a, b in zip(errs, errs[1:]))
+        assert errs[-1] < 1e-3 * errs[0]
