@@ -216,6 +216,28 @@ int hydot_get_tuning(const hydot_ctx* ctx, int* variant, int* planes, int* buffe
  * with FP64 refinement (or FP64 throughout), to the context's tolerances. Synchronous. */
 int hydot_set_absorption(hydot_ctx* ctx, const double* dc);
 
+/* Shift-invariant initial guesses (Section 3, 3.2; the base operator at the mean shift, Section
+ * 6.1). Builds, for every source and detector field, an orthonormal basis V (m vectors, FP32) of the
+ * Krylov space K_m(Ahat_0, e_cell) of the base operator Ahat_0 = Lg + mean(sigma) I + sum_f
+ * mean(bhat_f) B_f (the scaled operator of the coefficient table, averaged over the wavelengths),
+ * with Lanczos and full reorthogonalisation, together with the Lanczos tridiagonal and the
+ * boundary blocks V^T B_f V. From then on hydot_solve_fields starts every field of every wavelength
+ * j from the Galerkin projection x_j = V (V^T Ahat_j V)^-1 V^T e_cell, formed from those small
+ * matrices without products with Ahat_j, instead of from zero; the solves still converge to the
+ * context's tolerances (the guess changes where the iteration starts, not where it stops).
+ * m: 1..64 (capped at N), or 0 to remove the bases. Device memory: (n_src+n_det)*m*N*4 bytes,
+ * plus small tables. Continuous-wave contexts only (HYDOT_ERR_STATE for omega != 0), and not
+ * together with deflation_k > 0 (HYDOT_ERR_STATE); m outside 0..64: HYDOT_ERR_ARG. With an
+ * absorption perturbation set (hydot_set_absorption) the guess ignores it. Synchronous. */
+int hydot_set_shift_guess(hydot_ctx* ctx, int m);
+
+/* The initial guesses themselves, in field units phi = x / (D h), for the wavelengths lam0 ..
+ * lam0+nlam-1: phi_src [nlam][n_src][N], phi_det [nlam][n_det][N], DEVICE, element type as for
+ * hydot_solve_fields (FP32 for HYDOT_MIXED, FP64 for HYDOT_FP64). nlam*(n_src+n_det) must not exceed
+ * the context's simultaneous fields (max_lambda_per_call*(n_src+n_det)). HYDOT_ERR_STATE when no
+ * bases are built. Asynchronous on the context's stream. */
+int hydot_shift_guess_fields(hydot_ctx* ctx, int lam0, int nlam, void* phi_src, void* phi_det);
+
 /* Failure-path self-test (no counterpart in the paper): one thread waits on a shared-memory
  * mbarrier that nothing arrives at, through the same bounded poll loop the pipelined kernels use
  * for their TMA and tensor-core waits, but with `polls` polls (1..2^22) instead of their limit;

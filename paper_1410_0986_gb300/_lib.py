@@ -26,7 +26,7 @@ EXPORTS = ("hydot_version", "hydot_setup", "hydot_set_stream", "hydot_solve_fiel
            "hydot_sketch_project", "hydot_sketch_orthonormalize", "hydot_sketch_rank", "hydot_sketch_merge",
            "hydot_sketch_factor", "hydot_set_kernel_timing",
            "hydot_kernel_stats", "hydot_kernel_launches", "hydot_get_tuning", "hydot_set_absorption",
-           "hydot_wait_selftest",
+           "hydot_wait_selftest", "hydot_set_shift_guess", "hydot_shift_guess_fields",
            "hydot_last_error", "hydot_destroy")
 ROLL_VARIANTS = 4  # HYDOT_ROLL_VARIANTS
 KERNELS = {"dir": 0, "update": 1, "residual": 2, "born_rows": 3, "apply": 4, "apply_T": 5, "sketch_range": 6,
@@ -122,6 +122,10 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.hydot_set_absorption.restype = C.c_int
     lib.hydot_wait_selftest.argtypes = [vp, C.c_int]
     lib.hydot_wait_selftest.restype = C.c_int
+    lib.hydot_set_shift_guess.argtypes = [vp, C.c_int]
+    lib.hydot_set_shift_guess.restype = C.c_int
+    lib.hydot_shift_guess_fields.argtypes = [vp, C.c_int, C.c_int, vp, vp]
+    lib.hydot_shift_guess_fields.restype = C.c_int
     lib.hydot_last_error.argtypes = [vp]
     lib.hydot_last_error.restype = C.c_char_p
     lib.hydot_destroy.argtypes = [vp]

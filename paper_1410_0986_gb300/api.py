@@ -289,6 +289,22 @@ class Context:
         self._stream()
         self._check(self.lib.hydot_set_absorption(self._ctx, a.ctypes.data_as(C.POINTER(C.c_double))))
 
+    def set_shift_guess(self, m: int) -> None:
+        """hydot_set_shift_guess: build the per-optode Krylov bases (m vectors each) of the
+        mean-shift operator; later solves start from their Galerkin guesses. m = 0 removes them."""
+        self._stream()
+        self._check(self.lib.hydot_set_shift_guess(self._ctx, int(m)))
+
+    def shift_guess_fields(self, lam0: int, nlam: int):
+        """hydot_shift_guess_fields: the initial guesses (field units) of a wavelength slice,
+        as (phi_src [nlam][n_src][N], phi_det [nlam][n_det][N])."""
+        ps = torch.empty(nlam, self.n_src, self.N, dtype=self.real_dtype, device="cuda")
+        pd = torch.empty(nlam, self.n_det, self.N, dtype=self.real_dtype, device="cuda")
+        self._stream()
+        self._check(self.lib.hydot_shift_guess_fields(self._ctx, int(lam0), int(nlam), C.c_void_p(ps.data_ptr()),
+                                                      C.c_void_p(pd.data_ptr())))
+        return ps, pd
+
     def wait_selftest(self, polls: int = 1000) -> None:
         """hydot_wait_selftest: a bounded device wait that runs out; raises HydotError
         (HYDOT_ERR_TIMEOUT) as every pipelined kernel's timeout would."""

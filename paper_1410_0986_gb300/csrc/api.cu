@@ -85,6 +85,7 @@ void free_all(hydot_ctx* c) {
   cudaFree(c->d_W);
   cudaFree(c->d_Ginv);
   cudaFree(c->d_defl_coef);
+  hydot::shift_guess_free(c);
   cudaFree(c->d_apply_ws);
   cudaFree(c->d_sketch_ws);
 }
@@ -322,6 +323,16 @@ long long hydot_kernel_launches(const hydot_ctx* ctx) { return ctx ? ctx->launch
 int hydot_set_absorption(hydot_ctx* ctx, const double* dc) {
   if (!ctx) return HYDOT_ERR_ARG;
   return hydot::set_absorption_impl(ctx, dc);
+}
+
+int hydot_set_shift_guess(hydot_ctx* ctx, int m) {
+  if (!ctx) return HYDOT_ERR_ARG;
+  return hydot::set_shift_guess_impl(ctx, m);
+}
+
+int hydot_shift_guess_fields(hydot_ctx* ctx, int lam0, int nlam, void* phi_src, void* phi_det) {
+  if (!ctx) return HYDOT_ERR_ARG;
+  return hydot::shift_guess_fields_impl(ctx, lam0, nlam, phi_src, phi_det);
 }
 
 int hydot_wait_selftest(hydot_ctx* ctx, int polls) {

@@ -211,6 +211,18 @@ struct hydot_ctx {
   double* d_defl_coef = nullptr;               // [max_fields][k] G_j^-1 W^T b per field
   std::vector<double> deflation_ritz;          // Ritz values of the base operator (ascending)
 
+  // shift-invariant initial guesses: per optode field an FP32 orthonormal basis of the Krylov space
+  // of the mean-shift operator started at the optode cell, with its Lanczos coefficients and the
+  // boundary blocks V^T B_f V
+  int sg_m = 0;                // basis size (0: off)
+  float* d_sgV = nullptr;      // [n_src + n_det][sg_m][N]
+  double* d_sgA = nullptr;     // [n_src + n_det][64] Lanczos diagonal
+  double* d_sgB = nullptr;     // [n_src + n_det][64] Lanczos off-diagonal
+  double* d_sgP = nullptr;     // [n_src + n_det][6][sg_m][sg_m]
+  int* d_sgMeff = nullptr;     // [n_src + n_det] basis size (smaller after a breakdown)
+  float* d_sgY = nullptr;      // [max_fields][sg_m] Galerkin coefficients of a batch
+  double sg_base[7] = {0, 0, 0, 0, 0, 0, 0};  // mean sigma, mean bhat_f of the base operator
+
   long long launches = 0;  // kernels enqueued by this context
   hydot::KernelTimer timer;
 
@@ -266,6 +278,12 @@ int sketch_factor_impl(hydot_ctx* ctx, const float* Q, long long rows, long long
 // deflation.cu
 int build_deflation(hydot_ctx* ctx);
 int deflate_initial_guess(hydot_ctx* ctx, int lam0, int f_begin, int nf, int nrhs, double* x64);
+
+// shiftguess.cu
+int set_shift_guess_impl(hydot_ctx* ctx, int m);
+int shift_initial_guess(hydot_ctx* ctx, int lam0, int f_begin, int nf, int nrhs, double* x64);
+int shift_guess_fields_impl(hydot_ctx* ctx, int lam0, int nlam, void* phi_src, void* phi_det);
+void shift_guess_free(hydot_ctx* ctx);
 
 // api.cu
 void set_context_free_error(const std::string& msg);
