@@ -209,10 +209,16 @@ int hydot_setup(const hydot_problem* p, void* stream, hydot_ctx** out) {
   {
     std::vector<hydot::LamCoefF> cf(c->n_lambda);
     for (int j = 0; j < c->n_lambda; ++j) {
-      cf[j].dint = (float)(6.0 + c->coef[j].sigma_re);
+      const double d = 6.0 + c->coef[j].sigma_re;
+      cf[j].dint = (float)d;
+      cf[j].dint_lo = (float)(d - (double)cf[j].dint);
       cf[j].dim = (float)c->coef[j].sigma_im;
-      cf[j].idint = (float)(1.0 / (6.0 + c->coef[j].sigma_re));
-      for (int f = 0; f < 6; ++f) cf[j].fa[f] = (float)(c->coef[j].bhat[f] - 1.0);
+      cf[j].idint = (float)(1.0 / d);
+      for (int f = 0; f < 6; ++f) {
+        const double a = c->coef[j].bhat[f] - 1.0;
+        cf[j].fa[f] = (float)a;
+        cf[j].fa_lo[f] = (float)(a - (double)cf[j].fa[f]);
+      }
     }
     SETUP_TRY(cudaMalloc(&c->d_coef_f, sizeof(hydot::LamCoefF) * c->n_lambda));
     SETUP_TRY(cudaMemcpy(c->d_coef_f, cf.data(), sizeof(hydot::LamCoefF) * c->n_lambda, cudaMemcpyHostToDevice));

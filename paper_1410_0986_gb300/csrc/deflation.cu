@@ -17,6 +17,7 @@
 //      W^T b is the optode cell's row of W).
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "dense.h"
@@ -348,18 +349,20 @@ __global__ void k_deflate_x0(const double* __restrict__ Wt, const double* __rest
     for (int rhs = blockIdx.y; rhs < nrhs; rhs += gridDim.y) {
       double s = 0.0;
       for (int a = 0; a < k; ++a) s += wrow[a] * C[(size_t)rhs * k + a];
-      x64[(size_t)rhs * N + id] = s;
+      if constexpr (std::is_same<X, df32>::value) x64[(size_t)rhs * N + id] = df_from(s);
+      else x64[(size_t)rhs * N + id] = s;
     }
   }
 }
 
-int deflate_initial_guess(hydot_ctx* ctx, int lam0, int f_begin, int nf, int nrhs, double* x64) {
+int deflate_initial_guess(hydot_ctx* ctx, int lam0, int f_begin, int nf, int nrhs, void* x64, bool df) {
   const int k = ctx->deflation_k;
   double* C = ctx->d_defl_coef;
   k_deflate_coef<<<(nrhs + 127) / 128, 128, 0, ctx->stream>>>(ctx->d_W, ctx->d_Ginv, k, ctx->N, ctx->d_optode, lam0,
                                                                f_begin, nf, nrhs, C);
   dim3 grid((unsigned)std::min<long long>((ctx->N + 255) / 256, 1024), (unsigned)std::min(nrhs, 64));
-  k_deflate_x0<double><<<grid, 256, 0, ctx->stream>>>(ctx->d_W, C, k, ctx->N, nrhs, x64);
+  if (df) k_deflate_x0<df32><<<grid, 256, 0, ctx->stream>>>(ctx->d_W, C, k, ctx->N, nrhs, (df32*)x64);
+  else k_deflate_x0<double><<<grid, 256, 0, ctx->stream>>>(ctx->d_W, C, k, ctx->N, nrhs, (double*)x64);
   ctx->launches += 2;
   HYDOT_CUDA_TRY(ctx, cudaGetLastError());
   return HYDOT_OK;

@@ -85,6 +85,58 @@ template <> struct Traits<cpx<double>> {
   __host__ __device__ static double rim(cpx<double> v) { return v.im; }
 };
 
+// ----------------------------------------------------------------------------- double-float
+// An unevaluated sum hi + lo of two FP32 numbers with |lo| <= ulp(hi) / 2: about 48 significant
+// bits in the exponent range of FP32. GB300 runs FP32 at ~64x its FP64 rate, so the refinement
+// iterate of the mixed real path is held in this form and updated with error-free transformations
+// (Knuth's TwoSum, Dekker's FastTwoSum, the FMA-based exact product). The rounded-to-nearest
+// intrinsics keep the compiler from fusing the operations these rely on.
+struct __align__(8) df32 {
+  float hi, lo;
+};
+
+__host__ __device__ inline df32 df_from(double v) {
+  const float h = (float)v;
+  return {h, (float)(v - (double)h)};
+}
+
+#ifdef __CUDACC__
+// s + e = a + b exactly (Knuth)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// s + e = a + b exactly when |a| >= |b| or a == 0 (Dekker)
+__device__ __forceinline__ df32 fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+// p + e = a * b exactly
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = __fmul_rn(a, b);
+  e = fmaf(a, b, -p);
+}
+// a + b, accurate also under cancellation (both pairs of parts added with TwoSum)
+__device__ __forceinline__ df32 df_add(df32 a, df32 b) {
+  float s, e, t, f;
+  two_sum(a.hi, b.hi, s, e);
+  two_sum(a.lo, b.lo, t, f);
+  df32 r = fast_two_sum(s, __fadd_rn(e, t));
+  r = fast_two_sum(r.hi, __fadd_rn(r.lo, f));
+  return r;
+}
+// the biased FP64 exponent of |v.hi| (0 for zero and FP32 subnormals): integer operations only
+__device__ __forceinline__ int bexp(df32 v) {
+  const int e = (__float_as_int(v.hi) >> 23) & 0xff;
+  return e ? e + (1023 - 127) : 0;
+}
+__device__ __forceinline__ int bexp_f(float v) {
+  const int e = (__float_as_int(v) >> 23) & 0xff;
+  return e ? e + (1023 - 127) : 0;
+}
+#endif
+
 // ----------------------------------------------------------------------------- coefficients
 // Per-wavelength coefficients of the scaled operator  Ahat = A / (D h):
 //   off-diagonal -1 to each existing neighbour,
@@ -104,6 +156,8 @@ struct LamCoefF {
   float dim;    // sigma_im
   float idint;  // 1 / dint
   float fa[6];  // bhat_f - 1
+  float dint_lo;   // 6 + sigma_re - dint: with dint, the diagonal as a double-float
+  float fa_lo[6];  // bhat_f - 1 - fa[f]
 };
 
 // Solver state of one simultaneous field (right-hand side) of a batch.
@@ -277,11 +331,12 @@ int sketch_factor_impl(hydot_ctx* ctx, const float* Q, long long rows, long long
 
 // deflation.cu
 int build_deflation(hydot_ctx* ctx);
-int deflate_initial_guess(hydot_ctx* ctx, int lam0, int f_begin, int nf, int nrhs, double* x64);
+// x64: double [nrhs][N], or df32 (double-float) when df
+int deflate_initial_guess(hydot_ctx* ctx, int lam0, int f_begin, int nf, int nrhs, void* x64, bool df);
 
 // shiftguess.cu
 int set_shift_guess_impl(hydot_ctx* ctx, int m);
-int shift_initial_guess(hydot_ctx* ctx, int lam0, int f_begin, int nf, int nrhs, double* x64);
+int shift_initial_guess(hydot_ctx* ctx, int lam0, int f_begin, int nf, int nrhs, void* x64, bool df);
 int shift_guess_fields_impl(hydot_ctx* ctx, int lam0, int nlam, void* phi_src, void* phi_det);
 void shift_guess_free(hydot_ctx* ctx);
 

@@ -21,6 +21,7 @@
 // space: their FP32 rounding changes the guess by ~1e-7 relative, which the refinement removes.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "hydot_internal.cuh"
@@ -290,8 +291,12 @@ __global__ void __launch_bounds__(SG_T) k_sg_x0(const float* __restrict__ V, lon
       for (int l = 0; l < SG_LB; ++l) acc[l] = fmaf(v, ys[l][a], acc[l]);
     }
 #pragma unroll
-    for (int l = 0; l < SG_LB; ++l)
-      if (l < nl) x64[((size_t)(l0 + l) * nf + fl) * N + x] = (X)acc[l];
+    for (int l = 0; l < SG_LB; ++l) {
+      if (l < nl) {
+        if constexpr (std::is_same<X, df32>::value) x64[((size_t)(l0 + l) * nf + fl) * N + x] = df32{acc[l], 0.f};
+        else x64[((size_t)(l0 + l) * nf + fl) * N + x] = (X)acc[l];
+      }
+    }
   }
 }
 
@@ -426,7 +431,7 @@ int set_shift_guess_impl(hydot_ctx* ctx, int m) {
 }
 
 // x64 of a batch (nrhs = nlam * nf fields, rhs = l * nf + fl) = the Galerkin guesses
-int shift_initial_guess(hydot_ctx* ctx, int lam0, int f_begin, int nf, int nrhs, double* x64) {
+int shift_initial_guess(hydot_ctx* ctx, int lam0, int f_begin, int nf, int nrhs, void* x64, bool df) {
   const int m = ctx->sg_m;
   const long long N = ctx->N, ldf = (long long)m * N;
   const int nlam = nrhs / nf;
@@ -439,8 +444,12 @@ int shift_initial_guess(hydot_ctx* ctx, int lam0, int f_begin, int nf, int nrhs,
   ++ctx->launches;
   const unsigned gx = (unsigned)std::min<long long>((N + SG_T - 1) / SG_T, std::max<long long>(1, 152 * 8 / nf));
   for (int l0 = 0; l0 < nlam; l0 += SG_LB) {
-    k_sg_x0<double><<<dim3(gx, nf), SG_T, 0, s>>>(ctx->d_sgV, ldf, N, ctx->d_sgY, nf, f_begin, l0,
-                                                  std::min(SG_LB, nlam - l0), m, ctx->d_sgMeff, x64);
+    if (df)
+      k_sg_x0<df32><<<dim3(gx, nf), SG_T, 0, s>>>(ctx->d_sgV, ldf, N, ctx->d_sgY, nf, f_begin, l0,
+                                                  std::min(SG_LB, nlam - l0), m, ctx->d_sgMeff, (df32*)x64);
+    else
+      k_sg_x0<double><<<dim3(gx, nf), SG_T, 0, s>>>(ctx->d_sgV, ldf, N, ctx->d_sgY, nf, f_begin, l0,
+                                                    std::min(SG_LB, nlam - l0), m, ctx->d_sgMeff, (double*)x64);
     ++ctx->launches;
   }
   HYDOT_CUDA_TRY(ctx, cudaGetLastError());
@@ -454,7 +463,7 @@ int shift_guess_fields_impl(hydot_ctx* ctx, int lam0, int nlam, void* phi_src, v
   const int nf = ctx->n_src + ctx->n_det;
   if ((long long)nlam * nf > ctx->max_fields) return fail(ctx, HYDOT_ERR_ARG, "nlam exceeds max_lambda_per_call");
   double* x64 = (double*)ctx->d_x64;
-  int rc = shift_initial_guess(ctx, lam0, 0, nf, nlam * nf, x64);
+  int rc = shift_initial_guess(ctx, lam0, 0, nf, nlam * nf, x64, false);
   if (rc) return rc;
   const long long tot = (long long)nlam * nf * ctx->N;
   const unsigned g = (unsigned)std::min<long long>((tot + 255) / 256, 152 * 32);

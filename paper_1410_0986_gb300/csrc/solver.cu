@@ -5,9 +5,12 @@
 // operator of eqn:discincident restated as finite volumes, see hydot.h); the field is
 // phi = x / (D_j h). One refinement cycle:
 //   K_theta  floor of the componentwise test from the partner optode cells (optional)
-//   K_res    r64 = b - Ahat x64 in FP64, ||r64||_2, the componentwise backward error
-//            max_i |r64_i| / (|Ahat||x64| + |b| + theta)_i, and the inner right-hand side
+//   K_res    r64 = b - Ahat x64 to well beyond FP32 accuracy, ||r64||_2, the componentwise backward
+//            error max_i |r64_i| / (|Ahat||x64| + |b| + theta)_i, and the inner right-hand side
 //            r = r64 / scale in the inner precision with rho_0 = r^T D^-1 r  [per-tile partials]
+//            (FP64 iterate and arithmetic for the FP64 and complex paths; for the mixed real path
+//            the iterate x64 is double-float and the residual uses FP32 error-free transformations,
+//            as FP64 runs at ~1/64 of the FP32 rate on this GPU)
 //   K_decide stop, or start a cycle                                        [one thread per rhs]
 //   K_A/K_B  inner PCG/COCG on Ahat e = r (two kernels per iteration, see below)
 //   K_fold   x64 += scale * e
@@ -319,6 +322,163 @@ __global__ void __launch_bounds__(NTHREADS) k_residual(Geo g, Batch b, const X* 
   }
 }
 
+// The same pass for the mixed real path, whose iterate is double-float (df32). Per cell the
+// residual r = b - (d x_c - sum of the six neighbours) is a short signed sum; it is accumulated as
+// s + c: the high parts enter through TwoSum (exact), the low parts and the TwoSum errors through
+// the FP32 compensation c (the compensated summation of Ogita, Rump & Oishi), and each diagonal
+// product d x_c through the exact FMA product. The error of r is then ~n^2 2^-48 (|Ahat||x|)_i
+// (n <= 9 terms), far below the componentwise target, with FP32 operations only. r is rounded to
+// FP32 for the norm, the exponent bound and the inner right-hand side, which need no more.
+__global__ void __launch_bounds__(NTHREADS) k_residual_df(Geo g, Batch b, const LamCoefF* __restrict__ coef_f,
+                                                          const df32* __restrict__ x64, float* __restrict__ R) {
+  extern __shared__ __align__(16) unsigned char rsm_raw[];
+  __shared__ double sm[96];
+  __shared__ int smi[NWARPS];
+  TileCoord c = tile_coord(g);
+  if (b.status[c.rhs] != RHS_FINISHED) return;
+  // coefficients from the FP32 table (no FP64 arithmetic in this kernel): the diagonal of an
+  // interior cell and the face terms as double-floats
+  const LamCoefF cf = coef_f[rhs_lambda(b, c.rhs)];
+  DiagT<float> dgi;
+  dgi.dre = cf.dint;
+  dgi.dim = 0.f;
+#pragma unroll
+  for (int f = 0; f < 6; ++f) dgi.fa[f] = cf.fa[f];
+  const float idint = cf.idint;
+  const df32 d0{cf.dint, cf.dint_lo};
+  df32 dfa[6];
+#pragma unroll
+  for (int f = 0; f < 6; ++f) dfa[f] = df32{cf.fa[f], cf.fa_lo[f]};
+  const long long src = rhs_source(b, c.rhs);
+  const float pre = 1.f / (float)b.next[c.rhs];
+  const int etheta = bexp(b.theta[c.rhs]);
+  const df32* x = x64 + (size_t)c.rhs * g.N;
+  float* r = R + (size_t)c.rhs * g.N;
+  // the tile with a one-cell halo, [tz + 2][TY + 2][TX + 2], zeros outside the grid: every load of
+  // the block is issued before any cell is summed
+  df32* xs = reinterpret_cast<df32*>(rsm_raw);
+  constexpr int SX = TX + 2, SY = TY + 2;
+  const int i0 = c.i - (int)(threadIdx.x % TX), j0 = c.j - (int)(threadIdx.x / TX);
+  const int nzl = c.k1 - c.k0 + 2;
+  {
+    // thread t loads plane positions t and t + NTHREADS (< SX * SY) of every staged plane
+    const long long plane = (long long)g.nx * g.ny;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int q = threadIdx.x + u * NTHREADS;
+      if (q < SX * SY) {
+        const int ii = i0 - 1 + q % SX, jj = j0 - 1 + q / SX;
+        const bool inxy = ii >= 0 && ii < g.nx && jj >= 0 && jj < g.ny;
+        const df32* src_p = x + ((long long)(c.k0 - 1) * g.ny + jj) * g.nx + ii;
+        for (int kk = 0; kk < nzl; ++kk) {
+          const int kz = c.k0 - 1 + kk;
+          xs[kk * SX * SY + q] = (inxy && kz >= 0 && kz < g.nz) ? src_p[kk * plane] : df32{0.f, 0.f};
+        }
+      }
+    }
+  }
+  __syncthreads();
+  float rr = 0.f;
+  float acc[3] = {0.f, 0.f, 0.f};  // rho_0, (unused), ||r||^2
+  int om_e = -4096;
+  // s + c += coefficient * v, the product exact up to the coefficient's and v's low parts
+  auto add_prod = [](float& s, float& cc, df32 k, df32 v) {
+    float p, e, t;
+    two_prod(k.hi, v.hi, p, e);
+    e = fmaf(k.hi, v.lo, fmaf(k.lo, v.hi, e));
+    two_sum(s, p, s, t);
+    cc += t + e;
+  };
+  if (c.in) {
+    const int li = (int)(threadIdx.x % TX) + 1, lj = (int)(threadIdx.x / TX) + 1;
+    const int mxy = face_mask(g, c.i, c.j, 0) & 15;  // the x and y faces of the column
+    const long long plane = (long long)g.nx * g.ny;
+    long long id = vidx(g, c.i, c.j, c.k0);
+    for (int k = c.k0; k < c.k1; ++k, id += plane) {
+      const df32* xq = xs + ((k - c.k0 + 1) * SY + lj) * SX + li;
+      const df32 xc = xq[0];
+      const int m = mxy | ((k == 0) << 4) | ((k == g.nz - 1) << 5);
+      // A x = d x_c - sum of the neighbours, as s + cc (neighbours outside the grid are zero)
+      float s, cc;
+      two_prod(d0.hi, xc.hi, s, cc);
+      cc = fmaf(d0.hi, xc.lo, fmaf(d0.lo, xc.hi, cc));
+      if (m) {
+#pragma unroll
+        for (int f = 0; f < 6; ++f)
+          if (m & (1 << f)) add_prod(s, cc, dfa[f], xc);
+      }
+      if (b.dsig_d) add_prod(s, cc, df_from(dsig_at<double>(b, c.rhs, id, g.N)), xc);
+      float amax = 0.f;  // largest |neighbour|: the denominator's exponent comes from it once
+      auto sub_nb = [&](df32 v) {
+        float t;
+        two_sum(s, -v.hi, s, t);
+        cc += t - v.lo;
+        amax = fmaxf(amax, fabsf(v.hi));
+      };
+      sub_nb(xq[-SX * SY]);
+      sub_nb(xq[SX * SY]);
+      sub_nb(xq[-1]);
+      sub_nb(xq[1]);
+      sub_nb(xq[-SX]);
+      sub_nb(xq[SX]);
+      // r = b - A x
+      float rh = -s, rl = -cc;
+      if (id == src) {
+        float t;
+        two_sum(1.f, rh, rh, t);
+        rl += t;
+      }
+      const float rf = rh + rl;
+      rr = fmaf(rf, rf, rr);
+      int ed = max(etheta, bexp_f(amax));
+      const int ec = bexp(xc);
+      ed = max(ed, ec ? ec + 2 : 0);
+      if (id == src) ed = max(ed, 1023);
+      const int er = bexp_f(rf);
+      if (er) om_e = max(om_e, ed ? er + 1 - ed : 4096);
+      const float rv = rf * pre;
+      r[id] = rv;
+      const float dinv = (m || b.dsig_f) ? 1.f / (diag_at<float>(dgi, m) + (b.dsig_f ? dsig_at<float>(b, c.rhs, id, g.N) : 0.f))
+                                         : idint;
+      acc[0] = fmaf(rv * dinv, rv, acc[0]);
+      acc[2] = fmaf(rv, rv, acc[2]);
+    }
+  }
+  // block sums in FP32 (each partial needs only ~1e-7 relative accuracy; the FP64 pipe is slow on
+  // this GPU), one conversion per partial; the per-field sums over tiles stay FP64
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float v3[3] = {rr, acc[0], acc[2]};
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v3[q] += __shfl_down_sync(0xffffffffu, v3[q], o);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) om_e = max(om_e, __shfl_down_sync(0xffffffffu, om_e, o));
+  float* smf = reinterpret_cast<float*>(sm);
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) smf[q * NWARPS + warp] = v3[q];
+    smi[warp] = om_e;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t3[3] = {0.f, 0.f, 0.f};
+    int mx = -4096;
+    for (int w = 0; w < NWARPS; ++w) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) t3[q] += smf[q * NWARPS + w];
+      mx = max(mx, smi[w]);
+    }
+    const int T_ = g.ntiles;
+    double* pb = b.part + (size_t)c.rhs * part_stride(T_);
+    pb[8 * T_ + 2 * c.tile] = (double)t3[0];
+    pb[8 * T_ + 2 * c.tile + 1] = (mx <= -4096) ? 0.0 : (mx >= 4096 ? INFINITY : ldexp(1.0, mx));
+    pb[2 * c.tile] = (double)t3[1];   // rho parity 0
+    pb[2 * c.tile + 1] = 0.0;
+    pb[4 * T_ + c.tile] = (double)t3[2];  // ||r||^2 parity 0
+  }
+}
+
 // Floor of the componentwise test: theta = cw_floor * sigma * min |x| over the field's partner
 // optode cells (detectors for a source field, sources for a detector field).
 template <typename X>
@@ -333,7 +493,10 @@ __global__ void k_theta(Geo g, Batch b, const X* __restrict__ x64, const int* __
   if (b.cw_floor > 0.0 && np > 0) {
     const X* x = x64 + (size_t)rhs * g.N;
     double mn = INFINITY;
-    for (int q = 0; q < np; ++q) mn = fmin(mn, sqrt(Traits<X>::abs2(x[optode[p0 + q]])));
+    for (int q = 0; q < np; ++q) {
+      if constexpr (std::is_same<X, df32>::value) mn = fmin(mn, fabs((double)x[optode[p0 + q]].hi));
+      else mn = fmin(mn, sqrt(Traits<X>::abs2(x[optode[p0 + q]])));
+    }
     th = b.cw_floor * b.coef[rhs_lambda(b, rhs)].sigma_re * mn;
   }
   b.theta[rhs] = th;
@@ -941,9 +1104,20 @@ __global__ void k_fold(Geo g, Batch b, X* __restrict__ x64, const T* __restrict_
     const double s = b.scale[rhs];
     X* x = x64 + (size_t)rhs * g.N;
     const T* e = E + (size_t)rhs * g.N;
-    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < g.N; v += (long long)gridDim.x * blockDim.x) {
-      T ev = e[v];
-      x[v] = x[v] + Traits<X>::from(s * Traits<T>::re(ev), s * Traits<T>::im(ev));
+    if constexpr (std::is_same<X, df32>::value) {
+      // x += s e with the product exact up to s's low part and the sum accurate (double-float)
+      const df32 sd = df_from(s);
+      for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < g.N; v += (long long)gridDim.x * blockDim.x) {
+        float p, q;
+        two_prod(sd.hi, e[v], p, q);
+        q = fmaf(sd.lo, e[v], q);
+        x[v] = df_add(x[v], fast_two_sum(p, q));
+      }
+    } else {
+      for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < g.N; v += (long long)gridDim.x * blockDim.x) {
+        T ev = e[v];
+        x[v] = x[v] + Traits<X>::from(s * Traits<T>::re(ev), s * Traits<T>::im(ev));
+      }
     }
   }
 }
@@ -957,9 +1131,17 @@ __global__ void k_output(Geo g, Batch b, const X* __restrict__ x64, O* __restric
     const double sc = b.coef[b.lam0 + a].inv_Dh;
     O* out = (f < n_src) ? phi_src + ((size_t)a * n_src + f) * g.N : phi_det + ((size_t)a * n_det + (f - n_src)) * g.N;
     const X* x = x64 + (size_t)rhs * g.N;
-    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < g.N; v += (long long)gridDim.x * blockDim.x) {
-      X xv = x[v];
-      out[v] = Traits<O>::from(sc * Traits<X>::re(xv), sc * Traits<X>::im(xv));
+    if constexpr (std::is_same<X, df32>::value) {
+      const float scf = (float)sc;
+      for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < g.N; v += (long long)gridDim.x * blockDim.x) {
+        const df32 xv = x[v];
+        out[v] = (O)((xv.hi + xv.lo) * scf);
+      }
+    } else {
+      for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < g.N; v += (long long)gridDim.x * blockDim.x) {
+        X xv = x[v];
+        out[v] = Traits<O>::from(sc * Traits<X>::re(xv), sc * Traits<X>::im(xv));
+      }
     }
   }
 }
@@ -1217,14 +1399,15 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
   const unsigned nblk = (unsigned)((long long)b.nrhs * g.ntiles);
   const dim3 blk(NTHREADS);
 
-  if constexpr (std::is_same<X, double>::value) {
+  if constexpr (std::is_same<X, double>::value || std::is_same<X, df32>::value) {
+    constexpr bool df = std::is_same<X, df32>::value;
     if (ctx->deflation_k > 0) {
       // Galerkin initial guess from the recycled subspace (shared by all wavelengths)
-      int rc = deflate_initial_guess(ctx, lam0, b.f_begin, b.nf, b.nrhs, x64);
+      int rc = deflate_initial_guess(ctx, lam0, b.f_begin, b.nf, b.nrhs, x64, df);
       if (rc) return rc;
     } else if (ctx->sg_m > 0) {
       // Galerkin initial guess from each optode's Krylov space of the mean-shift operator
-      int rc = shift_initial_guess(ctx, lam0, b.f_begin, b.nf, b.nrhs, x64);
+      int rc = shift_initial_guess(ctx, lam0, b.f_begin, b.nf, b.nrhs, x64, df);
       if (rc) return rc;
     } else {
       HYDOT_CUDA_TRY(ctx, cudaMemsetAsync(x64, 0, sizeof(X) * (size_t)b.nrhs * g.N, s));
@@ -1233,6 +1416,9 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
     HYDOT_CUDA_TRY(ctx, cudaMemsetAsync(x64, 0, sizeof(X) * (size_t)b.nrhs * g.N, s));
   }
   HYDOT_CUDA_TRY(ctx, cudaMemsetAsync(b.err, 0, sizeof(int), s));
+  if constexpr (std::is_same<X, df32>::value)  // the residual's halo tile: up to 18 x 10 x 34 double-floats
+    HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(k_residual_df, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(sizeof(df32) * (g.tz + 2) * (TY + 2) * (TX + 2))));
   k_reset<<<(b.nrhs + 255) / 256, 256, 0, s>>>(b);
   ++ctx->launches;
   HYDOT_CUDA_TRY(ctx, cudaGetLastError());
@@ -1245,7 +1431,9 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
       ++ctx->launches;
     }
     cudaEvent_t t_res = timer_begin(ctx);
-    k_residual<T, X><<<nblk, blk, 0, s>>>(g, b, x64, R);
+    if constexpr (std::is_same<X, df32>::value)
+      k_residual_df<<<nblk, blk, sizeof(df32) * (g.tz + 2) * (TY + 2) * (TX + 2), s>>>(g, b, ctx->d_coef_f, x64, R);
+    else k_residual<T, X><<<nblk, blk, 0, s>>>(g, b, x64, R);
     ++ctx->launches;
     timer_end(ctx, t_res, HYDOT_KERNEL_RESIDUAL,
               (double)(cycle == 0 ? b.nrhs : prev_active) * (double)g.N * (double)(sizeof(X) + sizeof(T)));
@@ -1588,7 +1776,7 @@ int get_tuning_impl(const hydot_ctx* ctx, int* variant, int* planes, int* buffer
 int solve_fields_impl(hydot_ctx* ctx, int lam0, int nlam, void* phi_src, void* phi_det, hydot_stats* st) {
   const bool mixed = ctx->precision == HYDOT_MIXED;
   if (!ctx->cplx) {
-    if (mixed) return run_solve<float, double, float>(ctx, lam0, nlam, (float*)phi_src, (float*)phi_det, st);
+    if (mixed) return run_solve<float, df32, float>(ctx, lam0, nlam, (float*)phi_src, (float*)phi_det, st);
     return run_solve<double, double, double>(ctx, lam0, nlam, (double*)phi_src, (double*)phi_det, st);
   }
   using cf = cpx<float>;
