@@ -45,8 +45,9 @@ CW_FLOOR = 100.0
 WORKLOAD = ("cw-mixed-64x64x48: 64x64x48 grid (h=2 mm), 32 sources + 32 detectors, 128 wavelengths "
             "(8,192 field solves), explicit FP32 Born rows 131,072 x 786,432 in row chunks, J x and J^T r")
 KERNEL_NAMES = {"dir": "k_dir_roll (inner PCG pass 1)", "update": "k_update_roll (inner PCG pass 2)",
-                "residual": "k_residual (FP64 residual)", "born_rows": "k_born_rows (Born-row assembly)",
-                "apply": "k_apply_partial+reduce (J x)", "apply_T": "k_apply_T_partial+reduce (J^T y)",
+                "residual": "k_residual_df (residual of the double-float iterate)",
+                "born_rows": "k_born_rows (Born-row assembly)",
+                "apply": "k_apply_partial+reduce (J x)", "apply_T": "k_transpose_y+k_apply_T_tile+reduce (J^T y)",
                 "sketch_range": "k_range_ws (tensor-core Y = J Omega)",
                 "sketch_project": "k_project_ws (tensor-core B^T += J^T Q)"}
 # DRAM bytes (read + write, ncu) per algorithmic byte, from the captures summarised under profiles/

@@ -1105,14 +1105,31 @@ __global__ void k_fold(Geo g, Batch b, X* __restrict__ x64, const T* __restrict_
     X* x = x64 + (size_t)rhs * g.N;
     const T* e = E + (size_t)rhs * g.N;
     if constexpr (std::is_same<X, df32>::value) {
-      // x += s e with the product exact up to s's low part and the sum accurate (double-float)
+      // x += s e with the product exact up to s's low part and the sum accurate (double-float);
+      // four independent cells per thread and pass keep the dependent TwoSum chains overlapped
       const df32 sd = df_from(s);
-      for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < g.N; v += (long long)gridDim.x * blockDim.x) {
+      const long long step = (long long)gridDim.x * blockDim.x;
+      auto upd = [&](long long v) {
         float p, q;
         two_prod(sd.hi, e[v], p, q);
         q = fmaf(sd.lo, e[v], q);
         x[v] = df_add(x[v], fast_two_sum(p, q));
+      };
+      long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+      for (; v + 3 * step < g.N; v += 4 * step) {
+        float p[4], q[4];
+        df32 xv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float ev = e[v + u * step];
+          xv[u] = x[v + u * step];
+          two_prod(sd.hi, ev, p[u], q[u]);
+          q[u] = fmaf(sd.lo, ev, q[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) x[v + u * step] = df_add(xv[u], fast_two_sum(p[u], q[u]));
       }
+      for (; v < g.N; v += step) upd(v);
     } else {
       for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < g.N; v += (long long)gridDim.x * blockDim.x) {
         T ev = e[v];
@@ -1529,7 +1546,7 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
     }
     // any field still marked INNER hit the per-cycle cap: finish it
     {
-      dim3 fg((unsigned)std::min<long long>((g.N + 255) / 256, 1024), (unsigned)std::min(b.nrhs, 65535));
+      dim3 fg((unsigned)std::min<long long>((g.N + 2047) / 2048, 1024), (unsigned)std::min(b.nrhs, 65535));  // 8 cells per thread
       // fields that were still iterating when the cap hit are FINISHED by the next k_dir; run it
       k_dir<T><<<nblk, blk, 0, s>>>(g, b, MAX_INNER_PER_CYCLE, R, P[0], P[1]);
       ++ctx->launches;
@@ -1539,7 +1556,7 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
     }
   }
   {
-    dim3 fg((unsigned)std::min<long long>((g.N + 255) / 256, 1024), (unsigned)std::min(b.nrhs, 65535));
+    dim3 fg((unsigned)std::min<long long>((g.N + 2047) / 2048, 1024), (unsigned)std::min(b.nrhs, 65535));  // 8 cells per thread
     k_output<X, O><<<fg, 256, 0, s>>>(g, b, x64, phi_src, phi_det, ctx->n_src, ctx->n_det);
     ++ctx->launches;
     HYDOT_CUDA_TRY(ctx, cudaGetLastError());
