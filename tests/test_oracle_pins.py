@@ -468,3 +468,106 @@ def test_shift_guess_energy_error_decreases_with_m():
             errs.append(float(d @ (A @ d)))
         assert all(b <= a * (1 + 1e-9) for a, b in zip(errs, errs[1:]))
         assert errs[-1] < 1e-3 * errs[0]
+
+
+# --------------------------------------------------------------------------- PaLS reconstruction
+def _pals_case(seed=75, n_basis=2):
+    from oracle import recon
+
+    p = workloads.make_problem(workloads.Grid(14, 12, 10, 2.0), 3, 3, 4, seed=seed, geometry="transmission",
+                               margin=2)
+    X = recon.voxel_centres(p.grid)
+    rng = np.random.default_rng(seed)
+    L = np.array([p.grid.nx, p.grid.ny, p.grid.nz]) * p.grid.h
+    chi = L * (0.35 + 0.3 * rng.random((n_basis, 3)))
+    ptrue = np.concatenate([1.0 + 0.5 * rng.random(n_basis), 1.0 / (8.0 + 4.0 * rng.random(n_basis)),
+                            chi[:, 0], chi[:, 1], chi[:, 2]])
+    return p, X, ptrue
+
+
+def test_pals_jacobian_matches_central_differences():
+    from oracle import recon
+
+    _, X, p0 = _pals_case(n_basis=3)
+    model = recon.PalsModel()
+    mu, dmu = recon.shape_jacobian(p0, X, model)
+    assert np.abs(mu - recon.shape(p0, X, model)).max() == 0.0
+    for q in range(p0.size):
+        step = 1e-6 * max(1.0, abs(p0[q]))
+        e = np.zeros_like(p0)
+        e[q] = step
+        fd = (recon.shape(p0 + e, X, model) - recon.shape(p0 - e, X, model)) / (2 * step)
+        assert np.abs(fd - dmu[:, q]).max() <= 1e-5 * max(1e-12, np.abs(dmu[:, q]).max()) + 1e-9
+
+
+def test_wendland_function_is_c2_with_compact_support():
+    from oracle import recon
+
+    t = np.array([0.0, 1.0, 1.5])
+    assert np.allclose(recon.wendland(t), [1.0, 0.0, 0.0])
+    assert np.allclose(recon.wendland_d(t), [0.0, 0.0, 0.0])
+    # the derivative is the difference quotient of the function, and the second derivative is
+    # continuous across the support radius (zero on both sides of t = 1)
+    h = 1e-5
+    for t0 in (0.2, 0.5, 0.9):
+        assert abs((recon.wendland(t0 + h) - recon.wendland(t0 - h)) / (2 * h) - recon.wendland_d(t0)) < 1e-8
+    d2 = lambda t0: (recon.wendland_d(t0 + h) - recon.wendland_d(t0 - h)) / (2 * h)
+    assert abs(d2(1.0 - 1e-3)) < 1e-3 and abs(d2(1.0 + 1e-3)) == 0.0
+
+
+def test_reduced_residual_equals_the_truncated_operator_residual():
+    """|y - U S V^T (c (x) mu)|^2 computed directly equals (|y|^2 - |U^T y|^2) + |U^T y - S M c|^2
+    of the rank-r formulation, for a rank below the number of measurements."""
+    from oracle import born, recon
+    from oracle import solve as osolve
+
+    p, X, ptrue = _pals_case()
+    rs, rd = osolve.fields_splu(p)
+    J = born.born_matrix(p, rs, rd)
+    Uf, Sf, Vt = np.linalg.svd(J, full_matrices=False)
+    r = 20
+    U, S, V = Uf[:, :r], Sf[:r], Vt[:r].T
+    N, nc = p.grid.N, p.n_chrom
+    model = recon.PalsModel()
+    c = np.array([0.05, 0.02, 0.03, 0.01])
+    y = workloads.gaussian(76, J.shape[0])
+    mu, dmu = recon.shape_jacobian(ptrue, X, model)
+    Vc = V.reshape(nc, N, r)
+    A = recon.project(Vc, mu, dmu)
+    _, e, _ = recon.reduced_terms(A, S, U.T @ y, c)
+    direct = y - U @ (S * (V.T @ np.kron(c, mu)))
+    yh = U.T @ y
+    assert abs((y @ y - yh @ yh + e @ e) - direct @ direct) <= 1e-10 * (y @ y)
+
+
+def test_noiseless_reconstruction_drives_the_residual_to_zero():
+    from oracle import born, recon
+    from oracle import solve as osolve
+
+    p, X, ptrue = _pals_case()
+    rs, rd = osolve.fields_splu(p)
+    J = born.born_matrix(p, rs, rd)
+    U, S, Vt = np.linalg.svd(J, full_matrices=False)
+    N, nc = p.grid.N, p.n_chrom
+    model = recon.PalsModel()
+    c = np.array([0.05, 0.02, 0.03, 0.01])
+    mu_true = recon.shape(ptrue, X, model)
+    y = J @ np.kron(c, mu_true)
+    rng = np.random.default_rng(77)
+    p0 = ptrue + np.concatenate([0.05 * rng.standard_normal(2), 0.01 * rng.standard_normal(2),
+                                 0.8 * rng.standard_normal(6)])
+    pr, cr, hist, _ = recon.reconstruct(Vt.T.reshape(nc, N, -1), U.T @ y, float(y @ y), S, p0, X, model, c,
+                                        noise_norm=0.0, fix_c=True, max_outer=3, max_inner=100)
+    assert hist[-1] <= 1e-3 * hist[0]
+    assert recon.dice(mu_true, recon.shape(pr, X, model)) >= 0.9
+
+
+def test_dice_and_l2_definitions():
+    from oracle import recon
+
+    a = np.array([1.0, 1.0, 0.0, 0.0])
+    b = np.array([1.0, 0.0, 1.0, 0.0])
+    assert recon.dice(a, a) == 1.0 and recon.rel_l2(a, a) == 0.0
+    assert recon.dice(a, b) == 0.5
+    assert recon.dice(a, 1.0 - a) == 0.0
+    assert abs(recon.rel_l2(a, b) - 1.0) < 1e-15
