@@ -238,6 +238,62 @@ int hydot_set_shift_guess(hydot_ctx* ctx, int m);
  * bases are built. Asynchronous on the context's stream. */
 int hydot_shift_guess_fields(hydot_ctx* ctx, int lam0, int nlam, void* phi_src, void* phi_det);
 
+/* Shape reconstruction with parametric level sets (Section 5: eqn:pals, eqn:minimization,
+ * Algorithm alg:opt) on a compressed Born operator J ~ U diag(S) V^T (U with orthonormal columns,
+ * e.g. from hydot_sketch_factor or the recursive compression).
+ * Shape: mu(r) = H_eps(phi(r) - tau), phi(r) = sum_k alpha_k psi(beta_k |r - chi_k|_nu), |v|_nu =
+ * sqrt(|v|^2 + nu^2), psi(t) = (1 - t)_+^4 (4t + 1) (Wendland's compactly supported C2 function),
+ * H_eps(t) = 1/2 + arctan(pi t / eps) / pi; the points r are the voxel centres ((i + 1/2) h, ...)
+ * in mm. Parameters p = [alpha (n), beta (n), chi_x (n), chi_y (n), chi_z (n)], n = n_basis in 1..8,
+ * host FP64 [5 n]. Measurements y = sum_c c_c E_c H mu: J applied to the chromophore-major vector
+ * (c_0 mu, c_1 mu, ...). Errors: HYDOT_ERR_ARG for a bad size, pointer or model constant. */
+typedef struct {
+  double tau, eps, nu;   /* level, width of the smoothed Heaviside, smoothing of |r| (mm) */
+  double gamma;          /* discrepancy factor: stop when |y - D(p) c| <= gamma * noise_norm */
+  double noise_norm;     /* |eta|, the norm of the measurement noise (0: run to the iteration limits) */
+  double lm_nu0;         /* initial Levenberg-Marquardt damping, relative to max diag(J^T J) */
+  int max_outer;         /* alternations between the c step and the p steps */
+  int max_inner;         /* Levenberg-Marquardt trial steps per alternation */
+  int fix_c;             /* 1: c is known and kept (shape only), 0: c is estimated too */
+} hydot_pals_options;
+
+typedef struct {
+  int evaluations;       /* shape + projection evaluations */
+  int accepted;          /* accepted Levenberg-Marquardt steps */
+  double residual0;      /* |y - D(p0) c0| */
+  double residual;       /* |y - D(p) c| at the returned p, c */
+} hydot_pals_result;
+
+/* Algorithm alg:opt: alternate the linear least-squares step for c (skipped with fix_c) and
+ * Levenberg-Marquardt steps (J^T J + nu I) dp = -J^T eps on p (nu divided by 3 after an accepted
+ * step, multiplied by 4 after a rejected one), until the residual meets the discrepancy principle or
+ * the iteration limits, or an alternation stops reducing it. All in the rank coordinates:
+ * |y - D c|^2 = (|y|^2 - |U^T y|^2) + |U^T y - S M c|^2 with M[:, c] = V_c^T mu(p), and the
+ * Jacobian -S sum_c c_c V_c^T dmu/dp; mu and dmu/dp come from a kernel over the voxels, the products
+ * from tall-skinny FP32 kernels with FP64 sums, the small systems are solved on the host (FP64).
+ * U: DEVICE FP32 [rows][rank] (row stride ldU); S: HOST FP64 [rank]; V: DEVICE FP32
+ * [n_chrom * N][rank] (row stride ldV), rows chromophore-major; y: DEVICE FP32 [rows];
+ * p: HOST [5 n_basis] initial guess in, result out; c: HOST [n_chrom] initial (or known)
+ * concentrations in, result out; res: may be NULL. Synchronous. */
+int hydot_pals_reconstruct(hydot_ctx* ctx, const float* U, long long ldU, long long rows, const double* S,
+                           const float* V, long long ldV, int rank, const float* y, int n_basis, double* p,
+                           double* c, const hydot_pals_options* opt, hydot_pals_result* res);
+
+/* mu(r) at every voxel for the parameters p: mu DEVICE FP32 [N]. Synchronous. */
+int hydot_pals_shape(hydot_ctx* ctx, int n_basis, const double* p, double tau, double eps, double nu, float* mu);
+
+/* One evaluation of the reconstruction: A[c][k][q] = sum_x V[(c, x)][k] F[x][q] with
+ * F = [mu, dmu/dp] (q < 1 + 5 n_basis), for the tests and for inspection. V as above; A HOST FP64
+ * [n_chrom][rank][1 + 5 n_basis]. Synchronous. */
+int hydot_pals_project(hydot_ctx* ctx, const float* V, long long ldV, int rank, int n_basis, const double* p,
+                       double tau, double eps, double nu, double* A);
+
+/* The metrics of Section 6.2 between a true shape mu and a recovered one (DEVICE FP32 [N]):
+ * relative L2 error |mu - mu_hat| / |mu| and the Dice coefficient 2 |A and B| / (|A| + |B|) of the
+ * voxel sets where each exceeds `level` (1 when both are empty). Outputs may be NULL. Synchronous. */
+int hydot_shape_compare(hydot_ctx* ctx, const float* mu, const float* mu_hat, double level, double* rel_l2,
+                        double* dice);
+
 /* Failure-path self-test (no counterpart in the paper): one thread waits on a shared-memory
  * mbarrier that nothing arrives at, through the same bounded poll loop the pipelined kernels use
  * for their TMA and tensor-core waits, but with `polls` polls (1..2^22) instead of their limit;

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libhydot.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["api.cu", "solver.cu", "born.cu", "deflation.cu", "sketch.cu", "shiftguess.cu"]
+SOURCES = ["api.cu", "solver.cu", "born.cu", "deflation.cu", "sketch.cu", "shiftguess.cu", "recon.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 

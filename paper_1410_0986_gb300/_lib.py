@@ -27,6 +27,7 @@ EXPORTS = ("hydot_version", "hydot_setup", "hydot_set_stream", "hydot_solve_fiel
            "hydot_sketch_factor", "hydot_set_kernel_timing",
            "hydot_kernel_stats", "hydot_kernel_launches", "hydot_get_tuning", "hydot_set_absorption",
            "hydot_wait_selftest", "hydot_set_shift_guess", "hydot_shift_guess_fields",
+           "hydot_pals_reconstruct", "hydot_pals_shape", "hydot_pals_project", "hydot_shape_compare",
            "hydot_last_error", "hydot_destroy")
 ROLL_VARIANTS = 4  # HYDOT_ROLL_VARIANTS
 KERNELS = {"dir": 0, "update": 1, "residual": 2, "born_rows": 3, "apply": 4, "apply_T": 5, "sketch_range": 6,
@@ -55,6 +56,19 @@ class Stats(C.Structure):
         ("n_fields", C.c_int), ("n_not_converged", C.c_int), ("iters_max", C.c_int),
         ("iters_mean", C.c_double), ("cycles_max", C.c_int), ("resid_max", C.c_double), ("cw_max", C.c_double),
     ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class PalsOptions(C.Structure):
+    _fields_ = [("tau", C.c_double), ("eps", C.c_double), ("nu", C.c_double), ("gamma", C.c_double),
+                ("noise_norm", C.c_double), ("lm_nu0", C.c_double), ("max_outer", C.c_int), ("max_inner", C.c_int),
+                ("fix_c", C.c_int)]
+
+
+class PalsResult(C.Structure):
+    _fields_ = [("evaluations", C.c_int), ("accepted", C.c_int), ("residual0", C.c_double), ("residual", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -124,6 +138,17 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.hydot_wait_selftest.restype = C.c_int
     lib.hydot_set_shift_guess.argtypes = [vp, C.c_int]
     lib.hydot_set_shift_guess.restype = C.c_int
+    dp = C.POINTER(C.c_double)
+    lib.hydot_pals_reconstruct.argtypes = [vp, vp, C.c_longlong, C.c_longlong, dp, vp, C.c_longlong, C.c_int, vp,
+                                           C.c_int, dp, dp, C.POINTER(PalsOptions), C.POINTER(PalsResult)]
+    lib.hydot_pals_reconstruct.restype = C.c_int
+    lib.hydot_pals_shape.argtypes = [vp, C.c_int, dp, C.c_double, C.c_double, C.c_double, vp]
+    lib.hydot_pals_shape.restype = C.c_int
+    lib.hydot_pals_project.argtypes = [vp, vp, C.c_longlong, C.c_int, C.c_int, dp, C.c_double, C.c_double,
+                                       C.c_double, dp]
+    lib.hydot_pals_project.restype = C.c_int
+    lib.hydot_shape_compare.argtypes = [vp, vp, vp, C.c_double, dp, dp]
+    lib.hydot_shape_compare.restype = C.c_int
     lib.hydot_shift_guess_fields.argtypes = [vp, C.c_int, C.c_int, vp, vp]
     lib.hydot_shift_guess_fields.restype = C.c_int
     lib.hydot_last_error.argtypes = [vp]

@@ -305,6 +305,73 @@ class Context:
                                                       C.c_void_p(pd.data_ptr())))
         return ps, pd
 
+    # ------------------------------------------------------------------ reconstruction (PaLS)
+    @staticmethod
+    def _host_f64(a, n=None):
+        v = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+        if n is not None and v.size != n:
+            raise ValueError(f"expected {n} values, got {v.size}")
+        return v
+
+    def pals_shape(self, n_basis: int, p, tau=0.5, eps=0.1, nu=0.02) -> torch.Tensor:
+        """hydot_pals_shape: mu [N] (FP32, device) of the parameters p [5 n_basis]."""
+        pv = self._host_f64(p, 5 * n_basis)
+        mu = torch.empty(self.N, dtype=torch.float32, device="cuda")
+        self._stream()
+        self._check(self.lib.hydot_pals_shape(self._ctx, int(n_basis), pv.ctypes.data_as(C.POINTER(C.c_double)),
+                                              float(tau), float(eps), float(nu), C.c_void_p(mu.data_ptr())))
+        return mu
+
+    def pals_project(self, V: torch.Tensor, rank: int, n_basis: int, p, tau=0.5, eps=0.1, nu=0.02) -> np.ndarray:
+        """hydot_pals_project: A [n_chrom][rank][1 + 5 n_basis] = V_c^T [mu, dmu/dp]."""
+        if V.dtype != torch.float32 or not V.is_cuda or V.dim() != 2 or V.shape[0] != self.n_chrom * self.N:
+            raise ValueError("V must be a CUDA float32 [n_chrom * N][>= rank] tensor")
+        pv = self._host_f64(p, 5 * n_basis)
+        A = np.empty((self.n_chrom, rank, 1 + 5 * n_basis))
+        self._stream()
+        self._check(self.lib.hydot_pals_project(self._ctx, C.c_void_p(V.data_ptr()), V.stride(0), int(rank), int(n_basis),
+                                                pv.ctypes.data_as(C.POINTER(C.c_double)), float(tau), float(eps),
+                                                float(nu), A.ctypes.data_as(C.POINTER(C.c_double))))
+        return A
+
+    def shape_compare(self, mu: torch.Tensor, mu_hat: torch.Tensor, level: float = 0.5):
+        """hydot_shape_compare: (relative L2 error, Dice coefficient)."""
+        for t in (mu, mu_hat):
+            if t.dtype != torch.float32 or not t.is_cuda or t.numel() != self.N or not t.is_contiguous():
+                raise ValueError("shapes must be contiguous CUDA float32 [N] tensors")
+        l2, dc = C.c_double(), C.c_double()
+        self._stream()
+        self._check(self.lib.hydot_shape_compare(self._ctx, C.c_void_p(mu.data_ptr()), C.c_void_p(mu_hat.data_ptr()),
+                                                 float(level), C.byref(l2), C.byref(dc)))
+        return l2.value, dc.value
+
+    def pals_reconstruct(self, U: torch.Tensor, S, V: torch.Tensor, y: torch.Tensor, n_basis: int, p0, c0, *,
+                         tau=0.5, eps=0.1, nu=0.02, gamma=1.05, noise_norm=0.0, lm_nu0=1e-2, max_outer=10,
+                         max_inner=20, fix_c=False):
+        """hydot_pals_reconstruct (Algorithm alg:opt). U [rows][r], V [n_chrom N][r], y [rows]: CUDA float32;
+        S [r], p0 [5 n_basis], c0 [n_chrom]: host. Returns (p, c, result dict)."""
+        r = len(S)
+        for t, rows in ((U, None), (V, self.n_chrom * self.N)):
+            if t.dtype != torch.float32 or not t.is_cuda or t.dim() != 2 or t.shape[1] < r or t.stride(1) != 1:
+                raise ValueError("U and V must be CUDA float32 matrices with >= rank columns, unit column stride")
+            if rows is not None and t.shape[0] != rows:
+                raise ValueError("V must have n_chrom * N rows")
+        if y.dtype != torch.float32 or not y.is_cuda or y.numel() != U.shape[0] or not y.is_contiguous():
+            raise ValueError("y must be a contiguous CUDA float32 vector with one entry per row of U")
+        Sv = self._host_f64(S, r)
+        pv = self._host_f64(p0, 5 * n_basis).copy()
+        cv = self._host_f64(c0, self.n_chrom).copy()
+        opt = _lib.PalsOptions(float(tau), float(eps), float(nu), float(gamma), float(noise_norm), float(lm_nu0),
+                               int(max_outer), int(max_inner), 1 if fix_c else 0)
+        res = _lib.PalsResult()
+        self._stream()
+        dptr = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+        self._check(self.lib.hydot_pals_reconstruct(self._ctx, C.c_void_p(U.data_ptr()), U.stride(0), U.shape[0],
+                                                    dptr(Sv), C.c_void_p(V.data_ptr()), V.stride(0), r,
+                                                    C.c_void_p(y.data_ptr()), int(n_basis), dptr(pv), dptr(cv),
+                                                    C.byref(opt), C.byref(res)))
+        return pv, cv, res.as_dict()
+
     def wait_selftest(self, polls: int = 1000) -> None:
         """hydot_wait_selftest: a bounded device wait that runs out; raises HydotError
         (HYDOT_ERR_TIMEOUT) as every pipelined kernel's timeout would."""

@@ -331,6 +331,30 @@ int hydot_set_absorption(hydot_ctx* ctx, const double* dc) {
   return hydot::set_absorption_impl(ctx, dc);
 }
 
+int hydot_pals_reconstruct(hydot_ctx* ctx, const float* U, long long ldU, long long rows, const double* S,
+                           const float* V, long long ldV, int rank, const float* y, int n_basis, double* p,
+                           double* c, const hydot_pals_options* opt, hydot_pals_result* res) {
+  if (!ctx) return HYDOT_ERR_ARG;
+  return hydot::pals_reconstruct_impl(ctx, U, ldU, rows, S, V, ldV, rank, y, n_basis, p, c, opt, res);
+}
+
+int hydot_pals_shape(hydot_ctx* ctx, int n_basis, const double* p, double tau, double eps, double nu, float* mu) {
+  if (!ctx) return HYDOT_ERR_ARG;
+  return hydot::pals_shape_impl(ctx, n_basis, p, tau, eps, nu, mu);
+}
+
+int hydot_pals_project(hydot_ctx* ctx, const float* V, long long ldV, int rank, int n_basis, const double* p,
+                       double tau, double eps, double nu, double* A) {
+  if (!ctx) return HYDOT_ERR_ARG;
+  return hydot::pals_project_impl(ctx, V, ldV, rank, n_basis, p, tau, eps, nu, A);
+}
+
+int hydot_shape_compare(hydot_ctx* ctx, const float* mu, const float* mu_hat, double level, double* rel_l2,
+                        double* dice) {
+  if (!ctx) return HYDOT_ERR_ARG;
+  return hydot::shape_compare_impl(ctx, mu, mu_hat, level, rel_l2, dice);
+}
+
 int hydot_set_shift_guess(hydot_ctx* ctx, int m) {
   if (!ctx) return HYDOT_ERR_ARG;
   return hydot::set_shift_guess_impl(ctx, m);

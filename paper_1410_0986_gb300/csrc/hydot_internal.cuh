@@ -329,10 +329,23 @@ int sketch_merge_impl(hydot_ctx* ctx, const float* U1, long long ldU1, long long
 int sketch_factor_impl(hydot_ctx* ctx, const float* Q, long long rows, long long ldQ, const float* Bt, long long nb,
                        long long ldB, int ncols, int rank, float* U, long long ldU, double* S, float* V, long long ldV);
 
+int tall_cross(hydot_ctx* ctx, const float* X, long long ldx, int nx, const float* Y, long long ldy, int ny,
+               long long rows, std::vector<double>& C);
+
 // deflation.cu
 int build_deflation(hydot_ctx* ctx);
 // x64: double [nrhs][N], or df32 (double-float) when df
 int deflate_initial_guess(hydot_ctx* ctx, int lam0, int f_begin, int nf, int nrhs, void* x64, bool df);
+
+// recon.cu
+int pals_reconstruct_impl(hydot_ctx* ctx, const float* U, long long ldU, long long rows, const double* S,
+                          const float* V, long long ldV, int rank, const float* y, int n_basis, double* p, double* c,
+                          const hydot_pals_options* opt, hydot_pals_result* res);
+int pals_shape_impl(hydot_ctx* ctx, int n_basis, const double* p, double tau, double eps, double nu, float* mu);
+int pals_project_impl(hydot_ctx* ctx, const float* V, long long ldV, int rank, int n_basis, const double* p, double tau,
+                      double eps, double nu, double* A);
+int shape_compare_impl(hydot_ctx* ctx, const float* mu, const float* mu_hat, double level, double* rel_l2,
+                       double* dice);
 
 // shiftguess.cu
 int set_shift_guess_impl(hydot_ctx* ctx, int m);

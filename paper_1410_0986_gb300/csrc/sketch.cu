@@ -1291,4 +1291,11 @@ int sketch_merge_impl(hydot_ctx* ctx, const float* U1, long long ldU1, long long
   return HYDOT_OK;
 }
 
+// C = X^T Y for tall-skinny FP32 X [rows][nx] and Y [rows][ny] (row strides ldx, ldy): FP32
+// products summed in FP64 across 64-row blocks and chunks, in a fixed order; C on the host [nx][ny].
+int tall_cross(hydot_ctx* ctx, const float* X, long long ldx, int nx, const float* Y, long long ldy, int ny,
+               long long rows, std::vector<double>& C) {
+  return cross(ctx, X, ldx, nx, Y, ldy, ny, rows, C);
+}
+
 }  // namespace hydot
