@@ -386,6 +386,8 @@ def run_ours(args):
         out["sketch"] = sketch_phase(hd, pk)
     if rank == 0 and not args.no_recon:
         out["reconstruction"] = recon_phase(hd)
+    if rank == 0 and not args.no_gradient:
+        out["gradient_workload"] = gradient_phase(hd, pk)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_entry(run_cpu_sample(0))
     if rank == 0:
@@ -493,6 +495,59 @@ def tree_phase(hd, p, n_lam, tol=1e-2, leaf_rank=100, merge_rank=160, n_probe=16
             lr = U.double() @ (torch.tensor(S, device="cuda") * (V.double().T @ X[:, k].double()))
             errs.append(float((jx - lr).norm() / jx.norm()))
         out["probe_error"] = {"median": float(np.median(errs)), "max": max(errs), "n": n_probe}
+    return out
+
+
+def gradient_phase(hd, pk, reps=5):
+    """The gradient workload (96x96x64, h = 1.5 mm, 24 + 24 optodes, 256 wavelengths): all 12,288
+    fields solved into resident arrays (29 GB), then full gradients g = J^T r and products J x over
+    all 256 wavelengths, timed with CUDA events; rates and fractions of the HBM roofline
+    ((n_src + n_det) x N x 4 B per wavelength read once)."""
+    import torch
+
+    import workloads
+
+    p = workloads.config(3)
+    ns, nd, nc, N, nl = p.n_src, p.n_det, p.n_chrom, p.grid.N, p.n_lambda
+    chunk = 16
+    out = {"workload": "96x96x64 (h=1.5 mm), 24+24 optodes, 256 wavelengths: fields resident (29 GB)"}
+    with hd.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=TOL_CW, cw_floor=CW_FLOOR,
+                                 max_lambda_per_call=chunk) as ctx:
+        ctx.set_shift_guess(40)
+        ps = torch.empty(nl, ns, N, dtype=torch.float32, device="cuda")
+        pd = torch.empty(nl, nd, N, dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        iters = []
+        for lam0 in range(0, nl, chunk):
+            _, _, st = ctx.solve_fields(lam0, chunk, ps[lam0:lam0 + chunk], pd[lam0:lam0 + chunk])
+            iters.append(st["iters_mean"])
+        torch.cuda.synchronize()
+        t_solve = time.perf_counter() - t0
+        out["solves"] = {"fields": nl * (ns + nd), "seconds": t_solve, "solves_per_s": nl * (ns + nd) / t_solve,
+                         "iters_mean": sum(iters) / len(iters)}
+        gen = torch.Generator(device="cuda").manual_seed(workloads.SEED_BASE + 310)
+        r = torch.randn(p.M, device="cuda", generator=gen)
+        x = torch.randn(nc * N, device="cuda", generator=gen)
+        g = torch.zeros(nc * N, device="cuda")
+        bytes_pass = float(nl) * (ns + nd) * N * 4
+        for name, fn in (("gradient", lambda: ctx.born_apply_T(ps, pd, 0, nl, r, g)),
+                         ("jx", lambda: ctx.born_apply(ps, pd, 0, nl, x))):
+            fn()
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(reps):
+                fn()
+            b.record()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / reps
+            out[name] = {"ms": ms, "per_s": 1e3 / ms, "hbm_gbs": bytes_pass / (ms / 1e3) / 1e9,
+                         "hbm_frac": bytes_pass / (ms / 1e3) / 1e9 / pk["hbm_gbs"]}
+        out["roofline_per_s"] = pk["hbm_gbs"] * 1e9 / bytes_pass
+        del ps, pd
+    torch.cuda.empty_cache()
     return out
 
 
@@ -815,6 +870,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sketch", action="store_true")
     ap.add_argument("--no-recon", action="store_true", help="skip the PaLS reconstruction experiments")
+    ap.add_argument("--no-gradient", action="store_true",
+                    help="skip the gradient workload (96x96x64, 256 wavelengths, fields resident)")
     ap.add_argument("--no-compare-fp64", dest="compare_fp64", action="store_false")
     ap.add_argument("--cpu-sample", type=int, default=None, help=argparse.SUPPRESS)
     ap.add_argument("--kernel-case", default=None, help="born_rows | solver | apply: small profiling case")
