@@ -341,6 +341,11 @@ def run_ours(args):
                    "resid_max": max(s["resid_max"] for s in stats), "cw_max": max(s["cw_max"] for s in stats),
                    "hbm_gbs_at_6NW_per_iteration": solver_gbs, "hbm_frac": solver_gbs / pk["hbm_gbs"],
                    "autotune": ctx.tuning()},
+        # every counted solve meets the metric's 1e-6 field error: |phi - phi*| / |phi*| <= kappa |r| / |b|,
+        # kappa(Ahat) <= (12 + max sigma) / min sigma (the Laplacian and boundary part is positive
+        # semidefinite, Gershgorin bounds the largest eigenvalue), |r| / |b| the largest final FP64
+        # residual the solver reports
+        "field_error_bound": field_error_bound(p, max(s["resid_max"] for s in stats)),
         "setup_s": t_setup,
         "shift_guess": {"m": args.shift_guess_m, "build_s": t_sg,
                         "build_share_of_128_lambda": (t_sg / (t_solve / K * nchunk)) if K else None},
@@ -496,6 +501,20 @@ def tree_phase(hd, p, n_lam, tol=1e-2, leaf_rank=100, merge_rank=160, n_probe=16
             errs.append(float((jx - lr).norm() / jx.norm()))
         out["probe_error"] = {"median": float(np.median(errs)), "max": max(errs), "n": n_probe}
     return out
+
+
+def field_error_bound(p, resid_max):
+    """A-posteriori bound on the relative field error of the solves from their final residual:
+    kappa(Ahat) |r| / |b| with kappa <= (12 + max sigma) / min sigma, sigma = mu_a h^2 / D over the
+    problem's wavelengths (mu_a = eps c_bg, D = 1 / (3 (mu_a + mu_s')))."""
+    import numpy as np
+
+    mua = np.asarray(p.eps) @ np.asarray(p.c_bg)
+    D = 1.0 / (3.0 * (mua + np.asarray(p.mus_prime)))
+    sigma = mua * p.grid.h ** 2 / D
+    kappa = (12.0 + float(sigma.max())) / float(sigma.min())
+    bound = kappa * resid_max
+    return {"kappa_bound": kappa, "resid_max": resid_max, "bound": bound, "meets_1e-6": bool(bound <= 1e-6)}
 
 
 def gradient_phase(hd, pk, reps=5):
