@@ -117,9 +117,15 @@ template <typename E, int U>
 __host__ __device__ constexpr size_t apply_buf_elems(int nc) {
   return (size_t)8 * U * ap_ld<E>() + (size_t)nc * AP_XC;
 }
+// Narrow tiles (U <= 6, FP32) need fewer registers: three blocks per SM with a two-stage ring
+// (three stages would not fit three blocks' shared memory); U = 8 keeps two blocks and three stages.
+template <typename E, int U>
+__host__ __device__ constexpr int apply_nbuf() { return (U <= 6 && sizeof(E) == 4) ? 2 : AP_NBUF; }
+template <typename E, int U>
+__host__ __device__ constexpr int apply_min_blocks() { return sizeof(E) == 4 ? (U <= 6 ? 3 : 2) : 1; }
 template <typename E, int U>
 size_t apply_smem_bytes(int nc) {
-  return std::max(sizeof(E) * AP_NBUF * apply_buf_elems<E, U>(nc), sizeof(E) * 8 * 1024);  // the reduction reuses it
+  return std::max(sizeof(E) * apply_nbuf<E, U>() * apply_buf_elems<E, U>(nc), sizeof(E) * 8 * 1024);  // the reduction reuses it
 }
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src, uint32_t src_bytes) {
@@ -138,7 +144,7 @@ template <int N_>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N_) : "memory"); }
 
 template <typename E, int U>
-__global__ void __launch_bounds__(256) k_apply_partial(const E* __restrict__ ps, const E* __restrict__ pd,
+__global__ void __launch_bounds__(256, apply_min_blocks<E, U>()) k_apply_partial(const E* __restrict__ ps, const E* __restrict__ pd,
                                                        const E* __restrict__ xin, const double* __restrict__ eps,
                                                        int lam0, int ns, int nd, int nc, long long N, int nxb, int spb,
                                                        int vec, E* __restrict__ part) {
@@ -222,15 +228,16 @@ __global__ void __launch_bounds__(256) k_apply_partial(const E* __restrict__ ps,
     for (int v = 0; v < U; ++v) acc[u][v] = 0;
   const long long nstage = min((long long)spb, (N - (long long)xb * spb * AP_XC + AP_XC - 1) / AP_XC);
   const size_t be = apply_buf_elems<E, U>(nc);  // elements per stage buffer
-  static_assert(AP_NBUF == 2 || AP_NBUF == 3, "two or three stage buffers");
+  constexpr int NB = apply_nbuf<E, U>();
+  static_assert(NB == 2 || NB == 3, "two or three stage buffers");
   load(0, buf0);
-  if (AP_NBUF == 3 && nstage > 1) load(1, buf0 + be);
+  if (NB == 3 && nstage > 1) load(1, buf0 + be);
   for (int st = 0; st < nstage; ++st) {
-    E* b = buf0 + (st % AP_NBUF) * be;
-    if (st + AP_NBUF - 1 < nstage) {
-      load(st + AP_NBUF - 1, buf0 + ((st + AP_NBUF - 1) % AP_NBUF) * be);
-      cp_async_wait<AP_NBUF - 1>();
-    } else if (AP_NBUF == 3 && st + 1 < nstage) {
+    E* b = buf0 + (st % NB) * be;
+    if (st + NB - 1 < nstage) {
+      load(st + NB - 1, buf0 + ((st + NB - 1) % NB) * be);
+      cp_async_wait<NB - 1>();
+    } else if (NB == 3 && st + 1 < nstage) {
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
