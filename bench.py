@@ -393,6 +393,8 @@ def run_ours(args):
         out["reconstruction"] = recon_phase(hd)
     if rank == 0 and not args.no_gradient:
         out["gradient_workload"] = gradient_phase(hd, pk)
+    if rank == 0 and not args.no_batch:
+        out["phantom_batch"] = batch_phase(hd)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_entry(run_cpu_sample(0))
     if rank == 0:
@@ -566,6 +568,50 @@ def gradient_phase(hd, pk, reps=5):
                          "hbm_frac": bytes_pass / (ms / 1e3) / 1e9 / pk["hbm_gbs"]}
         out["roofline_per_s"] = pk["hbm_gbs"] * 1e9 / bytes_pass
         del ps, pd
+    torch.cuda.empty_cache()
+    return out
+
+
+def batch_phase(hd, n_lam=4, reps=2):
+    """The uneven frequency-domain batch: six 100 MHz phantoms from 32x32x24 to 112x96x64, 16 + 16
+    optodes each, complex64 COCG with complex128 refinement, wavelengths 0..n_lam-1 of the 64 (the
+    per-wavelength work is the same for every wavelength). The six contexts solved one after another
+    on one stream against all six from one hydot_solve_batch call (one stream each); complex field
+    solves per second of each, best of reps after one untimed pass of each (the autotuner's samples)."""
+    import torch
+
+    import workloads
+
+    probs = workloads.config4_batch()
+    fields = sum(n_lam * (p.n_src + p.n_det) for p in probs)
+    out = {"workload": "6 phantoms (" + ", ".join(f"{p.grid.nx}x{p.grid.ny}x{p.grid.nz}" for p in probs)
+           + f"), 16+16 optodes, 100 MHz, wavelengths 0-{n_lam - 1}: {fields} complex field solves"}
+    ctxs = [hd.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=TOL_CW, max_lambda_per_call=n_lam)
+            for p in probs]
+    try:
+        def sequential():
+            return [c.solve_fields(0, n_lam)[2] for c in ctxs]
+
+        def batch():
+            return [o[2] for o in hd.solve_batch(ctxs, 0, n_lam)]
+
+        for name, fn in (("sequential", sequential), ("batch", batch)):
+            fn()
+            best, st = float("inf"), None
+            for _ in range(reps):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st = fn()
+                torch.cuda.synchronize()
+                best = min(best, time.perf_counter() - t0)
+            out[name] = {"seconds": best, "solves_per_s": fields / best,
+                         "not_converged": sum(s["n_not_converged"] for s in st),
+                         "iters_mean": [round(s["iters_mean"], 1) for s in st],
+                         "resid_max": max(s["resid_max"] for s in st)}
+        out["batch_speedup"] = out["sequential"]["seconds"] / out["batch"]["seconds"]
+    finally:
+        for c in ctxs:
+            c.close()
     torch.cuda.empty_cache()
     return out
 
@@ -891,6 +937,8 @@ def main():
     ap.add_argument("--no-recon", action="store_true", help="skip the PaLS reconstruction experiments")
     ap.add_argument("--no-gradient", action="store_true",
                     help="skip the gradient workload (96x96x64, 256 wavelengths, fields resident)")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the uneven batch of six 100 MHz phantoms (sequential against hydot_solve_batch)")
     ap.add_argument("--no-compare-fp64", dest="compare_fp64", action="store_false")
     ap.add_argument("--cpu-sample", type=int, default=None, help=argparse.SUPPRESS)
     ap.add_argument("--kernel-case", default=None, help="born_rows | solver | apply: small profiling case")

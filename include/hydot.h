@@ -129,6 +129,21 @@ int hydot_set_stream(hydot_ctx* ctx, void* stream);
 int hydot_solve_fields(hydot_ctx* ctx, int lam0, int nlam, void* phi_src, void* phi_det,
                        hydot_stats* st);
 
+/* Field solves of several contexts in one call: a batch of independent problems of uneven size
+ * (one phantom per context, e.g. the frequency-domain phantoms of Section 6), each solved as
+ * hydot_solve_fields(ctxs[i], lam0[i], nlam[i], phi_src[i], phi_det[i], &st[i]) would. The
+ * contexts run concurrently, each from its own host thread on the stream its context holds, so
+ * small grids overlap on the GPU instead of queueing behind one another; give every context its
+ * own stream (hydot_set_stream) or the work serialises on the shared one. All contexts must be
+ * on the caller's current device and distinct (a context repeated in the list is HYDOT_ERR_ARG:
+ * its workspace would be shared by two threads). phi_src / phi_det entries follow the rules of
+ * hydot_solve_fields; st and status may be NULL, else they receive n entries (status: each
+ * context's own return code, its message in hydot_last_error of that context). Synchronous.
+ * Returns the first error other than HYDOT_ERR_NOT_CONVERGED in list order, else
+ * HYDOT_ERR_NOT_CONVERGED when any field missed its tolerance, else HYDOT_OK. */
+int hydot_solve_batch(hydot_ctx* const* ctxs, int n, const int* lam0, const int* nlam, void* const* phi_src,
+                      void* const* phi_det, hydot_stats* st, int* status);
+
 /* Born rows [row0, row0+nrows) of the slice [lam0, lam0+nlam) into J (device, row-major,
  * leading dimension ldJ >= n_chrom*N elements): J[r-row0][c*N + x]. Continuous wave only
  * (HYDOT_ERR_STATE otherwise). Rows outside the slice are HYDOT_ERR_ARG. Asynchronous. */
@@ -366,7 +381,8 @@ int hydot_sketch_factor(hydot_ctx* ctx, const float* Q, long long rows, long lon
                         long long ldB, int ncols, int rank, float* U, long long ldU, double* S, float* V,
                         long long ldV);
 
-/* Last error message of ctx (or of the last failed hydot_setup when ctx is NULL). */
+/* Last error message of ctx; with ctx NULL, that of the calling thread's last failed call that
+ * has no context (hydot_setup, the context-free Born call). */
 const char* hydot_last_error(const hydot_ctx* ctx);
 
 /* Frees everything hydot_setup allocated. NULL is ignored. */

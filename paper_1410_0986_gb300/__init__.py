@@ -4,5 +4,5 @@ Born rows, implicit J x / J^T y. The compute runs in libhydot.so (CUDA, sm_103a)
 the C ABI in include/hydot.h; this package only marshals arguments.
 """
 from ._lib import EXPORTS, HYDOT_FP64, HYDOT_MIXED, LIB_PATH, load  # noqa: F401
-from .api import Context, HydotError  # noqa: F401
+from .api import Context, HydotError, solve_batch  # noqa: F401
 from .autograd import BornApply, born_apply  # noqa: F401

@@ -21,7 +21,8 @@ HYDOT_FP64 = 0
 HYDOT_MIXED = 1
 
 # Every symbol include/hydot.h declares.
-EXPORTS = ("hydot_version", "hydot_setup", "hydot_set_stream", "hydot_solve_fields", "hydot_born_assemble",
+EXPORTS = ("hydot_version", "hydot_setup", "hydot_set_stream", "hydot_solve_fields", "hydot_solve_batch",
+           "hydot_born_assemble",
            "hydot_born_apply", "hydot_born_apply_T", "hydot_born_apply_noalloc", "hydot_sketch_range",
            "hydot_sketch_project", "hydot_sketch_orthonormalize", "hydot_sketch_rank", "hydot_sketch_merge",
            "hydot_sketch_factor", "hydot_set_kernel_timing",
@@ -94,6 +95,9 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.hydot_set_stream.restype = C.c_int
     lib.hydot_solve_fields.argtypes = [vp, C.c_int, C.c_int, vp, vp, C.POINTER(Stats)]
     lib.hydot_solve_fields.restype = C.c_int
+    lib.hydot_solve_batch.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(vp),
+                                      C.POINTER(vp), C.POINTER(Stats), C.POINTER(C.c_int)]
+    lib.hydot_solve_batch.restype = C.c_int
     lib.hydot_born_assemble.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_longlong, C.c_longlong, vp, C.c_longlong]
     lib.hydot_born_assemble.restype = C.c_int
     lib.hydot_born_apply.argtypes = [vp, vp, vp, C.c_int, C.c_int, vp, vp]

@@ -403,3 +403,43 @@ class Context:
 
     def __exit__(self, *a):
         self.close()
+
+
+def solve_batch(contexts: Sequence[Context], lam0, nlam, *, raise_not_converged: bool = True):
+    """hydot_solve_batch: the fields of several contexts (one independent problem each, of any size)
+    from one call, each context on a CUDA stream of its own so their solves overlap on the GPU.
+    lam0 / nlam: one int for every context or one per context. Returns one (phi_src, phi_det, stats)
+    per context, in order."""
+    n = len(contexts)
+    lam0 = [int(lam0)] * n if np.isscalar(lam0) else [int(v) for v in lam0]
+    nlam = [int(nlam)] * n if np.isscalar(nlam) else [int(v) for v in nlam]
+    if len(lam0) != n or len(nlam) != n:
+        raise ValueError("lam0 and nlam need one entry per context")
+    if n == 0:
+        return []
+    lib = contexts[0].lib
+    cur = torch.cuda.current_stream()
+    outs, srcs, dets = [], (C.c_void_p * n)(), (C.c_void_p * n)()
+    for i, ctx in enumerate(contexts):
+        ps = ctx.empty(nlam[i], ctx.n_src, ctx.N) if ctx.n_src else None
+        pd = ctx.empty(nlam[i], ctx.n_det, ctx.N) if ctx.n_det else None
+        outs.append((ps, pd))
+        srcs[i], dets[i] = (None if ps is None else ps.data_ptr()), (None if pd is None else pd.data_ptr())
+        # a side stream per context, ordered after the work that made the outputs' memory free
+        s = getattr(ctx, "_batch_stream", None)
+        if s is None:
+            s = ctx._batch_stream = torch.cuda.Stream()
+        s.wait_stream(cur)
+        lib.hydot_set_stream(ctx._ctx, C.c_void_p(s.cuda_stream))
+    st, status = (_lib.Stats * n)(), (C.c_int * n)()
+    rc = lib.hydot_solve_batch((C.c_void_p * n)(*[c._ctx for c in contexts]), n, (C.c_int * n)(*lam0),
+                               (C.c_int * n)(*nlam), srcs, dets, st, status)
+    # every worker synchronised its stream before the call returned; later calls go back to torch's stream
+    for ctx in contexts:
+        ctx._stream()
+    if rc != 0 and not (rc == _lib.HYDOT_ERR_NOT_CONVERGED and not raise_not_converged):
+        bad = next((i for i in range(n) if status[i] == rc), None)
+        if bad is None:  # the lists themselves were rejected before any context ran
+            raise HydotError(rc, lib.hydot_last_error(None).decode())
+        raise HydotError(rc, f"context {bad}: {lib.hydot_last_error(contexts[bad]._ctx).decode()}")
+    return [(ps, pd, st[i].as_dict()) for i, (ps, pd) in enumerate(outs)]

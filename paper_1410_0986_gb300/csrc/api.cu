@@ -1,9 +1,13 @@
 // C ABI of libhydot: validation, per-wavelength coefficients, context lifetime, dispatch.
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <set>
 #include <string>
+#include <thread>
+#include <vector>
 
 #include "hydot_internal.cuh"
 
@@ -11,7 +15,7 @@ using hydot::fail;
 
 namespace {
 
-std::string g_setup_error;  // message of the last failed hydot_setup (no context to hold it)
+thread_local std::string g_setup_error;  // this thread's last failure with no context to hold it
 
 // Per-wavelength coefficients of the scaled operator (Section 2.1-2.2):
 //   mu_a = sum_c eps_c(lambda) c_bg,c            (eqn:perturbation for the background)
@@ -95,6 +99,20 @@ void free_all(hydot_ctx* c) {
 namespace hydot {
 // Message of a failed call that has no context (reported by hydot_last_error(NULL)).
 void set_context_free_error(const std::string& msg) { g_setup_error = msg; }
+
+cudaError_t raise_smem_limit_raw(const void* func, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> limit;  // (kernel, device) -> bytes set
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& cur = limit[{func, dev}];
+  if (bytes <= cur) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
+}
 
 cudaEvent_t timer_begin(hydot_ctx* ctx) {
   KernelTimer& t = ctx->timer;
@@ -188,6 +206,7 @@ int hydot_setup(const hydot_problem* p, void* stream, hydot_ctx** out) {
   }
   c->max_fields = (p->max_lambda_per_call > 0 ? p->max_lambda_per_call : p->n_lambda) * (p->n_src + p->n_det);
   c->stream = (cudaStream_t)stream;
+  cudaGetDevice(&c->device);
   compute_coefficients(c);
 
   auto bail = [&](int code) {
@@ -253,6 +272,54 @@ int hydot_solve_fields(hydot_ctx* ctx, int lam0, int nlam, void* phi_src, void* 
   if ((long long)nf * nlam > ctx->max_fields)
     return fail(ctx, HYDOT_ERR_ARG, "nlam exceeds max_lambda_per_call given to hydot_setup");
   return hydot::solve_fields_impl(ctx, lam0, nlam, phi_src, phi_det, st);
+}
+
+int hydot_solve_batch(hydot_ctx* const* ctxs, int n, const int* lam0, const int* nlam, void* const* phi_src,
+                      void* const* phi_det, hydot_stats* st, int* status) {
+  auto bad = [](const char* m) { g_setup_error = m; return (int)HYDOT_ERR_ARG; };
+  if (n < 0) return bad("batch size is negative");
+  if (n > 0 && (!ctxs || !lam0 || !nlam || !phi_src || !phi_det)) return bad("a batch list is NULL");
+  std::set<const hydot_ctx*> seen;
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]) return bad("a batch context is NULL");
+    if (!seen.insert(ctxs[i]).second) return bad("a context appears twice in the batch");
+  }
+  if (n == 0) return HYDOT_OK;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    g_setup_error = "cudaGetDevice failed";
+    return HYDOT_ERR_CUDA;
+  }
+  for (int i = 0; i < n; ++i)
+    if (ctxs[i]->device != dev) return fail(ctxs[i], HYDOT_ERR_ARG, "context is not on the caller's current device");
+  std::vector<int> rc(n, HYDOT_OK);
+  auto one = [&](int i) {
+    // a new host thread starts on device 0: adopt the caller's device before any CUDA call
+    if (cudaSetDevice(dev) != cudaSuccess) {
+      rc[i] = fail(ctxs[i], HYDOT_ERR_CUDA, "cudaSetDevice failed in a batch worker");
+      return;
+    }
+    rc[i] = hydot_solve_fields(ctxs[i], lam0[i], nlam[i], phi_src[i], phi_det[i], st ? st + i : nullptr);
+  };
+  std::vector<std::thread> workers;
+  workers.reserve(n > 0 ? n - 1 : 0);
+  try {
+    for (int i = 1; i < n; ++i) workers.emplace_back(one, i);
+  } catch (...) {  // no thread could be started: run the rest here, in order
+    for (int i = 1 + (int)workers.size(); i < n; ++i) one(i);
+  }
+  if (n > 0) one(0);
+  for (auto& w : workers) w.join();
+  int out = HYDOT_OK;
+  for (int i = 0; i < n; ++i) {
+    if (status) status[i] = rc[i];
+    if (rc[i] == HYDOT_ERR_NOT_CONVERGED) {
+      if (out == HYDOT_OK) out = HYDOT_ERR_NOT_CONVERGED;
+    } else if (rc[i] != HYDOT_OK && (out == HYDOT_OK || out == HYDOT_ERR_NOT_CONVERGED)) {
+      out = rc[i];
+    }
+  }
+  return out;
 }
 
 int hydot_born_assemble(hydot_ctx* ctx, const void* phi_src, const void* phi_det, int lam0, int nlam, long long row0,

@@ -399,7 +399,7 @@ template <typename E, int U>
 cudaError_t launch_apply_partial(dim3 grid, cudaStream_t st, const E* ps, const E* pd, const E* x, const double* eps,
                                  int lam0, int ns, int nd, int nc, long long N, int nxb, int spb, int vec, E* part) {
   const size_t smem = apply_smem_bytes<E, U>(nc);
-  cudaError_t e = cudaFuncSetAttribute(k_apply_partial<E, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = raise_smem_limit(k_apply_partial<E, U>, smem);
   if (e != cudaSuccess) return e;
   k_apply_partial<E, U><<<grid, 256, smem, st>>>(ps, pd, x, eps, lam0, ns, nd, nc, N, nxb, spb, vec, part);
   return cudaGetLastError();
@@ -820,7 +820,7 @@ int apply_T_tile(hydot_ctx* ctx, const float* ps, const float* pd, int lam0, int
                                                                                       : k_apply_T_tile<2>;
   const size_t smem = TT_SMEM + sizeof(float) * (size_t)lpg * TT_NC;
   if (smem > 200 * 1024) return fail(ctx, HYDOT_ERR_ARG, "too many wavelengths per J^T y call");
-  HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  HYDOT_CUDA_TRY(ctx, raise_smem_limit(kern, smem));
   dim3 grid((unsigned)xblocks, ngrp);
   cudaEvent_t t0 = timer_begin(ctx);
   k_transpose_y<<<(unsigned)std::min<long long>((M + 255) / 256, 4096), 256, 0, ctx->stream>>>(y, nlam, ns, nd, yT);
@@ -861,7 +861,7 @@ int apply_T_t(hydot_ctx* ctx, const E* ps, const E* pd, int lam0, int nlam, cons
   const bool full = ns % AT_B == 0 && nd % AT_B == 0;
   auto kern = full ? k_apply_T_partial<E, true> : k_apply_T_partial<E, false>;
   if (smem > 48 * 1024) {
-    HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    HYDOT_CUDA_TRY(ctx, raise_smem_limit(kern, smem));
   }
   cudaEvent_t t0 = timer_begin(ctx);
   kern<<<grid, 256, smem, ctx->stream>>>(ps, pd, y, ctx->d_eps, lam0, nlam, ns, nd, nc, N, lpg, part);

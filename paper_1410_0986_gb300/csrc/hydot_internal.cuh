@@ -188,6 +188,7 @@ struct KernelTimer {
 
 // ----------------------------------------------------------------------------- context
 struct hydot_ctx {
+  int device = 0;  // CUDA device current at hydot_setup (all of the context's memory lives there)
   // problem
   int nx, ny, nz;
   long long N;
@@ -303,6 +304,17 @@ namespace hydot {
 inline int fail(hydot_ctx* ctx, int code, const std::string& msg) {
   ctx->err = msg;
   return code;
+}
+
+// Raises a kernel's dynamic shared-memory limit on the current device to at least `bytes`, never
+// lowering it. Contexts solving concurrently from several host threads can need different sizes
+// of one kernel; a lower limit set between another thread's raise and its launch would fail that
+// launch, so the limit only grows (under a lock). The limit bounds what a launch may ask for and
+// does not change what a smaller launch gets.
+cudaError_t raise_smem_limit_raw(const void* func, size_t bytes);
+template <typename F>
+cudaError_t raise_smem_limit(F* func, size_t bytes) {
+  return raise_smem_limit_raw(reinterpret_cast<const void*>(func), bytes);
 }
 
 // solver.cu

@@ -639,14 +639,14 @@ __global__ void k_form_qc(const float* __restrict__ Q, long long ldq, const doub
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder(hydot_ctx* ctx) {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
+    return (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+               ? reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p)
+               : nullptr;
+  }();
   if (!fn) fail(ctx, HYDOT_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
   return fn;
 }
@@ -705,13 +705,9 @@ int sketch_check(hydot_ctx* ctx, int lam0, int nlam, int ncols) {
 }
 
 int set_sketch_smem(hydot_ctx* ctx) {
-  static bool done = false;
-  if (!done) {
-    HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(k_project_generic, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SK_SMEM));
-    HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(k_range_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RG_SMEM));
-    HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(k_project_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PJ_SMEM));
-    done = true;
-  }
+  HYDOT_CUDA_TRY(ctx, raise_smem_limit(k_project_generic, SK_SMEM));
+  HYDOT_CUDA_TRY(ctx, raise_smem_limit(k_range_ws, RG_SMEM));
+  HYDOT_CUDA_TRY(ctx, raise_smem_limit(k_project_ws, PJ_SMEM));
   return HYDOT_OK;
 }
 

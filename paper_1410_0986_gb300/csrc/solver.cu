@@ -1218,10 +1218,8 @@ __host__ __device__ constexpr int rp_index(int rp) { return rp == 2 ? 0 : (rp ==
 
 template <int RP, int RS, int MB1, int MB2>
 int roll_attrs(hydot_ctx* ctx) {
-  HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(k_dir_roll<RP, RS, MB1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)roll_smem<RP, RS>()));
-  HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(k_update_roll<RP, RS, MB2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)upd_smem<RP, RS>()));
+  HYDOT_CUDA_TRY(ctx, raise_smem_limit(k_dir_roll<RP, RS, MB1>, roll_smem<RP, RS>()));
+  HYDOT_CUDA_TRY(ctx, raise_smem_limit(k_update_roll<RP, RS, MB2>, upd_smem<RP, RS>()));
   return HYDOT_OK;
 }
 
@@ -1434,8 +1432,7 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
   }
   HYDOT_CUDA_TRY(ctx, cudaMemsetAsync(b.err, 0, sizeof(int), s));
   if constexpr (std::is_same<X, df32>::value)  // the residual's halo tile: up to 18 x 10 x 34 double-floats
-    HYDOT_CUDA_TRY(ctx, cudaFuncSetAttribute(k_residual_df, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(sizeof(df32) * (g.tz + 2) * (TY + 2) * (TX + 2))));
+    HYDOT_CUDA_TRY(ctx, raise_smem_limit(k_residual_df, sizeof(df32) * (g.tz + 2) * (TY + 2) * (TX + 2)));
   k_reset<<<(b.nrhs + 255) / 256, 256, 0, s>>>(b);
   ++ctx->launches;
   HYDOT_CUDA_TRY(ctx, cudaGetLastError());
@@ -1536,8 +1533,10 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
       // algorithmic bytes of the inner passes: fields active at each iteration (the counters
       // k_dir increments) x 12 B (pass 1) or 20 B (pass 2) per cell in the inner precision
       std::vector<int> cnt(it);
-      if (it > 0)
-        HYDOT_CUDA_TRY(ctx, cudaMemcpy(cnt.data(), b.counter + 1, sizeof(int) * it, cudaMemcpyDeviceToHost));
+      if (it > 0) {  // on the context's stream: a legacy-stream copy would serialise concurrent contexts
+        HYDOT_CUDA_TRY(ctx, cudaMemcpyAsync(cnt.data(), b.counter + 1, sizeof(int) * it, cudaMemcpyDeviceToHost, s));
+        HYDOT_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+      }
       double active = 0.0;
       for (int q = 0; q < it; ++q) active += cnt[q];
       ctx->timer.bytes[HYDOT_KERNEL_DIR] += active * 3.0 * (double)g.N * sizeof(T);
@@ -1609,15 +1608,15 @@ bool getenv_flag(const char* name) {
 
 // 4-D tensor map {nx, ny, nz, max_fields} of an FP32 field buffer with a bx x by x bz box.
 int encode_field_map(hydot_ctx* ctx, void* base, CUtensorMap* map, int bx, int by, int bz) {
-  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-  if (!encode) {
+  // looked up once (a function-local static is initialised once even when batch workers race here)
+  static const PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
     void* fn = nullptr;
     cudaDriverEntryPointQueryResult q;
     cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
-    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
-      return fail(ctx, HYDOT_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
-    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-  }
+    return (e == cudaSuccess && q == cudaDriverEntryPointSuccess) ? reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn)
+                                                                   : nullptr;
+  }();
+  if (!encode) return fail(ctx, HYDOT_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
   const cuuint64_t nx = ctx->nx, ny = ctx->ny, nz = ctx->nz, F = ctx->max_fields;
   cuuint64_t dims[4] = {nx, ny, nz, F};
   cuuint64_t strides[3] = {nx * 4, nx * ny * 4, nx * ny * nz * 4};

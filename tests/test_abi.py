@@ -122,4 +122,11 @@ def test_null_arguments(lib):
     assert lib.hydot_setup(None, None, None) == L.HYDOT_ERR_ARG
     assert lib.hydot_solve_fields(None, 0, 1, None, None, None) == L.HYDOT_ERR_ARG
     assert lib.hydot_born_apply(None, None, None, 0, 1, None, None) == L.HYDOT_ERR_ARG
+    # the batch call checks its lists before it asks for a device: an empty batch is a no-op and a
+    # missing list or context is an argument error
+    i1, v1 = (C.c_int * 1)(0), (C.c_void_p * 1)(None)
+    assert lib.hydot_solve_batch(None, 0, None, None, None, None, None, None) == L.HYDOT_OK
+    assert lib.hydot_solve_batch(None, -1, None, None, None, None, None, None) == L.HYDOT_ERR_ARG
+    assert lib.hydot_solve_batch(None, 1, i1, i1, v1, v1, None, None) == L.HYDOT_ERR_ARG
+    assert lib.hydot_solve_batch(v1, 1, i1, i1, v1, v1, None, None) == L.HYDOT_ERR_ARG
     lib.hydot_destroy(None)
