@@ -692,9 +692,10 @@ __global__ void __launch_bounds__(NTHREADS) k_update(Geo g, Batch b, int it, T* 
 }
 
 // ---------------------------------------------------------------- inner passes with TMA slabs
-// FP32 real fields whose row pitch is a multiple of 16 bytes (nx % 4 == 0). Tiles are 32 x 8 cells
-// in x-y; TMA copies bring planes of a tile plus its one-cell x-y halo (x rounded out to x0 - 4 so
-// the x coordinate stays 16-byte aligned); cells outside the grid arrive as zeros, so the stencil
+// FP32 real fields whose row pitch is a multiple of 16 bytes (nx % 4 == 0), and complex64 fields
+// (8-byte elements: nx even). Tiles are 32 x 8 cells in x-y; TMA copies bring planes of a tile plus
+// its one-cell x-y halo (x rounded out to x0 - 4 so the x coordinate stays 16-byte aligned for
+// either element size); cells outside the grid arrive as zeros, so the stencil
 // adds its six neighbours without branches (the Robin/Dirichlet faces live in the diagonal).
 // Every wait on an mbarrier is bounded: on timeout the block flags b.err, waits (bounded) for the
 // copies it issued and returns. The partial sums of a block go to the slot of its first 8-plane
@@ -703,8 +704,9 @@ __global__ void __launch_bounds__(NTHREADS) k_update(Geo g, Batch b, int it, T* 
 constexpr int TZT = 8;               // planes per partial-sum tile on this path
 constexpr int BXT = 40, BYT = 10;    // x-y extent of a halo box
 
-__device__ __forceinline__ float* align128(unsigned char* p) {
-  return reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(p) + 127) & ~uintptr_t(127));
+template <typename E>
+__device__ __forceinline__ E* align128(unsigned char* p) {
+  return reinterpret_cast<E*>((reinterpret_cast<uintptr_t>(p) + 127) & ~uintptr_t(127));
 }
 
 __device__ __forceinline__ float diag_f(const LamCoefF& cf, int m) {
@@ -713,6 +715,41 @@ __device__ __forceinline__ float diag_f(const LamCoefF& cf, int m) {
   for (int f = 0; f < 6; ++f)
     if (m & (1 << f)) a += cf.fa[f];
   return a;
+}
+
+// Element arithmetic of the rolling passes: float for real fields, float2 (re, im) for complex64
+// fields, whose COCG uses the unconjugated bilinear form (x^T y, not x^H y), so a "product" is
+// the plain complex product and the only conjugate-free norm is |r|^2 for the stopping test.
+__device__ __forceinline__ float e_add(float a, float b) { return a + b; }
+__device__ __forceinline__ float2 e_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float e_sub(float a, float b) { return a - b; }
+__device__ __forceinline__ float2 e_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float e_mul(float a, float b) { return a * b; }
+__device__ __forceinline__ float2 e_mul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float e_fma(float a, float b, float c) { return fmaf(a, b, c); }  // a b + c
+__device__ __forceinline__ float2 e_fma(float2 a, float2 b, float2 c) {
+  return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));
+}
+__device__ __forceinline__ float e_neg(float a) { return -a; }
+__device__ __forceinline__ float2 e_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float e_abs2_fma(float v, float acc) { return fmaf(v, v, acc); }  // |v|^2 + acc
+__device__ __forceinline__ float e_abs2_fma(float2 v, float acc) { return fmaf(v.x, v.x, fmaf(v.y, v.y, acc)); }
+__device__ __forceinline__ float e_re(float a) { return a; }
+__device__ __forceinline__ float e_re(float2 a) { return a.x; }
+__device__ __forceinline__ float e_im(float) { return 0.f; }
+__device__ __forceinline__ float e_im(float2 a) { return a.y; }
+
+// Quotient (a_re + i a_im) / (b_re + i b_im) of per-field FP64 sums, rounded to the element type.
+template <typename E>
+__device__ __forceinline__ E e_quot(double ar, double ai, double br, double bi) {
+  if constexpr (std::is_same<E, float>::value) {
+    return (float)(ar / br);
+  } else {
+    const double den = br * br + bi * bi;
+    return make_float2((float)((ar * br + ai * bi) / den), (float)((ai * br - ar * bi) / den));
+  }
 }
 
 // Pass 1 with a rolling window of planes. A block owns a (field, x-tile, y-tile, z-segment)
@@ -726,12 +763,14 @@ __device__ __forceinline__ float diag_f(const LamCoefF& cf, int m) {
 // are in flight while a slab is processed. The diagonal and its inverse depend on the cell only
 // through its face mask: each thread precomputes them for its column and its halo cell (four z
 // cases: interior, bottom, top, both).
-// RP (planes per slab) and RS (slab buffers) are template parameters; the variants compute the
-// same values in the same order (bitwise identical results) and differ only in how much data is
-// in flight per block and how many blocks fit on an SM, which the autotuner times.
-constexpr int PLN = BXT * BYT;        // floats in one box plane
-template <int RP, int RS>
-constexpr size_t roll_smem() { return (size_t)RS * 2 * RP * PLN * 4 + 128; }
+// E is float (real fields) or float2 (complex64 fields: the same passes in complex arithmetic,
+// 8-byte elements in the slabs). RP (planes per slab) and RS (slab buffers) are template
+// parameters; the variants compute the same values in the same order (bitwise identical results)
+// and differ only in how much data is in flight per block and how many blocks fit on an SM,
+// which the autotuner times.
+constexpr int PLN = BXT * BYT;  // elements in one box plane
+template <typename E, int RP, int RS>
+constexpr size_t roll_smem() { return (size_t)RS * 2 * RP * PLN * sizeof(E) + 128; }
 
 __device__ __forceinline__ void col_diag(const LamCoefF& cf, int mxy, float (&d)[4], float (&di)[4]) {
 #pragma unroll
@@ -741,25 +780,38 @@ __device__ __forceinline__ void col_diag(const LamCoefF& cf, int mxy, float (&d)
     di[zb] = m ? 1.f / d[zb] : cf.idint;
   }
 }
+// complex diagonal (6 + sigma + face terms) + i sigma_im and its inverse
+__device__ __forceinline__ void col_diag(const LamCoefF& cf, int mxy, float2 (&d)[4], float2 (&di)[4]) {
+#pragma unroll
+  for (int zb = 0; zb < 4; ++zb) {
+    const int m = mxy | ((zb & 1) << 4) | ((zb >> 1) << 5);
+    const float re = m ? diag_f(cf, m) : cf.dint;
+    d[zb] = make_float2(re, cf.dim);
+    const float den = fmaf(re, re, cf.dim * cf.dim);
+    di[zb] = make_float2(re / den, -cf.dim / den);
+  }
+}
 // v[zb] with selects (a dynamic index would put the array in local memory)
-__device__ __forceinline__ float pick4(const float (&v)[4], int zb) {
+template <typename E>
+__device__ __forceinline__ E pick4(const E (&v)[4], int zb) {
   return zb == 0 ? v[0] : (zb == 1 ? v[1] : (zb == 2 ? v[2] : v[3]));
 }
 
-template <int RP, int RS, int MINB>
+template <typename E, int RP, int RS, int MINB>
 __global__ void __launch_bounds__(NTHREADS, MINB) k_dir_roll(Geo g, Batch b, const int* __restrict__ it_dev, int k,
                                                              int seg,
                                                           const LamCoefF* __restrict__ coef_f,
                                                           const __grid_constant__ CUtensorMap mapR,
                                                           const __grid_constant__ CUtensorMap mapPold,
-                                                          float* __restrict__ Pnew) {
+                                                          E* __restrict__ Pnew) {
+  constexpr bool CPLX = !std::is_same<E, float>::value;
   extern __shared__ unsigned char dsm[];
-  float* slab = align128(dsm);  // [RS][r -> p_new, p_old][RP planes]
+  E* slab = align128<E>(dsm);  // [RS][r -> p_new, p_old][RP planes]
   __shared__ uint64_t mbar[RS];
   __shared__ double sm[96];
-  __shared__ float s_beta;
+  __shared__ E s_beta;
   __shared__ int s_go, s_st;
-  constexpr uint32_t SLAB_BYTES = RP * PLN * 4;
+  constexpr uint32_t SLAB_BYTES = RP * PLN * sizeof(E);
   const int it = *it_dev + k;  // iteration index: group base on the device + offset in the group
   const int ncol = g.ntx * g.nty;
   const int nseg = (g.nz + seg - 1) / seg;
@@ -778,7 +830,7 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_dir_roll(Geo g, Batch b, con
   const int nfirst = min(RS, nslab);
   const uint32_t tx_bytes = (first ? 1u : 2u) * SLAB_BYTES;
   auto issue = [&](int q) {
-    float* dst = slab + (q % RS) * 2 * RP * PLN;
+    E* dst = slab + (q % RS) * 2 * RP * PLN;
     mbar_expect_tx(&mbar[q % RS], tx_bytes);
     tma_load_4d(dst, &mapR, &mbar[q % RS], x0 - 4, y0 - 1, z0 - 1 + q * RP, rhs);
     if (!first) tma_load_4d(dst + RP * PLN, &mapPold, &mbar[q % RS], x0 - 4, y0 - 1, z0 - 1 + q * RP, rhs);
@@ -798,25 +850,34 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_dir_roll(Geo g, Batch b, con
   __syncthreads();
   if (s_st != RHS_INNER) return;
   if (threadIdx.x < 32) {
-    double v0 = 0.0, v1 = 0.0, v2 = 0.0;
+    // rho of the current residual (re, im), ||r||^2, and rho of the previous one (re, im)
+    double v0 = 0.0, v0i = 0.0, v1 = 0.0, v2 = 0.0, v2i = 0.0;
     for (int t = threadIdx.x; t < T_; t += 32) {
       v0 += pb[2 * T_ * par + 2 * t];
       v1 += pb[4 * T_ + T_ * par + t];
       if (!first) v2 += pb[2 * T_ * (par ^ 1) + 2 * t];
+      if constexpr (CPLX) {
+        v0i += pb[2 * T_ * par + 2 * t + 1];
+        if (!first) v2i += pb[2 * T_ * (par ^ 1) + 2 * t + 1];
+      }
     }
     v0 = warp_sum(v0);
     v1 = warp_sum(v1);
     v2 = warp_sum(v2);
+    if constexpr (CPLX) {
+      v0i = warp_sum(v0i);
+      v2i = warp_sum(v2i);
+    }
     if (threadIdx.x == 0) {
       int go = 0;
-      float beta = 0.f;
+      E beta{};
       const bool done = v1 <= b.tol_in2 * b.rr0[rhs] || it >= b.max_inner || b.iters[rhs] >= b.max_iter ||
                         v1 == 0.0;
       if (done) {
         if (lead) b.status[rhs] = RHS_FINISHED;
       } else {
         go = 1;
-        beta = first ? 0.f : (float)(v0 / v2);
+        if (!first) beta = e_quot<E>(v0, v0i, v2, v2i);
         if (lead) atomicAdd(&b.counter[1 + it], 1);
       }
       s_go = go;
@@ -830,20 +891,20 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_dir_roll(Geo g, Batch b, con
       for (int q = 0; q < nfirst; ++q) mbar_wait_bounded(&mbar[q % RS], 0u);
     return;
   }
-  const float beta = s_beta;
+  const E beta = s_beta;
 
   // own column and halo cell of this thread
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const int i = x0 + tx, j = y0 + ty;
   const bool in = (i < g.nx) && (j < g.ny);
   const int ob = (ty + 1) * BXT + tx + 4;
-  float dd[4], di[4];
+  E dd[4], di[4];
   col_diag(cf, (i == 0) | ((i == g.nx - 1) << 1) | ((j == 0) << 2) | ((j == g.ny - 1) << 3), dd, di);
   // halo: threads 0..63 take the rows y0-1 and y0+8, threads 64..79 the columns x0-1 and x0+32
   const int h = threadIdx.x;
   const bool has_halo = h < 2 * TX + 2 * TY;
   int hb = 0;
-  float hdi[4] = {0.f, 0.f, 0.f, 0.f};
+  E hdi[4] = {};
   if (has_halo) {
     int hx, hy;
     if (h < 2 * TX) {
@@ -855,33 +916,33 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_dir_roll(Geo g, Batch b, con
     }
     hb = (hy + 1) * BXT + hx + 4;
     const int gi = x0 + hx, gj = y0 + hy;
-    float hd[4];
+    E hd[4];
     col_diag(cf, (gi == 0) | ((gi == g.nx - 1) << 1) | ((gj == 0) << 2) | ((gj == g.ny - 1) << 3), hd, hdi);
   }
   const int plane_n = g.nx * g.ny;
-  float* out = Pnew + (size_t)rhs * g.N + (size_t)j * g.nx + i;
-  float acc = 0.f, pm2 = 0.f, pm1 = 0.f;  // own p_new of the previous slab's last two planes
-  const float* prev = slab;               // previous slab's p_new planes
+  E* out = Pnew + (size_t)rhs * g.N + (size_t)j * g.nx + i;
+  E acc{}, pm2{}, pm1{};      // own p_new of the previous slab's last two planes
+  const E* prev = slab;       // previous slab's p_new planes
   for (int q = 0; q < nslab; ++q) {
-    float* cur = slab + (q % RS) * 2 * RP * PLN;
+    E* cur = slab + (q % RS) * 2 * RP * PLN;
     const bool ok = mbar_wait_bounded(&mbar[q % RS], (uint32_t)((q / RS) & 1));
     const int t0 = q * RP;
     const int a0 = z0 - 1 + t0;  // first plane formed from this slab
-    float pv[RP];
+    E pv[RP];
     // (B) p_new in place; slabs without a grid z-face take the interior diagonal
     auto form = [&](auto edge) {
 #pragma unroll
       for (int u = 0; u < RP; ++u) {
         int zb = 0;
         if constexpr (decltype(edge)::value) zb = (a0 + u == 0) | ((a0 + u == g.nz - 1) << 1);
-        float* pl = cur + u * PLN;
-        float v = pl[ob] * (decltype(edge)::value ? pick4(di, zb) : di[0]);
-        if (!first) v = fmaf(beta, pl[RP * PLN + ob], v);
+        E* pl = cur + u * PLN;
+        E v = e_mul(pl[ob], decltype(edge)::value ? pick4(di, zb) : di[0]);
+        if (!first) v = e_fma(beta, pl[RP * PLN + ob], v);
         pl[ob] = v;
         pv[u] = v;
         if (has_halo) {
-          float hv = pl[hb] * (decltype(edge)::value ? pick4(hdi, zb) : hdi[0]);
-          if (!first) hv = fmaf(beta, pl[RP * PLN + hb], hv);
+          E hv = e_mul(pl[hb], decltype(edge)::value ? pick4(hdi, zb) : hdi[0]);
+          if (!first) hv = e_fma(beta, pl[RP * PLN + hb], hv);
           pl[hb] = hv;
         }
       }
@@ -903,20 +964,21 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_dir_roll(Geo g, Batch b, con
     if (threadIdx.x == 0 && q >= 2 && q - 2 + RS < nslab) issue(q - 2 + RS);
     // (D) stencils of the planes t0 - 1 .. t0 + RP - 2 (plane t0 - 1 lies in the previous slab)
     auto stencil = [&](auto edge) {
-      float* o = out + (ptrdiff_t)(a0 - 1) * plane_n;
+      E* o = out + (ptrdiff_t)(a0 - 1) * plane_n;
 #pragma unroll
       for (int u = 0; u < RP; ++u) {
         const int c = a0 - 1 + u;
-        float d = dd[0];
+        E d = dd[0];
         if constexpr (decltype(edge)::value) {
           if (c < z0 || c >= z1) continue;
           d = pick4(dd, (c == 0) | ((c == g.nz - 1) << 1));
         }
-        const float* pl = (u == 0) ? prev + (RP - 1) * PLN : cur + (u - 1) * PLN;
-        const float below = (u == 0) ? pm2 : (u == 1 ? pm1 : pv[u - 2]);
-        const float centre = (u == 0) ? pm1 : pv[u - 1];
-        const float sn = (pl[ob - 1] + pl[ob + 1]) + (pl[ob - BXT] + pl[ob + BXT]) + (below + pv[u]);
-        acc = fmaf(centre, d * centre - sn, acc);
+        const E* pl = (u == 0) ? prev + (RP - 1) * PLN : cur + (u - 1) * PLN;
+        const E below = (u == 0) ? pm2 : (u == 1 ? pm1 : pv[u - 2]);
+        const E centre = (u == 0) ? pm1 : pv[u - 1];
+        const E sn = e_add(e_add(e_add(pl[ob - 1], pl[ob + 1]), e_add(pl[ob - BXT], pl[ob + BXT])),
+                           e_add(below, pv[u]));
+        acc = e_fma(centre, e_sub(e_mul(d, centre), sn), acc);
         o[u * plane_n] = centre;
       }
     };
@@ -928,42 +990,52 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_dir_roll(Geo g, Batch b, con
     pm1 = pv[RP - 1];
     prev = cur;
   }
-  float a1[1] = {acc};
-  double o1[1];
-  block_sum<1, float>(a1, o1, sm);
+  float a2[2] = {e_re(acc), e_im(acc)};
+  double o2[2];
+  if constexpr (CPLX) block_sum<2, float>(a2, o2, sm);
+  else {
+    float a1[1] = {a2[0]};
+    double o1[1];
+    block_sum<1, float>(a1, o1, sm);
+    o2[0] = o1[0];
+    o2[1] = 0.0;
+  }
   const int nsl = (z1 - z0 + g.tz - 1) / g.tz;
   if (threadIdx.x < nsl) {
     const int slot = col + (z0 / g.tz + threadIdx.x) * ncol;
-    pb[6 * T_ + 2 * slot] = threadIdx.x == 0 ? o1[0] : 0.0;
-    pb[6 * T_ + 2 * slot + 1] = 0.0;
+    pb[6 * T_ + 2 * slot] = threadIdx.x == 0 ? o2[0] : 0.0;
+    pb[6 * T_ + 2 * slot + 1] = threadIdx.x == 0 ? o2[1] : 0.0;
   }
 }
 
 // Pass 2 with the same rolling window: a slab holds RP planes of p (tile + x-y halo) and of e
 // and r (tile only), all by TMA; the stencil of plane k runs once plane k+1 of p is resident.
 // Threads write nothing to shared memory, so one barrier per slab only guards the refill.
-template <int RP>
-__host__ __device__ constexpr uint32_t upd_slab() { return RP * PLN * 4 + 2 * RP * TX * TY * 4; }  // p | e | r
-template <int RP, int RS>
-constexpr size_t upd_smem() { return (size_t)RS * upd_slab<RP>() + 128; }
+template <typename E, int RP>
+__host__ __device__ constexpr uint32_t upd_slab() {  // p | e | r
+  return (uint32_t)((RP * PLN + 2 * RP * TX * TY) * sizeof(E));
+}
+template <typename E, int RP, int RS>
+constexpr size_t upd_smem() { return (size_t)RS * upd_slab<E, RP>() + 128; }
 
-template <int RP, int RS, int MINB>
+template <typename E, int RP, int RS, int MINB>
 __global__ void __launch_bounds__(NTHREADS, MINB) k_update_roll(Geo g, Batch b, const int* __restrict__ it_dev,
                                                                 int k, int seg,
                                                              const LamCoefF* __restrict__ coef_f,
-                                                             float* __restrict__ E, float* __restrict__ R,
+                                                             E* __restrict__ Eo, E* __restrict__ R,
                                                              const __grid_constant__ CUtensorMap mapP,
                                                              const __grid_constant__ CUtensorMap mapE,
                                                              const __grid_constant__ CUtensorMap mapR) {
+  constexpr bool CPLX = !std::is_same<E, float>::value;
   extern __shared__ unsigned char dsm[];
-  unsigned char* slab = reinterpret_cast<unsigned char*>(align128(dsm));  // [RS][p | e | r]
+  unsigned char* slab = reinterpret_cast<unsigned char*>(align128<E>(dsm));  // [RS][p | e | r]
   __shared__ uint64_t mbar[RS];
   __shared__ double sm[96];
-  __shared__ float s_alpha;
+  __shared__ E s_alpha;
   __shared__ int s_st;
-  constexpr uint32_t UP_P = RP * PLN * 4;      // p planes of a slab (bytes)
-  constexpr uint32_t UP_V = RP * TX * TY * 4;  // e or r planes of a slab (bytes)
-  constexpr uint32_t UP_SLAB = upd_slab<RP>();
+  constexpr uint32_t UP_P = RP * PLN * sizeof(E);      // p planes of a slab (bytes)
+  constexpr uint32_t UP_V = RP * TX * TY * sizeof(E);  // e or r planes of a slab (bytes)
+  constexpr uint32_t UP_SLAB = upd_slab<E, RP>();
   const int it = *it_dev + k;  // iteration index: group base on the device + offset in the group
   const int ncol = g.ntx * g.nty;
   const int nseg = (g.nz + seg - 1) / seg;
@@ -1002,29 +1074,40 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_update_roll(Geo g, Batch b, 
   __syncthreads();
   if (s_st != RHS_INNER) return;
   if (threadIdx.x < 32) {
-    double v0 = 0.0, v1 = 0.0;
+    // alpha = rho / gamma (complex for complex fields)
+    double v0 = 0.0, v0i = 0.0, v1 = 0.0, v1i = 0.0;
     for (int t = threadIdx.x; t < T_; t += 32) {
       v0 += pb[2 * T_ * par + 2 * t];
       v1 += pb[6 * T_ + 2 * t];
+      if constexpr (CPLX) {
+        v0i += pb[2 * T_ * par + 2 * t + 1];
+        v1i += pb[6 * T_ + 2 * t + 1];
+      }
     }
     v0 = warp_sum(v0);
     v1 = warp_sum(v1);
-    if (threadIdx.x == 0) s_alpha = (float)(v0 / v1);
+    if constexpr (CPLX) {
+      v0i = warp_sum(v0i);
+      v1i = warp_sum(v1i);
+    }
+    if (threadIdx.x == 0) s_alpha = e_quot<E>(v0, v0i, v1, v1i);
   }
   const LamCoefF cf = coef_f[rhs_lambda(b, rhs)];
   __syncthreads();
-  const float alpha = s_alpha;
+  const E alpha = s_alpha;
+  const E nalpha = e_neg(alpha);
 
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const int i = x0 + tx, j = y0 + ty;
   const bool in = (i < g.nx) && (j < g.ny);
   const int ob = (ty + 1) * BXT + tx + 4;
   const int ov = threadIdx.x;  // (ty, tx) in an e / r plane
-  float dd[4], di[4];
+  E dd[4], di[4];
   col_diag(cf, (i == 0) | ((i == g.nx - 1) << 1) | ((j == 0) << 2) | ((j == g.ny - 1) << 3), dd, di);
   const int plane_n = g.nx * g.ny;
   const size_t base = (size_t)rhs * g.N + (size_t)j * g.nx + i;
-  float acc0 = 0.f, acc1 = 0.f, pm2 = 0.f, pm1 = 0.f;
+  E acc0{}, pm2{}, pm1{};
+  float acc1 = 0.f;
   const unsigned char* prev = slab;
   for (int q = 0; q < nslab; ++q) {
     const unsigned char* cur = slab + (size_t)(q % RS) * UP_SLAB;
@@ -1040,8 +1123,8 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_update_roll(Geo g, Batch b, 
     // every thread is past the stencils that read slab q - 2: refill its buffer
     if (threadIdx.x == 0 && q >= 2 && q - 2 + RS < nslab) issue(q - 2 + RS);
     const int a0 = z0 - 1 + q * RP;
-    const float* cp = reinterpret_cast<const float*>(cur);
-    float pv[RP];
+    const E* cp = reinterpret_cast<const E*>(cur);
+    E pv[RP];
 #pragma unroll
     for (int u = 0; u < RP; ++u) pv[u] = cp[u * PLN + ob];
     auto stencil = [&](auto edge) {
@@ -1049,7 +1132,7 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_update_roll(Geo g, Batch b, 
 #pragma unroll
       for (int u = 0; u < RP; ++u) {
         const int c = a0 - 1 + u;
-        float d = dd[0], dinv = di[0];
+        E d = dd[0], dinv = di[0];
         if constexpr (decltype(edge)::value) {
           if (c < z0 || c >= z1) continue;
           const int zc = (c == 0) | ((c == g.nz - 1) << 1);
@@ -1058,20 +1141,21 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_update_roll(Geo g, Batch b, 
         }
         const unsigned char* sl = (u == 0) ? prev : cur;
         const int pu = (u == 0) ? RP - 1 : u - 1;
-        const float* pl = reinterpret_cast<const float*>(sl) + pu * PLN;
-        const float* ev = reinterpret_cast<const float*>(sl + UP_P) + pu * TX * TY;
-        const float* rv = reinterpret_cast<const float*>(sl + UP_P + UP_V) + pu * TX * TY;
-        const float below = (u == 0) ? pm2 : (u == 1 ? pm1 : pv[u - 2]);
-        const float centre = (u == 0) ? pm1 : pv[u - 1];
-        const float sn = (pl[ob - 1] + pl[ob + 1]) + (pl[ob - BXT] + pl[ob + BXT]) + (below + pv[u]);
-        const float qv = d * centre - sn;
-        const float en = first ? alpha * centre : fmaf(alpha, centre, ev[ov]);
-        const float rn = fmaf(-alpha, qv, rv[ov]);
+        const E* pl = reinterpret_cast<const E*>(sl) + pu * PLN;
+        const E* ev = reinterpret_cast<const E*>(sl + UP_P) + pu * TX * TY;
+        const E* rv = reinterpret_cast<const E*>(sl + UP_P + UP_V) + pu * TX * TY;
+        const E below = (u == 0) ? pm2 : (u == 1 ? pm1 : pv[u - 2]);
+        const E centre = (u == 0) ? pm1 : pv[u - 1];
+        const E sn = e_add(e_add(e_add(pl[ob - 1], pl[ob + 1]), e_add(pl[ob - BXT], pl[ob + BXT])),
+                           e_add(below, pv[u]));
+        const E qv = e_sub(e_mul(d, centre), sn);
+        const E en = first ? e_mul(alpha, centre) : e_fma(alpha, centre, ev[ov]);
+        const E rn = e_fma(nalpha, qv, rv[ov]);
         const size_t id = o0 + (size_t)u * plane_n;
-        E[id] = en;
+        Eo[id] = en;
         R[id] = rn;
-        acc0 = fmaf(rn, rn * dinv, acc0);
-        acc1 = fmaf(rn, rn, acc1);
+        acc0 = e_fma(rn, e_mul(rn, dinv), acc0);
+        acc1 = e_abs2_fma(rn, acc1);
       }
     };
     if (in) {
@@ -1082,15 +1166,23 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_update_roll(Geo g, Batch b, 
     pm1 = pv[RP - 1];
     prev = cur;
   }
-  float accs[2] = {acc0, acc1};
-  double outs[2];
-  block_sum<2, float>(accs, outs, sm);
+  double outs[3] = {0.0, 0.0, 0.0};
+  if constexpr (CPLX) {
+    float accs[3] = {e_re(acc0), acc1, e_im(acc0)};
+    block_sum<3, float>(accs, outs, sm);
+  } else {
+    float accs[2] = {e_re(acc0), acc1};
+    double o2[2];
+    block_sum<2, float>(accs, o2, sm);
+    outs[0] = o2[0];
+    outs[1] = o2[1];
+  }
   const int nsl = (z1 - z0 + g.tz - 1) / g.tz;
   if (threadIdx.x < nsl) {
     const int slot = col + (z0 / g.tz + threadIdx.x) * ncol;
     const bool z = threadIdx.x == 0;
     pb[2 * T_ * (par ^ 1) + 2 * slot] = z ? outs[0] : 0.0;
-    pb[2 * T_ * (par ^ 1) + 2 * slot + 1] = 0.0;
+    pb[2 * T_ * (par ^ 1) + 2 * slot + 1] = z ? outs[2] : 0.0;
     pb[4 * T_ + T_ * (par ^ 1) + slot] = z ? outs[1] : 0.0;
     if (z && lead) b.iters[rhs] += 1;
   }
@@ -1209,57 +1301,81 @@ __global__ void k_dsig(const double* __restrict__ dc, const double* __restrict__
 
 // ---------------------------------------------------------------- rolling-pass variants
 // {planes per slab, slab buffers}; the autotuner picks one per context (they give identical bits).
+// Complex64 slabs take twice the shared memory per plane, hence their own, shallower set.
 struct RollVariant {
   int rp, rs;
 };
 constexpr RollVariant ROLL_VARIANTS[HYDOT_ROLL_VARIANTS] = {{4, 4}, {2, 6}, {8, 3}, {4, 5}};
+constexpr RollVariant ROLL_VARIANTS_C[HYDOT_ROLL_VARIANTS] = {{2, 4}, {2, 6}, {4, 3}, {4, 4}};
 
 __host__ __device__ constexpr int rp_index(int rp) { return rp == 2 ? 0 : (rp == 4 ? 1 : 2); }
 
-template <int RP, int RS, int MB1, int MB2>
+template <typename E, int RP, int RS, int MB1, int MB2>
 int roll_attrs(hydot_ctx* ctx) {
-  HYDOT_CUDA_TRY(ctx, raise_smem_limit(k_dir_roll<RP, RS, MB1>, roll_smem<RP, RS>()));
-  HYDOT_CUDA_TRY(ctx, raise_smem_limit(k_update_roll<RP, RS, MB2>, upd_smem<RP, RS>()));
+  HYDOT_CUDA_TRY(ctx, raise_smem_limit(k_dir_roll<E, RP, RS, MB1>, roll_smem<E, RP, RS>()));
+  HYDOT_CUDA_TRY(ctx, raise_smem_limit(k_update_roll<E, RP, RS, MB2>, upd_smem<E, RP, RS>()));
   return HYDOT_OK;
 }
 
 // One inner iteration (pass 1, pass 2) with variant <RP, RS>.
-template <int RP, int RS, int MB1, int MB2>
-void roll_iteration(hydot_ctx* ctx, const Geo& g, const Batch& b, int it, unsigned nrb, float* E, float* R,
-                    float* const* P) {
+template <typename E, int RP, int RS, int MB1, int MB2>
+void roll_iteration(hydot_ctx* ctx, const Geo& g, const Batch& b, int it, unsigned nrb, E* Ev, E* R, E* const* P) {
   const int k = rp_index(RP);
   const int seg = ctx->dir_seg;
   cudaStream_t s = ctx->stream;
   cudaEvent_t t0 = timer_begin(ctx);
   const int o = it % POLL_GROUP;  // groups start at multiples of POLL_GROUP (even): parity of it = parity of o
-  k_dir_roll<RP, RS, MB1><<<nrb, NTHREADS, roll_smem<RP, RS>(), s>>>(g, b, ctx->d_it, o, seg, ctx->d_coef_f,
-                                                                   ctx->tm_rh[k], ctx->tm_ph[k][it & 1],
-                                                                   P[(it + 1) & 1]);
+  k_dir_roll<E, RP, RS, MB1><<<nrb, NTHREADS, roll_smem<E, RP, RS>(), s>>>(g, b, ctx->d_it, o, seg, ctx->d_coef_f,
+                                                                         ctx->tm_rh[k], ctx->tm_ph[k][it & 1],
+                                                                         P[(it + 1) & 1]);
   ++ctx->launches;
   timer_end(ctx, t0, HYDOT_KERNEL_DIR, 0.0);
   t0 = timer_begin(ctx);
-  k_update_roll<RP, RS, MB2><<<nrb, NTHREADS, upd_smem<RP, RS>(), s>>>(g, b, ctx->d_it, o, seg, ctx->d_coef_f, E, R,
-                                                                     ctx->tm_ph[k][(it + 1) & 1], ctx->tm_e[k],
-                                                                     ctx->tm_rv[k]);
+  k_update_roll<E, RP, RS, MB2><<<nrb, NTHREADS, upd_smem<E, RP, RS>(), s>>>(
+      g, b, ctx->d_it, o, seg, ctx->d_coef_f, Ev, R, ctx->tm_ph[k][(it + 1) & 1], ctx->tm_e[k], ctx->tm_rv[k]);
   ++ctx->launches;
   timer_end(ctx, t0, HYDOT_KERNEL_UPDATE, 0.0);
 }
 
-void roll_dispatch(hydot_ctx* ctx, int v, const Geo& g, const Batch& b, int it, unsigned nrb, float* E, float* R,
-                   float* const* P) {
+// The variants' template arguments follow ROLL_VARIANTS / ROLL_VARIANTS_C; the blocks-per-SM
+// bounds are what their shared memory allows (228 KB per SM).
+void roll_dispatch(hydot_ctx* ctx, int v, const Geo& g, const Batch& b, int it, unsigned nrb, void* Ev, void* R,
+                   void* const* P) {
+  if (ctx->cplx) {
+    float2* e = (float2*)Ev;
+    float2* r = (float2*)R;
+    float2* p[2] = {(float2*)P[0], (float2*)P[1]};
+    switch (v) {
+      case 1: roll_iteration<float2, 2, 6, 2, 2>(ctx, g, b, it, nrb, e, r, p); break;
+      case 2: roll_iteration<float2, 4, 3, 2, 2>(ctx, g, b, it, nrb, e, r, p); break;
+      case 3: roll_iteration<float2, 4, 4, 2, 1>(ctx, g, b, it, nrb, e, r, p); break;
+      default: roll_iteration<float2, 2, 4, 3, 3>(ctx, g, b, it, nrb, e, r, p); break;
+    }
+    return;
+  }
+  float* e = (float*)Ev;
+  float* r = (float*)R;
+  float* p[2] = {(float*)P[0], (float*)P[1]};
   switch (v) {
-    case 1: roll_iteration<2, 6, 4, 4>(ctx, g, b, it, nrb, E, R, P); break;
-    case 2: roll_iteration<8, 3, 2, 2>(ctx, g, b, it, nrb, E, R, P); break;
-    case 3: roll_iteration<4, 5, 3, 3>(ctx, g, b, it, nrb, E, R, P); break;
-    default: roll_iteration<4, 4, 4, 3>(ctx, g, b, it, nrb, E, R, P); break;
+    case 1: roll_iteration<float, 2, 6, 4, 4>(ctx, g, b, it, nrb, e, r, p); break;
+    case 2: roll_iteration<float, 8, 3, 2, 2>(ctx, g, b, it, nrb, e, r, p); break;
+    case 3: roll_iteration<float, 4, 5, 3, 3>(ctx, g, b, it, nrb, e, r, p); break;
+    default: roll_iteration<float, 4, 4, 4, 3>(ctx, g, b, it, nrb, e, r, p); break;
   }
 }
 
 int roll_setup(hydot_ctx* ctx) {
-  int rc = roll_attrs<4, 4, 4, 3>(ctx);
-  if (!rc) rc = roll_attrs<2, 6, 4, 4>(ctx);
-  if (!rc) rc = roll_attrs<8, 3, 2, 2>(ctx);
-  if (!rc) rc = roll_attrs<4, 5, 3, 3>(ctx);
+  if (ctx->cplx) {
+    int rc = roll_attrs<float2, 2, 4, 3, 3>(ctx);
+    if (!rc) rc = roll_attrs<float2, 2, 6, 2, 2>(ctx);
+    if (!rc) rc = roll_attrs<float2, 4, 3, 2, 2>(ctx);
+    if (!rc) rc = roll_attrs<float2, 4, 4, 2, 1>(ctx);
+    return rc;
+  }
+  int rc = roll_attrs<float, 4, 4, 4, 3>(ctx);
+  if (!rc) rc = roll_attrs<float, 2, 6, 4, 4>(ctx);
+  if (!rc) rc = roll_attrs<float, 8, 3, 2, 2>(ctx);
+  if (!rc) rc = roll_attrs<float, 4, 5, 3, 3>(ctx);
   return rc;
 }
 
@@ -1302,8 +1418,8 @@ struct GraphKey {
   const void *E, *R, *P0, *P1;
 };
 
-int inner_graph_launch(hydot_ctx* ctx, const Geo& g, const Batch& b, int variant, unsigned nrb, float* E, float* R,
-                       float* const* P) {
+int inner_graph_launch(hydot_ctx* ctx, const Geo& g, const Batch& b, int variant, unsigned nrb, void* E, void* R,
+                       void* const* P) {
   GraphKey key;
   std::memset(&key, 0, sizeof(key));
   key.b = b;
@@ -1467,8 +1583,10 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
     HYDOT_CUDA_TRY(ctx, cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
     int slot = 0;
     bool stop = false;
-    // rolling passes (FP32 real fields, TMA): the iteration index lives on the device
-    const bool roll = std::is_same<T, float>::value && ctx->use_tma && !ctx->d_dc;
+    // rolling passes (FP32 real or complex64 fields, TMA): the iteration index lives on the device
+    const bool roll = (std::is_same<T, float>::value || std::is_same<T, cpx<float>>::value) && ctx->use_tma &&
+                      !ctx->d_dc;
+    void* const Pv[2] = {P[0], P[1]};
     const unsigned nrb =
         roll ? (unsigned)((long long)b.nrhs * g.ntx * g.nty * ((g.nz + ctx->dir_seg - 1) / ctx->dir_seg)) : 0u;
     if (roll) HYDOT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_it, 0, sizeof(int), s));
@@ -1481,11 +1599,11 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
       if (tuning) HYDOT_CUDA_TRY(ctx, cudaEventRecord(ctx->tune_ev[0], s));
       if (roll) {
         if (ctx->use_graphs && !tuning && ctx->tune.variant >= 0 && !ctx->timer.on) {
-          int rc = inner_graph_launch(ctx, g, b, variant, nrb, (float*)E, (float*)R, (float* const*)P);
+          int rc = inner_graph_launch(ctx, g, b, variant, nrb, E, R, Pv);
           if (rc) return rc;
           it = g_end;
         } else {
-          for (; it < g_end; ++it) roll_dispatch(ctx, variant, g, b, it, nrb, (float*)E, (float*)R, (float* const*)P);
+          for (; it < g_end; ++it) roll_dispatch(ctx, variant, g, b, it, nrb, E, R, Pv);
           k_bump<<<1, 1, 0, s>>>(ctx->d_it, POLL_GROUP);
           ++ctx->launches;
         }
@@ -1606,7 +1724,8 @@ bool getenv_flag(const char* name) {
   return v && *v && std::strcmp(v, "0") != 0;
 }
 
-// 4-D tensor map {nx, ny, nz, max_fields} of an FP32 field buffer with a bx x by x bz box.
+// 4-D tensor map {nx, ny, nz, max_fields} of an FP32 (real) or complex64 (8-byte elements, copied
+// as opaque 64-bit words) field buffer with a bx x by x bz box.
 int encode_field_map(hydot_ctx* ctx, void* base, CUtensorMap* map, int bx, int by, int bz) {
   // looked up once (a function-local static is initialised once even when batch workers race here)
   static const PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
@@ -1619,10 +1738,12 @@ int encode_field_map(hydot_ctx* ctx, void* base, CUtensorMap* map, int bx, int b
   if (!encode) return fail(ctx, HYDOT_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
   const cuuint64_t nx = ctx->nx, ny = ctx->ny, nz = ctx->nz, F = ctx->max_fields;
   cuuint64_t dims[4] = {nx, ny, nz, F};
-  cuuint64_t strides[3] = {nx * 4, nx * ny * 4, nx * ny * nz * 4};
+  const cuuint64_t w = ctx->cplx ? 8 : 4;
+  cuuint64_t strides[3] = {nx * w, nx * ny * w, nx * ny * nz * w};
   cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz, 1};
   cuuint32_t estr[4] = {1, 1, 1, 1};
-  CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, estr,
+  const CUtensorMapDataType dt = ctx->cplx ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  CUresult r = encode(map, dt, 4, base, dims, strides, box, estr,
                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(ctx, HYDOT_ERR_CUDA, "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
@@ -1635,8 +1756,8 @@ int solver_alloc(hydot_ctx* ctx) {
   Tiling& t = ctx->tiling;
   t.tx = TX;
   t.ty = TY;
-  // FP32 real fields with a 16-byte row pitch take the TMA inner kernels (8-plane tiles)
-  ctx->use_tma = ctx->precision == HYDOT_MIXED && !ctx->cplx && (ctx->nx % 4 == 0) && !getenv_flag("HYDOT_NO_TMA");
+  // FP32 real / complex64 fields with a 16-byte row pitch take the TMA inner kernels (8-plane tiles)
+  ctx->use_tma = ctx->precision == HYDOT_MIXED && (ctx->nx % (ctx->cplx ? 2 : 4) == 0) && !getenv_flag("HYDOT_NO_TMA");
   t.tz = ctx->use_tma ? std::min(ctx->nz, TZT) : std::min(ctx->nz, 16);
   t.ntx = (ctx->nx + TX - 1) / TX;
   t.nty = (ctx->ny + TY - 1) / TY;
@@ -1781,8 +1902,9 @@ int set_absorption_impl(hydot_ctx* ctx, const double* dc) {
 int get_tuning_impl(const hydot_ctx* ctx, int* variant, int* planes, int* buffers, double* ns_per_cell) {
   if (variant) *variant = ctx->use_tma ? ctx->tune.variant : -1;
   for (int v = 0; v < HYDOT_ROLL_VARIANTS; ++v) {
-    if (planes) planes[v] = ROLL_VARIANTS[v].rp;
-    if (buffers) buffers[v] = ROLL_VARIANTS[v].rs;
+    const RollVariant& rv = ctx->cplx ? ROLL_VARIANTS_C[v] : ROLL_VARIANTS[v];
+    if (planes) planes[v] = rv.rp;
+    if (buffers) buffers[v] = rv.rs;
     if (ns_per_cell)
       ns_per_cell[v] = ctx->tune.cells[v] > 0.0 ? 1e6 * ctx->tune.ms[v] / ctx->tune.cells[v] : 0.0;
   }

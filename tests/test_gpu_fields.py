@@ -152,6 +152,48 @@ def test_frequency_domain_cocg(hd, precision, tol):
     assert rel_err(ps, rs) <= tol and rel_err(pd, rd) <= tol
 
 
+@pytest.mark.parametrize("grid,faces", [((38, 19, 21), (3.0,) * 6), ((34, 12, 10), (0.0, 3.0, 1.0, 3.0, 0.5, 2.0)),
+                                         ((15, 12, 9), (3.0,) * 6)])
+def test_frequency_domain_tma_and_generic_kernels_agree(hd, monkeypatch, grid, faces):
+    """Complex64 COCG through the TMA rolling passes (nx even: 8-byte rows stay 16-byte aligned;
+    ragged tiles in x, y and z, Dirichlet and Robin faces) and through the generic kernels (odd nx,
+    or the TMA path switched off): both meet the oracle's complex128 fields to 1e-6."""
+    nx, ny, nz = grid
+    p = workloads.small(seed=41 + nx, nx=nx, ny=ny, nz=nz, n_src=2, n_det=3, n_lambda=2, freq_mhz=100.0,
+                        robin_A=faces)
+    rs, rd = osolve.fields_splu(p)
+    out = []
+    for flag in ("0", "1"):
+        monkeypatch.setenv("HYDOT_NO_TMA", flag)
+        with hd.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=1e-8) as ctx:
+            ps, pd, st = ctx.solve_fields(0, p.n_lambda)
+        assert ps.dtype == torch.complex64 and st["n_not_converged"] == 0
+        assert rel_err(ps, rs) <= 1e-6 and rel_err(pd, rd) <= 1e-6
+        out.append((ps, pd))
+    a, b = out
+    assert (a[0] - b[0]).abs().max() <= 1e-6 * a[0].abs().max()
+
+
+def test_frequency_domain_roll_variants_and_graphs_bitwise(hd, monkeypatch):
+    """The four complex slab shapes give the same bits, with and without CUDA-graph replay, and the
+    autotuner reports the complex set."""
+    p = workloads.make_problem(workloads.Grid(48, 40, 36, 2.0), 4, 4, 2, seed=22, geometry="transmission",
+                               freq_mhz=100.0)
+    out = []
+    for v in range(4):
+        monkeypatch.setenv("HYDOT_ROLL_VARIANT", str(v))
+        for graphs in ("0", "1"):
+            monkeypatch.setenv("HYDOT_NO_GRAPHS", graphs)
+            with hd.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=1e-8) as ctx:
+                ps, pd, st = ctx.solve_fields(0, p.n_lambda)
+                assert ctx.tuning()["variant"] == v and st["n_not_converged"] == 0
+                tu = ctx.tuning()
+            out.append((ps, pd))
+    for ps, pd in out[1:]:
+        assert torch.equal(ps, out[0][0]) and torch.equal(pd, out[0][1])
+    assert [(v["planes"], v["buffers"]) for v in tu["variants"]] == [(2, 4), (2, 6), (4, 3), (4, 4)]
+
+
 def test_wavelength_slice_and_single_sets(hd, oracle_fields):
     p, (rs, rd) = oracle_fields["reflection-13x11x9"]
     with hd.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=1e-8, max_lambda_per_call=2) as ctx:
