@@ -92,7 +92,10 @@ typedef struct {
                             * partner value anywhere, so c = tau / tol_cw keeps every Born entry
                             * J[(s,d,.),.] within about tau of its row maximum while cells far from
                             * every optode stop driving refinement. 0: plain componentwise test.
-                            * Continuous wave only (ignored when omega != 0). */
+                            * With omega != 0 the same holds with |x| the modulus and sigma_j the
+                            * real part: the frequency term is one imaginary shift i w on every
+                            * cell, so |A^-1| = |int_0^inf e^(-t Re A) e^(-i w t) dt| <= (Re A)^-1
+                            * entrywise, and Re A is the continuous-wave operator. */
 } hydot_problem;
 
 typedef struct {

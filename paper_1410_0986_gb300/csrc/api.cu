@@ -198,7 +198,7 @@ int hydot_setup(const hydot_problem* p, void* stream, hydot_ctx** out) {
   c->inner_tol = p->inner_tol;
   c->max_iter = p->max_iter > 0 ? p->max_iter : 20000;
   c->deflation_k = p->deflation_k;
-  c->cw_floor = p->omega == 0.0 ? p->cw_floor : 0.0;
+  c->cw_floor = p->cw_floor;
   if (p->deflation_k > 0 && p->omega != 0.0) {
     g_setup_error = "deflation is available for continuous-wave (real) fields only";
     delete c;

@@ -480,7 +480,8 @@ __global__ void __launch_bounds__(NTHREADS) k_residual_df(Geo g, Batch b, const 
 }
 
 // Floor of the componentwise test: theta = cw_floor * sigma * min |x| over the field's partner
-// optode cells (detectors for a source field, sources for a detector field).
+// optode cells (detectors for a source field, sources for a detector field); sigma is the real
+// shift and |x| the modulus for complex fields.
 template <typename X>
 __global__ void k_theta(Geo g, Batch b, const X* __restrict__ x64, const int* __restrict__ optode) {
   int rhs = blockIdx.x * blockDim.x + threadIdx.x;

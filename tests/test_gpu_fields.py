@@ -174,6 +174,24 @@ def test_frequency_domain_tma_and_generic_kernels_agree(hd, monkeypatch, grid, f
     assert (a[0] - b[0]).abs().max() <= 1e-6 * a[0].abs().max()
 
 
+def test_frequency_domain_born_aware_floor(hd):
+    """The Born-aware floor on complex fields (|A^-1| <= (Re A)^-1 entrywise for the constant
+    imaginary shift): fields to 1e-6 and every Born product phi_s phi_d within 1e-5 of its row
+    maximum against the oracle, in no more refinement cycles than the plain componentwise test."""
+    p = workloads.make_problem(workloads.Grid(48, 40, 36, 2.0), 4, 4, 2, seed=24, geometry="transmission",
+                               freq_mhz=100.0)
+    rs, rd = osolve.fields_separable(p)
+    cyc = {}
+    for floor in (0.0, 100.0):
+        with hd.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=1e-8, cw_floor=floor) as ctx:
+            ps, pd, st = ctx.solve_fields(0, p.n_lambda)
+        assert st["n_not_converged"] == 0
+        assert rel_err(ps, rs) <= 1e-6 and rel_err(pd, rd) <= 1e-6
+        assert born_rowmax_err(p, ps, pd, rs, rd) <= 1e-5
+        cyc[floor] = st["cycles_max"]
+    assert cyc[100.0] <= cyc[0.0]
+
+
 def test_frequency_domain_roll_variants_and_graphs_bitwise(hd, monkeypatch):
     """The four complex slab shapes give the same bits, with and without CUDA-graph replay, and the
     autotuner reports the complex set."""
