@@ -232,6 +232,7 @@ int hydot_setup(const hydot_problem* p, void* stream, hydot_ctx** out) {
       cf[j].dint = (float)d;
       cf[j].dint_lo = (float)(d - (double)cf[j].dint);
       cf[j].dim = (float)c->coef[j].sigma_im;
+      cf[j].dim_lo = (float)(c->coef[j].sigma_im - (double)cf[j].dim);
       cf[j].idint = (float)(1.0 / d);
       for (int f = 0; f < 6; ++f) {
         const double a = c->coef[j].bhat[f] - 1.0;

@@ -95,6 +95,11 @@ struct __align__(8) df32 {
   float hi, lo;
 };
 
+// A complex number with double-float parts: the refinement iterate of the mixed complex path.
+struct __align__(16) cdf32 {
+  df32 re, im;
+};
+
 __host__ __device__ inline df32 df_from(double v) {
   const float h = (float)v;
   return {h, (float)(v - (double)h)};
@@ -158,6 +163,7 @@ struct LamCoefF {
   float fa[6];  // bhat_f - 1
   float dint_lo;   // 6 + sigma_re - dint: with dint, the diagonal as a double-float
   float fa_lo[6];  // bhat_f - 1 - fa[f]
+  float dim_lo;    // sigma_im - dim
 };
 
 // Solver state of one simultaneous field (right-hand side) of a batch.

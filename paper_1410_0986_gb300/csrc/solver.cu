@@ -8,9 +8,9 @@
 //   K_res    r64 = b - Ahat x64 to well beyond FP32 accuracy, ||r64||_2, the componentwise backward
 //            error max_i |r64_i| / (|Ahat||x64| + |b| + theta)_i, and the inner right-hand side
 //            r = r64 / scale in the inner precision with rho_0 = r^T D^-1 r  [per-tile partials]
-//            (FP64 iterate and arithmetic for the FP64 and complex paths; for the mixed real path
-//            the iterate x64 is double-float and the residual uses FP32 error-free transformations,
-//            as FP64 runs at ~1/64 of the FP32 rate on this GPU)
+//            (FP64 iterate and arithmetic for the FP64 paths; for the mixed paths, real and
+//            complex, the iterate x64 is double-float and the residual uses FP32 error-free
+//            transformations, as FP64 runs at ~1/64 of the FP32 rate on this GPU)
 //   K_decide stop, or start a cycle                                        [one thread per rhs]
 //   K_A/K_B  inner PCG/COCG on Ahat e = r (two kernels per iteration, see below)
 //   K_fold   x64 += scale * e
@@ -479,6 +479,174 @@ __global__ void __launch_bounds__(NTHREADS) k_residual_df(Geo g, Batch b, const 
   }
 }
 
+// The same pass for complex fields with a double-float iterate (re and im each a df32). The
+// operator is the real stencil plus one imaginary shift on the diagonal, so
+//   Re(A x) = d x_re - sigma_im x_im - (neighbours of x_re),
+//   Im(A x) = d x_im + sigma_im x_re - (neighbours of x_im),
+// each accumulated as s + cc exactly as in k_residual_df (TwoSum for the high parts, FP32
+// compensation for the rest, exact FMA products for the diagonal terms). The exponent bound of
+// the componentwise backward error takes the larger part of each complex number and one more
+// bit for |z| <= sqrt(2) max(|re|, |im|), as the FP64 kernel does.
+__global__ void __launch_bounds__(NTHREADS) k_residual_cdf(Geo g, Batch b, const LamCoefF* __restrict__ coef_f,
+                                                           const cdf32* __restrict__ x64, float2* __restrict__ R) {
+  extern __shared__ __align__(16) unsigned char rsm_raw[];
+  __shared__ double sm[96];
+  __shared__ int smi[NWARPS];
+  TileCoord c = tile_coord(g);
+  if (b.status[c.rhs] != RHS_FINISHED) return;
+  const LamCoefF cf = coef_f[rhs_lambda(b, c.rhs)];
+  const df32 d0{cf.dint, cf.dint_lo};
+  const df32 dsi{cf.dim, cf.dim_lo}, ndsi{-cf.dim, -cf.dim_lo};
+  df32 dfa[6];
+#pragma unroll
+  for (int f = 0; f < 6; ++f) dfa[f] = df32{cf.fa[f], cf.fa_lo[f]};
+  const long long src = rhs_source(b, c.rhs);
+  const float pre = 1.f / (float)b.next[c.rhs];
+  const int etheta = bexp(b.theta[c.rhs]);
+  const cdf32* x = x64 + (size_t)c.rhs * g.N;
+  float2* r = R + (size_t)c.rhs * g.N;
+  cdf32* xs = reinterpret_cast<cdf32*>(rsm_raw);
+  constexpr int SX = TX + 2, SY = TY + 2;
+  const int i0 = c.i - (int)(threadIdx.x % TX), j0 = c.j - (int)(threadIdx.x / TX);
+  const int nzl = c.k1 - c.k0 + 2;
+  {
+    const long long plane = (long long)g.nx * g.ny;
+    const cdf32 zero{{0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int q = threadIdx.x + u * NTHREADS;
+      if (q < SX * SY) {
+        const int ii = i0 - 1 + q % SX, jj = j0 - 1 + q / SX;
+        const bool inxy = ii >= 0 && ii < g.nx && jj >= 0 && jj < g.ny;
+        const cdf32* src_p = x + ((long long)(c.k0 - 1) * g.ny + jj) * g.nx + ii;
+        for (int kk = 0; kk < nzl; ++kk) {
+          const int kz = c.k0 - 1 + kk;
+          xs[kk * SX * SY + q] = (inxy && kz >= 0 && kz < g.nz) ? src_p[kk * plane] : zero;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  float rr = 0.f;
+  float acc[3] = {0.f, 0.f, 0.f};  // rho_0 re, im, ||r||^2
+  int om_e = -4096;
+  auto add_prod = [](float& s, float& cc, df32 k, df32 v) {
+    float p, e, t;
+    two_prod(k.hi, v.hi, p, e);
+    e = fmaf(k.hi, v.lo, fmaf(k.lo, v.hi, e));
+    two_sum(s, p, s, t);
+    cc += t + e;
+  };
+  if (c.in) {
+    const int li = (int)(threadIdx.x % TX) + 1, lj = (int)(threadIdx.x / TX) + 1;
+    const int mxy = face_mask(g, c.i, c.j, 0) & 15;
+    const long long plane = (long long)g.nx * g.ny;
+    long long id = vidx(g, c.i, c.j, c.k0);
+    for (int k = c.k0; k < c.k1; ++k, id += plane) {
+      const cdf32* xq = xs + ((k - c.k0 + 1) * SY + lj) * SX + li;
+      const cdf32 xc = xq[0];
+      const int m = mxy | ((k == 0) << 4) | ((k == g.nz - 1) << 5);
+      float sr, cr, si, ci;
+      two_prod(d0.hi, xc.re.hi, sr, cr);
+      cr = fmaf(d0.hi, xc.re.lo, fmaf(d0.lo, xc.re.hi, cr));
+      two_prod(d0.hi, xc.im.hi, si, ci);
+      ci = fmaf(d0.hi, xc.im.lo, fmaf(d0.lo, xc.im.hi, ci));
+      if (m) {
+#pragma unroll
+        for (int f = 0; f < 6; ++f)
+          if (m & (1 << f)) {
+            add_prod(sr, cr, dfa[f], xc.re);
+            add_prod(si, ci, dfa[f], xc.im);
+          }
+      }
+      if (b.dsig_d) {
+        const df32 ds = df_from(dsig_at<double>(b, c.rhs, id, g.N));
+        add_prod(sr, cr, ds, xc.re);
+        add_prod(si, ci, ds, xc.im);
+      }
+      add_prod(sr, cr, ndsi, xc.im);
+      add_prod(si, ci, dsi, xc.re);
+      float amax = 0.f;
+      auto sub_nb = [&](const cdf32& v) {
+        float t;
+        two_sum(sr, -v.re.hi, sr, t);
+        cr += t - v.re.lo;
+        two_sum(si, -v.im.hi, si, t);
+        ci += t - v.im.lo;
+        amax = fmaxf(amax, fmaxf(fabsf(v.re.hi), fabsf(v.im.hi)));
+      };
+      sub_nb(xq[-SX * SY]);
+      sub_nb(xq[SX * SY]);
+      sub_nb(xq[-1]);
+      sub_nb(xq[1]);
+      sub_nb(xq[-SX]);
+      sub_nb(xq[SX]);
+      float rh = -sr, rl = -cr;
+      if (id == src) {
+        float t;
+        two_sum(1.f, rh, rh, t);
+        rl += t;
+      }
+      const float fr = rh + rl, fi = -si + -ci;
+      rr = fmaf(fr, fr, fmaf(fi, fi, rr));
+      int ed = max(etheta, bexp_f(amax));
+      const int ec = max(bexp(xc.re), bexp(xc.im));
+      ed = max(ed, ec ? ec + 2 : 0);
+      if (id == src) ed = max(ed, 1023);
+      const int er = max(bexp_f(fr), bexp_f(fi));
+      if (er) om_e = max(om_e, ed ? er + 2 - ed : 4096);
+      const float2 rv = make_float2(fr * pre, fi * pre);
+      r[id] = rv;
+      // D^-1 of the cell: the real diagonal (faces, absorption perturbation) plus i sigma_im
+      float dre = cf.dint;
+      if (m) {
+#pragma unroll
+        for (int f = 0; f < 6; ++f)
+          if (m & (1 << f)) dre += cf.fa[f];
+      }
+      if (b.dsig_f) dre += dsig_at<float>(b, c.rhs, id, g.N);
+      const float den = fmaf(dre, dre, cf.dim * cf.dim);
+      const float2 dinv = make_float2(dre / den, -cf.dim / den);
+      // rho_0 = r^T D^-1 r (bilinear), ||r||^2
+      const float2 zr = make_float2(fmaf(rv.x, dinv.x, -rv.y * dinv.y), fmaf(rv.x, dinv.y, rv.y * dinv.x));
+      acc[0] = fmaf(rv.x, zr.x, fmaf(-rv.y, zr.y, acc[0]));
+      acc[1] = fmaf(rv.x, zr.y, fmaf(rv.y, zr.x, acc[1]));
+      acc[2] = fmaf(rv.x, rv.x, fmaf(rv.y, rv.y, acc[2]));
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float v4[4] = {rr, acc[0], acc[1], acc[2]};
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v4[q] += __shfl_down_sync(0xffffffffu, v4[q], o);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) om_e = max(om_e, __shfl_down_sync(0xffffffffu, om_e, o));
+  float* smf = reinterpret_cast<float*>(sm);
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) smf[q * NWARPS + warp] = v4[q];
+    smi[warp] = om_e;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t4[4] = {0.f, 0.f, 0.f, 0.f};
+    int mx = -4096;
+    for (int w = 0; w < NWARPS; ++w) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) t4[q] += smf[q * NWARPS + w];
+      mx = max(mx, smi[w]);
+    }
+    const int T_ = g.ntiles;
+    double* pb = b.part + (size_t)c.rhs * part_stride(T_);
+    pb[8 * T_ + 2 * c.tile] = (double)t4[0];
+    pb[8 * T_ + 2 * c.tile + 1] = (mx <= -4096) ? 0.0 : (mx >= 4096 ? INFINITY : ldexp(1.0, mx));
+    pb[2 * c.tile] = (double)t4[1];  // rho parity 0
+    pb[2 * c.tile + 1] = (double)t4[2];
+    pb[4 * T_ + c.tile] = (double)t4[3];  // ||r||^2 parity 0
+  }
+}
+
 // Floor of the componentwise test: theta = cw_floor * sigma * min |x| over the field's partner
 // optode cells (detectors for a source field, sources for a detector field); sigma is the real
 // shift and |x| the modulus for complex fields.
@@ -495,8 +663,14 @@ __global__ void k_theta(Geo g, Batch b, const X* __restrict__ x64, const int* __
     const X* x = x64 + (size_t)rhs * g.N;
     double mn = INFINITY;
     for (int q = 0; q < np; ++q) {
-      if constexpr (std::is_same<X, df32>::value) mn = fmin(mn, fabs((double)x[optode[p0 + q]].hi));
-      else mn = fmin(mn, sqrt(Traits<X>::abs2(x[optode[p0 + q]])));
+      if constexpr (std::is_same<X, df32>::value) {
+        mn = fmin(mn, fabs((double)x[optode[p0 + q]].hi));
+      } else if constexpr (std::is_same<X, cdf32>::value) {
+        const cdf32 v = x[optode[p0 + q]];
+        mn = fmin(mn, hypot((double)v.re.hi, (double)v.im.hi));
+      } else {
+        mn = fmin(mn, sqrt(Traits<X>::abs2(x[optode[p0 + q]])));
+      }
     }
     th = b.cw_floor * b.coef[rhs_lambda(b, rhs)].sigma_re * mn;
   }
@@ -1197,7 +1371,24 @@ __global__ void k_fold(Geo g, Batch b, X* __restrict__ x64, const T* __restrict_
     const double s = b.scale[rhs];
     X* x = x64 + (size_t)rhs * g.N;
     const T* e = E + (size_t)rhs * g.N;
-    if constexpr (std::is_same<X, df32>::value) {
+    if constexpr (std::is_same<X, cdf32>::value) {
+      // complex: both parts as in the real double-float update below
+      const df32 sd = df_from(s);
+      const cpx<float>* ec = reinterpret_cast<const cpx<float>*>(e);
+      for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < g.N;
+           v += (long long)gridDim.x * blockDim.x) {
+        const cpx<float> ev = ec[v];
+        cdf32 xv = x[v];
+        float p, q;
+        two_prod(sd.hi, ev.re, p, q);
+        q = fmaf(sd.lo, ev.re, q);
+        xv.re = df_add(xv.re, fast_two_sum(p, q));
+        two_prod(sd.hi, ev.im, p, q);
+        q = fmaf(sd.lo, ev.im, q);
+        xv.im = df_add(xv.im, fast_two_sum(p, q));
+        x[v] = xv;
+      }
+    } else if constexpr (std::is_same<X, df32>::value) {
       // x += s e with the product exact up to s's low part and the sum accurate (double-float);
       // four independent cells per thread and pass keep the dependent TwoSum chains overlapped
       const df32 sd = df_from(s);
@@ -1241,7 +1432,13 @@ __global__ void k_output(Geo g, Batch b, const X* __restrict__ x64, O* __restric
     const double sc = b.coef[b.lam0 + a].inv_Dh;
     O* out = (f < n_src) ? phi_src + ((size_t)a * n_src + f) * g.N : phi_det + ((size_t)a * n_det + (f - n_src)) * g.N;
     const X* x = x64 + (size_t)rhs * g.N;
-    if constexpr (std::is_same<X, df32>::value) {
+    if constexpr (std::is_same<X, cdf32>::value) {
+      const float scf = (float)sc;
+      for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < g.N; v += (long long)gridDim.x * blockDim.x) {
+        const cdf32 xv = x[v];
+        out[v] = O{(xv.re.hi + xv.re.lo) * scf, (xv.im.hi + xv.im.lo) * scf};
+      }
+    } else if constexpr (std::is_same<X, df32>::value) {
       const float scf = (float)sc;
       for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < g.N; v += (long long)gridDim.x * blockDim.x) {
         const df32 xv = x[v];
@@ -1550,6 +1747,8 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
   HYDOT_CUDA_TRY(ctx, cudaMemsetAsync(b.err, 0, sizeof(int), s));
   if constexpr (std::is_same<X, df32>::value)  // the residual's halo tile: up to 18 x 10 x 34 double-floats
     HYDOT_CUDA_TRY(ctx, raise_smem_limit(k_residual_df, sizeof(df32) * (g.tz + 2) * (TY + 2) * (TX + 2)));
+  if constexpr (std::is_same<X, cdf32>::value)
+    HYDOT_CUDA_TRY(ctx, raise_smem_limit(k_residual_cdf, sizeof(cdf32) * (g.tz + 2) * (TY + 2) * (TX + 2)));
   k_reset<<<(b.nrhs + 255) / 256, 256, 0, s>>>(b);
   ++ctx->launches;
   HYDOT_CUDA_TRY(ctx, cudaGetLastError());
@@ -1564,6 +1763,9 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
     cudaEvent_t t_res = timer_begin(ctx);
     if constexpr (std::is_same<X, df32>::value)
       k_residual_df<<<nblk, blk, sizeof(df32) * (g.tz + 2) * (TY + 2) * (TX + 2), s>>>(g, b, ctx->d_coef_f, x64, R);
+    else if constexpr (std::is_same<X, cdf32>::value)
+      k_residual_cdf<<<nblk, blk, sizeof(cdf32) * (g.tz + 2) * (TY + 2) * (TX + 2), s>>>(g, b, ctx->d_coef_f, x64,
+                                                                                        (float2*)R);
     else k_residual<T, X><<<nblk, blk, 0, s>>>(g, b, x64, R);
     ++ctx->launches;
     timer_end(ctx, t_res, HYDOT_KERNEL_RESIDUAL,
@@ -1920,7 +2122,7 @@ int solve_fields_impl(hydot_ctx* ctx, int lam0, int nlam, void* phi_src, void* p
   }
   using cf = cpx<float>;
   using cd = cpx<double>;
-  if (mixed) return run_solve<cf, cd, cf>(ctx, lam0, nlam, (cf*)phi_src, (cf*)phi_det, st);
+  if (mixed) return run_solve<cf, cdf32, cf>(ctx, lam0, nlam, (cf*)phi_src, (cf*)phi_det, st);
   return run_solve<cd, cd, cd>(ctx, lam0, nlam, (cd*)phi_src, (cd*)phi_det, st);
 }
 
