@@ -852,11 +852,29 @@ def run_kernel_case(name: str, reps: int = 3):
     sketch      the tensor-core passes Y = J Omega and B^T += J^T Q over one 16-wavelength chunk
                 (rank 200 + 20)
     apply       J x and J^T r over one 16-wavelength chunk of fields
+    solver_fd   the 32 complex fields of one wavelength of the 112x96x64 100 MHz phantom
+                (complex64 COCG + double-float refinement, ~1 GB of vectors)
     """
     import torch
 
     import paper_1410_0986_gb300 as hd
     import workloads
+
+    if name == "solver_fd":
+        p = workloads.config4_batch()[-1]
+        times = []
+        with hd.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=TOL_CW, cw_floor=CW_FLOOR,
+                                     max_lambda_per_call=1) as ctx:
+            for _ in range(reps):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record()
+                ctx.solve_fields(0, 1)
+                b.record()
+                torch.cuda.synchronize()
+                times.append(a.elapsed_time(b))
+        print(json.dumps({"kernel_case": name, "ms": times}))
+        return
 
     p = workloads.config(2)
     ns, nd, nc, N = p.n_src, p.n_det, p.n_chrom, p.grid.N
@@ -943,7 +961,8 @@ def main():
                     help="skip the uneven batch of six 100 MHz phantoms (sequential against hydot_solve_batch)")
     ap.add_argument("--no-compare-fp64", dest="compare_fp64", action="store_false")
     ap.add_argument("--cpu-sample", type=int, default=None, help=argparse.SUPPRESS)
-    ap.add_argument("--kernel-case", default=None, help="born_rows | solver | apply: small profiling case")
+    ap.add_argument("--kernel-case", default=None,
+                    help="born_rows | solver | solver_fd | sketch | apply: small profiling case")
     args = ap.parse_args()
     if args.kernel_case:
         run_kernel_case(args.kernel_case)

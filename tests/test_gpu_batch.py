@@ -92,3 +92,31 @@ def test_batch_errors(lib):
     finally:
         a.close()
         b.close()
+
+
+def test_config4_all_six_phantoms_in_one_call(lib):
+    """All six 100 MHz phantoms (32x32x24 ... 112x96x64, 16 + 16 optodes) at the last of the 64
+    wavelengths from one hydot_solve_batch call, with the benchmark's stopping rule (tol 1e-10,
+    tol_cw 1e-8, Born-aware floor 100): sampled fields (sources 0 and 15, detector 7) of every
+    phantom against the oracle's complex128 fields to 1e-6, and their Born products phi_s phi_d
+    within 1e-5 of the product's maximum."""
+    probs = workloads.config4_batch()
+    lam = probs[0].n_lambda - 1
+    ctxs = [lib.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=1e-8, cw_floor=100.0,
+                                     max_lambda_per_call=1) for p in probs]
+    try:
+        out = lib.solve_batch(ctxs, lam, 1)
+    finally:
+        for c in ctxs:
+            c.close()
+    for p, (ps, pd, st) in zip(probs, out):
+        assert st["n_not_converged"] == 0 and ps.dtype == torch.complex64
+        src, det = [0, p.n_src - 1], [7]
+        rs, rd = osolve.fields_separable(p, [lam], src=src, det=det)
+        gs = ps[0, src].cpu().numpy().astype(np.complex128)
+        gd = pd[0, det].cpu().numpy().astype(np.complex128)
+        for g, r in ((gs, rs[0]), (gd, rd[0])):
+            assert (np.linalg.norm(g - r, axis=-1) / np.linalg.norm(r, axis=-1)).max() <= 1e-6, p.name
+        for a in range(len(src)):
+            Hr, Hg = rs[0, a] * rd[0, 0], gs[a] * gd[0]
+            assert np.abs(Hg - Hr).max() <= 1e-5 * np.abs(Hr).max(), p.name
