@@ -52,8 +52,8 @@ KERNEL_NAMES = {"dir": "k_dir_roll (inner PCG pass 1)", "update": "k_update_roll
                 "sketch_project": "k_project_ws (tensor-core B^T += J^T Q)"}
 # DRAM bytes (read + write, ncu) per algorithmic byte, from the captures summarised under profiles/
 # (smaller cases of the same kernels, scaled by the units processed: active fields or rows)
-DRAM_PER_ALGORITHMIC_BYTE = {"dir": (100.97e6 + 22.14e6) / (64 * 3 * 196608 * 4),
-                             "update": (151.25e6 + 46.51e6) / (64 * 5 * 196608 * 4),
+DRAM_PER_ALGORITHMIC_BYTE = {"dir": (100.97e6 + 22.41e6) / (64 * 3 * 196608 * 4),
+                             "update": (151.24e6 + 45.80e6) / (64 * 5 * 196608 * 4),
                              "born_rows": (893.83e6 + 12.96e9) / (4096 * 4 * 196608 * 4)}
 TRAFFIC_NOTE = {"dir": "ncu on 64 fields of one wavelength (profiles/solver_roll_64fields.md), scaled by active "
                        "fields; writes partly still in L2 at kernel end",
