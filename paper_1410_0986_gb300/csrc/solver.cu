@@ -979,6 +979,7 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_dir_roll(Geo g, Batch b, con
                                                           const __grid_constant__ CUtensorMap mapR,
                                                           const __grid_constant__ CUtensorMap mapPold,
                                                           E* __restrict__ Pnew) {
+  static_assert(RS >= 3, "a slab buffer is refilled two slabs after its own");
   constexpr bool CPLX = !std::is_same<E, float>::value;
   extern __shared__ unsigned char dsm[];
   E* slab = align128<E>(dsm);  // [RS][r -> p_new, p_old][RP planes]
@@ -1201,6 +1202,7 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_update_roll(Geo g, Batch b, 
                                                              const __grid_constant__ CUtensorMap mapP,
                                                              const __grid_constant__ CUtensorMap mapE,
                                                              const __grid_constant__ CUtensorMap mapR) {
+  static_assert(RS >= 3, "a slab buffer is refilled two slabs after its own");
   constexpr bool CPLX = !std::is_same<E, float>::value;
   extern __shared__ unsigned char dsm[];
   unsigned char* slab = reinterpret_cast<unsigned char*>(align128<E>(dsm));  // [RS][p | e | r]

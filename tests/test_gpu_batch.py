@@ -120,3 +120,57 @@ def test_config4_all_six_phantoms_in_one_call(lib):
         for a in range(len(src)):
             Hr, Hg = rs[0, a] * rd[0, 0], gs[a] * gd[0]
             assert np.abs(Hg - Hr).max() <= 1e-5 * np.abs(Hr).max(), p.name
+
+
+def _perturbed_oracle(p, dc):
+    """Fields of the medium with a per-voxel absorption change: sparse LU of A_lambda + h^3 diag(dmu_a)
+    (complex when the problem is modulated)."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+
+    from oracle import model
+
+    N, nc = p.grid.N, p.n_chrom
+    outs = []
+    for lam in range(p.n_lambda):
+        dmua = sum(p.eps[lam, c] * dc[c * N:(c + 1) * N] for c in range(nc))
+        lu = spla.splu((model.operator(p, lam) + sp.diags(p.grid.h ** 3 * dmua)).tocsc())
+        cells = list(p.src_voxels()) + list(p.det_voxels())
+        B = np.zeros((N, len(cells)), dtype=lu.L.dtype)
+        B[cells, np.arange(len(cells))] = 1.0
+        outs.append(lu.solve(B).T)
+    out = np.stack(outs)
+    return out[:, :p.n_src], out[:, p.n_src:]
+
+
+def test_batch_of_mixed_kinds(lib):
+    """One call over contexts that take different paths: FP64 real, mixed real with an absorption
+    perturbation (generic kernels), mixed complex with odd nx and a perturbation (generic complex
+    kernels, double-float complex residual with the per-voxel term), and mixed real with
+    shift-invariant guesses (TMA passes). Each equals its own single call bit for bit and meets the
+    oracle (1e-10 FP64, 1e-6 mixed)."""
+    pa = workloads.small(seed=61, nx=13, ny=11, nz=9, n_src=2, n_det=2, n_lambda=2)
+    pb = workloads.make_problem(workloads.Grid(20, 16, 12, 2.0), 2, 3, 2, seed=62, geometry="transmission", margin=1)
+    pc = workloads.small(seed=63, nx=15, ny=12, nz=9, n_src=2, n_det=2, n_lambda=2, freq_mhz=100.0)
+    pdd = workloads.make_problem(workloads.Grid(24, 24, 16, 2.0), 3, 3, 2, seed=64, geometry="transmission", margin=1)
+    dcb = workloads.ellipsoid_anomaly(pb.grid, seed=65, contrast=0.5)
+    dcc = workloads.ellipsoid_anomaly(pc.grid, seed=66, contrast=0.5)
+    ctxs = [lib.Context.from_problem(pa, precision="fp64", tol=1e-13, tol_cw=0.0),
+            lib.Context.from_problem(pb, precision="mixed", tol=1e-10, tol_cw=1e-8),
+            lib.Context.from_problem(pc, precision="mixed", tol=1e-10, tol_cw=1e-8),
+            lib.Context.from_problem(pdd, precision="mixed", tol=1e-10, tol_cw=1e-8, cw_floor=100.0)]
+    try:
+        ctxs[1].set_absorption(dcb)
+        ctxs[2].set_absorption(dcc)
+        ctxs[3].set_shift_guess(16)
+        out = lib.solve_batch(ctxs, 0, 2)
+        single = [c.solve_fields(0, 2) for c in ctxs]
+    finally:
+        for c in ctxs:
+            c.close()
+    refs = [osolve.fields_splu(pa), _perturbed_oracle(pb, dcb), _perturbed_oracle(pc, dcc), osolve.fields_splu(pdd)]
+    for q, ((ps, pd, st), (qs, qd, _), (rs, rd)) in enumerate(zip(out, single, refs)):
+        assert st["n_not_converged"] == 0, q
+        assert torch.equal(ps, qs) and torch.equal(pd, qd), q
+        tol = 1e-10 if q == 0 else 1e-6
+        assert _rel(ps, rs) <= tol and _rel(pd, rd) <= tol, q
