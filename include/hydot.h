@@ -141,7 +141,9 @@ int hydot_solve_fields(hydot_ctx* ctx, int lam0, int nlam, void* phi_src, void* 
  * on the caller's current device and distinct (a context repeated in the list is HYDOT_ERR_ARG:
  * its workspace would be shared by two threads). phi_src / phi_det entries follow the rules of
  * hydot_solve_fields; st and status may be NULL, else they receive n entries (status: each
- * context's own return code, its message in hydot_last_error of that context). Synchronous.
+ * context's own return code, its message in hydot_last_error of that context; when the lists
+ * themselves are rejected, no context runs, every status entry holds that code and the message is
+ * in hydot_last_error(NULL)). Synchronous.
  * Returns the first error other than HYDOT_ERR_NOT_CONVERGED in list order, else
  * HYDOT_ERR_NOT_CONVERGED when any field missed its tolerance, else HYDOT_OK. */
 int hydot_solve_batch(hydot_ctx* const* ctxs, int n, const int* lam0, const int* nlam, void* const* phi_src,

@@ -438,8 +438,9 @@ def solve_batch(contexts: Sequence[Context], lam0, nlam, *, raise_not_converged:
     for ctx in contexts:
         ctx._stream()
     if rc != 0 and not (rc == _lib.HYDOT_ERR_NOT_CONVERGED and not raise_not_converged):
-        bad = next((i for i in range(n) if status[i] == rc), None)
-        if bad is None:  # the lists themselves were rejected before any context ran
-            raise HydotError(rc, lib.hydot_last_error(None).decode())
+        whole = lib.hydot_last_error(None).decode()
+        if whole:  # the lists themselves were rejected before any context ran
+            raise HydotError(rc, whole)
+        bad = next(i for i in range(n) if status[i] == rc)
         raise HydotError(rc, f"context {bad}: {lib.hydot_last_error(contexts[bad]._ctx).decode()}")
     return [(ps, pd, st[i].as_dict()) for i, (ps, pd) in enumerate(outs)]

@@ -277,7 +277,13 @@ int hydot_solve_fields(hydot_ctx* ctx, int lam0, int nlam, void* phi_src, void* 
 
 int hydot_solve_batch(hydot_ctx* const* ctxs, int n, const int* lam0, const int* nlam, void* const* phi_src,
                       void* const* phi_det, hydot_stats* st, int* status) {
-  auto bad = [](const char* m) { g_setup_error = m; return (int)HYDOT_ERR_ARG; };
+  g_setup_error.clear();  // set again below only when the lists themselves are rejected
+  auto bad = [&](const char* m) {  // the lists themselves are wrong: no context ran
+    g_setup_error = m;
+    if (status && n > 0)
+      for (int i = 0; i < n; ++i) status[i] = HYDOT_ERR_ARG;
+    return (int)HYDOT_ERR_ARG;
+  };
   if (n < 0) return bad("batch size is negative");
   if (n > 0 && (!ctxs || !lam0 || !nlam || !phi_src || !phi_det)) return bad("a batch list is NULL");
   std::set<const hydot_ctx*> seen;
@@ -289,10 +295,17 @@ int hydot_solve_batch(hydot_ctx* const* ctxs, int n, const int* lam0, const int*
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     g_setup_error = "cudaGetDevice failed";
+    if (status)
+      for (int i = 0; i < n; ++i) status[i] = HYDOT_ERR_CUDA;
     return HYDOT_ERR_CUDA;
   }
   for (int i = 0; i < n; ++i)
-    if (ctxs[i]->device != dev) return fail(ctxs[i], HYDOT_ERR_ARG, "context is not on the caller's current device");
+    if (ctxs[i]->device != dev) {
+      if (status)
+        for (int q = 0; q < n; ++q) status[q] = HYDOT_ERR_ARG;
+      g_setup_error = "context " + std::to_string(i) + " is not on the caller's current device";
+      return fail(ctxs[i], HYDOT_ERR_ARG, g_setup_error);
+    }
   std::vector<int> rc(n, HYDOT_OK);
   auto one = [&](int i) {
     // a new host thread starts on device 0: adopt the caller's device before any CUDA call

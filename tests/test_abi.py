@@ -128,5 +128,7 @@ def test_null_arguments(lib):
     assert lib.hydot_solve_batch(None, 0, None, None, None, None, None, None) == L.HYDOT_OK
     assert lib.hydot_solve_batch(None, -1, None, None, None, None, None, None) == L.HYDOT_ERR_ARG
     assert lib.hydot_solve_batch(None, 1, i1, i1, v1, v1, None, None) == L.HYDOT_ERR_ARG
-    assert lib.hydot_solve_batch(v1, 1, i1, i1, v1, v1, None, None) == L.HYDOT_ERR_ARG
+    st1 = (C.c_int * 1)(7)
+    assert lib.hydot_solve_batch(v1, 1, i1, i1, v1, v1, None, st1) == L.HYDOT_ERR_ARG
+    assert st1[0] == L.HYDOT_ERR_ARG and "NULL" in lib.hydot_last_error(None).decode()
     lib.hydot_destroy(None)
