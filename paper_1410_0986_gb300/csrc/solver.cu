@@ -322,6 +322,67 @@ __global__ void __launch_bounds__(NTHREADS) k_residual(Geo g, Batch b, const X* 
   }
 }
 
+// Stages a tile of the iterate with its one-cell halo, [nzl][TY + 2][TX + 2] elements of X, zeros
+// outside the grid, into xs: thread t takes plane positions t and t + NTHREADS of every staged
+// plane, and every load of the block is issued before any cell is summed.
+template <typename X>
+__device__ __forceinline__ void stage_halo_tile(const Geo& g, const TileCoord& c, const X* __restrict__ x, X* xs) {
+  constexpr int SX = TX + 2, SY = TY + 2;
+  const int i0 = c.i - (int)(threadIdx.x % TX), j0 = c.j - (int)(threadIdx.x / TX);
+  const int nzl = c.k1 - c.k0 + 2;
+  const long long plane = (long long)g.nx * g.ny;
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int q = threadIdx.x + u * NTHREADS;
+    if (q < SX * SY) {
+      const int ii = i0 - 1 + q % SX, jj = j0 - 1 + q / SX;
+      const bool inxy = ii >= 0 && ii < g.nx && jj >= 0 && jj < g.ny;
+      const X* src_p = x + ((long long)(c.k0 - 1) * g.ny + jj) * g.nx + ii;
+      for (int kk = 0; kk < nzl; ++kk) {
+        const int kz = c.k0 - 1 + kk;
+        xs[kk * SX * SY + q] = (inxy && kz >= 0 && kz < g.nz) ? src_p[kk * plane] : X{};
+      }
+    }
+  }
+}
+
+// Block sums of the residual pass in FP32 (each partial needs only ~1e-7 relative accuracy; the
+// FP64 pipe is slow on this GPU), one conversion per partial, written to the tile's slots:
+// v = {||r64||^2, rho re, rho im, ||r||^2}; the per-field sums over tiles stay FP64.
+__device__ __forceinline__ void residual_partials(const Geo& g, const Batch& b, const TileCoord& c, float (&v)[4],
+                                                  int om_e, double* sm, int* smi) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) om_e = max(om_e, __shfl_down_sync(0xffffffffu, om_e, o));
+  float* smf = reinterpret_cast<float*>(sm);
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) smf[q * NWARPS + warp] = v[q];
+    smi[warp] = om_e;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t4[4] = {0.f, 0.f, 0.f, 0.f};
+    int mx = -4096;
+    for (int w = 0; w < NWARPS; ++w) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) t4[q] += smf[q * NWARPS + w];
+      mx = max(mx, smi[w]);
+    }
+    const int T_ = g.ntiles;
+    double* pb = b.part + (size_t)c.rhs * part_stride(T_);
+    pb[8 * T_ + 2 * c.tile] = (double)t4[0];
+    pb[8 * T_ + 2 * c.tile + 1] = (mx <= -4096) ? 0.0 : (mx >= 4096 ? INFINITY : ldexp(1.0, mx));
+    pb[2 * c.tile] = (double)t4[1];  // rho parity 0
+    pb[2 * c.tile + 1] = (double)t4[2];
+    pb[4 * T_ + c.tile] = (double)t4[3];  // ||r||^2 parity 0
+  }
+}
+
 // The same pass for the mixed real path, whose iterate is double-float (df32). Per cell the
 // residual r = b - (d x_c - sum of the six neighbours) is a short signed sum; it is accumulated as
 // s + c: the high parts enter through TwoSum (exact), the low parts and the TwoSum errors through
@@ -354,29 +415,10 @@ __global__ void __launch_bounds__(NTHREADS) k_residual_df(Geo g, Batch b, const 
   const int etheta = bexp(b.theta[c.rhs]);
   const df32* x = x64 + (size_t)c.rhs * g.N;
   float* r = R + (size_t)c.rhs * g.N;
-  // the tile with a one-cell halo, [tz + 2][TY + 2][TX + 2], zeros outside the grid: every load of
-  // the block is issued before any cell is summed
+  // the tile with a one-cell halo, [tz + 2][TY + 2][TX + 2], zeros outside the grid
   df32* xs = reinterpret_cast<df32*>(rsm_raw);
   constexpr int SX = TX + 2, SY = TY + 2;
-  const int i0 = c.i - (int)(threadIdx.x % TX), j0 = c.j - (int)(threadIdx.x / TX);
-  const int nzl = c.k1 - c.k0 + 2;
-  {
-    // thread t loads plane positions t and t + NTHREADS (< SX * SY) of every staged plane
-    const long long plane = (long long)g.nx * g.ny;
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int q = threadIdx.x + u * NTHREADS;
-      if (q < SX * SY) {
-        const int ii = i0 - 1 + q % SX, jj = j0 - 1 + q / SX;
-        const bool inxy = ii >= 0 && ii < g.nx && jj >= 0 && jj < g.ny;
-        const df32* src_p = x + ((long long)(c.k0 - 1) * g.ny + jj) * g.nx + ii;
-        for (int kk = 0; kk < nzl; ++kk) {
-          const int kz = c.k0 - 1 + kk;
-          xs[kk * SX * SY + q] = (inxy && kz >= 0 && kz < g.nz) ? src_p[kk * plane] : df32{0.f, 0.f};
-        }
-      }
-    }
-  }
+  stage_halo_tile(g, c, x, xs);
   __syncthreads();
   float rr = 0.f;
   float acc[3] = {0.f, 0.f, 0.f};  // rho_0, (unused), ||r||^2
@@ -444,39 +486,8 @@ __global__ void __launch_bounds__(NTHREADS) k_residual_df(Geo g, Batch b, const 
       acc[2] = fmaf(rv, rv, acc[2]);
     }
   }
-  // block sums in FP32 (each partial needs only ~1e-7 relative accuracy; the FP64 pipe is slow on
-  // this GPU), one conversion per partial; the per-field sums over tiles stay FP64
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float v3[3] = {rr, acc[0], acc[2]};
-#pragma unroll
-  for (int q = 0; q < 3; ++q)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v3[q] += __shfl_down_sync(0xffffffffu, v3[q], o);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) om_e = max(om_e, __shfl_down_sync(0xffffffffu, om_e, o));
-  float* smf = reinterpret_cast<float*>(sm);
-  if (lane == 0) {
-#pragma unroll
-    for (int q = 0; q < 3; ++q) smf[q * NWARPS + warp] = v3[q];
-    smi[warp] = om_e;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float t3[3] = {0.f, 0.f, 0.f};
-    int mx = -4096;
-    for (int w = 0; w < NWARPS; ++w) {
-#pragma unroll
-      for (int q = 0; q < 3; ++q) t3[q] += smf[q * NWARPS + w];
-      mx = max(mx, smi[w]);
-    }
-    const int T_ = g.ntiles;
-    double* pb = b.part + (size_t)c.rhs * part_stride(T_);
-    pb[8 * T_ + 2 * c.tile] = (double)t3[0];
-    pb[8 * T_ + 2 * c.tile + 1] = (mx <= -4096) ? 0.0 : (mx >= 4096 ? INFINITY : ldexp(1.0, mx));
-    pb[2 * c.tile] = (double)t3[1];   // rho parity 0
-    pb[2 * c.tile + 1] = 0.0;
-    pb[4 * T_ + c.tile] = (double)t3[2];  // ||r||^2 parity 0
-  }
+  float v4[4] = {rr, acc[0], 0.f, acc[2]};
+  residual_partials(g, b, c, v4, om_e, sm, smi);
 }
 
 // The same pass for complex fields with a double-float iterate (re and im each a df32). The
@@ -507,25 +518,7 @@ __global__ void __launch_bounds__(NTHREADS) k_residual_cdf(Geo g, Batch b, const
   float2* r = R + (size_t)c.rhs * g.N;
   cdf32* xs = reinterpret_cast<cdf32*>(rsm_raw);
   constexpr int SX = TX + 2, SY = TY + 2;
-  const int i0 = c.i - (int)(threadIdx.x % TX), j0 = c.j - (int)(threadIdx.x / TX);
-  const int nzl = c.k1 - c.k0 + 2;
-  {
-    const long long plane = (long long)g.nx * g.ny;
-    const cdf32 zero{{0.f, 0.f}, {0.f, 0.f}};
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int q = threadIdx.x + u * NTHREADS;
-      if (q < SX * SY) {
-        const int ii = i0 - 1 + q % SX, jj = j0 - 1 + q / SX;
-        const bool inxy = ii >= 0 && ii < g.nx && jj >= 0 && jj < g.ny;
-        const cdf32* src_p = x + ((long long)(c.k0 - 1) * g.ny + jj) * g.nx + ii;
-        for (int kk = 0; kk < nzl; ++kk) {
-          const int kz = c.k0 - 1 + kk;
-          xs[kk * SX * SY + q] = (inxy && kz >= 0 && kz < g.nz) ? src_p[kk * plane] : zero;
-        }
-      }
-    }
-  }
+  stage_halo_tile(g, c, x, xs);
   __syncthreads();
   float rr = 0.f;
   float acc[3] = {0.f, 0.f, 0.f};  // rho_0 re, im, ||r||^2
@@ -614,37 +607,8 @@ __global__ void __launch_bounds__(NTHREADS) k_residual_cdf(Geo g, Batch b, const
       acc[2] = fmaf(rv.x, rv.x, fmaf(rv.y, rv.y, acc[2]));
     }
   }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float v4[4] = {rr, acc[0], acc[1], acc[2]};
-#pragma unroll
-  for (int q = 0; q < 4; ++q)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v4[q] += __shfl_down_sync(0xffffffffu, v4[q], o);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) om_e = max(om_e, __shfl_down_sync(0xffffffffu, om_e, o));
-  float* smf = reinterpret_cast<float*>(sm);
-  if (lane == 0) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) smf[q * NWARPS + warp] = v4[q];
-    smi[warp] = om_e;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float t4[4] = {0.f, 0.f, 0.f, 0.f};
-    int mx = -4096;
-    for (int w = 0; w < NWARPS; ++w) {
-#pragma unroll
-      for (int q = 0; q < 4; ++q) t4[q] += smf[q * NWARPS + w];
-      mx = max(mx, smi[w]);
-    }
-    const int T_ = g.ntiles;
-    double* pb = b.part + (size_t)c.rhs * part_stride(T_);
-    pb[8 * T_ + 2 * c.tile] = (double)t4[0];
-    pb[8 * T_ + 2 * c.tile + 1] = (mx <= -4096) ? 0.0 : (mx >= 4096 ? INFINITY : ldexp(1.0, mx));
-    pb[2 * c.tile] = (double)t4[1];  // rho parity 0
-    pb[2 * c.tile + 1] = (double)t4[2];
-    pb[4 * T_ + c.tile] = (double)t4[3];  // ||r||^2 parity 0
-  }
+  residual_partials(g, b, c, v4, om_e, sm, smi);
 }
 
 // Floor of the componentwise test: theta = cw_floor * sigma * min |x| over the field's partner
