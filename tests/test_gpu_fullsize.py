@@ -26,6 +26,7 @@ def solved(lib):
     p = workloads.config(2)
     ctx = lib.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=1e-8, max_lambda_per_call=CHUNK,
                                   cw_floor=CW_FLOOR)
+    ctx.set_shift_guess(40)  # the benchmark's setting: solves start from the shift-invariant guesses
     out = {}
     for a, lam in enumerate(gold["lams"]):
         lam0 = (int(lam) // CHUNK) * CHUNK
@@ -114,6 +115,7 @@ def test_config3_misfit_gradient_on_a_wavelength_slice(lib):
     del rs, rd
     with lib.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=1e-8, cw_floor=CW_FLOOR,
                                   max_lambda_per_call=nl) as ctx:
+        ctx.set_shift_guess(40)  # as in the benchmark's gradient workload
         ps, pd, st = ctx.solve_fields(0, nl)
         x = torch.tensor(dc, dtype=torch.float32, device="cuda", requires_grad=True)
         r = born_apply(x, ctx, ps, pd, 0, nl) - torch.tensor(y, dtype=torch.float32, device="cuda")
@@ -125,6 +127,43 @@ def test_config3_misfit_gradient_on_a_wavelength_slice(lib):
     # all 2.36 M components, norm-wise (the components at optode cells carry products with the
     # far field of the other optodes, which the oracle's fields resolve entry by entry)
     assert np.linalg.norm(g - g_ref) <= 1e-5 * np.linalg.norm(g_ref)
+
+
+def test_config5_fields_at_the_sketch_configuration(lib):
+    """Config 5 at full size (128x128x96, h = 1 mm, 1.57 M voxels, 64 + 64 optodes) on wavelengths
+    0-3, solved as the benchmark's sketch phase solves them (512 fields in one call): sources 0 and
+    63 and detectors 0 and 63 at wavelengths 0 and 3 against the oracle's separable FP64 fields, at
+    2,000 sampled voxels and every optode cell (entrywise against the field norm <= 1e-6, optode
+    cells entry by entry <= 1e-5), and their Born products within 1e-5 of the row maximum."""
+    from oracle import solve as osolve
+
+    p = workloads.config(5)
+    lams, src, det = [0, 3], [0, p.n_src - 1], [0, p.n_det - 1]
+    rs, rd = osolve.fields_separable(p, lams, src=src, det=det)
+    with lib.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=1e-8, cw_floor=CW_FLOOR,
+                                  max_lambda_per_call=4) as ctx:
+        ps, pd, st = ctx.solve_fields(0, 4)
+    assert st["n_not_converged"] == 0 and st["n_fields"] == 4 * (p.n_src + p.n_det)
+    n_opt = p.n_src + p.n_det
+    vox = np.concatenate([np.random.default_rng(501).choice(p.grid.N, 2000, replace=False),
+                          p.src_voxels(), p.det_voxels()])
+    vt = torch.tensor(vox, device="cuda")
+    for a, lam in enumerate(lams):
+        gs = ps[lam][src][:, vt].double().cpu().numpy()
+        gd = pd[lam][det][:, vt].double().cpu().numpy()
+        for got, full in ((gs, rs[a]), (gd, rd[a])):
+            ref = full[:, vox]
+            nrm = np.linalg.norm(full, axis=1)
+            assert (np.abs(got - ref).max(axis=1) / nrm).max() <= 1e-6
+            rel = np.abs(got[:, -n_opt:] - ref[:, -n_opt:]) / np.abs(ref[:, -n_opt:])
+            assert rel.max() <= 1e-5, rel.max()
+        for i in range(len(src)):
+            for j in range(len(det)):
+                Hr = rs[a][i, vox] * rd[a][j, vox]
+                Hg = gs[i] * gd[j]
+                # the row maximum of H over all voxels, from the oracle's full fields
+                hmax = np.abs(rs[a][i] * rd[a][j]).max()
+                assert np.abs(Hg - Hr).max() <= 1e-5 * hmax
 
 
 @pytest.mark.parametrize("which", [0, 1])
