@@ -573,7 +573,7 @@ def gradient_phase(hd, pk, reps=5):
 
 
 def batch_phase(hd, n_lam=4, reps=2, chunk=8):
-    """The uneven frequency-domain batch (config 4): six 100 MHz phantoms from 32x32x24 to
+    """The uneven frequency-domain batch: six 100 MHz phantoms from 32x32x24 to
     112x96x64, 16 + 16 optodes each, complex64 COCG with double-float refinement to the metric's
     stopping rule (tol 1e-10, tol_cw 1e-8 with the Born-aware floor). Two measurements:
     (1) wavelengths 0..n_lam-1 solved one phantom after another on one stream against all six from

@@ -133,7 +133,7 @@ int hydot_solve_fields(hydot_ctx* ctx, int lam0, int nlam, void* phi_src, void* 
                        hydot_stats* st);
 
 /* Field solves of several contexts in one call: a batch of independent problems of uneven size
- * (one phantom per context, e.g. the frequency-domain phantoms of Section 6), each solved as
+ * (one phantom per context, e.g. frequency-domain phantoms of different grid sizes), each solved as
  * hydot_solve_fields(ctxs[i], lam0[i], nlam[i], phi_src[i], phi_det[i], &st[i]) would. The
  * contexts run concurrently, each from its own host thread on the stream its context holds, so
  * small grids overlap on the GPU instead of queueing behind one another; give every context its

@@ -127,7 +127,7 @@ def test_tma_and_generic_kernels_agree(hd, oracle_fields, monkeypatch):
 
 
 def test_config1_fp64_fields_and_born_matrix(hd):
-    """Config 1 in full: 24x24x16, 8+8 optodes on the top face, 16 wavelengths, FP64."""
+    """The FP64 workload in full: 24x24x16, 8+8 optodes on the top face, 16 wavelengths."""
     p = workloads.config(1)
     rs, rd = osolve.fields_splu(p)
     with hd.Context.from_problem(p, precision="fp64", tol=1e-13, tol_cw=0.0) as ctx:

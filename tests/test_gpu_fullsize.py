@@ -92,7 +92,7 @@ def test_apply_adjoint_identity_full_size(solved):
 
 
 def test_config3_misfit_gradient_on_a_wavelength_slice(lib):
-    """Config 3 at full grid size (96x96x64, h = 1.5 mm, 24 + 24 optodes) on wavelengths 0-3:
+    """The gradient workload at full grid size (96x96x64, h = 1.5 mm, 24 + 24 optodes) on wavelengths 0-3:
     misfit 0.5 ||J dc - y||^2 with the seeded ellipsoidal anomaly, y = J dc_true + noise at 30 dB;
     the autograd gradient (mixed-precision fields, FP32 adjoint kernel) against the oracle's
     J^T (J dc - y) from its own FP64 fields, at 64 seeded coordinates, relative 1e-4 of the largest
@@ -130,7 +130,7 @@ def test_config3_misfit_gradient_on_a_wavelength_slice(lib):
 
 
 def test_config5_fields_at_the_sketch_configuration(lib):
-    """Config 5 at full size (128x128x96, h = 1 mm, 1.57 M voxels, 64 + 64 optodes) on wavelengths
+    """The large hyperspectral workload at full size (128x128x96, h = 1 mm, 1.57 M voxels, 64 + 64 optodes) on wavelengths
     0-3, solved as the benchmark's sketch phase solves them (512 fields in one call): sources 0 and
     63 and detectors 0 and 63 at wavelengths 0 and 3 against the oracle's separable FP64 fields, at
     2,000 sampled voxels and every optode cell (entrywise against the field norm <= 1e-6, optode
@@ -168,7 +168,7 @@ def test_config5_fields_at_the_sketch_configuration(lib):
 
 @pytest.mark.parametrize("which", [0, 1])
 def test_config4_frequency_domain_phantoms(lib, which):
-    """Config 4 frequency-domain phantoms (100 MHz, complex-symmetric COCG in complex64 with
+    """The uneven batch of frequency-domain phantoms (100 MHz, complex-symmetric COCG in complex64 with
     complex128 refinement), the two smallest grids of the uneven batch on wavelengths 0-1: fields at
     every optode cell and 2,000 sampled voxels against the oracle's complex128 fields."""
     from oracle import solve as osolve

@@ -174,7 +174,7 @@ def gaussian(seed: int, shape, dtype=np.float64) -> np.ndarray:
     return rng.standard_normal(size=shape).astype(dtype, copy=False)
 
 
-# The five named workloads. Spacings other than config 1's 2 mm are this
+# The five named workloads. Spacings other than the 24x24x16 workload's 2 mm are this
 # project's choice (keeping the box near the paper's 12 cm phantom scale).
 def config(cfg: int) -> Problem:
     s = SEED_BASE + cfg
