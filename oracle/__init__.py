@@ -17,7 +17,7 @@ solve   Sparse-direct (SuperLU) fields, the definition of record; an
 born    Eqn:lippschwin / eqn:measurement: explicit Born matrix J, J x, J^T y,
         and the adjoint-solve form of J^T y.
 sketch  Appendix A.1: randomized range finder + SVD at fixed rank, and the
-        exact truncated-SVD optimum it is judged against.
+        exact truncated-SVD optimum it is compared with.
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test against
 something other than itself (closed forms, conservation, finite differences

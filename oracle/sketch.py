@@ -14,7 +14,7 @@ The merge across source-detector blocks (Section 4.2, agglomeration) is the
 row-block sum B = sum_blocks Q_blk^T A_blk, which this unblocked restatement
 computes in one product.
 
-``truncated_svd`` is the optimum the sketch is judged against: the best rank-r
+``truncated_svd`` is the optimum the sketch is compared with: the best rank-r
 approximation error in the 2-norm is sigma_{r+1} (Section 4.2).
 """
 from __future__ import annotations
