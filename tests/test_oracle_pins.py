@@ -203,6 +203,28 @@ def test_frequency_domain_limits():
     assert np.array_equal(A, A.T) and not np.allclose(A, A.conj().T)
 
 
+
+@pytest.mark.parametrize("freq", [100.0, 400.0])
+def test_frequency_domain_inverse_bounded_by_the_continuous_wave_inverse(freq):
+    """The bound behind the componentwise floor for complex fields: the modulation adds the same
+    imaginary shift to every diagonal entry, so |A^-1| <= (Re A)^-1 entrywise, and Re A is the
+    continuous-wave operator (an M-matrix with (Re A) 1 >= mu_a h^3 entrywise, so the row sums of
+    (Re A)^-1 are at most 1 / (mu_a h^3)). Dense inverses on a small grid, all faces Robin and one
+    Dirichlet face."""
+    p = workloads.small(nx=7, ny=6, nz=5, freq_mhz=freq, robin_A=(0.0, 3.0, 3.0, 3.0, 3.0, 3.0))
+    A = model.operator(p, 0).toarray()
+    Ar = A.real
+    assert np.allclose(A.imag, np.diag(np.diag(A.imag))) and np.ptp(np.diag(A.imag)) == 0.0
+    assert np.diag(A.imag)[0] > 0.0
+    ia, ir = np.abs(np.linalg.inv(A)), np.linalg.inv(Ar)
+    assert ir.min() > 0.0
+    assert (ia <= ir * (1 + 1e-12)).all()
+    # strictly below where the modulation matters (its shift is not negligible here)
+    assert (ia < ir).mean() > 0.99
+    mua, _ = model.wavelength_coefficients(p)
+    assert (ir.sum(axis=1) <= 1.0 / (mua[0] * p.grid.h ** 3) * (1 + 1e-12)).all()
+
+
 # ---------------------------------------------------------------- Born rows (eqn:lippschwin)
 
 def test_born_entries_are_fd_of_nonlinear_forward_model():
