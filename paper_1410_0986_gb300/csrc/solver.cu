@@ -1465,12 +1465,14 @@ __global__ void k_dsig(const double* __restrict__ dc, const double* __restrict__
 
 // ---------------------------------------------------------------- rolling-pass variants
 // {planes per slab, slab buffers}; the autotuner picks one per context (they give identical bits).
-// Complex64 slabs take twice the shared memory per plane, hence their own, shallower set.
+// Complex64 slabs take twice the shared memory per plane, hence their own, shallower set; complex
+// variants 0 and 3 share the 2 x 4 slabs and differ in pass 1's register budget (three or four
+// blocks per SM).
 struct RollVariant {
   int rp, rs;
 };
 constexpr RollVariant ROLL_VARIANTS[HYDOT_ROLL_VARIANTS] = {{4, 4}, {2, 6}, {8, 3}, {4, 5}};
-constexpr RollVariant ROLL_VARIANTS_C[HYDOT_ROLL_VARIANTS] = {{2, 4}, {2, 6}, {4, 3}, {4, 4}};
+constexpr RollVariant ROLL_VARIANTS_C[HYDOT_ROLL_VARIANTS] = {{2, 4}, {2, 6}, {4, 3}, {2, 4}};
 
 __host__ __device__ constexpr int rp_index(int rp) { return rp == 2 ? 0 : (rp == 4 ? 1 : 2); }
 
@@ -1512,7 +1514,7 @@ void roll_dispatch(hydot_ctx* ctx, int v, const Geo& g, const Batch& b, int it, 
     switch (v) {
       case 1: roll_iteration<float2, 2, 6, 2, 2>(ctx, g, b, it, nrb, e, r, p); break;
       case 2: roll_iteration<float2, 4, 3, 2, 2>(ctx, g, b, it, nrb, e, r, p); break;
-      case 3: roll_iteration<float2, 4, 4, 2, 1>(ctx, g, b, it, nrb, e, r, p); break;
+      case 3: roll_iteration<float2, 2, 4, 4, 3>(ctx, g, b, it, nrb, e, r, p); break;
       default: roll_iteration<float2, 2, 4, 3, 3>(ctx, g, b, it, nrb, e, r, p); break;
     }
     return;
@@ -1533,7 +1535,7 @@ int roll_setup(hydot_ctx* ctx) {
     int rc = roll_attrs<float2, 2, 4, 3, 3>(ctx);
     if (!rc) rc = roll_attrs<float2, 2, 6, 2, 2>(ctx);
     if (!rc) rc = roll_attrs<float2, 4, 3, 2, 2>(ctx);
-    if (!rc) rc = roll_attrs<float2, 4, 4, 2, 1>(ctx);
+    if (!rc) rc = roll_attrs<float2, 2, 4, 4, 3>(ctx);
     return rc;
   }
   int rc = roll_attrs<float, 4, 4, 4, 3>(ctx);
