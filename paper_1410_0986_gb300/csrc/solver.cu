@@ -1471,7 +1471,7 @@ __global__ void k_dsig(const double* __restrict__ dc, const double* __restrict__
 struct RollVariant {
   int rp, rs;
 };
-constexpr RollVariant ROLL_VARIANTS[HYDOT_ROLL_VARIANTS] = {{4, 4}, {2, 6}, {8, 3}, {4, 5}};
+constexpr RollVariant ROLL_VARIANTS[HYDOT_ROLL_VARIANTS] = {{4, 4}, {2, 6}, {4, 3}, {4, 5}};
 constexpr RollVariant ROLL_VARIANTS_C[HYDOT_ROLL_VARIANTS] = {{2, 4}, {2, 6}, {4, 3}, {2, 4}};
 
 __host__ __device__ constexpr int rp_index(int rp) { return rp == 2 ? 0 : (rp == 4 ? 1 : 2); }
@@ -1524,7 +1524,7 @@ void roll_dispatch(hydot_ctx* ctx, int v, const Geo& g, const Batch& b, int it, 
   float* p[2] = {(float*)P[0], (float*)P[1]};
   switch (v) {
     case 1: roll_iteration<float, 2, 6, 4, 4>(ctx, g, b, it, nrb, e, r, p); break;
-    case 2: roll_iteration<float, 8, 3, 2, 2>(ctx, g, b, it, nrb, e, r, p); break;
+    case 2: roll_iteration<float, 4, 3, 5, 5>(ctx, g, b, it, nrb, e, r, p); break;
     case 3: roll_iteration<float, 4, 5, 3, 3>(ctx, g, b, it, nrb, e, r, p); break;
     default: roll_iteration<float, 4, 4, 4, 3>(ctx, g, b, it, nrb, e, r, p); break;
   }
@@ -1540,7 +1540,7 @@ int roll_setup(hydot_ctx* ctx) {
   }
   int rc = roll_attrs<float, 4, 4, 4, 3>(ctx);
   if (!rc) rc = roll_attrs<float, 2, 6, 4, 4>(ctx);
-  if (!rc) rc = roll_attrs<float, 8, 3, 2, 2>(ctx);
+  if (!rc) rc = roll_attrs<float, 4, 3, 5, 5>(ctx);
   if (!rc) rc = roll_attrs<float, 4, 5, 3, 3>(ctx);
   return rc;
 }

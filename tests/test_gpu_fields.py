@@ -285,7 +285,7 @@ def test_roll_variants_bitwise_identical_and_autotuner_settles(hd, oracle_fields
         tu = ctx.tuning()
     assert tu["variant"] in range(4)
     assert all(v["ns_per_cell"] > 0 for v in tu["variants"])
-    assert [(v["planes"], v["buffers"]) for v in tu["variants"]] == [(4, 4), (2, 6), (8, 3), (4, 5)]
+    assert [(v["planes"], v["buffers"]) for v in tu["variants"]] == [(4, 4), (2, 6), (4, 3), (4, 5)]
 
 
 def test_graph_replay_matches_direct_launches(hd, monkeypatch):
