@@ -132,3 +132,15 @@ def test_null_arguments(lib):
     assert lib.hydot_solve_batch(v1, 1, i1, i1, v1, v1, None, st1) == L.HYDOT_ERR_ARG
     assert st1[0] == L.HYDOT_ERR_ARG and "NULL" in lib.hydot_last_error(None).decode()
     lib.hydot_destroy(None)
+
+
+def test_solve_batch_binding_checks_its_lists_without_a_device(lib):
+    """The Python batch call checks the per-context wavelength lists before it touches a context."""
+    import paper_1410_0986_gb300 as hd
+
+    assert hd.solve_batch([], 0, 1) == []
+    dummies = [object(), object()]
+    with pytest.raises(ValueError):
+        hd.solve_batch(dummies, [0], 1)
+    with pytest.raises(ValueError):
+        hd.solve_batch(dummies, 0, [1, 1, 1])
