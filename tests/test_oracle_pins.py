@@ -122,6 +122,79 @@ def test_infinite_medium_green_function():
     assert diffs[0] / diffs[1] > 3.0
 
 
+@pytest.mark.parametrize("mua_t,musp_t", [(0.1, 0.5), (0.03, 1.2)])
+def test_green_function_written_in_mua_and_musp(mua_t, musp_t):
+    """The diffusion coefficient of the medium (Section 2.1, the reduced-scattering form of D in the
+    workload definitions) pinned by the continuum: with one chromophore and mu_a, mu_s' given, the
+    lattice field of a unit source far from the boundary must converge at second order in h to
+        3 (mu_a + mu_s') / (4 pi r) * exp(-sqrt(3 mu_a (mu_a + mu_s')) r),
+    the infinite-medium Green's function written in mu_a and mu_s' only (no D from the oracle).
+    A slip such as D = 1/(3 mu_s') moves the amplitude and the decay rate by tens of per cent."""
+    diffs = []
+    r = 6.0
+    for n, h in ((32, 1.5), (64, 0.75)):
+        p = workloads.make_problem(workloads.Grid(n, n, n, h), 1, 1, 1, seed=5, n_chrom=1)
+        p.c_bg = np.array([0.05])
+        p.eps = np.array([[mua_t / 0.05]])
+        p.mus_prime = np.array([musp_t])
+        p.src_ijk = np.array([[n // 2, n // 2, n // 2]])
+        phis, _ = solve.fields_separable(p, [0], det=[])
+        F = phis[0, 0].reshape(n, n, n)
+        G = 3.0 * (mua_t + musp_t) / (4.0 * math.pi * r) * math.exp(-math.sqrt(3.0 * mua_t * (mua_t + musp_t)) * r)
+        off = int(round(r / h))
+        diffs.append(F[n // 2, n // 2, n // 2 + off] / G - 1.0)
+    # second order in h (ratio ~4 under halving); Richardson's extrapolation of the two lattice
+    # values removes the h^2 term and must land within 1.5 % of the closed form
+    assert abs(diffs[0]) < 0.15 and abs(diffs[1]) < 0.03, diffs
+    assert abs(diffs[0] / diffs[1]) > 3.5, diffs
+    assert abs((4.0 * diffs[1] - diffs[0]) / 3.0) < 0.015, diffs
+
+
+def test_mu_a_is_the_concentration_slope_of_the_forward_model():
+    """eqn:perturbation: mu_a(lambda) = sum_c eps_c(lambda) c_c, so d mu_a / d c_c = eps_c(lambda).
+    Central differences of the discrete forward value e_d^T A^-1 e_s in the background concentration
+    c_bg[c], with D held at its background value (the Born model's medium), must equal the row sum
+    of J's chromophore-c block, sum_x J[(s,d,lambda), c N + x] (J pinned above by differences of the
+    nonlinear model); and mu_a itself must equal sum_c c_c times the measured slope d mu_a / d c_c,
+    each slope read off the forward model as the ratio of its c_c derivative to its derivative in a
+    uniform mu_a. n_lambda != n_chrom, so a transposed eps cannot pass."""
+    import scipy.sparse.linalg as spla
+
+    p = workloads.small(nx=6, ny=5, nz=4, n_src=2, n_det=2, n_lambda=3)
+    g = p.grid
+    mua0, D0 = model.wavelength_coefficients(p)
+    phis, phid = solve.fields_splu(p)
+    J = born.born_matrix(p, phis, phid)
+    N, nd, nl = g.N, p.n_det, p.n_lambda
+
+    def fwd(cb, lam):
+        A = model.assemble(g.nx, g.ny, g.nz, g.h, float(D0[lam]), float(model.mu_a(p.eps, cb)[lam]), p.robin_A)
+        lu = spla.splu(A.tocsc())
+        out = np.empty((p.n_src, nd))
+        for a, s in enumerate(p.src_voxels()):
+            e = np.zeros(N)
+            e[s] = 1.0
+            out[a] = lu.solve(e)[p.det_voxels()]
+        return out
+
+    delta = 1e-6
+    for lam in range(nl):
+        du = (born.forward_value(p, lam, delta * np.ones(N)) - born.forward_value(p, lam, -delta * np.ones(N))) / (2 * delta)
+        mua_rebuilt = 0.0
+        for c in range(p.n_chrom):
+            cp, cm = p.c_bg.copy(), p.c_bg.copy()
+            cp[c] += delta
+            cm[c] -= delta
+            fd = (fwd(cp, lam) - fwd(cm, lam)) / (2 * delta)
+            for s in range(p.n_src):
+                for d in range(nd):
+                    r = (s * nd + d) * nl + lam
+                    row_sum = J[r, c * N:(c + 1) * N].sum()
+                    assert abs(fd[s, d] - row_sum) <= 1e-6 * abs(row_sum), (lam, c, s, d)
+            mua_rebuilt += p.c_bg[c] * float(np.median(fd / du))
+        assert math.isclose(mua_rebuilt, mua0[lam], rel_tol=1e-6), (lam, mua_rebuilt, mua0[lam])
+
+
 # ---------------------------------------------------------------- fields (Section 3 target)
 
 def test_dense_brute_force_matches_splu():
@@ -411,6 +484,37 @@ def test_recursive_lowrank_exact_and_within_the_section_bound():
     W = np.vstack([s[:, None] * vt for (_, s, vt) in f])
     assert np.allclose(np.linalg.svd(W, compute_uv=False), np.linalg.svd(np.vstack([A, B]), compute_uv=False),
                        rtol=1e-10, atol=1e-14 * np.abs(A).max())
+
+
+@pytest.mark.parametrize("depth", [1, 2, 3, 5])
+def test_recursive_error_bound_is_the_leaf_sum_bound_at_its_equality_case(depth):
+    """Section 4.5 first bounds the error by (L + 1) eps sum_b ||H_b||_F over the leaf blocks, then
+    uses Cauchy-Schwarz over the (at most 2^L) leaves: sum_b ||H_b||_F <= 2^(L/2) ||H||_F, with
+    equality when a full binary tree of depth L has 2^L leaves of equal norm. For such a tree the
+    leaf-sum form, computed from the blocks themselves, must equal recursive_error_bound; for
+    leaves of unequal norm it must stay below it. A 2^L or an L in place of L + 1 fails."""
+    from oracle import sketch as osk
+
+    eps = 1e-3
+    rng = np.random.default_rng(depth)
+    nleaf = 2 ** depth
+    blocks = [rng.standard_normal((3, 7)) for _ in range(nleaf)]
+    blocks = [b / np.linalg.norm(b) * 2.5 for b in blocks]  # equal Frobenius norms
+    H = np.vstack(blocks)
+    leaf_sum = (depth + 1) * eps * sum(np.linalg.norm(b) for b in blocks)
+    assert math.isclose(osk.recursive_error_bound(eps, depth, np.linalg.norm(H)), leaf_sum, rel_tol=1e-12)
+    uneven = [b * (1.0 + i) for i, b in enumerate(blocks)]
+    leaf_sum_u = (depth + 1) * eps * sum(np.linalg.norm(b) for b in uneven)
+    assert leaf_sum_u <= osk.recursive_error_bound(eps, depth, np.linalg.norm(np.vstack(uneven))) * (1 + 1e-12)
+
+
+def test_recursive_error_bound_literal_values():
+    """2^(L/2) (L + 1) eps ||H||_F at two depths, by hand: L = 2, eps = 1e-3, ||H|| = 1 gives
+    2 * 3 * 1e-3 = 6e-3; L = 4, eps = 1e-2, ||H|| = 2 gives 4 * 5 * 1e-2 * 2 = 0.4."""
+    from oracle import sketch as osk
+
+    assert math.isclose(osk.recursive_error_bound(1e-3, 2, 1.0), 6e-3, rel_tol=1e-15)
+    assert math.isclose(osk.recursive_error_bound(1e-2, 4, 2.0), 0.4, rel_tol=1e-15)
 
 
 # --------------------------------------------------------------------------- shift-invariant guess
