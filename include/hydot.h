@@ -45,16 +45,22 @@ typedef struct hydot_ctx hydot_ctx; /* opaque: device coefficient tables, worksp
 typedef enum {
   HYDOT_OK = 0,
   HYDOT_ERR_ARG = -1,           /* invalid argument; nothing was enqueued */
-  HYDOT_ERR_OOM = -2,           /* device allocation failed */
+  HYDOT_ERR_OOM = -2,           /* a device or host allocation failed */
   HYDOT_ERR_CUDA = -3,          /* a CUDA call failed (message holds cudaGetErrorString) */
-  HYDOT_ERR_NOT_CONVERGED = -4, /* some field missed its tolerance: best iterate written */
+  HYDOT_ERR_NOT_CONVERGED = -4, /* some field missed its tolerance: best iterate written; or the
+                                 * host eigensolver of a sketch or deflation step did not converge
+                                 * (the message says which; outputs are then not valid) */
   HYDOT_ERR_TIMEOUT = -5,       /* a bounded device wait gave up */
-  HYDOT_ERR_STATE = -6          /* call not valid for this context (e.g. complex Born) */
+  HYDOT_ERR_STATE = -6,         /* call not valid for this context (e.g. complex Born) */
+  HYDOT_ERR_HOST = -7           /* a host-side failure other than an allocation (for example a
+                                 * worker thread that could not start); the message says what */
 } hydot_status;
 
 typedef enum {
   HYDOT_FP64 = 0,  /* FP64 Jacobi-PCG (COCG when omega != 0), no refinement */
-  HYDOT_MIXED = 1  /* FP32 inner PCG/COCG with FP64 residuals and iterative refinement */
+  HYDOT_MIXED = 1  /* FP32 inner PCG/COCG with iterative refinement: the iterate and its residual
+                    * are double-float (two FP32 words, about 48 significant bits) computed with
+                    * FP32 error-free transformations; per-field sums and tests in FP64 */
 } hydot_precision;
 
 typedef struct {
@@ -180,8 +186,11 @@ int hydot_born_apply_T(hydot_ctx* ctx, const void* phi_src, const void* phi_det,
  * (16 MiB of partial sums); larger sizes return HYDOT_ERR_ARG with a message from
  * hydot_last_error(NULL). The first call on a device, with that device current, looks up the
  * array's device address (cudaGetSymbolAddress) once; make that first call before any stream
- * capture. All calls share the array, which keeps the last call's contents (nothing in it needs
- * to start at zero): calls that overlap on the GPU, on any streams of one device, race. */
+ * capture. eps is copied to the device by cudaMemcpyAsync on stream: from pageable memory the
+ * call returns once eps has been read, from pinned memory eps must stay valid and unchanged until
+ * the stream has run the copy. All calls share the array, which keeps the last call's contents
+ * (nothing in it needs to start at zero): calls that overlap on the GPU, on any streams of one
+ * device, race. Devices with an index of 64 or more are rejected (HYDOT_ERR_CUDA). */
 int hydot_born_apply_noalloc(long long N, int n_src, int n_det, int n_chrom, int nlam, double h_mm,
                              const double* eps, const float* phi_src, const float* phi_det, const float* x,
                              float* y, void* stream);

@@ -14,8 +14,10 @@ HYDOT_ERR_CUDA = -3
 HYDOT_ERR_NOT_CONVERGED = -4
 HYDOT_ERR_TIMEOUT = -5
 HYDOT_ERR_STATE = -6
+HYDOT_ERR_HOST = -7
 STATUS_NAMES = {0: "HYDOT_OK", -1: "HYDOT_ERR_ARG", -2: "HYDOT_ERR_OOM", -3: "HYDOT_ERR_CUDA",
-                -4: "HYDOT_ERR_NOT_CONVERGED", -5: "HYDOT_ERR_TIMEOUT", -6: "HYDOT_ERR_STATE"}
+                -4: "HYDOT_ERR_NOT_CONVERGED", -5: "HYDOT_ERR_TIMEOUT", -6: "HYDOT_ERR_STATE",
+                -7: "HYDOT_ERR_HOST"}
 
 HYDOT_FP64 = 0
 HYDOT_MIXED = 1

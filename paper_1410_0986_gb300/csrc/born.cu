@@ -5,6 +5,7 @@
 //   g[c*N+x]        += -h^3 sum_a eps_c(lambda_a) sum_s phi_s[a][s][x] sum_d Y_a[s][d] phi_d[a][d][x]
 // with slice rows r = (s*n_det + d)*nlam + a.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdlib>
 
@@ -918,7 +919,7 @@ int born_apply_T_impl(hydot_ctx* ctx, const void* phi_src, const void* phi_det, 
 
 // ---------------------------------------------------------------- J x without device allocation
 // For callers that cannot allocate device memory themselves (code running where cudaMalloc is
-// not allowed, such as inside a host callback or under an allocator owned by someone else):
+// not allowed, or under an allocator owned by someone else):
 // the per-block partial sums of J x live in a fixed file-scope device array instead of a
 // library workspace, and the wavelength slice's extinction coefficients are staged there too.
 // Every GPU that loads the library holds this array until the process exits.
@@ -931,7 +932,9 @@ constexpr size_t NOALLOC_BYTES = NOALLOC_EPS_BYTES + NOALLOC_PART_BYTES;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 
 constexpr int NOALLOC_MAX_DEVICES = 64;
-void* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {nullptr};  // device address of the array, per device
+// device address of the array, per device; host threads may make their first call on a device at
+// the same time, so each slot is atomic (both then look up the same address)
+std::atomic<void*> g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
 
 }  // namespace
 
@@ -939,61 +942,67 @@ extern "C" int hydot_born_apply_noalloc(long long N, int n_src, int n_det, int n
                                         const double* eps, const float* phi_src, const float* phi_det,
                                         const float* x, float* y, void* stream) {
   using namespace hydot;
-  auto bad = [](const std::string& m) {
-    set_context_free_error(m);
-    return (int)HYDOT_ERR_ARG;
-  };
-  if (N < 1 || n_src < 1 || n_det < 1 || nlam < 1 || n_chrom < 1) return bad("sizes must be >= 1");
-  if (n_chrom > MAXC) return bad("n_chrom must be <= 16");
-  if (!(h_mm > 0.0)) return bad("h_mm must be > 0");
-  if (!eps || !phi_src || !phi_det || !x || !y) return bad("null pointer");
-  const size_t eps_bytes = sizeof(double) * (size_t)nlam * n_chrom;
-  if (eps_bytes > NOALLOC_EPS_BYTES) return bad("nlam * n_chrom exceeds the static limit of 8192");
-  const int nts = (n_src + 31) / 32, ntd = (n_det + 31) / 32;
-  const long long per_blk = (long long)AP_XC * AP_STAGES;
-  const long long nxb = (N + per_blk - 1) / per_blk;
-  const double part_bytes = 4.0 * (double)nlam * nts * ntd * (double)nxb * 1024.0;
-  if (part_bytes > (double)NOALLOC_PART_BYTES)
-    return bad("nlam * ceil(n_src/32) * ceil(n_det/32) * ceil(N/1024) * 4 KiB exceeds the 16 MiB static scratch");
-  if (nlam > 65535 || nts * ntd > 65535) return bad("too many wavelengths or optode tiles for one launch");
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
-    set_context_free_error(std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-    return HYDOT_ERR_CUDA;
-  }
-  // once per device, with that device current: the array's device address (the host-side name
-  // of a __device__ array is only a stand-in and must not be passed to a kernel)
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      set_context_free_error(std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+  return abi_guard(nullptr, [&]() -> int {
+    auto bad = [](const std::string& m) {
+      set_context_free_error(m);
+      return (int)HYDOT_ERR_ARG;
+    };
+    if (N < 1 || n_src < 1 || n_det < 1 || nlam < 1 || n_chrom < 1) return bad("sizes must be >= 1");
+    if (n_chrom > MAXC) return bad("n_chrom must be <= 16");
+    if (!(h_mm > 0.0)) return bad("h_mm must be > 0");
+    if (!eps || !phi_src || !phi_det || !x || !y) return bad("null pointer");
+    const size_t eps_bytes = sizeof(double) * (size_t)nlam * n_chrom;
+    if (eps_bytes > NOALLOC_EPS_BYTES) return bad("nlam * n_chrom exceeds the static limit of 8192");
+    const int nts = (n_src + 31) / 32, ntd = (n_det + 31) / 32;
+    const long long per_blk = (long long)AP_XC * AP_STAGES;
+    const long long nxb = (N + per_blk - 1) / per_blk;
+    const double part_bytes = 4.0 * (double)nlam * nts * ntd * (double)nxb * 1024.0;
+    if (part_bytes > (double)NOALLOC_PART_BYTES)
+      return bad("nlam * ceil(n_src/32) * ceil(n_det/32) * ceil(N/1024) * 4 KiB exceeds the 16 MiB static scratch");
+    if (nlam > 65535 || nts * ntd > 65535) return bad("too many wavelengths or optode tiles for one launch");
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+      set_context_free_error(std::string("cudaGetDevice: ") + cudaGetErrorString(e));
       return HYDOT_ERR_CUDA;
     }
-    g_noalloc_ptr[dev] = p;
-  }
-  unsigned char* base = static_cast<unsigned char*>(g_noalloc_ptr[dev]);
-  double* d_eps = reinterpret_cast<double*>(base);
-  float* part = reinterpret_cast<float*>(base + NOALLOC_EPS_BYTES);
-  cudaStream_t s = (cudaStream_t)stream;
-  e = cudaMemcpyAsync(d_eps, eps, eps_bytes, cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) {
-    set_context_free_error(std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e));
-    return HYDOT_ERR_CUDA;
-  }
-  {
-    dim3 grid((unsigned)nxb, nlam, nts * ntd);
-    // 32-wide optode tiles; every partial slot that is summed is written first, so nothing in the
-    // array needs clearing
-    e = launch_apply_partial<float, 8>(grid, s, phi_src, phi_det, x, d_eps, 0, n_src, n_det, n_chrom, N, (int)nxb,
-                                       AP_STAGES, apply_vec_ok(phi_src, phi_det, x, N, 4), part);
-    if (e == cudaSuccess)
-      e = launch_apply_reduce<float>(part, nlam, n_src, n_det, nts, ntd, 32, (int)nxb, h_mm * h_mm * h_mm, y, s);
-  }
-  if (e != cudaSuccess) {
-    set_context_free_error(std::string("launch: ") + cudaGetErrorString(e));
-    return HYDOT_ERR_CUDA;
-  }
-  return HYDOT_OK;
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
+      set_context_free_error("device index " + std::to_string(dev) + " exceeds the 64 devices this call supports");
+      return HYDOT_ERR_CUDA;
+    }
+    // once per device, with that device current: the array's device address (the host-side name
+    // of a __device__ array is only a stand-in and must not be passed to a kernel)
+    void* addr = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+    if (!addr) {
+      e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
+      if (e != cudaSuccess || !addr) {
+        set_context_free_error(std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        return HYDOT_ERR_CUDA;
+      }
+      g_noalloc_ptr[dev].store(addr, std::memory_order_release);
+    }
+    unsigned char* base = static_cast<unsigned char*>(addr);
+    double* d_eps = reinterpret_cast<double*>(base);
+    float* part = reinterpret_cast<float*>(base + NOALLOC_EPS_BYTES);
+    cudaStream_t s = (cudaStream_t)stream;
+    e = cudaMemcpyAsync(d_eps, eps, eps_bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) {
+      set_context_free_error(std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e));
+      return HYDOT_ERR_CUDA;
+    }
+    {
+      dim3 grid((unsigned)nxb, nlam, nts * ntd);
+      // 32-wide optode tiles; every partial slot that is summed is written first, so nothing in the
+      // array needs clearing
+      e = launch_apply_partial<float, 8>(grid, s, phi_src, phi_det, x, d_eps, 0, n_src, n_det, n_chrom, N, (int)nxb,
+                                         AP_STAGES, apply_vec_ok(phi_src, phi_det, x, N, 4), part);
+      if (e == cudaSuccess)
+        e = launch_apply_reduce<float>(part, nlam, n_src, n_det, nts, ntd, 32, (int)nxb, h_mm * h_mm * h_mm, y, s);
+    }
+    if (e != cudaSuccess) {
+      set_context_free_error(std::string("launch: ") + cudaGetErrorString(e));
+      return HYDOT_ERR_CUDA;
+    }
+    return HYDOT_OK;
+  });
 }

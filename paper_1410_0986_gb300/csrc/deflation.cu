@@ -244,7 +244,10 @@ int build_deflation(hydot_ctx* ctx) {
     T[(size_t)i * mm + i] = alpha[i];
     if (i + 1 < mm) T[(size_t)i * mm + i + 1] = T[(size_t)(i + 1) * mm + i] = beta[i];
   }
-  sym_eig(T, mm, lam, Z);
+  if (!sym_eig(T, mm, lam, Z)) {
+    cleanup();
+    return fail(ctx, HYDOT_ERR_NOT_CONVERGED, "host eigensolver did not converge on the Lanczos tridiagonal");
+  }
   std::vector<int> order(mm);
   for (int i = 0; i < mm; ++i) order[i] = i;
   std::sort(order.begin(), order.end(), [&](int a, int b) { return lam[a] < lam[b]; });

@@ -11,11 +11,15 @@ namespace hydot {
 // implicit-shift symmetric QR iteration (Wilkinson shift, Givens bulge chasing), with the
 // transformations accumulated: A (n x n, row-major) -> eigenvalues in lam, eigenvectors in the
 // columns of V (row-major, V[i*n + j] = component i of eigenvector j). O(n^3) with small constants
-// (n = 320: ~0.1 s; a cyclic Jacobi method takes ~16x longer).
-inline void sym_eig(std::vector<double> A, int n, std::vector<double>& lam, std::vector<double>& V) {
+// (n = 320: ~0.1 s; a cyclic Jacobi method takes ~16x longer). Returns false when the QR
+// iteration has not deflated every coupling after max_sweeps bulge chases (default 64 n; a
+// symmetric tridiagonal matrix needs about 2 n), in which case lam and V are not valid.
+inline bool sym_eig(std::vector<double> A, int n, std::vector<double>& lam, std::vector<double>& V,
+                    long long max_sweeps = -1) {
   lam.assign(n, 0.0);
   V.assign((size_t)n * n, 0.0);
-  if (n == 0) return;
+  if (n == 0) return true;
+  if (max_sweeps < 0) max_sweeps = 64LL * n;
   auto a = [&](int i, int j) -> double& { return A[(size_t)i * n + j]; };
   // Q accumulated as a row-major matrix, starting from the identity
   std::vector<double> Q((size_t)n * n, 0.0);
@@ -62,8 +66,8 @@ inline void sym_eig(std::vector<double> A, int n, std::vector<double>& lam, std:
   for (int i = 0; i + 1 < n; ++i) e[i] = a(i + 1, i);
   // 2. implicit symmetric QR on the unreduced trailing block [lo, hi]
   int hi = n - 1;
-  int guard = 0;
-  while (hi > 0 && guard < 64 * n) {
+  long long guard = 0;
+  while (hi > 0 && guard < max_sweeps) {
     ++guard;
     // deflate negligible couplings from the bottom
     if (std::fabs(e[hi - 1]) <= 1e-15 * (std::fabs(d[hi - 1]) + std::fabs(d[hi]))) {
@@ -104,6 +108,7 @@ inline void sym_eig(std::vector<double> A, int n, std::vector<double>& lam, std:
   }
   lam = d;
   V = Q;
+  return hi == 0;
 }
 
 inline bool cholesky_upper(const std::vector<double>& G, int k, std::vector<double>& R) {

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <exception>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -373,6 +375,33 @@ void shift_guess_free(hydot_ctx* ctx);
 
 // api.cu
 void set_context_free_error(const std::string& msg);
+
+// Runs the body of a C-ABI entry point so that no C++ exception crosses the ABI: a failed host
+// allocation (std::bad_alloc, e.g. from a std::vector or std::string) becomes HYDOT_ERR_OOM and any
+// other exception HYDOT_ERR_HOST, with the message kept in the context (or, for calls without
+// one, in the calling thread's context-free message).
+template <typename F>
+int abi_guard(const hydot_ctx* ctx, F&& body) noexcept {
+  auto note = [ctx](const char* what) noexcept {
+    try {
+      if (ctx) const_cast<hydot_ctx*>(ctx)->err = what;
+      else set_context_free_error(what);
+    } catch (...) {  // no memory even for the message: the status alone reports it
+    }
+  };
+  try {
+    return body();
+  } catch (const std::bad_alloc&) {
+    note("host memory allocation failed");
+    return HYDOT_ERR_OOM;
+  } catch (const std::exception& e) {
+    note(e.what());
+    return HYDOT_ERR_HOST;
+  } catch (...) {
+    note("unknown host-side exception");
+    return HYDOT_ERR_HOST;
+  }
+}
 
 // Instrumentation helpers (api.cu): a timed launch is bracketed by timer_begin/timer_end;
 // timer_flush reads the completed events (call after the stream was synchronised).

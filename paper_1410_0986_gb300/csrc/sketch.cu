@@ -1116,9 +1116,10 @@ int right_mul(hydot_ctx* ctx, const float* X, long long rows, long long ldx, int
 }
 
 // eigen-pairs of a symmetric n x n matrix, descending
-void eig_desc(const std::vector<double>& G, int n, std::vector<double>& lam, std::vector<double>& V) {
+// (false when the host eigensolver did not converge)
+bool eig_desc(const std::vector<double>& G, int n, std::vector<double>& lam, std::vector<double>& V) {
   std::vector<double> l, Z;
-  sym_eig(G, n, l, Z);
+  if (!sym_eig(G, n, l, Z)) return false;
   std::vector<int> ord(n);
   for (int i = 0; i < n; ++i) ord[i] = i;
   std::sort(ord.begin(), ord.end(), [&](int a, int b) { return l[a] > l[b]; });
@@ -1128,6 +1129,7 @@ void eig_desc(const std::vector<double>& G, int n, std::vector<double>& lam, std
     lam[j] = l[ord[j]];
     for (int i = 0; i < n; ++i) V[(size_t)i * n + j] = Z[(size_t)i * n + ord[j]];
   }
+  return true;
 }
 
 }  // namespace
@@ -1145,7 +1147,10 @@ int sketch_orthonormalize_impl(hydot_ctx* ctx, float* Y, long long rows, int nco
     std::vector<double> G, lam, V;
     int rc = gram(ctx, Y, rows, ldY, ncols, G);
     if (rc) { cudaFree(Z); return rc; }
-    eig_desc(G, ncols, lam, V);
+    if (!eig_desc(G, ncols, lam, V)) {
+      cudaFree(Z);
+      return fail(ctx, HYDOT_ERR_NOT_CONVERGED, "host eigensolver did not converge on the Gram of Y");
+    }
     const double smax = std::sqrt(std::max(lam[0], 0.0));
     if (round == 0 && smax_out) *smax_out = smax;
     kept = 0;
@@ -1181,7 +1186,8 @@ int sketch_factor_impl(hydot_ctx* ctx, const float* Q, long long rows, long long
   std::vector<double> G, lam, UB;
   int rc = gram(ctx, Bt, nb, ldB, ncols, G);
   if (rc) return rc;
-  eig_desc(G, ncols, lam, UB);
+  if (!eig_desc(G, ncols, lam, UB))
+    return fail(ctx, HYDOT_ERR_NOT_CONVERGED, "host eigensolver did not converge on the Gram of B");
   std::vector<float> WV((size_t)ncols * rank, 0.f), WU((size_t)ncols * rank, 0.f);
   for (int j = 0; j < rank; ++j) {
     const double sj = std::sqrt(std::max(lam[j], 0.0));
@@ -1213,7 +1219,8 @@ int sketch_rank_impl(hydot_ctx* ctx, const float* Q, long long ldQ, long long ro
   int r = 0;
   double e = 0.0;
   for (;; ++r) {
-    sym_eig(R, k, lam, V);
+    if (!sym_eig(R, k, lam, V))
+      return fail(ctx, HYDOT_ERR_NOT_CONVERGED, "host eigensolver did not converge in the rank estimator");
     double lmax = 0.0;
     for (double v : lam) lmax = std::max(lmax, v);
     e = std::sqrt(std::max(lmax, 0.0));
@@ -1259,7 +1266,8 @@ int sketch_merge_impl(hydot_ctx* ctx, const float* U1, long long ldU1, long long
       G[(size_t)(r1 + j) * rt + i] = v;
     }
   std::vector<double> lam, E;
-  eig_desc(G, rt, lam, E);
+  if (!eig_desc(G, rt, lam, E))
+    return fail(ctx, HYDOT_ERR_NOT_CONVERGED, "host eigensolver did not converge on the merge Gram");
   const double s_1 = std::sqrt(std::max(lam[0], 0.0));
   int r = 0;
   while (r < rt && r < max_rank && std::sqrt(std::max(lam[r], 0.0)) > tol * s_1 && lam[r] > 0.0) ++r;

@@ -144,3 +144,33 @@ def test_solve_batch_binding_checks_its_lists_without_a_device(lib):
         hd.solve_batch(dummies, [0], 1)
     with pytest.raises(ValueError):
         hd.solve_batch(dummies, 0, [1, 1, 1])
+
+
+def test_status_codes_match_the_header():
+    """The binding's status table is the header's enum, value by value."""
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    body = re.search(r"typedef enum \{(.*?)\} hydot_status;", src, re.S).group(1)
+    codes = {name: int(val) for name, val in re.findall(r"(HYDOT_\w+)\s*=\s*(-?\d+)", body)}
+    assert codes == {v: k for k, v in L.STATUS_NAMES.items()}
+
+
+def test_every_status_returning_entry_point_is_exception_guarded():
+    """No C++ exception may cross the ABI: every extern "C" function that returns a status runs
+    its body inside abi_guard (std::bad_alloc -> HYDOT_ERR_OOM, anything else -> HYDOT_ERR_HOST)."""
+    csrc = os.path.join(ROOT, "paper_1410_0986_gb300", "csrc")
+    found = 0
+    for fn in os.listdir(csrc):
+        if not fn.endswith(".cu"):
+            continue
+        text = open(os.path.join(csrc, fn)).read()
+        for m in re.finditer(r"^(?:extern \"C\" )?int (hydot_\w+)\([^)]*\) \{\n(.*?)\n\}", text, re.M | re.S):
+            if m.group(1) not in L.EXPORTS:
+                continue
+            found += 1
+            first = m.group(2).lstrip().splitlines()[0]
+            if "using namespace" in first:
+                first = m.group(2).lstrip().splitlines()[1]
+            assert "abi_guard(" in first, (fn, m.group(1))
+    assert found == len([n for n in L.EXPORTS if n not in ("hydot_version", "hydot_kernel_launches",
+                                                            "hydot_last_error", "hydot_destroy")])

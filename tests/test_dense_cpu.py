@@ -20,7 +20,7 @@ int main() {
     std::vector<double> A((size_t)n * n);
     for (auto& v : A) std::scanf("%lf", &v);
     std::vector<double> lam, V;
-    hydot::sym_eig(A, n, lam, V);
+    if (!hydot::sym_eig(A, n, lam, V)) return 3;
     for (int i = 0; i < n; ++i) std::printf("%.17g\n", lam[i]);
     for (auto v : V) std::printf("%.17g\n", v);
   }
@@ -68,3 +68,33 @@ def test_sym_eig_matches_numpy(exe):
         assert np.abs(np.sort(lam) - np.linalg.eigvalsh(A)).max() <= 1e-12 * scale * max(1, n / 32)
         assert np.abs(A @ V - V * lam).max() <= 1e-12 * scale * max(1, n / 32)
         assert np.abs(V.T @ V - np.eye(n)).max() <= 1e-12 * max(1, n / 32)
+
+
+CAP_PROG = r"""
+#include <cstdio>
+#include <vector>
+#include "dense.h"
+int main() {
+  // a symmetric 40 x 40 matrix with distinct eigenvalues: the QR iteration needs about 2 n bulge
+  // chases; with a cap of 3 it must report that it did not converge, with the default it converges
+  const int n = 40;
+  std::vector<double> A((size_t)n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) A[(size_t)i * n + j] = 1.0 / (1.0 + i + j) + (i == j ? i : 0.0);
+  std::vector<double> lam, V;
+  const bool capped = hydot::sym_eig(A, n, lam, V, 3);
+  const bool full = hydot::sym_eig(A, n, lam, V);
+  std::printf("%d %d\n", (int)capped, (int)full);
+}
+"""
+
+
+def test_sym_eig_reports_non_convergence(tmp_path):
+    """The eigensolver returns false when its sweep cap stops it before every coupling is deflated
+    (its callers turn that into HYDOT_ERR_NOT_CONVERGED instead of using unconverged factors)."""
+    src, out = tmp_path / "cap.cpp", tmp_path / "cap"
+    src.write_text(CAP_PROG)
+    subprocess.run(["g++", "-O2", "-std=c++17", "-I", os.path.join(ROOT, "paper_1410_0986_gb300", "csrc"), str(src),
+                    "-o", str(out)], check=True)
+    r = subprocess.run([str(out)], capture_output=True, text=True, check=True)
+    assert r.stdout.split() == ["0", "1"]

@@ -3,8 +3,9 @@
 Some callers cannot allocate GPU memory themselves, for instance code that runs where
 cudaMalloc is not permitted, or that must stay within memory another component owns. This
 entry point serves them: its scratch is a fixed device array inside the library. These tests
-call it through the C ABI and compare it with the context-based hydot_born_apply on the same
-inputs, twice in a row (the second call must not see the first call's leftovers).
+call it through the C ABI and compare it with the context-based hydot_born_apply and with the
+CPU FP64 oracle's J x on the same inputs, twice in a row (the second call must not see the first
+call's leftovers).
 """
 import ctypes as C
 
@@ -14,6 +15,7 @@ import torch
 
 import workloads
 import paper_1410_0986_gb300._lib as L
+from oracle import born as oborn
 
 pytestmark = pytest.mark.gpu
 
@@ -45,6 +47,10 @@ def test_noalloc_matches_context_entry_point_twice(lib):
             torch.cuda.synchronize()
             assert torch.isfinite(y).all()
             assert (y - ref).abs().max() <= 2e-5 * ref.abs().max()
+            # the plain FP64 definition (eqn:measurement) on the same FP32 inputs
+            yo = oborn.apply(p, ps.double().cpu().numpy(), pd.double().cpu().numpy(), x.double().cpu().numpy(),
+                             list(range(lam0, lam0 + nlam)))
+            assert np.abs(y.double().cpu().numpy() - yo).max() <= 2e-5 * np.abs(yo).max()
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(lib):
