@@ -44,21 +44,19 @@ TOL_CW = 1e-8
 CW_FLOOR = 100.0
 WORKLOAD = ("cw-mixed-64x64x48: 64x64x48 grid (h=2 mm), 32 sources + 32 detectors, 128 wavelengths "
             "(8,192 field solves), explicit FP32 Born rows 131,072 x 786,432 in row chunks, J x and J^T r")
-KERNEL_NAMES = {"dir": "k_dir_roll (inner PCG pass 1)", "update": "k_update_roll (inner PCG pass 2)",
+KERNEL_NAMES = {"iter": "inner CG iteration (every pass of one Krylov iteration; graph replays of 8 iterations)",
+                "dir": "k_dir_roll (inner PCG pass 1)", "update": "k_update_roll (inner PCG pass 2)",
                 "residual": "k_residual_df (residual of the double-float iterate)",
                 "born_rows": "k_born_rows (Born-row assembly)",
                 "apply": "k_apply_partial+reduce (J x)", "apply_T": "k_transpose_y+k_apply_T_tile+reduce (J^T y)",
                 "sketch_range": "k_range_ws (tensor-core Y = J Omega)",
                 "sketch_project": "k_project_ws (tensor-core B^T += J^T Q)"}
 # DRAM bytes (read + write, ncu) per algorithmic byte, from the captures summarised under profiles/
-# (smaller cases of the same kernels, scaled by the units processed: active fields or rows)
-DRAM_PER_ALGORITHMIC_BYTE = {"dir": (100.97e6 + 22.41e6) / (64 * 3 * 196608 * 4),
-                             "update": (151.24e6 + 45.80e6) / (64 * 5 * 196608 * 4),
+# (smaller cases of the same kernels, scaled by the units processed: active fields or rows). The
+# CG iteration's entry is filled from a capture whose working set exceeds L2; None until then.
+DRAM_PER_ALGORITHMIC_BYTE = {"iter": None,
                              "born_rows": (893.83e6 + 12.96e9) / (4096 * 4 * 196608 * 4)}
-TRAFFIC_NOTE = {"dir": "ncu on 64 fields of one wavelength (profiles/solver_roll_64fields.md), scaled by active "
-                       "fields; writes partly still in L2 at kernel end",
-                "update": "ncu on 64 fields of one wavelength (profiles/solver_roll_64fields.md), scaled by active "
-                          "fields; writes partly still in L2 at kernel end",
+TRAFFIC_NOTE = {"iter": None,
                 "born_rows": "ncu on a full 4,096-row launch of the benchmark (profiles/k_born_rows_4096rows.md)"}
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
 
@@ -266,6 +264,8 @@ def run_ours(args):
     barrier(world)
     torch.cuda.synchronize()
     launches0 = ctx.kernel_launches()
+    # CUDA events per launch on the library's stream; the inner iterations keep running as CUDA-graph
+    # replays (the product's default) and are timed per 8-iteration group
     ctx.set_kernel_timing(True)
     clocks = ClockSampler(local)
     clocks.start()
@@ -292,14 +292,17 @@ def run_ours(args):
     solves = K * (ns + nd) * CHUNK * world
     value = solves / (ms / 1e3)
     pk = peaks()
-    # dominant kernel = the one with the most device time in the timed region (CUDA events on the
-    # library's stream); achieved = its algorithmic bytes per launch / its mean launch time
-    dom = max(kstats, key=lambda k: kstats[k]["ms"])
+    # the unit of the roofline is the CG iteration (the step's dominant work: most of the device
+    # time in the timed region): 6 N w algorithmic bytes per active field (x, r, p read and written
+    # once) over the measured time per iteration of all its passes (CUDA events on the library's
+    # stream around each 8-iteration group)
+    dom = "iter"
     kd = kstats[dom]
     t_launch = kd["ms"] / kd["launches"] / 1e3
     bytes_launch = kd["bytes"] / kd["launches"]
     achieved = bytes_launch / t_launch / 1e9
     dram_ratio = DRAM_PER_ALGORITHMIC_BYTE.get(dom)
+    ktotal = sum(v["ms"] for k, v in kstats.items() if k in ("iter", "residual", "born_rows", "apply", "apply_T"))
     # solver roofline: 6 N w per RHS-iteration (x, r, p read and written once; FP32)
     iters = sum(s["iters_mean"] * s["n_fields"] for s in stats)
     t_solve = sum(phase["solve"]) / 1e3
@@ -316,17 +319,19 @@ def run_ours(args):
                    "parallelism": f"lambda-chunks over {world} GPU(s), no data exchange"},
         "roofline": {"kernel": KERNEL_NAMES[dom], "bound": "hbm", "achieved": achieved,
                      "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
-                     "peak_source": pk["source"],
+                     "peak_source": pk["source"], "frac_of_nominal_8tbs": achieved / 8000.0,
                      "traffic": None if dram_ratio is None else dram_ratio * bytes_launch,
                      "traffic_note": TRAFFIC_NOTE.get(dom),
                      "algorithmic_bytes_per_launch": bytes_launch, "launch_ms": t_launch * 1e3,
-                     "launches": kd["launches"]},
+                     "launches": kd["launches"],
+                     "unit_of_work": "one CG iteration of the chunk's active fields: 6 N x 4 B per field",
+                     "share_of_kernel_time": kd["ms"] / max(1e-9, ktotal)},
         "kernels": {KERNEL_NAMES[k]: {"ms": v["ms"], "launches": v["launches"],
-                                      "share": v["ms"] / max(1e-9, sum(w["ms"] for w in kstats.values())),
+                                      "share": v["ms"] / max(1e-9, ktotal),
                                       "gbs": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 else None,
                                       "hbm_frac": ((v["bytes"] / (v["ms"] / 1e3) / 1e9) / pk["hbm_gbs"])
                                       if v["ms"] > 0 else None}
-                    for k, v in kstats.items() if v["launches"] > 0},
+                    for k, v in kstats.items() if v["launches"] > 0 and v["ms"] > 0},
         "rates": {
             "born_rows_per_s": K * Mc * world / (sum(phase["assemble"]) / 1e3),
             "grads_per_s": (K / nchunk) / (sum(phase["apply_T"]) / 1e3),
@@ -353,14 +358,16 @@ def run_ours(args):
         "gpu_launches": int(n_launch),
     }
     # end to end through the public API: pinned host inputs in, results back, every step
-    if args.e2e_steps > 0:
+    e2e_steps = args.steps if args.e2e_steps is None else args.e2e_steps
+    if e2e_steps > 0:
+        # the same chunks as the timed steps (step k walks chunk k), the same step count
         xh = x.cpu().pin_memory()
         yh = torch.empty(Mc, dtype=torch.float32).pin_memory()
         gh = torch.empty(nc * N, dtype=torch.float32).pin_memory()
         torch.cuda.synchronize()
         barrier(world)
         s0 = ev()
-        for k in range(args.e2e_steps):
+        for k in range(args.warmup, args.warmup + e2e_steps):
             xd = xh.to("cuda", non_blocking=True)
             c = shard.chunk_of_step(k, rank, world, nchunk)
             lam0 = c * CHUNK
@@ -374,15 +381,20 @@ def run_ours(args):
         s1 = ev()
         torch.cuda.synchronize()
         ems = max_over_ranks(s0.elapsed_time(s1), world)
-        out["e2e"] = {"value": args.e2e_steps * (ns + nd) * CHUNK * world / (ems / 1e3), "unit": UNIT,
+        out["e2e"] = {"value": e2e_steps * (ns + nd) * CHUNK * world / (ems / 1e3), "unit": UNIT,
                       "h2d_bytes_per_step": int(xh.numel() * 4), "d2h_bytes_per_step": int((Mc + nc * N) * 4),
-                      "steps": args.e2e_steps}
+                      "steps": e2e_steps, "chunks": "the timed steps' chunks, in the same order"}
+    # per-pass breakdown of the CG iteration, outside the timed region: one chunk with the inner
+    # passes launched directly (no graph replay) so that each pass gets its own events
+    if rank == 0 and not args.no_pass_breakdown:
+        out["passes"] = pass_breakdown(ctx, ps, pd, pk)
     # the plain FP64 GPU solve against the mixed form, both to a field error of 1e-6 (norm-wise)
     ctx.close()
     del ps, pd, J
     torch.cuda.empty_cache()
     if args.compare_fp64 and rank == 0:
         out["fp64_vs_mixed_at_1e-6"] = compare_fp64(hd, p)
+        out["config1_fp64"] = config1_phase(hd)
         out["deflation"] = compare_deflation(hd, p)
         out["shift_guess_compare"] = compare_shift_guess(hd, p, args.shift_guess_m or 40)
         out["cuda_graphs"] = compare_graphs(hd, p)
@@ -502,6 +514,26 @@ def tree_phase(hd, p, n_lam, tol=1e-2, leaf_rank=100, merge_rank=160, n_probe=16
             lr = U.double() @ (torch.tensor(S, device="cuda") * (V.double().T @ X[:, k].double()))
             errs.append(float((jx - lr).norm() / jx.norm()))
         out["probe_error"] = {"median": float(np.median(errs)), "max": max(errs), "n": n_probe}
+    return out
+
+
+def pass_breakdown(ctx, ps, pd, pk):
+    """Time of each pass of the CG iteration on one chunk (wavelengths 0-15), with the inner passes
+    launched directly so that every launch has its own CUDA events; the per-pass algorithmic bytes
+    are this design's (12 B and 20 B per cell and active field), the iteration's 24 B (x, r, p once)."""
+    ctx.set_graphs(False)
+    ctx.set_kernel_timing(True)
+    ctx.solve_fields(0, CHUNK, ps, pd)
+    ks = ctx.kernel_stats()
+    ctx.set_kernel_timing(False)
+    ctx.set_graphs(True)
+    out = {}
+    for k in ("dir", "update", "iter", "residual"):
+        v = ks[k]
+        if v["ms"] > 0 and v["launches"] > 0:
+            gbs = v["bytes"] / (v["ms"] / 1e3) / 1e9
+            out[KERNEL_NAMES[k]] = {"ms": v["ms"], "launches": v["launches"], "ms_per_launch": v["ms"] / v["launches"],
+                                    "gbs": gbs, "hbm_frac": gbs / pk["hbm_gbs"]}
     return out
 
 
@@ -848,25 +880,139 @@ def born_validity(hd, p, contrasts=(0.001, 0.005, 0.01, 0.02, 0.05, 0.1), lam=0)
     return res
 
 
-def compare_fp64(hd, p):
+def slice_kappa(p, lams):
+    """Upper bound on kappa(Ahat) over the given wavelengths: (12 + max sigma) / min sigma with
+    sigma = mu_a h^2 / D (the Laplacian and boundary part is positive semidefinite, Gershgorin
+    bounds the largest eigenvalue)."""
+    import numpy as np
+
+    mua = (np.asarray(p.eps) @ np.asarray(p.c_bg))[lams]
+    D = 1.0 / (3.0 * (mua + np.asarray(p.mus_prime)[lams]))
+    sigma = mua * p.grid.h ** 2 / D
+    return (12.0 + float(sigma.max())) / float(sigma.min())
+
+
+def golden_check(gold, a, lam0, lam, ps, pd):
+    """Sampled entries of the chunk's fields at wavelength lam against the oracle's sparse-direct
+    fields stored in tests/golden (written by the oracle only): the largest entry error relative to
+    each field's 2-norm, and the relative error of the field norms."""
+    import numpy as np
     import torch
 
-    res = {}
-    for prec, kw in (("mixed", dict(tol=1e-7, tol_cw=0.0)), ("fp64", dict(tol=1e-7, tol_cw=0.0))):
-        with hd.Context.from_problem(p, precision=prec, max_lambda_per_call=CHUNK, **kw) as c:
-            c.solve_fields(0, CHUNK)  # warm-up
+    vox = torch.tensor(gold["vox"], device="cuda")
+    worst, norm_err = 0.0, 0.0
+    for got_t, ref, nrm in ((ps, gold["phis"][a], gold["norms_s"][a]), (pd, gold["phid"][a], gold["norms_d"][a])):
+        f = got_t[lam - lam0]
+        got = f[:, vox].double().cpu().numpy()
+        worst = max(worst, float((np.abs(got - ref).max(axis=1) / nrm).max()))
+        norm_err = max(norm_err, float((np.abs(f.double().norm(dim=1).cpu().numpy() - nrm) / nrm).max()))
+    return {"entry_error_over_norm": worst, "norm_rel_error": norm_err}
+
+
+def compare_fp64(hd, p):
+    """The plain FP64 GPU solve (batched FP64 Jacobi-PCG, no deflation, no refinement) against the
+    mixed-precision batched form on the chunk of wavelengths 0-15, both stopped at the relative
+    residual that the chunk's condition bound maps to a field error of 1e-6
+    (|phi - phi*| / |phi*| <= kappa |r| / |b|), and both checked at wavelength 3 against the
+    oracle's sparse-direct fields stored in tests/golden."""
+    import numpy as np
+    import torch
+
+    gold = np.load(os.path.join(ROOT, "tests", "golden", "cw_mixed_64x64x48.npz"))
+    lam_chk = 3
+    a = int(np.nonzero(gold["lams"] == lam_chk)[0][0])
+    kappa = slice_kappa(p, list(range(CHUNK)))
+    tol = 0.9e-6 / kappa
+    pk = peaks()
+    res = {"criterion": f"relative residual <= 0.9e-6 / kappa = {tol:.3g} (kappa bound {kappa:.1f} over wavelengths "
+                        f"0-15), so every field error <= 1e-6; 1,024 fields; fields at wavelength 3 checked "
+                        f"against the oracle's stored sparse-direct values"}
+    arms = (("fp64", "fp64", 0), ("mixed", "mixed", 0), ("mixed_shift_guess_m40", "mixed", 40))
+    for name, prec, m in arms:
+        with hd.Context.from_problem(p, precision=prec, max_lambda_per_call=CHUNK, tol=tol, tol_cw=0.0) as c:
+            if m:
+                c.set_shift_guess(m)
+            ps, pd, _ = c.solve_fields(0, CHUNK)  # warm-up (autotuner, graphs)
             torch.cuda.synchronize()
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record()
-            _, _, st = c.solve_fields(CHUNK, CHUNK)
-            b.record()
+            c.set_kernel_timing(True)
+            a0 = torch.cuda.Event(enable_timing=True)
+            b0 = torch.cuda.Event(enable_timing=True)
+            a0.record()
+            ps, pd, st = c.solve_fields(0, CHUNK, ps, pd)
+            b0.record()
             torch.cuda.synchronize()
-            res[prec] = {"solves_per_s": (p.n_src + p.n_det) * CHUNK / (a.elapsed_time(b) / 1e3),
-                         "iters_mean": st["iters_mean"], "resid_max": st["resid_max"]}
-    res["speedup"] = res["mixed"]["solves_per_s"] / res["fp64"]["solves_per_s"]
-    res["criterion"] = "relative residual <= 1e-7 (field error <= 1e-6), 1,024 fields, wavelengths 16-31"
+            ks = c.kernel_stats()
+            c.set_kernel_timing(False)
+            it = ks["iter"]
+            gbs = it["bytes"] / (it["ms"] / 1e3) / 1e9 if it["ms"] > 0 else None
+            res[name] = {"solves_per_s": (p.n_src + p.n_det) * CHUNK / (a0.elapsed_time(b0) / 1e3),
+                         "iters_mean": st["iters_mean"], "resid_max": st["resid_max"],
+                         "not_converged": st["n_not_converged"],
+                         "field_error_bound": kappa * st["resid_max"],
+                         "cg_iteration_gbs_at_6NW": gbs, "cg_iteration_hbm_frac": gbs / pk["hbm_gbs"] if gbs else None,
+                         "golden_wavelength_3": golden_check(gold, a, 0, lam_chk, ps, pd)}
+            r = res[name]
+            r["verified_1e-6"] = bool(r["field_error_bound"] <= 1e-6 and r["not_converged"] == 0 and
+                                      r["golden_wavelength_3"]["entry_error_over_norm"] <= 1e-6 and
+                                      r["golden_wavelength_3"]["norm_rel_error"] <= 1e-6)
+            del ps, pd
+            torch.cuda.empty_cache()
+    for name in ("mixed", "mixed_shift_guess_m40"):
+        res[f"speedup_{name}_over_fp64"] = res[name]["solves_per_s"] / res["fp64"]["solves_per_s"]
+    res["speedup"] = res["mixed_shift_guess_m40"]["solves_per_s"] / res["fp64"]["solves_per_s"]
     return res
+
+
+def config1_phase(hd, reps=5):
+    """The FP64 workload in full (24x24x16, h = 2 mm, 8 + 8 optodes on the top face, 16 wavelengths:
+    256 solves and the explicit FP64 Born matrix 1,024 x 36,864): absolute solves/s and the latency
+    of one call, its working set L2-resident (57 MB of Krylov vectors); the Born matrix, J x and
+    J^T y checked against the oracle's values stored in tests/golden."""
+    import numpy as np
+    import torch
+
+    import workloads
+
+    p = workloads.config(1)
+    gold = np.load(os.path.join(ROOT, "tests", "golden", "cw_fp64_24x24x16.npz"))
+    N, nc = p.grid.N, p.n_chrom
+    out = {"workload": "cw-fp64-24x24x16: 24x24x16 grid (h=2 mm), 8+8 optodes (top face), 16 wavelengths, FP64"}
+    with hd.Context.from_problem(p, precision="fp64", tol=1e-13, tol_cw=0.0) as c:
+        ps, pd, _ = c.solve_fields(0, p.n_lambda)
+        J = c.born_assemble(ps, pd, 0, p.n_lambda)
+        torch.cuda.synchronize()
+        solve_ms, asm_ms = [], []
+        for _ in range(reps):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record()
+            ps, pd, st = c.solve_fields(0, p.n_lambda, ps, pd)
+            e[1].record()
+            c.born_assemble(ps, pd, 0, p.n_lambda, 0, 1024, J)
+            e[2].record()
+            torch.cuda.synchronize()
+            solve_ms.append(e[0].elapsed_time(e[1]))
+            asm_ms.append(e[1].elapsed_time(e[2]))
+        x = torch.tensor(0.05 * np.abs(workloads.gaussian(20141010, nc * N)), dtype=torch.float64, device="cuda")
+        y = torch.tensor(np.abs(workloads.gaussian(20141011, 1024)), dtype=torch.float64, device="cuda")
+        jx = c.born_apply(ps, pd, 0, p.n_lambda, x).cpu().numpy()
+        jty = c.born_apply_T(ps, pd, 0, p.n_lambda, y).cpu().numpy()
+        Jg = J.cpu().numpy()
+    jerr = float((np.abs(Jg[gold["rows"], gold["cols"]] - gold["jval"]) / gold["rowmax"][gold["rows"]]).max())
+    rowmax_err = float((np.abs(np.abs(Jg).max(axis=1) - gold["rowmax"]) / gold["rowmax"]).max())
+    med = float(np.median(solve_ms))
+    out.update({
+        "solves_per_s": 256 / (med / 1e3), "call_latency_ms": {"median": med, "min": min(solve_ms)},
+        "born_assemble_ms": float(np.median(asm_ms)),
+        "born_rows_per_s": 1024 / (float(np.median(asm_ms)) / 1e3),
+        "iters_mean": st["iters_mean"], "resid_max": st["resid_max"], "not_converged": st["n_not_converged"],
+        "check_against_oracle": {"J_sampled_8192_entries_err_over_row_max": jerr, "J_row_max_rel_err": rowmax_err,
+                                 "jx_err_over_max": float(np.abs(jx - gold["jx"]).max() / np.abs(gold["jx"]).max()),
+                                 "jty_err_over_max": float(np.abs(jty - gold["jty"]).max() / np.abs(gold["jty"]).max())},
+        "hbm_frac": "n/a (L2-resident working set)"})
+    ck = out["check_against_oracle"]
+    out["check_against_oracle"]["pass"] = bool(jerr <= 1e-8 and rowmax_err <= 1e-8 and ck["jx_err_over_max"] <= 1e-10
+                                               and ck["jty_err_over_max"] <= 1e-10)
+    return out
 
 
 # ----------------------------------------------------------------------------- profiling cases
@@ -973,7 +1119,8 @@ def main():
     ap.add_argument("--steps", type=int, default=8)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=4)
+    ap.add_argument("--e2e-steps", type=int, default=None, help="end-to-end steps (default: --steps)")
+    ap.add_argument("--no-pass-breakdown", action="store_true")
     ap.add_argument("--deflation-k", type=int, default=0)
     ap.add_argument("--shift-guess-m", type=int, default=40,
                     help="Krylov basis size of the shift-invariant initial guesses (0: start from zero)")

@@ -205,20 +205,33 @@ typedef enum {
   HYDOT_KERNEL_APPLY_T = 5,    /* J^T y (partial sums) */
   HYDOT_KERNEL_SKETCH_RANGE = 6,   /* tensor-core Y = J Omega (work counted in flops) */
   HYDOT_KERNEL_SKETCH_PROJECT = 7, /* tensor-core B^T += J^T Q (work counted in flops) */
-  HYDOT_KERNEL_COUNT = 8
+  HYDOT_KERNEL_ITER = 8,       /* one inner Krylov iteration of the slice's active fields, all its
+                                * passes together; timed per group of 8 iterations (one CUDA-graph
+                                * replay or 8 direct iterations), so "launches" counts iterations */
+  HYDOT_KERNEL_COUNT = 9
 } hydot_kernel;
 
 /* Instrumentation: on != 0 makes later calls record CUDA events around each launch of the
  * kernels above (on the context's stream) and count the algorithmic bytes each launch moves
  * (the bytes the operation must read and write once: 12 B per cell and active field for
  * HYDOT_KERNEL_DIR, 20 B for HYDOT_KERNEL_UPDATE in FP32, 12 B for HYDOT_KERNEL_RESIDUAL, the rows
- * written for HYDOT_KERNEL_BORN_ROWS, the fields read for the products). Resets the totals. */
+ * written for HYDOT_KERNEL_BORN_ROWS, the fields read for the products, and for HYDOT_KERNEL_ITER
+ * 6 N w per active field and iteration: the Krylov vectors x, r and p read and written once, the
+ * least any CG iteration moves). Inner iterations replayed from a CUDA graph are timed as whole
+ * groups (HYDOT_KERNEL_ITER only); the per-pass kinds are timed when the passes are launched
+ * directly. Resets the totals. */
 int hydot_set_kernel_timing(hydot_ctx* ctx, int on);
 
 /* Totals since the last hydot_set_kernel_timing: summed device time in ms, launches, and
  * algorithmic bytes of `kernel` (a hydot_kernel). Synchronises the context's stream. Any output
  * pointer may be NULL. */
 int hydot_kernel_stats(hydot_ctx* ctx, int kernel, double* ms, long long* launches, double* bytes);
+
+/* Inner iterations of the rolling passes replay a CUDA graph per group of 8 iterations when on
+ * != 0 (the default, unless the environment variable HYDOT_NO_GRAPHS was set at hydot_setup);
+ * with on == 0 every pass is launched directly, which lets the instrumentation time each pass on
+ * its own. Results are bitwise identical either way. */
+int hydot_set_graphs(hydot_ctx* ctx, int on);
 
 /* Number of kernels this context has launched since hydot_setup (instrumentation: lets a
  * caller count the library's launches inside a timed region). */

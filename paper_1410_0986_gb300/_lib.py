@@ -27,14 +27,14 @@ EXPORTS = ("hydot_version", "hydot_setup", "hydot_set_stream", "hydot_solve_fiel
            "hydot_born_assemble",
            "hydot_born_apply", "hydot_born_apply_T", "hydot_born_apply_noalloc", "hydot_sketch_range",
            "hydot_sketch_project", "hydot_sketch_orthonormalize", "hydot_sketch_rank", "hydot_sketch_merge",
-           "hydot_sketch_factor", "hydot_set_kernel_timing",
+           "hydot_sketch_factor", "hydot_set_kernel_timing", "hydot_set_graphs",
            "hydot_kernel_stats", "hydot_kernel_launches", "hydot_get_tuning", "hydot_set_absorption",
            "hydot_wait_selftest", "hydot_set_shift_guess", "hydot_shift_guess_fields",
            "hydot_pals_reconstruct", "hydot_pals_shape", "hydot_pals_project", "hydot_shape_compare",
            "hydot_last_error", "hydot_destroy")
 ROLL_VARIANTS = 4  # HYDOT_ROLL_VARIANTS
 KERNELS = {"dir": 0, "update": 1, "residual": 2, "born_rows": 3, "apply": 4, "apply_T": 5, "sketch_range": 6,
-           "sketch_project": 7}
+           "sketch_project": 7, "iter": 8}
 
 
 class Problem(C.Structure):
@@ -91,6 +91,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib = C.CDLL(path)
     vp = C.c_void_p
     lib.hydot_version.restype = C.c_int
+    lib.hydot_set_graphs.argtypes = [vp, C.c_int]
+    lib.hydot_set_graphs.restype = C.c_int
     lib.hydot_setup.argtypes = [C.POINTER(Problem), vp, C.POINTER(vp)]
     lib.hydot_setup.restype = C.c_int
     lib.hydot_set_stream.argtypes = [vp, vp]

@@ -265,6 +265,11 @@ class Context:
         """Record CUDA events around the hot kernels from now on (resets the totals)."""
         self._check(self.lib.hydot_set_kernel_timing(self._ctx, 1 if on else 0))
 
+    def set_graphs(self, on: bool = True):
+        """Replay groups of inner iterations from a CUDA graph (default) or launch every pass
+        directly (each pass then gets its own events under set_kernel_timing)."""
+        self._check(self.lib.hydot_set_graphs(self._ctx, 1 if on else 0))
+
     def kernel_stats(self) -> dict:
         """{kernel: {"ms", "launches", "bytes"}} since set_kernel_timing (synchronises)."""
         out = {}

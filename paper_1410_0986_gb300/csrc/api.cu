@@ -129,13 +129,13 @@ cudaEvent_t timer_begin(hydot_ctx* ctx) {
   return a;
 }
 
-void timer_end(hydot_ctx* ctx, cudaEvent_t a, int kind, double bytes) {
+void timer_end(hydot_ctx* ctx, cudaEvent_t a, int kind, double bytes, int count) {
   KernelTimer& t = ctx->timer;
   if (!t.on || !a) return;
   cudaEvent_t b = t.pool[t.used++];
   cudaEventRecord(b, ctx->stream);
   t.pending.push_back({a, b, kind});
-  t.n[kind] += 1;
+  t.n[kind] += count;
   t.bytes[kind] += bytes;
 }
 
@@ -512,6 +512,14 @@ int hydot_set_kernel_timing(hydot_ctx* ctx, int on) {
       t.n[k] = 0;
       t.bytes[k] = 0.0;
     }
+    return HYDOT_OK;
+  });
+}
+
+int hydot_set_graphs(hydot_ctx* ctx, int on) {
+  return hydot::abi_guard(ctx, [&]() -> int {
+    if (!ctx) return HYDOT_ERR_ARG;
+    ctx->use_graphs = on != 0;
     return HYDOT_OK;
   });
 }

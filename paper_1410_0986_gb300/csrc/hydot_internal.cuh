@@ -406,7 +406,7 @@ int abi_guard(const hydot_ctx* ctx, F&& body) noexcept {
 // Instrumentation helpers (api.cu): a timed launch is bracketed by timer_begin/timer_end;
 // timer_flush reads the completed events (call after the stream was synchronised).
 cudaEvent_t timer_begin(hydot_ctx* ctx);
-void timer_end(hydot_ctx* ctx, cudaEvent_t a, int kind, double bytes);
+void timer_end(hydot_ctx* ctx, cudaEvent_t a, int kind, double bytes, int count = 1);
 void timer_flush(hydot_ctx* ctx);
 
 // born.cu

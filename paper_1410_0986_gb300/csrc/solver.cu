@@ -1608,8 +1608,11 @@ int inner_graph_launch(hydot_ctx* ctx, const Geo& g, const Batch& b, int variant
     cudaStream_t cs = ctx->cap_stream;
     HYDOT_CUDA_TRY(ctx, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     ctx->stream = cs;
+    const bool timing = ctx->timer.on;  // no per-pass events inside the graph: it is timed whole
+    ctx->timer.on = false;
     for (int o = 0; o < POLL_GROUP; ++o) roll_dispatch(ctx, variant, g, b, o, nrb, E, R, P);
     k_bump<<<1, 1, 0, cs>>>(ctx->d_it, POLL_GROUP);
+    ctx->timer.on = timing;
     ctx->stream = s;
     cudaError_t e = cudaStreamEndCapture(cs, &graph);
     ctx->launches = launches;
@@ -1761,6 +1764,7 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
     const unsigned nrb =
         roll ? (unsigned)((long long)b.nrhs * g.ntx * g.nty * ((g.nz + ctx->dir_seg - 1) / ctx->dir_seg)) : 0u;
     if (roll) HYDOT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_it, 0, sizeof(int), s));
+    std::vector<unsigned char> replayed;  // per group: 1 if it ran as a graph replay (no per-pass events)
     while (!stop && it < MAX_INNER_PER_CYCLE) {
       int g_end = std::min(it + POLL_GROUP, MAX_INNER_PER_CYCLE);
       // autotuning: a group that does not start the cycle runs one candidate variant and is timed
@@ -1768,12 +1772,15 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
       const bool tuning = roll && ctx->tune.variant < 0 && it > 0;
       const int g_begin = it;
       if (tuning) HYDOT_CUDA_TRY(ctx, cudaEventRecord(ctx->tune_ev[0], s));
+      cudaEvent_t t_grp = timer_begin(ctx);  // the whole group: every pass of its iterations
       if (roll) {
-        if (ctx->use_graphs && !tuning && ctx->tune.variant >= 0 && !ctx->timer.on) {
+        if (ctx->use_graphs && !tuning && ctx->tune.variant >= 0) {
           int rc = inner_graph_launch(ctx, g, b, variant, nrb, E, R, Pv);
           if (rc) return rc;
           it = g_end;
+          replayed.push_back(1);
         } else {
+          replayed.push_back(0);
           for (; it < g_end; ++it) roll_dispatch(ctx, variant, g, b, it, nrb, E, R, Pv);
           k_bump<<<1, 1, 0, s>>>(ctx->d_it, POLL_GROUP);
           ++ctx->launches;
@@ -1789,6 +1796,7 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
         ++ctx->launches;
         timer_end(ctx, t0, HYDOT_KERNEL_UPDATE, 0.0);
       }
+      timer_end(ctx, t_grp, HYDOT_KERNEL_ITER, 0.0, g_end - g_begin);
       HYDOT_CUDA_TRY(ctx, cudaGetLastError());
       if (tuning) {
         // time of the group per active cell-iteration (fields that ran x cells)
@@ -1826,10 +1834,16 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
         HYDOT_CUDA_TRY(ctx, cudaMemcpyAsync(cnt.data(), b.counter + 1, sizeof(int) * it, cudaMemcpyDeviceToHost, s));
         HYDOT_CUDA_TRY(ctx, cudaStreamSynchronize(s));
       }
-      double active = 0.0;
-      for (int q = 0; q < it; ++q) active += cnt[q];
-      ctx->timer.bytes[HYDOT_KERNEL_DIR] += active * 3.0 * (double)g.N * sizeof(T);
-      ctx->timer.bytes[HYDOT_KERNEL_UPDATE] += active * 5.0 * (double)g.N * sizeof(T);
+      // (per-pass kinds only for the groups whose passes were launched, and timed, directly)
+      double active = 0.0, direct = 0.0;
+      for (int q = 0; q < it; ++q) {
+        active += cnt[q];
+        const size_t grp = (size_t)(q / POLL_GROUP);
+        if (grp >= replayed.size() || !replayed[grp]) direct += cnt[q];
+      }
+      ctx->timer.bytes[HYDOT_KERNEL_DIR] += direct * 3.0 * (double)g.N * sizeof(T);
+      ctx->timer.bytes[HYDOT_KERNEL_UPDATE] += direct * 5.0 * (double)g.N * sizeof(T);
+      ctx->timer.bytes[HYDOT_KERNEL_ITER] += active * 6.0 * (double)g.N * sizeof(T);
       timer_flush(ctx);
     }
     // any field still marked INNER hit the per-cycle cap: finish it

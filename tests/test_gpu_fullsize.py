@@ -2,8 +2,10 @@
 16-wavelength chunks, FP32 PCG with FP64 refinement to a componentwise backward error <= 1e-8).
 
 Expected values are the oracle's sparse-direct fields at sampled voxels and at every optode
-cell, written by tests/golden/make_golden.py (oracle only). Born entries are checked at those
-voxels against the row maximum of the oracle's H row; J x / J^T y by the adjoint identity.
+cell, and its J x (every row) and J^T y (sampled voxels) on one-wavelength slices, written by
+tests/golden/make_golden.py (oracle only). Born entries are checked at the sampled voxels against
+the row maximum of the oracle's H row; J x and J^T y element by element against the oracle's
+products of its own FP64 fields, and by the adjoint identity.
 """
 import os
 
@@ -76,6 +78,27 @@ def test_born_rows_at_sampled_voxels(solved, lib):
             assert err.max() <= 1e-5, err.max()
             assert np.abs(rowmax_gpu - rowmax).max() <= 1e-5 * rowmax.max()
             assert (np.abs(rowmax_gpu - rowmax) / rowmax).max() <= 1e-5
+
+
+def test_apply_and_transpose_elementwise_full_size(solved):
+    """eqn:measurement and its transpose on one-wavelength slices of the solved chunks, against the
+    oracle's products of its sparse-direct fields: y = J x at all 1,024 (s, d) rows and g = J^T y at
+    the sampled voxels of every chromophore, each within 2e-5 of the largest entry. The probe vectors
+    are positive (x = 0.05 |gaussian|, y = |gaussian|, the recipe make_golden.py stores)."""
+    p, gold, ctx, out = solved
+    N, nc = p.grid.N, p.n_chrom
+    x = torch.tensor(0.05 * np.abs(workloads.gaussian(20141010, nc * N)), dtype=torch.float32, device="cuda")
+    y = torch.tensor(np.abs(workloads.gaussian(20141011, p.n_src * p.n_det)), dtype=torch.float32, device="cuda")
+    vox = torch.tensor(gold["vox"], device="cuda")
+    for lam, (lam0, ps, pd, st, a) in out.items():
+        k = lam - lam0
+        psl, pdl = ps[k:k + 1].contiguous(), pd[k:k + 1].contiguous()
+        jx = ctx.born_apply(psl, pdl, lam, 1, x).double().cpu().numpy()
+        ref = gold["jx"][a]
+        assert np.abs(jx - ref).max() <= 2e-5 * np.abs(ref).max(), np.abs(jx - ref).max() / np.abs(ref).max()
+        g = ctx.born_apply_T(psl, pdl, lam, 1, y).view(nc, N)[:, vox].double().cpu().numpy()
+        refg = gold["jty"][a]
+        assert np.abs(g - refg).max() <= 2e-5 * gold["jty_max"][a], np.abs(g - refg).max() / gold["jty_max"][a]
 
 
 def test_apply_adjoint_identity_full_size(solved):
