@@ -45,6 +45,8 @@ CW_FLOOR = 100.0
 WORKLOAD = ("cw-mixed-64x64x48: 64x64x48 grid (h=2 mm), 32 sources + 32 detectors, 128 wavelengths "
             "(8,192 field solves), explicit FP32 Born rows 131,072 x 786,432 in row chunks, J x and J^T r")
 KERNEL_NAMES = {"iter": "inner CG iteration (every pass of one Krylov iteration; graph replays of 8 iterations)",
+                "sweep": "k_cg_sweep (single-sweep inner CG iteration)",
+                "prime": "k_cg_sweep<PRIME> (first inner products of a refinement cycle)",
                 "dir": "k_dir_roll (inner PCG pass 1)", "update": "k_update_roll (inner PCG pass 2)",
                 "residual": "k_residual_df (residual of the double-float iterate)",
                 "born_rows": "k_born_rows (Born-row assembly)",
@@ -302,7 +304,8 @@ def run_ours(args):
     bytes_launch = kd["bytes"] / kd["launches"]
     achieved = bytes_launch / t_launch / 1e9
     dram_ratio = DRAM_PER_ALGORITHMIC_BYTE.get(dom)
-    ktotal = sum(v["ms"] for k, v in kstats.items() if k in ("iter", "residual", "born_rows", "apply", "apply_T"))
+    ktotal = sum(v["ms"] for k, v in kstats.items() if k in ("iter", "prime", "residual", "born_rows", "apply",
+                                                              "apply_T"))
     # solver roofline: 6 N w per RHS-iteration (x, r, p read and written once; FP32)
     iters = sum(s["iters_mean"] * s["n_fields"] for s in stats)
     t_solve = sum(phase["solve"]) / 1e3
@@ -393,6 +396,7 @@ def run_ours(args):
     del ps, pd, J
     torch.cuda.empty_cache()
     if args.compare_fp64 and rank == 0:
+        out["iteration_forms"] = compare_iteration_forms(hd, p)
         out["fp64_vs_mixed_at_1e-6"] = compare_fp64(hd, p)
         out["config1_fp64"] = config1_phase(hd)
         out["deflation"] = compare_deflation(hd, p)
@@ -518,9 +522,10 @@ def tree_phase(hd, p, n_lam, tol=1e-2, leaf_rank=100, merge_rank=160, n_probe=16
 
 
 def pass_breakdown(ctx, ps, pd, pk):
-    """Time of each pass of the CG iteration on one chunk (wavelengths 0-15), with the inner passes
-    launched directly so that every launch has its own CUDA events; the per-pass algorithmic bytes
-    are this design's (12 B and 20 B per cell and active field), the iteration's 24 B (x, r, p once)."""
+    """Time of each launch of the CG iteration on one chunk (wavelengths 0-15), with the inner
+    launches made directly so that every launch has its own CUDA events: the single sweep (24 B per
+    cell and active field: x, r, p once) and the cycle's priming pass, or the two passes of the
+    two-pass form (12 B and 20 B)."""
     ctx.set_graphs(False)
     ctx.set_kernel_timing(True)
     ctx.solve_fields(0, CHUNK, ps, pd)
@@ -528,7 +533,7 @@ def pass_breakdown(ctx, ps, pd, pk):
     ctx.set_kernel_timing(False)
     ctx.set_graphs(True)
     out = {}
-    for k in ("dir", "update", "iter", "residual"):
+    for k in ("sweep", "prime", "dir", "update", "iter", "residual"):
         v = ks[k]
         if v["ms"] > 0 and v["launches"] > 0:
             gbs = v["bytes"] / (v["ms"] / 1e3) / 1e9
@@ -752,6 +757,43 @@ def recon_phase(hd, tols=(1e-2, 1e-3), n_basis=3):
             out[f"tol={tol:g}"] = res
         del om
     return out
+
+
+def compare_iteration_forms(hd, p):
+    """Field solves/s of one 16-wavelength chunk (wavelengths 16-31) with the single-sweep inner
+    iteration against the two-pass one (the same CG in exact arithmetic), each after a warm-up
+    call on the same chunk (autotuner settled, graphs captured); shift-invariant guesses m = 40."""
+    import torch
+
+    res = {}
+    for label, flag in (("single_sweep", "0"), ("two_pass", "1")):
+        os.environ["HYDOT_TWO_PASS"] = flag
+        try:
+            with hd.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=TOL_CW, cw_floor=CW_FLOOR,
+                                         max_lambda_per_call=CHUNK) as c:
+                c.set_shift_guess(40)
+                c.solve_fields(CHUNK, CHUNK)
+                c.solve_fields(CHUNK, CHUNK)
+                torch.cuda.synchronize()
+                c.set_kernel_timing(True)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record()
+                _, _, st = c.solve_fields(CHUNK, CHUNK)
+                b.record()
+                torch.cuda.synchronize()
+                ks = c.kernel_stats()
+                c.set_kernel_timing(False)
+                it = ks["iter"]
+                gbs = it["bytes"] / (it["ms"] / 1e3) / 1e9 if it["ms"] > 0 else None
+                res[label] = {"solves_per_s": (p.n_src + p.n_det) * CHUNK / (a.elapsed_time(b) / 1e3),
+                              "iters_mean": st["iters_mean"], "cycles_max": st["cycles_max"],
+                              "cg_iteration_gbs_at_6NW": gbs, "cg_iteration_hbm_frac": gbs / peaks()["hbm_gbs"] if gbs
+                              else None, "autotune": c.tuning()}
+        finally:
+            os.environ.pop("HYDOT_TWO_PASS", None)
+    res["speedup"] = res["single_sweep"]["solves_per_s"] / res["two_pass"]["solves_per_s"]
+    return res
 
 
 def compare_deflation(hd, p, k=16):
@@ -1010,7 +1052,8 @@ def config1_phase(hd, reps=5):
                                  "jty_err_over_max": float(np.abs(jty - gold["jty"]).max() / np.abs(gold["jty"]).max())},
         "hbm_frac": "n/a (L2-resident working set)"})
     ck = out["check_against_oracle"]
-    out["check_against_oracle"]["pass"] = bool(jerr <= 1e-8 and rowmax_err <= 1e-8 and ck["jx_err_over_max"] <= 1e-10
+    # Born entries within 1e-5 of their row maximum (the project's Born tolerance), products to 1e-10
+    out["check_against_oracle"]["pass"] = bool(jerr <= 1e-5 and rowmax_err <= 1e-5 and ck["jx_err_over_max"] <= 1e-10
                                                and ck["jty_err_over_max"] <= 1e-10)
     return out
 
@@ -1019,7 +1062,8 @@ def config1_phase(hd, reps=5):
 def run_kernel_case(name: str, reps: int = 3):
     """A small, bounded case of one hot kernel on the workload's grid, for profiler captures:
     born_rows   512 rows of one 16-wavelength chunk (1.6 GB written per launch)
-    solver      the 64 fields of one wavelength (FP32 PCG + FP64 refinement, ~300 MB of vectors)
+    solver      the 64 fields of one wavelength (FP32 PCG + FP64 refinement, ~350 MB of vectors)
+    solver256   the 256 fields of four wavelengths (~1.4 GB of vectors: well above L2)
     sketch      the tensor-core passes Y = J Omega and B^T += J^T Q over one 16-wavelength chunk
                 (rank 200 + 20)
     apply       J x and J^T r over one 16-wavelength chunk of fields
@@ -1049,7 +1093,7 @@ def run_kernel_case(name: str, reps: int = 3):
 
     p = workloads.config(2)
     ns, nd, nc, N = p.n_src, p.n_det, p.n_chrom, p.grid.N
-    lam_n = 1 if name == "solver" else CHUNK
+    lam_n = {"solver": 1, "solver256": 4}.get(name, CHUNK)
     ctx = hd.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=TOL_CW, cw_floor=CW_FLOOR,
                                   max_lambda_per_call=lam_n)
     gen = torch.Generator(device="cuda").manual_seed(7)
@@ -1063,9 +1107,9 @@ def run_kernel_case(name: str, reps: int = 3):
             J = torch.empty(512, nc * N, device="cuda") if not times else J
             a.record()
             ctx.born_assemble(ps, pd, 0, CHUNK, 0, 512, J)
-        elif name == "solver":
+        elif name in ("solver", "solver256"):
             a.record()
-            ctx.solve_fields(0, 1, ps, pd)
+            ctx.solve_fields(0, lam_n, ps, pd)
         elif name == "sketch":
             if not times:
                 om = torch.randn(nc, 220, N, device="cuda", generator=gen).to(torch.bfloat16)
@@ -1134,7 +1178,7 @@ def main():
     ap.add_argument("--no-compare-fp64", dest="compare_fp64", action="store_false")
     ap.add_argument("--cpu-sample", type=int, default=None, help=argparse.SUPPRESS)
     ap.add_argument("--kernel-case", default=None,
-                    help="born_rows | solver | solver_fd | sketch | apply: small profiling case")
+                    help="born_rows | solver | solver256 | solver_fd | sketch | apply: small profiling case")
     args = ap.parse_args()
     if args.kernel_case:
         run_kernel_case(args.kernel_case)

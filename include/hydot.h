@@ -208,13 +208,18 @@ typedef enum {
   HYDOT_KERNEL_ITER = 8,       /* one inner Krylov iteration of the slice's active fields, all its
                                 * passes together; timed per group of 8 iterations (one CUDA-graph
                                 * replay or 8 direct iterations), so "launches" counts iterations */
-  HYDOT_KERNEL_COUNT = 9
+  HYDOT_KERNEL_SWEEP = 9,      /* single-sweep inner CG iteration (real FP32 fields): p, s = A p,
+                                * x, r, u = D^-1 r, A u and both inner products in one pass */
+  HYDOT_KERNEL_PRIME = 10,     /* once per refinement cycle before the single-sweep iterations:
+                                * the first inner products from r_0 (reads r) */
+  HYDOT_KERNEL_COUNT = 11
 } hydot_kernel;
 
 /* Instrumentation: on != 0 makes later calls record CUDA events around each launch of the
  * kernels above (on the context's stream) and count the algorithmic bytes each launch moves
  * (the bytes the operation must read and write once: 12 B per cell and active field for
- * HYDOT_KERNEL_DIR, 20 B for HYDOT_KERNEL_UPDATE in FP32, 12 B for HYDOT_KERNEL_RESIDUAL, the rows
+ * HYDOT_KERNEL_DIR, 20 B for HYDOT_KERNEL_UPDATE in FP32, 24 B for HYDOT_KERNEL_SWEEP, 4 B for
+ * HYDOT_KERNEL_PRIME, 12 B for HYDOT_KERNEL_RESIDUAL, the rows
  * written for HYDOT_KERNEL_BORN_ROWS, the fields read for the products, and for HYDOT_KERNEL_ITER
  * 6 N w per active field and iteration: the Krylov vectors x, r and p read and written once, the
  * least any CG iteration moves). Inner iterations replayed from a CUDA graph are timed as whole

@@ -34,7 +34,7 @@ EXPORTS = ("hydot_version", "hydot_setup", "hydot_set_stream", "hydot_solve_fiel
            "hydot_last_error", "hydot_destroy")
 ROLL_VARIANTS = 4  # HYDOT_ROLL_VARIANTS
 KERNELS = {"dir": 0, "update": 1, "residual": 2, "born_rows": 3, "apply": 4, "apply_T": 5, "sketch_range": 6,
-           "sketch_project": 7, "iter": 8}
+           "sketch_project": 7, "iter": 8, "sweep": 9, "prime": 10}
 
 
 class Problem(C.Structure):

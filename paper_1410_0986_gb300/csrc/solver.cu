@@ -1329,6 +1329,351 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_update_roll(Geo g, Batch b, 
   }
 }
 
+// ---------------------------------------------------------------- single-sweep inner iteration
+// One pass over memory per inner iteration: Jacobi-preconditioned CG in the form of Chronopoulos
+// & Gear (1989), whose two inner products of an iteration, gamma = r^T u and delta = (Ahat u)^T u
+// with u = D^-1 r, come from the same sweep, so that alpha and beta of the next iteration are
+// known before it starts:
+//   beta_k = gamma_k / gamma_(k-1),  alpha_k = gamma_k / (delta_k - beta_k gamma_k / alpha_(k-1))
+//   (alpha_0 = gamma_0 / delta_0, beta_0 = 0), and then, in one sweep,
+//   p_k = u_k + beta_k p_(k-1),  s_k = Ahat p_k,  e_(k+1) = e_k + alpha_k p_k,
+//   r_(k+1) = r_k - alpha_k s_k,  u_(k+1) = D^-1 r_(k+1),  w_(k+1) = Ahat u_(k+1),
+//   gamma_(k+1) = r_(k+1)^T u_(k+1),  delta_(k+1) = w_(k+1)^T u_(k+1),  ||r_(k+1)||^2.
+// s_k is recomputed from p_k instead of carried by a recurrence, so the sweep reads r, p and e once
+// and writes them once (6 words per cell: the least a CG iteration moves). Recomputing s on the
+// tile and its one-cell ring and w on the tile needs p on a two-cell ring: a block's slabs are
+// boxes of 40 x 12 cells (the 32 x 8 tile, two cells around it, x rounded out to x0 - 4 for the
+// 16-byte rule) of r and p_(k-1), plus the tile's e, arriving by TMA. Per slab of RP planes:
+//   (A) p_k on the tile and both rings, in place over p_(k-1);            barrier
+//   (B) s, r_(k+1), u_(k+1) on the tile and the inner ring one plane behind (u in place over r);
+//       e, p and r of the tile cells to global memory;                      barrier
+//   (C) w = Ahat u and the inner products on the tile two planes behind.
+// r is double-buffered (neighbouring blocks read r_k on their ring while this block writes
+// r_(k+1)); p already is. A block of the first sweep of a cycle reads neither p nor e (both zero).
+// The priming launch of a cycle (PRIME) computes only gamma_0, delta_0 and ||r_0||^2 from r_0.
+// Per-field scalars: every block of a field forms the same gamma_k, delta_k from the per-tile
+// partials in the same order; gamma_k and alpha_k of iteration k are kept per field (one block
+// writes them) for iteration k + 1. Threads 0..91 form p on the outer ring, threads 172..255 run
+// (A) and (B) on the inner ring as well; the z-neighbours of every column are registers.
+constexpr int BX2 = 40, BY2 = 12;
+constexpr int PL2 = BX2 * BY2;  // cells of one box plane
+constexpr int TPL = TX * TY;    // cells of one tile plane
+template <int RP>
+__host__ __device__ constexpr uint32_t sw_slab_bytes() {  // r | p | e
+  return (uint32_t)((2 * RP * PL2 + RP * TPL) * sizeof(float));
+}
+template <int RP, int RS>
+constexpr size_t sw_smem() { return (size_t)RS * sw_slab_bytes<RP>() + 128; }
+constexpr int RING1 = 84, RING2 = 92, RING1_T0 = NTHREADS - RING1;
+
+// (hx, hy) of ring cell q, relative to the tile origin: ring 1 (one cell out) or ring 2 (two)
+__device__ __forceinline__ void ring_cell(int ring, int q, int& hx, int& hy) {
+  const int w = TX + 2 * ring, h = TY + 2 * ring;  // extent of the ring's outline
+  if (q < 2 * w) {
+    hx = q % w - ring;
+    hy = (q < w) ? -ring : TY - 1 + ring;
+  } else {
+    q -= 2 * w;
+    const int hh = h - 2;
+    hx = (q < hh) ? -ring : TX - 1 + ring;
+    hy = q % hh - ring + 1;
+  }
+}
+
+// Per-field scalars of the single-sweep iteration: [parity][field] {gamma, alpha}.
+struct SweepScalars {
+  double* s;  // [2][nrhs_max][2]
+  int stride; // fields per parity
+};
+
+template <int RP, int RS, int MINB, bool PRIME>
+__global__ void __launch_bounds__(NTHREADS, MINB) k_cg_sweep(Geo g, Batch b, const int* __restrict__ it_dev, int k,
+                                                             int seg, const LamCoefF* __restrict__ coef_f,
+                                                             SweepScalars sc,
+                                                             const __grid_constant__ CUtensorMap mapR0,
+                                                             const __grid_constant__ CUtensorMap mapR1,
+                                                             const __grid_constant__ CUtensorMap mapP0,
+                                                             const __grid_constant__ CUtensorMap mapP1,
+                                                             const __grid_constant__ CUtensorMap mapE,
+                                                             float* __restrict__ R0, float* __restrict__ R1,
+                                                             float* __restrict__ P0, float* __restrict__ P1,
+                                                             float* __restrict__ Eo) {
+  static_assert(RP >= 3 && RS >= 3, "stage C reads u one slab back; a buffer is refilled two slabs after its own");
+  extern __shared__ unsigned char dsm[];
+  float* slab = align128<float>(dsm);  // [RS][r -> u: RP planes][p: RP planes][e: RP tile planes]
+  constexpr int SLAB = 2 * RP * PL2 + RP * TPL;  // floats per slab buffer
+  __shared__ uint64_t mbar[RS];
+  __shared__ double sm[96];
+  __shared__ float s_beta, s_alpha;
+  __shared__ int s_go, s_st;
+  const int it = PRIME ? 0 : *it_dev + k;
+  const int ncol = g.ntx * g.nty;
+  const int nseg = (g.nz + seg - 1) / seg;
+  const int rhs = blockIdx.x / (ncol * nseg);
+  const int rem = blockIdx.x - rhs * ncol * nseg;
+  const int zs = rem / ncol, col = rem - zs * ncol;
+  const int x0 = (col % g.ntx) * TX, y0 = (col / g.ntx) * TY;
+  const int z0 = zs * seg, z1 = min(z0 + seg, g.nz);
+  const bool lead = (col == 0 && zs == 0);
+  const int T_ = g.ntiles;
+  double* pb = b.part + (size_t)rhs * part_stride(T_);
+  const int par = it & 1;
+  const bool first = PRIME || it == 0;
+  const int np = z1 - z0 + 4;  // planes z0-2 .. z1+1 (t = plane - (z0 - 2))
+  const int nslab = (np + RP - 1) / RP;
+  const int nfirst = min(RS, nslab);
+  const CUtensorMap* mr = par ? &mapR1 : &mapR0;
+  const CUtensorMap* mp = par ? &mapP0 : &mapP1;  // p_(k-1) was written by iteration k-1 into P[k & 1 ^ 1]
+  const uint32_t tx_bytes = first ? RP * PL2 * 4u : (2u * RP * PL2 + RP * TPL) * 4u;
+  auto issue = [&](int q) {
+    float* dst = slab + (q % RS) * SLAB;
+    const int zq = z0 - 2 + q * RP;
+    mbar_expect_tx(&mbar[q % RS], tx_bytes);
+    tma_load_4d(dst, mr, &mbar[q % RS], x0 - 4, y0 - 2, zq, rhs);
+    if (!first) {
+      tma_load_4d(dst + RP * PL2, mp, &mbar[q % RS], x0 - 4, y0 - 2, zq, rhs);
+      tma_load_4d(dst + 2 * RP * PL2, &mapE, &mbar[q % RS], x0, y0, zq, rhs);
+    }
+  };
+  if (threadIdx.x == 0) {
+    const int st = b.status[rhs];
+    s_st = st;
+    if (st == RHS_INNER) {
+      for (int q = 0; q < RS; ++q) mbar_init(&mbar[q], 1);
+      mbar_fence_init();
+      for (int q = 0; q < nfirst; ++q) issue(q);
+    }
+  }
+  __syncthreads();
+  if (s_st != RHS_INNER) return;
+  if (!PRIME) {
+    if (threadIdx.x < 32) {
+      double vg = 0.0, vd = 0.0, vr = 0.0;
+      for (int t = threadIdx.x; t < T_; t += 32) {
+        vg += pb[T_ * par + t];
+        vd += pb[2 * T_ + T_ * par + t];
+        vr += pb[4 * T_ + T_ * par + t];
+      }
+      vg = warp_sum(vg);
+      vd = warp_sum(vd);
+      vr = warp_sum(vr);
+      if (threadIdx.x == 0) {
+        bool done = vr <= b.tol_in2 * b.rr0[rhs] || it >= b.max_inner || b.iters[rhs] >= b.max_iter || vr == 0.0;
+        double alpha = 0.0, beta = 0.0;
+        if (!done) {
+          if (it == 0) {
+            alpha = vg / vd;
+          } else {
+            const double* prev = sc.s + ((size_t)(par ^ 1) * sc.stride + rhs) * 2;
+            beta = vg / prev[0];
+            const double den = vd - beta * vg / prev[1];
+            alpha = vg / den;
+            done = !(den > 0.0);  // breakdown (p^T Ahat p not positive in rounding): end this inner solve
+          }
+          done = done || !(vd > 0.0) || !isfinite(alpha);
+        }
+        if (done) {
+          if (lead) b.status[rhs] = RHS_FINISHED;
+        } else if (lead) {
+          double* cur = sc.s + ((size_t)par * sc.stride + rhs) * 2;
+          cur[0] = vg;
+          cur[1] = alpha;
+          atomicAdd(&b.counter[1 + it], 1);
+        }
+        s_go = done ? 0 : 1;
+        s_alpha = (float)alpha;
+        s_beta = (float)beta;
+      }
+    }
+  } else if (threadIdx.x == 0) {
+    s_go = 1;
+    s_alpha = 0.f;
+    s_beta = 0.f;
+  }
+  const LamCoefF cf = coef_f[rhs_lambda(b, rhs)];
+  __syncthreads();
+  if (!s_go) {
+    if (threadIdx.x == 0)
+      for (int q = 0; q < nfirst; ++q) mbar_wait_bounded(&mbar[q % RS], 0u);
+    return;
+  }
+  const float alpha = s_alpha, beta = s_beta;
+
+  // own column
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int i = x0 + tx, j = y0 + ty;
+  const bool in = (i < g.nx) && (j < g.ny);
+  const int ob = (ty + 2) * BX2 + tx + 4;
+  float dd[4], di[4];
+  col_diag(cf, (i == 0) | ((i == g.nx - 1) << 1) | ((j == 0) << 2) | ((j == g.ny - 1) << 3), dd, di);
+  // ring cells: outer ring (p only) for threads 0..91, inner ring (p, s, r, u) for threads 172..255
+  const bool has2 = threadIdx.x < RING2;
+  const bool has1 = threadIdx.x >= RING1_T0;
+  int h2b = 0, h1b = 0;
+  bool h1in = false;
+  float h2di[4] = {}, h1d[4] = {}, h1di[4] = {};
+  if (has2) {
+    int hx, hy;
+    ring_cell(2, threadIdx.x, hx, hy);
+    h2b = (hy + 2) * BX2 + hx + 4;
+    const int gi = x0 + hx, gj = y0 + hy;
+    float d4[4];
+    col_diag(cf, (gi == 0) | ((gi == g.nx - 1) << 1) | ((gj == 0) << 2) | ((gj == g.ny - 1) << 3), d4, h2di);
+  }
+  if (has1) {
+    int hx, hy;
+    ring_cell(1, threadIdx.x - RING1_T0, hx, hy);
+    h1b = (hy + 2) * BX2 + hx + 4;
+    const int gi = x0 + hx, gj = y0 + hy;
+    h1in = gi >= 0 && gi < g.nx && gj >= 0 && gj < g.ny;
+    col_diag(cf, (gi == 0) | ((gi == g.nx - 1) << 1) | ((gj == 0) << 2) | ((gj == g.ny - 1) << 3), h1d, h1di);
+  }
+  const int plane_n = g.nx * g.ny;
+  const size_t base = (size_t)rhs * g.N + (size_t)j * g.nx + i;
+  float* Rn = par ? R0 : R1;  // r_(k+1)
+  float* Pn = par ? P1 : P0;  // p_k (read back as p_(k-1) by iteration k + 1 from the other buffer)
+  // z-queues: p of the own column and inner-ring cell (two planes back), u and r_(k+1) of the own column
+  float pq2 = 0.f, pq1 = 0.f, hq2 = 0.f, hq1 = 0.f, uq2 = 0.f, uq1 = 0.f, rq1 = 0.f;
+  float ag = 0.f, ad = 0.f, ar = 0.f;
+  const float* prev = slab;
+  for (int q = 0; q < nslab; ++q) {
+    float* cur = slab + (q % RS) * SLAB;
+    const bool ok = mbar_wait_bounded(&mbar[q % RS], (uint32_t)((q / RS) & 1));
+    const int zA = z0 - 2 + q * RP;  // plane of (A)'s first slab plane
+    float pA[RP], hA[RP];
+#pragma unroll
+    for (int u = 0; u < RP; ++u) pA[u] = hA[u] = 0.f;
+    // (A) p_k = D^-1 r_k + beta p_(k-1) on the tile and both rings (zero outside the grid: r and
+    // p arrive as zeros there)
+    if (!PRIME) {
+      const bool edge = zA <= 0 || zA + RP - 1 >= g.nz - 1;
+#pragma unroll
+      for (int u = 0; u < RP; ++u) {
+        const int zt = zA + u;
+        const int zb = edge ? ((zt == 0) | ((zt == g.nz - 1) << 1)) : 0;
+        float* rp = cur + u * PL2;
+        float* pp = cur + RP * PL2 + u * PL2;
+        float v = rp[ob] * pick4(di, zb);
+        if (!first) v = fmaf(beta, pp[ob], v);
+        pp[ob] = v;
+        pA[u] = v;
+        if (has2) {
+          float hv = rp[h2b] * pick4(h2di, zb);
+          if (!first) hv = fmaf(beta, pp[h2b], hv);
+          pp[h2b] = hv;
+        }
+        hA[u] = 0.f;
+        if (has1) {
+          float hv = rp[h1b] * pick4(h1di, zb);
+          if (!first) hv = fmaf(beta, pp[h1b], hv);
+          pp[h1b] = hv;
+          hA[u] = hv;
+        }
+      }
+    }
+    if (!__syncthreads_and(ok)) {
+      if (threadIdx.x == 0) {
+        atomicExch(b.err, 1);
+        const int last = min(max(RS - 1, q + RS - 3), nslab - 1);
+        for (int u = q; u <= last; ++u) mbar_wait_bounded(&mbar[u % RS], (uint32_t)((u / RS) & 1));
+      }
+      return;
+    }
+    // every thread is past (C) of slab q - 1, the last reader of slab q - 2: refill its buffer
+    if (threadIdx.x == 0 && q >= 2 && q - 2 + RS < nslab) issue(q - 2 + RS);
+    // (B) planes zA - 1 .. zA + RP - 2 (the first in the previous slab's buffer)
+    float uB[RP], rB[RP];
+#pragma unroll
+    for (int u = 0; u < RP; ++u) {
+      const int zt = zA - 1 + u;
+      uB[u] = 0.f;
+      rB[u] = 0.f;
+      if (zt < z0 - 1 || zt > z1) continue;  // not needed by (C)
+      const bool zin = zt >= 0 && zt < g.nz;
+      const int zb = (zt == 0) | ((zt == g.nz - 1) << 1);
+      float* rpl = (u == 0) ? const_cast<float*>(prev) + (RP - 1) * PL2 : cur + (u - 1) * PL2;
+      const float* ppl = rpl + RP * PL2;
+      if (PRIME) {
+        const float rv = rpl[ob];
+        const float uv = (in && zin) ? rv * pick4(di, zb) : 0.f;
+        rpl[ob] = uv;
+        uB[u] = uv;
+        rB[u] = rv;
+        if (has1) rpl[h1b] = (h1in && zin) ? rpl[h1b] * pick4(h1di, zb) : 0.f;
+        continue;
+      }
+      {
+        const float below = (u == 0) ? pq2 : (u == 1 ? pq1 : pA[u - 2]);
+        const float centre = (u == 0) ? pq1 : pA[u - 1];
+        const float sn = (ppl[ob - 1] + ppl[ob + 1]) + (ppl[ob - BX2] + ppl[ob + BX2]) + (below + pA[u]);
+        const float s = fmaf(pick4(dd, zb), centre, -sn);
+        const float rn = fmaf(-alpha, s, rpl[ob]);
+        const float uv = (in && zin) ? rn * pick4(di, zb) : 0.f;
+        rpl[ob] = uv;
+        uB[u] = uv;
+        rB[u] = rn;
+        if (in && zt >= z0 && zt < z1) {
+          const float* epl = ((u == 0) ? prev + 2 * RP * PL2 + (RP - 1) * TPL : cur + 2 * RP * PL2 + (u - 1) * TPL);
+          const size_t id = base + (size_t)zt * plane_n;
+          Eo[id] = first ? alpha * centre : fmaf(alpha, centre, epl[threadIdx.x]);
+          Pn[id] = centre;
+          Rn[id] = rn;
+        }
+      }
+      if (has1) {
+        const float below = (u == 0) ? hq2 : (u == 1 ? hq1 : hA[u - 2]);
+        const float centre = (u == 0) ? hq1 : hA[u - 1];
+        const float sn = (ppl[h1b - 1] + ppl[h1b + 1]) + (ppl[h1b - BX2] + ppl[h1b + BX2]) + (below + hA[u]);
+        const float s = fmaf(pick4(h1d, zb), centre, -sn);
+        const float rn = fmaf(-alpha, s, rpl[h1b]);
+        rpl[h1b] = (h1in && zin) ? rn * pick4(h1di, zb) : 0.f;
+      }
+    }
+    // the in-place writes are ordered before the copies that later refill these buffers
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    // (C) planes zA - 2 .. zA + RP - 3: w = Ahat u and the inner products
+    if (in) {
+#pragma unroll
+      for (int u = 0; u < RP; ++u) {
+        const int zt = zA - 2 + u;
+        if (zt < z0 || zt >= z1) continue;
+        const int zb = (zt == 0) | ((zt == g.nz - 1) << 1);
+        const float* upl = (u <= 1) ? prev + (RP - 2 + u) * PL2 : cur + (u - 2) * PL2;
+        const float below = (u == 0) ? uq2 : (u == 1 ? uq1 : uB[u - 2]);
+        const float centre = (u == 0) ? uq1 : uB[u - 1];
+        const float rn = (u == 0) ? rq1 : rB[u - 1];
+        const float sn = (upl[ob - 1] + upl[ob + 1]) + (upl[ob - BX2] + upl[ob + BX2]) + (below + uB[u]);
+        const float w = fmaf(pick4(dd, zb), centre, -sn);
+        ag = fmaf(rn, centre, ag);
+        ad = fmaf(w, centre, ad);
+        ar = fmaf(rn, rn, ar);
+      }
+    }
+    pq2 = pA[RP - 2];
+    pq1 = pA[RP - 1];
+    hq2 = hA[RP - 2];
+    hq1 = hA[RP - 1];
+    uq2 = uB[RP - 2];
+    uq1 = uB[RP - 1];
+    rq1 = rB[RP - 1];
+    prev = cur;
+  }
+  float a3[3] = {ag, ad, ar};
+  double o3[3];
+  block_sum<3, float>(a3, o3, sm);
+  const int npar = PRIME ? 0 : (par ^ 1);
+  const int nsl = (z1 - z0 + g.tz - 1) / g.tz;
+  if (threadIdx.x < nsl) {
+    const int slot = col + (z0 / g.tz + threadIdx.x) * ncol;
+    const bool z = threadIdx.x == 0;
+    pb[T_ * npar + slot] = z ? o3[0] : 0.0;
+    pb[2 * T_ + T_ * npar + slot] = z ? o3[1] : 0.0;
+    pb[4 * T_ + T_ * npar + slot] = z ? o3[2] : 0.0;
+    if (!PRIME && z && lead) b.iters[rhs] += 1;
+  }
+}
+
 // ---------------------------------------------------------------- fold, output
 template <typename T, typename X>
 __global__ void k_fold(Geo g, Batch b, X* __restrict__ x64, const T* __restrict__ E) {
@@ -1476,6 +1821,44 @@ constexpr RollVariant ROLL_VARIANTS_C[HYDOT_ROLL_VARIANTS] = {{2, 4}, {2, 6}, {4
 
 __host__ __device__ constexpr int rp_index(int rp) { return rp == 2 ? 0 : (rp == 4 ? 1 : 2); }
 
+// Single-sweep variants {planes per slab, slab buffers} (real FP32 fields); bitwise identical results.
+// The blocks-per-SM bounds are what their shared memory allows: {4,3} and {3,4} 58 KB, {3,5} 73 KB
+// (three blocks per SM), {4,4} 78 KB (two).
+constexpr RollVariant SWEEP_VARIANTS[HYDOT_ROLL_VARIANTS] = {{4, 3}, {4, 4}, {3, 4}, {3, 5}};
+__host__ __device__ constexpr int sw_index(int rp) { return rp == 3 ? 0 : 1; }
+
+template <int RP, int RS, int MB>
+int sweep_attrs(hydot_ctx* ctx) {
+  HYDOT_CUDA_TRY(ctx, raise_smem_limit(k_cg_sweep<RP, RS, MB, false>, sw_smem<RP, RS>()));
+  HYDOT_CUDA_TRY(ctx, raise_smem_limit(k_cg_sweep<RP, RS, MB, true>, sw_smem<RP, RS>()));
+  return HYDOT_OK;
+}
+
+// One single-sweep iteration (k_off: offset of the iteration in its group; the group's base index
+// is on the device) or, with PRIME, the cycle's priming pass.
+template <int RP, int RS, int MB, bool PRIME>
+void sweep_launch(hydot_ctx* ctx, const Geo& g, const Batch& b, int k_off, unsigned nrb) {
+  const int d = sw_index(RP);
+  const SweepScalars sc{ctx->d_cgsc, ctx->max_fields};
+  cudaEvent_t t0 = timer_begin(ctx);
+  k_cg_sweep<RP, RS, MB, PRIME><<<nrb, NTHREADS, sw_smem<RP, RS>(), ctx->stream>>>(
+      g, b, ctx->d_it, k_off, ctx->dir_seg, ctx->d_coef_f, sc, ctx->tm_r2[d][0], ctx->tm_r2[d][1], ctx->tm_p2[d][0],
+      ctx->tm_p2[d][1], ctx->tm_e2[d], (float*)ctx->d_r, (float*)ctx->d_r2, (float*)ctx->d_p[0], (float*)ctx->d_p[1],
+      (float*)ctx->d_e);
+  ++ctx->launches;
+  timer_end(ctx, t0, PRIME ? HYDOT_KERNEL_PRIME : HYDOT_KERNEL_SWEEP, 0.0);
+}
+
+template <bool PRIME>
+void sweep_dispatch(hydot_ctx* ctx, int v, const Geo& g, const Batch& b, int k_off, unsigned nrb) {
+  switch (v) {
+    case 1: sweep_launch<4, 4, 2, PRIME>(ctx, g, b, k_off, nrb); break;
+    case 2: sweep_launch<3, 4, 3, PRIME>(ctx, g, b, k_off, nrb); break;
+    case 3: sweep_launch<3, 5, 3, PRIME>(ctx, g, b, k_off, nrb); break;
+    default: sweep_launch<4, 3, 3, PRIME>(ctx, g, b, k_off, nrb); break;
+  }
+}
+
 template <typename E, int RP, int RS, int MB1, int MB2>
 int roll_attrs(hydot_ctx* ctx) {
   HYDOT_CUDA_TRY(ctx, raise_smem_limit(k_dir_roll<E, RP, RS, MB1>, roll_smem<E, RP, RS>()));
@@ -1507,6 +1890,10 @@ void roll_iteration(hydot_ctx* ctx, const Geo& g, const Batch& b, int it, unsign
 // bounds are what their shared memory allows (228 KB per SM).
 void roll_dispatch(hydot_ctx* ctx, int v, const Geo& g, const Batch& b, int it, unsigned nrb, void* Ev, void* R,
                    void* const* P) {
+  if (ctx->use_sweep) {
+    sweep_dispatch<false>(ctx, v, g, b, it % POLL_GROUP, nrb);
+    return;
+  }
   if (ctx->cplx) {
     float2* e = (float2*)Ev;
     float2* r = (float2*)R;
@@ -1531,6 +1918,13 @@ void roll_dispatch(hydot_ctx* ctx, int v, const Geo& g, const Batch& b, int it, 
 }
 
 int roll_setup(hydot_ctx* ctx) {
+  if (ctx->use_sweep) {
+    int rc = sweep_attrs<4, 3, 3>(ctx);
+    if (!rc) rc = sweep_attrs<4, 4, 2>(ctx);
+    if (!rc) rc = sweep_attrs<3, 4, 3>(ctx);
+    if (!rc) rc = sweep_attrs<3, 5, 3>(ctx);
+    return rc;
+  }
   if (ctx->cplx) {
     int rc = roll_attrs<float2, 2, 4, 3, 3>(ctx);
     if (!rc) rc = roll_attrs<float2, 2, 6, 2, 2>(ctx);
@@ -1764,6 +2158,12 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
     const unsigned nrb =
         roll ? (unsigned)((long long)b.nrhs * g.ntx * g.nty * ((g.nz + ctx->dir_seg - 1) / ctx->dir_seg)) : 0u;
     if (roll) HYDOT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_it, 0, sizeof(int), s));
+    if (roll && ctx->use_sweep) {
+      // the cycle's first inner products (gamma_0, delta_0, ||r_0||^2) from r_0
+      sweep_dispatch<true>(ctx, roll_pick(ctx), g, b, 0, nrb);
+      if (ctx->timer.on) ctx->timer.bytes[HYDOT_KERNEL_PRIME] += (double)prev_active * (double)g.N * sizeof(T);
+      HYDOT_CUDA_TRY(ctx, cudaGetLastError());
+    }
     std::vector<unsigned char> replayed;  // per group: 1 if it ran as a graph replay (no per-pass events)
     while (!stop && it < MAX_INNER_PER_CYCLE) {
       int g_end = std::min(it + POLL_GROUP, MAX_INNER_PER_CYCLE);
@@ -1841,8 +2241,12 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
         const size_t grp = (size_t)(q / POLL_GROUP);
         if (grp >= replayed.size() || !replayed[grp]) direct += cnt[q];
       }
-      ctx->timer.bytes[HYDOT_KERNEL_DIR] += direct * 3.0 * (double)g.N * sizeof(T);
-      ctx->timer.bytes[HYDOT_KERNEL_UPDATE] += direct * 5.0 * (double)g.N * sizeof(T);
+      if (roll && ctx->use_sweep) {
+        ctx->timer.bytes[HYDOT_KERNEL_SWEEP] += direct * 6.0 * (double)g.N * sizeof(T);
+      } else {
+        ctx->timer.bytes[HYDOT_KERNEL_DIR] += direct * 3.0 * (double)g.N * sizeof(T);
+        ctx->timer.bytes[HYDOT_KERNEL_UPDATE] += direct * 5.0 * (double)g.N * sizeof(T);
+      }
       ctx->timer.bytes[HYDOT_KERNEL_ITER] += active * 6.0 * (double)g.N * sizeof(T);
       timer_flush(ctx);
     }
@@ -1977,8 +2381,23 @@ int solver_alloc(hydot_ctx* ctx) {
   HYDOT_CUDA_TRY(ctx, cudaMemset(ctx->d_it, 0, sizeof(int)));
   ctx->use_graphs = !getenv_flag("HYDOT_NO_GRAPHS");
   HYDOT_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+  // real FP32 fields on the TMA path iterate in single sweeps (HYDOT_TWO_PASS=1: the two-pass form)
+  ctx->use_sweep = ctx->use_tma && !ctx->cplx && !getenv_flag("HYDOT_TWO_PASS");
+  if (ctx->use_sweep) {
+    HYDOT_CUDA_TRY(ctx, cudaMalloc(&ctx->d_r2, iw * F * N));
+    HYDOT_CUDA_TRY(ctx, cudaMalloc(&ctx->d_cgsc, sizeof(double) * 4 * F));
+    HYDOT_CUDA_TRY(ctx, cudaMemset(ctx->d_cgsc, 0, sizeof(double) * 4 * F));
+  }
   if (ctx->use_tma) {
     int rc = roll_setup(ctx);
+    for (int d = 0; d < 2 && !rc && ctx->use_sweep; ++d) {
+      const int bz = 3 + d;
+      rc = encode_field_map(ctx, ctx->d_r, &ctx->tm_r2[d][0], BX2, BY2, bz);
+      if (!rc) rc = encode_field_map(ctx, ctx->d_r2, &ctx->tm_r2[d][1], BX2, BY2, bz);
+      if (!rc) rc = encode_field_map(ctx, ctx->d_p[0], &ctx->tm_p2[d][0], BX2, BY2, bz);
+      if (!rc) rc = encode_field_map(ctx, ctx->d_p[1], &ctx->tm_p2[d][1], BX2, BY2, bz);
+      if (!rc) rc = encode_field_map(ctx, ctx->d_e, &ctx->tm_e2[d], TX, TY, bz);
+    }
     // per slab depth (2, 4, 8 planes): halo slabs of r and p (pass 1 reads r and p_old, pass 2 reads
     // p_new), plain slabs of e and r
     for (int k = 0; k < 3 && !rc; ++k) {
@@ -2008,6 +2427,8 @@ int solver_alloc(hydot_ctx* ctx) {
 
 void solver_free(hydot_ctx* ctx) {
   cudaFree(ctx->d_x64);
+  cudaFree(ctx->d_r2);
+  cudaFree(ctx->d_cgsc);
   cudaFree(ctx->d_e);
   cudaFree(ctx->d_r);
   cudaFree(ctx->d_p[0]);
@@ -2087,7 +2508,7 @@ int set_absorption_impl(hydot_ctx* ctx, const double* dc) {
 int get_tuning_impl(const hydot_ctx* ctx, int* variant, int* planes, int* buffers, double* ns_per_cell) {
   if (variant) *variant = ctx->use_tma ? ctx->tune.variant : -1;
   for (int v = 0; v < HYDOT_ROLL_VARIANTS; ++v) {
-    const RollVariant& rv = ctx->cplx ? ROLL_VARIANTS_C[v] : ROLL_VARIANTS[v];
+    const RollVariant& rv = ctx->use_sweep ? SWEEP_VARIANTS[v] : (ctx->cplx ? ROLL_VARIANTS_C[v] : ROLL_VARIANTS[v]);
     if (planes) planes[v] = rv.rp;
     if (buffers) buffers[v] = rv.rs;
     if (ns_per_cell)

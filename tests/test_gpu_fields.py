@@ -285,7 +285,40 @@ def test_roll_variants_bitwise_identical_and_autotuner_settles(hd, oracle_fields
         tu = ctx.tuning()
     assert tu["variant"] in range(4)
     assert all(v["ns_per_cell"] > 0 for v in tu["variants"])
-    assert [(v["planes"], v["buffers"]) for v in tu["variants"]] == [(4, 4), (2, 6), (4, 3), (4, 5)]
+    # the single-sweep slab shapes {planes, buffers}
+    assert [(v["planes"], v["buffers"]) for v in tu["variants"]] == [(4, 3), (4, 4), (3, 4), (3, 5)]
+
+
+@pytest.mark.parametrize("name", ["tma-ragged-36x19x21", "tma-faces-40x16x9"])
+def test_single_sweep_and_two_pass_iterations_agree(hd, oracle_fields, monkeypatch, name):
+    """The single-sweep inner iteration (Chronopoulos-Gear recurrences, s = A p recomputed on a
+    two-cell ring) and the two-pass one are the same CG in exact arithmetic: both reach the oracle's
+    fields and Born rows to the stated tolerances, with Krylov iteration counts within a few per cent."""
+    p, (rs, rd) = oracle_fields[name]
+    stats = {}
+    for flag in ("0", "1"):
+        monkeypatch.setenv("HYDOT_TWO_PASS", flag)
+        with hd.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=1e-8, cw_floor=100.0) as ctx:
+            ps, pd, st = ctx.solve_fields(0, p.n_lambda)
+        assert st["n_not_converged"] == 0
+        assert rel_err(ps, rs) <= 1e-6 and rel_err(pd, rd) <= 1e-6
+        assert born_rowmax_err(p, ps, pd, rs, rd) <= 1e-5
+        stats[flag] = st
+    assert abs(stats["0"]["iters_mean"] - stats["1"]["iters_mean"]) <= 0.05 * stats["1"]["iters_mean"] + 2
+
+
+@pytest.mark.parametrize("seg", ["8", "16"])
+def test_z_segmented_blocks(hd, oracle_fields, monkeypatch, seg):
+    """Blocks that own a z-segment of a column instead of the whole column (segments of 8 or 16
+    planes over nz = 21: a ragged last segment; each segment reads two planes beyond both its ends)
+    reach the oracle's fields and Born rows to the same tolerances."""
+    p, (rs, rd) = oracle_fields["tma-ragged-36x19x21"]
+    monkeypatch.setenv("HYDOT_DIR_SEG", seg)
+    with hd.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=1e-8, cw_floor=100.0) as ctx:
+        ps, pd, st = ctx.solve_fields(0, p.n_lambda)
+    assert st["n_not_converged"] == 0
+    assert rel_err(ps, rs) <= 1e-6 and rel_err(pd, rd) <= 1e-6
+    assert born_rowmax_err(p, ps, pd, rs, rd) <= 1e-5
 
 
 def test_graph_replay_matches_direct_launches(hd, monkeypatch):
