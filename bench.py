@@ -766,8 +766,8 @@ def compare_iteration_forms(hd, p):
     import torch
 
     res = {}
-    for label, flag in (("single_sweep", "0"), ("two_pass", "1")):
-        os.environ["HYDOT_TWO_PASS"] = flag
+    for label, flag in (("single_sweep", "1"), ("two_pass", "0")):
+        os.environ["HYDOT_SINGLE_SWEEP"] = flag
         try:
             with hd.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=TOL_CW, cw_floor=CW_FLOOR,
                                          max_lambda_per_call=CHUNK) as c:
@@ -791,7 +791,7 @@ def compare_iteration_forms(hd, p):
                               "cg_iteration_gbs_at_6NW": gbs, "cg_iteration_hbm_frac": gbs / peaks()["hbm_gbs"] if gbs
                               else None, "autotune": c.tuning()}
         finally:
-            os.environ.pop("HYDOT_TWO_PASS", None)
+            os.environ.pop("HYDOT_SINGLE_SWEEP", None)
     res["speedup"] = res["single_sweep"]["solves_per_s"] / res["two_pass"]["solves_per_s"]
     return res
 

@@ -843,9 +843,12 @@ __global__ void __launch_bounds__(NTHREADS) k_update(Geo g, Batch b, int it, T* 
 constexpr int TZT = 8;               // planes per partial-sum tile on this path
 constexpr int BXT = 40, BYT = 10;    // x-y extent of a halo box
 
+// The dynamic shared-memory block rounded up to 128 bytes. The rounding is added to the __shared__
+// pointer itself (not done on an integer), so the compiler keeps the shared address space and the
+// slab accesses stay 32-bit shared-memory operations.
 template <typename E>
 __device__ __forceinline__ E* align128(unsigned char* p) {
-  return reinterpret_cast<E*>((reinterpret_cast<uintptr_t>(p) + 127) & ~uintptr_t(127));
+  return reinterpret_cast<E*>(p + ((128u - (smem_addr(p) & 127u)) & 127u));
 }
 
 __device__ __forceinline__ float diag_f(const LamCoefF& cf, int m) {
@@ -1529,42 +1532,53 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_cg_sweep(Geo g, Batch b, con
     col_diag(cf, (gi == 0) | ((gi == g.nx - 1) << 1) | ((gj == 0) << 2) | ((gj == g.ny - 1) << 3), h1d, h1di);
   }
   const int plane_n = g.nx * g.ny;
-  const size_t base = (size_t)rhs * g.N + (size_t)j * g.nx + i;
-  float* Rn = par ? R0 : R1;  // r_(k+1)
-  float* Pn = par ? P1 : P0;  // p_k (read back as p_(k-1) by iteration k + 1 from the other buffer)
+  // the column's cells in this field's part of e, r_(k+1) and p_k (offsets within a field fit 32 bits)
+  const size_t fbase = (size_t)rhs * g.N + (size_t)j * g.nx + i;
+  float* const eo = Eo + fbase;
+  float* const rn_out = (par ? R0 : R1) + fbase;  // r_(k+1)
+  float* const pn_out = (par ? P1 : P0) + fbase;  // p_k (read back as p_(k-1) from the other buffer)
   // z-queues: p of the own column and inner-ring cell (two planes back), u and r_(k+1) of the own column
   float pq2 = 0.f, pq1 = 0.f, hq2 = 0.f, hq1 = 0.f, uq2 = 0.f, uq1 = 0.f, rq1 = 0.f;
   float ag = 0.f, ad = 0.f, ar = 0.f;
   const float* prev = slab;
-  for (int q = 0; q < nslab; ++q) {
+  // One slab: (A), barrier, (B), barrier, (C). EDGE: a slab whose planes touch a grid z-face or
+  // lie outside the block's segment (per-plane checks, z-face diagonals); otherwise every plane of
+  // (A), (B) and (C) is an interior plane of the segment and the diagonals are the column's
+  // interior ones. Returns false when a TMA slab never arrived.
+  auto run_slab = [&](int q, auto edge_t) -> bool {
+    constexpr bool EDGE = decltype(edge_t)::value;
     float* cur = slab + (q % RS) * SLAB;
-    const bool ok = mbar_wait_bounded(&mbar[q % RS], (uint32_t)((q / RS) & 1));
+    // one lane per warp polls the slab's barrier; the warp's other lanes are ordered after it by
+    // __syncwarp (the copy's writes are visible to every thread that synchronises with the observer)
+    bool ok = true;
+    if ((threadIdx.x & 31) == 0) ok = mbar_wait_bounded(&mbar[q % RS], (uint32_t)((q / RS) & 1));
+    ok = __shfl_sync(0xffffffffu, (int)ok, 0) != 0;
+    __syncwarp();
     const int zA = z0 - 2 + q * RP;  // plane of (A)'s first slab plane
+    auto zcase = [&](int zt) { return EDGE ? ((zt == 0) | ((zt == g.nz - 1) << 1)) : 0; };
+    auto dsel = [&](const float (&v)[4], int zb) { return EDGE ? pick4(v, zb) : v[0]; };
     float pA[RP], hA[RP];
 #pragma unroll
     for (int u = 0; u < RP; ++u) pA[u] = hA[u] = 0.f;
     // (A) p_k = D^-1 r_k + beta p_(k-1) on the tile and both rings (zero outside the grid: r and
     // p arrive as zeros there)
     if (!PRIME) {
-      const bool edge = zA <= 0 || zA + RP - 1 >= g.nz - 1;
 #pragma unroll
       for (int u = 0; u < RP; ++u) {
-        const int zt = zA + u;
-        const int zb = edge ? ((zt == 0) | ((zt == g.nz - 1) << 1)) : 0;
+        const int zb = zcase(zA + u);
         float* rp = cur + u * PL2;
         float* pp = cur + RP * PL2 + u * PL2;
-        float v = rp[ob] * pick4(di, zb);
+        float v = rp[ob] * dsel(di, zb);
         if (!first) v = fmaf(beta, pp[ob], v);
         pp[ob] = v;
         pA[u] = v;
         if (has2) {
-          float hv = rp[h2b] * pick4(h2di, zb);
+          float hv = rp[h2b] * dsel(h2di, zb);
           if (!first) hv = fmaf(beta, pp[h2b], hv);
           pp[h2b] = hv;
         }
-        hA[u] = 0.f;
         if (has1) {
-          float hv = rp[h1b] * pick4(h1di, zb);
+          float hv = rp[h1b] * dsel(h1di, zb);
           if (!first) hv = fmaf(beta, pp[h1b], hv);
           pp[h1b] = hv;
           hA[u] = hv;
@@ -1577,7 +1591,7 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_cg_sweep(Geo g, Batch b, con
         const int last = min(max(RS - 1, q + RS - 3), nslab - 1);
         for (int u = q; u <= last; ++u) mbar_wait_bounded(&mbar[u % RS], (uint32_t)((u / RS) & 1));
       }
-      return;
+      return false;
     }
     // every thread is past (C) of slab q - 1, the last reader of slab q - 2: refill its buffer
     if (threadIdx.x == 0 && q >= 2 && q - 2 + RS < nslab) issue(q - 2 + RS);
@@ -1588,45 +1602,45 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_cg_sweep(Geo g, Batch b, con
       const int zt = zA - 1 + u;
       uB[u] = 0.f;
       rB[u] = 0.f;
-      if (zt < z0 - 1 || zt > z1) continue;  // not needed by (C)
-      const bool zin = zt >= 0 && zt < g.nz;
-      const int zb = (zt == 0) | ((zt == g.nz - 1) << 1);
+      if (EDGE && (zt < z0 - 1 || zt > z1)) continue;  // not needed by (C)
+      const bool zin = !EDGE || (zt >= 0 && zt < g.nz);
+      const int zb = zcase(zt);
       float* rpl = (u == 0) ? const_cast<float*>(prev) + (RP - 1) * PL2 : cur + (u - 1) * PL2;
       const float* ppl = rpl + RP * PL2;
       if (PRIME) {
         const float rv = rpl[ob];
-        const float uv = (in && zin) ? rv * pick4(di, zb) : 0.f;
+        const float uv = (in && zin) ? rv * dsel(di, zb) : 0.f;
         rpl[ob] = uv;
         uB[u] = uv;
         rB[u] = rv;
-        if (has1) rpl[h1b] = (h1in && zin) ? rpl[h1b] * pick4(h1di, zb) : 0.f;
+        if (has1) rpl[h1b] = (h1in && zin) ? rpl[h1b] * dsel(h1di, zb) : 0.f;
         continue;
       }
       {
         const float below = (u == 0) ? pq2 : (u == 1 ? pq1 : pA[u - 2]);
         const float centre = (u == 0) ? pq1 : pA[u - 1];
         const float sn = (ppl[ob - 1] + ppl[ob + 1]) + (ppl[ob - BX2] + ppl[ob + BX2]) + (below + pA[u]);
-        const float s = fmaf(pick4(dd, zb), centre, -sn);
+        const float s = fmaf(dsel(dd, zb), centre, -sn);
         const float rn = fmaf(-alpha, s, rpl[ob]);
-        const float uv = (in && zin) ? rn * pick4(di, zb) : 0.f;
+        const float uv = (in && zin) ? rn * dsel(di, zb) : 0.f;
         rpl[ob] = uv;
         uB[u] = uv;
         rB[u] = rn;
-        if (in && zt >= z0 && zt < z1) {
-          const float* epl = ((u == 0) ? prev + 2 * RP * PL2 + (RP - 1) * TPL : cur + 2 * RP * PL2 + (u - 1) * TPL);
-          const size_t id = base + (size_t)zt * plane_n;
-          Eo[id] = first ? alpha * centre : fmaf(alpha, centre, epl[threadIdx.x]);
-          Pn[id] = centre;
-          Rn[id] = rn;
+        if (in && (!EDGE || (zt >= z0 && zt < z1))) {
+          const float* epl = (u == 0) ? prev + 2 * RP * PL2 + (RP - 1) * TPL : cur + 2 * RP * PL2 + (u - 1) * TPL;
+          const int off = zt * plane_n;
+          eo[off] = first ? alpha * centre : fmaf(alpha, centre, epl[threadIdx.x]);
+          pn_out[off] = centre;
+          rn_out[off] = rn;
         }
       }
       if (has1) {
         const float below = (u == 0) ? hq2 : (u == 1 ? hq1 : hA[u - 2]);
         const float centre = (u == 0) ? hq1 : hA[u - 1];
         const float sn = (ppl[h1b - 1] + ppl[h1b + 1]) + (ppl[h1b - BX2] + ppl[h1b + BX2]) + (below + hA[u]);
-        const float s = fmaf(pick4(h1d, zb), centre, -sn);
+        const float s = fmaf(dsel(h1d, zb), centre, -sn);
         const float rn = fmaf(-alpha, s, rpl[h1b]);
-        rpl[h1b] = (h1in && zin) ? rn * pick4(h1di, zb) : 0.f;
+        rpl[h1b] = (h1in && zin) ? rn * dsel(h1di, zb) : 0.f;
       }
     }
     // the in-place writes are ordered before the copies that later refill these buffers
@@ -1637,14 +1651,14 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_cg_sweep(Geo g, Batch b, con
 #pragma unroll
       for (int u = 0; u < RP; ++u) {
         const int zt = zA - 2 + u;
-        if (zt < z0 || zt >= z1) continue;
-        const int zb = (zt == 0) | ((zt == g.nz - 1) << 1);
+        if (EDGE && (zt < z0 || zt >= z1)) continue;
+        const int zb = zcase(zt);
         const float* upl = (u <= 1) ? prev + (RP - 2 + u) * PL2 : cur + (u - 2) * PL2;
         const float below = (u == 0) ? uq2 : (u == 1 ? uq1 : uB[u - 2]);
         const float centre = (u == 0) ? uq1 : uB[u - 1];
         const float rn = (u == 0) ? rq1 : rB[u - 1];
         const float sn = (upl[ob - 1] + upl[ob + 1]) + (upl[ob - BX2] + upl[ob + BX2]) + (below + uB[u]);
-        const float w = fmaf(pick4(dd, zb), centre, -sn);
+        const float w = fmaf(dsel(dd, zb), centre, -sn);
         ag = fmaf(rn, centre, ag);
         ad = fmaf(w, centre, ad);
         ar = fmaf(rn, rn, ar);
@@ -1658,6 +1672,15 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_cg_sweep(Geo g, Batch b, con
     uq1 = uB[RP - 1];
     rq1 = rB[RP - 1];
     prev = cur;
+    return true;
+  };
+  for (int q = 0; q < nslab; ++q) {
+    const int zA = z0 - 2 + q * RP;
+    // interior: (A)'s planes zA .. zA+RP-1, (B)'s zA-1 .. zA+RP-2 and (C)'s zA-2 .. zA+RP-3 all
+    // inside the segment and away from the grid's z-faces
+    const bool interior = zA - 2 >= max(z0, 1) && zA + RP - 1 <= min(z1 - 1, g.nz - 2);
+    const bool ok = interior ? run_slab(q, std::false_type{}) : run_slab(q, std::true_type{});
+    if (!ok) return;
   }
   float a3[3] = {ag, ad, ar};
   double o3[3];
@@ -2381,8 +2404,9 @@ int solver_alloc(hydot_ctx* ctx) {
   HYDOT_CUDA_TRY(ctx, cudaMemset(ctx->d_it, 0, sizeof(int)));
   ctx->use_graphs = !getenv_flag("HYDOT_NO_GRAPHS");
   HYDOT_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
-  // real FP32 fields on the TMA path iterate in single sweeps (HYDOT_TWO_PASS=1: the two-pass form)
-  ctx->use_sweep = ctx->use_tma && !ctx->cplx && !getenv_flag("HYDOT_TWO_PASS");
+  // real FP32 fields on the TMA path: the two-pass iteration, or with HYDOT_SINGLE_SWEEP=1 the
+  // single-sweep one
+  ctx->use_sweep = ctx->use_tma && !ctx->cplx && getenv_flag("HYDOT_SINGLE_SWEEP");
   if (ctx->use_sweep) {
     HYDOT_CUDA_TRY(ctx, cudaMalloc(&ctx->d_r2, iw * F * N));
     HYDOT_CUDA_TRY(ctx, cudaMalloc(&ctx->d_cgsc, sizeof(double) * 4 * F));

@@ -263,9 +263,11 @@ def test_bitwise_repeatable(hd):
     assert torch.equal(a, c) and torch.equal(b, d)
 
 
-def test_roll_variants_bitwise_identical_and_autotuner_settles(hd, oracle_fields, monkeypatch):
-    """The slab shapes the autotuner chooses from give the same bits; an untuned context times the
-    variants on groups of inner iterations and then keeps one."""
+@pytest.mark.parametrize("sweep", ["0", "1"])
+def test_roll_variants_bitwise_identical_and_autotuner_settles(hd, oracle_fields, monkeypatch, sweep):
+    """The slab shapes the autotuner chooses from give the same bits (two-pass and single-sweep
+    forms); an untuned context times the variants on groups of inner iterations and then keeps one."""
+    monkeypatch.setenv("HYDOT_SINGLE_SWEEP", sweep)
     p = workloads.make_problem(workloads.Grid(64, 40, 36, 2.0), 4, 4, 4, seed=21, geometry="transmission")
     out = []
     for v in range(4):
@@ -285,8 +287,9 @@ def test_roll_variants_bitwise_identical_and_autotuner_settles(hd, oracle_fields
         tu = ctx.tuning()
     assert tu["variant"] in range(4)
     assert all(v["ns_per_cell"] > 0 for v in tu["variants"])
-    # the single-sweep slab shapes {planes, buffers}
-    assert [(v["planes"], v["buffers"]) for v in tu["variants"]] == [(4, 3), (4, 4), (3, 4), (3, 5)]
+    # slab shapes {planes, buffers} of the two-pass and the single-sweep forms
+    expect = [(4, 3), (4, 4), (3, 4), (3, 5)] if sweep == "1" else [(4, 4), (2, 6), (4, 3), (4, 5)]
+    assert [(v["planes"], v["buffers"]) for v in tu["variants"]] == expect
 
 
 @pytest.mark.parametrize("name", ["tma-ragged-36x19x21", "tma-faces-40x16x9"])
@@ -296,8 +299,8 @@ def test_single_sweep_and_two_pass_iterations_agree(hd, oracle_fields, monkeypat
     fields and Born rows to the stated tolerances, with Krylov iteration counts within a few per cent."""
     p, (rs, rd) = oracle_fields[name]
     stats = {}
-    for flag in ("0", "1"):
-        monkeypatch.setenv("HYDOT_TWO_PASS", flag)
+    for flag in ("1", "0"):
+        monkeypatch.setenv("HYDOT_SINGLE_SWEEP", flag)
         with hd.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=1e-8, cw_floor=100.0) as ctx:
             ps, pd, st = ctx.solve_fields(0, p.n_lambda)
         assert st["n_not_converged"] == 0
@@ -307,13 +310,15 @@ def test_single_sweep_and_two_pass_iterations_agree(hd, oracle_fields, monkeypat
     assert abs(stats["0"]["iters_mean"] - stats["1"]["iters_mean"]) <= 0.05 * stats["1"]["iters_mean"] + 2
 
 
+@pytest.mark.parametrize("sweep", ["0", "1"])
 @pytest.mark.parametrize("seg", ["8", "16"])
-def test_z_segmented_blocks(hd, oracle_fields, monkeypatch, seg):
+def test_z_segmented_blocks(hd, oracle_fields, monkeypatch, seg, sweep):
     """Blocks that own a z-segment of a column instead of the whole column (segments of 8 or 16
     planes over nz = 21: a ragged last segment; each segment reads two planes beyond both its ends)
     reach the oracle's fields and Born rows to the same tolerances."""
     p, (rs, rd) = oracle_fields["tma-ragged-36x19x21"]
     monkeypatch.setenv("HYDOT_DIR_SEG", seg)
+    monkeypatch.setenv("HYDOT_SINGLE_SWEEP", sweep)
     with hd.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=1e-8, cw_floor=100.0) as ctx:
         ps, pd, st = ctx.solve_fields(0, p.n_lambda)
     assert st["n_not_converged"] == 0
