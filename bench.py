@@ -55,10 +55,13 @@ KERNEL_NAMES = {"iter": "inner CG iteration (every pass of one Krylov iteration;
                 "sketch_project": "k_project_ws (tensor-core B^T += J^T Q)"}
 # DRAM bytes (read + write, ncu) per algorithmic byte, from the captures summarised under profiles/
 # (smaller cases of the same kernels, scaled by the units processed: active fields or rows). The
-# CG iteration's entry is filled from a capture whose working set exceeds L2; None until then.
-DRAM_PER_ALGORITHMIC_BYTE = {"iter": None,
+# CG iteration's (two-pass form, the default): k_dir_roll + k_update_roll on 256 fields, a 1.4 GB
+# working set (eleven times L2), per 24 B algorithmic bytes per cell-iteration.
+DRAM_PER_ALGORITHMIC_BYTE = {"iter": (403.75e6 + 174.34e6 + 604.92e6 + 345.27e6) / (256 * 196608 * 24),
                              "born_rows": (893.83e6 + 12.96e9) / (4096 * 4 * 196608 * 4)}
-TRAFFIC_NOTE = {"iter": None,
+TRAFFIC_NOTE = {"iter": "ncu on one two-pass iteration over 256 active fields (1.4 GB of vectors, profiles/"
+                        "cg_iteration_256fields_64x64x48.md), scaled by active fields: the 32 B per cell the "
+                        "two passes move against the 24 B algorithmic",
                 "born_rows": "ncu on a full 4,096-row launch of the benchmark (profiles/k_born_rows_4096rows.md)"}
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
 
@@ -348,7 +351,7 @@ def run_ours(args):
                    "cycles_max": max(s["cycles_max"] for s in stats),
                    "resid_max": max(s["resid_max"] for s in stats), "cw_max": max(s["cw_max"] for s in stats),
                    "hbm_gbs_at_6NW_per_iteration": solver_gbs, "hbm_frac": solver_gbs / pk["hbm_gbs"],
-                   "autotune": ctx.tuning()},
+                   "autotune": ctx.tuning(), "launch_form": ctx.launch_mode()},
         # every counted solve meets the metric's 1e-6 field error: |phi - phi*| / |phi*| <= kappa |r| / |b|,
         # kappa(Ahat) <= (12 + max sigma) / min sigma (the Laplacian and boundary part is positive
         # semidefinite, Gershgorin bounds the largest eigenvalue), |r| / |b| the largest final FP64
@@ -768,6 +771,7 @@ def compare_iteration_forms(hd, p):
     res = {}
     for label, flag in (("single_sweep", "1"), ("two_pass", "0")):
         os.environ["HYDOT_SINGLE_SWEEP"] = flag
+        os.environ["HYDOT_PERSISTENT"] = "0"  # launched iterations in both arms
         try:
             with hd.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=TOL_CW, cw_floor=CW_FLOOR,
                                          max_lambda_per_call=CHUNK) as c:
@@ -792,6 +796,7 @@ def compare_iteration_forms(hd, p):
                               else None, "autotune": c.tuning()}
         finally:
             os.environ.pop("HYDOT_SINGLE_SWEEP", None)
+            os.environ.pop("HYDOT_PERSISTENT", None)
     res["speedup"] = res["single_sweep"]["solves_per_s"] / res["two_pass"]["solves_per_s"]
     return res
 
@@ -851,39 +856,52 @@ def compare_shift_guess(hd, p, m):
 
 
 def compare_graphs(hd, p):
-    """Field solves/s with groups of inner iterations replayed from a CUDA graph against direct
-    launches, on the benchmark chunk and on a small problem (config-1 grid, 16 wavelengths, FP32
-    inner) where launch cost matters; kernel timing is off, the autotuned variant is kept."""
-    import os
+    """Field solves/s of the inner-solve forms: one persistent cooperative launch per refinement
+    cycle (single sweeps, device-side convergence), launched single sweeps and launched two-pass
+    iterations replayed from a CUDA graph in groups of 8, and direct two-pass launches; on the
+    benchmark chunk and on the 24x24x16 reflection workload (256 fields, FP32 inner with
+    refinement) where launch cost matters. Kernel timing is off; each form is fixed by its
+    environment switches, the slab variant autotuned; a single-sweep context whose launch-form tuner
+    picks launched or persistent by itself is reported too."""
     import torch
     import workloads
 
     small = workloads.config(1)
     cases = {"cw-mixed-64x64x48 chunk (1,024 fields)": (p, CHUNK),
              "24x24x16 grid, 16 wavelengths (256 fields)": (small, small.n_lambda)}
+    forms = (("persistent", {"HYDOT_PERSISTENT": "1"}),
+             ("graph_sweep", {"HYDOT_PERSISTENT": "0", "HYDOT_SINGLE_SWEEP": "1"}),
+             ("graph", {"HYDOT_SINGLE_SWEEP": "0"}),
+             ("direct", {"HYDOT_SINGLE_SWEEP": "0", "HYDOT_NO_GRAPHS": "1"}),
+             ("tuned_sweep", {"HYDOT_SINGLE_SWEEP": "1"}))
     res = {}
     for name, (prob, nl) in cases.items():
         row = {}
-        for label, flag in (("graph", "0"), ("direct", "1")):
-            os.environ["HYDOT_NO_GRAPHS"] = flag
+        for label, env in forms:
+            os.environ.update(env)
             try:
                 with hd.Context.from_problem(prob, precision="mixed", tol=1e-10, tol_cw=TOL_CW, cw_floor=CW_FLOOR,
                                              max_lambda_per_call=nl) as c:
-                    for _ in range(3):
-                        c.solve_fields(0, nl)  # autotuning settles, graph captured
+                    for _ in range(4):
+                        c.solve_fields(0, nl)  # slab variant and launch form settle, graph captured
                     torch.cuda.synchronize()
                     a = torch.cuda.Event(enable_timing=True)
                     b = torch.cuda.Event(enable_timing=True)
-                    reps = 2
+                    reps = 3
                     a.record()
                     for _ in range(reps):
                         c.solve_fields(0, nl)
                     b.record()
                     torch.cuda.synchronize()
                     row[label] = (prob.n_src + prob.n_det) * nl * reps / (a.elapsed_time(b) / 1e3)
+                    if label == "tuned_sweep":
+                        row["tuned_form"] = c.launch_mode()
+                    row[f"{label}_call_ms"] = a.elapsed_time(b) / reps
             finally:
-                os.environ.pop("HYDOT_NO_GRAPHS", None)
-        row["speedup"] = row["graph"] / row["direct"]
+                for k in env:
+                    os.environ.pop(k, None)
+        row["graph_over_direct"] = row["graph"] / row["direct"]
+        row["persistent_over_graph"] = row["persistent"] / row["graph"]
         res[name] = row
     return res
 

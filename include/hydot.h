@@ -232,6 +232,21 @@ int hydot_set_kernel_timing(hydot_ctx* ctx, int on);
  * pointer may be NULL. */
 int hydot_kernel_stats(hydot_ctx* ctx, int kernel, double* ms, long long* launches, double* bytes);
 
+/* Iteration and launch form of the inner solves (HYDOT_MIXED, real fields, nx % 4 == 0). An inner
+ * CG iteration is either two passes over memory (the default) or one sweep (the Chronopoulos-Gear
+ * recurrences: both inner products of an iteration from one pass; the environment variable
+ * HYDOT_SINGLE_SWEEP=1 at hydot_setup selects it). With single sweeps a refinement
+ * cycle's iterations run either launched (groups of 8 replayed from a CUDA graph, the host polling
+ * one word per group) or as one persistent cooperative launch: co-resident blocks iterate over
+ * (field, column) work items with a grid-wide barrier after each iteration and stop on the device
+ * when no field is still iterating (every barrier wait is bounded: one that runs out ends the call
+ * with HYDOT_ERR_TIMEOUT). Both do the same arithmetic (the same bits). While *mode is -1 the solver
+ * times whole cycles in each, per active cell-iteration, and then keeps the faster (1: persistent,
+ * 0: launched; always 0 with two-pass iterations); HYDOT_PERSISTENT=0 or 1 at hydot_setup fixes
+ * the choice (1 also selects single sweeps). ns_launched / ns_persistent: measured ns per cell-iteration (0 if not timed). Any
+ * output pointer may be NULL. */
+int hydot_get_launch_mode(const hydot_ctx* ctx, int* mode, double* ns_launched, double* ns_persistent);
+
 /* Inner iterations of the rolling passes replay a CUDA graph per group of 8 iterations when on
  * != 0 (the default, unless the environment variable HYDOT_NO_GRAPHS was set at hydot_setup);
  * with on == 0 every pass is launched directly, which lets the instrumentation time each pass on
@@ -341,11 +356,13 @@ int hydot_pals_project(hydot_ctx* ctx, const float* V, long long ldV, int rank, 
 int hydot_shape_compare(hydot_ctx* ctx, const float* mu, const float* mu_hat, double level, double* rel_l2,
                         double* dice);
 
-/* Failure-path self-test (no counterpart in the paper): one thread waits on a shared-memory
- * mbarrier that nothing arrives at, through the same bounded poll loop the pipelined kernels use
- * for their TMA and tensor-core waits, but with `polls` polls (1..2^22) instead of their limit;
- * it raises the device error flag and returns. The call returns HYDOT_ERR_TIMEOUT with a message,
- * and the context stays usable (the flag is cleared). Synchronises the stream. */
+/* Failure-path self-test (no counterpart in the paper), with `polls` polls (1..2^22) per wait
+ * instead of the kernels' own limits: (1) one thread waits on a shared-memory mbarrier that nothing
+ * arrives at, through the bounded poll loop the pipelined kernels use for their TMA and
+ * tensor-core waits; (2) in a cooperative launch of two blocks only one arrives at the grid barrier
+ * of the persistent inner solve, so its bounded wait runs out. Each raises the device error flag
+ * and returns. The call returns HYDOT_ERR_TIMEOUT when both waits gave up (HYDOT_ERR_STATE if one
+ * did not), and the context stays usable (the flag is cleared). Synchronises the stream. */
 int hydot_wait_selftest(hydot_ctx* ctx, int polls);
 
 /* Randomised sketch of J, pass 1 (Appendix A.1, alg:randsvd: Y = A Omega with Gaussian Omega):

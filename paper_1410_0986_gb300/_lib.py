@@ -27,7 +27,7 @@ EXPORTS = ("hydot_version", "hydot_setup", "hydot_set_stream", "hydot_solve_fiel
            "hydot_born_assemble",
            "hydot_born_apply", "hydot_born_apply_T", "hydot_born_apply_noalloc", "hydot_sketch_range",
            "hydot_sketch_project", "hydot_sketch_orthonormalize", "hydot_sketch_rank", "hydot_sketch_merge",
-           "hydot_sketch_factor", "hydot_set_kernel_timing", "hydot_set_graphs",
+           "hydot_sketch_factor", "hydot_set_kernel_timing", "hydot_set_graphs", "hydot_get_launch_mode",
            "hydot_kernel_stats", "hydot_kernel_launches", "hydot_get_tuning", "hydot_set_absorption",
            "hydot_wait_selftest", "hydot_set_shift_guess", "hydot_shift_guess_fields",
            "hydot_pals_reconstruct", "hydot_pals_shape", "hydot_pals_project", "hydot_shape_compare",
@@ -93,6 +93,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.hydot_version.restype = C.c_int
     lib.hydot_set_graphs.argtypes = [vp, C.c_int]
     lib.hydot_set_graphs.restype = C.c_int
+    lib.hydot_get_launch_mode.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    lib.hydot_get_launch_mode.restype = C.c_int
     lib.hydot_setup.argtypes = [C.POINTER(Problem), vp, C.POINTER(vp)]
     lib.hydot_setup.restype = C.c_int
     lib.hydot_set_stream.argtypes = [vp, vp]

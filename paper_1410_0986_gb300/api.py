@@ -265,6 +265,13 @@ class Context:
         """Record CUDA events around the hot kernels from now on (resets the totals)."""
         self._check(self.lib.hydot_set_kernel_timing(self._ctx, 1 if on else 0))
 
+    def launch_mode(self) -> dict:
+        """Launch form of the inner solves: mode -1 while the tuner compares them, 0 launched
+        iterations (graph replay), 1 one persistent launch per cycle; measured ns per cell-iteration."""
+        m, a, b = C.c_int(0), C.c_double(0), C.c_double(0)
+        self._check(self.lib.hydot_get_launch_mode(self._ctx, C.byref(m), C.byref(a), C.byref(b)))
+        return {"mode": m.value, "ns_per_cell_launched": a.value, "ns_per_cell_persistent": b.value}
+
     def set_graphs(self, on: bool = True):
         """Replay groups of inner iterations from a CUDA graph (default) or launch every pass
         directly (each pass then gets its own events under set_kernel_timing)."""

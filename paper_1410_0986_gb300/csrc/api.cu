@@ -516,6 +516,13 @@ int hydot_set_kernel_timing(hydot_ctx* ctx, int on) {
   });
 }
 
+int hydot_get_launch_mode(const hydot_ctx* ctx, int* mode, double* ns_launched, double* ns_persistent) {
+  return hydot::abi_guard(ctx, [&]() -> int {
+    if (!ctx) return HYDOT_ERR_ARG;
+    return hydot::get_launch_mode_impl(ctx, mode, ns_launched, ns_persistent);
+  });
+}
+
 int hydot_set_graphs(hydot_ctx* ctx, int on) {
   return hydot::abi_guard(ctx, [&]() -> int {
     if (!ctx) return HYDOT_ERR_ARG;

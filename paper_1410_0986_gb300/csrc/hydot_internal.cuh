@@ -253,7 +253,18 @@ struct hydot_ctx {
   // per-field scalars {gamma, alpha} per parity [2][max_fields][2], and maps per slab depth 3, 4:
   // r (both buffers) and p (both) in boxes of the tile plus a two-cell ring (40 x 12 x depth), e in
   // boxes of the tile
-  bool use_sweep = false;
+  bool sweep_ok = false;   // single-sweep resources allocated (real FP32 fields on the TMA path)
+  bool use_sweep = false;  // launched iterations use the single-sweep form (else the two passes)
+  // persistent form of a cycle's inner solve: mode -1 while the tuner compares it with launched
+  // iterations (ms per active cell-iteration, per mode), then 0 (launched) or 1 (persistent)
+  struct {
+    int mode = -1;
+    int samples[2] = {0, 0};
+    double ms[2] = {0.0, 0.0};
+    double cells[2] = {0.0, 0.0};
+  } persist;
+  unsigned* d_gsync = nullptr;  // grid barrier words {count, generation}
+  int persist_blocks = 0;       // co-resident blocks of the persistent kernel (whole GPU)
   void* d_r2 = nullptr;
   double* d_cgsc = nullptr;
   CUtensorMap tm_r2[2][2]{}, tm_p2[2][2]{}, tm_e2[2]{};
@@ -337,6 +348,7 @@ cudaError_t raise_smem_limit(F* func, size_t bytes) {
 int solve_fields_impl(hydot_ctx* ctx, int lam0, int nlam, void* phi_src, void* phi_det, hydot_stats* st);
 int get_tuning_impl(const hydot_ctx* ctx, int* variant, int* planes, int* buffers, double* ns_per_cell);
 int wait_selftest_impl(hydot_ctx* ctx, int polls);
+int get_launch_mode_impl(const hydot_ctx* ctx, int* mode, double* ns_launched, double* ns_persistent);
 int set_absorption_impl(hydot_ctx* ctx, const double* dc);
 int solver_alloc(hydot_ctx* ctx);
 void solver_free(hydot_ctx* ctx);

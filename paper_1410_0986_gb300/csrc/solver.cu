@@ -1389,31 +1389,35 @@ struct SweepScalars {
   int stride; // fields per parity
 };
 
-template <int RP, int RS, int MINB, bool PRIME>
-__global__ void __launch_bounds__(NTHREADS, MINB) k_cg_sweep(Geo g, Batch b, const int* __restrict__ it_dev, int k,
-                                                             int seg, const LamCoefF* __restrict__ coef_f,
-                                                             SweepScalars sc,
-                                                             const __grid_constant__ CUtensorMap mapR0,
-                                                             const __grid_constant__ CUtensorMap mapR1,
-                                                             const __grid_constant__ CUtensorMap mapP0,
-                                                             const __grid_constant__ CUtensorMap mapP1,
-                                                             const __grid_constant__ CUtensorMap mapE,
-                                                             float* __restrict__ R0, float* __restrict__ R1,
-                                                             float* __restrict__ P0, float* __restrict__ P1,
-                                                             float* __restrict__ Eo) {
+// Shared scalars and barriers of one block of the single-sweep iteration.
+template <int RS>
+struct SweepShared {
+  uint64_t mbar[RS];
+  double sm[96];
+  float beta, alpha;
+  int go, st;
+};
+
+// One work item of the single-sweep iteration: the (field, x-y column, z-segment) `item` at inner
+// iteration `it` (or the cycle's priming pass). Run by all threads of a block; slab is the block's
+// dynamic shared memory rounded to 128 bytes. Returns false when a TMA slab never arrived (the
+// device error flag is then set and the copies issued so far have been waited for).
+template <int RP, int RS, bool PRIME>
+__device__ __forceinline__ bool sweep_item(const Geo& g, const Batch& b, const int it, const int item, const int seg,
+                                           const LamCoefF* __restrict__ coef_f, const SweepScalars& sc,
+                                           const CUtensorMap* mapR0, const CUtensorMap* mapR1,
+                                           const CUtensorMap* mapP0, const CUtensorMap* mapP1,
+                                           const CUtensorMap* mapE, float* __restrict__ R0, float* __restrict__ R1,
+                                           float* __restrict__ P0, float* __restrict__ P1, float* __restrict__ Eo,
+                                           float* slab, SweepShared<RS>& sh) {
   static_assert(RP >= 3 && RS >= 3, "stage C reads u one slab back; a buffer is refilled two slabs after its own");
-  extern __shared__ unsigned char dsm[];
-  float* slab = align128<float>(dsm);  // [RS][r -> u: RP planes][p: RP planes][e: RP tile planes]
   constexpr int SLAB = 2 * RP * PL2 + RP * TPL;  // floats per slab buffer
-  __shared__ uint64_t mbar[RS];
-  __shared__ double sm[96];
-  __shared__ float s_beta, s_alpha;
-  __shared__ int s_go, s_st;
-  const int it = PRIME ? 0 : *it_dev + k;
+  uint64_t* mbar = sh.mbar;
+  double* sm = sh.sm;
   const int ncol = g.ntx * g.nty;
   const int nseg = (g.nz + seg - 1) / seg;
-  const int rhs = blockIdx.x / (ncol * nseg);
-  const int rem = blockIdx.x - rhs * ncol * nseg;
+  const int rhs = item / (ncol * nseg);
+  const int rem = item - rhs * ncol * nseg;
   const int zs = rem / ncol, col = rem - zs * ncol;
   const int x0 = (col % g.ntx) * TX, y0 = (col / g.ntx) * TY;
   const int z0 = zs * seg, z1 = min(z0 + seg, g.nz);
@@ -1425,8 +1429,8 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_cg_sweep(Geo g, Batch b, con
   const int np = z1 - z0 + 4;  // planes z0-2 .. z1+1 (t = plane - (z0 - 2))
   const int nslab = (np + RP - 1) / RP;
   const int nfirst = min(RS, nslab);
-  const CUtensorMap* mr = par ? &mapR1 : &mapR0;
-  const CUtensorMap* mp = par ? &mapP0 : &mapP1;  // p_(k-1) was written by iteration k-1 into P[k & 1 ^ 1]
+  const CUtensorMap* mr = par ? mapR1 : mapR0;
+  const CUtensorMap* mp = par ? mapP0 : mapP1;  // p_(k-1) was written by iteration k-1 into P[k & 1 ^ 1]
   const uint32_t tx_bytes = first ? RP * PL2 * 4u : (2u * RP * PL2 + RP * TPL) * 4u;
   auto issue = [&](int q) {
     float* dst = slab + (q % RS) * SLAB;
@@ -1435,12 +1439,13 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_cg_sweep(Geo g, Batch b, con
     tma_load_4d(dst, mr, &mbar[q % RS], x0 - 4, y0 - 2, zq, rhs);
     if (!first) {
       tma_load_4d(dst + RP * PL2, mp, &mbar[q % RS], x0 - 4, y0 - 2, zq, rhs);
-      tma_load_4d(dst + 2 * RP * PL2, &mapE, &mbar[q % RS], x0, y0, zq, rhs);
+      tma_load_4d(dst + 2 * RP * PL2, mapE, &mbar[q % RS], x0, y0, zq, rhs);
     }
   };
+  __syncthreads();  // the previous item's threads are done with the barriers re-initialised below
   if (threadIdx.x == 0) {
     const int st = b.status[rhs];
-    s_st = st;
+    sh.st = st;
     if (st == RHS_INNER) {
       for (int q = 0; q < RS; ++q) mbar_init(&mbar[q], 1);
       mbar_fence_init();
@@ -1448,7 +1453,7 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_cg_sweep(Geo g, Batch b, con
     }
   }
   __syncthreads();
-  if (s_st != RHS_INNER) return;
+  if (sh.st != RHS_INNER) return true;
   if (!PRIME) {
     if (threadIdx.x < 32) {
       double vg = 0.0, vd = 0.0, vr = 0.0;
@@ -1483,24 +1488,24 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_cg_sweep(Geo g, Batch b, con
           cur[1] = alpha;
           atomicAdd(&b.counter[1 + it], 1);
         }
-        s_go = done ? 0 : 1;
-        s_alpha = (float)alpha;
-        s_beta = (float)beta;
+        sh.go = done ? 0 : 1;
+        sh.alpha = (float)alpha;
+        sh.beta = (float)beta;
       }
     }
   } else if (threadIdx.x == 0) {
-    s_go = 1;
-    s_alpha = 0.f;
-    s_beta = 0.f;
+    sh.go = 1;
+    sh.alpha = 0.f;
+    sh.beta = 0.f;
   }
   const LamCoefF cf = coef_f[rhs_lambda(b, rhs)];
   __syncthreads();
-  if (!s_go) {
+  if (!sh.go) {
     if (threadIdx.x == 0)
       for (int q = 0; q < nfirst; ++q) mbar_wait_bounded(&mbar[q % RS], 0u);
-    return;
+    return true;
   }
-  const float alpha = s_alpha, beta = s_beta;
+  const float alpha = sh.alpha, beta = sh.beta;
 
   // own column
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
@@ -1680,7 +1685,7 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_cg_sweep(Geo g, Batch b, con
     // inside the segment and away from the grid's z-faces
     const bool interior = zA - 2 >= max(z0, 1) && zA + RP - 1 <= min(z1 - 1, g.nz - 2);
     const bool ok = interior ? run_slab(q, std::false_type{}) : run_slab(q, std::true_type{});
-    if (!ok) return;
+    if (!ok) return false;
   }
   float a3[3] = {ag, ad, ar};
   double o3[3];
@@ -1695,6 +1700,109 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_cg_sweep(Geo g, Batch b, con
     pb[4 * T_ + T_ * npar + slot] = z ? o3[2] : 0.0;
     if (!PRIME && z && lead) b.iters[rhs] += 1;
   }
+  return true;
+}
+
+
+template <int RP, int RS, int MINB, bool PRIME>
+__global__ void __launch_bounds__(NTHREADS, MINB) k_cg_sweep(Geo g, Batch b, const int* __restrict__ it_dev, int k,
+                                                             int seg, const LamCoefF* __restrict__ coef_f,
+                                                             SweepScalars sc,
+                                                             const __grid_constant__ CUtensorMap mapR0,
+                                                             const __grid_constant__ CUtensorMap mapR1,
+                                                             const __grid_constant__ CUtensorMap mapP0,
+                                                             const __grid_constant__ CUtensorMap mapP1,
+                                                             const __grid_constant__ CUtensorMap mapE,
+                                                             float* __restrict__ R0, float* __restrict__ R1,
+                                                             float* __restrict__ P0, float* __restrict__ P1,
+                                                             float* __restrict__ Eo) {
+  extern __shared__ unsigned char dsm[];
+  __shared__ SweepShared<RS> sh;
+  const int it = PRIME ? 0 : *it_dev + k;
+  sweep_item<RP, RS, PRIME>(g, b, it, blockIdx.x, seg, coef_f, sc, &mapR0, &mapR1, &mapP0, &mapP1, &mapE, R0, R1,
+                            P0, P1, Eo, align128<float>(dsm), sh);
+}
+
+// Grid-wide barrier of the persistent iteration (its blocks are co-resident: cooperative launch).
+// Arrivals count up; the last arrival resets the count and advances the generation the others
+// poll. Every wait is bounded: a block that gives up raises the device error flag and returns false
+// (the kernel then ends; blocks still waiting for it give up in turn), so no launch can hang.
+struct GridSync {
+  unsigned* count;
+  unsigned* gen;
+  uint32_t polls;  // bound on the polls of one wait (64 ns pauses between polls)
+};
+
+__device__ __forceinline__ bool grid_sync(const GridSync& gs, int* err) {
+  __shared__ int s_ok;
+  // this block's global writes (fields, partials, per-field scalars) are ordered before the
+  // arrival, also for the TMA (async-proxy) reads of the next iteration
+  asm volatile("fence.proxy.async;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned g0 = *(volatile unsigned*)gs.gen;
+    bool ok = true;
+    if (atomicAdd(gs.count, 1u) == gridDim.x - 1) {
+      *(volatile unsigned*)gs.count = 0u;
+      __threadfence();
+      atomicAdd(gs.gen, 1u);
+    } else {
+      uint32_t n = 0;
+      while (*(volatile unsigned*)gs.gen == g0) {
+        if (++n > gs.polls) {
+          ok = false;
+          atomicExch(err, 1);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    asm volatile("fence.proxy.async;" ::: "memory");
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Persistent form of one refinement cycle's inner solve (small batches, where per-iteration launch
+// and polling latency matter): one cooperative launch of co-resident blocks runs the priming pass
+// and then the single-sweep iterations, each block taking work items (field, column, segment)
+// in turn, with a grid barrier after every pass. The iteration stops on the device once an
+// iteration finds no field still iterating (per-field convergence as in the launched form) or at
+// the per-cycle cap. Block 0 writes the number of iterations run to *it_out. A wait that gives up
+// ends the launch with the device error flag set.
+template <int RP, int RS, int MINB>
+__global__ void __launch_bounds__(NTHREADS, MINB) k_cg_persist(Geo g, Batch b, int seg,
+                                                               const LamCoefF* __restrict__ coef_f, SweepScalars sc,
+                                                               const __grid_constant__ CUtensorMap mapR0,
+                                                               const __grid_constant__ CUtensorMap mapR1,
+                                                               const __grid_constant__ CUtensorMap mapP0,
+                                                               const __grid_constant__ CUtensorMap mapP1,
+                                                               const __grid_constant__ CUtensorMap mapE,
+                                                               float* __restrict__ R0, float* __restrict__ R1,
+                                                               float* __restrict__ P0, float* __restrict__ P1,
+                                                               float* __restrict__ Eo, GridSync gs, int nitems,
+                                                               int* __restrict__ it_out) {
+  extern __shared__ unsigned char dsm[];
+  __shared__ SweepShared<RS> sh;
+  float* slab = align128<float>(dsm);
+  for (int w = blockIdx.x; w < nitems; w += gridDim.x)
+    if (!sweep_item<RP, RS, true>(g, b, 0, w, seg, coef_f, sc, &mapR0, &mapR1, &mapP0, &mapP1, &mapE, R0, R1, P0,
+                                  P1, Eo, slab, sh))
+      return;
+  if (!grid_sync(gs, b.err)) return;
+  int it = 0;
+  for (; it < b.max_inner; ++it) {
+    for (int w = blockIdx.x; w < nitems; w += gridDim.x)
+      if (!sweep_item<RP, RS, false>(g, b, it, w, seg, coef_f, sc, &mapR0, &mapR1, &mapP0, &mapP1, &mapE, R0, R1,
+                                     P0, P1, Eo, slab, sh))
+        return;
+    if (!grid_sync(gs, b.err)) return;
+    if (*(volatile int*)&b.counter[1 + it] == 0) break;  // no field iterated: every one has finished
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *it_out = min(it + 1, b.max_inner);
 }
 
 // ---------------------------------------------------------------- fold, output
@@ -1870,6 +1978,68 @@ void sweep_launch(hydot_ctx* ctx, const Geo& g, const Batch& b, int k_off, unsig
       (float*)ctx->d_e);
   ++ctx->launches;
   timer_end(ctx, t0, PRIME ? HYDOT_KERNEL_PRIME : HYDOT_KERNEL_SWEEP, 0.0);
+}
+
+// The persistent kernel runs the {3 planes, 4 buffers} slabs (58 KB: three blocks per SM).
+constexpr int PERSIST_RP = 3, PERSIST_RS = 4, PERSIST_MB = 3;
+constexpr uint32_t GRID_WAIT_POLLS = 1u << 24;  // about a second of 64 ns pauses per grid barrier
+
+int persist_setup(hydot_ctx* ctx) {
+  auto kern = k_cg_persist<PERSIST_RP, PERSIST_RS, PERSIST_MB>;
+  const size_t smem = sw_smem<PERSIST_RP, PERSIST_RS>();
+  HYDOT_CUDA_TRY(ctx, raise_smem_limit(kern, smem));
+  int per_sm = 0, sms = 0, coop = 0;
+  HYDOT_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NTHREADS, smem));
+  HYDOT_CUDA_TRY(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+  HYDOT_CUDA_TRY(ctx, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device));
+  ctx->persist_blocks = coop ? per_sm * sms : 0;
+  if (ctx->persist_blocks <= 0) ctx->persist.mode = 0;  // no co-resident launch possible: launched only
+  HYDOT_CUDA_TRY(ctx, cudaMalloc(&ctx->d_gsync, 2 * sizeof(unsigned)));
+  HYDOT_CUDA_TRY(ctx, cudaMemset(ctx->d_gsync, 0, 2 * sizeof(unsigned)));
+  return HYDOT_OK;
+}
+
+// One cooperative launch for the whole inner solve of a cycle; returns the iterations it ran in *iters.
+int persist_launch(hydot_ctx* ctx, const Geo& g, const Batch& b, unsigned nitems, int* iters) {
+  const int d = sw_index(PERSIST_RP);
+  SweepScalars sc{ctx->d_cgsc, ctx->max_fields};
+  GridSync gs{ctx->d_gsync, ctx->d_gsync + 1, GRID_WAIT_POLLS};
+  int seg = ctx->dir_seg;
+  int ni = (int)nitems;
+  int* it_out = ctx->d_it;
+  float* r0 = (float*)ctx->d_r;
+  float* r1 = (float*)ctx->d_r2;
+  float* p0 = (float*)ctx->d_p[0];
+  float* p1 = (float*)ctx->d_p[1];
+  float* e = (float*)ctx->d_e;
+  Geo gg = g;
+  Batch bb = b;
+  const LamCoefF* cf = ctx->d_coef_f;
+  void* args[] = {&gg, &bb, &seg, &cf, &sc, &ctx->tm_r2[d][0], &ctx->tm_r2[d][1], &ctx->tm_p2[d][0],
+                  &ctx->tm_p2[d][1], &ctx->tm_e2[d], &r0, &r1, &p0, &p1, &e, &gs, &ni, &it_out};
+  const unsigned grid = std::min<unsigned>(nitems, (unsigned)ctx->persist_blocks);
+  HYDOT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_gsync, 0, 2 * sizeof(unsigned), ctx->stream));
+  HYDOT_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((const void*)k_cg_persist<PERSIST_RP, PERSIST_RS, PERSIST_MB>,
+                                                  dim3(grid), dim3(NTHREADS), args,
+                                                  sw_smem<PERSIST_RP, PERSIST_RS>(), ctx->stream));
+  ++ctx->launches;
+  HYDOT_CUDA_TRY(ctx, cudaMemcpyAsync(iters, ctx->d_it, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  HYDOT_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  return HYDOT_OK;
+}
+
+// Mode of the next cycle's inner solve: the chosen one, else (tuning) the mode with fewer samples.
+int persist_pick(const hydot_ctx* ctx) {
+  if (ctx->persist.mode >= 0) return ctx->persist.mode;
+  return ctx->persist.samples[1] < ctx->persist.samples[0] ? 1 : 0;
+}
+void persist_record(hydot_ctx* ctx, int mode, double ms, double cell_iters) {
+  if (ctx->persist.mode >= 0 || cell_iters <= 0.0) return;
+  ctx->persist.ms[mode] += ms;
+  ctx->persist.cells[mode] += cell_iters;
+  ctx->persist.samples[mode] += 1;
+  if (ctx->persist.samples[0] >= 2 && ctx->persist.samples[1] >= 2)
+    ctx->persist.mode = (ctx->persist.ms[1] / ctx->persist.cells[1] < ctx->persist.ms[0] / ctx->persist.cells[0]) ? 1 : 0;
 }
 
 template <bool PRIME>
@@ -2181,13 +2351,29 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
     const unsigned nrb =
         roll ? (unsigned)((long long)b.nrhs * g.ntx * g.nty * ((g.nz + ctx->dir_seg - 1) / ctx->dir_seg)) : 0u;
     if (roll) HYDOT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_it, 0, sizeof(int), s));
-    if (roll && ctx->use_sweep) {
+    // persistent form: only once the slab variant of the launched form is settled, so that the
+    // two forms are compared at their best
+    const int mode = (roll && ctx->sweep_ok && ctx->tune.variant >= 0) ? persist_pick(ctx) : 0;
+    const bool persistent = mode == 1;
+    const bool tuning_mode = roll && ctx->sweep_ok && ctx->tune.variant >= 0 && ctx->persist.mode < 0;
+    if (tuning_mode) HYDOT_CUDA_TRY(ctx, cudaEventRecord(ctx->tune_ev[0], s));
+    if (persistent) {
+      cudaEvent_t t_grp = timer_begin(ctx);
+      int ran = 0;
+      int rc = persist_launch(ctx, g, b, nrb, &ran);
+      if (rc) return rc;
+      timer_end(ctx, t_grp, HYDOT_KERNEL_ITER, 0.0, ran);
+      it = ran;
+      stop = true;
+    }
+    if (roll && ctx->use_sweep && !persistent) {
       // the cycle's first inner products (gamma_0, delta_0, ||r_0||^2) from r_0
       sweep_dispatch<true>(ctx, roll_pick(ctx), g, b, 0, nrb);
       if (ctx->timer.on) ctx->timer.bytes[HYDOT_KERNEL_PRIME] += (double)prev_active * (double)g.N * sizeof(T);
       HYDOT_CUDA_TRY(ctx, cudaGetLastError());
     }
     std::vector<unsigned char> replayed;  // per group: 1 if it ran as a graph replay (no per-pass events)
+    if (persistent) replayed.assign((it + POLL_GROUP - 1) / POLL_GROUP, 1);
     while (!stop && it < MAX_INNER_PER_CYCLE) {
       int g_end = std::min(it + POLL_GROUP, MAX_INNER_PER_CYCLE);
       // autotuning: a group that does not start the cycle runs one candidate variant and is timed
@@ -2249,6 +2435,18 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
     HYDOT_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     cudaEventDestroy(ev[0]);
     cudaEventDestroy(ev[1]);
+    if (tuning_mode && it > 0) {
+      // the cycle's inner solve per active cell-iteration, in the mode it ran
+      HYDOT_CUDA_TRY(ctx, cudaEventRecord(ctx->tune_ev[1], s));
+      std::vector<int> cnt(it);
+      HYDOT_CUDA_TRY(ctx, cudaMemcpyAsync(cnt.data(), b.counter + 1, sizeof(int) * it, cudaMemcpyDeviceToHost, s));
+      HYDOT_CUDA_TRY(ctx, cudaEventSynchronize(ctx->tune_ev[1]));
+      float ms = 0.f;
+      HYDOT_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, ctx->tune_ev[0], ctx->tune_ev[1]));
+      double work = 0.0;
+      for (int q = 0; q < it; ++q) work += (double)cnt[q] * (double)g.N;
+      if (it >= POLL_GROUP) persist_record(ctx, mode, ms, work);
+    }
     if (ctx->timer.on) {
       // algorithmic bytes of the inner passes: fields active at each iteration (the counters
       // k_dir increments) x 12 B (pass 1) or 20 B (pass 2) per cell in the inner precision
@@ -2264,7 +2462,7 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
         const size_t grp = (size_t)(q / POLL_GROUP);
         if (grp >= replayed.size() || !replayed[grp]) direct += cnt[q];
       }
-      if (roll && ctx->use_sweep) {
+      if (roll && (ctx->use_sweep || persistent)) {
         ctx->timer.bytes[HYDOT_KERNEL_SWEEP] += direct * 6.0 * (double)g.N * sizeof(T);
       } else {
         ctx->timer.bytes[HYDOT_KERNEL_DIR] += direct * 3.0 * (double)g.N * sizeof(T);
@@ -2404,17 +2602,32 @@ int solver_alloc(hydot_ctx* ctx) {
   HYDOT_CUDA_TRY(ctx, cudaMemset(ctx->d_it, 0, sizeof(int)));
   ctx->use_graphs = !getenv_flag("HYDOT_NO_GRAPHS");
   HYDOT_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
-  // real FP32 fields on the TMA path: the two-pass iteration, or with HYDOT_SINGLE_SWEEP=1 the
-  // single-sweep one
-  ctx->use_sweep = ctx->use_tma && !ctx->cplx && getenv_flag("HYDOT_SINGLE_SWEEP");
-  if (ctx->use_sweep) {
+  // Real FP32 fields on the TMA path iterate in two passes (measured faster on every workload
+  // here), or in single sweeps with HYDOT_SINGLE_SWEEP=1. Only with single sweeps is the persistent
+  // form tuned against launched iterations: the two do the same arithmetic, so the tuner never
+  // changes a result's bits (HYDOT_PERSISTENT=0 or 1 fixes the launch form; 1 implies sweeps).
+  ctx->sweep_ok = ctx->use_tma && !ctx->cplx;
+  if (ctx->sweep_ok) {
+    ctx->use_sweep = getenv_flag("HYDOT_SINGLE_SWEEP");
+    ctx->persist.mode = ctx->use_sweep ? -1 : 0;
+  }
+  if (ctx->sweep_ok) {
     HYDOT_CUDA_TRY(ctx, cudaMalloc(&ctx->d_r2, iw * F * N));
     HYDOT_CUDA_TRY(ctx, cudaMalloc(&ctx->d_cgsc, sizeof(double) * 4 * F));
     HYDOT_CUDA_TRY(ctx, cudaMemset(ctx->d_cgsc, 0, sizeof(double) * 4 * F));
+    if (const char* v = std::getenv("HYDOT_PERSISTENT")) ctx->persist.mode = (std::atoi(v) != 0) ? 1 : 0;
+    if (ctx->persist.mode == 1 && !ctx->use_sweep) ctx->use_sweep = true;  // the persistent form iterates in sweeps
   }
   if (ctx->use_tma) {
     int rc = roll_setup(ctx);
-    for (int d = 0; d < 2 && !rc && ctx->use_sweep; ++d) {
+    if (!rc && ctx->sweep_ok && !ctx->use_sweep) {  // the sweep kernels also serve the priming pass
+      rc = sweep_attrs<4, 3, 3>(ctx);
+      if (!rc) rc = sweep_attrs<4, 4, 2>(ctx);
+      if (!rc) rc = sweep_attrs<3, 4, 3>(ctx);
+      if (!rc) rc = sweep_attrs<3, 5, 3>(ctx);
+    }
+    if (!rc && ctx->sweep_ok) rc = persist_setup(ctx);
+    for (int d = 0; d < 2 && !rc && ctx->sweep_ok; ++d) {
       const int bz = 3 + d;
       rc = encode_field_map(ctx, ctx->d_r, &ctx->tm_r2[d][0], BX2, BY2, bz);
       if (!rc) rc = encode_field_map(ctx, ctx->d_r2, &ctx->tm_r2[d][1], BX2, BY2, bz);
@@ -2453,6 +2666,7 @@ void solver_free(hydot_ctx* ctx) {
   cudaFree(ctx->d_x64);
   cudaFree(ctx->d_r2);
   cudaFree(ctx->d_cgsc);
+  cudaFree(ctx->d_gsync);
   cudaFree(ctx->d_e);
   cudaFree(ctx->d_r);
   cudaFree(ctx->d_p[0]);
@@ -2492,17 +2706,53 @@ __global__ void k_wait_selftest(int* err, uint32_t polls) {
 }
 }  // namespace
 
+// Two co-resident blocks; only block 0 arrives at the grid barrier, so its bounded wait runs out.
+__global__ void k_grid_wait_selftest(GridSync gs, int* err) {
+  if (blockIdx.x == 0) grid_sync(gs, err);
+}
+
 int wait_selftest_impl(hydot_ctx* ctx, int polls) {
   if (polls < 1 || (uint32_t)polls > WAIT_POLLS) return fail(ctx, HYDOT_ERR_ARG, "polls must be in 1..2^22");
+  int flag[2] = {0, 0};
+  // (1) an mbarrier that nothing arrives at, polled as the pipelined kernels poll their slabs
   HYDOT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
   k_wait_selftest<<<1, 32, 0, ctx->stream>>>(ctx->d_err, (uint32_t)polls);
   ++ctx->launches;
   HYDOT_CUDA_TRY(ctx, cudaGetLastError());
-  int flag = 0;
-  HYDOT_CUDA_TRY(ctx, cudaMemcpyAsync(&flag, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  HYDOT_CUDA_TRY(ctx, cudaMemcpyAsync(&flag[0], ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   HYDOT_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  // (2) the persistent kernel's grid barrier with one of two blocks never arriving
   HYDOT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
-  if (flag) return fail(ctx, HYDOT_ERR_TIMEOUT, "bounded wait gave up (self-test)");
+  unsigned* words = ctx->d_gsync;
+  bool own = false;
+  if (!words) {
+    HYDOT_CUDA_TRY(ctx, cudaMalloc(&words, 2 * sizeof(unsigned)));
+    own = true;
+  }
+  HYDOT_CUDA_TRY(ctx, cudaMemsetAsync(words, 0, 2 * sizeof(unsigned), ctx->stream));
+  GridSync gs{words, words + 1, (uint32_t)polls};
+  int* err = ctx->d_err;
+  void* args[] = {&gs, &err};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_grid_wait_selftest, dim3(2), dim3(32), args, 0,
+                                              ctx->stream);
+  ++ctx->launches;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&flag[1], ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (own) cudaFree(words);
+  if (e != cudaSuccess) return fail(ctx, HYDOT_ERR_CUDA, std::string("grid-barrier self-test: ") + cudaGetErrorString(e));
+  HYDOT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
+  HYDOT_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  if (flag[0] && flag[1]) return fail(ctx, HYDOT_ERR_TIMEOUT, "bounded waits gave up (self-test: mbarrier and grid barrier)");
+  return fail(ctx, HYDOT_ERR_STATE, std::string("self-test: a bounded wait did not give up (mbarrier ") +
+                                        (flag[0] ? "yes" : "no") + ", grid barrier " + (flag[1] ? "yes" : "no") + ")");
+}
+
+int get_launch_mode_impl(const hydot_ctx* ctx, int* mode, double* ns_launched, double* ns_persistent) {
+  const auto& p = ctx->persist;
+  if (mode) *mode = ctx->sweep_ok ? p.mode : 0;
+  if (ns_launched) *ns_launched = p.cells[0] > 0.0 ? 1e6 * p.ms[0] / p.cells[0] : 0.0;
+  if (ns_persistent) *ns_persistent = p.cells[1] > 0.0 ? 1e6 * p.ms[1] / p.cells[1] : 0.0;
   return HYDOT_OK;
 }
 

@@ -268,6 +268,7 @@ def test_roll_variants_bitwise_identical_and_autotuner_settles(hd, oracle_fields
     """The slab shapes the autotuner chooses from give the same bits (two-pass and single-sweep
     forms); an untuned context times the variants on groups of inner iterations and then keeps one."""
     monkeypatch.setenv("HYDOT_SINGLE_SWEEP", sweep)
+    monkeypatch.setenv("HYDOT_PERSISTENT", "0")
     p = workloads.make_problem(workloads.Grid(64, 40, 36, 2.0), 4, 4, 4, seed=21, geometry="transmission")
     out = []
     for v in range(4):
@@ -344,8 +345,9 @@ def test_graph_replay_matches_direct_launches(hd, monkeypatch):
 
 
 def test_bounded_wait_timeout_keeps_context_usable(hd):
-    """A device wait that runs out (an mbarrier nothing arrives at, through the kernels' bounded
-    poll loop) comes back as HYDOT_ERR_TIMEOUT; the context then solves as before."""
+    """Device waits that run out (an mbarrier nothing arrives at, through the kernels' bounded poll
+    loop; the persistent solve's grid barrier with one of two co-resident blocks never arriving)
+    come back as HYDOT_ERR_TIMEOUT; the context then solves as before."""
     p = workloads.small(seed=5, nx=16, ny=11, nz=9, n_src=2, n_det=2, n_lambda=2)
     with hd.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=1e-8) as ctx:
         a, b, _ = ctx.solve_fields(0, 2)
@@ -355,3 +357,64 @@ def test_bounded_wait_timeout_keeps_context_usable(hd):
         c, d, st = ctx.solve_fields(0, 2)
         assert st["n_not_converged"] == 0
     assert torch.equal(a, c) and torch.equal(b, d)
+
+
+@pytest.mark.parametrize("seg", [None, "8"])
+@pytest.mark.parametrize("name", ["tma-ragged-36x19x21", "tma-faces-40x16x9"])
+def test_persistent_inner_solve_matches_launched_sweeps(hd, oracle_fields, monkeypatch, name, seg):
+    """The persistent form (one cooperative launch per refinement cycle: co-resident blocks iterate
+    single sweeps over (field, column, z-segment) items with a grid barrier per iteration and stop
+    on the device) does the same arithmetic as launched single sweeps with the same slabs: the same
+    bits, and the oracle's fields and Born rows to the stated tolerances."""
+    p, (rs, rd) = oracle_fields[name]
+    monkeypatch.setenv("HYDOT_SINGLE_SWEEP", "1")
+    monkeypatch.setenv("HYDOT_ROLL_VARIANT", "2")  # the persistent kernel's {3 planes, 4 buffers}
+    if seg:
+        monkeypatch.setenv("HYDOT_DIR_SEG", seg)
+    out = {}
+    for flag in ("0", "1"):
+        monkeypatch.setenv("HYDOT_PERSISTENT", flag)
+        with hd.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=1e-8, cw_floor=100.0) as ctx:
+            ps, pd, st = ctx.solve_fields(0, p.n_lambda)
+            assert ctx.launch_mode()["mode"] == int(flag)
+        assert st["n_not_converged"] == 0
+        out[flag] = (ps, pd, st)
+    assert torch.equal(out["0"][0], out["1"][0]) and torch.equal(out["0"][1], out["1"][1])
+    assert out["0"][2]["iters_mean"] == out["1"][2]["iters_mean"]
+    ps, pd, _ = out["1"]
+    assert rel_err(ps, rs) <= 1e-6 and rel_err(pd, rd) <= 1e-6
+    assert born_rowmax_err(p, ps, pd, rs, rd) <= 1e-5
+
+
+def test_persistent_inner_solve_on_the_small_reflection_batch(hd):
+    """The 24x24x16 reflection workload (8 + 8 optodes on the top face, 16 wavelengths: 256 fields,
+    L2-resident) in the mixed form through one persistent launch per cycle, against the oracle's
+    sparse-direct fields; then an untuned single-sweep context compares the two launch forms on
+    whole cycles (same bits in both) and keeps one."""
+    p = workloads.config(1)
+    rs, rd = osolve.fields_splu(p)
+    import os
+    os.environ["HYDOT_PERSISTENT"] = "1"
+    try:
+        with hd.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=1e-8, cw_floor=100.0) as ctx:
+            ps, pd, st = ctx.solve_fields(0, p.n_lambda)
+            assert ctx.launch_mode()["mode"] == 1
+    finally:
+        os.environ.pop("HYDOT_PERSISTENT", None)
+    assert st["n_not_converged"] == 0
+    assert rel_err(ps, rs) <= 1e-6 and rel_err(pd, rd) <= 1e-6
+    assert born_rowmax_err(p, ps, pd, rs, rd) <= 1e-5
+    os.environ["HYDOT_SINGLE_SWEEP"] = "1"  # the launch-form tuner runs for single-sweep contexts
+    try:
+        with hd.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=1e-8, cw_floor=100.0) as ctx:
+            assert ctx.launch_mode()["mode"] == -1
+            first, _, _ = ctx.solve_fields(0, p.n_lambda)
+            for _ in range(5):
+                qs, qd, st2 = ctx.solve_fields(0, p.n_lambda)
+                assert st2["n_not_converged"] == 0
+                assert torch.equal(qs, first)  # launched and persistent cycles give the same bits
+            lm = ctx.launch_mode()
+    finally:
+        os.environ.pop("HYDOT_SINGLE_SWEEP", None)
+    assert lm["mode"] in (0, 1) and lm["ns_per_cell_launched"] > 0 and lm["ns_per_cell_persistent"] > 0
+    assert rel_err(qs, rs) <= 1e-6 and rel_err(qd, rd) <= 1e-6
