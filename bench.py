@@ -482,6 +482,102 @@ def sketch_phase(hd, pk, n_lam=4, rank=200, over=20, n_probe=32):
     return out
 
 
+def sketch_full(hd, pk, chunk=8, rank=200, over=20, n_probe=32, n_lambda=None):
+    """The rank-200 randomised sketch of the whole 128x128x96 / 64+64-optode / 512-wavelength Born
+    matrix (J: 2,097,152 x 6,291,456; Appendix A.1 with the Section 4.2 sum over row blocks): pass 1
+    solves every wavelength chunk, runs the tensor-core range pass Y = J Omega and the exact
+    implicit J X for 32 Gaussian probes; Q = orth(Y); pass 2 solves every chunk again and
+    accumulates B^T = J^T Q; the rank-200 factors follow from B. Reports the wall time of each
+    phase and the probe error of U S V^T against the exact J X. About 8 minutes on one GB300."""
+    import numpy as np
+    import torch
+
+    import workloads
+
+    p = workloads.config(5)
+    N, nc, ns, nd = p.grid.N, p.n_chrom, p.n_src, p.n_det
+    ncols = rank + over
+    nl_all = p.n_lambda if n_lambda is None else min(n_lambda, p.n_lambda)
+    chunks = [(l0, chunk) for l0 in range(0, nl_all, chunk)]
+    rows = ns * nd * chunk
+    M = rows * len(chunks)
+    out = {"workload": f"cw-sketch-128x128x96: 128x128x96 grid (h=1 mm), {ns}+{nd} optodes, wavelengths 0-{nl_all - 1} "
+                       f"of {p.n_lambda} ({(ns + nd) * nl_all} field solves per pass, two passes), "
+                       f"J {M} x {nc * N}, rank {rank} + {over}, chunks of {chunk} wavelengths",
+           "phases_s": {}}
+    t = out["phases_s"]
+    sync = torch.cuda.synchronize
+    with hd.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=TOL_CW, cw_floor=CW_FLOOR,
+                                 max_lambda_per_call=chunk) as ctx:
+        gen = torch.Generator(device="cuda").manual_seed(workloads.SEED_BASE + 5)
+        om = torch.randn(nc, ncols, N, device="cuda", generator=gen).to(torch.bfloat16)
+        X = torch.randn(nc * N, n_probe, device="cuda", generator=gen)
+        Y = torch.empty(M, 224, dtype=torch.float32, device="cuda")
+        JX = torch.empty(M, n_probe, dtype=torch.float64, device="cuda")
+        ps = torch.empty(chunk, ns, N, dtype=torch.float32, device="cuda")
+        pd = torch.empty(chunk, nd, N, dtype=torch.float32, device="cuda")
+        e2 = torch.tensor((p.eps ** 2).sum(1), device="cuda", dtype=torch.float64)
+        jf2 = 0.0
+        solves, iters = 0, []
+        for k in ("solve_1", "range", "probes", "orthonormalize", "solve_2", "project", "factor"):
+            t[k] = 0.0
+        for i, (l0, nl) in enumerate(chunks):
+            sync()
+            a = time.perf_counter()
+            _, _, st = ctx.solve_fields(l0, nl, ps, pd)
+            sync()
+            b = time.perf_counter()
+            ctx.sketch_range(ps, pd, l0, nl, om, ncols, Y[i * rows:(i + 1) * rows])
+            sync()
+            c = time.perf_counter()
+            for q in range(n_probe):
+                JX[i * rows:(i + 1) * rows, q] = ctx.born_apply(ps, pd, l0, nl, X[:, q].contiguous()).double()
+            jf2 += float((p.grid.h ** 6) * (e2[l0:l0 + nl] * ((ps.double() ** 2).sum(1) * (pd.double() ** 2).sum(1))
+                                             .sum(1)).sum())
+            sync()
+            d = time.perf_counter()
+            t["solve_1"] += b - a
+            t["range"] += c - b
+            t["probes"] += d - c
+            solves += st["n_fields"]
+            iters.append(st["iters_mean"])
+        a = time.perf_counter()
+        kept = ctx.sketch_orthonormalize(Y, ncols)
+        sync()
+        t["orthonormalize"] = time.perf_counter() - a
+        Bt = torch.zeros(nc * N, 224, dtype=torch.float32, device="cuda")
+        for i, (l0, nl) in enumerate(chunks):
+            sync()
+            a = time.perf_counter()
+            ctx.solve_fields(l0, nl, ps, pd)
+            sync()
+            b = time.perf_counter()
+            ctx.sketch_project(ps, pd, l0, nl, Y[i * rows:(i + 1) * rows], ncols, Bt)
+            sync()
+            t["solve_2"] += b - a
+            t["project"] += time.perf_counter() - b
+        del ps, pd
+        a = time.perf_counter()
+        U, S, V = ctx.sketch_factor(Y, Bt, ncols, rank)
+        sync()
+        t["factor"] = time.perf_counter() - a
+        del Bt, Y, om
+        lr = U.double() @ (torch.tensor(S, device="cuda")[:, None] * (V.double().T @ X.double()))
+        errs = ((JX - lr).norm(dim=0) / JX.norm(dim=0)).cpu().numpy()
+    tot = sum(t.values())
+    out.update({
+        "total_s": tot, "solves": 2 * solves, "solves_per_s": 2 * solves / (t["solve_1"] + t["solve_2"]),
+        "iters_mean": float(np.mean(iters)), "kept_directions": kept,
+        "range_tflops": 2.0 * M * N * 224 / t["range"] / 1e12 if t["range"] else None,
+        "project_tflops": 2.0 * nc * N * M * 224 / t["project"] / 1e12 if t["project"] else None,
+        "singular_values": {"s1": float(S[0]), "s200": float(S[rank - 1]), "s200_over_s1": float(S[rank - 1] / S[0])},
+        "probe_error": {"max": float(errs.max()), "median": float(np.median(errs)),
+                        "rms": float(np.sqrt(np.mean(errs ** 2))), "n": n_probe},
+        "frobenius_error_of_factors": float(max(0.0, 1.0 - float((S[:rank] ** 2).sum()) / jf2) ** 0.5),
+        "peak_bf16_tflops": pk["bf16_tflops"]})
+    return out
+
+
 def tree_phase(hd, p, n_lam, tol=1e-2, leaf_rank=100, merge_rank=160, n_probe=16):
     """Recursive compression (Section 4, alg:recursive) of the same chunk: sources ordered by the
     geometric bisection tree, randomised leaves with the adaptive-rank estimator, agglomeration up
@@ -1194,12 +1290,22 @@ def main():
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the uneven batch of six 100 MHz phantoms (sequential against hydot_solve_batch)")
     ap.add_argument("--no-compare-fp64", dest="compare_fp64", action="store_false")
+    ap.add_argument("--sketch-full", action="store_true",
+                    help="only the rank-200 sketch of the whole 128x128x96 / 512-wavelength Born matrix "
+                         "(two solve passes, about 8 minutes); prints its own JSON line")
+    ap.add_argument("--sketch-lambdas", type=int, default=None,
+                    help="with --sketch-full: only the first this many wavelengths (a multiple of 8)")
     ap.add_argument("--cpu-sample", type=int, default=None, help=argparse.SUPPRESS)
     ap.add_argument("--kernel-case", default=None,
                     help="born_rows | solver | solver256 | solver_fd | sketch | apply: small profiling case")
     args = ap.parse_args()
     if args.kernel_case:
         run_kernel_case(args.kernel_case)
+        return
+    if args.sketch_full:
+        import paper_1410_0986_gb300 as hd
+
+        print(json.dumps({"sketch_full": sketch_full(hd, peaks(), n_lambda=args.sketch_lambdas)}))
         return
     if args.cpu_sample is not None:
         print(json.dumps(cpu_sample(args.cpu_sample)))

@@ -303,15 +303,29 @@ __global__ void __launch_bounds__(RG_THREADS, 1)
       const float* fps = reinterpret_cast<const float*>(base + (size_t)st * RG_STAGE + RG_B_BYTES);
       const float* fpd = fps + 2 * a.S_a * SK_K;
       uint8_t* At = abuf + (size_t)as * RG_A_STAGE;
+      // the eight lanes of a 16-byte access phase read chunks ch = 0..7 of one row: lanes with
+      // ch >= 4 read their chunk's second half first, so that the phase's eight 16-byte words fall
+      // on distinct bank groups (ch * 32 + 16 * (ch >> 2) mod 128 is a permutation of 16 * 0..7)
       for (int pc = f; pc < C; pc += 256) {
         const int dl = pc >> 3, ch = pc & 7;
-        const float4 d0v = *reinterpret_cast<const float4*>(fpd + dl * SK_K + ch * 8);
-        const float4 d1v = *reinterpret_cast<const float4*>(fpd + dl * SK_K + ch * 8 + 4);
+        const int h0 = (ch >> 2) * 4, h1 = 4 - h0;
+        float4 d0v = *reinterpret_cast<const float4*>(fpd + dl * SK_K + ch * 8 + h0);
+        float4 d1v = *reinterpret_cast<const float4*>(fpd + dl * SK_K + ch * 8 + h1);
+        if (h0) {
+          const float4 t = d0v;
+          d0v = d1v;
+          d1v = t;
+        }
         for (int sl = 0; sl < 2 * a.S_a; ++sl) {
           const int acc = sl >= a.S_a ? 1 : 0;
           const int rr = (sl - acc * a.S_a) * a.D_t + dl;
-          const float4 s0v = *reinterpret_cast<const float4*>(fps + sl * SK_K + ch * 8);
-          const float4 s1v = *reinterpret_cast<const float4*>(fps + sl * SK_K + ch * 8 + 4);
+          float4 s0v = *reinterpret_cast<const float4*>(fps + sl * SK_K + ch * 8 + h0);
+          float4 s1v = *reinterpret_cast<const float4*>(fps + sl * SK_K + ch * 8 + h1);
+          if (h0) {
+            const float4 t = s0v;
+            s0v = s1v;
+            s1v = t;
+          }
           uint4 pk;
           pk.x = pack_bf16x2(s0v.x * d0v.x, s0v.y * d0v.y);
           pk.y = pack_bf16x2(s0v.z * d0v.z, s0v.w * d0v.w);
