@@ -511,9 +511,9 @@ def sketch_full(hd, pk, chunk=8, rank=200, over=20, n_probe=32, n_lambda=None):
                                  max_lambda_per_call=chunk) as ctx:
         gen = torch.Generator(device="cuda").manual_seed(workloads.SEED_BASE + 5)
         om = torch.randn(nc, ncols, N, device="cuda", generator=gen).to(torch.bfloat16)
-        X = torch.randn(nc * N, n_probe, device="cuda", generator=gen)
+        X = torch.randn(n_probe, nc * N, device="cuda", generator=gen)  # one probe per row
         Y = torch.empty(M, 224, dtype=torch.float32, device="cuda")
-        JX = torch.empty(M, n_probe, dtype=torch.float64, device="cuda")
+        JX = torch.empty(n_probe, M, dtype=torch.float32, device="cuda")
         ps = torch.empty(chunk, ns, N, dtype=torch.float32, device="cuda")
         pd = torch.empty(chunk, nd, N, dtype=torch.float32, device="cuda")
         e2 = torch.tensor((p.eps ** 2).sum(1), device="cuda", dtype=torch.float64)
@@ -531,7 +531,7 @@ def sketch_full(hd, pk, chunk=8, rank=200, over=20, n_probe=32, n_lambda=None):
             sync()
             c = time.perf_counter()
             for q in range(n_probe):
-                JX[i * rows:(i + 1) * rows, q] = ctx.born_apply(ps, pd, l0, nl, X[:, q].contiguous()).double()
+                ctx.born_apply(ps, pd, l0, nl, X[q], JX[q, i * rows:(i + 1) * rows])
             jf2 += float((p.grid.h ** 6) * (e2[l0:l0 + nl] * ((ps.double() ** 2).sum(1) * (pd.double() ** 2).sum(1))
                                              .sum(1)).sum())
             sync()
@@ -562,8 +562,9 @@ def sketch_full(hd, pk, chunk=8, rank=200, over=20, n_probe=32, n_lambda=None):
         sync()
         t["factor"] = time.perf_counter() - a
         del Bt, Y, om
-        lr = U.double() @ (torch.tensor(S, device="cuda")[:, None] * (V.double().T @ X.double()))
-        errs = ((JX - lr).norm(dim=0) / JX.norm(dim=0)).cpu().numpy()
+        lr = U.double() @ (torch.tensor(S, device="cuda")[:, None] * (V.double().T @ X.double().T))
+        JXd = JX.double().T
+        errs = ((JXd - lr).norm(dim=0) / JXd.norm(dim=0)).cpu().numpy()
     tot = sum(t.values())
     out.update({
         "total_s": tot, "solves": 2 * solves, "solves_per_s": 2 * solves / (t["solve_1"] + t["solve_2"]),

@@ -171,6 +171,24 @@ int hydot_born_apply(hydot_ctx* ctx, const void* phi_src, const void* phi_det, i
 int hydot_born_apply_T(hydot_ctx* ctx, const void* phi_src, const void* phi_det, int lam0, int nlam,
                        const void* y, void* g);
 
+/* Adjoint fields (Section 5: the misfit gradient -dmu/dp^T H^T (y - H mu) needs H^T times a data
+ * vector; since phi_d = A^-1 e_d and A is symmetric, sum_d y[s,d,lambda] phi_d = A^-1 (sum_d
+ * y[s,d,lambda] e_d), one solve per source and wavelength instead of the stored detector fields):
+ *     A_lambda psi[a][s] = sum_d y[(s*n_det + d)*nlam + a] e_(detector cell d)
+ * for every source s and wavelength lambda = lam0 + a of the slice. y: DEVICE [n_src*n_det*nlam]
+ * (slice rows as for hydot_born_apply); psi: DEVICE [nlam][n_src][N], written. The same solver,
+ * tolerances and refinement as hydot_solve_fields (each right-hand side normalised to unit 2-norm,
+ * the norm applied to the output; the componentwise floor weighs the field against its own source
+ * cell); starts from zero. Continuous wave only (HYDOT_ERR_STATE otherwise); needs
+ * nlam * n_src <= max_lambda_per_call * (n_src + n_det). Synchronises the stream. */
+int hydot_solve_adjoint(hydot_ctx* ctx, int lam0, int nlam, const void* y, void* psi, hydot_stats* st);
+
+/* g += J^T y for the slice from the source fields and the adjoint fields of y:
+ *     g[c*N + x] += -h^3 sum_lambda eps_c(lambda) sum_s phi_s(x; lambda) psi_s(x; lambda).
+ * phi_src [nlam][n_src][N], psi [nlam][n_src][N] (hydot_solve_adjoint), g [n_chrom*N] (accumulated).
+ * Equals hydot_born_apply_T without the detector fields. Continuous wave only. Asynchronous. */
+int hydot_born_apply_T_adjoint(hydot_ctx* ctx, const void* phi_src, const void* psi, int lam0, int nlam, void* g);
+
 /* y = J x for one wavelength slice in FP32 without allocating device memory and without a
  * context. The paper has no counterpart: this exists for callers that cannot allocate device
  * memory themselves (code running where cudaMalloc is not allowed, or whose allocator is owned

@@ -25,7 +25,8 @@ HYDOT_MIXED = 1
 # Every symbol include/hydot.h declares.
 EXPORTS = ("hydot_version", "hydot_setup", "hydot_set_stream", "hydot_solve_fields", "hydot_solve_batch",
            "hydot_born_assemble",
-           "hydot_born_apply", "hydot_born_apply_T", "hydot_born_apply_noalloc", "hydot_sketch_range",
+           "hydot_born_apply", "hydot_born_apply_T", "hydot_born_apply_noalloc", "hydot_solve_adjoint",
+           "hydot_born_apply_T_adjoint", "hydot_sketch_range",
            "hydot_sketch_project", "hydot_sketch_orthonormalize", "hydot_sketch_rank", "hydot_sketch_merge",
            "hydot_sketch_factor", "hydot_set_kernel_timing", "hydot_set_graphs", "hydot_get_launch_mode",
            "hydot_kernel_stats", "hydot_kernel_launches", "hydot_get_tuning", "hydot_set_absorption",
@@ -110,6 +111,10 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.hydot_born_apply.restype = C.c_int
     lib.hydot_born_apply_T.argtypes = [vp, vp, vp, C.c_int, C.c_int, vp, vp]
     lib.hydot_born_apply_T.restype = C.c_int
+    lib.hydot_solve_adjoint.argtypes = [vp, C.c_int, C.c_int, vp, vp, C.POINTER(Stats)]
+    lib.hydot_solve_adjoint.restype = C.c_int
+    lib.hydot_born_apply_T_adjoint.argtypes = [vp, vp, vp, C.c_int, C.c_int, vp]
+    lib.hydot_born_apply_T_adjoint.restype = C.c_int
     lib.hydot_born_apply_noalloc.argtypes = [C.c_longlong, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
                                              C.POINTER(C.c_double), vp, vp, vp, vp, vp]
     lib.hydot_born_apply_noalloc.restype = C.c_int

@@ -124,6 +124,31 @@ class Context:
         self._check(rc, allow_not_converged=not raise_not_converged)
         return phi_src, phi_det, st.as_dict()
 
+    def solve_adjoint(self, lam0: int, nlam: int, y: torch.Tensor, psi: Optional[torch.Tensor] = None,
+                      raise_not_converged: bool = True):
+        """hydot_solve_adjoint: psi[a][s] = A^-1 sum_d y[(s*n_det + d)*nlam + a] e_d. Returns (psi, stats)."""
+        M = self.n_src * self.n_det * nlam
+        if psi is None:
+            psi = self.empty(nlam, self.n_src, self.N, dtype=self.real_dtype)
+        st = _lib.Stats()
+        self._stream()
+        rc = self.lib.hydot_solve_adjoint(self._ctx, lam0, nlam, self._ptr(y, (M,), self.real_dtype),
+                                          self._ptr(psi, (nlam, self.n_src, self.N), self.real_dtype), C.byref(st))
+        self._check(rc, allow_not_converged=not raise_not_converged)
+        return psi, st.as_dict()
+
+    def born_apply_T_adjoint(self, phi_src, psi, lam0: int, nlam: int, g: Optional[torch.Tensor] = None):
+        """hydot_born_apply_T_adjoint: g += J^T y from the source fields and the adjoint fields of y."""
+        if g is None:
+            g = torch.zeros(self.n_chrom * self.N, dtype=self.real_dtype, device="cuda")
+        self._stream()
+        rc = self.lib.hydot_born_apply_T_adjoint(self._ctx,
+                                                 self._ptr(phi_src, (nlam, self.n_src, self.N), self.real_dtype),
+                                                 self._ptr(psi, (nlam, self.n_src, self.N), self.real_dtype), lam0,
+                                                 nlam, self._ptr(g, (self.n_chrom * self.N,), self.real_dtype))
+        self._check(rc)
+        return g
+
     def born_assemble(self, phi_src, phi_det, lam0: int, nlam: int, row0: int = 0, nrows: Optional[int] = None,
                       J: Optional[torch.Tensor] = None, ldJ: Optional[int] = None) -> torch.Tensor:
         M = self.n_src * self.n_det * nlam

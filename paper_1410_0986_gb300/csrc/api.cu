@@ -344,6 +344,20 @@ int hydot_solve_batch(hydot_ctx* const* ctxs, int n, const int* lam0, const int*
   });
 }
 
+int hydot_solve_adjoint(hydot_ctx* ctx, int lam0, int nlam, const void* y, void* psi, hydot_stats* st) {
+  return hydot::abi_guard(ctx, [&]() -> int {
+    if (!ctx) return HYDOT_ERR_ARG;
+    return hydot::solve_adjoint_impl(ctx, lam0, nlam, y, psi, st);
+  });
+}
+
+int hydot_born_apply_T_adjoint(hydot_ctx* ctx, const void* phi_src, const void* psi, int lam0, int nlam, void* g) {
+  return hydot::abi_guard(ctx, [&]() -> int {
+    if (!ctx) return HYDOT_ERR_ARG;
+    return hydot::born_apply_T_adjoint_impl(ctx, phi_src, psi, lam0, nlam, g);
+  });
+}
+
 int hydot_born_assemble(hydot_ctx* ctx, const void* phi_src, const void* phi_det, int lam0, int nlam, long long row0,
                         long long nrows, void* J, long long ldJ) {
   return hydot::abi_guard(ctx, [&]() -> int {

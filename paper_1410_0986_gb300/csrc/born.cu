@@ -904,6 +904,68 @@ int born_apply_impl(hydot_ctx* ctx, const void* phi_src, const void* phi_det, in
   return apply_t<double>(ctx, (const double*)phi_src, (const double*)phi_det, lam0, nlam, (const double*)x, (double*)y);
 }
 
+// J^T y from the adjoint fields (Section 5, the gradient by one extra solve per source):
+//   g[c*N + x] += -h^3 sum_a eps_c(lambda_a) sum_s phi_s[a][s][x] psi[a][s][x]
+// with psi[a][s] = A^-1 (sum_d y[s,d,a] e_d) from hydot_solve_adjoint. One thread per voxel, the
+// wavelengths and sources of the slice in a fixed order (the same bits on every run); reads each
+// field value once, coalesced along x.
+template <typename E>
+__global__ void __launch_bounds__(256) k_apply_T_adjoint(const E* __restrict__ ps, const E* __restrict__ psi,
+                                                        const double* __restrict__ eps, int lam0, int nlam, int ns,
+                                                        int nc, long long N, E scale, E* __restrict__ g) {
+  __shared__ E w[64 * MAXC];  // eps of up to 64 wavelengths of the slice at a time
+  for (long long x0 = (long long)blockIdx.x * blockDim.x; x0 < N; x0 += (long long)gridDim.x * blockDim.x) {
+    const long long x = x0 + threadIdx.x;
+    E acc[MAXC];
+#pragma unroll
+    for (int c = 0; c < MAXC; ++c) acc[c] = E(0);
+    for (int a0 = 0; a0 < nlam; a0 += 64) {
+      const int na = min(64, nlam - a0);
+      __syncthreads();
+      for (int q = threadIdx.x; q < na * nc; q += blockDim.x) w[q] = (E)eps[(size_t)(lam0 + a0) * nc + q];
+      __syncthreads();
+      if (x < N) {
+        for (int a = 0; a < na; ++a) {
+          const size_t f0 = (size_t)(a0 + a) * ns;
+          E t = E(0);
+          for (int s = 0; s < ns; ++s) t = fma(ps[(f0 + s) * N + x], psi[(f0 + s) * N + x], t);
+#pragma unroll
+          for (int c = 0; c < MAXC; ++c)
+            if (c < nc) acc[c] = fma(w[a * nc + c], t, acc[c]);
+        }
+      }
+    }
+    if (x < N) {
+#pragma unroll
+      for (int c = 0; c < MAXC; ++c)
+        if (c < nc) g[(size_t)c * N + x] += scale * acc[c];
+    }
+  }
+}
+
+int born_apply_T_adjoint_impl(hydot_ctx* ctx, const void* phi_src, const void* psi, int lam0, int nlam, void* g) {
+  int rc = check_slice(ctx, lam0, nlam);
+  if (rc) return rc;
+  if (!phi_src || !psi || !g) return fail(ctx, HYDOT_ERR_ARG, "null pointer");
+  if (ctx->n_src < 1) return fail(ctx, HYDOT_ERR_STATE, "no sources");
+  const double h3 = ctx->h * ctx->h * ctx->h;
+  const unsigned blocks = (unsigned)std::min<long long>((ctx->N + 255) / 256, 152LL * 16);
+  cudaEvent_t t0 = timer_begin(ctx);
+  if (ctx->precision == HYDOT_MIXED)
+    k_apply_T_adjoint<float><<<blocks, 256, 0, ctx->stream>>>((const float*)phi_src, (const float*)psi, ctx->d_eps, lam0,
+                                                              nlam, ctx->n_src, ctx->n_chrom, ctx->N, (float)(-h3),
+                                                              (float*)g);
+  else
+    k_apply_T_adjoint<double><<<blocks, 256, 0, ctx->stream>>>((const double*)phi_src, (const double*)psi, ctx->d_eps,
+                                                               lam0, nlam, ctx->n_src, ctx->n_chrom, ctx->N, -h3,
+                                                               (double*)g);
+  ++ctx->launches;
+  timer_end(ctx, t0, HYDOT_KERNEL_APPLY_T,
+            2.0 * nlam * ctx->n_src * (double)ctx->N * (ctx->precision == HYDOT_MIXED ? 4.0 : 8.0));
+  HYDOT_CUDA_TRY(ctx, cudaGetLastError());
+  return HYDOT_OK;
+}
+
 int born_apply_T_impl(hydot_ctx* ctx, const void* phi_src, const void* phi_det, int lam0, int nlam, const void* y,
                       void* g) {
   int rc = check_slice(ctx, lam0, nlam);

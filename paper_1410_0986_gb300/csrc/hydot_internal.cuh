@@ -264,10 +264,16 @@ struct hydot_ctx {
     double cells[2] = {0.0, 0.0};
   } persist;
   unsigned* d_gsync = nullptr;  // grid barrier words {count, generation}
+  // adjoint solves: detector slot of every cell (-1 elsewhere), normalised weights [max_fields][n_det]
+  // and their norms [max_fields] (allocated at the first adjoint solve)
+  int* d_rhs_slot = nullptr;
+  double* d_rhs_w = nullptr;
+  double* d_rhs_scale = nullptr;
   int persist_blocks = 0;       // co-resident blocks of the persistent kernel (whole GPU)
   void* d_r2 = nullptr;
   double* d_cgsc = nullptr;
   CUtensorMap tm_r2[2][2]{}, tm_p2[2][2]{}, tm_e2[2]{};
+  CUtensorMap tm_r4[2][2]{}, tm_p4[2][2]{}, tm_e4[2]{};  // the same for 32 x 16 tiles (40 x 20 boxes)
   // autotuner of the rolling inner passes: variant -1 while groups of iterations are being timed
   struct {
     int variant = -1;
@@ -346,6 +352,8 @@ cudaError_t raise_smem_limit(F* func, size_t bytes) {
 
 // solver.cu
 int solve_fields_impl(hydot_ctx* ctx, int lam0, int nlam, void* phi_src, void* phi_det, hydot_stats* st);
+int solve_adjoint_impl(hydot_ctx* ctx, int lam0, int nlam, const void* y, void* psi, hydot_stats* st);
+int born_apply_T_adjoint_impl(hydot_ctx* ctx, const void* phi_src, const void* psi, int lam0, int nlam, void* g);
 int get_tuning_impl(const hydot_ctx* ctx, int* variant, int* planes, int* buffers, double* ns_per_cell);
 int wait_selftest_impl(hydot_ctx* ctx, int polls);
 int get_launch_mode_impl(const hydot_ctx* ctx, int* mode, double* ns_launched, double* ns_persistent);

@@ -84,6 +84,14 @@ struct Batch {
   // wavelengths of the slice ([nlam][N]); null without an absorption perturbation
   const float* dsig_f;
   const double* dsig_d;
+  // general sparse right-hand side (adjoint solves, Section 5's gradient by one extra solve per
+  // source): b_rhs = sum_k w[rhs][k] e_(cell k) with the weights of each field normalised to unit
+  // 2-norm (rhs_scale holds the norms, applied to the output); rhs_slot[x] is k for the cells of
+  // the right-hand side, -1 elsewhere. Null for the one-hot optode right-hand sides.
+  const int* rhs_slot;
+  const double* rhs_w;
+  const double* rhs_scale;
+  int n_rhs_cells;
 };
 
 // Increment of the diagonal of field rhs at voxel id in precision T (real part only).
@@ -97,6 +105,16 @@ __device__ __forceinline__ T dsig_at(const Batch& b, int rhs, long long id, long
 }
 
 __device__ __forceinline__ int rhs_lambda(const Batch& b, int rhs) { return b.lam0 + rhs / b.nf; }
+
+// Entry `id` of field rhs's right-hand side: 1 at the optode cell `src`, or the field's weight at
+// the cells of a general right-hand side.
+__device__ __forceinline__ double rhs_value(const Batch& b, int rhs, long long id, long long src) {
+  if (b.rhs_slot) {
+    const int k = b.rhs_slot[id];
+    return k >= 0 ? b.rhs_w[(size_t)rhs * b.n_rhs_cells + k] : 0.0;
+  }
+  return id == src ? 1.0 : 0.0;
+}
 __device__ __forceinline__ long long rhs_source(const Batch& b, int rhs) {
   return (long long)b.optode[b.f_begin + rhs % b.nf];
 }
@@ -283,11 +301,12 @@ __global__ void __launch_bounds__(NTHREADS) k_residual(Geo g, Batch b, const X* 
       X d = diag_at<X>(dg, m);
       if (b.dsig_d) d = d + dsig_at<X>(b, c.rhs, id, g.N);
       X ax = d * xc - sn;
-      X r64 = (id == src) ? Traits<X>::make(1.0, 0.0) - ax : zero - ax;
+      const double bv = rhs_value(b, c.rhs, id, src);
+      X r64 = Traits<X>::make(bv, 0.0) - ax;
       rr += Traits<X>::abs2(r64);
       int ec = bexp(xc);
       ed = max(ed, ec ? ec + 2 : 0);
-      if (id == src) ed = max(ed, 1023);
+      if (bv != 0.0) ed = max(ed, bexp(bv));
       int er = bexp(r64);
       if (er) om_e = max(om_e, ed ? er + 1 + cplx_extra - ed : 4096);
       T rv = Traits<T>::from(Traits<X>::re(r64) * pre, Traits<X>::im(r64) * pre);
@@ -465,17 +484,28 @@ __global__ void __launch_bounds__(NTHREADS) k_residual_df(Geo g, Batch b, const 
       sub_nb(xq[SX]);
       // r = b - A x
       float rh = -s, rl = -cc;
-      if (id == src) {
+      int eb = 0;  // binary exponent of |b| at this cell (0: b is zero here)
+      if (b.rhs_slot) {
+        const double bv = rhs_value(b, c.rhs, id, src);
+        if (bv != 0.0) {
+          const df32 bd = df_from(bv);
+          float t;
+          two_sum(bd.hi, rh, rh, t);
+          rl += t + bd.lo;
+          eb = bexp(bv);
+        }
+      } else if (id == src) {
         float t;
         two_sum(1.f, rh, rh, t);
         rl += t;
+        eb = 1023;
       }
       const float rf = rh + rl;
       rr = fmaf(rf, rf, rr);
       int ed = max(etheta, bexp_f(amax));
       const int ec = bexp(xc);
       ed = max(ed, ec ? ec + 2 : 0);
-      if (id == src) ed = max(ed, 1023);
+      if (eb) ed = max(ed, eb);
       const int er = bexp_f(rf);
       if (er) om_e = max(om_e, ed ? er + 1 - ed : 4096);
       const float rv = rf * pre;
@@ -621,7 +651,9 @@ __global__ void k_theta(Geo g, Batch b, const X* __restrict__ x64, const int* __
   if (b.status[rhs] != RHS_FINISHED) return;
   const int f = b.f_begin + rhs % b.nf;
   const bool is_src = f < b.n_src;
-  const int p0 = is_src ? b.n_src : 0, np = is_src ? b.n_det : b.n_src;
+  // a general right-hand side (adjoint field of source f) is weighed against its own source's field
+  const int p0 = b.rhs_slot ? f : (is_src ? b.n_src : 0);
+  const int np = b.rhs_slot ? 1 : (is_src ? b.n_det : b.n_src);
   double th = 0.0;
   if (b.cw_floor > 0.0 && np > 0) {
     const X* x = x64 + (size_t)rhs * g.N;
@@ -1358,23 +1390,34 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_update_roll(Geo g, Batch b, 
 // partials in the same order; gamma_k and alpha_k of iteration k are kept per field (one block
 // writes them) for iteration k + 1. Threads 0..91 form p on the outer ring, threads 172..255 run
 // (A) and (B) on the inner ring as well; the z-neighbours of every column are registers.
-constexpr int BX2 = 40, BY2 = 12;
-constexpr int PL2 = BX2 * BY2;  // cells of one box plane
-constexpr int TPL = TX * TY;    // cells of one tile plane
-template <int RP>
-__host__ __device__ constexpr uint32_t sw_slab_bytes() {  // r | p | e
-  return (uint32_t)((2 * RP * PL2 + RP * TPL) * sizeof(float));
-}
-template <int RP, int RS>
-constexpr size_t sw_smem() { return (size_t)RS * sw_slab_bytes<RP>() + 128; }
-constexpr int RING1 = 84, RING2 = 92, RING1_T0 = NTHREADS - RING1;
+constexpr int BX2 = 40;  // x extent of a box: x0 - 4 .. x0 + 35 (the 16-byte rule rounds x0 - 2 down)
 
-// (hx, hy) of ring cell q, relative to the tile origin: ring 1 (one cell out) or ring 2 (two)
-__device__ __forceinline__ void ring_cell(int ring, int q, int& hx, int& hy) {
-  const int w = TX + 2 * ring, h = TY + 2 * ring;  // extent of the ring's outline
+// Tile shape of the single sweep: 32 x (8 CY) cells, one thread per column of 8-row groups (a thread
+// owns the CY cells (tx, ty + 8 c)); boxes of the tile plus a two-cell ring, 40 x (8 CY + 4) cells.
+template <int CY>
+struct SweepShape {
+  static constexpr int TYB = TY * CY;               // tile rows
+  static constexpr int BYB = TYB + 4;               // box rows
+  static constexpr int PLANE = BX2 * BYB;           // cells of one box plane
+  static constexpr int TILE_PLANE = TX * TYB;       // cells of one tile plane
+  static constexpr int RING2 = 2 * (TX + 4) + 2 * (TYB + 2);  // outer-ring cells (p only)
+  static constexpr int RING1 = 2 * (TX + 2) + 2 * TYB;        // inner-ring cells (p, s, r, u)
+  static_assert(RING2 <= NTHREADS - RING1, "the two rings go to disjoint threads");
+};
+template <int RP, int CY>
+__host__ __device__ constexpr uint32_t sw_slab_bytes() {  // r | p | e
+  return (uint32_t)((2 * RP * SweepShape<CY>::PLANE + RP * SweepShape<CY>::TILE_PLANE) * sizeof(float));
+}
+template <int RP, int RS, int CY>
+constexpr size_t sw_smem() { return (size_t)RS * sw_slab_bytes<RP, CY>() + 128; }
+
+// (hx, hy) of ring cell q, relative to the tile origin, for a tile of TX x tyb cells: ring 1 (one cell
+// out) or ring 2 (two)
+__device__ __forceinline__ void ring_cell(int ring, int q, int tyb, int& hx, int& hy) {
+  const int w = TX + 2 * ring, h = tyb + 2 * ring;  // extent of the ring's outline
   if (q < 2 * w) {
     hx = q % w - ring;
-    hy = (q < w) ? -ring : TY - 1 + ring;
+    hy = (q < w) ? -ring : tyb - 1 + ring;
   } else {
     q -= 2 * w;
     const int hh = h - 2;
@@ -1402,7 +1445,7 @@ struct SweepShared {
 // iteration `it` (or the cycle's priming pass). Run by all threads of a block; slab is the block's
 // dynamic shared memory rounded to 128 bytes. Returns false when a TMA slab never arrived (the
 // device error flag is then set and the copies issued so far have been waited for).
-template <int RP, int RS, bool PRIME>
+template <int RP, int RS, int CY, bool PRIME>
 __device__ __forceinline__ bool sweep_item(const Geo& g, const Batch& b, const int it, const int item, const int seg,
                                            const LamCoefF* __restrict__ coef_f, const SweepScalars& sc,
                                            const CUtensorMap* mapR0, const CUtensorMap* mapR1,
@@ -1411,15 +1454,21 @@ __device__ __forceinline__ bool sweep_item(const Geo& g, const Batch& b, const i
                                            float* __restrict__ P0, float* __restrict__ P1, float* __restrict__ Eo,
                                            float* slab, SweepShared<RS>& sh) {
   static_assert(RP >= 3 && RS >= 3, "stage C reads u one slab back; a buffer is refilled two slabs after its own");
-  constexpr int SLAB = 2 * RP * PL2 + RP * TPL;  // floats per slab buffer
+  // Products that later sums take in are rounded on their own (__fmul_rn is never merged into a
+  // multiply-add), so every slab shape, tile shape and launch form rounds alike: the same bits.
+  using Sh = SweepShape<CY>;
+  constexpr int PLB = Sh::PLANE, TPB = Sh::TILE_PLANE;
+  constexpr int SLAB = 2 * RP * PLB + RP * TPB;  // floats per slab buffer
   uint64_t* mbar = sh.mbar;
   double* sm = sh.sm;
-  const int ncol = g.ntx * g.nty;
+  const int nty2 = (g.nty + CY - 1) / CY;  // tile rows of this shape
+  const int ncol = g.ntx * nty2;
   const int nseg = (g.nz + seg - 1) / seg;
   const int rhs = item / (ncol * nseg);
   const int rem = item - rhs * ncol * nseg;
   const int zs = rem / ncol, col = rem - zs * ncol;
-  const int x0 = (col % g.ntx) * TX, y0 = (col / g.ntx) * TY;
+  const int cx = col % g.ntx, cy2 = col / g.ntx;
+  const int x0 = cx * TX, y0 = cy2 * Sh::TYB;
   const int z0 = zs * seg, z1 = min(z0 + seg, g.nz);
   const bool lead = (col == 0 && zs == 0);
   const int T_ = g.ntiles;
@@ -1431,15 +1480,15 @@ __device__ __forceinline__ bool sweep_item(const Geo& g, const Batch& b, const i
   const int nfirst = min(RS, nslab);
   const CUtensorMap* mr = par ? mapR1 : mapR0;
   const CUtensorMap* mp = par ? mapP0 : mapP1;  // p_(k-1) was written by iteration k-1 into P[k & 1 ^ 1]
-  const uint32_t tx_bytes = first ? RP * PL2 * 4u : (2u * RP * PL2 + RP * TPL) * 4u;
+  const uint32_t tx_bytes = first ? RP * PLB * 4u : (2u * RP * PLB + RP * TPB) * 4u;
   auto issue = [&](int q) {
     float* dst = slab + (q % RS) * SLAB;
     const int zq = z0 - 2 + q * RP;
     mbar_expect_tx(&mbar[q % RS], tx_bytes);
     tma_load_4d(dst, mr, &mbar[q % RS], x0 - 4, y0 - 2, zq, rhs);
     if (!first) {
-      tma_load_4d(dst + RP * PL2, mp, &mbar[q % RS], x0 - 4, y0 - 2, zq, rhs);
-      tma_load_4d(dst + 2 * RP * PL2, mapE, &mbar[q % RS], x0, y0, zq, rhs);
+      tma_load_4d(dst + RP * PLB, mp, &mbar[q % RS], x0 - 4, y0 - 2, zq, rhs);
+      tma_load_4d(dst + 2 * RP * PLB, mapE, &mbar[q % RS], x0, y0, zq, rhs);
     }
   };
   __syncthreads();  // the previous item's threads are done with the barriers re-initialised below
@@ -1507,22 +1556,28 @@ __device__ __forceinline__ bool sweep_item(const Geo& g, const Batch& b, const i
   }
   const float alpha = sh.alpha, beta = sh.beta;
 
-  // own column
+  // own cells: column (tx, ty + 8 c) of the tile for c < CY
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-  const int i = x0 + tx, j = y0 + ty;
-  const bool in = (i < g.nx) && (j < g.ny);
-  const int ob = (ty + 2) * BX2 + tx + 4;
-  float dd[4], di[4];
-  col_diag(cf, (i == 0) | ((i == g.nx - 1) << 1) | ((j == 0) << 2) | ((j == g.ny - 1) << 3), dd, di);
-  // ring cells: outer ring (p only) for threads 0..91, inner ring (p, s, r, u) for threads 172..255
-  const bool has2 = threadIdx.x < RING2;
-  const bool has1 = threadIdx.x >= RING1_T0;
+  const int i = x0 + tx;
+  bool in[CY];
+  int ob[CY];
+  float dd[CY][4], di[CY][4];
+#pragma unroll
+  for (int c = 0; c < CY; ++c) {
+    const int j = y0 + ty + TY * c;
+    in[c] = (i < g.nx) && (j < g.ny);
+    ob[c] = (ty + TY * c + 2) * BX2 + tx + 4;
+    col_diag(cf, (i == 0) | ((i == g.nx - 1) << 1) | ((j == 0) << 2) | ((j == g.ny - 1) << 3), dd[c], di[c]);
+  }
+  // ring cells: outer ring (p only) for the first threads, inner ring (p, s, r, u) for the last
+  const bool has2 = threadIdx.x < Sh::RING2;
+  const bool has1 = threadIdx.x >= NTHREADS - Sh::RING1;
   int h2b = 0, h1b = 0;
   bool h1in = false;
   float h2di[4] = {}, h1d[4] = {}, h1di[4] = {};
   if (has2) {
     int hx, hy;
-    ring_cell(2, threadIdx.x, hx, hy);
+    ring_cell(2, threadIdx.x, Sh::TYB, hx, hy);
     h2b = (hy + 2) * BX2 + hx + 4;
     const int gi = x0 + hx, gj = y0 + hy;
     float d4[4];
@@ -1530,7 +1585,7 @@ __device__ __forceinline__ bool sweep_item(const Geo& g, const Batch& b, const i
   }
   if (has1) {
     int hx, hy;
-    ring_cell(1, threadIdx.x - RING1_T0, hx, hy);
+    ring_cell(1, threadIdx.x - (NTHREADS - Sh::RING1), Sh::TYB, hx, hy);
     h1b = (hy + 2) * BX2 + hx + 4;
     const int gi = x0 + hx, gj = y0 + hy;
     h1in = gi >= 0 && gi < g.nx && gj >= 0 && gj < g.ny;
@@ -1538,13 +1593,20 @@ __device__ __forceinline__ bool sweep_item(const Geo& g, const Batch& b, const i
   }
   const int plane_n = g.nx * g.ny;
   // the column's cells in this field's part of e, r_(k+1) and p_k (offsets within a field fit 32 bits)
-  const size_t fbase = (size_t)rhs * g.N + (size_t)j * g.nx + i;
+  const size_t fbase = (size_t)rhs * g.N + (size_t)(y0 + ty) * g.nx + i;
   float* const eo = Eo + fbase;
   float* const rn_out = (par ? R0 : R1) + fbase;  // r_(k+1)
   float* const pn_out = (par ? P1 : P0) + fbase;  // p_k (read back as p_(k-1) from the other buffer)
-  // z-queues: p of the own column and inner-ring cell (two planes back), u and r_(k+1) of the own column
-  float pq2 = 0.f, pq1 = 0.f, hq2 = 0.f, hq1 = 0.f, uq2 = 0.f, uq1 = 0.f, rq1 = 0.f;
-  float ag = 0.f, ad = 0.f, ar = 0.f;
+  const int row8 = TY * g.nx;                     // offset of the cell eight rows further
+  // z-queues: p of the own cells and inner-ring cell (two planes back), u and r_(k+1) of the own cells
+  float pq2[CY], pq1[CY], uq2[CY], uq1[CY], rq1[CY];
+#pragma unroll
+  for (int c = 0; c < CY; ++c) pq2[c] = pq1[c] = uq2[c] = uq1[c] = rq1[c] = 0.f;
+  float hq2 = 0.f, hq1 = 0.f;
+  // inner products per 32 x 8 column (each column's sums in the same order whatever CY is)
+  float ag[CY], ad[CY], ar[CY];
+#pragma unroll
+  for (int c = 0; c < CY; ++c) ag[c] = ad[c] = ar[c] = 0.f;
   const float* prev = slab;
   // One slab: (A), barrier, (B), barrier, (C). EDGE: a slab whose planes touch a grid z-face or
   // lie outside the block's segment (per-plane checks, z-face diagonals); otherwise every plane of
@@ -1562,28 +1624,35 @@ __device__ __forceinline__ bool sweep_item(const Geo& g, const Batch& b, const i
     const int zA = z0 - 2 + q * RP;  // plane of (A)'s first slab plane
     auto zcase = [&](int zt) { return EDGE ? ((zt == 0) | ((zt == g.nz - 1) << 1)) : 0; };
     auto dsel = [&](const float (&v)[4], int zb) { return EDGE ? pick4(v, zb) : v[0]; };
-    float pA[RP], hA[RP];
+    float pA[CY][RP], hA[RP];
 #pragma unroll
-    for (int u = 0; u < RP; ++u) pA[u] = hA[u] = 0.f;
+    for (int u = 0; u < RP; ++u) {
+      hA[u] = 0.f;
+#pragma unroll
+      for (int c = 0; c < CY; ++c) pA[c][u] = 0.f;
+    }
     // (A) p_k = D^-1 r_k + beta p_(k-1) on the tile and both rings (zero outside the grid: r and
     // p arrive as zeros there)
     if (!PRIME) {
 #pragma unroll
       for (int u = 0; u < RP; ++u) {
         const int zb = zcase(zA + u);
-        float* rp = cur + u * PL2;
-        float* pp = cur + RP * PL2 + u * PL2;
-        float v = rp[ob] * dsel(di, zb);
-        if (!first) v = fmaf(beta, pp[ob], v);
-        pp[ob] = v;
-        pA[u] = v;
+        float* rp = cur + u * PLB;
+        float* pp = cur + RP * PLB + u * PLB;
+#pragma unroll
+        for (int c = 0; c < CY; ++c) {
+          float v = __fmul_rn(rp[ob[c]], dsel(di[c], zb));
+          if (!first) v = fmaf(beta, pp[ob[c]], v);
+          pp[ob[c]] = v;
+          pA[c][u] = v;
+        }
         if (has2) {
-          float hv = rp[h2b] * dsel(h2di, zb);
+          float hv = __fmul_rn(rp[h2b], dsel(h2di, zb));
           if (!first) hv = fmaf(beta, pp[h2b], hv);
           pp[h2b] = hv;
         }
         if (has1) {
-          float hv = rp[h1b] * dsel(h1di, zb);
+          float hv = __fmul_rn(rp[h1b], dsel(h1di, zb));
           if (!first) hv = fmaf(beta, pp[h1b], hv);
           pp[h1b] = hv;
           hA[u] = hv;
@@ -1601,42 +1670,49 @@ __device__ __forceinline__ bool sweep_item(const Geo& g, const Batch& b, const i
     // every thread is past (C) of slab q - 1, the last reader of slab q - 2: refill its buffer
     if (threadIdx.x == 0 && q >= 2 && q - 2 + RS < nslab) issue(q - 2 + RS);
     // (B) planes zA - 1 .. zA + RP - 2 (the first in the previous slab's buffer)
-    float uB[RP], rB[RP];
+    float uB[CY][RP], rB[CY][RP];
 #pragma unroll
     for (int u = 0; u < RP; ++u) {
       const int zt = zA - 1 + u;
-      uB[u] = 0.f;
-      rB[u] = 0.f;
+#pragma unroll
+      for (int c = 0; c < CY; ++c) uB[c][u] = rB[c][u] = 0.f;
       if (EDGE && (zt < z0 - 1 || zt > z1)) continue;  // not needed by (C)
       const bool zin = !EDGE || (zt >= 0 && zt < g.nz);
       const int zb = zcase(zt);
-      float* rpl = (u == 0) ? const_cast<float*>(prev) + (RP - 1) * PL2 : cur + (u - 1) * PL2;
-      const float* ppl = rpl + RP * PL2;
+      float* rpl = (u == 0) ? const_cast<float*>(prev) + (RP - 1) * PLB : cur + (u - 1) * PLB;
+      const float* ppl = rpl + RP * PLB;
       if (PRIME) {
-        const float rv = rpl[ob];
-        const float uv = (in && zin) ? rv * dsel(di, zb) : 0.f;
-        rpl[ob] = uv;
-        uB[u] = uv;
-        rB[u] = rv;
-        if (has1) rpl[h1b] = (h1in && zin) ? rpl[h1b] * dsel(h1di, zb) : 0.f;
+#pragma unroll
+        for (int c = 0; c < CY; ++c) {
+          const float rv = rpl[ob[c]];
+          const float uv = (in[c] && zin) ? __fmul_rn(rv, dsel(di[c], zb)) : 0.f;
+          rpl[ob[c]] = uv;
+          uB[c][u] = uv;
+          rB[c][u] = rv;
+        }
+        if (has1) rpl[h1b] = (h1in && zin) ? __fmul_rn(rpl[h1b], dsel(h1di, zb)) : 0.f;
         continue;
       }
-      {
-        const float below = (u == 0) ? pq2 : (u == 1 ? pq1 : pA[u - 2]);
-        const float centre = (u == 0) ? pq1 : pA[u - 1];
-        const float sn = (ppl[ob - 1] + ppl[ob + 1]) + (ppl[ob - BX2] + ppl[ob + BX2]) + (below + pA[u]);
-        const float s = fmaf(dsel(dd, zb), centre, -sn);
-        const float rn = fmaf(-alpha, s, rpl[ob]);
-        const float uv = (in && zin) ? rn * dsel(di, zb) : 0.f;
-        rpl[ob] = uv;
-        uB[u] = uv;
-        rB[u] = rn;
-        if (in && (!EDGE || (zt >= z0 && zt < z1))) {
-          const float* epl = (u == 0) ? prev + 2 * RP * PL2 + (RP - 1) * TPL : cur + 2 * RP * PL2 + (u - 1) * TPL;
-          const int off = zt * plane_n;
-          eo[off] = first ? alpha * centre : fmaf(alpha, centre, epl[threadIdx.x]);
-          pn_out[off] = centre;
-          rn_out[off] = rn;
+      const bool wr = !EDGE || (zt >= z0 && zt < z1);
+      const int off = zt * plane_n;
+#pragma unroll
+      for (int c = 0; c < CY; ++c) {
+        const int o = ob[c];
+        const float below = (u == 0) ? pq2[c] : (u == 1 ? pq1[c] : pA[c][u - 2]);
+        const float centre = (u == 0) ? pq1[c] : pA[c][u - 1];
+        const float sn = (ppl[o - 1] + ppl[o + 1]) + (ppl[o - BX2] + ppl[o + BX2]) + (below + pA[c][u]);
+        const float s = fmaf(dsel(dd[c], zb), centre, -sn);
+        const float rn = fmaf(-alpha, s, rpl[o]);
+        const float uv = (in[c] && zin) ? __fmul_rn(rn, dsel(di[c], zb)) : 0.f;
+        rpl[o] = uv;
+        uB[c][u] = uv;
+        rB[c][u] = rn;
+        if (in[c] && wr) {
+          const float* epl = (u == 0) ? prev + 2 * RP * PLB + (RP - 1) * TPB : cur + 2 * RP * PLB + (u - 1) * TPB;
+          const int oc = off + c * row8;
+          eo[oc] = first ? __fmul_rn(alpha, centre) : fmaf(alpha, centre, epl[threadIdx.x + c * NTHREADS]);
+          pn_out[oc] = centre;
+          rn_out[oc] = rn;
         }
       }
       if (has1) {
@@ -1645,37 +1721,43 @@ __device__ __forceinline__ bool sweep_item(const Geo& g, const Batch& b, const i
         const float sn = (ppl[h1b - 1] + ppl[h1b + 1]) + (ppl[h1b - BX2] + ppl[h1b + BX2]) + (below + hA[u]);
         const float s = fmaf(dsel(h1d, zb), centre, -sn);
         const float rn = fmaf(-alpha, s, rpl[h1b]);
-        rpl[h1b] = (h1in && zin) ? rn * dsel(h1di, zb) : 0.f;
+        rpl[h1b] = (h1in && zin) ? __fmul_rn(rn, dsel(h1di, zb)) : 0.f;
       }
     }
     // the in-place writes are ordered before the copies that later refill these buffers
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     // (C) planes zA - 2 .. zA + RP - 3: w = Ahat u and the inner products
-    if (in) {
 #pragma unroll
-      for (int u = 0; u < RP; ++u) {
-        const int zt = zA - 2 + u;
-        if (EDGE && (zt < z0 || zt >= z1)) continue;
-        const int zb = zcase(zt);
-        const float* upl = (u <= 1) ? prev + (RP - 2 + u) * PL2 : cur + (u - 2) * PL2;
-        const float below = (u == 0) ? uq2 : (u == 1 ? uq1 : uB[u - 2]);
-        const float centre = (u == 0) ? uq1 : uB[u - 1];
-        const float rn = (u == 0) ? rq1 : rB[u - 1];
-        const float sn = (upl[ob - 1] + upl[ob + 1]) + (upl[ob - BX2] + upl[ob + BX2]) + (below + uB[u]);
-        const float w = fmaf(dsel(dd, zb), centre, -sn);
-        ag = fmaf(rn, centre, ag);
-        ad = fmaf(w, centre, ad);
-        ar = fmaf(rn, rn, ar);
+    for (int u = 0; u < RP; ++u) {
+      const int zt = zA - 2 + u;
+      if (EDGE && (zt < z0 || zt >= z1)) continue;
+      const int zb = zcase(zt);
+      const float* upl = (u <= 1) ? prev + (RP - 2 + u) * PLB : cur + (u - 2) * PLB;
+#pragma unroll
+      for (int c = 0; c < CY; ++c) {
+        if (!in[c]) continue;
+        const int o = ob[c];
+        const float below = (u == 0) ? uq2[c] : (u == 1 ? uq1[c] : uB[c][u - 2]);
+        const float centre = (u == 0) ? uq1[c] : uB[c][u - 1];
+        const float rn = (u == 0) ? rq1[c] : rB[c][u - 1];
+        const float sn = (upl[o - 1] + upl[o + 1]) + (upl[o - BX2] + upl[o + BX2]) + (below + uB[c][u]);
+        const float w = fmaf(dsel(dd[c], zb), centre, -sn);
+        ag[c] = fmaf(rn, centre, ag[c]);
+        ad[c] = fmaf(w, centre, ad[c]);
+        ar[c] = fmaf(rn, rn, ar[c]);
       }
     }
-    pq2 = pA[RP - 2];
-    pq1 = pA[RP - 1];
+#pragma unroll
+    for (int c = 0; c < CY; ++c) {
+      pq2[c] = pA[c][RP - 2];
+      pq1[c] = pA[c][RP - 1];
+      uq2[c] = uB[c][RP - 2];
+      uq1[c] = uB[c][RP - 1];
+      rq1[c] = rB[c][RP - 1];
+    }
     hq2 = hA[RP - 2];
     hq1 = hA[RP - 1];
-    uq2 = uB[RP - 2];
-    uq1 = uB[RP - 1];
-    rq1 = rB[RP - 1];
     prev = cur;
     return true;
   };
@@ -1687,24 +1769,47 @@ __device__ __forceinline__ bool sweep_item(const Geo& g, const Batch& b, const i
     const bool ok = interior ? run_slab(q, std::false_type{}) : run_slab(q, std::true_type{});
     if (!ok) return false;
   }
-  float a3[3] = {ag, ad, ar};
-  double o3[3];
-  block_sum<3, float>(a3, o3, sm);
+  float a3[3 * CY];
+#pragma unroll
+  for (int c = 0; c < CY; ++c) {
+    a3[3 * c] = ag[c];
+    a3[3 * c + 1] = ad[c];
+    a3[3 * c + 2] = ar[c];
+  }
+  double o3[3 * CY];
+  block_sum<3 * CY, float>(a3, o3, sm);
+  // each 32 x 8 column's sums go to its partial slot of the segment's first 8-plane tile, zeros to
+  // the segment's later tiles (the per-tile layout the per-field sums read)
   const int npar = PRIME ? 0 : (par ^ 1);
   const int nsl = (z1 - z0 + g.tz - 1) / g.tz;
-  if (threadIdx.x < nsl) {
-    const int slot = col + (z0 / g.tz + threadIdx.x) * ncol;
-    const bool z = threadIdx.x == 0;
-    pb[T_ * npar + slot] = z ? o3[0] : 0.0;
-    pb[2 * T_ + T_ * npar + slot] = z ? o3[1] : 0.0;
-    pb[4 * T_ + T_ * npar + slot] = z ? o3[2] : 0.0;
-    if (!PRIME && z && lead) b.iters[rhs] += 1;
+  const int ncols = min(CY, g.nty - cy2 * CY);
+  const int ncol8 = g.ntx * g.nty;
+  if (threadIdx.x < nsl * ncols) {  // zeros for the later tiles of each column
+    const int ct = threadIdx.x / nsl, zt = threadIdx.x - ct * nsl;
+    if (zt > 0) {
+      const int slot = (cy2 * CY + ct) * g.ntx + cx + (z0 / g.tz + zt) * ncol8;
+      pb[T_ * npar + slot] = 0.0;
+      pb[2 * T_ + T_ * npar + slot] = 0.0;
+      pb[4 * T_ + T_ * npar + slot] = 0.0;
+    }
+  }
+  if (threadIdx.x == 0) {  // the sums (valid in thread 0) for the first tile of each column
+#pragma unroll
+    for (int c = 0; c < CY; ++c) {
+      if (c >= ncols) break;
+      const int slot = (cy2 * CY + c) * g.ntx + cx + (z0 / g.tz) * ncol8;
+      pb[T_ * npar + slot] = o3[3 * c];
+      pb[2 * T_ + T_ * npar + slot] = o3[3 * c + 1];
+      pb[4 * T_ + T_ * npar + slot] = o3[3 * c + 2];
+    }
+    if (!PRIME && lead) b.iters[rhs] += 1;
   }
   return true;
+
 }
 
 
-template <int RP, int RS, int MINB, bool PRIME>
+template <int RP, int RS, int CY, int MINB, bool PRIME>
 __global__ void __launch_bounds__(NTHREADS, MINB) k_cg_sweep(Geo g, Batch b, const int* __restrict__ it_dev, int k,
                                                              int seg, const LamCoefF* __restrict__ coef_f,
                                                              SweepScalars sc,
@@ -1719,8 +1824,8 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_cg_sweep(Geo g, Batch b, con
   extern __shared__ unsigned char dsm[];
   __shared__ SweepShared<RS> sh;
   const int it = PRIME ? 0 : *it_dev + k;
-  sweep_item<RP, RS, PRIME>(g, b, it, blockIdx.x, seg, coef_f, sc, &mapR0, &mapR1, &mapP0, &mapP1, &mapE, R0, R1,
-                            P0, P1, Eo, align128<float>(dsm), sh);
+  sweep_item<RP, RS, CY, PRIME>(g, b, it, blockIdx.x, seg, coef_f, sc, &mapR0, &mapR1, &mapP0, &mapP1, &mapE, R0,
+                                R1, P0, P1, Eo, align128<float>(dsm), sh);
 }
 
 // Grid-wide barrier of the persistent iteration (its blocks are co-resident: cooperative launch).
@@ -1789,15 +1894,15 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_cg_persist(Geo g, Batch b, i
   __shared__ SweepShared<RS> sh;
   float* slab = align128<float>(dsm);
   for (int w = blockIdx.x; w < nitems; w += gridDim.x)
-    if (!sweep_item<RP, RS, true>(g, b, 0, w, seg, coef_f, sc, &mapR0, &mapR1, &mapP0, &mapP1, &mapE, R0, R1, P0,
-                                  P1, Eo, slab, sh))
+    if (!sweep_item<RP, RS, 1, true>(g, b, 0, w, seg, coef_f, sc, &mapR0, &mapR1, &mapP0, &mapP1, &mapE, R0, R1,
+                                     P0, P1, Eo, slab, sh))
       return;
   if (!grid_sync(gs, b.err)) return;
   int it = 0;
   for (; it < b.max_inner; ++it) {
     for (int w = blockIdx.x; w < nitems; w += gridDim.x)
-      if (!sweep_item<RP, RS, false>(g, b, it, w, seg, coef_f, sc, &mapR0, &mapR1, &mapP0, &mapP1, &mapE, R0, R1,
-                                     P0, P1, Eo, slab, sh))
+      if (!sweep_item<RP, RS, 1, false>(g, b, it, w, seg, coef_f, sc, &mapR0, &mapR1, &mapP0, &mapP1, &mapE, R0,
+                                        R1, P0, P1, Eo, slab, sh))
         return;
     if (!grid_sync(gs, b.err)) return;
     if (*(volatile int*)&b.counter[1 + it] == 0) break;  // no field iterated: every one has finished
@@ -1871,7 +1976,7 @@ __global__ void k_output(Geo g, Batch b, const X* __restrict__ x64, O* __restric
   for (int rhs = blockIdx.y; rhs < b.nrhs; rhs += gridDim.y) {
     int a = rhs / b.nf;
     int f = b.f_begin + rhs % b.nf;
-    const double sc = b.coef[b.lam0 + a].inv_Dh;
+    const double sc = b.coef[b.lam0 + a].inv_Dh * (b.rhs_scale ? b.rhs_scale[rhs] : 1.0);
     O* out = (f < n_src) ? phi_src + ((size_t)a * n_src + f) * g.N : phi_det + ((size_t)a * n_det + (f - n_src)) * g.N;
     const X* x = x64 + (size_t)rhs * g.N;
     if constexpr (std::is_same<X, cdf32>::value) {
@@ -1946,36 +2051,45 @@ __global__ void k_dsig(const double* __restrict__ dc, const double* __restrict__
 // blocks per SM).
 struct RollVariant {
   int rp, rs;
+  int cy = 1;  // single sweep: cells per thread in y (tiles of 32 x 8 cy)
 };
 constexpr RollVariant ROLL_VARIANTS[HYDOT_ROLL_VARIANTS] = {{4, 4}, {2, 6}, {4, 3}, {4, 5}};
 constexpr RollVariant ROLL_VARIANTS_C[HYDOT_ROLL_VARIANTS] = {{2, 4}, {2, 6}, {4, 3}, {2, 4}};
 
 __host__ __device__ constexpr int rp_index(int rp) { return rp == 2 ? 0 : (rp == 4 ? 1 : 2); }
 
-// Single-sweep variants {planes per slab, slab buffers} (real FP32 fields); bitwise identical results.
-// The blocks-per-SM bounds are what their shared memory allows: {4,3} and {3,4} 58 KB, {3,5} 73 KB
-// (three blocks per SM), {4,4} 78 KB (two).
-constexpr RollVariant SWEEP_VARIANTS[HYDOT_ROLL_VARIANTS] = {{4, 3}, {4, 4}, {3, 4}, {3, 5}};
+// Single-sweep variants {planes per slab, slab buffers, cells per thread in y} (real FP32 fields);
+// bitwise identical results (each 32 x 8 column's inner products are summed in the same order). The
+// blocks-per-SM bounds are what their shared memory allows: 32 x 8 tiles {4,3} and {3,4} 58 KB (three
+// blocks per SM); 32 x 16 tiles {3,3} 76 KB and {4,3} 101 KB (two).
+constexpr RollVariant SWEEP_VARIANTS[HYDOT_ROLL_VARIANTS] = {{4, 3, 1}, {3, 4, 1}, {3, 3, 2}, {4, 3, 2}};
 __host__ __device__ constexpr int sw_index(int rp) { return rp == 3 ? 0 : 1; }
 
-template <int RP, int RS, int MB>
+template <int RP, int RS, int CY, int MB>
 int sweep_attrs(hydot_ctx* ctx) {
-  HYDOT_CUDA_TRY(ctx, raise_smem_limit(k_cg_sweep<RP, RS, MB, false>, sw_smem<RP, RS>()));
-  HYDOT_CUDA_TRY(ctx, raise_smem_limit(k_cg_sweep<RP, RS, MB, true>, sw_smem<RP, RS>()));
+  HYDOT_CUDA_TRY(ctx, raise_smem_limit(k_cg_sweep<RP, RS, CY, MB, false>, sw_smem<RP, RS, CY>()));
+  HYDOT_CUDA_TRY(ctx, raise_smem_limit(k_cg_sweep<RP, RS, CY, MB, true>, sw_smem<RP, RS, CY>()));
   return HYDOT_OK;
+}
+
+// Work items of the single sweep: (field, 32 x 8CY column, z-segment).
+unsigned sweep_items(const hydot_ctx* ctx, const Geo& g, const Batch& b, int cy) {
+  return (unsigned)((long long)b.nrhs * g.ntx * ((g.nty + cy - 1) / cy) * ((g.nz + ctx->dir_seg - 1) / ctx->dir_seg));
 }
 
 // One single-sweep iteration (k_off: offset of the iteration in its group; the group's base index
 // is on the device) or, with PRIME, the cycle's priming pass.
-template <int RP, int RS, int MB, bool PRIME>
-void sweep_launch(hydot_ctx* ctx, const Geo& g, const Batch& b, int k_off, unsigned nrb) {
+template <int RP, int RS, int CY, int MB, bool PRIME>
+void sweep_launch(hydot_ctx* ctx, const Geo& g, const Batch& b, int k_off) {
   const int d = sw_index(RP);
   const SweepScalars sc{ctx->d_cgsc, ctx->max_fields};
+  const CUtensorMap* mr = CY == 1 ? ctx->tm_r2[d] : ctx->tm_r4[d];
+  const CUtensorMap* mp = CY == 1 ? ctx->tm_p2[d] : ctx->tm_p4[d];
+  const CUtensorMap& me = CY == 1 ? ctx->tm_e2[d] : ctx->tm_e4[d];
   cudaEvent_t t0 = timer_begin(ctx);
-  k_cg_sweep<RP, RS, MB, PRIME><<<nrb, NTHREADS, sw_smem<RP, RS>(), ctx->stream>>>(
-      g, b, ctx->d_it, k_off, ctx->dir_seg, ctx->d_coef_f, sc, ctx->tm_r2[d][0], ctx->tm_r2[d][1], ctx->tm_p2[d][0],
-      ctx->tm_p2[d][1], ctx->tm_e2[d], (float*)ctx->d_r, (float*)ctx->d_r2, (float*)ctx->d_p[0], (float*)ctx->d_p[1],
-      (float*)ctx->d_e);
+  k_cg_sweep<RP, RS, CY, MB, PRIME><<<sweep_items(ctx, g, b, CY), NTHREADS, sw_smem<RP, RS, CY>(), ctx->stream>>>(
+      g, b, ctx->d_it, k_off, ctx->dir_seg, ctx->d_coef_f, sc, mr[0], mr[1], mp[0], mp[1], me, (float*)ctx->d_r,
+      (float*)ctx->d_r2, (float*)ctx->d_p[0], (float*)ctx->d_p[1], (float*)ctx->d_e);
   ++ctx->launches;
   timer_end(ctx, t0, PRIME ? HYDOT_KERNEL_PRIME : HYDOT_KERNEL_SWEEP, 0.0);
 }
@@ -1986,7 +2100,7 @@ constexpr uint32_t GRID_WAIT_POLLS = 1u << 24;  // about a second of 64 ns pause
 
 int persist_setup(hydot_ctx* ctx) {
   auto kern = k_cg_persist<PERSIST_RP, PERSIST_RS, PERSIST_MB>;
-  const size_t smem = sw_smem<PERSIST_RP, PERSIST_RS>();
+  const size_t smem = sw_smem<PERSIST_RP, PERSIST_RS, 1>();
   HYDOT_CUDA_TRY(ctx, raise_smem_limit(kern, smem));
   int per_sm = 0, sms = 0, coop = 0;
   HYDOT_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NTHREADS, smem));
@@ -2021,7 +2135,7 @@ int persist_launch(hydot_ctx* ctx, const Geo& g, const Batch& b, unsigned nitems
   HYDOT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_gsync, 0, 2 * sizeof(unsigned), ctx->stream));
   HYDOT_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((const void*)k_cg_persist<PERSIST_RP, PERSIST_RS, PERSIST_MB>,
                                                   dim3(grid), dim3(NTHREADS), args,
-                                                  sw_smem<PERSIST_RP, PERSIST_RS>(), ctx->stream));
+                                                  sw_smem<PERSIST_RP, PERSIST_RS, 1>(), ctx->stream));
   ++ctx->launches;
   HYDOT_CUDA_TRY(ctx, cudaMemcpyAsync(iters, ctx->d_it, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   HYDOT_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
@@ -2043,12 +2157,12 @@ void persist_record(hydot_ctx* ctx, int mode, double ms, double cell_iters) {
 }
 
 template <bool PRIME>
-void sweep_dispatch(hydot_ctx* ctx, int v, const Geo& g, const Batch& b, int k_off, unsigned nrb) {
+void sweep_dispatch(hydot_ctx* ctx, int v, const Geo& g, const Batch& b, int k_off) {
   switch (v) {
-    case 1: sweep_launch<4, 4, 2, PRIME>(ctx, g, b, k_off, nrb); break;
-    case 2: sweep_launch<3, 4, 3, PRIME>(ctx, g, b, k_off, nrb); break;
-    case 3: sweep_launch<3, 5, 3, PRIME>(ctx, g, b, k_off, nrb); break;
-    default: sweep_launch<4, 3, 3, PRIME>(ctx, g, b, k_off, nrb); break;
+    case 1: sweep_launch<3, 4, 1, 3, PRIME>(ctx, g, b, k_off); break;
+    case 2: sweep_launch<3, 3, 2, 2, PRIME>(ctx, g, b, k_off); break;
+    case 3: sweep_launch<4, 3, 2, 2, PRIME>(ctx, g, b, k_off); break;
+    default: sweep_launch<4, 3, 1, 3, PRIME>(ctx, g, b, k_off); break;
   }
 }
 
@@ -2084,7 +2198,7 @@ void roll_iteration(hydot_ctx* ctx, const Geo& g, const Batch& b, int it, unsign
 void roll_dispatch(hydot_ctx* ctx, int v, const Geo& g, const Batch& b, int it, unsigned nrb, void* Ev, void* R,
                    void* const* P) {
   if (ctx->use_sweep) {
-    sweep_dispatch<false>(ctx, v, g, b, it % POLL_GROUP, nrb);
+    sweep_dispatch<false>(ctx, v, g, b, it % POLL_GROUP);
     return;
   }
   if (ctx->cplx) {
@@ -2112,10 +2226,10 @@ void roll_dispatch(hydot_ctx* ctx, int v, const Geo& g, const Batch& b, int it, 
 
 int roll_setup(hydot_ctx* ctx) {
   if (ctx->use_sweep) {
-    int rc = sweep_attrs<4, 3, 3>(ctx);
-    if (!rc) rc = sweep_attrs<4, 4, 2>(ctx);
-    if (!rc) rc = sweep_attrs<3, 4, 3>(ctx);
-    if (!rc) rc = sweep_attrs<3, 5, 3>(ctx);
+    int rc = sweep_attrs<4, 3, 1, 3>(ctx);
+    if (!rc) rc = sweep_attrs<3, 4, 1, 3>(ctx);
+    if (!rc) rc = sweep_attrs<3, 3, 2, 2>(ctx);
+    if (!rc) rc = sweep_attrs<4, 3, 2, 2>(ctx);
     return rc;
   }
   if (ctx->cplx) {
@@ -2232,10 +2346,25 @@ int inner_graph_launch(hydot_ctx* ctx, const Geo& g, const Batch& b, int variant
   return HYDOT_OK;
 }
 
+// A general right-hand side for run_solve (adjoint solves): see Batch.
+struct GeneralRhs {
+  const int* slot;
+  const double* w;
+  const double* scale;
+  int n_cells;
+};
+
 template <typename T, typename X, typename O>
-int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_stats* st) {
+int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_stats* st,
+              const GeneralRhs* gr = nullptr) {
   Geo g = make_geo(ctx);
   Batch b{};
+  if (gr) {
+    b.rhs_slot = gr->slot;
+    b.rhs_w = gr->w;
+    b.rhs_scale = gr->scale;
+    b.n_rhs_cells = gr->n_cells;
+  }
   b.coef = ctx->d_coef;
   b.optode = ctx->d_optode;
   b.lam0 = lam0;
@@ -2288,7 +2417,10 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
 
   if constexpr (std::is_same<X, double>::value || std::is_same<X, df32>::value) {
     constexpr bool df = std::is_same<X, df32>::value;
-    if (ctx->deflation_k > 0) {
+    if (gr) {
+      // the starting subspaces are built for the one-hot optode right-hand sides: start from zero
+      HYDOT_CUDA_TRY(ctx, cudaMemsetAsync(x64, 0, sizeof(X) * (size_t)b.nrhs * g.N, s));
+    } else if (ctx->deflation_k > 0) {
       // Galerkin initial guess from the recycled subspace (shared by all wavelengths)
       int rc = deflate_initial_guess(ctx, lam0, b.f_begin, b.nf, b.nrhs, x64, df);
       if (rc) return rc;
@@ -2368,7 +2500,7 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
     }
     if (roll && ctx->use_sweep && !persistent) {
       // the cycle's first inner products (gamma_0, delta_0, ||r_0||^2) from r_0
-      sweep_dispatch<true>(ctx, roll_pick(ctx), g, b, 0, nrb);
+      sweep_dispatch<true>(ctx, roll_pick(ctx), g, b, 0);
       if (ctx->timer.on) ctx->timer.bytes[HYDOT_KERNEL_PRIME] += (double)prev_active * (double)g.N * sizeof(T);
       HYDOT_CUDA_TRY(ctx, cudaGetLastError());
     }
@@ -2621,19 +2753,25 @@ int solver_alloc(hydot_ctx* ctx) {
   if (ctx->use_tma) {
     int rc = roll_setup(ctx);
     if (!rc && ctx->sweep_ok && !ctx->use_sweep) {  // the sweep kernels also serve the priming pass
-      rc = sweep_attrs<4, 3, 3>(ctx);
-      if (!rc) rc = sweep_attrs<4, 4, 2>(ctx);
-      if (!rc) rc = sweep_attrs<3, 4, 3>(ctx);
-      if (!rc) rc = sweep_attrs<3, 5, 3>(ctx);
+      rc = sweep_attrs<4, 3, 1, 3>(ctx);
+      if (!rc) rc = sweep_attrs<3, 4, 1, 3>(ctx);
+      if (!rc) rc = sweep_attrs<3, 3, 2, 2>(ctx);
+      if (!rc) rc = sweep_attrs<4, 3, 2, 2>(ctx);
     }
     if (!rc && ctx->sweep_ok) rc = persist_setup(ctx);
     for (int d = 0; d < 2 && !rc && ctx->sweep_ok; ++d) {
       const int bz = 3 + d;
-      rc = encode_field_map(ctx, ctx->d_r, &ctx->tm_r2[d][0], BX2, BY2, bz);
-      if (!rc) rc = encode_field_map(ctx, ctx->d_r2, &ctx->tm_r2[d][1], BX2, BY2, bz);
-      if (!rc) rc = encode_field_map(ctx, ctx->d_p[0], &ctx->tm_p2[d][0], BX2, BY2, bz);
-      if (!rc) rc = encode_field_map(ctx, ctx->d_p[1], &ctx->tm_p2[d][1], BX2, BY2, bz);
+      constexpr int B1 = SweepShape<1>::BYB, B2 = SweepShape<2>::BYB;
+      rc = encode_field_map(ctx, ctx->d_r, &ctx->tm_r2[d][0], BX2, B1, bz);
+      if (!rc) rc = encode_field_map(ctx, ctx->d_r2, &ctx->tm_r2[d][1], BX2, B1, bz);
+      if (!rc) rc = encode_field_map(ctx, ctx->d_p[0], &ctx->tm_p2[d][0], BX2, B1, bz);
+      if (!rc) rc = encode_field_map(ctx, ctx->d_p[1], &ctx->tm_p2[d][1], BX2, B1, bz);
       if (!rc) rc = encode_field_map(ctx, ctx->d_e, &ctx->tm_e2[d], TX, TY, bz);
+      if (!rc) rc = encode_field_map(ctx, ctx->d_r, &ctx->tm_r4[d][0], BX2, B2, bz);
+      if (!rc) rc = encode_field_map(ctx, ctx->d_r2, &ctx->tm_r4[d][1], BX2, B2, bz);
+      if (!rc) rc = encode_field_map(ctx, ctx->d_p[0], &ctx->tm_p4[d][0], BX2, B2, bz);
+      if (!rc) rc = encode_field_map(ctx, ctx->d_p[1], &ctx->tm_p4[d][1], BX2, B2, bz);
+      if (!rc) rc = encode_field_map(ctx, ctx->d_e, &ctx->tm_e4[d], TX, 2 * TY, bz);
     }
     // per slab depth (2, 4, 8 planes): halo slabs of r and p (pass 1 reads r and p_old, pass 2 reads
     // p_new), plain slabs of e and r
@@ -2667,6 +2805,9 @@ void solver_free(hydot_ctx* ctx) {
   cudaFree(ctx->d_r2);
   cudaFree(ctx->d_cgsc);
   cudaFree(ctx->d_gsync);
+  cudaFree(ctx->d_rhs_slot);
+  cudaFree(ctx->d_rhs_w);
+  cudaFree(ctx->d_rhs_scale);
   cudaFree(ctx->d_e);
   cudaFree(ctx->d_r);
   cudaFree(ctx->d_p[0]);
@@ -2789,6 +2930,65 @@ int get_tuning_impl(const hydot_ctx* ctx, int* variant, int* planes, int* buffer
       ns_per_cell[v] = ctx->tune.cells[v] > 0.0 ? 1e6 * ctx->tune.ms[v] / ctx->tune.cells[v] : 0.0;
   }
   return HYDOT_OK;
+}
+
+namespace {
+// w[rhs][d] = y[(s*nd + d)*nlam + a] / |w[rhs]|_2 and scale[rhs] = |w[rhs]|_2 for rhs = a*ns + s: the
+// adjoint right-hand side sum_d y[s,d,lambda] e_d of source s at wavelength a of the slice.
+template <typename Y>
+__global__ void k_adjoint_weights(const Y* __restrict__ y, int nlam, int ns, int nd, double* __restrict__ w,
+                                  double* __restrict__ scale) {
+  const int rhs = blockIdx.x * blockDim.x + threadIdx.x;
+  if (rhs >= nlam * ns) return;
+  const int a = rhs / ns, s = rhs - a * ns;
+  double n2 = 0.0;
+  for (int d = 0; d < nd; ++d) {
+    const double v = (double)y[((size_t)s * nd + d) * nlam + a];
+    n2 += v * v;
+  }
+  const double n = sqrt(n2);
+  const double inv = n > 0.0 ? 1.0 / n : 0.0;
+  for (int d = 0; d < nd; ++d) w[(size_t)rhs * nd + d] = (double)y[((size_t)s * nd + d) * nlam + a] * inv;
+  scale[rhs] = n;
+}
+
+// slot[x] = d at the cell of detector d, -1 elsewhere
+__global__ void k_detector_slots(const int* __restrict__ optode, int ns, int nd, int* __restrict__ slot) {
+  const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d < nd) slot[optode[ns + d]] = d;
+}
+}  // namespace
+
+int solve_adjoint_impl(hydot_ctx* ctx, int lam0, int nlam, const void* y, void* psi, hydot_stats* st) {
+  if (ctx->cplx) return fail(ctx, HYDOT_ERR_STATE, "adjoint solves are available for continuous-wave (real) fields only");
+  if (ctx->n_src < 1 || ctx->n_det < 1) return fail(ctx, HYDOT_ERR_STATE, "adjoint solves need sources and detectors");
+  if (!y || !psi) return fail(ctx, HYDOT_ERR_ARG, "null pointer");
+  if (lam0 < 0 || nlam < 1 || lam0 + nlam > ctx->n_lambda) return fail(ctx, HYDOT_ERR_ARG, "wavelength slice out of range");
+  if ((long long)nlam * ctx->n_src > ctx->max_fields)
+    return fail(ctx, HYDOT_ERR_ARG, "nlam * n_src exceeds the fields the workspace holds");
+  cudaStream_t s = ctx->stream;
+  if (!ctx->d_rhs_slot) {
+    HYDOT_CUDA_TRY(ctx, cudaMalloc(&ctx->d_rhs_slot, sizeof(int) * (size_t)ctx->N));
+    HYDOT_CUDA_TRY(ctx, cudaMalloc(&ctx->d_rhs_w, sizeof(double) * (size_t)ctx->max_fields * ctx->n_det));
+    HYDOT_CUDA_TRY(ctx, cudaMalloc(&ctx->d_rhs_scale, sizeof(double) * (size_t)ctx->max_fields));
+    HYDOT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_rhs_slot, 0xff, sizeof(int) * (size_t)ctx->N, s));
+    k_detector_slots<<<(ctx->n_det + 127) / 128, 128, 0, s>>>(ctx->d_optode, ctx->n_src, ctx->n_det, ctx->d_rhs_slot);
+    ++ctx->launches;
+    HYDOT_CUDA_TRY(ctx, cudaGetLastError());
+  }
+  const int nrhs = nlam * ctx->n_src;
+  const bool mixed = ctx->precision == HYDOT_MIXED;
+  if (mixed)
+    k_adjoint_weights<float><<<(nrhs + 127) / 128, 128, 0, s>>>((const float*)y, nlam, ctx->n_src, ctx->n_det,
+                                                                ctx->d_rhs_w, ctx->d_rhs_scale);
+  else
+    k_adjoint_weights<double><<<(nrhs + 127) / 128, 128, 0, s>>>((const double*)y, nlam, ctx->n_src, ctx->n_det,
+                                                                 ctx->d_rhs_w, ctx->d_rhs_scale);
+  ++ctx->launches;
+  HYDOT_CUDA_TRY(ctx, cudaGetLastError());
+  const GeneralRhs gr{ctx->d_rhs_slot, ctx->d_rhs_w, ctx->d_rhs_scale, ctx->n_det};
+  if (mixed) return run_solve<float, df32, float>(ctx, lam0, nlam, (float*)psi, (float*)nullptr, st, &gr);
+  return run_solve<double, double, double>(ctx, lam0, nlam, (double*)psi, (double*)nullptr, st, &gr);
 }
 
 int solve_fields_impl(hydot_ctx* ctx, int lam0, int nlam, void* phi_src, void* phi_det, hydot_stats* st) {

@@ -289,7 +289,8 @@ def test_roll_variants_bitwise_identical_and_autotuner_settles(hd, oracle_fields
     assert tu["variant"] in range(4)
     assert all(v["ns_per_cell"] > 0 for v in tu["variants"])
     # slab shapes {planes, buffers} of the two-pass and the single-sweep forms
-    expect = [(4, 3), (4, 4), (3, 4), (3, 5)] if sweep == "1" else [(4, 4), (2, 6), (4, 3), (4, 5)]
+    # (single-sweep variants 2 and 3 use 32 x 16 tiles, two cells per thread: the same bits)
+    expect = [(4, 3), (3, 4), (3, 3), (4, 3)] if sweep == "1" else [(4, 4), (2, 6), (4, 3), (4, 5)]
     assert [(v["planes"], v["buffers"]) for v in tu["variants"]] == expect
 
 
@@ -368,7 +369,7 @@ def test_persistent_inner_solve_matches_launched_sweeps(hd, oracle_fields, monke
     bits, and the oracle's fields and Born rows to the stated tolerances."""
     p, (rs, rd) = oracle_fields[name]
     monkeypatch.setenv("HYDOT_SINGLE_SWEEP", "1")
-    monkeypatch.setenv("HYDOT_ROLL_VARIANT", "2")  # the persistent kernel's {3 planes, 4 buffers}
+    monkeypatch.setenv("HYDOT_ROLL_VARIANT", "1")  # the persistent kernel's {3 planes, 4 buffers}
     if seg:
         monkeypatch.setenv("HYDOT_DIR_SEG", seg)
     out = {}
