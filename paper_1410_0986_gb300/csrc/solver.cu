@@ -902,6 +902,11 @@ __device__ __forceinline__ float e_mul(float a, float b) { return a * b; }
 __device__ __forceinline__ float2 e_mul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
+// a b rounded on its own: never merged into a multiply-add (complex: the product as e_mul forms it)
+__device__ __forceinline__ float e_mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float2 e_mul_rn(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
 __device__ __forceinline__ float e_fma(float a, float b, float c) { return fmaf(a, b, c); }  // a b + c
 __device__ __forceinline__ float2 e_fma(float2 a, float2 b, float2 c) {
   return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));
@@ -942,9 +947,9 @@ __device__ __forceinline__ E e_quot(double ar, double ai, double br, double bi) 
 // parameters; the variants compute the same values in the same order (bitwise identical results)
 // and differ only in how much data is in flight per block and how many blocks fit on an SM,
 // which the autotuner times.
-constexpr int PLN = BXT * BYT;  // elements in one box plane
-template <typename E, int RP, int RS>
-constexpr size_t roll_smem() { return (size_t)RS * 2 * RP * PLN * sizeof(E) + 128; }
+constexpr int PLN = BXT * BYT;  // elements in one box plane (32 x 8 tiles)
+template <typename E, int RP, int RS, int CY = 1>
+constexpr size_t roll_smem() { return (size_t)RS * 2 * RP * (BXT * (TY * CY + 2)) * sizeof(E) + 128; }
 
 __device__ __forceinline__ void col_diag(const LamCoefF& cf, int mxy, float (&d)[4], float (&di)[4]) {
 #pragma unroll
@@ -971,7 +976,7 @@ __device__ __forceinline__ E pick4(const E (&v)[4], int zb) {
   return zb == 0 ? v[0] : (zb == 1 ? v[1] : (zb == 2 ? v[2] : v[3]));
 }
 
-template <typename E, int RP, int RS, int MINB>
+template <typename E, int RP, int RS, int CY, int MINB>
 __global__ void __launch_bounds__(NTHREADS, MINB) k_dir_roll(Geo g, Batch b, const int* __restrict__ it_dev, int k,
                                                              int seg,
                                                           const LamCoefF* __restrict__ coef_f,
@@ -980,20 +985,25 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_dir_roll(Geo g, Batch b, con
                                                           E* __restrict__ Pnew) {
   static_assert(RS >= 3, "a slab buffer is refilled two slabs after its own");
   constexpr bool CPLX = !std::is_same<E, float>::value;
+  static_assert(CY == 1 || !CPLX, "complex fields use 32 x 8 tiles");
+  constexpr int TYB = TY * CY;          // tile rows
+  constexpr int PLB = BXT * (TYB + 2);  // elements in one box plane (tile plus a one-cell x-y ring)
   extern __shared__ unsigned char dsm[];
   E* slab = align128<E>(dsm);  // [RS][r -> p_new, p_old][RP planes]
   __shared__ uint64_t mbar[RS];
   __shared__ double sm[96];
   __shared__ E s_beta;
   __shared__ int s_go, s_st;
-  constexpr uint32_t SLAB_BYTES = RP * PLN * sizeof(E);
+  constexpr uint32_t SLAB_BYTES = RP * PLB * sizeof(E);
   const int it = *it_dev + k;  // iteration index: group base on the device + offset in the group
-  const int ncol = g.ntx * g.nty;
+  const int nty2 = (g.nty + CY - 1) / CY;
+  const int ncol = g.ntx * nty2;
   const int nseg = (g.nz + seg - 1) / seg;
   const int rhs = blockIdx.x / (ncol * nseg);
   const int rem = blockIdx.x - rhs * ncol * nseg;
   const int zs = rem / ncol, col = rem - zs * ncol;
-  const int x0 = (col % g.ntx) * TX, y0 = (col / g.ntx) * TY;
+  const int cx = col % g.ntx, cy2 = col / g.ntx;
+  const int x0 = cx * TX, y0 = cy2 * TYB;
   const int z0 = zs * seg, z1 = min(z0 + seg, g.nz);
   const bool lead = (col == 0 && zs == 0);
   const int T_ = g.ntiles;
@@ -1005,10 +1015,10 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_dir_roll(Geo g, Batch b, con
   const int nfirst = min(RS, nslab);
   const uint32_t tx_bytes = (first ? 1u : 2u) * SLAB_BYTES;
   auto issue = [&](int q) {
-    E* dst = slab + (q % RS) * 2 * RP * PLN;
+    E* dst = slab + (q % RS) * 2 * RP * PLB;
     mbar_expect_tx(&mbar[q % RS], tx_bytes);
     tma_load_4d(dst, &mapR, &mbar[q % RS], x0 - 4, y0 - 1, z0 - 1 + q * RP, rhs);
-    if (!first) tma_load_4d(dst + RP * PLN, &mapPold, &mbar[q % RS], x0 - 4, y0 - 1, z0 - 1 + q * RP, rhs);
+    if (!first) tma_load_4d(dst + RP * PLB, &mapPold, &mbar[q % RS], x0 - 4, y0 - 1, z0 - 1 + q * RP, rhs);
   };
   // A field still iterating gets its first slabs requested at once; the convergence test and
   // beta (FP64 sums of the per-tile partials) are formed while they are in flight. A field that
@@ -1068,26 +1078,32 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_dir_roll(Geo g, Batch b, con
   }
   const E beta = s_beta;
 
-  // own column and halo cell of this thread
+  // own cells (tx, ty + 8 c) and the halo cell of this thread
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-  const int i = x0 + tx, j = y0 + ty;
-  const bool in = (i < g.nx) && (j < g.ny);
-  const int ob = (ty + 1) * BXT + tx + 4;
-  E dd[4], di[4];
-  col_diag(cf, (i == 0) | ((i == g.nx - 1) << 1) | ((j == 0) << 2) | ((j == g.ny - 1) << 3), dd, di);
-  // halo: threads 0..63 take the rows y0-1 and y0+8, threads 64..79 the columns x0-1 and x0+32
+  const int i = x0 + tx;
+  bool in[CY];
+  int ob[CY];
+  E dd[CY][4], di[CY][4];
+#pragma unroll
+  for (int c = 0; c < CY; ++c) {
+    const int j = y0 + ty + TY * c;
+    in[c] = (i < g.nx) && (j < g.ny);
+    ob[c] = (ty + TY * c + 1) * BXT + tx + 4;
+    col_diag(cf, (i == 0) | ((i == g.nx - 1) << 1) | ((j == 0) << 2) | ((j == g.ny - 1) << 3), dd[c], di[c]);
+  }
+  // halo: the first 64 threads take the rows y0-1 and y0+TYB, the next 2 TYB the columns x0-1 and x0+32
   const int h = threadIdx.x;
-  const bool has_halo = h < 2 * TX + 2 * TY;
+  const bool has_halo = h < 2 * TX + 2 * TYB;
   int hb = 0;
   E hdi[4] = {};
   if (has_halo) {
     int hx, hy;
     if (h < 2 * TX) {
       hx = h % TX;
-      hy = (h < TX) ? -1 : TY;
+      hy = (h < TX) ? -1 : TYB;
     } else {
-      hx = (h - 2 * TX < TY) ? -1 : TX;
-      hy = (h - 2 * TX) % TY;
+      hx = (h - 2 * TX < TYB) ? -1 : TX;
+      hy = (h - 2 * TX) % TYB;
     }
     hb = (hy + 1) * BXT + hx + 4;
     const int gi = x0 + hx, gj = y0 + hy;
@@ -1095,29 +1111,39 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_dir_roll(Geo g, Batch b, con
     col_diag(cf, (gi == 0) | ((gi == g.nx - 1) << 1) | ((gj == 0) << 2) | ((gj == g.ny - 1) << 3), hd, hdi);
   }
   const int plane_n = g.nx * g.ny;
-  E* out = Pnew + (size_t)rhs * g.N + (size_t)j * g.nx + i;
-  E acc{}, pm2{}, pm1{};      // own p_new of the previous slab's last two planes
-  const E* prev = slab;       // previous slab's p_new planes
+  E* out = Pnew + (size_t)rhs * g.N + (size_t)(y0 + ty) * g.nx + i;
+  const int row8 = TY * g.nx;  // offset of the cell eight rows further
+  // own p_new of the previous slab's last two planes; gamma per 32 x 8 column (each column's sum
+  // in the same order whatever CY is)
+  E acc[CY], pm2[CY], pm1[CY];
+#pragma unroll
+  for (int c = 0; c < CY; ++c) acc[c] = pm2[c] = pm1[c] = E{};
+  const E* prev = slab;  // previous slab's p_new planes
   for (int q = 0; q < nslab; ++q) {
-    E* cur = slab + (q % RS) * 2 * RP * PLN;
+    E* cur = slab + (q % RS) * 2 * RP * PLB;
     const bool ok = mbar_wait_bounded(&mbar[q % RS], (uint32_t)((q / RS) & 1));
     const int t0 = q * RP;
     const int a0 = z0 - 1 + t0;  // first plane formed from this slab
-    E pv[RP];
-    // (B) p_new in place; slabs without a grid z-face take the interior diagonal
+    E pv[CY][RP];
+    // (B) p_new in place; slabs without a grid z-face take the interior diagonal. The product
+    // D^-1 r is rounded on its own (never merged into a multiply-add), so that every variant rounds
+    // alike.
     auto form = [&](auto edge) {
 #pragma unroll
       for (int u = 0; u < RP; ++u) {
         int zb = 0;
         if constexpr (decltype(edge)::value) zb = (a0 + u == 0) | ((a0 + u == g.nz - 1) << 1);
-        E* pl = cur + u * PLN;
-        E v = e_mul(pl[ob], decltype(edge)::value ? pick4(di, zb) : di[0]);
-        if (!first) v = e_fma(beta, pl[RP * PLN + ob], v);
-        pl[ob] = v;
-        pv[u] = v;
+        E* pl = cur + u * PLB;
+#pragma unroll
+        for (int c = 0; c < CY; ++c) {
+          E v = e_mul_rn(pl[ob[c]], decltype(edge)::value ? pick4(di[c], zb) : di[c][0]);
+          if (!first) v = e_fma(beta, pl[RP * PLB + ob[c]], v);
+          pl[ob[c]] = v;
+          pv[c][u] = v;
+        }
         if (has_halo) {
-          E hv = e_mul(pl[hb], decltype(edge)::value ? pick4(hdi, zb) : hdi[0]);
-          if (!first) hv = e_fma(beta, pl[RP * PLN + hb], hv);
+          E hv = e_mul_rn(pl[hb], decltype(edge)::value ? pick4(hdi, zb) : hdi[0]);
+          if (!first) hv = e_fma(beta, pl[RP * PLB + hb], hv);
           pl[hb] = hv;
         }
       }
@@ -1139,47 +1165,81 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_dir_roll(Geo g, Batch b, con
     if (threadIdx.x == 0 && q >= 2 && q - 2 + RS < nslab) issue(q - 2 + RS);
     // (D) stencils of the planes t0 - 1 .. t0 + RP - 2 (plane t0 - 1 lies in the previous slab)
     auto stencil = [&](auto edge) {
-      E* o = out + (ptrdiff_t)(a0 - 1) * plane_n;
 #pragma unroll
       for (int u = 0; u < RP; ++u) {
-        const int c = a0 - 1 + u;
-        E d = dd[0];
+        const int zc = a0 - 1 + u;
+        int zb = 0;
         if constexpr (decltype(edge)::value) {
-          if (c < z0 || c >= z1) continue;
-          d = pick4(dd, (c == 0) | ((c == g.nz - 1) << 1));
+          if (zc < z0 || zc >= z1) continue;
+          zb = (zc == 0) | ((zc == g.nz - 1) << 1);
         }
-        const E* pl = (u == 0) ? prev + (RP - 1) * PLN : cur + (u - 1) * PLN;
-        const E below = (u == 0) ? pm2 : (u == 1 ? pm1 : pv[u - 2]);
-        const E centre = (u == 0) ? pm1 : pv[u - 1];
-        const E sn = e_add(e_add(e_add(pl[ob - 1], pl[ob + 1]), e_add(pl[ob - BXT], pl[ob + BXT])),
-                           e_add(below, pv[u]));
-        acc = e_fma(centre, e_sub(e_mul(d, centre), sn), acc);
-        o[u * plane_n] = centre;
+        const E* pl = (u == 0) ? prev + (RP - 1) * PLB : cur + (u - 1) * PLB;
+#pragma unroll
+        for (int c = 0; c < CY; ++c) {
+          if (!in[c]) continue;
+          const int o = ob[c];
+          const E d = decltype(edge)::value ? pick4(dd[c], zb) : dd[c][0];
+          const E below = (u == 0) ? pm2[c] : (u == 1 ? pm1[c] : pv[c][u - 2]);
+          const E centre = (u == 0) ? pm1[c] : pv[c][u - 1];
+          const E sn = e_add(e_add(e_add(pl[o - 1], pl[o + 1]), e_add(pl[o - BXT], pl[o + BXT])),
+                             e_add(below, pv[c][u]));
+          if constexpr (CPLX) acc[c] = e_fma(centre, e_sub(e_mul(d, centre), sn), acc[c]);
+          else acc[c] = e_fma(centre, e_fma(d, centre, e_neg(sn)), acc[c]);  // s = d p - sum: one rounding
+          out[(ptrdiff_t)zc * plane_n + c * row8] = centre;
+        }
       }
     };
-    if (in) {
-      if (a0 - 1 < max(z0, 1) || a0 + RP - 2 > min(z1 - 1, g.nz - 2)) stencil(std::true_type{});
-      else stencil(std::false_type{});
+    if (a0 - 1 < max(z0, 1) || a0 + RP - 2 > min(z1 - 1, g.nz - 2)) stencil(std::true_type{});
+    else stencil(std::false_type{});
+#pragma unroll
+    for (int c = 0; c < CY; ++c) {
+      pm2[c] = pv[c][RP - 2];
+      pm1[c] = pv[c][RP - 1];
     }
-    pm2 = pv[RP - 2];
-    pm1 = pv[RP - 1];
     prev = cur;
   }
-  float a2[2] = {e_re(acc), e_im(acc)};
-  double o2[2];
-  if constexpr (CPLX) block_sum<2, float>(a2, o2, sm);
-  else {
-    float a1[1] = {a2[0]};
-    double o1[1];
-    block_sum<1, float>(a1, o1, sm);
-    o2[0] = o1[0];
-    o2[1] = 0.0;
+  float a2[2 * CY];
+#pragma unroll
+  for (int c = 0; c < CY; ++c) {
+    a2[2 * c] = e_re(acc[c]);
+    a2[2 * c + 1] = e_im(acc[c]);
   }
+  double o2[2 * CY];
+  if constexpr (CPLX) {
+    block_sum<2 * CY, float>(a2, o2, sm);
+  } else {
+    float a1[CY];
+#pragma unroll
+    for (int c = 0; c < CY; ++c) a1[c] = a2[2 * c];
+    double o1[CY];
+    block_sum<CY, float>(a1, o1, sm);
+#pragma unroll
+    for (int c = 0; c < CY; ++c) {
+      o2[2 * c] = o1[c];
+      o2[2 * c + 1] = 0.0;
+    }
+  }
+  // each 32 x 8 column's gamma goes to its partial slot of the segment's first 8-plane tile, zeros
+  // to the segment's later tiles
   const int nsl = (z1 - z0 + g.tz - 1) / g.tz;
-  if (threadIdx.x < nsl) {
-    const int slot = col + (z0 / g.tz + threadIdx.x) * ncol;
-    pb[6 * T_ + 2 * slot] = threadIdx.x == 0 ? o2[0] : 0.0;
-    pb[6 * T_ + 2 * slot + 1] = threadIdx.x == 0 ? o2[1] : 0.0;
+  const int ncols = min(CY, g.nty - cy2 * CY);
+  const int ncol8 = g.ntx * g.nty;
+  if (threadIdx.x < nsl * ncols) {
+    const int ct = threadIdx.x / nsl, zt = threadIdx.x - ct * nsl;
+    if (zt > 0) {
+      const int slot = (cy2 * CY + ct) * g.ntx + cx + (z0 / g.tz + zt) * ncol8;
+      pb[6 * T_ + 2 * slot] = 0.0;
+      pb[6 * T_ + 2 * slot + 1] = 0.0;
+    }
+  }
+  if (threadIdx.x == 0) {  // the sums (valid in thread 0) for the first tile of each column
+#pragma unroll
+    for (int c = 0; c < CY; ++c) {
+      if (c >= ncols) break;
+      const int slot = (cy2 * CY + c) * g.ntx + cx + (z0 / g.tz) * ncol8;
+      pb[6 * T_ + 2 * slot] = o2[2 * c];
+      pb[6 * T_ + 2 * slot + 1] = o2[2 * c + 1];
+    }
   }
 }
 
@@ -2053,7 +2113,8 @@ struct RollVariant {
   int rp, rs;
   int cy = 1;  // single sweep: cells per thread in y (tiles of 32 x 8 cy)
 };
-constexpr RollVariant ROLL_VARIANTS[HYDOT_ROLL_VARIANTS] = {{4, 4}, {2, 6}, {4, 3}, {4, 5}};
+// Real fields: pass 1 on 32 x 8 tiles (variant 0) or 32 x 16 tiles, two cells per thread (1-3).
+constexpr RollVariant ROLL_VARIANTS[HYDOT_ROLL_VARIANTS] = {{4, 4, 1}, {4, 3, 2}, {2, 6, 2}, {4, 4, 2}};
 constexpr RollVariant ROLL_VARIANTS_C[HYDOT_ROLL_VARIANTS] = {{2, 4}, {2, 6}, {4, 3}, {2, 4}};
 
 __host__ __device__ constexpr int rp_index(int rp) { return rp == 2 ? 0 : (rp == 4 ? 1 : 2); }
@@ -2166,24 +2227,27 @@ void sweep_dispatch(hydot_ctx* ctx, int v, const Geo& g, const Batch& b, int k_o
   }
 }
 
-template <typename E, int RP, int RS, int MB1, int MB2>
+template <typename E, int RP, int RS, int CY, int MB1, int MB2>
 int roll_attrs(hydot_ctx* ctx) {
-  HYDOT_CUDA_TRY(ctx, raise_smem_limit(k_dir_roll<E, RP, RS, MB1>, roll_smem<E, RP, RS>()));
+  HYDOT_CUDA_TRY(ctx, raise_smem_limit(k_dir_roll<E, RP, RS, CY, MB1>, roll_smem<E, RP, RS, CY>()));
   HYDOT_CUDA_TRY(ctx, raise_smem_limit(k_update_roll<E, RP, RS, MB2>, upd_smem<E, RP, RS>()));
   return HYDOT_OK;
 }
 
-// One inner iteration (pass 1, pass 2) with variant <RP, RS>.
-template <typename E, int RP, int RS, int MB1, int MB2>
+// One inner iteration (pass 1, pass 2) with variant <RP, RS, CY>: pass 1 on tiles of 32 x 8 CY (its
+// blocks cover ceil(nty / CY) tile rows), pass 2 on 32 x 8 tiles (nrb blocks).
+template <typename E, int RP, int RS, int CY, int MB1, int MB2>
 void roll_iteration(hydot_ctx* ctx, const Geo& g, const Batch& b, int it, unsigned nrb, E* Ev, E* R, E* const* P) {
   const int k = rp_index(RP);
   const int seg = ctx->dir_seg;
   cudaStream_t s = ctx->stream;
   cudaEvent_t t0 = timer_begin(ctx);
   const int o = it % POLL_GROUP;  // groups start at multiples of POLL_GROUP (even): parity of it = parity of o
-  k_dir_roll<E, RP, RS, MB1><<<nrb, NTHREADS, roll_smem<E, RP, RS>(), s>>>(g, b, ctx->d_it, o, seg, ctx->d_coef_f,
-                                                                         ctx->tm_rh[k], ctx->tm_ph[k][it & 1],
-                                                                         P[(it + 1) & 1]);
+  const unsigned nrb1 = CY == 1 ? nrb : sweep_items(ctx, g, b, CY);
+  const CUtensorMap& mr = CY == 1 ? ctx->tm_rh[k] : ctx->tm_rh2[k];
+  const CUtensorMap& mp = CY == 1 ? ctx->tm_ph[k][it & 1] : ctx->tm_ph2[k][it & 1];
+  k_dir_roll<E, RP, RS, CY, MB1><<<nrb1, NTHREADS, roll_smem<E, RP, RS, CY>(), s>>>(
+      g, b, ctx->d_it, o, seg, ctx->d_coef_f, mr, mp, P[(it + 1) & 1]);
   ++ctx->launches;
   timer_end(ctx, t0, HYDOT_KERNEL_DIR, 0.0);
   t0 = timer_begin(ctx);
@@ -2206,10 +2270,10 @@ void roll_dispatch(hydot_ctx* ctx, int v, const Geo& g, const Batch& b, int it, 
     float2* r = (float2*)R;
     float2* p[2] = {(float2*)P[0], (float2*)P[1]};
     switch (v) {
-      case 1: roll_iteration<float2, 2, 6, 2, 2>(ctx, g, b, it, nrb, e, r, p); break;
-      case 2: roll_iteration<float2, 4, 3, 2, 2>(ctx, g, b, it, nrb, e, r, p); break;
-      case 3: roll_iteration<float2, 2, 4, 4, 3>(ctx, g, b, it, nrb, e, r, p); break;
-      default: roll_iteration<float2, 2, 4, 3, 3>(ctx, g, b, it, nrb, e, r, p); break;
+      case 1: roll_iteration<float2, 2, 6, 1, 2, 2>(ctx, g, b, it, nrb, e, r, p); break;
+      case 2: roll_iteration<float2, 4, 3, 1, 2, 2>(ctx, g, b, it, nrb, e, r, p); break;
+      case 3: roll_iteration<float2, 2, 4, 1, 4, 3>(ctx, g, b, it, nrb, e, r, p); break;
+      default: roll_iteration<float2, 2, 4, 1, 3, 3>(ctx, g, b, it, nrb, e, r, p); break;
     }
     return;
   }
@@ -2217,10 +2281,10 @@ void roll_dispatch(hydot_ctx* ctx, int v, const Geo& g, const Batch& b, int it, 
   float* r = (float*)R;
   float* p[2] = {(float*)P[0], (float*)P[1]};
   switch (v) {
-    case 1: roll_iteration<float, 2, 6, 4, 4>(ctx, g, b, it, nrb, e, r, p); break;
-    case 2: roll_iteration<float, 4, 3, 5, 5>(ctx, g, b, it, nrb, e, r, p); break;
-    case 3: roll_iteration<float, 4, 5, 3, 3>(ctx, g, b, it, nrb, e, r, p); break;
-    default: roll_iteration<float, 4, 4, 4, 3>(ctx, g, b, it, nrb, e, r, p); break;
+    case 1: roll_iteration<float, 4, 3, 2, 3, 5>(ctx, g, b, it, nrb, e, r, p); break;
+    case 2: roll_iteration<float, 2, 6, 2, 3, 4>(ctx, g, b, it, nrb, e, r, p); break;
+    case 3: roll_iteration<float, 4, 4, 2, 2, 3>(ctx, g, b, it, nrb, e, r, p); break;
+    default: roll_iteration<float, 4, 4, 1, 4, 3>(ctx, g, b, it, nrb, e, r, p); break;
   }
 }
 
@@ -2233,16 +2297,16 @@ int roll_setup(hydot_ctx* ctx) {
     return rc;
   }
   if (ctx->cplx) {
-    int rc = roll_attrs<float2, 2, 4, 3, 3>(ctx);
-    if (!rc) rc = roll_attrs<float2, 2, 6, 2, 2>(ctx);
-    if (!rc) rc = roll_attrs<float2, 4, 3, 2, 2>(ctx);
-    if (!rc) rc = roll_attrs<float2, 2, 4, 4, 3>(ctx);
+    int rc = roll_attrs<float2, 2, 4, 1, 3, 3>(ctx);
+    if (!rc) rc = roll_attrs<float2, 2, 6, 1, 2, 2>(ctx);
+    if (!rc) rc = roll_attrs<float2, 4, 3, 1, 2, 2>(ctx);
+    if (!rc) rc = roll_attrs<float2, 2, 4, 1, 4, 3>(ctx);
     return rc;
   }
-  int rc = roll_attrs<float, 4, 4, 4, 3>(ctx);
-  if (!rc) rc = roll_attrs<float, 2, 6, 4, 4>(ctx);
-  if (!rc) rc = roll_attrs<float, 4, 3, 5, 5>(ctx);
-  if (!rc) rc = roll_attrs<float, 4, 5, 3, 3>(ctx);
+  int rc = roll_attrs<float, 4, 4, 1, 4, 3>(ctx);
+  if (!rc) rc = roll_attrs<float, 4, 3, 2, 3, 5>(ctx);
+  if (!rc) rc = roll_attrs<float, 2, 6, 2, 3, 4>(ctx);
+  if (!rc) rc = roll_attrs<float, 4, 4, 2, 2, 3>(ctx);
   return rc;
 }
 
@@ -2780,6 +2844,11 @@ int solver_alloc(hydot_ctx* ctx) {
       rc = encode_field_map(ctx, ctx->d_r, &ctx->tm_rh[k], BXT, BYT, bz);
       if (!rc) rc = encode_field_map(ctx, ctx->d_p[0], &ctx->tm_ph[k][0], BXT, BYT, bz);
       if (!rc) rc = encode_field_map(ctx, ctx->d_p[1], &ctx->tm_ph[k][1], BXT, BYT, bz);
+      if (!rc && !ctx->cplx) {  // pass 1 on 32 x 16 tiles (real fields)
+        rc = encode_field_map(ctx, ctx->d_r, &ctx->tm_rh2[k], BXT, 2 * TY + 2, bz);
+        if (!rc) rc = encode_field_map(ctx, ctx->d_p[0], &ctx->tm_ph2[k][0], BXT, 2 * TY + 2, bz);
+        if (!rc) rc = encode_field_map(ctx, ctx->d_p[1], &ctx->tm_ph2[k][1], BXT, 2 * TY + 2, bz);
+      }
       if (!rc) rc = encode_field_map(ctx, ctx->d_e, &ctx->tm_e[k], TX, TY, bz);
       if (!rc) rc = encode_field_map(ctx, ctx->d_r, &ctx->tm_rv[k], TX, TY, bz);
     }
