@@ -250,6 +250,7 @@ struct hydot_ctx {
   // x-y halo (40 x 10 x depth), d_e and d_r in slabs of the tile alone (32 x 8 x depth)
   CUtensorMap tm_rh[3]{}, tm_ph[3][2]{}, tm_e[3]{}, tm_rv[3]{};
   CUtensorMap tm_rh2[3]{}, tm_ph2[3][2]{};  // pass 1 on 32 x 16 tiles: r and p_old in 40 x 18 boxes
+  CUtensorMap tm_rx[2][3]{}, tm_px[2][3][2]{};  // pass 1 on x-pairs: 72 x 10 and 72 x 18 boxes
   // single-sweep inner iteration (FP32 real fields on the TMA path): a second residual buffer,
   // per-field scalars {gamma, alpha} per parity [2][max_fields][2], and maps per slab depth 3, 4:
   // r (both buffers) and p (both) in boxes of the tile plus a two-cell ring (40 x 12 x depth), e in

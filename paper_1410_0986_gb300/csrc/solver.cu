@@ -976,6 +976,49 @@ __device__ __forceinline__ E pick4(const E (&v)[4], int zb) {
   return zb == 0 ? v[0] : (zb == 1 ? v[1] : (zb == 2 ? v[2] : v[3]));
 }
 
+// Pass-1 prologue, run by one warp: the stopping test on ||r||^2 and beta = rho / rho_prev, from
+// the per-tile partials in FP64 in a fixed order (every block of a field decides alike). Sets
+// *s_go (1: iterate) and *s_beta in thread 0; the field's lead block marks a finished field.
+template <typename E>
+__device__ __forceinline__ void dir_scalars(const Batch& b, const double* pb, int T_, int it, int rhs, bool lead,
+                                            int* s_go, E* s_beta) {
+  constexpr bool CPLX = !std::is_same<E, float>::value;
+  const int par = it & 1;
+  const bool first = (it == 0);
+  // rho of the current residual (re, im), ||r||^2, and rho of the previous one (re, im)
+  double v0 = 0.0, v0i = 0.0, v1 = 0.0, v2 = 0.0, v2i = 0.0;
+  for (int t = threadIdx.x; t < T_; t += 32) {
+    v0 += pb[2 * T_ * par + 2 * t];
+    v1 += pb[4 * T_ + T_ * par + t];
+    if (!first) v2 += pb[2 * T_ * (par ^ 1) + 2 * t];
+    if constexpr (CPLX) {
+      v0i += pb[2 * T_ * par + 2 * t + 1];
+      if (!first) v2i += pb[2 * T_ * (par ^ 1) + 2 * t + 1];
+    }
+  }
+  v0 = warp_sum(v0);
+  v1 = warp_sum(v1);
+  v2 = warp_sum(v2);
+  if constexpr (CPLX) {
+    v0i = warp_sum(v0i);
+    v2i = warp_sum(v2i);
+  }
+  if (threadIdx.x == 0) {
+    int go = 0;
+    E beta{};
+    const bool done = v1 <= b.tol_in2 * b.rr0[rhs] || it >= b.max_inner || b.iters[rhs] >= b.max_iter || v1 == 0.0;
+    if (done) {
+      if (lead) b.status[rhs] = RHS_FINISHED;
+    } else {
+      go = 1;
+      if (!first) beta = e_quot<E>(v0, v0i, v2, v2i);
+      if (lead) atomicAdd(&b.counter[1 + it], 1);
+    }
+    *s_go = go;
+    *s_beta = beta;
+  }
+}
+
 template <typename E, int RP, int RS, int CY, int MINB>
 __global__ void __launch_bounds__(NTHREADS, MINB) k_dir_roll(Geo g, Batch b, const int* __restrict__ it_dev, int k,
                                                              int seg,
@@ -1008,7 +1051,6 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_dir_roll(Geo g, Batch b, con
   const bool lead = (col == 0 && zs == 0);
   const int T_ = g.ntiles;
   double* pb = b.part + (size_t)rhs * part_stride(T_);
-  const int par = it & 1;
   const bool first = (it == 0);
   const int np = z1 - z0 + 2;  // planes z0-1 .. z1 (t = plane - (z0 - 1))
   const int nslab = (np + RP - 1) / RP;
@@ -1034,41 +1076,7 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_dir_roll(Geo g, Batch b, con
   }
   __syncthreads();
   if (s_st != RHS_INNER) return;
-  if (threadIdx.x < 32) {
-    // rho of the current residual (re, im), ||r||^2, and rho of the previous one (re, im)
-    double v0 = 0.0, v0i = 0.0, v1 = 0.0, v2 = 0.0, v2i = 0.0;
-    for (int t = threadIdx.x; t < T_; t += 32) {
-      v0 += pb[2 * T_ * par + 2 * t];
-      v1 += pb[4 * T_ + T_ * par + t];
-      if (!first) v2 += pb[2 * T_ * (par ^ 1) + 2 * t];
-      if constexpr (CPLX) {
-        v0i += pb[2 * T_ * par + 2 * t + 1];
-        if (!first) v2i += pb[2 * T_ * (par ^ 1) + 2 * t + 1];
-      }
-    }
-    v0 = warp_sum(v0);
-    v1 = warp_sum(v1);
-    v2 = warp_sum(v2);
-    if constexpr (CPLX) {
-      v0i = warp_sum(v0i);
-      v2i = warp_sum(v2i);
-    }
-    if (threadIdx.x == 0) {
-      int go = 0;
-      E beta{};
-      const bool done = v1 <= b.tol_in2 * b.rr0[rhs] || it >= b.max_inner || b.iters[rhs] >= b.max_iter ||
-                        v1 == 0.0;
-      if (done) {
-        if (lead) b.status[rhs] = RHS_FINISHED;
-      } else {
-        go = 1;
-        if (!first) beta = e_quot<E>(v0, v0i, v2, v2i);
-        if (lead) atomicAdd(&b.counter[1 + it], 1);
-      }
-      s_go = go;
-      s_beta = beta;
-    }
-  }
+  if (threadIdx.x < 32) dir_scalars<E>(b, pb, T_, it, rhs, lead, &s_go, &s_beta);
   const LamCoefF cf = coef_f[rhs_lambda(b, rhs)];
   __syncthreads();
   if (!s_go) {
@@ -1239,6 +1247,300 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_dir_roll(Geo g, Batch b, con
       const int slot = (cy2 * CY + c) * g.ntx + cx + (z0 / g.tz) * ncol8;
       pb[6 * T_ + 2 * slot] = o2[2 * c];
       pb[6 * T_ + 2 * slot + 1] = o2[2 * c + 1];
+    }
+  }
+}
+
+// Pass 1 on 64 x 8 CY tiles with two x-adjacent cells per thread (real fields). The same rolling
+// slabs as k_dir_roll, with boxes 72 wide (x0 - 4 .. x0 + 67) and 8 CY + 2 rows, but a thread owns
+// the cells (x0 + 2m, y) and (x0 + 2m + 1, y) for y = y0 + ty + 8 c: it forms both with one 8-byte
+// shared load of r and of p_old and one 8-byte store, and in the stencil each cell of the pair is
+// the other's x-neighbour (a register), so a pair takes two 4-byte loads (x - 1, x + 2) and two
+// 8-byte loads (the rows above and below) where two single cells take eight 4-byte loads. The
+// arithmetic per cell and the order of every sum are those of k_dir_roll: gamma per 32 x 8
+// column is formed as its warp reduction forms it (the even and the odd cells of a row as two
+// shuffle trees over 16 lanes, then their sum; the rows in order in FP64), so both kernels give
+// the same bits. The diagonal of a cell on a grid z-face is formed when that plane comes up (it
+// is rare); the cell's interior-z diagonal and its inverse stay in registers. Needs nx % 4 == 0
+// (the TMA row pitch), so the pairs never straddle the grid's x-extent and 8-byte global stores
+// are aligned.
+constexpr int TXP = 64;  // tile width of the paired-cell pass 1
+constexpr int BXP = 72;  // its box width: x0 - 4 .. x0 + 67
+template <int RP, int RS, int CY>
+constexpr size_t xp_smem() { return (size_t)RS * 2 * RP * (BXP * (TY * CY + 2)) * sizeof(float) + 128; }
+
+// Diagonal of the cell with face mask m (bits: x low, x high, y low, y high, z low, z high) and its
+// inverse, as col_diag forms them.
+__device__ __forceinline__ void cell_diag(const LamCoefF& cf, int m, float& d, float& di) {
+  d = m ? diag_f(cf, m) : cf.dint;
+  di = m ? 1.f / d : cf.idint;
+}
+__device__ __forceinline__ int zmask(int zb) { return ((zb & 1) << 4) | ((zb >> 1) << 5); }
+
+template <int RP, int RS, int CY, int MINB>
+__global__ void __launch_bounds__(NTHREADS, MINB) k_dir_xp(Geo g, Batch b, const int* __restrict__ it_dev, int k,
+                                                           int seg, const LamCoefF* __restrict__ coef_f,
+                                                           const __grid_constant__ CUtensorMap mapR,
+                                                           const __grid_constant__ CUtensorMap mapPold,
+                                                           float* __restrict__ Pnew) {
+  static_assert(RS >= 3, "a slab buffer is refilled two slabs after its own");
+  constexpr int TYB = TY * CY;          // tile rows
+  constexpr int PLB = BXP * (TYB + 2);  // elements in one box plane
+  extern __shared__ unsigned char dsm[];
+  float* slab = align128<float>(dsm);  // [RS][r -> p_new, p_old][RP planes]
+  __shared__ uint64_t mbar[RS];
+  __shared__ double sm[2 * CY * NWARPS];  // row sums per (8-row group, 32-column half, row)
+  __shared__ LamCoefF s_cf;
+  __shared__ float s_beta;
+  __shared__ int s_go, s_st;
+  constexpr uint32_t SLAB_BYTES = RP * PLB * sizeof(float);
+  const int it = *it_dev + k;
+  const int ntxp = (g.nx + TXP - 1) / TXP;
+  const int nty2 = (g.nty + CY - 1) / CY;
+  const int ncol = ntxp * nty2;
+  const int nseg = (g.nz + seg - 1) / seg;
+  const int rhs = blockIdx.x / (ncol * nseg);
+  const int rem = blockIdx.x - rhs * ncol * nseg;
+  const int zs = rem / ncol, col = rem - zs * ncol;
+  const int cx = col % ntxp, cy2 = col / ntxp;
+  const int x0 = cx * TXP, y0 = cy2 * TYB;
+  const int z0 = zs * seg, z1 = min(z0 + seg, g.nz);
+  const bool lead = (col == 0 && zs == 0);
+  const int T_ = g.ntiles;
+  double* pb = b.part + (size_t)rhs * part_stride(T_);
+  const bool first = (it == 0);
+  const int np = z1 - z0 + 2;  // planes z0-1 .. z1
+  const int nslab = (np + RP - 1) / RP;
+  const int nfirst = min(RS, nslab);
+  const uint32_t tx_bytes = (first ? 1u : 2u) * SLAB_BYTES;
+  auto issue = [&](int q) {
+    float* dst = slab + (q % RS) * 2 * RP * PLB;
+    mbar_expect_tx(&mbar[q % RS], tx_bytes);
+    tma_load_4d(dst, &mapR, &mbar[q % RS], x0 - 4, y0 - 1, z0 - 1 + q * RP, rhs);
+    if (!first) tma_load_4d(dst + RP * PLB, &mapPold, &mbar[q % RS], x0 - 4, y0 - 1, z0 - 1 + q * RP, rhs);
+  };
+  if (threadIdx.x == 0) {
+    const int st = b.status[rhs];
+    s_st = st;
+    if (st == RHS_INNER) {
+      for (int q = 0; q < RS; ++q) mbar_init(&mbar[q], 1);
+      mbar_fence_init();
+      for (int q = 0; q < nfirst; ++q) issue(q);
+    }
+  }
+  __syncthreads();
+  if (s_st != RHS_INNER) return;
+  if (threadIdx.x < 32) dir_scalars<float>(b, pb, T_, it, rhs, lead, &s_go, &s_beta);
+  if (threadIdx.x == 32) s_cf = coef_f[rhs_lambda(b, rhs)];
+  __syncthreads();
+  if (!s_go) {
+    if (threadIdx.x == 0)
+      for (int q = 0; q < nfirst; ++q) mbar_wait_bounded(&mbar[q % RS], 0u);
+    return;
+  }
+  const float beta = s_beta;
+  const LamCoefF& cf = s_cf;
+
+  // own pairs (x0 + 2m + {0, 1}, y0 + ty + 8 c): face masks, interior-z diagonals and inverses
+  const int m = threadIdx.x % 32, ty = threadIdx.x / 32;
+  const int i = x0 + 2 * m;  // even; i < nx implies i + 1 < nx (nx % 4 == 0)
+  bool in[CY];
+  int ob[CY], msk[CY][2];
+  float d0[CY][2], i0[CY][2];
+#pragma unroll
+  for (int c = 0; c < CY; ++c) {
+    const int j = y0 + ty + TY * c;
+    in[c] = (i < g.nx) && (j < g.ny);
+    ob[c] = (ty + TY * c + 1) * BXP + 4 + 2 * m;
+    const int my = ((j == 0) << 2) | ((j == g.ny - 1) << 3);
+    msk[c][0] = (i == 0) | my;
+    msk[c][1] = ((i + 1 == g.nx - 1) << 1) | my;
+    cell_diag(cf, msk[c][0], d0[c][0], i0[c][0]);
+    cell_diag(cf, msk[c][1], d0[c][1], i0[c][1]);
+  }
+  // halo: threads 0..63 form the pairs of the rows y0 - 1 and y0 + TYB, threads 64 .. 64 + 2 TYB - 1
+  // the cells of the columns x0 - 1 and x0 + 64
+  const int h = threadIdx.x;
+  const bool hpair = h < 2 * 32;
+  const bool hcol = !hpair && h < 2 * 32 + 2 * TYB;
+  int hb = 0, hm0 = 0, hm1 = 0;
+  float hi0 = 0.f, hi1 = 0.f;
+  if (hpair) {
+    const int hx = 2 * (h % 32), hy = h < 32 ? -1 : TYB;
+    hb = (hy + 1) * BXP + 4 + hx;
+    const int gi = x0 + hx, gj = y0 + hy;
+    const int my = ((gj == 0) << 2) | ((gj == g.ny - 1) << 3);
+    hm0 = (gi == 0) | my;
+    hm1 = ((gi + 1 == g.nx - 1) << 1) | my;
+  } else if (hcol) {
+    const int q = h - 2 * 32;
+    const int hx = q < TYB ? -1 : TXP, hy = q % TYB;
+    hb = (hy + 1) * BXP + 4 + hx;
+    const int gi = x0 + hx, gj = y0 + hy;
+    hm0 = (gi == 0) | ((gi == g.nx - 1) << 1) | ((gj == 0) << 2) | ((gj == g.ny - 1) << 3);
+  }
+  {
+    float dd;
+    cell_diag(cf, hm0, dd, hi0);
+    cell_diag(cf, hm1, dd, hi1);
+  }
+  const int plane_n = g.nx * g.ny;
+  float* out = Pnew + (size_t)rhs * g.N + (size_t)(y0 + ty) * g.nx + i;
+  const int row8 = TY * g.nx;  // offset of the cell eight rows further
+  float acc[CY][2];
+  float2 pm2[CY], pm1[CY];  // own p_new of the previous slab's last two planes
+#pragma unroll
+  for (int c = 0; c < CY; ++c) {
+    acc[c][0] = acc[c][1] = 0.f;
+    pm2[c] = pm1[c] = make_float2(0.f, 0.f);
+  }
+  const float* prev = slab;
+  for (int q = 0; q < nslab; ++q) {
+    float* cur = slab + (q % RS) * 2 * RP * PLB;
+    const bool ok = mbar_wait_bounded(&mbar[q % RS], (uint32_t)((q / RS) & 1));
+    const int a0 = z0 - 1 + q * RP;  // first plane formed from this slab
+    float2 pv[CY][RP];
+    // (B) p_new = D^-1 r + beta p_old in place (the product rounded on its own, as k_dir_roll)
+    auto form = [&](auto edge) {
+#pragma unroll
+      for (int u = 0; u < RP; ++u) {
+        int zm = 0;
+        if constexpr (decltype(edge)::value) zm = zmask((a0 + u == 0) | ((a0 + u == g.nz - 1) << 1));
+        float* pl = cur + u * PLB;
+#pragma unroll
+        for (int c = 0; c < CY; ++c) {
+          float ia = i0[c][0], ib = i0[c][1];
+          if constexpr (decltype(edge)::value) {
+            if (zm) {
+              float dd;
+              cell_diag(cf, msk[c][0] | zm, dd, ia);
+              cell_diag(cf, msk[c][1] | zm, dd, ib);
+            }
+          }
+          const float2 rv = *reinterpret_cast<const float2*>(pl + ob[c]);
+          float2 v = make_float2(__fmul_rn(rv.x, ia), __fmul_rn(rv.y, ib));
+          if (!first) {
+            const float2 po = *reinterpret_cast<const float2*>(pl + RP * PLB + ob[c]);
+            v.x = fmaf(beta, po.x, v.x);
+            v.y = fmaf(beta, po.y, v.y);
+          }
+          *reinterpret_cast<float2*>(pl + ob[c]) = v;
+          pv[c][u] = v;
+        }
+        if (hpair || hcol) {
+          float ia = hi0, ib = hi1;
+          if constexpr (decltype(edge)::value) {
+            if (zm) {
+              float dd;
+              cell_diag(cf, hm0 | zm, dd, ia);
+              cell_diag(cf, hm1 | zm, dd, ib);
+            }
+          }
+          if (hpair) {
+            const float2 rv = *reinterpret_cast<const float2*>(pl + hb);
+            float2 v = make_float2(__fmul_rn(rv.x, ia), __fmul_rn(rv.y, ib));
+            if (!first) {
+              const float2 po = *reinterpret_cast<const float2*>(pl + RP * PLB + hb);
+              v.x = fmaf(beta, po.x, v.x);
+              v.y = fmaf(beta, po.y, v.y);
+            }
+            *reinterpret_cast<float2*>(pl + hb) = v;
+          } else {
+            float v = __fmul_rn(pl[hb], ia);
+            if (!first) v = fmaf(beta, pl[RP * PLB + hb], v);
+            pl[hb] = v;
+          }
+        }
+      }
+    };
+    if (a0 <= 0 || a0 + RP - 1 >= g.nz - 1) form(std::true_type{});
+    else form(std::false_type{});
+    // the in-place writes are ordered before the copy that later refills this buffer
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (!__syncthreads_and(ok)) {
+      if (threadIdx.x == 0) {
+        atomicExch(b.err, 1);
+        const int last = min(max(RS - 1, q + RS - 3), nslab - 1);
+        for (int u = q; u <= last; ++u) mbar_wait_bounded(&mbar[u % RS], (uint32_t)((u / RS) & 1));
+      }
+      return;
+    }
+    if (threadIdx.x == 0 && q >= 2 && q - 2 + RS < nslab) issue(q - 2 + RS);
+    // (D) stencils of the planes a0 - 1 .. a0 + RP - 2 (the first lies in the previous slab)
+    auto stencil = [&](auto edge) {
+#pragma unroll
+      for (int u = 0; u < RP; ++u) {
+        const int zc = a0 - 1 + u;
+        int zm = 0;
+        if constexpr (decltype(edge)::value) {
+          if (zc < z0 || zc >= z1) continue;
+          zm = zmask((zc == 0) | ((zc == g.nz - 1) << 1));
+        }
+        const float* pl = (u == 0) ? prev + (RP - 1) * PLB : cur + (u - 1) * PLB;
+#pragma unroll
+        for (int c = 0; c < CY; ++c) {
+          if (!in[c]) continue;
+          const int o = ob[c];
+          float da = d0[c][0], db = d0[c][1];
+          if constexpr (decltype(edge)::value) {
+            if (zm) {
+              float dummy;
+              cell_diag(cf, msk[c][0] | zm, da, dummy);
+              cell_diag(cf, msk[c][1] | zm, db, dummy);
+            }
+          }
+          const float2 below = (u == 0) ? pm2[c] : (u == 1 ? pm1[c] : pv[c][u - 2]);
+          const float2 centre = (u == 0) ? pm1[c] : pv[c][u - 1];
+          const float2 above = pv[c][u];
+          const float2 ylo = *reinterpret_cast<const float2*>(pl + o - BXP);
+          const float2 yhi = *reinterpret_cast<const float2*>(pl + o + BXP);
+          const float sa = ((pl[o - 1] + centre.y) + (ylo.x + yhi.x)) + (below.x + above.x);
+          const float sb = ((centre.x + pl[o + 2]) + (ylo.y + yhi.y)) + (below.y + above.y);
+          acc[c][0] = fmaf(centre.x, fmaf(da, centre.x, -sa), acc[c][0]);
+          acc[c][1] = fmaf(centre.y, fmaf(db, centre.y, -sb), acc[c][1]);
+          *reinterpret_cast<float2*>(out + (ptrdiff_t)zc * plane_n + c * row8) = centre;
+        }
+      }
+    };
+    if (a0 - 1 < max(z0, 1) || a0 + RP - 2 > min(z1 - 1, g.nz - 2)) stencil(std::true_type{});
+    else stencil(std::false_type{});
+#pragma unroll
+    for (int c = 0; c < CY; ++c) {
+      pm2[c] = pv[c][RP - 2];
+      pm1[c] = pv[c][RP - 1];
+    }
+    prev = cur;
+  }
+  // gamma per 32 x 8 column: each row's even and odd cells as shuffle trees over the half-warp
+  // (the first four steps of k_dir_roll's lane tree), then even + odd (its last step); the rows
+  // are summed in order in FP64 as block_sum does
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < CY; ++c) {
+    float ea = acc[c][0], oa = acc[c][1];
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) {
+      ea += __shfl_down_sync(0xffffffffu, ea, o, 16);
+      oa += __shfl_down_sync(0xffffffffu, oa, o, 16);
+    }
+    if ((lane & 15) == 0) sm[(2 * c + (lane >> 4)) * NWARPS + warp] = (double)(ea + oa);
+  }
+  __syncthreads();
+  const int nsl = (z1 - z0 + g.tz - 1) / g.tz;
+  const int nyc = min(CY, g.nty - cy2 * CY), nxc = min(2, g.ntx - 2 * cx);
+  const int ncol8 = g.ntx * g.nty;
+  // each 32 x 8 column's gamma goes to its partial slot of the segment's first 8-plane tile, zeros
+  // to the segment's later tiles
+  for (int idx = threadIdx.x; idx < nsl * 2 * CY; idx += NTHREADS) {
+    const int qc = idx / nsl, zt = idx - qc * nsl;
+    const int c = qc >> 1, hf = qc & 1;
+    if (c < nyc && hf < nxc) {
+      const int slot = (cy2 * CY + c) * g.ntx + 2 * cx + hf + (z0 / g.tz + zt) * ncol8;
+      double v = 0.0;
+      if (zt == 0)
+        for (int w = 0; w < NWARPS; ++w) v += sm[qc * NWARPS + w];
+      pb[6 * T_ + 2 * slot] = v;
+      pb[6 * T_ + 2 * slot + 1] = 0.0;
     }
   }
 }
@@ -2111,10 +2413,12 @@ __global__ void k_dsig(const double* __restrict__ dc, const double* __restrict__
 // blocks per SM).
 struct RollVariant {
   int rp, rs;
-  int cy = 1;  // single sweep: cells per thread in y (tiles of 32 x 8 cy)
+  int cy = 1;       // cells per thread in y (tiles of 32 x 8 cy, or 64 x 8 cy with xp)
+  bool xp = false;  // pass 1 on paired x-adjacent cells (k_dir_xp)
 };
-// Real fields: pass 1 on 32 x 8 tiles (variant 0) or 32 x 16 tiles, two cells per thread (1-3).
-constexpr RollVariant ROLL_VARIANTS[HYDOT_ROLL_VARIANTS] = {{4, 4, 1}, {4, 3, 2}, {2, 6, 2}, {4, 4, 2}};
+// Real fields, pass 1 on: 32 x 8 tiles (variant 0); 64 x 8 tiles, x-pairs (1); 32 x 16 tiles, two
+// cells per thread (2); 64 x 16 tiles, two x-pairs per thread (3). Pass 2 runs on 32 x 8 tiles.
+constexpr RollVariant ROLL_VARIANTS[HYDOT_ROLL_VARIANTS] = {{4, 4, 1}, {2, 6, 1, true}, {2, 6, 2}, {2, 4, 2, true}};
 constexpr RollVariant ROLL_VARIANTS_C[HYDOT_ROLL_VARIANTS] = {{2, 4}, {2, 6}, {4, 3}, {2, 4}};
 
 __host__ __device__ constexpr int rp_index(int rp) { return rp == 2 ? 0 : (rp == 4 ? 1 : 2); }
@@ -2227,31 +2531,45 @@ void sweep_dispatch(hydot_ctx* ctx, int v, const Geo& g, const Batch& b, int k_o
   }
 }
 
-template <typename E, int RP, int RS, int CY, int MB1, int MB2>
+template <typename E, int RP, int RS, int CY, int MB1, int MB2, bool XP = false, int RS2 = RS>
 int roll_attrs(hydot_ctx* ctx) {
-  HYDOT_CUDA_TRY(ctx, raise_smem_limit(k_dir_roll<E, RP, RS, CY, MB1>, roll_smem<E, RP, RS, CY>()));
-  HYDOT_CUDA_TRY(ctx, raise_smem_limit(k_update_roll<E, RP, RS, MB2>, upd_smem<E, RP, RS>()));
+  if constexpr (XP) {
+    HYDOT_CUDA_TRY(ctx, raise_smem_limit(k_dir_xp<RP, RS, CY, MB1>, xp_smem<RP, RS, CY>()));
+  } else {
+    HYDOT_CUDA_TRY(ctx, raise_smem_limit(k_dir_roll<E, RP, RS, CY, MB1>, roll_smem<E, RP, RS, CY>()));
+  }
+  HYDOT_CUDA_TRY(ctx, raise_smem_limit(k_update_roll<E, RP, RS2, MB2>, upd_smem<E, RP, RS2>()));
   return HYDOT_OK;
 }
 
-// One inner iteration (pass 1, pass 2) with variant <RP, RS, CY>: pass 1 on tiles of 32 x 8 CY (its
-// blocks cover ceil(nty / CY) tile rows), pass 2 on 32 x 8 tiles (nrb blocks).
-template <typename E, int RP, int RS, int CY, int MB1, int MB2>
+// One inner iteration (pass 1, pass 2) with variant <RP, RS, CY, XP>: pass 1 on tiles of 32 x 8 CY, or
+// with XP 64 x 8 CY (its blocks cover the tile rows and columns of that size), pass 2 on 32 x 8
+// tiles (nrb blocks) with RS2 slab buffers.
+template <typename E, int RP, int RS, int CY, int MB1, int MB2, bool XP = false, int RS2 = RS>
 void roll_iteration(hydot_ctx* ctx, const Geo& g, const Batch& b, int it, unsigned nrb, E* Ev, E* R, E* const* P) {
   const int k = rp_index(RP);
   const int seg = ctx->dir_seg;
   cudaStream_t s = ctx->stream;
   cudaEvent_t t0 = timer_begin(ctx);
   const int o = it % POLL_GROUP;  // groups start at multiples of POLL_GROUP (even): parity of it = parity of o
-  const unsigned nrb1 = CY == 1 ? nrb : sweep_items(ctx, g, b, CY);
-  const CUtensorMap& mr = CY == 1 ? ctx->tm_rh[k] : ctx->tm_rh2[k];
-  const CUtensorMap& mp = CY == 1 ? ctx->tm_ph[k][it & 1] : ctx->tm_ph2[k][it & 1];
-  k_dir_roll<E, RP, RS, CY, MB1><<<nrb1, NTHREADS, roll_smem<E, RP, RS, CY>(), s>>>(
-      g, b, ctx->d_it, o, seg, ctx->d_coef_f, mr, mp, P[(it + 1) & 1]);
+  if constexpr (XP) {
+    static_assert(std::is_same<E, float>::value, "paired cells are a real-field layout");
+    const unsigned nrb1 = (unsigned)((long long)b.nrhs * ((g.nx + TXP - 1) / TXP) * ((g.nty + CY - 1) / CY) *
+                                     ((g.nz + seg - 1) / seg));
+    const int c = CY - 1;
+    k_dir_xp<RP, RS, CY, MB1><<<nrb1, NTHREADS, xp_smem<RP, RS, CY>(), s>>>(
+        g, b, ctx->d_it, o, seg, ctx->d_coef_f, ctx->tm_rx[c][k], ctx->tm_px[c][k][it & 1], P[(it + 1) & 1]);
+  } else {
+    const unsigned nrb1 = CY == 1 ? nrb : sweep_items(ctx, g, b, CY);
+    const CUtensorMap& mr = CY == 1 ? ctx->tm_rh[k] : ctx->tm_rh2[k];
+    const CUtensorMap& mp = CY == 1 ? ctx->tm_ph[k][it & 1] : ctx->tm_ph2[k][it & 1];
+    k_dir_roll<E, RP, RS, CY, MB1><<<nrb1, NTHREADS, roll_smem<E, RP, RS, CY>(), s>>>(
+        g, b, ctx->d_it, o, seg, ctx->d_coef_f, mr, mp, P[(it + 1) & 1]);
+  }
   ++ctx->launches;
   timer_end(ctx, t0, HYDOT_KERNEL_DIR, 0.0);
   t0 = timer_begin(ctx);
-  k_update_roll<E, RP, RS, MB2><<<nrb, NTHREADS, upd_smem<E, RP, RS>(), s>>>(
+  k_update_roll<E, RP, RS2, MB2><<<nrb, NTHREADS, upd_smem<E, RP, RS2>(), s>>>(
       g, b, ctx->d_it, o, seg, ctx->d_coef_f, Ev, R, ctx->tm_ph[k][(it + 1) & 1], ctx->tm_e[k], ctx->tm_rv[k]);
   ++ctx->launches;
   timer_end(ctx, t0, HYDOT_KERNEL_UPDATE, 0.0);
@@ -2281,9 +2599,9 @@ void roll_dispatch(hydot_ctx* ctx, int v, const Geo& g, const Batch& b, int it, 
   float* r = (float*)R;
   float* p[2] = {(float*)P[0], (float*)P[1]};
   switch (v) {
-    case 1: roll_iteration<float, 4, 3, 2, 3, 5>(ctx, g, b, it, nrb, e, r, p); break;
+    case 1: roll_iteration<float, 2, 6, 1, 3, 4, true>(ctx, g, b, it, nrb, e, r, p); break;
     case 2: roll_iteration<float, 2, 6, 2, 3, 4>(ctx, g, b, it, nrb, e, r, p); break;
-    case 3: roll_iteration<float, 4, 4, 2, 2, 3>(ctx, g, b, it, nrb, e, r, p); break;
+    case 3: roll_iteration<float, 2, 4, 2, 2, 4, true, 6>(ctx, g, b, it, nrb, e, r, p); break;
     default: roll_iteration<float, 4, 4, 1, 4, 3>(ctx, g, b, it, nrb, e, r, p); break;
   }
 }
@@ -2304,9 +2622,9 @@ int roll_setup(hydot_ctx* ctx) {
     return rc;
   }
   int rc = roll_attrs<float, 4, 4, 1, 4, 3>(ctx);
-  if (!rc) rc = roll_attrs<float, 4, 3, 2, 3, 5>(ctx);
+  if (!rc) rc = roll_attrs<float, 2, 6, 1, 3, 4, true>(ctx);
   if (!rc) rc = roll_attrs<float, 2, 6, 2, 3, 4>(ctx);
-  if (!rc) rc = roll_attrs<float, 4, 4, 2, 2, 3>(ctx);
+  if (!rc) rc = roll_attrs<float, 2, 4, 2, 2, 4, true, 6>(ctx);
   return rc;
 }
 
@@ -2844,10 +3162,15 @@ int solver_alloc(hydot_ctx* ctx) {
       rc = encode_field_map(ctx, ctx->d_r, &ctx->tm_rh[k], BXT, BYT, bz);
       if (!rc) rc = encode_field_map(ctx, ctx->d_p[0], &ctx->tm_ph[k][0], BXT, BYT, bz);
       if (!rc) rc = encode_field_map(ctx, ctx->d_p[1], &ctx->tm_ph[k][1], BXT, BYT, bz);
-      if (!rc && !ctx->cplx) {  // pass 1 on 32 x 16 tiles (real fields)
+      if (!rc && !ctx->cplx) {  // pass 1 on 32 x 16 tiles, and on 64 x 8 / 64 x 16 tiles (real fields)
         rc = encode_field_map(ctx, ctx->d_r, &ctx->tm_rh2[k], BXT, 2 * TY + 2, bz);
         if (!rc) rc = encode_field_map(ctx, ctx->d_p[0], &ctx->tm_ph2[k][0], BXT, 2 * TY + 2, bz);
         if (!rc) rc = encode_field_map(ctx, ctx->d_p[1], &ctx->tm_ph2[k][1], BXT, 2 * TY + 2, bz);
+        for (int c = 0; c < 2 && !rc; ++c) {
+          rc = encode_field_map(ctx, ctx->d_r, &ctx->tm_rx[c][k], BXP, (c + 1) * TY + 2, bz);
+          if (!rc) rc = encode_field_map(ctx, ctx->d_p[0], &ctx->tm_px[c][k][0], BXP, (c + 1) * TY + 2, bz);
+          if (!rc) rc = encode_field_map(ctx, ctx->d_p[1], &ctx->tm_px[c][k][1], BXP, (c + 1) * TY + 2, bz);
+        }
       }
       if (!rc) rc = encode_field_map(ctx, ctx->d_e, &ctx->tm_e[k], TX, TY, bz);
       if (!rc) rc = encode_field_map(ctx, ctx->d_r, &ctx->tm_rv[k], TX, TY, bz);

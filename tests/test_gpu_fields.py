@@ -290,9 +290,31 @@ def test_roll_variants_bitwise_identical_and_autotuner_settles(hd, oracle_fields
     assert all(v["ns_per_cell"] > 0 for v in tu["variants"])
     # slab shapes {planes, buffers} of the two-pass and the single-sweep forms
     # (single-sweep variants 2 and 3 use 32 x 16 tiles, two cells per thread: the same bits)
-    # (two-pass variants 1-3 run pass 1 on 32 x 16 tiles)
-    expect = [(4, 3), (3, 4), (3, 3), (4, 3)] if sweep == "1" else [(4, 4), (4, 3), (2, 6), (4, 4)]
+    # (two-pass variants 1-3 run pass 1 on 64 x 8 pairs, 32 x 16 and 64 x 16 pairs)
+    expect = [(4, 3), (3, 4), (3, 3), (4, 3)] if sweep == "1" else [(4, 4), (2, 6), (2, 6), (2, 4)]
     assert [(v["planes"], v["buffers"]) for v in tu["variants"]] == expect
+
+
+@pytest.mark.parametrize("seg", [None, "8"])
+def test_paired_cell_pass1_bitwise_on_ragged_tiles(hd, monkeypatch, seg):
+    """Pass 1 on 64-wide tiles of x-adjacent cell pairs (two-pass variants 1 and 3) gives the bits of
+    the 32-wide tiles (variants 0 and 2) where the 64-wide tiles are ragged: nx = 100 leaves a last
+    tile with one full and one partial 32-cell half, ny = 19 a last 8-row group with three rows,
+    nz = 21 a ragged last z-segment of 8 planes."""
+    monkeypatch.setenv("HYDOT_SINGLE_SWEEP", "0")
+    monkeypatch.setenv("HYDOT_PERSISTENT", "0")
+    if seg:
+        monkeypatch.setenv("HYDOT_DIR_SEG", seg)
+    p = workloads.make_problem(workloads.Grid(100, 19, 21, 2.0), 3, 3, 3, seed=24, geometry="transmission")
+    out = []
+    for v in range(4):
+        monkeypatch.setenv("HYDOT_ROLL_VARIANT", str(v))
+        with hd.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=1e-8, cw_floor=100.0) as ctx:
+            ps, pd, st = ctx.solve_fields(0, p.n_lambda)
+            assert ctx.tuning()["variant"] == v and st["n_not_converged"] == 0
+        out.append((ps, pd))
+    for ps, pd in out[1:]:
+        assert torch.equal(ps, out[0][0]) and torch.equal(pd, out[0][1])
 
 
 @pytest.mark.parametrize("name", ["tma-ragged-36x19x21", "tma-faces-40x16x9"])
