@@ -60,6 +60,12 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
   return *reinterpret_cast<uint32_t*>(&h);
 }
 
+// 16-byte store to a shared-memory address
+__device__ __forceinline__ void sts_v4(uint32_t addr, uint4 v) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+               : "memory");
+}
+
 // Bounded wait by one thread; on timeout the error flag is raised and the wait is retried once
 // (bounded) so that no copy or MMA is left writing into shared memory that is about to be reused.
 __device__ __forceinline__ void wait_or_flag(uint64_t* m, uint32_t parity, int* err) {
@@ -194,6 +200,7 @@ __global__ void __launch_bounds__(128) k_project_generic(SketchArgs a, const __g
 constexpr int RG_THREADS = 320;
 constexpr int RG_STAGES = 3;
 constexpr int RG_FROWS = 72;                                   // field rows per stage (2 S_a + D_t <= 72)
+constexpr int RG_ND = 4, RG_NS = 2;                            // detectors and sources of a former's work unit
 constexpr uint32_t RG_B_BYTES = SK_N * SK_K * 2;               // 28,672
 constexpr uint32_t RG_F_BYTES = RG_FROWS * SK_K * 4;           // 18,432
 constexpr uint32_t RG_STAGE = RG_B_BYTES + RG_F_BYTES;         // 47,104 = 46 x 1024
@@ -284,12 +291,20 @@ __global__ void __launch_bounds__(RG_THREADS, 1)
       tc_commit(&accf);
     }
   } else {
-    // ---- A formers. Thread f keeps detector chunks (d, 8 voxels) pc = f, f + 256, ... in registers
-    // and multiplies each by the matching chunk of every source of the item (those reads are warp
-    // broadcasts), so each field value is read from shared memory about once per K-step.
+    // ---- A formers. Work unit (chunk ch of 8 voxels, a group of RG_ND detectors, a group of RG_NS
+    // sources): the unit's RG_ND detector and RG_NS source chunks are read into registers once and
+    // give RG_NS x RG_ND chunk products, so a K-step reads each detector chunk 2 S_a / RG_NS times and
+    // each source chunk D_t / RG_ND times from shared memory, whose bandwidth the TMA copies and the
+    // MMAs share with these loads (one product per detector and source chunk read 8 times over).
+    // The eight lanes of a 16-byte load phase read chunks ch = 0..7 of one row: lanes with ch >= 4
+    // read their chunk's second half first, so that the phase's eight 16-byte words fall on distinct
+    // bank groups (ch * 32 + 16 * (ch >> 2) mod 128 is a permutation of 16 * 0..7); [0] is the half
+    // read first, and the products keep that order until the store puts the halves in place.
     const int f = tid - 64;
     const int rows = a.S_a * a.D_t;
-    const int C = a.D_t * 8;
+    const int nsrc = 2 * a.S_a;
+    const int ndg = (a.D_t + RG_ND - 1) / RG_ND, nsg = (nsrc + RG_NS - 1) / RG_NS;
+    const int nunit = 8 * ndg * nsg;
     // rows that no pair maps to stay zero: write them once in both A stages
     for (int e = f; e < 2 * 2 * (SK_M - rows) * 8; e += 256) {
       const int ch = e & 7, rr = rows + ((e >> 3) % (SK_M - rows)), sa = (e >> 3) / (SK_M - rows);
@@ -302,36 +317,40 @@ __global__ void __launch_bounds__(RG_THREADS, 1)
       if (u >= 2 && !mbar_wait_bounded(&aempty[as], (uint32_t)((u / 2 - 1) & 1))) atomicExch(a.err, 1);
       const float* fps = reinterpret_cast<const float*>(base + (size_t)st * RG_STAGE + RG_B_BYTES);
       const float* fpd = fps + 2 * a.S_a * SK_K;
-      uint8_t* At = abuf + (size_t)as * RG_A_STAGE;
-      // the eight lanes of a 16-byte access phase read chunks ch = 0..7 of one row: lanes with
-      // ch >= 4 read their chunk's second half first, so that the phase's eight 16-byte words fall
-      // on distinct bank groups (ch * 32 + 16 * (ch >> 2) mod 128 is a permutation of 16 * 0..7)
-      for (int pc = f; pc < C; pc += 256) {
-        const int dl = pc >> 3, ch = pc & 7;
+      const uint32_t At = smem_addr(abuf + (size_t)as * RG_A_STAGE);
+      for (int w = f; w < nunit; w += 256) {
+        const int ch = w & 7, rest = w >> 3;
+        const int dg = rest % ndg, sg = rest / ndg;
         const int h0 = (ch >> 2) * 4, h1 = 4 - h0;
-        float4 d0v = *reinterpret_cast<const float4*>(fpd + dl * SK_K + ch * 8 + h0);
-        float4 d1v = *reinterpret_cast<const float4*>(fpd + dl * SK_K + ch * 8 + h1);
-        if (h0) {
-          const float4 t = d0v;
-          d0v = d1v;
-          d1v = t;
+        float4 dv[RG_ND][2], sv[RG_NS][2];
+#pragma unroll
+        for (int j = 0; j < RG_ND; ++j) {
+          const int d = min(dg * RG_ND + j, a.D_t - 1);
+          dv[j][0] = *reinterpret_cast<const float4*>(fpd + d * SK_K + ch * 8 + h0);
+          dv[j][1] = *reinterpret_cast<const float4*>(fpd + d * SK_K + ch * 8 + h1);
         }
-        for (int sl = 0; sl < 2 * a.S_a; ++sl) {
+#pragma unroll
+        for (int i = 0; i < RG_NS; ++i) {
+          const int sl = min(sg * RG_NS + i, nsrc - 1);
+          sv[i][0] = *reinterpret_cast<const float4*>(fps + sl * SK_K + ch * 8 + h0);
+          sv[i][1] = *reinterpret_cast<const float4*>(fps + sl * SK_K + ch * 8 + h1);
+        }
+#pragma unroll
+        for (int i = 0; i < RG_NS; ++i) {
+          const int sl = sg * RG_NS + i;
           const int acc = sl >= a.S_a ? 1 : 0;
-          const int rr = (sl - acc * a.S_a) * a.D_t + dl;
-          float4 s0v = *reinterpret_cast<const float4*>(fps + sl * SK_K + ch * 8 + h0);
-          float4 s1v = *reinterpret_cast<const float4*>(fps + sl * SK_K + ch * 8 + h1);
-          if (h0) {
-            const float4 t = s0v;
-            s0v = s1v;
-            s1v = t;
+#pragma unroll
+          for (int j = 0; j < RG_ND; ++j) {
+            const int dl = dg * RG_ND + j;
+            if (sl >= nsrc || dl >= a.D_t) continue;
+            const int rr = (sl - acc * a.S_a) * a.D_t + dl;
+            const uint32_t p0 = pack_bf16x2(sv[i][0].x * dv[j][0].x, sv[i][0].y * dv[j][0].y);
+            const uint32_t p1 = pack_bf16x2(sv[i][0].z * dv[j][0].z, sv[i][0].w * dv[j][0].w);
+            const uint32_t p2 = pack_bf16x2(sv[i][1].x * dv[j][1].x, sv[i][1].y * dv[j][1].y);
+            const uint32_t p3 = pack_bf16x2(sv[i][1].z * dv[j][1].z, sv[i][1].w * dv[j][1].w);
+            const uint4 pk = h0 ? make_uint4(p2, p3, p0, p1) : make_uint4(p0, p1, p2, p3);
+            sts_v4(At + acc * SK_A_BYTES + sw128_offset(rr, ch * 8), pk);
           }
-          uint4 pk;
-          pk.x = pack_bf16x2(s0v.x * d0v.x, s0v.y * d0v.y);
-          pk.y = pack_bf16x2(s0v.z * d0v.z, s0v.w * d0v.w);
-          pk.z = pack_bf16x2(s1v.x * d1v.x, s1v.y * d1v.y);
-          pk.w = pack_bf16x2(s1v.z * d1v.z, s1v.w * d1v.w);
-          *reinterpret_cast<uint4*>(At + acc * SK_A_BYTES + sw128_offset(rr, ch * 8)) = pk;
         }
       }
       fence_async_smem();
@@ -400,16 +419,20 @@ __global__ void k_range_reduce(const float* __restrict__ part, int nsplit, long 
 // B^T[(c,x), k] += -h^3 sum_(l,s,d) eps_c(l) phi_s(x) phi_d(x) Q[(s,d,l), k] for a tile of 128 voxels
 // and two chromophores (two 128 x 224 accumulators sharing each A tile). K runs over the pairs of
 // each wavelength (padded to a multiple of 64 per wavelength). The tile's fields of the current
-// wavelength (n_src + n_det rows of 128 voxels, FP32) stay in shared memory while its K-steps run.
-//   warp 0        TMA: the two B tiles (eps_c-scaled Q, 224 x 64 BF16 each) per K-step;
+// wavelength (n_src + n_det rows of 128 voxels, FP32) stay in shared memory while its K-steps run;
+// with n_src + n_det <= 64 the field buffer holds two wavelengths, so the next one arrives while
+// the current one is formed.
+//   warp 0        TMA: the B tiles (eps_c-scaled Q, 224 x 64 BF16), one stage per (K-step,
+//                 chromophore): four stages of one tile each, so that loads run 1.5 K-steps ahead;
 //   warp 1        one thread issues the MMAs;
-//   warp 2        TMA: the field block of each wavelength, once its predecessor is consumed;
+//   warp 2        TMA: the field block of each wavelength, once its buffer is consumed;
 //   warps 3..10   form the A tiles and read the accumulators back.
 constexpr int PJ_THREADS = 352;
 constexpr int PJ_M = 128;                                     // voxels per tile
-constexpr uint32_t PJ_B_STAGE = 2 * SK_N * SK_K * 2;          // two B tiles: 57,344 B
+constexpr uint32_t PJ_B_TILE = SK_N * SK_K * 2;               // one B tile: 28,672 B
+constexpr int PJ_B_STAGES = 4;
 constexpr uint32_t PJ_F_BYTES = 128 * PJ_M * 4;               // n_src + n_det <= 128 rows: 65,536 B
-constexpr size_t PJ_SMEM = 2 * (size_t)PJ_B_STAGE + 2 * (size_t)SK_A_BYTES + PJ_F_BYTES + 1024;
+constexpr size_t PJ_SMEM = PJ_B_STAGES * (size_t)PJ_B_TILE + 2 * (size_t)SK_A_BYTES + PJ_F_BYTES + 1024;
 
 struct ProjArgs {
   int ns, nd, nlam, nc, Kl;  // ns: sources of the range src0 .. src0 + ns - 1; Kl: K-steps per wavelength
@@ -426,24 +449,28 @@ __global__ void __launch_bounds__(PJ_THREADS, 1)
                  const __grid_constant__ CUtensorMap mapPd) {
   extern __shared__ uint8_t sk_dsm[];
   uint8_t* base = align1024(sk_dsm);
-  uint8_t* abuf = base + 2 * (size_t)PJ_B_STAGE;
-  float* fld = reinterpret_cast<float*>(abuf + 2 * (size_t)SK_A_BYTES);  // [ns + nd][128]
-  __shared__ uint64_t bfull[2], bempty[2], afull[2], aempty[2], ffull, fempty, accf;
+  uint8_t* abuf = base + PJ_B_STAGES * (size_t)PJ_B_TILE;
+  float* fld = reinterpret_cast<float*>(abuf + 2 * (size_t)SK_A_BYTES);  // [nfb][ns + nd][128]
+  __shared__ uint64_t bfull[PJ_B_STAGES], bempty[PJ_B_STAGES], afull[2], aempty[2], ffull[2], fempty[2], accf;
   __shared__ uint32_t s_tmem;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int tile = blockIdx.x / ((a.nc + 1) / 2), cp = blockIdx.x - tile * ((a.nc + 1) / 2);
   const long long x0 = (long long)tile * PJ_M;
   const int c0 = 2 * cp;
   const int nku = a.nlam * a.Kl;
+  const int frow = (a.ns + a.nd) * PJ_M;                        // floats of one wavelength's field block
+  const int nfb = 2 * frow * 4 <= (int)PJ_F_BYTES ? 2 : 1;      // field buffers
   if (tid == 0) {
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < PJ_B_STAGES; ++q) {
       mbar_init(&bfull[q], 1);
       mbar_init(&bempty[q], 1);
+    }
+    for (int q = 0; q < 2; ++q) {
       mbar_init(&afull[q], 8);
       mbar_init(&aempty[q], 1);
+      mbar_init(&ffull[q], 1);
+      mbar_init(&fempty[q], 8);
     }
-    mbar_init(&ffull, 1);
-    mbar_init(&fempty, 8);
     mbar_init(&accf, 1);
     mbar_fence_init();
   }
@@ -455,58 +482,72 @@ __global__ void __launch_bounds__(PJ_THREADS, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      for (int u = 0; u < nku; ++u) {
-        const int bs = u & 1;
-        if (u >= 2) wait_or_flag(&bempty[bs], (uint32_t)((u / 2 - 1) & 1), a.err);
-        uint8_t* dst = base + (size_t)bs * PJ_B_STAGE;
-        mbar_expect_tx(&bfull[bs], PJ_B_STAGE);
-        tma_load_3d(dst, &mapB, &bfull[bs], u * SK_K, 0, c0);
-        tma_load_3d(dst + SK_N * SK_K * 2, &mapB, &bfull[bs], u * SK_K, 0, c0 + 1);
+      // stage use q = 2 u + h: K-step u, chromophore c0 + h
+      for (int q = 0; q < 2 * nku; ++q) {
+        const int bs = q % PJ_B_STAGES;
+        if (q >= PJ_B_STAGES) wait_or_flag(&bempty[bs], (uint32_t)((q / PJ_B_STAGES - 1) & 1), a.err);
+        mbar_expect_tx(&bfull[bs], PJ_B_TILE);
+        tma_load_3d(base + (size_t)bs * PJ_B_TILE, &mapB, &bfull[bs], (q >> 1) * SK_K, 0, c0 + (q & 1));
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       constexpr uint32_t IDESC = idesc_bf16_f32(SK_M, SK_N);
       for (int u = 0; u < nku; ++u) {
-        const int bs = u & 1;
-        wait_or_flag(&bfull[bs], (uint32_t)((u >> 1) & 1), a.err);
-        wait_or_flag(&afull[bs], (uint32_t)((u >> 1) & 1), a.err);
-        tc_fence_after();
-        const uint32_t b_addr = smem_addr(base + (size_t)bs * PJ_B_STAGE);
-        const uint32_t a_addr = smem_addr(abuf + (size_t)bs * SK_A_BYTES);
+        const int as = u & 1;
+        wait_or_flag(&afull[as], (uint32_t)((u >> 1) & 1), a.err);
+        const uint32_t a_addr = smem_addr(abuf + (size_t)as * SK_A_BYTES);
 #pragma unroll
-        for (int acc = 0; acc < 2; ++acc)
+        for (int acc = 0; acc < 2; ++acc) {
+          const int q = 2 * u + acc, bs = q % PJ_B_STAGES;
+          wait_or_flag(&bfull[bs], (uint32_t)((q / PJ_B_STAGES) & 1), a.err);
+          tc_fence_after();
+          const uint32_t b_addr = smem_addr(base + (size_t)bs * PJ_B_TILE);
 #pragma unroll
           for (int kk = 0; kk < SK_K / 16; ++kk)
             tc_mma_bf16(tmem + (uint32_t)(acc * 256), smem_desc_sw128(a_addr + kk * 32),
-                        smem_desc_sw128(b_addr + acc * SK_N * SK_K * 2 + kk * 32), IDESC, (u > 0 || kk > 0) ? 1u : 0u);
-        tc_commit(&bempty[bs]);
-        tc_commit(&aempty[bs]);
+                        smem_desc_sw128(b_addr + kk * 32), IDESC, (u > 0 || kk > 0) ? 1u : 0u);
+          tc_commit(&bempty[bs]);
+        }
+        tc_commit(&aempty[as]);
       }
       tc_commit(&accf);
     }
   } else if (warp == 2) {
     if (lane == 0) {
-      const uint32_t fb = (uint32_t)(a.ns + a.nd) * PJ_M * 4;
+      const uint32_t fb = (uint32_t)frow * 4;
       for (int l = 0; l < a.nlam; ++l) {
-        if (l >= 1) wait_or_flag(&fempty, (uint32_t)((l - 1) & 1), a.err);
-        mbar_expect_tx(&ffull, fb);
-        tma_load_3d(fld, &mapPs, &ffull, (int)x0, a.src0, l);
-        tma_load_3d(fld + a.ns * PJ_M, &mapPd, &ffull, (int)x0, 0, l);
+        const int b = l % nfb;
+        float* dst = fld + (size_t)b * frow;
+        if (l >= nfb) wait_or_flag(&fempty[b], (uint32_t)((l / nfb - 1) & 1), a.err);
+        mbar_expect_tx(&ffull[b], fb);
+        tma_load_3d(dst, &mapPs, &ffull[b], (int)x0, a.src0, l);
+        tma_load_3d(dst + a.ns * PJ_M, &mapPd, &ffull[b], (int)x0, 0, l);
       }
     }
   } else {
-    // ---- A formers: thread f takes voxel row (id & 127) and pair chunk (id >> 7) for id = j*256 + f
+    // ---- A formers: thread f takes voxel row (id & 127) and pair chunk (id >> 7) for id = j*256 + f.
+    // With n_det % 8 == 0 the chunk's eight pairs share their source and take detectors d .. d + 7;
+    // the thread keeps those eight detector values of its row in registers while d stays the same
+    // (for every K-step of a wavelength when n_det divides 64 or 64 divides it), so a K-step mostly
+    // reads one source value per chunk from shared memory.
     const int f = tid - 96;
     const int npairs = a.ns * a.nd;
     const bool nd8 = (a.nd & 7) == 0;
-    const float* psm = fld;
-    const float* pdm = fld + a.ns * PJ_M;
+    float dreg[4][8];
+    int dkey[4] = {-1, -1, -1, -1};  // detector offset d of the values in dreg[j] (-1: none)
     for (int u = 0; u < nku; ++u) {
       const int l = u / a.Kl, kq = u - l * a.Kl, as = u & 1;
-      if (kq == 0 && !mbar_wait_bounded(&ffull, (uint32_t)(l & 1))) atomicExch(a.err, 1);
+      const int fbi = l % nfb;
+      const float* psm = fld + (size_t)fbi * frow;
+      const float* pdm = psm + a.ns * PJ_M;
+      if (kq == 0) {
+        if (!mbar_wait_bounded(&ffull[fbi], (uint32_t)((l / nfb) & 1))) atomicExch(a.err, 1);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) dkey[j] = -1;  // a new wavelength's fields
+      }
       if (u >= 2 && !mbar_wait_bounded(&aempty[as], (uint32_t)((u / 2 - 1) & 1))) atomicExch(a.err, 1);
-      uint8_t* At = abuf + (size_t)as * SK_A_BYTES;
+      const uint32_t At = smem_addr(abuf + (size_t)as * SK_A_BYTES);
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int id = j * 256 + f;
@@ -515,11 +556,15 @@ __global__ void __launch_bounds__(PJ_THREADS, 1)
         int s = q0 / a.nd, d = q0 - s * a.nd;
         float v[8];
         if (nd8 && q0 + 8 <= npairs) {
-          // the 8 pairs share their source (n_det % 8 == 0): one source value, 8 detector values
-          const float sv = psm[s * PJ_M + row];
-          const float* pr = pdm + d * PJ_M + row;
+          if (d != dkey[j]) {
+            const float* pr = pdm + d * PJ_M + row;
 #pragma unroll
-          for (int i = 0; i < 8; ++i) v[i] = sv * pr[i * PJ_M];
+            for (int i = 0; i < 8; ++i) dreg[j][i] = pr[i * PJ_M];
+            dkey[j] = d;
+          }
+          const float sv = psm[s * PJ_M + row];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) v[i] = sv * dreg[j][i];
         } else {
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
@@ -537,13 +582,13 @@ __global__ void __launch_bounds__(PJ_THREADS, 1)
         pk.y = pack_bf16x2(v[2], v[3]);
         pk.z = pack_bf16x2(v[4], v[5]);
         pk.w = pack_bf16x2(v[6], v[7]);
-        *reinterpret_cast<uint4*>(At + sw128_offset(row, ch * 8)) = pk;
+        sts_v4(At + sw128_offset(row, ch * 8), pk);
       }
       fence_async_smem();
       __syncwarp();
       if (lane == 0) {
         mbar_arrive(&afull[as]);
-        if (kq == a.Kl - 1) mbar_arrive(&fempty);
+        if (kq == a.Kl - 1) mbar_arrive(&fempty[fbi]);
       }
     }
     // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 of accumulator (w - 3) / 4

@@ -54,7 +54,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* m, uint32_t parity) 
   return mbar_wait_polls(m, parity, WAIT_POLLS);
 }
 
-
 // 4-D tiled tensor load global -> shared; coordinates innermost first. The x coordinate times the
 // element size must be a multiple of 16 bytes; out-of-range elements are filled with zeros.
 __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* m, int x, int y, int z,

@@ -101,6 +101,40 @@ def test_sketch_project_pass_accumulates_over_slices(lib, case):
     assert err_i.max() <= 2e-3, err_i.max()
 
 
+def test_sketch_project_double_buffered_fields(lib):
+    """n_src + n_det <= 64: the projection keeps two wavelengths' field blocks in shared memory (the
+    next one loads while the current one is formed); five wavelengths cycle both buffers, and three
+    chromophores leave the second accumulator of the last chromophore pair empty. Compared with the
+    exact emulation of the BF16 operands."""
+    p = workloads.make_problem(workloads.Grid(20, 16, 12, 2.0), 6, 10, 5, seed=45, n_chrom=3,
+                               geometry="transmission", margin=0)
+    rs, rd = osolve.fields_separable(p)
+    rs, rd = rs.astype(np.float32), rd.astype(np.float32)
+    N, nc, ncols = p.grid.N, p.n_chrom, 200
+    nd, nl = p.n_det, p.n_lambda
+    Q = workloads.gaussian(46, (p.M, ncols)).astype(np.float32)
+    Qp = np.zeros((p.M, 224), dtype=np.float32)
+    Qp[:, :ncols] = Q
+    with lib.Context.from_problem(p, precision="mixed", tol=1e-8, tol_cw=0.0) as ctx:
+        Bt = torch.zeros(nc * N, 224, device="cuda")
+        ctx.sketch_project(torch.tensor(rs, device="cuda"), torch.tensor(rd, device="cuda"), 0, nl,
+                           torch.tensor(Qp, device="cuda"), ncols, Bt)
+        Bt = Bt.cpu().double().numpy()
+    assert np.all(Bt[:, ncols:] == 0.0)
+    Bt = Bt[:, :ncols]
+    h3 = p.grid.h ** 3
+    ref_i = np.zeros((nc * N, ncols))
+    for lam in range(nl):
+        for s in range(p.n_src):
+            A = bf16_round(rs[lam, s][None, :] * rd[lam])
+            rows = [(s * nd + d) * nl + lam for d in range(nd)]
+            for c in range(nc):
+                Bq = bf16_round((np.float32(p.eps[lam, c]) * Q[rows]).astype(np.float32))
+                ref_i[c * N:(c + 1) * N] += -h3 * A.T @ Bq
+    err_i = np.abs(Bt - ref_i).max(axis=0) / np.abs(ref_i).max(axis=0)
+    assert err_i.max() <= 2e-3, err_i.max()
+
+
 def test_rank_r_factorisation_near_optimal(lib, case):
     """Full pipeline (range, orthonormalisation, projection over two row blocks, recompression):
     the error of U S V^T is within a small factor of the exact optimum sigma_(r+1) plus the BF16
