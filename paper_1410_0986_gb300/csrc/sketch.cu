@@ -304,7 +304,17 @@ __global__ void __launch_bounds__(RG_THREADS, 1)
     const int rows = a.S_a * a.D_t;
     const int nsrc = 2 * a.S_a;
     const int ndg = (a.D_t + RG_ND - 1) / RG_ND, nsg = (nsrc + RG_NS - 1) / RG_NS;
-    const int nunit = 8 * ndg * nsg;
+    const int nunit = 8 * ndg * nsg;  // at most 400 (D_t = 5): two rounds of 256 formers
+    // this thread's work units w = f and f + 256 (chunk, detector group, source group), fixed over K
+    const int nrounds = f < nunit ? (f + 256 < nunit ? 2 : 1) : 0;
+    int uch[2], udg[2], usg[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int w = f + r * 256;
+      uch[r] = w & 7;
+      udg[r] = (w >> 3) % ndg;
+      usg[r] = (w >> 3) / ndg;
+    }
     // rows that no pair maps to stay zero: write them once in both A stages
     for (int e = f; e < 2 * 2 * (SK_M - rows) * 8; e += 256) {
       const int ch = e & 7, rr = rows + ((e >> 3) % (SK_M - rows)), sa = (e >> 3) / (SK_M - rows);
@@ -318,9 +328,9 @@ __global__ void __launch_bounds__(RG_THREADS, 1)
       const float* fps = reinterpret_cast<const float*>(base + (size_t)st * RG_STAGE + RG_B_BYTES);
       const float* fpd = fps + 2 * a.S_a * SK_K;
       const uint32_t At = smem_addr(abuf + (size_t)as * RG_A_STAGE);
-      for (int w = f; w < nunit; w += 256) {
-        const int ch = w & 7, rest = w >> 3;
-        const int dg = rest % ndg, sg = rest / ndg;
+      for (int r = 0; r < 2; ++r) {
+        if (r >= nrounds) break;
+        const int ch = uch[r], dg = udg[r], sg = usg[r];
         const int h0 = (ch >> 2) * 4, h1 = 4 - h0;
         float4 dv[RG_ND][2], sv[RG_NS][2];
 #pragma unroll
@@ -535,25 +545,38 @@ __global__ void __launch_bounds__(PJ_THREADS, 1)
     const int npairs = a.ns * a.nd;
     const bool nd8 = (a.nd & 7) == 0;
     float dreg[4][8];
-    int dkey[4] = {-1, -1, -1, -1};  // detector offset d of the values in dreg[j] (-1: none)
+    int dkey[4];       // detector offset d of the values in dreg[j] (-1: none)
+    int sj[4], dj[4];  // source and detector of the first pair of item j's chunk at this K-step
+    int l = 0, kq = 0, fbi = 0;  // wavelength, K-step in it, field buffer (no divisions in the loop)
     for (int u = 0; u < nku; ++u) {
-      const int l = u / a.Kl, kq = u - l * a.Kl, as = u & 1;
-      const int fbi = l % nfb;
+      const int as = u & 1;
       const float* psm = fld + (size_t)fbi * frow;
       const float* pdm = psm + a.ns * PJ_M;
       if (kq == 0) {
-        if (!mbar_wait_bounded(&ffull[fbi], (uint32_t)((l / nfb) & 1))) atomicExch(a.err, 1);
+        const uint32_t fpar = (uint32_t)((nfb == 2 ? (l >> 1) : l) & 1);
+        if (!mbar_wait_bounded(&ffull[fbi], fpar)) atomicExch(a.err, 1);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) dkey[j] = -1;  // a new wavelength's fields
+        for (int j = 0; j < 4; ++j) {  // a new wavelength's fields
+          const int q0 = ((j * 256 + f) >> 7) * 8;
+          sj[j] = q0 / a.nd;
+          dj[j] = q0 - sj[j] * a.nd;
+          dkey[j] = -1;
+        }
       }
-      if (u >= 2 && !mbar_wait_bounded(&aempty[as], (uint32_t)((u / 2 - 1) & 1))) atomicExch(a.err, 1);
+      if (u >= 2 && !mbar_wait_bounded(&aempty[as], (uint32_t)(((u >> 1) - 1) & 1))) atomicExch(a.err, 1);
       const uint32_t At = smem_addr(abuf + (size_t)as * SK_A_BYTES);
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int id = j * 256 + f;
         const int row = id & (PJ_M - 1), ch = id >> 7;
         const int q0 = kq * SK_K + ch * 8;
-        int s = q0 / a.nd, d = q0 - s * a.nd;
+        int s = sj[j], d = dj[j];
+        // the next K-step's first pair of this chunk is 64 pairs on
+        dj[j] += SK_K;
+        while (dj[j] >= a.nd) {
+          dj[j] -= a.nd;
+          ++sj[j];
+        }
         float v[8];
         if (nd8 && q0 + 8 <= npairs) {
           if (d != dkey[j]) {
@@ -589,6 +612,11 @@ __global__ void __launch_bounds__(PJ_THREADS, 1)
       if (lane == 0) {
         mbar_arrive(&afull[as]);
         if (kq == a.Kl - 1) mbar_arrive(&fempty[fbi]);
+      }
+      if (++kq == a.Kl) {
+        kq = 0;
+        ++l;
+        fbi = nfb == 2 ? fbi ^ 1 : 0;
       }
     }
     // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 of accumulator (w - 3) / 4

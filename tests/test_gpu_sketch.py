@@ -185,6 +185,8 @@ def _range_ref_bf16(p, rs, rd, om_b, rows_sel):
     ((24, 20, 16), 30, 24, 2),
     # more than 64 detectors: two detector blocks, the second partial
     ((16, 16, 12), 6, 100, 1),
+    # five detectors: 25 sources per accumulator, 400 former work units (two per former thread)
+    ((16, 12, 10), 60, 5, 1),
 ])
 def test_sketch_range_shapes(lib, shape):
     (nx, ny, nz), ns, nd, nl = shape
