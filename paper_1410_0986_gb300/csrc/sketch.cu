@@ -441,6 +441,8 @@ constexpr int PJ_THREADS = 352;
 constexpr int PJ_M = 128;                                     // voxels per tile
 constexpr uint32_t PJ_B_TILE = SK_N * SK_K * 2;               // one B tile: 28,672 B
 constexpr int PJ_B_STAGES = 4;
+constexpr int PJ_BT0_COLS = 116;                              // epilogue boxes: columns 0..115, 116..223
+constexpr uint32_t PJ_STG_BYTES = 32 * PJ_BT0_COLS * 4;       // one warp's staged rows: 14,848 B (116 x 128)
 constexpr uint32_t PJ_F_BYTES = 128 * PJ_M * 4;               // n_src + n_det <= 128 rows: 65,536 B
 constexpr size_t PJ_SMEM = PJ_B_STAGES * (size_t)PJ_B_TILE + 2 * (size_t)SK_A_BYTES + PJ_F_BYTES + 1024;
 
@@ -456,7 +458,8 @@ struct ProjArgs {
 
 __global__ void __launch_bounds__(PJ_THREADS, 1)
     k_project_ws(ProjArgs a, const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapPs,
-                 const __grid_constant__ CUtensorMap mapPd) {
+                 const __grid_constant__ CUtensorMap mapPd, const __grid_constant__ CUtensorMap mapBt0,
+                 const __grid_constant__ CUtensorMap mapBt1) {
   extern __shared__ uint8_t sk_dsm[];
   uint8_t* base = align1024(sk_dsm);
   uint8_t* abuf = base + PJ_B_STAGES * (size_t)PJ_B_TILE;
@@ -619,30 +622,43 @@ __global__ void __launch_bounds__(PJ_THREADS, 1)
         fbi = nfb == 2 ? fbi ^ 1 : 0;
       }
     }
-    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 of accumulator (w - 3) / 4
+    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 of accumulator (w - 3) / 4, i.e. the
+    // scaled rows of 32 voxels, stages them in the (now idle) B / A stage buffers and adds them to
+    // B^T with TMA reductions, columns 0..115 and then 116..223 (row pitches of 29 and 27 16-byte
+    // units: the lanes' 16-byte stores fall on distinct bank groups). B^T is never read by the SM.
     if (!mbar_wait_bounded(&accf, 0u)) atomicExch(a.err, 1);
     tc_fence_after();
     const int q4 = warp & 3, acc = (warp - 3) >> 2;
-    const long long x = x0 + q4 * 32 + lane;
     const int c = c0 + acc;
-    const bool ok = nku > 0 && x < a.N && c < a.nc;
-    float* dst = a.Bt + ((long long)c * a.N + x) * a.ldB;
+    const long long xr = x0 + q4 * 32;  // first voxel of the warp's rows
+    const bool ok = nku > 0 && xr < a.N && c < a.nc;
+    float* stg = reinterpret_cast<float*>(base + (size_t)(warp - 3) * PJ_STG_BYTES);
     const uint32_t tbase = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(acc * 256);
-    for (int k0 = 0; k0 < SK_N; k0 += 16) {
-      float v[16];
-      tmem_ld16(tbase + (uint32_t)k0, v);
-      if (ok) {
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+      const int g0 = h ? PJ_BT0_COLS / 4 : 0, g1 = h ? SK_N / 4 : PJ_BT0_COLS / 4;  // 4-column groups
+      const int pitch = h ? SK_N - PJ_BT0_COLS : PJ_BT0_COLS;                          // floats per staged row
+      for (int k0 = (g0 * 4) & ~15; k0 < g1 * 4; k0 += 16) {
+        float v[16];
+        tmem_ld16(tbase + (uint32_t)k0, v);
 #pragma unroll
         for (int q = 0; q < 16; q += 4) {
-          float4 o = *reinterpret_cast<float4*>(dst + k0 + q);
-          o.x = fmaf(a.scale, v[q], o.x);
-          o.y = fmaf(a.scale, v[q + 1], o.y);
-          o.z = fmaf(a.scale, v[q + 2], o.z);
-          o.w = fmaf(a.scale, v[q + 3], o.w);
-          *reinterpret_cast<float4*>(dst + k0 + q) = o;
+          const int g = (k0 + q) >> 2;
+          if (g < g0 || g >= g1) continue;
+          *reinterpret_cast<float4*>(stg + lane * pitch + (g - g0) * 4) =
+              make_float4(a.scale * v[q], a.scale * v[q + 1], a.scale * v[q + 2], a.scale * v[q + 3]);
         }
       }
+      fence_async_smem();
+      __syncwarp();
+      if (lane == 0 && ok) {
+        tma_reduce_add_3d(h ? &mapBt1 : &mapBt0, stg, g0 * 4, (int)xr, c);
+        bulk_commit_group();
+        bulk_wait_read_all();  // the staging rows are reused by the second half
+      }
+      __syncwarp();
     }
+    if (lane == 0 && ok) bulk_wait_all();
   }
   tc_fence_before();
   __syncthreads();
@@ -766,6 +782,22 @@ int encode_f32_map(hydot_ctx* ctx, const void* base, long long d0, long long d1,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(ctx, HYDOT_ERR_CUDA, "cuTensorMapEncodeTiled failed for a field slab map");
+  return HYDOT_OK;
+}
+
+// 3-D FP32 map over B^T [(c, x)][ldB] as {224 columns, N voxels, nc chromophores} with a {b0, 32, 1}
+// box, for the projection epilogue's TMA reductions (voxels past N are outside the map, so a partial
+// voxel tile never reaches the next chromophore's rows).
+int encode_bt_map(hydot_ctx* ctx, float* Bt, long long N, int nc, long long ldB, int b0, CUtensorMap* map) {
+  auto enc = tensor_map_encoder(ctx);
+  if (!enc) return HYDOT_ERR_CUDA;
+  cuuint64_t dims[3] = {(cuuint64_t)SK_N, (cuuint64_t)N, (cuuint64_t)nc};
+  cuuint64_t strides[2] = {(cuuint64_t)ldB * 4, (cuuint64_t)ldB * 4 * N};
+  cuuint32_t box[3] = {(cuuint32_t)b0, 32, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, Bt, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(ctx, HYDOT_ERR_CUDA, "cuTensorMapEncodeTiled failed for the B^T map");
   return HYDOT_OK;
 }
 
@@ -900,6 +932,9 @@ int sketch_project_impl(hydot_ctx* ctx, const float* ps, const float* pd, int la
     if ((rc = encode_b_map(ctx, Qc, nlam * Pl, nc, &mapB))) return rc;
     if ((rc = encode_f32_map(ctx, ps, N, ctx->n_src, nlam, PJ_M, ns, &mapPs))) return rc;
     if ((rc = encode_f32_map(ctx, pd, N, nd, nlam, PJ_M, nd, &mapPd))) return rc;
+    CUtensorMap mapBt0, mapBt1;
+    if ((rc = encode_bt_map(ctx, Bt, N, nc, ldB, PJ_BT0_COLS, &mapBt0))) return rc;
+    if ((rc = encode_bt_map(ctx, Bt, N, nc, ldB, SK_N - PJ_BT0_COLS, &mapBt1))) return rc;
     ProjArgs a{};
     a.ns = ns;
     a.src0 = src0;
@@ -914,7 +949,7 @@ int sketch_project_impl(hydot_ctx* ctx, const float* ps, const float* pd, int la
     a.err = ctx->d_err;
     const long long grid = ((N + PJ_M - 1) / PJ_M) * ((nc + 1) / 2);
     cudaEvent_t t0 = timer_begin(ctx);
-    k_project_ws<<<(unsigned)grid, PJ_THREADS, PJ_SMEM, ctx->stream>>>(a, mapB, mapPs, mapPd);
+    k_project_ws<<<(unsigned)grid, PJ_THREADS, PJ_SMEM, ctx->stream>>>(a, mapB, mapPs, mapPd, mapBt0, mapBt1);
     ++ctx->launches;
     timer_end(ctx, t0, HYDOT_KERNEL_SKETCH_PROJECT, 2.0 * (double)nc * (double)N * (double)P * ncols);
     HYDOT_CUDA_TRY(ctx, cudaGetLastError());
