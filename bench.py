@@ -55,9 +55,10 @@ KERNEL_NAMES = {"iter": "inner CG iteration (every pass of one Krylov iteration;
                 "sketch_project": "k_project_ws (tensor-core B^T += J^T Q)"}
 # DRAM bytes (read + write, ncu) per algorithmic byte, from the captures summarised under profiles/
 # (smaller cases of the same kernels, scaled by the units processed: active fields or rows). The
-# CG iteration's (two-pass form, the default): k_dir_roll + k_update_roll on 256 fields, a 1.4 GB
-# working set (eleven times L2), per 24 B algorithmic bytes per cell-iteration.
-DRAM_PER_ALGORITHMIC_BYTE = {"iter": (403.75e6 + 174.34e6 + 604.92e6 + 345.27e6) / (256 * 196608 * 24),
+# CG iteration's (two-pass form, the default): pass 1 on paired cells (k_dir_xp, the variant the
+# autotuner keeps on this grid) + k_update_roll on 256 fields, a 1.4 GB working set (eleven times
+# L2), per 24 B algorithmic bytes per cell-iteration.
+DRAM_PER_ALGORITHMIC_BYTE = {"iter": (403.76e6 + 169.56e6 + 604.92e6 + 345.27e6) / (256 * 196608 * 24),
                              "born_rows": (893.83e6 + 12.96e9) / (4096 * 4 * 196608 * 4)}
 TRAFFIC_NOTE = {"iter": "ncu on one two-pass iteration over 256 active fields (1.4 GB of vectors, profiles/"
                         "cg_iteration_256fields_64x64x48.md), scaled by active fields: the 32 B per cell the "
