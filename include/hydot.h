@@ -448,6 +448,19 @@ int hydot_sketch_factor(hydot_ctx* ctx, const float* Q, long long rows, long lon
                         long long ldB, int ncols, int rank, float* U, long long ldU, double* S, float* V,
                         long long ldV);
 
+/* Geometric bisection tree of the sources (Section 4.1, Algorithm alg:geom), which orders the row
+ * blocks for the recursive compression: the box [x_lo, x_hi] x [y_lo, y_hi] is split across its
+ * longer side (the first on a tie) at the midpoint, the positions at or below the split coordinate
+ * going to the first side, recursively, until a cell holds at most leaf_max positions (or below 64
+ * levels). A side without positions is dropped, and a split that leaves one side empty makes no
+ * node. xy: HOST double [n][2]. Outputs, HOST: order int [n], the position indices leaf by leaf,
+ * depth first, first side first; nodes int [2n][4] = (lo, hi, first child, second child), a node
+ * covering order[lo .. hi-1], children -1 for a leaf; *n_nodes the number of nodes written (at most
+ * 2n - 1) and *root the index of the root. Host arithmetic only (no GPU, no context); n >= 1 and
+ * leaf_max >= 1, else HYDOT_ERR_ARG with the message in hydot_last_error(NULL). */
+int hydot_source_tree(const double* xy, int n, double x_lo, double y_lo, double x_hi, double y_hi, int leaf_max,
+                      int* order, int* nodes, int* n_nodes, int* root);
+
 /* Last error message of ctx; with ctx NULL, that of the calling thread's last failed call that
  * has no context (hydot_setup, the context-free Born call). */
 const char* hydot_last_error(const hydot_ctx* ctx);

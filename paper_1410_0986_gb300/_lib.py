@@ -28,6 +28,7 @@ EXPORTS = ("hydot_version", "hydot_setup", "hydot_set_stream", "hydot_solve_fiel
            "hydot_born_apply", "hydot_born_apply_T", "hydot_born_apply_noalloc", "hydot_solve_adjoint",
            "hydot_born_apply_T_adjoint", "hydot_sketch_range",
            "hydot_sketch_project", "hydot_sketch_orthonormalize", "hydot_sketch_rank", "hydot_sketch_merge",
+           "hydot_source_tree",
            "hydot_sketch_factor", "hydot_set_kernel_timing", "hydot_set_graphs", "hydot_get_launch_mode",
            "hydot_kernel_stats", "hydot_kernel_launches", "hydot_get_tuning", "hydot_set_absorption",
            "hydot_wait_selftest", "hydot_set_shift_guess", "hydot_shift_guess_fields",
@@ -134,6 +135,10 @@ def load(path: str = LIB_PATH) -> C.CDLL:
                                        C.c_longlong, C.c_int, C.c_longlong, C.c_double, C.c_int, vp, C.c_longlong,
                                        C.POINTER(C.c_double), vp, C.c_longlong, C.POINTER(C.c_int)]
     lib.hydot_sketch_merge.restype = C.c_int
+    dp, ip = C.POINTER(C.c_double), C.POINTER(C.c_int)
+    lib.hydot_source_tree.argtypes = [dp, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, ip, ip,
+                                      ip, ip]
+    lib.hydot_source_tree.restype = C.c_int
     lib.hydot_sketch_factor.argtypes = [vp, vp, C.c_longlong, C.c_longlong, vp, C.c_longlong, C.c_longlong, C.c_int,
                                         C.c_int, vp, C.c_longlong, C.POINTER(C.c_double), vp, C.c_longlong]
     lib.hydot_sketch_factor.restype = C.c_int

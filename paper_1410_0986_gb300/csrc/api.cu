@@ -425,6 +425,13 @@ int hydot_sketch_rank(hydot_ctx* ctx, const float* Q, long long ldQ, long long r
   });
 }
 
+int hydot_source_tree(const double* xy, int n, double x_lo, double y_lo, double x_hi, double y_hi, int leaf_max,
+                      int* order, int* nodes, int* n_nodes, int* root) {
+  return hydot::abi_guard(nullptr, [&]() -> int {
+    return hydot::source_tree_impl(xy, n, x_lo, y_lo, x_hi, y_hi, leaf_max, order, nodes, n_nodes, root);
+  });
+}
+
 int hydot_sketch_merge(hydot_ctx* ctx, const float* U1, long long ldU1, long long m1, const double* S1, const float* V1,
                        long long ldV1, int r1, const float* U2, long long ldU2, long long m2, const double* S2,
                        const float* V2, long long ldV2, int r2, long long n, double tol, int max_rank, float* U,

@@ -372,6 +372,8 @@ int sketch_orthonormalize_impl(hydot_ctx* ctx, float* Y, long long rows, int nco
                                double* smax_out);
 int sketch_rank_impl(hydot_ctx* ctx, const float* Q, long long ldQ, long long rows, int nq, const float* Y2,
                      long long ldY2, int k, double s1, double tol, int* rank, double* estimate);
+int source_tree_impl(const double* xy, int n, double x_lo, double y_lo, double x_hi, double y_hi, int leaf_max,
+                     int* order, int* nodes, int* n_nodes, int* root);
 int sketch_merge_impl(hydot_ctx* ctx, const float* U1, long long ldU1, long long m1, const double* S1, const float* V1,
                       long long ldV1, int r1, const float* U2, long long ldU2, long long m2, const double* S2,
                       const float* V2, long long ldV2, int r2, long long n, double tol, int max_rank, float* U,

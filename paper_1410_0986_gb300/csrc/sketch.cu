@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstring>
 #include <cudaTypedefs.h>
+#include <array>
 #include <vector>
 
 #include <cuda_bf16.h>
@@ -1422,6 +1423,64 @@ int sketch_merge_impl(hydot_ctx* ctx, const float* U1, long long ldU1, long long
 int tall_cross(hydot_ctx* ctx, const float* X, long long ldx, int nx, const float* Y, long long ldy, int ny,
                long long rows, std::vector<double>& C) {
   return cross(ctx, X, ldx, nx, Y, ldy, ny, rows, C);
+}
+
+
+// ---------------------------------------------------------------- source tree (alg:geom)
+namespace {
+struct TreeBuild {
+  const double* xy;
+  int leaf_max;
+  int* order;
+  int* nodes;
+  int pos = 0, cnt = 0;
+};
+
+// Node of the positions idx inside the box [lo, hi]; returns its index (a split with one empty side
+// returns the other side's node).
+int tree_split(TreeBuild& t, const std::vector<int>& idx, std::array<double, 2> lo, std::array<double, 2> hi,
+               int depth) {
+  const int start = t.pos;
+  if ((int)idx.size() <= t.leaf_max || depth > 64) {
+    for (int i : idx) t.order[t.pos++] = i;
+    const int id = t.cnt++;
+    t.nodes[4 * id] = start;
+    t.nodes[4 * id + 1] = t.pos;
+    t.nodes[4 * id + 2] = t.nodes[4 * id + 3] = -1;
+    return id;
+  }
+  const int j = (hi[0] - lo[0] >= hi[1] - lo[1]) ? 0 : 1;  // direction of the larger extent
+  const double gamma = 0.5 * (lo[j] + hi[j]);                 // midpoint split
+  std::vector<int> t1, t2;
+  for (int i : idx) (t.xy[2 * i + j] <= gamma ? t1 : t2).push_back(i);
+  std::array<double, 2> hi1 = hi, lo2 = lo;
+  hi1[j] = gamma;
+  lo2[j] = gamma;
+  int kids[2], nk = 0;
+  if (!t1.empty()) kids[nk++] = tree_split(t, t1, lo, hi1, depth + 1);
+  if (!t2.empty()) kids[nk++] = tree_split(t, t2, lo2, hi, depth + 1);
+  if (nk == 1) return kids[0];
+  const int id = t.cnt++;
+  t.nodes[4 * id] = start;
+  t.nodes[4 * id + 1] = t.pos;
+  t.nodes[4 * id + 2] = kids[0];
+  t.nodes[4 * id + 3] = kids[1];
+  return id;
+}
+}  // namespace
+
+int source_tree_impl(const double* xy, int n, double x_lo, double y_lo, double x_hi, double y_hi, int leaf_max,
+                     int* order, int* nodes, int* n_nodes, int* root) {
+  if (!xy || !order || !nodes || !n_nodes || !root || n < 1 || leaf_max < 1) {
+    set_context_free_error("hydot_source_tree: null pointer, n < 1 or leaf_max < 1");
+    return HYDOT_ERR_ARG;
+  }
+  TreeBuild t{xy, leaf_max, order, nodes};
+  std::vector<int> all((size_t)n);
+  for (int i = 0; i < n; ++i) all[(size_t)i] = i;
+  *root = tree_split(t, all, {x_lo, y_lo}, {x_hi, y_hi}, 0);
+  *n_nodes = t.cnt;
+  return HYDOT_OK;
 }
 
 }  // namespace hydot

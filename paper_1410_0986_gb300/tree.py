@@ -10,17 +10,21 @@ depth L; `paper_tolerance` inverts that bound.
 
 The sketch passes of libhydot take contiguous source ranges, so a problem's sources are first put
 in tree order (`order_problem`); every node of the tree is then a range [lo, hi) of source indices.
-This module only builds the tree and sequences library calls (range pass, orthonormalisation, rank
-estimate, projection, factorisation, merge); the arithmetic runs in libhydot.
+This module holds the tree that libhydot's hydot_source_tree computes and sequences library calls
+(range pass, orthonormalisation, rank estimate, projection, factorisation, merge); the arithmetic
+runs in libhydot.
 """
 from __future__ import annotations
 
+import ctypes as C
 import dataclasses
 import math
 from typing import Callable, List, Optional, Sequence, Tuple
 
 import numpy as np
 import torch
+
+from . import _lib
 
 NCOLS_MAX = 224
 
@@ -43,36 +47,29 @@ class Node:
 
 
 def bisection_order(xy: np.ndarray, box_lo: Sequence[float], box_hi: Sequence[float], leaf_max: int = 2):
-    """Algorithm alg:geom on 2-D source positions xy [n][2] inside the box [box_lo, box_hi].
+    """Algorithm alg:geom on 2-D source positions xy [n][2] inside the box [box_lo, box_hi], computed
+    by hydot_source_tree.
 
     Returns (order, root): `order` lists the source indices leaf by leaf (depth first, the side
     at or below the split coordinate first), and `root` is the tree whose nodes are ranges of
     positions in `order`."""
-    xy = np.asarray(xy, dtype=np.float64)
-    order: List[int] = []
+    xy = np.ascontiguousarray(np.asarray(xy, dtype=np.float64).reshape(-1, 2))
+    n = len(xy)
+    lib = _lib.load()
+    order = (C.c_int * n)()
+    nodes = (C.c_int * (8 * n))()
+    n_nodes, root = C.c_int(), C.c_int()
+    rc = lib.hydot_source_tree(xy.ctypes.data_as(C.POINTER(C.c_double)), n, float(box_lo[0]), float(box_lo[1]),
+                               float(box_hi[0]), float(box_hi[1]), int(leaf_max), order, nodes, C.byref(n_nodes),
+                               C.byref(root))
+    if rc != 0:
+        raise RuntimeError(lib.hydot_last_error(None).decode())
 
-    def split(idx: List[int], lo: np.ndarray, hi: np.ndarray, depth: int) -> Node:
-        start = len(order)
-        if len(idx) <= leaf_max or depth > 64:
-            order.extend(idx)
-            return Node(start, len(order))
-        j = int(np.argmax(hi - lo))                  # direction of maximum extent
-        gamma = 0.5 * (lo[j] + hi[j])                # split at the midpoint
-        t1 = [i for i in idx if xy[i, j] <= gamma]
-        t2 = [i for i in idx if xy[i, j] > gamma]
-        hi1, lo2 = hi.copy(), lo.copy()
-        hi1[j] = gamma
-        lo2[j] = gamma
-        kids = []
-        for t, a, b in ((t1, lo, hi1), (t2, lo2, hi)):
-            if t:
-                kids.append(split(t, a, b, depth + 1))
-        if len(kids) == 1:                           # every point on one side: that side is the node
-            return kids[0]
-        return Node(start, len(order), tuple(kids))
+    def node(i: int) -> Node:
+        lo, hi, c1, c2 = nodes[4 * i:4 * i + 4]
+        return Node(lo, hi) if c1 < 0 else Node(lo, hi, (node(c1), node(c2)))
 
-    root = split(list(range(len(xy))), np.asarray(box_lo, float), np.asarray(box_hi, float), 0)
-    return order, root
+    return list(order), node(root.value)
 
 
 def order_problem(problem):

@@ -21,6 +21,28 @@ def test_bisection_order_matches_oracle(n, seed):
     assert sorted(order) == list(range(n))
 
 
+def test_bisection_ties_duplicates_and_arguments():
+    """Positions on the split lines go to the first side, a wider-than-tall box splits in x first,
+    coincident positions end in one leaf once the depth limit is reached, and bad arguments are
+    rejected with a message."""
+    import ctypes as C
+    import paper_1410_0986_gb300._lib as L
+    grid = np.array([(x, y) for x in (0.0, 3.0, 6.0, 9.0, 12.0) for y in (0.0, 4.0, 8.0)])  # 5 x 3, on cuts
+    dup = np.vstack([grid, np.full((5, 2), 6.0)])                                             # five at one point
+    for pts, lo, hi in ((grid, (0.0, 0.0), (12.0, 8.0)), (dup, (0.0, 0.0), (12.0, 8.0))):
+        order, root = tree.bisection_order(pts, lo, hi)
+        ref = osk.geometric_bisection(pts, lo, hi)
+        assert [order[l.lo:l.hi] for l in root.leaves()] == osk.tree_leaves(ref)
+        assert root.depth() == osk.tree_depth(ref)
+    lib = L.load()
+    xy = np.zeros((1, 2))
+    ip = (C.c_int * 8)()
+    n, r = C.c_int(), C.c_int()
+    assert lib.hydot_source_tree(xy.ctypes.data_as(C.POINTER(C.c_double)), 0, 0.0, 0.0, 1.0, 1.0, 2, ip, ip,
+                                 C.byref(n), C.byref(r)) == L.HYDOT_ERR_ARG
+    assert "leaf_max" in lib.hydot_last_error(None).decode()
+
+
 def test_order_problem_permutes_sources_only():
     p = workloads.config(5)
     q, order, root = tree.order_problem(p)
