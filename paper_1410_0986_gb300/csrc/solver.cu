@@ -1266,34 +1266,63 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_dir_roll(Geo g, Batch b, con
 // are aligned.
 constexpr int TXP = 64;  // tile width of the paired-cell pass 1
 constexpr int BXP = 72;  // its box width: x0 - 4 .. x0 + 67
-template <int RP, int RS, int CY>
-constexpr size_t xp_smem() { return (size_t)RS * 2 * RP * (BXP * (TY * CY + 2)) * sizeof(float) + 128; }
+template <typename E, int RP, int RS, int CY>
+constexpr size_t xp_smem() { return (size_t)RS * 2 * RP * (BXP * (TY * CY + 2)) * sizeof(E) + 128; }
 
 // Diagonal of the cell with face mask m (bits: x low, x high, y low, y high, z low, z high) and its
-// inverse, as col_diag forms them.
+// inverse, as col_diag forms them (real, and complex: the face terms on the real part, sigma_im on
+// the imaginary part).
 __device__ __forceinline__ void cell_diag(const LamCoefF& cf, int m, float& d, float& di) {
   d = m ? diag_f(cf, m) : cf.dint;
   di = m ? 1.f / d : cf.idint;
 }
+__device__ __forceinline__ void cell_diag(const LamCoefF& cf, int m, float2& d, float2& di) {
+  const float re = m ? diag_f(cf, m) : cf.dint;
+  d = make_float2(re, cf.dim);
+  const float den = fmaf(re, re, cf.dim * cf.dim);
+  di = make_float2(re / den, -cf.dim / den);
+}
 __device__ __forceinline__ int zmask(int zb) { return ((zb & 1) << 4) | ((zb >> 1) << 5); }
 
-template <int RP, int RS, int CY, int MINB>
+// Two x-adjacent cells of element type E, moved as one 8-byte (real) or 16-byte (complex) word.
+template <typename E>
+struct CellPair;
+template <>
+struct CellPair<float> {
+  using T = float2;
+  static __device__ __forceinline__ float a(float2 p) { return p.x; }
+  static __device__ __forceinline__ float b(float2 p) { return p.y; }
+  static __device__ __forceinline__ float2 make(float u, float v) { return make_float2(u, v); }
+};
+template <>
+struct CellPair<float2> {
+  using T = float4;
+  static __device__ __forceinline__ float2 a(float4 p) { return make_float2(p.x, p.y); }
+  static __device__ __forceinline__ float2 b(float4 p) { return make_float2(p.z, p.w); }
+  static __device__ __forceinline__ float4 make(float2 u, float2 v) { return make_float4(u.x, u.y, v.x, v.y); }
+};
+
+template <typename E, int RP, int RS, int CY, int MINB>
 __global__ void __launch_bounds__(NTHREADS, MINB) k_dir_xp(Geo g, Batch b, const int* __restrict__ it_dev, int k,
                                                            int seg, const LamCoefF* __restrict__ coef_f,
                                                            const __grid_constant__ CUtensorMap mapR,
                                                            const __grid_constant__ CUtensorMap mapPold,
-                                                           float* __restrict__ Pnew) {
+                                                           E* __restrict__ Pnew) {
   static_assert(RS >= 3, "a slab buffer is refilled two slabs after its own");
+  constexpr bool CPLX = !std::is_same<E, float>::value;
+  constexpr int NV = CPLX ? 2 : 1;      // real and imaginary parts of gamma
+  using CP = CellPair<E>;
+  using PT = typename CP::T;
   constexpr int TYB = TY * CY;          // tile rows
   constexpr int PLB = BXP * (TYB + 2);  // elements in one box plane
   extern __shared__ unsigned char dsm[];
-  float* slab = align128<float>(dsm);  // [RS][r -> p_new, p_old][RP planes]
+  E* slab = align128<E>(dsm);  // [RS][r -> p_new, p_old][RP planes]
   __shared__ uint64_t mbar[RS];
-  __shared__ double sm[2 * CY * NWARPS];  // row sums per (8-row group, 32-column half, row)
+  __shared__ double sm[NV * 2 * CY * NWARPS];  // row sums per (part, 8-row group, 32-column half, row)
   __shared__ LamCoefF s_cf;
-  __shared__ float s_beta;
+  __shared__ E s_beta;
   __shared__ int s_go, s_st;
-  constexpr uint32_t SLAB_BYTES = RP * PLB * sizeof(float);
+  constexpr uint32_t SLAB_BYTES = RP * PLB * sizeof(E);
   const int it = *it_dev + k;
   const int ntxp = (g.nx + TXP - 1) / TXP;
   const int nty2 = (g.nty + CY - 1) / CY;
@@ -1314,7 +1343,7 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_dir_xp(Geo g, Batch b, const
   const int nfirst = min(RS, nslab);
   const uint32_t tx_bytes = (first ? 1u : 2u) * SLAB_BYTES;
   auto issue = [&](int q) {
-    float* dst = slab + (q % RS) * 2 * RP * PLB;
+    E* dst = slab + (q % RS) * 2 * RP * PLB;
     mbar_expect_tx(&mbar[q % RS], tx_bytes);
     tma_load_4d(dst, &mapR, &mbar[q % RS], x0 - 4, y0 - 1, z0 - 1 + q * RP, rhs);
     if (!first) tma_load_4d(dst + RP * PLB, &mapPold, &mbar[q % RS], x0 - 4, y0 - 1, z0 - 1 + q * RP, rhs);
@@ -1330,7 +1359,7 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_dir_xp(Geo g, Batch b, const
   }
   __syncthreads();
   if (s_st != RHS_INNER) return;
-  if (threadIdx.x < 32) dir_scalars<float>(b, pb, T_, it, rhs, lead, &s_go, &s_beta);
+  if (threadIdx.x < 32) dir_scalars<E>(b, pb, T_, it, rhs, lead, &s_go, &s_beta);
   if (threadIdx.x == 32) s_cf = coef_f[rhs_lambda(b, rhs)];
   __syncthreads();
   if (!s_go) {
@@ -1338,15 +1367,15 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_dir_xp(Geo g, Batch b, const
       for (int q = 0; q < nfirst; ++q) mbar_wait_bounded(&mbar[q % RS], 0u);
     return;
   }
-  const float beta = s_beta;
+  const E beta = s_beta;
   const LamCoefF& cf = s_cf;
 
   // own pairs (x0 + 2m + {0, 1}, y0 + ty + 8 c): face masks, interior-z diagonals and inverses
   const int m = threadIdx.x % 32, ty = threadIdx.x / 32;
-  const int i = x0 + 2 * m;  // even; i < nx implies i + 1 < nx (nx % 4 == 0)
+  const int i = x0 + 2 * m;  // even; i < nx implies i + 1 < nx (nx even on this path)
   bool in[CY];
   int ob[CY], msk[CY][2];
-  float d0[CY][2], i0[CY][2];
+  E d0[CY][2], i0[CY][2];
 #pragma unroll
   for (int c = 0; c < CY; ++c) {
     const int j = y0 + ty + TY * c;
@@ -1364,7 +1393,7 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_dir_xp(Geo g, Batch b, const
   const bool hpair = h < 2 * 32;
   const bool hcol = !hpair && h < 2 * 32 + 2 * TYB;
   int hb = 0, hm0 = 0, hm1 = 0;
-  float hi0 = 0.f, hi1 = 0.f;
+  E hi0{}, hi1{};
   if (hpair) {
     const int hx = 2 * (h % 32), hy = h < 32 ? -1 : TYB;
     hb = (hy + 1) * BXP + 4 + hx;
@@ -1380,74 +1409,75 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_dir_xp(Geo g, Batch b, const
     hm0 = (gi == 0) | ((gi == g.nx - 1) << 1) | ((gj == 0) << 2) | ((gj == g.ny - 1) << 3);
   }
   {
-    float dd;
+    E dd;
     cell_diag(cf, hm0, dd, hi0);
     cell_diag(cf, hm1, dd, hi1);
   }
   const int plane_n = g.nx * g.ny;
-  float* out = Pnew + (size_t)rhs * g.N + (size_t)(y0 + ty) * g.nx + i;
+  E* out = Pnew + (size_t)rhs * g.N + (size_t)(y0 + ty) * g.nx + i;
   const int row8 = TY * g.nx;  // offset of the cell eight rows further
-  float acc[CY][2];
-  float2 pm2[CY], pm1[CY];  // own p_new of the previous slab's last two planes
+  E acc[CY][2];
+  PT pm2[CY], pm1[CY];  // own p_new of the previous slab's last two planes
 #pragma unroll
   for (int c = 0; c < CY; ++c) {
-    acc[c][0] = acc[c][1] = 0.f;
-    pm2[c] = pm1[c] = make_float2(0.f, 0.f);
+    acc[c][0] = acc[c][1] = E{};
+    pm2[c] = pm1[c] = PT{};
   }
-  const float* prev = slab;
+  const E* prev = slab;
   for (int q = 0; q < nslab; ++q) {
-    float* cur = slab + (q % RS) * 2 * RP * PLB;
+    E* cur = slab + (q % RS) * 2 * RP * PLB;
     const bool ok = mbar_wait_bounded(&mbar[q % RS], (uint32_t)((q / RS) & 1));
     const int a0 = z0 - 1 + q * RP;  // first plane formed from this slab
-    float2 pv[CY][RP];
+    PT pv[CY][RP];
     // (B) p_new = D^-1 r + beta p_old in place (the product rounded on its own, as k_dir_roll)
     auto form = [&](auto edge) {
 #pragma unroll
       for (int u = 0; u < RP; ++u) {
         int zm = 0;
         if constexpr (decltype(edge)::value) zm = zmask((a0 + u == 0) | ((a0 + u == g.nz - 1) << 1));
-        float* pl = cur + u * PLB;
+        E* pl = cur + u * PLB;
 #pragma unroll
         for (int c = 0; c < CY; ++c) {
-          float ia = i0[c][0], ib = i0[c][1];
+          E ia = i0[c][0], ib = i0[c][1];
           if constexpr (decltype(edge)::value) {
             if (zm) {
-              float dd;
+              E dd;
               cell_diag(cf, msk[c][0] | zm, dd, ia);
               cell_diag(cf, msk[c][1] | zm, dd, ib);
             }
           }
-          const float2 rv = *reinterpret_cast<const float2*>(pl + ob[c]);
-          float2 v = make_float2(__fmul_rn(rv.x, ia), __fmul_rn(rv.y, ib));
+          const PT rv = *reinterpret_cast<const PT*>(pl + ob[c]);
+          E va = e_mul_rn(CP::a(rv), ia), vb = e_mul_rn(CP::b(rv), ib);
           if (!first) {
-            const float2 po = *reinterpret_cast<const float2*>(pl + RP * PLB + ob[c]);
-            v.x = fmaf(beta, po.x, v.x);
-            v.y = fmaf(beta, po.y, v.y);
+            const PT po = *reinterpret_cast<const PT*>(pl + RP * PLB + ob[c]);
+            va = e_fma(beta, CP::a(po), va);
+            vb = e_fma(beta, CP::b(po), vb);
           }
-          *reinterpret_cast<float2*>(pl + ob[c]) = v;
+          const PT v = CP::make(va, vb);
+          *reinterpret_cast<PT*>(pl + ob[c]) = v;
           pv[c][u] = v;
         }
         if (hpair || hcol) {
-          float ia = hi0, ib = hi1;
+          E ia = hi0, ib = hi1;
           if constexpr (decltype(edge)::value) {
             if (zm) {
-              float dd;
+              E dd;
               cell_diag(cf, hm0 | zm, dd, ia);
               cell_diag(cf, hm1 | zm, dd, ib);
             }
           }
           if (hpair) {
-            const float2 rv = *reinterpret_cast<const float2*>(pl + hb);
-            float2 v = make_float2(__fmul_rn(rv.x, ia), __fmul_rn(rv.y, ib));
+            const PT rv = *reinterpret_cast<const PT*>(pl + hb);
+            E va = e_mul_rn(CP::a(rv), ia), vb = e_mul_rn(CP::b(rv), ib);
             if (!first) {
-              const float2 po = *reinterpret_cast<const float2*>(pl + RP * PLB + hb);
-              v.x = fmaf(beta, po.x, v.x);
-              v.y = fmaf(beta, po.y, v.y);
+              const PT po = *reinterpret_cast<const PT*>(pl + RP * PLB + hb);
+              va = e_fma(beta, CP::a(po), va);
+              vb = e_fma(beta, CP::b(po), vb);
             }
-            *reinterpret_cast<float2*>(pl + hb) = v;
+            *reinterpret_cast<PT*>(pl + hb) = CP::make(va, vb);
           } else {
-            float v = __fmul_rn(pl[hb], ia);
-            if (!first) v = fmaf(beta, pl[RP * PLB + hb], v);
+            E v = e_mul_rn(pl[hb], ia);
+            if (!first) v = e_fma(beta, pl[RP * PLB + hb], v);
             pl[hb] = v;
           }
         }
@@ -1476,29 +1506,37 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_dir_xp(Geo g, Batch b, const
           if (zc < z0 || zc >= z1) continue;
           zm = zmask((zc == 0) | ((zc == g.nz - 1) << 1));
         }
-        const float* pl = (u == 0) ? prev + (RP - 1) * PLB : cur + (u - 1) * PLB;
+        const E* pl = (u == 0) ? prev + (RP - 1) * PLB : cur + (u - 1) * PLB;
 #pragma unroll
         for (int c = 0; c < CY; ++c) {
           if (!in[c]) continue;
           const int o = ob[c];
-          float da = d0[c][0], db = d0[c][1];
+          E da = d0[c][0], db = d0[c][1];
           if constexpr (decltype(edge)::value) {
             if (zm) {
-              float dummy;
+              E dummy;
               cell_diag(cf, msk[c][0] | zm, da, dummy);
               cell_diag(cf, msk[c][1] | zm, db, dummy);
             }
           }
-          const float2 below = (u == 0) ? pm2[c] : (u == 1 ? pm1[c] : pv[c][u - 2]);
-          const float2 centre = (u == 0) ? pm1[c] : pv[c][u - 1];
-          const float2 above = pv[c][u];
-          const float2 ylo = *reinterpret_cast<const float2*>(pl + o - BXP);
-          const float2 yhi = *reinterpret_cast<const float2*>(pl + o + BXP);
-          const float sa = ((pl[o - 1] + centre.y) + (ylo.x + yhi.x)) + (below.x + above.x);
-          const float sb = ((centre.x + pl[o + 2]) + (ylo.y + yhi.y)) + (below.y + above.y);
-          acc[c][0] = fmaf(centre.x, fmaf(da, centre.x, -sa), acc[c][0]);
-          acc[c][1] = fmaf(centre.y, fmaf(db, centre.y, -sb), acc[c][1]);
-          *reinterpret_cast<float2*>(out + (ptrdiff_t)zc * plane_n + c * row8) = centre;
+          const PT below = (u == 0) ? pm2[c] : (u == 1 ? pm1[c] : pv[c][u - 2]);
+          const PT centre = (u == 0) ? pm1[c] : pv[c][u - 1];
+          const PT above = pv[c][u];
+          const PT ylo = *reinterpret_cast<const PT*>(pl + o - BXP);
+          const PT yhi = *reinterpret_cast<const PT*>(pl + o + BXP);
+          const E ca = CP::a(centre), cb = CP::b(centre);
+          const E sa = e_add(e_add(e_add(pl[o - 1], cb), e_add(CP::a(ylo), CP::a(yhi))),
+                             e_add(CP::a(below), CP::a(above)));
+          const E sb = e_add(e_add(e_add(ca, pl[o + 2]), e_add(CP::b(ylo), CP::b(yhi))),
+                             e_add(CP::b(below), CP::b(above)));
+          if constexpr (CPLX) {
+            acc[c][0] = e_fma(ca, e_sub(e_mul(da, ca), sa), acc[c][0]);
+            acc[c][1] = e_fma(cb, e_sub(e_mul(db, cb), sb), acc[c][1]);
+          } else {
+            acc[c][0] = e_fma(ca, e_fma(da, ca, e_neg(sa)), acc[c][0]);
+            acc[c][1] = e_fma(cb, e_fma(db, cb, e_neg(sb)), acc[c][1]);
+          }
+          *reinterpret_cast<PT*>(out + (ptrdiff_t)zc * plane_n + c * row8) = centre;
         }
       }
     };
@@ -1511,20 +1549,22 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_dir_xp(Geo g, Batch b, const
     }
     prev = cur;
   }
-  // gamma per 32 x 8 column: each row's even and odd cells as shuffle trees over the half-warp
-  // (the first four steps of k_dir_roll's lane tree), then even + odd (its last step); the rows
-  // are summed in order in FP64 as block_sum does
+  // gamma per 32 x 8 column (each part): each row's even and odd cells as shuffle trees over the
+  // half-warp (the first four steps of k_dir_roll's lane tree), then even + odd (its last step); the
+  // rows are summed in order in FP64 as block_sum does
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int c = 0; c < CY; ++c) {
-    float ea = acc[c][0], oa = acc[c][1];
+  for (int c = 0; c < CY; ++c)
 #pragma unroll
-    for (int o = 8; o > 0; o >>= 1) {
-      ea += __shfl_down_sync(0xffffffffu, ea, o, 16);
-      oa += __shfl_down_sync(0xffffffffu, oa, o, 16);
+    for (int pv2 = 0; pv2 < NV; ++pv2) {
+      float ea = pv2 ? e_im(acc[c][0]) : e_re(acc[c][0]), oa = pv2 ? e_im(acc[c][1]) : e_re(acc[c][1]);
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) {
+        ea += __shfl_down_sync(0xffffffffu, ea, o, 16);
+        oa += __shfl_down_sync(0xffffffffu, oa, o, 16);
+      }
+      if ((lane & 15) == 0) sm[((pv2 * CY + c) * 2 + (lane >> 4)) * NWARPS + warp] = (double)(ea + oa);
     }
-    if ((lane & 15) == 0) sm[(2 * c + (lane >> 4)) * NWARPS + warp] = (double)(ea + oa);
-  }
   __syncthreads();
   const int nsl = (z1 - z0 + g.tz - 1) / g.tz;
   const int nyc = min(CY, g.nty - cy2 * CY), nxc = min(2, g.ntx - 2 * cx);
@@ -1536,11 +1576,14 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_dir_xp(Geo g, Batch b, const
     const int c = qc >> 1, hf = qc & 1;
     if (c < nyc && hf < nxc) {
       const int slot = (cy2 * CY + c) * g.ntx + 2 * cx + hf + (z0 / g.tz + zt) * ncol8;
-      double v = 0.0;
-      if (zt == 0)
-        for (int w = 0; w < NWARPS; ++w) v += sm[qc * NWARPS + w];
-      pb[6 * T_ + 2 * slot] = v;
-      pb[6 * T_ + 2 * slot + 1] = 0.0;
+      double vr = 0.0, vi = 0.0;
+      if (zt == 0) {
+        for (int w = 0; w < NWARPS; ++w) vr += sm[qc * NWARPS + w];
+        if constexpr (CPLX)
+          for (int w = 0; w < NWARPS; ++w) vi += sm[(CY * 2 + qc) * NWARPS + w];
+      }
+      pb[6 * T_ + 2 * slot] = vr;
+      pb[6 * T_ + 2 * slot + 1] = vi;
     }
   }
 }
@@ -2410,7 +2453,7 @@ __global__ void k_dsig(const double* __restrict__ dc, const double* __restrict__
 // {planes per slab, slab buffers}; the autotuner picks one per context (they give identical bits).
 // Complex64 slabs take twice the shared memory per plane, hence their own, shallower set; complex
 // variants 0 and 3 share the 2 x 4 slabs and differ in pass 1's register budget (three or four
-// blocks per SM).
+// blocks per SM), and variant 2 runs pass 1 on 64 x 8 tiles of paired cells (16-byte pairs).
 struct RollVariant {
   int rp, rs;
   int cy = 1;       // cells per thread in y (tiles of 32 x 8 cy, or 64 x 8 cy with xp)
@@ -2419,7 +2462,7 @@ struct RollVariant {
 // Real fields, pass 1 on: 32 x 8 tiles (variant 0); 64 x 8 tiles, x-pairs (1); 32 x 16 tiles, two
 // cells per thread (2); 64 x 16 tiles, two x-pairs per thread (3). Pass 2 runs on 32 x 8 tiles.
 constexpr RollVariant ROLL_VARIANTS[HYDOT_ROLL_VARIANTS] = {{4, 4, 1}, {2, 6, 1, true}, {2, 6, 2}, {2, 4, 2, true}};
-constexpr RollVariant ROLL_VARIANTS_C[HYDOT_ROLL_VARIANTS] = {{2, 4}, {2, 6}, {4, 3}, {2, 4}};
+constexpr RollVariant ROLL_VARIANTS_C[HYDOT_ROLL_VARIANTS] = {{2, 4}, {2, 6}, {2, 3, 1, true}, {2, 4}};
 
 __host__ __device__ constexpr int rp_index(int rp) { return rp == 2 ? 0 : (rp == 4 ? 1 : 2); }
 
@@ -2534,7 +2577,7 @@ void sweep_dispatch(hydot_ctx* ctx, int v, const Geo& g, const Batch& b, int k_o
 template <typename E, int RP, int RS, int CY, int MB1, int MB2, bool XP = false, int RS2 = RS>
 int roll_attrs(hydot_ctx* ctx) {
   if constexpr (XP) {
-    HYDOT_CUDA_TRY(ctx, raise_smem_limit(k_dir_xp<RP, RS, CY, MB1>, xp_smem<RP, RS, CY>()));
+    HYDOT_CUDA_TRY(ctx, raise_smem_limit(k_dir_xp<E, RP, RS, CY, MB1>, xp_smem<E, RP, RS, CY>()));
   } else {
     HYDOT_CUDA_TRY(ctx, raise_smem_limit(k_dir_roll<E, RP, RS, CY, MB1>, roll_smem<E, RP, RS, CY>()));
   }
@@ -2553,11 +2596,10 @@ void roll_iteration(hydot_ctx* ctx, const Geo& g, const Batch& b, int it, unsign
   cudaEvent_t t0 = timer_begin(ctx);
   const int o = it % POLL_GROUP;  // groups start at multiples of POLL_GROUP (even): parity of it = parity of o
   if constexpr (XP) {
-    static_assert(std::is_same<E, float>::value, "paired cells are a real-field layout");
     const unsigned nrb1 = (unsigned)((long long)b.nrhs * ((g.nx + TXP - 1) / TXP) * ((g.nty + CY - 1) / CY) *
                                      ((g.nz + seg - 1) / seg));
     const int c = CY - 1;
-    k_dir_xp<RP, RS, CY, MB1><<<nrb1, NTHREADS, xp_smem<RP, RS, CY>(), s>>>(
+    k_dir_xp<E, RP, RS, CY, MB1><<<nrb1, NTHREADS, xp_smem<E, RP, RS, CY>(), s>>>(
         g, b, ctx->d_it, o, seg, ctx->d_coef_f, ctx->tm_rx[c][k], ctx->tm_px[c][k][it & 1], P[(it + 1) & 1]);
   } else {
     const unsigned nrb1 = CY == 1 ? nrb : sweep_items(ctx, g, b, CY);
@@ -2589,7 +2631,7 @@ void roll_dispatch(hydot_ctx* ctx, int v, const Geo& g, const Batch& b, int it, 
     float2* p[2] = {(float2*)P[0], (float2*)P[1]};
     switch (v) {
       case 1: roll_iteration<float2, 2, 6, 1, 2, 2>(ctx, g, b, it, nrb, e, r, p); break;
-      case 2: roll_iteration<float2, 4, 3, 1, 2, 2>(ctx, g, b, it, nrb, e, r, p); break;
+      case 2: roll_iteration<float2, 2, 3, 1, 3, 3, true, 4>(ctx, g, b, it, nrb, e, r, p); break;
       case 3: roll_iteration<float2, 2, 4, 1, 4, 3>(ctx, g, b, it, nrb, e, r, p); break;
       default: roll_iteration<float2, 2, 4, 1, 3, 3>(ctx, g, b, it, nrb, e, r, p); break;
     }
@@ -2617,7 +2659,7 @@ int roll_setup(hydot_ctx* ctx) {
   if (ctx->cplx) {
     int rc = roll_attrs<float2, 2, 4, 1, 3, 3>(ctx);
     if (!rc) rc = roll_attrs<float2, 2, 6, 1, 2, 2>(ctx);
-    if (!rc) rc = roll_attrs<float2, 4, 3, 1, 2, 2>(ctx);
+    if (!rc) rc = roll_attrs<float2, 2, 3, 1, 3, 3, true, 4>(ctx);
     if (!rc) rc = roll_attrs<float2, 2, 4, 1, 4, 3>(ctx);
     return rc;
   }
@@ -3162,10 +3204,12 @@ int solver_alloc(hydot_ctx* ctx) {
       rc = encode_field_map(ctx, ctx->d_r, &ctx->tm_rh[k], BXT, BYT, bz);
       if (!rc) rc = encode_field_map(ctx, ctx->d_p[0], &ctx->tm_ph[k][0], BXT, BYT, bz);
       if (!rc) rc = encode_field_map(ctx, ctx->d_p[1], &ctx->tm_ph[k][1], BXT, BYT, bz);
-      if (!rc && !ctx->cplx) {  // pass 1 on 32 x 16 tiles, and on 64 x 8 / 64 x 16 tiles (real fields)
+      if (!rc && !ctx->cplx) {  // pass 1 on 32 x 16 tiles (real fields)
         rc = encode_field_map(ctx, ctx->d_r, &ctx->tm_rh2[k], BXT, 2 * TY + 2, bz);
         if (!rc) rc = encode_field_map(ctx, ctx->d_p[0], &ctx->tm_ph2[k][0], BXT, 2 * TY + 2, bz);
         if (!rc) rc = encode_field_map(ctx, ctx->d_p[1], &ctx->tm_ph2[k][1], BXT, 2 * TY + 2, bz);
+      }
+      if (!rc) {  // pass 1 on paired cells: 64 x 8 and 64 x 16 tiles
         for (int c = 0; c < 2 && !rc; ++c) {
           rc = encode_field_map(ctx, ctx->d_r, &ctx->tm_rx[c][k], BXP, (c + 1) * TY + 2, bz);
           if (!rc) rc = encode_field_map(ctx, ctx->d_p[0], &ctx->tm_px[c][k][0], BXP, (c + 1) * TY + 2, bz);

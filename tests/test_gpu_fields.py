@@ -209,8 +209,9 @@ def test_frequency_domain_roll_variants_and_graphs_bitwise(hd, monkeypatch):
             out.append((ps, pd))
     for ps, pd in out[1:]:
         assert torch.equal(ps, out[0][0]) and torch.equal(pd, out[0][1])
-    # variant 3: the 2 x 4 slabs of variant 0 with four blocks per SM for pass 1
-    assert [(v["planes"], v["buffers"]) for v in tu["variants"]] == [(2, 4), (2, 6), (4, 3), (2, 4)]
+    # variant 3: the 2 x 4 slabs of variant 0 with four blocks per SM for pass 1; variant 2: pass 1
+    # on 64 x 8 tiles of paired complex cells
+    assert [(v["planes"], v["buffers"]) for v in tu["variants"]] == [(2, 4), (2, 6), (2, 3), (2, 4)]
 
 
 def test_wavelength_slice_and_single_sets(hd, oracle_fields):
