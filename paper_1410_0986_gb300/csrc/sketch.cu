@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(RG_THREADS, 1)
     // The eight lanes of a 16-byte load phase read chunks ch = 0..7 of one row: lanes with ch >= 4
     // read their chunk's second half first, so that the phase's eight 16-byte words fall on distinct
     // bank groups (ch * 32 + 16 * (ch >> 2) mod 128 is a permutation of 16 * 0..7); [0] is the half
-    // read first, and the products keep that order until the store puts the halves in place.
+    // read first, and the products are stored in that order.
     const int f = tid - 64;
     const int rows = a.S_a * a.D_t;
     const int nsrc = 2 * a.S_a;
@@ -359,8 +359,9 @@ __global__ void __launch_bounds__(RG_THREADS, 1)
             const uint32_t p1 = pack_bf16x2(sv[i][0].z * dv[j][0].z, sv[i][0].w * dv[j][0].w);
             const uint32_t p2 = pack_bf16x2(sv[i][1].x * dv[j][1].x, sv[i][1].y * dv[j][1].y);
             const uint32_t p3 = pack_bf16x2(sv[i][1].z * dv[j][1].z, sv[i][1].w * dv[j][1].w);
-            const uint4 pk = h0 ? make_uint4(p2, p3, p0, p1) : make_uint4(p0, p1, p2, p3);
-            sts_v4(At + acc * SK_A_BYTES + sw128_offset(rr, ch * 8), pk);
+            // chunks ch >= 4 keep the order they were read in (second half first): M_l's K order
+            // within those chunks is the same (k_form_mt)
+            sts_v4(At + acc * SK_A_BYTES + sw128_offset(rr, ch * 8), make_uint4(p0, p1, p2, p3));
           }
         }
       }
@@ -689,6 +690,10 @@ __global__ void k_form_qc_padded(const float* __restrict__ Q, long long ldq, con
 }
 
 // Mt[l][k][x] = sum_c eps_c(lambda_(lam0+l)) * Omega_t[c][k][x] in BF16 (k >= ncols: 0); 8 voxels per thread.
+// Within each 64-voxel K-step, 8-voxel chunks 4..7 are stored with their halves swapped (voxels 4..7,
+// then 0..3): the range pass's A formers read those chunks' halves in that order (a bank-conflict
+// rule) and store their products as read; the K order of A and B is permuted alike, so the product
+// A B^T is unchanged.
 __global__ void k_form_mt(const __nv_bfloat16* __restrict__ om, const double* __restrict__ eps, int lam0, int nlam,
                           int nc, int ncols, long long N, __nv_bfloat16* __restrict__ Mt) {
   const long long nv = N / 8;
@@ -716,6 +721,7 @@ __global__ void k_form_mt(const __nv_bfloat16* __restrict__ om, const double* __
     out.y = pack_bf16x2(acc[2], acc[3]);
     out.z = pack_bf16x2(acc[4], acc[5]);
     out.w = pack_bf16x2(acc[6], acc[7]);
+    if ((xv & 7) >= 4) out = make_uint4(out.z, out.w, out.x, out.y);
     *reinterpret_cast<uint4*>(Mt + ((size_t)l * SK_N + k) * N + xv * 8) = out;
   }
 }
