@@ -275,9 +275,13 @@ template <typename X>
 __global__ void __launch_bounds__(SG_T) k_sg_x0(const float* __restrict__ V, long long ldf, long long N,
                                                 const float* __restrict__ Y, int nf, int f_begin, int l0, int nl, int m,
                                                 const int* __restrict__ meff, X* __restrict__ x64) {
-  __shared__ float ys[SG_LB][SG_MAXM];
+  // coefficients as ys[a][l] (zero for l >= nl): the 16 of one basis vector are four 16-byte loads
+  __shared__ __align__(16) float ys[SG_MAXM][SG_LB];
   const int fl = blockIdx.y, f = f_begin + fl;
-  for (int e = threadIdx.x; e < nl * m; e += SG_T) ys[e / m][e % m] = Y[((size_t)(l0 + e / m) * nf + fl) * m + e % m];
+  for (int e = threadIdx.x; e < SG_LB * m; e += SG_T) {
+    const int l = e / m, a = e % m;
+    ys[a][l] = l < nl ? Y[((size_t)(l0 + l) * nf + fl) * m + a] : 0.f;
+  }
   __syncthreads();
   const int me = meff[f];
   const float* vf = V + (size_t)f * ldf;
@@ -287,8 +291,15 @@ __global__ void __launch_bounds__(SG_T) k_sg_x0(const float* __restrict__ V, lon
     for (int l = 0; l < SG_LB; ++l) acc[l] = 0.f;
     for (int a = 0; a < me; ++a) {
       const float v = vf[(size_t)a * N + x];
+      const float4* y4 = reinterpret_cast<const float4*>(ys[a]);
 #pragma unroll
-      for (int l = 0; l < SG_LB; ++l) acc[l] = fmaf(v, ys[l][a], acc[l]);
+      for (int q = 0; q < SG_LB / 4; ++q) {
+        const float4 c = y4[q];
+        acc[4 * q] = fmaf(v, c.x, acc[4 * q]);
+        acc[4 * q + 1] = fmaf(v, c.y, acc[4 * q + 1]);
+        acc[4 * q + 2] = fmaf(v, c.z, acc[4 * q + 2]);
+        acc[4 * q + 3] = fmaf(v, c.w, acc[4 * q + 3]);
+      }
     }
 #pragma unroll
     for (int l = 0; l < SG_LB; ++l) {
