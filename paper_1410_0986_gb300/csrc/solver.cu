@@ -3030,9 +3030,13 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
     // any field still marked INNER hit the per-cycle cap: finish it
     {
       dim3 fg((unsigned)std::min<long long>((g.N + 2047) / 2048, 1024), (unsigned)std::min(b.nrhs, 65535));  // 8 cells per thread
-      // fields that were still iterating when the cap hit are FINISHED by the next k_dir; run it
-      k_dir<T><<<nblk, blk, 0, s>>>(g, b, MAX_INNER_PER_CYCLE, R, P[0], P[1]);
-      ++ctx->launches;
+      // fields that were still iterating when the cap hit are FINISHED by a k_dir at the cap; a
+      // launched loop that stopped on a zero count of iterating fields left none (the persistent
+      // form may stop at the cap itself)
+      if (!stop || persistent) {
+        k_dir<T><<<nblk, blk, 0, s>>>(g, b, MAX_INNER_PER_CYCLE, R, P[0], P[1]);
+        ++ctx->launches;
+      }
       k_fold<T, X><<<fg, 256, 0, s>>>(g, b, x64, E);
       ++ctx->launches;
       HYDOT_CUDA_TRY(ctx, cudaGetLastError());
