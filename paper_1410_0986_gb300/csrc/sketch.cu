@@ -6,11 +6,13 @@
 //   pass 2 (projection):  B^T[(c,x), k] += -h^3 sum_(s,d,l) eps_c(lambda_l) phi_s(x) phi_d(x) Q[(s,d,l), k]
 //                         (summing over wavelength slices merges the row blocks)
 //
-// Both passes are one BF16 x BF16 -> FP32 tcgen05 GEMM with a 128 x 224 accumulator in tensor
-// memory: the A tile (the Hadamard product of a source and a detector field) is formed by the
-// CTA's threads straight into shared memory in the 128-byte swizzled K-major layout, the B tile
-// (M_l or eps-scaled Q, prepared once per call in BF16) arrives by TMA with the same swizzle, and
-// one thread issues the MMAs. Two pipeline stages; every mbarrier wait is bounded.
+// Both passes are BF16 x BF16 -> FP32 tcgen05 GEMMs with two 128 x 224 accumulators in tensor
+// memory: the A tiles (Hadamard products of source and detector fields) are formed by the CTA's
+// threads straight into shared memory in the 128-byte swizzled K-major layout, the B tiles (M_l or
+// eps-scaled Q, prepared once per call in BF16) arrive by TMA with the same swizzle, and one
+// thread issues the MMAs. Multi-stage mbarrier pipelines (the range pass: three operand stages and
+// two A stages; the projection: four B stages, two A stages, two field buffers); every wait is
+// bounded. The general-shape projection kernel below is a simpler two-stage form.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
