@@ -214,6 +214,24 @@ def test_frequency_domain_roll_variants_and_graphs_bitwise(hd, monkeypatch):
     assert [(v["planes"], v["buffers"]) for v in tu["variants"]] == [(2, 4), (2, 6), (2, 3), (2, 4)]
 
 
+def test_frequency_domain_variants_on_z_segments_bitwise(hd, monkeypatch):
+    """Complex fields on blocks that own z-segments of 8 planes (a ragged last segment over nz = 21)
+    and on a grid whose 64-wide paired-cell tiles are ragged (nx = 52): the four complex variants,
+    the paired-cell one included, give the same bits, and every field converges."""
+    monkeypatch.setenv("HYDOT_DIR_SEG", "8")
+    p = workloads.make_problem(workloads.Grid(52, 19, 21, 2.0), 3, 2, 2, seed=26, geometry="transmission",
+                               freq_mhz=100.0)
+    out = []
+    for v in range(4):
+        monkeypatch.setenv("HYDOT_ROLL_VARIANT", str(v))
+        with hd.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=1e-8) as ctx:
+            ps, pd, st = ctx.solve_fields(0, p.n_lambda)
+            assert ctx.tuning()["variant"] == v and st["n_not_converged"] == 0
+        out.append((ps, pd))
+    for ps, pd in out[1:]:
+        assert torch.equal(ps, out[0][0]) and torch.equal(pd, out[0][1])
+
+
 def test_wavelength_slice_and_single_sets(hd, oracle_fields):
     p, (rs, rd) = oracle_fields["reflection-13x11x9"]
     with hd.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=1e-8, max_lambda_per_call=2) as ctx:
