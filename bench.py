@@ -317,7 +317,7 @@ def run_ours(args):
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "refinement_dtype": "f64", "data": "synthetic (seeded; workloads.config(2))",
+        "dtype": "f32", "refinement_dtype": "df32 (double-float iterate and residual: FP32 pairs; per-field scalars in f64)", "data": "synthetic (seeded; workloads.config(2))",
         "config": {"workload": WORKLOAD, "step": "one 16-wavelength chunk: 1,024 solves + 16,384 Born rows + J x + "
                    "J^T r", "grid": [64, 64, 48], "n_src": ns, "n_det": nd, "n_lambda": p.n_lambda,
                    "chunk_lambda": CHUNK, "tol_cw": TOL_CW, "cw_floor": CW_FLOOR, "tol": 1e-10, "deflation_k": args.deflation_k,
