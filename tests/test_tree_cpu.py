@@ -9,12 +9,12 @@ from oracle import sketch as osk
 from paper_1410_0986_gb300 import tree
 
 
-@pytest.mark.parametrize("n,seed", [(7, 1), (37, 2), (64, 3), (2, 4)])
-def test_bisection_order_matches_oracle(n, seed):
+@pytest.mark.parametrize("n,seed,leaf", [(7, 1, 2), (37, 2, 2), (64, 3, 2), (2, 4, 2), (50, 5, 1), (50, 6, 5)])
+def test_bisection_order_matches_oracle(n, seed, leaf):
     rng = np.random.default_rng(seed)
     pts = rng.uniform(0.0, 12.0, size=(n, 2))
-    order, root = tree.bisection_order(pts, (0.0, 0.0), (12.0, 12.0))
-    ref = osk.geometric_bisection(pts, (0.0, 0.0), (12.0, 12.0))
+    order, root = tree.bisection_order(pts, (0.0, 0.0), (12.0, 12.0), leaf_max=leaf)
+    ref = osk.geometric_bisection(pts, (0.0, 0.0), (12.0, 12.0), max_leaf=leaf)
     leaves = [order[l.lo:l.hi] for l in root.leaves()]
     assert leaves == osk.tree_leaves(ref)
     assert root.depth() == osk.tree_depth(ref)
