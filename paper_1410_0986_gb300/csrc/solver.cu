@@ -405,10 +405,23 @@ __device__ __forceinline__ void residual_partials(const Geo& g, const Batch& b, 
 // The same pass for the mixed real path, whose iterate is double-float (df32). Per cell the
 // residual r = b - (d x_c - sum of the six neighbours) is a short signed sum; it is accumulated as
 // s + c: the high parts enter through TwoSum (exact), the low parts and the TwoSum errors through
-// the FP32 compensation c (the compensated summation of Ogita, Rump & Oishi), and each diagonal
+// the FP32 compensation c (the compensated summation of Ogita, Rump & Oishi), and the diagonal
 // product d x_c through the exact FMA product. The error of r is then ~n^2 2^-48 (|Ahat||x|)_i
 // (n <= 9 terms), far below the componentwise target, with FP32 operations only. r is rounded to
 // FP32 for the norm, the exponent bound and the inner right-hand side, which need no more.
+// What does not change down a column is set up once per thread: the diagonal of its x and y faces
+// (a double-float sum for the residual; in FP32, in the face order of diag_at, for the Jacobi
+// weight of rho_0, with its reciprocal). The per-cell body is compiled once per kind of plane
+// (interior, k = 0, k = nz - 1, both): the z faces belong to whole planes, the same plane for
+// every thread of a block, so interior planes carry no face terms at all. GEN selects the body
+// with a per-cell absorption shift or a general right-hand side; the common case (a unit point
+// source, no shift) is compiled without either.
+template <int ZF>
+struct ZFace {
+  static constexpr bool lo = (ZF & 1) != 0, hi = (ZF & 2) != 0;
+};
+
+template <bool GEN>
 __global__ void __launch_bounds__(NTHREADS) k_residual_df(Geo g, Batch b, const LamCoefF* __restrict__ coef_f,
                                                           const df32* __restrict__ x64, float* __restrict__ R) {
   extern __shared__ __align__(16) unsigned char rsm_raw[];
@@ -416,19 +429,8 @@ __global__ void __launch_bounds__(NTHREADS) k_residual_df(Geo g, Batch b, const 
   __shared__ int smi[NWARPS];
   TileCoord c = tile_coord(g);
   if (b.status[c.rhs] != RHS_FINISHED) return;
-  // coefficients from the FP32 table (no FP64 arithmetic in this kernel): the diagonal of an
-  // interior cell and the face terms as double-floats
+  // coefficients from the FP32 table (no FP64 arithmetic in this kernel)
   const LamCoefF cf = coef_f[rhs_lambda(b, c.rhs)];
-  DiagT<float> dgi;
-  dgi.dre = cf.dint;
-  dgi.dim = 0.f;
-#pragma unroll
-  for (int f = 0; f < 6; ++f) dgi.fa[f] = cf.fa[f];
-  const float idint = cf.idint;
-  const df32 d0{cf.dint, cf.dint_lo};
-  df32 dfa[6];
-#pragma unroll
-  for (int f = 0; f < 6; ++f) dfa[f] = df32{cf.fa[f], cf.fa_lo[f]};
   const long long src = rhs_source(b, c.rhs);
   const float pre = 1.f / (float)b.next[c.rhs];
   const int etheta = bexp(b.theta[c.rhs]);
@@ -453,23 +455,32 @@ __global__ void __launch_bounds__(NTHREADS) k_residual_df(Geo g, Batch b, const 
   if (c.in) {
     const int li = (int)(threadIdx.x % TX) + 1, lj = (int)(threadIdx.x / TX) + 1;
     const int mxy = face_mask(g, c.i, c.j, 0) & 15;  // the x and y faces of the column
+    df32 dcol{cf.dint, cf.dint_lo};
+    float axy = 0.f;
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+      if (mxy & (1 << f)) {
+        dcol = df_add(dcol, df32{cf.fa[f], cf.fa_lo[f]});
+        axy += cf.fa[f];
+      }
+    const float wcol = mxy ? 1.f / (cf.dint + axy) : cf.idint;
     const long long plane = (long long)g.nx * g.ny;
     long long id = vidx(g, c.i, c.j, c.k0);
-    for (int k = c.k0; k < c.k1; ++k, id += plane) {
-      const df32* xq = xs + ((k - c.k0 + 1) * SY + lj) * SX + li;
+    const df32* xq = xs + (SY + lj) * SX + li;
+    auto cell = [&](auto zf) {
+      constexpr bool zlo = decltype(zf)::lo, zhi = decltype(zf)::hi;
       const df32 xc = xq[0];
-      const int m = mxy | ((k == 0) << 4) | ((k == g.nz - 1) << 5);
       // A x = d x_c - sum of the neighbours, as s + cc (neighbours outside the grid are zero)
       float s, cc;
-      two_prod(d0.hi, xc.hi, s, cc);
-      cc = fmaf(d0.hi, xc.lo, fmaf(d0.lo, xc.hi, cc));
-      if (m) {
-#pragma unroll
-        for (int f = 0; f < 6; ++f)
-          if (m & (1 << f)) add_prod(s, cc, dfa[f], xc);
-      }
-      if (b.dsig_d) add_prod(s, cc, df_from(dsig_at<double>(b, c.rhs, id, g.N)), xc);
-      float amax = 0.f;  // largest |neighbour|: the denominator's exponent comes from it once
+      two_prod(dcol.hi, xc.hi, s, cc);
+      cc = fmaf(dcol.hi, xc.lo, fmaf(dcol.lo, xc.hi, cc));
+      if constexpr (zlo) add_prod(s, cc, df32{cf.fa[4], cf.fa_lo[4]}, xc);
+      if constexpr (zhi) add_prod(s, cc, df32{cf.fa[5], cf.fa_lo[5]}, xc);
+      if constexpr (GEN)
+        if (b.dsig_d) add_prod(s, cc, df_from(dsig_at<double>(b, c.rhs, id, g.N)), xc);
+      // the denominator's exponent comes once from the largest of |d x_c| >= 4 |x_c| and the
+      // neighbours' moduli
+      float amax = 4.f * fabsf(xc.hi);
       auto sub_nb = [&](df32 v) {
         float t;
         two_sum(s, -v.hi, s, t);
@@ -485,7 +496,7 @@ __global__ void __launch_bounds__(NTHREADS) k_residual_df(Geo g, Batch b, const 
       // r = b - A x
       float rh = -s, rl = -cc;
       int eb = 0;  // binary exponent of |b| at this cell (0: b is zero here)
-      if (b.rhs_slot) {
+      if (GEN && b.rhs_slot) {
         const double bv = rhs_value(b, c.rhs, id, src);
         if (bv != 0.0) {
           const df32 bd = df_from(bv);
@@ -502,18 +513,31 @@ __global__ void __launch_bounds__(NTHREADS) k_residual_df(Geo g, Batch b, const 
       }
       const float rf = rh + rl;
       rr = fmaf(rf, rf, rr);
-      int ed = max(etheta, bexp_f(amax));
-      const int ec = bexp(xc);
-      ed = max(ed, ec ? ec + 2 : 0);
-      if (eb) ed = max(ed, eb);
+      const int ed = max(max(etheta, bexp_f(amax)), eb);
       const int er = bexp_f(rf);
       if (er) om_e = max(om_e, ed ? er + 1 - ed : 4096);
       const float rv = rf * pre;
       r[id] = rv;
-      const float dinv = (m || b.dsig_f) ? 1.f / (diag_at<float>(dgi, m) + (b.dsig_f ? dsig_at<float>(b, c.rhs, id, g.N) : 0.f))
-                                         : idint;
+      // the Jacobi weight 1 / d_i: the column's, except on z-face planes and with a per-cell shift
+      float dinv = wcol;
+      if constexpr (zlo || zhi || GEN) {
+        float a = axy;
+        if constexpr (zlo) a += cf.fa[4];
+        if constexpr (zhi) a += cf.fa[5];
+        const int m = mxy | (zlo << 4) | (zhi << 5);
+        const bool sh = GEN && b.dsig_f;
+        if (m || sh) dinv = 1.f / ((m ? cf.dint + a : cf.dint) + (sh ? dsig_at<float>(b, c.rhs, id, g.N) : 0.f));
+        else dinv = cf.idint;
+      }
       acc[0] = fmaf(rv * dinv, rv, acc[0]);
       acc[2] = fmaf(rv, rv, acc[2]);
+    };
+    for (int k = c.k0; k < c.k1; ++k, id += plane, xq += SX * SY) {
+      const int zf = (k == 0) | ((k == g.nz - 1) << 1);  // the same for the whole block
+      if (zf == 0) cell(ZFace<0>{});
+      else if (zf == 1) cell(ZFace<1>{});
+      else if (zf == 2) cell(ZFace<2>{});
+      else cell(ZFace<3>{});
     }
   }
   float v4[4] = {rr, acc[0], 0.f, acc[2]};
@@ -528,6 +552,9 @@ __global__ void __launch_bounds__(NTHREADS) k_residual_df(Geo g, Batch b, const 
 // compensation for the rest, exact FMA products for the diagonal terms). The exponent bound of
 // the componentwise backward error takes the larger part of each complex number and one more
 // bit for |z| <= sqrt(2) max(|re|, |im|), as the FP64 kernel does.
+// The diagonal and D^-1 of a column are set up once, and the per-cell body is compiled per kind
+// of plane and with or without a per-cell shift (GEN), as in k_residual_df.
+template <bool GEN>
 __global__ void __launch_bounds__(NTHREADS) k_residual_cdf(Geo g, Batch b, const LamCoefF* __restrict__ coef_f,
                                                            const cdf32* __restrict__ x64, float2* __restrict__ R) {
   extern __shared__ __align__(16) unsigned char rsm_raw[];
@@ -563,33 +590,46 @@ __global__ void __launch_bounds__(NTHREADS) k_residual_cdf(Geo g, Batch b, const
   if (c.in) {
     const int li = (int)(threadIdx.x % TX) + 1, lj = (int)(threadIdx.x / TX) + 1;
     const int mxy = face_mask(g, c.i, c.j, 0) & 15;
-    const long long plane = (long long)g.nx * g.ny;
-    long long id = vidx(g, c.i, c.j, c.k0);
-    for (int k = c.k0; k < c.k1; ++k, id += plane) {
-      const cdf32* xq = xs + ((k - c.k0 + 1) * SY + lj) * SX + li;
-      const cdf32 xc = xq[0];
-      const int m = mxy | ((k == 0) << 4) | ((k == g.nz - 1) << 5);
-      float sr, cr, si, ci;
-      two_prod(d0.hi, xc.re.hi, sr, cr);
-      cr = fmaf(d0.hi, xc.re.lo, fmaf(d0.lo, xc.re.hi, cr));
-      two_prod(d0.hi, xc.im.hi, si, ci);
-      ci = fmaf(d0.hi, xc.im.lo, fmaf(d0.lo, xc.im.hi, ci));
-      if (m) {
+    df32 dcol = d0;
+    float dre_col = cf.dint;  // the real diagonal in FP32, faces added in order
 #pragma unroll
-        for (int f = 0; f < 6; ++f)
-          if (m & (1 << f)) {
-            add_prod(sr, cr, dfa[f], xc.re);
-            add_prod(si, ci, dfa[f], xc.im);
-          }
+    for (int f = 0; f < 4; ++f)
+      if (mxy & (1 << f)) {
+        dcol = df_add(dcol, dfa[f]);
+        dre_col += cf.fa[f];
       }
-      if (b.dsig_d) {
-        const df32 ds = df_from(dsig_at<double>(b, c.rhs, id, g.N));
-        add_prod(sr, cr, ds, xc.re);
-        add_prod(si, ci, ds, xc.im);
+    const float den_col = fmaf(dre_col, dre_col, cf.dim * cf.dim);
+    const float2 dinv_col = make_float2(dre_col / den_col, -cf.dim / den_col);
+    const long long plane = (long long)g.nx * g.ny;
+    const long long col = vidx(g, c.i, c.j, 0);
+    long long id = col + (long long)c.k0 * plane;
+    const cdf32* xq = xs + (SY + lj) * SX + li;
+    auto cell = [&](auto zf) {
+      constexpr bool zlo = decltype(zf)::lo, zhi = decltype(zf)::hi;
+      const cdf32 xc = xq[0];
+      float sr, cr, si, ci;
+      two_prod(dcol.hi, xc.re.hi, sr, cr);
+      cr = fmaf(dcol.hi, xc.re.lo, fmaf(dcol.lo, xc.re.hi, cr));
+      two_prod(dcol.hi, xc.im.hi, si, ci);
+      ci = fmaf(dcol.hi, xc.im.lo, fmaf(dcol.lo, xc.im.hi, ci));
+      if constexpr (zlo) {
+        add_prod(sr, cr, dfa[4], xc.re);
+        add_prod(si, ci, dfa[4], xc.im);
       }
+      if constexpr (zhi) {
+        add_prod(sr, cr, dfa[5], xc.re);
+        add_prod(si, ci, dfa[5], xc.im);
+      }
+      if constexpr (GEN)
+        if (b.dsig_d) {
+          const df32 ds = df_from(dsig_at<double>(b, c.rhs, id, g.N));
+          add_prod(sr, cr, ds, xc.re);
+          add_prod(si, ci, ds, xc.im);
+        }
       add_prod(sr, cr, ndsi, xc.im);
       add_prod(si, ci, dsi, xc.re);
-      float amax = 0.f;
+      // |d x_c| >= 4 max(|re|, |im|) enters the denominator's exponent with the neighbours
+      float amax = 4.f * fmaxf(fabsf(xc.re.hi), fabsf(xc.im.hi));
       auto sub_nb = [&](const cdf32& v) {
         float t;
         two_sum(sr, -v.re.hi, sr, t);
@@ -605,36 +645,43 @@ __global__ void __launch_bounds__(NTHREADS) k_residual_cdf(Geo g, Batch b, const
       sub_nb(xq[-SX]);
       sub_nb(xq[SX]);
       float rh = -sr, rl = -cr;
+      int ed = max(etheta, bexp_f(amax));
       if (id == src) {
         float t;
         two_sum(1.f, rh, rh, t);
         rl += t;
+        ed = max(ed, 1023);
       }
       const float fr = rh + rl, fi = -si + -ci;
       rr = fmaf(fr, fr, fmaf(fi, fi, rr));
-      int ed = max(etheta, bexp_f(amax));
-      const int ec = max(bexp(xc.re), bexp(xc.im));
-      ed = max(ed, ec ? ec + 2 : 0);
-      if (id == src) ed = max(ed, 1023);
       const int er = max(bexp_f(fr), bexp_f(fi));
       if (er) om_e = max(om_e, ed ? er + 2 - ed : 4096);
       const float2 rv = make_float2(fr * pre, fi * pre);
       r[id] = rv;
       // D^-1 of the cell: the real diagonal (faces, absorption perturbation) plus i sigma_im
-      float dre = cf.dint;
-      if (m) {
-#pragma unroll
-        for (int f = 0; f < 6; ++f)
-          if (m & (1 << f)) dre += cf.fa[f];
+      float2 dinv = dinv_col;
+      if constexpr (zlo || zhi || GEN) {
+        float dre = dre_col;
+        if constexpr (zlo) dre += cf.fa[4];
+        if constexpr (zhi) dre += cf.fa[5];
+        if (GEN && b.dsig_f) dre += dsig_at<float>(b, c.rhs, id, g.N);
+        if (zlo || zhi || (GEN && b.dsig_f)) {
+          const float den = fmaf(dre, dre, cf.dim * cf.dim);
+          dinv = make_float2(dre / den, -cf.dim / den);
+        }
       }
-      if (b.dsig_f) dre += dsig_at<float>(b, c.rhs, id, g.N);
-      const float den = fmaf(dre, dre, cf.dim * cf.dim);
-      const float2 dinv = make_float2(dre / den, -cf.dim / den);
       // rho_0 = r^T D^-1 r (bilinear), ||r||^2
       const float2 zr = make_float2(fmaf(rv.x, dinv.x, -rv.y * dinv.y), fmaf(rv.x, dinv.y, rv.y * dinv.x));
       acc[0] = fmaf(rv.x, zr.x, fmaf(-rv.y, zr.y, acc[0]));
       acc[1] = fmaf(rv.x, zr.y, fmaf(rv.y, zr.x, acc[1]));
       acc[2] = fmaf(rv.x, rv.x, fmaf(rv.y, rv.y, acc[2]));
+    };
+    for (int k = c.k0; k < c.k1; ++k, id += plane, xq += SX * SY) {
+      const int zf = (k == 0) | ((k == g.nz - 1) << 1);  // the same for the whole block
+      if (zf == 0) cell(ZFace<0>{});
+      else if (zf == 1) cell(ZFace<1>{});
+      else if (zf == 2) cell(ZFace<2>{});
+      else cell(ZFace<3>{});
     }
   }
   float v4[4] = {rr, acc[0], acc[1], acc[2]};
@@ -2859,10 +2906,14 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
     HYDOT_CUDA_TRY(ctx, cudaMemsetAsync(x64, 0, sizeof(X) * (size_t)b.nrhs * g.N, s));
   }
   HYDOT_CUDA_TRY(ctx, cudaMemsetAsync(b.err, 0, sizeof(int), s));
-  if constexpr (std::is_same<X, df32>::value)  // the residual's halo tile: up to 18 x 10 x 34 double-floats
-    HYDOT_CUDA_TRY(ctx, raise_smem_limit(k_residual_df, sizeof(df32) * (g.tz + 2) * (TY + 2) * (TX + 2)));
-  if constexpr (std::is_same<X, cdf32>::value)
-    HYDOT_CUDA_TRY(ctx, raise_smem_limit(k_residual_cdf, sizeof(cdf32) * (g.tz + 2) * (TY + 2) * (TX + 2)));
+  if constexpr (std::is_same<X, df32>::value) {  // the residual's halo tile: up to 18 x 10 x 34 double-floats
+    HYDOT_CUDA_TRY(ctx, raise_smem_limit(k_residual_df<false>, sizeof(df32) * (g.tz + 2) * (TY + 2) * (TX + 2)));
+    HYDOT_CUDA_TRY(ctx, raise_smem_limit(k_residual_df<true>, sizeof(df32) * (g.tz + 2) * (TY + 2) * (TX + 2)));
+  }
+  if constexpr (std::is_same<X, cdf32>::value) {
+    HYDOT_CUDA_TRY(ctx, raise_smem_limit(k_residual_cdf<false>, sizeof(cdf32) * (g.tz + 2) * (TY + 2) * (TX + 2)));
+    HYDOT_CUDA_TRY(ctx, raise_smem_limit(k_residual_cdf<true>, sizeof(cdf32) * (g.tz + 2) * (TY + 2) * (TX + 2)));
+  }
   k_reset<<<(b.nrhs + 255) / 256, 256, 0, s>>>(b);
   ++ctx->launches;
   HYDOT_CUDA_TRY(ctx, cudaGetLastError());
@@ -2875,12 +2926,22 @@ int run_solve(hydot_ctx* ctx, int lam0, int nlam, O* phi_src, O* phi_det, hydot_
       ++ctx->launches;
     }
     cudaEvent_t t_res = timer_begin(ctx);
-    if constexpr (std::is_same<X, df32>::value)
-      k_residual_df<<<nblk, blk, sizeof(df32) * (g.tz + 2) * (TY + 2) * (TX + 2), s>>>(g, b, ctx->d_coef_f, x64, R);
-    else if constexpr (std::is_same<X, cdf32>::value)
-      k_residual_cdf<<<nblk, blk, sizeof(cdf32) * (g.tz + 2) * (TY + 2) * (TX + 2), s>>>(g, b, ctx->d_coef_f, x64,
-                                                                                        (float2*)R);
-    else k_residual<T, X><<<nblk, blk, 0, s>>>(g, b, x64, R);
+    if constexpr (std::is_same<X, df32>::value) {
+      // the general body only where a field has a per-cell shift or a general right-hand side
+      const size_t sm_df = sizeof(df32) * (g.tz + 2) * (TY + 2) * (TX + 2);
+      if (b.dsig_d || b.dsig_f || b.rhs_slot)
+        k_residual_df<true><<<nblk, blk, sm_df, s>>>(g, b, ctx->d_coef_f, x64, R);
+      else
+        k_residual_df<false><<<nblk, blk, sm_df, s>>>(g, b, ctx->d_coef_f, x64, R);
+    } else if constexpr (std::is_same<X, cdf32>::value) {
+      const size_t sm_c = sizeof(cdf32) * (g.tz + 2) * (TY + 2) * (TX + 2);
+      if (b.dsig_d || b.dsig_f)
+        k_residual_cdf<true><<<nblk, blk, sm_c, s>>>(g, b, ctx->d_coef_f, x64, (float2*)R);
+      else
+        k_residual_cdf<false><<<nblk, blk, sm_c, s>>>(g, b, ctx->d_coef_f, x64, (float2*)R);
+    } else {
+      k_residual<T, X><<<nblk, blk, 0, s>>>(g, b, x64, R);
+    }
     ++ctx->launches;
     timer_end(ctx, t_res, HYDOT_KERNEL_RESIDUAL,
               (double)(cycle == 0 ? b.nrhs : prev_active) * (double)g.N * (double)(sizeof(X) + sizeof(T)));
