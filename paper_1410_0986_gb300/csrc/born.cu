@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(256) k_born_rows_scalar(const E* __restrict__ 
 // Block partials go to a workspace and a second kernel sums them in a fixed order.
 constexpr int AP_XC = 128;   // voxels per stage
 constexpr int AP_STAGES = 8; // stages per block of the allocation-free entry point (the library picks
-                              // 4 .. 32 per problem, see apply_spb)
+                              // 4 .. 64 per problem, see apply_spb)
 constexpr int AP_NBUF = 3;    // stage buffers: two stages in flight while one is contracted
 
 template <typename E>
@@ -420,12 +420,33 @@ cudaError_t launch_apply_partial_u(int u, dim3 grid, cudaStream_t st, const E* p
 
 // stages (of AP_XC voxels) per J x block: the largest of 32, 16, 8 that leaves at least four waves
 // of two blocks per SM (fewer, longer blocks mean fewer partial sums and block epilogues), else 4
-int apply_spb(long long N, int nlam, int ntiles) {
-  for (int spb : {32, 16, 8}) {
-    const long long nxb = (N + (long long)spb * AP_XC - 1) / ((long long)spb * AP_XC);
-    if (nxb * nlam * ntiles >= 4LL * 2 * 152) return spb;
+// Stages per block of the J x kernel. Its blocks are bound by instruction issue on their SM, so a
+// partial last wave of blocks takes as long as a full one: the count chosen is the one with the
+// fewest whole waves x (stages per block + about two stages of per-block cost: the pipeline fill,
+// the block reduction and its partial write). 1,536 blocks of 16 stages on 304 resident slots
+// (5.05 waves) take as long as six full waves; 608 blocks of 41 stages fill two.
+int apply_spb(long long N, int nlam, int ntiles, int resident) {
+  const long long nst = (N + AP_XC - 1) / AP_XC;
+  int best = 4;
+  double best_t = 0.0;
+  for (int spb = 4; spb <= 64; ++spb) {
+    const long long nxb = (nst + spb - 1) / spb;
+    const long long waves = (nxb * nlam * ntiles + resident - 1) / resident;
+    const double t = (double)waves * (spb + 2.0);
+    if (spb == 4 || t < best_t) best = spb, best_t = t;
   }
-  return 4;
+  return best;
+}
+
+// resident blocks of the J x kernel on this GPU for tile parameter u (the launch bounds fix the
+// blocks per SM: two at u = 8 and three below in FP32, one in FP64)
+template <typename E>
+int apply_resident(int u) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      sms <= 0)
+    sms = 152;
+  return sms * (u == 8 ? apply_min_blocks<E, 8>() : apply_min_blocks<E, 6>());
 }
 
 // ---------------------------------------------------------------- J^T y
@@ -757,7 +778,7 @@ int apply_t(hydot_ctx* ctx, const E* ps, const E* pd, int lam0, int nlam, const 
   const int ns = ctx->n_src, nd = ctx->n_det, nc = ctx->n_chrom;
   const int u = apply_u(ns, nd), tw = 4 * u;
   const int nts = (ns + tw - 1) / tw, ntd = (nd + tw - 1) / tw;
-  const int spb = apply_spb(N, nlam, nts * ntd);
+  const int spb = apply_spb(N, nlam, nts * ntd, apply_resident<E>(u));
   const long long per_blk = (long long)AP_XC * spb;
   const int nxb = (int)((N + per_blk - 1) / per_blk);
   size_t bytes = sizeof(E) * (size_t)nlam * nts * ntd * nxb * 1024;

@@ -251,6 +251,21 @@ def test_degenerate_single_plane_grid(hd):
     assert rel_err(ps, rs) <= 1e-10 and rel_err(pd, rd) <= 1e-10
 
 
+@pytest.mark.parametrize("freq", [0.0, 100.0])
+@pytest.mark.parametrize("nz", [1, 2])
+def test_thin_grids_mixed_precision(hd, nz, freq):
+    """nz = 1 and 2 on the mixed path (continuous-wave and frequency domain): the double-float
+    residual compiles its per-cell body per kind of plane, and on these grids every plane is a
+    z-face plane (both faces at nz = 1, the lower and then the upper face at nz = 2); an odd nx
+    keeps the launched generic passes. Dense brute-force oracle."""
+    p = workloads.small(seed=30 + nz, nx=9, ny=7, nz=nz, n_src=2, n_det=2, n_lambda=2, freq_mhz=freq)
+    rs, rd = osolve.fields_dense(p)
+    with hd.Context.from_problem(p, precision="mixed", tol=1e-10, tol_cw=1e-8) as ctx:
+        ps, pd, st = ctx.solve_fields(0, 2)
+    assert st["n_not_converged"] == 0 and st["cw_max"] <= 1e-8
+    assert rel_err(ps, rs) <= 1e-6 and rel_err(pd, rd) <= 1e-6
+
+
 def test_single_cell_grid(hd):
     """1x1x1: the field is 1 / (mu_a h^3 + six face terms)."""
     p = workloads.make_problem(workloads.Grid(1, 1, 1, 2.0), 1, 0, 2, seed=4, geometry="reflection", margin=0)
