@@ -217,7 +217,8 @@ int hydot_born_apply_noalloc(long long N, int n_src, int n_det, int n_chrom, int
 typedef enum {
   HYDOT_KERNEL_DIR = 0,        /* inner PCG pass 1: p = D^-1 r + beta p, gamma = p^T A p */
   HYDOT_KERNEL_UPDATE = 1,     /* inner PCG pass 2: x += alpha p, r -= alpha A p, rho */
-  HYDOT_KERNEL_RESIDUAL = 2,   /* FP64 residual and refinement test, once per cycle */
+  HYDOT_KERNEL_RESIDUAL = 2,   /* residual of the refinement iterate (double-float on the mixed
+                                * paths, FP64 on the FP64 paths) and its test, once per cycle */
   HYDOT_KERNEL_BORN_ROWS = 3,  /* Born-row assembly */
   HYDOT_KERNEL_APPLY = 4,      /* J x (partial sums) */
   HYDOT_KERNEL_APPLY_T = 5,    /* J^T y (partial sums) */
