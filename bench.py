@@ -7,7 +7,7 @@ solves, an explicit FP32 Born matrix of 131,072 x 786,432 assembled in row chunk
 implicit products J x and J^T r. Synthetic, seeded inputs (workloads.config(2)).
 
 One step = one 16-wavelength chunk of that workload, the whole hot path over it:
-  1. 1,024 field solves (FP32 PCG, FP64 residuals and refinement to a componentwise backward
+  1. 1,024 field solves (FP32 PCG, double-float residuals and refinement to a componentwise backward
      error <= 1e-8 with the Born-aware floor, so that Born entries meet 1e-5 of their row maximum),
   2. the chunk's 16,384 Born rows (FP32, 4,096-row launches into a reused 12.9 GB buffer),
   3. y = J x for the chunk (x = a seeded ellipsoidal anomaly),

@@ -418,13 +418,11 @@ cudaError_t launch_apply_partial_u(int u, dim3 grid, cudaStream_t st, const E* p
   }
 }
 
-// stages (of AP_XC voxels) per J x block: the largest of 32, 16, 8 that leaves at least four waves
-// of two blocks per SM (fewer, longer blocks mean fewer partial sums and block epilogues), else 4
-// Stages per block of the J x kernel. Its blocks are bound by instruction issue on their SM, so a
-// partial last wave of blocks takes as long as a full one: the count chosen is the one with the
-// fewest whole waves x (stages per block + about two stages of per-block cost: the pipeline fill,
-// the block reduction and its partial write). 1,536 blocks of 16 stages on 304 resident slots
-// (5.05 waves) take as long as six full waves; 608 blocks of 41 stages fill two.
+// Stages (of AP_XC voxels) per block of the J x kernel. Its blocks are bound by instruction issue
+// on their SM, so a partial last wave of blocks takes as long as a full one: the count chosen is
+// the one with the fewest whole waves x (stages per block + about two stages of per-block cost: the
+// pipeline fill, the block reduction and its partial write). 1,536 blocks of 16 stages on 304
+// resident slots (5.05 waves) take as long as six full waves; 608 blocks of 41 stages fill two.
 int apply_spb(long long N, int nlam, int ntiles, int resident) {
   const long long nst = (N + AP_XC - 1) / AP_XC;
   int best = 4;

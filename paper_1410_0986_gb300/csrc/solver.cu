@@ -1,5 +1,6 @@
 // Batched field solves: matrix-free FV diffusion operator, Jacobi-preconditioned CG (COCG for
-// the complex-symmetric frequency-domain operator) with FP64 residuals and iterative refinement.
+// the complex-symmetric frequency-domain operator) with iterative refinement: on the mixed paths FP32
+// inner solves and a double-float iterate and residual, on the FP64 paths FP64 throughout.
 //
 // Each simultaneous field ("rhs") solves  Ahat x = e_cell  with Ahat = A_j / (D_j h) (the
 // operator of eqn:discincident restated as finite volumes, see hydot.h); the field is
