@@ -235,15 +235,13 @@ __global__ void __launch_bounds__(256, apply_min_blocks<E, U>()) k_apply_partial
   if (NB == 3 && nstage > 1) load(1, buf0 + be);
   for (int st = 0; st < nstage; ++st) {
     E* b = buf0 + (st % NB) * be;
-    if (st + NB - 1 < nstage) {
-      load(st + NB - 1, buf0 + ((st + NB - 1) % NB) * be);
-      cp_async_wait<NB - 1>();
-    } else if (NB == 3 && st + 1 < nstage) {
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
+    // stage st has landed (the copies still pending are stage st's and, with three buffers, the
+    // next one's); after the barrier every thread is done with stage st - 1, whose buffer the copy
+    // issued next refills, so one barrier per stage orders both
+    if (NB == 3 && st + 1 < nstage) cp_async_wait<1>();
+    else cp_async_wait<0>();
     __syncthreads();
+    if (st + NB - 1 < nstage) load(st + NB - 1, buf0 + ((st + NB - 1) % NB) * be);
     const E* S = b;
     const E* D = b + TILE * LD;
     const E* X = b + 2 * TILE * LD;
@@ -310,7 +308,6 @@ __global__ void __launch_bounds__(256, apply_min_blocks<E, U>()) k_apply_partial
           for (int v = 0; v < U; ++v) acc[u][v] += sv[u] * dv[v];
       }
     }
-    __syncthreads();  // this buffer is refilled by the load issued in the next iteration
   }
   // tree reduction over the 16 voxel groups (fixed order -> deterministic)
   for (int half = 8; half >= 1; half >>= 1) {
@@ -632,15 +629,12 @@ __global__ void __launch_bounds__(256, 2) k_apply_T_tile(const float* __restrict
         fs[j] = sb + j < ns ? *reinterpret_cast<const float4*>(sp + (size_t)j * N) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     float* b = buf0 + (k % TT_NBUF) * TT_STAGE_FLOATS;
-    if (k + TT_NBUF - 1 < nstage) {
-      load(buf0 + ((k + TT_NBUF - 1) % TT_NBUF) * TT_STAGE_FLOATS);
-      cp_async_wait<TT_NBUF - 1>();
-    } else if (TT_NBUF == 3 && k + 1 < nstage) {
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
+    // stage k has landed; after the barrier every thread is done with stage k - 1, whose buffer
+    // the copy issued next refills (one barrier per stage)
+    if (TT_NBUF == 3 && k + 1 < nstage) cp_async_wait<1>();
+    else cp_async_wait<0>();
     __syncthreads();
+    if (k + TT_NBUF - 1 < nstage) load(buf0 + ((k + TT_NBUF - 1) % TT_NBUF) * TT_STAGE_FLOATS);
     const float* Dt = b + 4 * q;
     const float* Yt = b + (size_t)TT_DC * TT_XC + g * 8;
     const int dn = min(TT_DC, nd - dc * TT_DC);
@@ -661,7 +655,6 @@ __global__ void __launch_bounds__(256, 2) k_apply_T_tile(const float* __restrict
         W[j][3] = fmaf(yv[j], f.w, W[j][3]);
       }
     }
-    __syncthreads();  // this buffer is refilled by the load issued in the next iteration
     if (dc == ndc - 1) {
 #pragma unroll
       for (int j = 0; j < SPT; ++j) {
